@@ -1,0 +1,329 @@
+"""Pins for the CPU oracle, against facts fixed outside the oracle itself.
+
+The oracle (``oracle/``) states what the GPU path must compute.  These tests
+tie each of its functions to something independent: a published test vector
+(splitmix64), the exact value of Eq. 1 within binary32 rounding, closed forms
+of the result on graph families, exhaustive enumeration on tiny graphs, the
+greedy characterisation of the round iteration's result, and the paper's
+printed worked-example numbers (Sec. 3.1).
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_29604_gb300 import graphgen as gg
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+GAMMA = 0x9E3779B97F4A7C15
+M64 = (1 << 64) - 1
+
+
+def _members(status):
+    return set(np.flatnonzero(status).tolist())
+
+
+def _solve(g, seed):
+    n, rp, col = g
+    key = oracle.keys(n, rp, seed)
+    return key, oracle.rounds(n, rp, col, key)
+
+
+# ---------------------------------------------------------------- Eq. 1 pieces
+
+def test_splitmix64_matches_published_vector():
+    want = [int(x) for x in open(os.path.join(GOLDEN, "splitmix64_seed1234567.txt"))
+            if x.strip() and not x.startswith("#")]
+    x = 1234567
+    got = []
+    for _ in range(5):
+        x = (x + GAMMA) & M64
+        got.append(oracle.splitmix64_mix(x))
+    assert got == want
+
+
+def test_eps_range_and_grid():
+    # eps must lie in [0, 1) on the 2^-24 grid, and look uniform over ids
+    vals = np.array([oracle.eps(7, v) for v in range(20000)])
+    assert vals.min() >= 0.0 and vals.max() < 1.0
+    assert np.all(vals * 2**24 == np.floor(vals * 2**24))
+    assert abs(vals.mean() - 0.5) < 0.01
+    assert abs(np.mean(vals < 0.25) - 0.25) < 0.015
+    # different seeds decorrelate the perturbation
+    other = np.array([oracle.eps(8, v) for v in range(20000)])
+    assert np.mean(other == vals) < 0.01
+
+
+def test_eps_uses_high_bits_of_double_mix():
+    # eps is the top 24 bits of mix(mix(seed) ^ v) scaled to [0, 1): with the
+    # finaliser pinned by the published vector above, check the composition
+    # on a few values by reading bit fields, not by recomputing Eq. 1.
+    for seed, v in [(0, 0), (1, 5), (12345, 777), (2**63 + 11, 2**31 - 1)]:
+        h = oracle.splitmix64_mix(oracle.splitmix64_mix(seed) ^ v)
+        top24 = h >> 40
+        assert oracle.eps(seed, v) == top24 / 2**24
+
+
+@pytest.mark.parametrize("seed", [1, 99, 2024])
+def test_priority_is_eq1_within_binary32_rounding(seed):
+    # Exact rational value of Eq. 1 at the binary32 inputs, versus the
+    # oracle's three round-to-nearest operations: relative error <= ~3 u.
+    rng = np.random.default_rng(seed)
+    u = Fraction(1, 2**24)
+    for _ in range(400):
+        dbar = float(np.float32(rng.uniform(0.5, 200.0)))
+        deg = int(rng.integers(1, 100000))
+        e = float(rng.integers(0, 2**24)) / 2**24
+        p = oracle.priority(dbar, deg, e)
+        exact = Fraction(dbar) / (Fraction(dbar) + deg - Fraction(e))
+        assert abs(Fraction(p) - exact) <= 4 * u * exact
+        # the perturbation enters with the sign that raises P (Eq. 1)
+        assert Fraction(p) >= Fraction(dbar) / (Fraction(dbar) + deg) * (1 - 4 * u)
+        assert Fraction(p) <= Fraction(dbar) / (Fraction(dbar) + deg - 1) * (1 + 4 * u)
+
+
+def test_keys_degree_monotone_and_isolated():
+    n, rp, col = gg.rmat(12, 8, 0.57, 0.19, 0.19, seed=5, permute=True)
+    key = oracle.keys(n, rp, 3)
+    deg = np.diff(rp)
+    iso = deg == 0
+    assert iso.any()
+    assert np.all(key[iso] == 0xFFFFFFFF)
+    k = key[~iso].view(np.float32).astype(np.float64)
+    d = deg[~iso]
+    # deg1 < deg2 implies P1 >= P2 (eps < 1 keeps degree classes apart)
+    order = np.argsort(d, kind="stable")
+    ds, ks = d[order], k[order]
+    for lo, hi in zip(np.unique(ds)[:-1], np.unique(ds)[1:]):
+        assert ks[ds == lo].min() >= ks[ds == hi].max()
+    # P in (0, 1]
+    assert k.min() > 0 and k.max() <= 1.0
+    # dbar is arcs / n
+    dbar = float(np.float32(np.float32(rp[-1]) / np.float32(n)))
+    v = int(np.flatnonzero(~iso)[0])
+    e = oracle.eps(3, v)
+    exact = Fraction(dbar) / (Fraction(dbar) + int(deg[v]) - Fraction(e))
+    assert abs(Fraction(float(key[v:v + 1].view(np.float32)[0])) - exact) <= 4 * exact / 2**24
+
+
+# ---------------------------------------------------------------- round rule
+
+def test_worked_example_sec31():
+    # Build a graph consistent with the printed numbers: vertex 1 (P=73) with
+    # neighbours of priority <= 45 (one of them 45); vertex 5 adjacent to
+    # vertex 1 and holding a larger id than nothing else that matters.
+    lines = [l.split() for l in open(os.path.join(GOLDEN, "worked_example_sec31.txt"))
+             if l.strip() and not l.startswith("#")]
+    v1 = dict(zip(lines[0][::2], lines[0][1::2]))
+    v5 = dict(zip(lines[1][::2], lines[1][1::2]))
+    assert v1["vertex"] == "1" and v5["vertex"] == "5"
+    # vertices 0..5; edges 1-2 (P 45), 1-3 (P 20), 1-5 (P 30), 5-4 (P 10), 0-2
+    n, rp, col = gg.from_edges(6, [1, 1, 1, 5, 0], [2, 3, 5, 4, 2])
+    key = np.array([50, int(v1["P"]), int(v1["max_np"]), 20, 10, 30], dtype=np.uint32)
+    res = oracle.rounds(n, rp, col, key)
+    st = res.status
+    assert int(v1["candidate"]) == 1 and st[1] == 1
+    assert int(v5["in_mis"]) == 0 and st[5] == 0
+    # round 1: candidates are 1 (73 > 45) and 0 (50 > 45); 5 is excluded
+    assert res.alive_per_round[0] == 6
+    assert res.alive_per_round[1] == 1  # only vertex 4 (P=10, neighbour 5 gone) remains
+    assert st.tolist() == [1, 1, 0, 0, 1, 0]
+
+
+def test_ties_broken_by_larger_id():
+    # all keys equal: the order is by id, larger id first; on a path
+    # 0-1-...-(n-1) the result is {n-1, n-3, ...}
+    n, rp, col = gg.path(9)
+    key = np.full(n, 1000, dtype=np.uint32)
+    st = oracle.rounds(n, rp, col, key).status
+    assert _members(st) == {8, 6, 4, 2, 0}
+    n, rp, col = gg.path(8)
+    key = np.full(n, 1000, dtype=np.uint32)
+    assert _members(oracle.rounds(n, rp, col, key).status) == {7, 5, 3, 1}
+    assert _members(oracle.greedy(n, rp, col, key)) == {7, 5, 3, 1}
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 40])
+def test_complete_graph(k):
+    g = gg.complete(k)
+    key, res = _solve(g, 11)
+    best = max(range(k), key=lambda v: (int(key[v]), v))
+    assert _members(res.status) == {best}
+
+
+def test_empty_graph():
+    g = gg.empty(17)
+    key, res = _solve(g, 1)
+    assert res.status.tolist() == [1] * 17
+    assert res.rounds == 1
+    assert np.all(key == 0xFFFFFFFF)
+
+
+@pytest.mark.parametrize("k", [3, 4, 10, 200])
+def test_star_gives_leaves(k):
+    g = gg.star(k)
+    for seed in range(5):
+        _, res = _solve(g, seed)
+        assert _members(res.status) == set(range(1, k + 1))
+
+
+@pytest.mark.parametrize("a,b", [(1, 3), (2, 4), (3, 7), (5, 20)])
+def test_complete_bipartite_low_degree_side(a, b):
+    g = gg.complete_bipartite(a, b)
+    for seed in range(4):
+        _, res = _solve(g, seed)
+        assert _members(res.status) == set(range(a, a + b))
+
+
+@pytest.mark.parametrize("a", [1, 2, 6])
+def test_complete_bipartite_balanced(a):
+    g = gg.complete_bipartite(a, a)
+    for seed in range(4):
+        key, res = _solve(g, seed)
+        best = max(range(2 * a), key=lambda v: (int(key[v]), v))
+        side = set(range(a)) if best < a else set(range(a, 2 * a))
+        assert _members(res.status) == side
+
+
+@pytest.mark.parametrize("n", [2, 3, 7, 50, 501])
+def test_path(n):
+    g = gg.path(n)
+    for seed in range(3):
+        _, res = _solve(g, seed)
+        m = _members(res.status)
+        if n >= 3:
+            assert 0 in m and n - 1 in m  # degree-1 ends beat their degree-2 neighbours
+        assert math.ceil(n / 3) <= len(m) <= math.ceil(n / 2)
+
+
+@pytest.mark.parametrize("n", [3, 4, 9, 100, 1001])
+def test_cycle(n):
+    g = gg.cycle(n)
+    for seed in range(3):
+        _, res = _solve(g, seed)
+        m = len(_members(res.status))
+        assert math.ceil(n / 3) <= m <= n // 2 or (n == 3 and m == 1)
+
+
+def test_disjoint_union_with_per_graph_keys():
+    parts = [gg.er_gnm(300, 900, 1), gg.star(5), gg.cycle(30), gg.rgg(400, 10.0, 2),
+             gg.empty(3), gg.complete(6)]
+    seeds = [3, 4, 5, 6, 7, 8]
+    n, rp, col = gg.disjoint_union(parts)
+    keys = np.concatenate([oracle.keys(p[0], p[1], s) for p, s in zip(parts, seeds)])
+    res = oracle.rounds(n, rp, col, keys)
+    want = np.concatenate([_solve(p, s)[1].status for p, s in zip(parts, seeds)])
+    assert np.array_equal(res.status, want)
+
+
+# ---------------------------------------------------------------- brute force
+
+def _lex_first_by_priority(n, key, sets):
+    """Among all maximal independent sets, the one whose membership vector,
+    read in decreasing (key, id) order, is lexicographically largest."""
+    order = sorted(range(n), key=lambda v: (int(key[v]), v), reverse=True)
+    return max(sets, key=lambda s: [(s >> v) & 1 for v in order])
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_brute_force_small(seed):
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(1, 15))
+    p = float(rng.uniform(0.05, 0.8))
+    g = gg.random_small(n, p, seed)
+    key, res = _solve(g, seed)
+    sets = oracle.brute_force_mis(*g)
+    mask = sum(1 << v for v in _members(res.status))
+    assert mask in sets
+    assert mask == _lex_first_by_priority(n, key, sets)
+    assert res.rounds <= n
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_brute_force_n20(seed):
+    g = gg.random_small(20, 0.18, 77 + seed)
+    key, res = _solve(g, seed)
+    sets = oracle.brute_force_mis(*g)
+    mask = sum(1 << v for v in _members(res.status))
+    assert mask == _lex_first_by_priority(20, key, sets)
+
+
+def test_brute_force_enumeration_counts():
+    # closed forms for the number of maximal independent sets:
+    # empty graph 1, K_n n, path P_n Padovan-like recurrence, cycle C_n Perrin numbers
+    assert len(oracle.brute_force_mis(*gg.empty(6))) == 1
+    assert len(oracle.brute_force_mis(*gg.complete(7))) == 7
+    # P_n: 1, 2, 2, 3, 4, 5, 7, 9, 12, 16 for n = 1..10 (a(n) = a(n-2) + a(n-3))
+    assert [len(oracle.brute_force_mis(*gg.path(n))) for n in range(2, 11)] == \
+        [2, 2, 3, 4, 5, 7, 9, 12, 16]
+    # C_n: Perrin numbers 3, 2, 5, 5, 7, 10, 12, 17 for n = 3..10
+    assert [len(oracle.brute_force_mis(*gg.cycle(n))) for n in range(3, 11)] == \
+        [3, 2, 5, 5, 7, 10, 12, 17]
+
+
+# ---------------------------------------------------------------- greedy + invariants
+
+GRAPHS = {
+    "er": lambda: gg.er_gnm(3000, 12000, 4),
+    "rmat": lambda: gg.rmat(13, 16, 0.57, 0.19, 0.19, 9, permute=True),
+    "grid": lambda: gg.grid_diag(60, 0.05, 2),
+    "grid_perm": lambda: gg.grid_diag(60, 0.05, 2, permute=True),
+    "rgg": lambda: gg.rgg(4000, 10.0, 3),
+    "dense": lambda: gg.random_small(200, 0.4, 6),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_rounds_equal_greedy_and_valid(name, seed):
+    n, rp, col = GRAPHS[name]()
+    key, res = _solve((n, rp, col), seed)
+    assert oracle.check(n, rp, col, res.status) == (0, -1)
+    assert np.array_equal(res.status, oracle.greedy(n, rp, col, key))
+    assert res.work >= rp[-1]
+    assert res.rounds <= n
+    assert res.alive_per_round[0] == n
+    assert np.all(np.diff(res.alive_per_round) < 0)
+
+
+def test_check_catches_planted_mistakes():
+    n, rp, col = gg.er_gnm(500, 1500, 8)
+    _, res = _solve((n, rp, col), 1)
+    st = res.status.copy()
+    assert oracle.check(n, rp, col, st)[0] == 0
+    # add a neighbour of a member: independence breaks
+    v = int(np.flatnonzero(st)[0])
+    u = int(col[rp[v]])
+    bad = st.copy()
+    bad[u] = 1
+    assert oracle.check(n, rp, col, bad)[0] == 1
+    # drop a member whose neighbours are all outside: maximality breaks
+    bad = st.copy()
+    bad[v] = 0
+    code, where = oracle.check(n, rp, col, bad)
+    assert code == 2
+
+
+def test_round_count_follows_snapshot_rule():
+    # Hand-computed: on the path 0-1-2-3 with priorities 1, 4, 3, 2 round 1
+    # selects {1} and removes {0, 2}; vertex 3 is blocked by 2 in the round-1
+    # snapshot, so it joins only in round 2.  An implementation that updated
+    # the alive set in place during candidate selection (no snapshot, against
+    # the H3 ordering of Sec. 3.3) could finish in one round.
+    n, rp, col = gg.path(4)
+    key = np.array([1, 4, 3, 2], dtype=np.uint32)
+    res = oracle.rounds(n, rp, col, key)
+    assert _members(res.status) == {1, 3}
+    assert res.rounds == 2
+
+
+def test_min_degree_greedy_valid():
+    for g in (gg.er_gnm(2000, 8000, 1), gg.star(9), gg.rgg(1500, 10.0, 1)):
+        size, st = oracle.min_degree_greedy(*g)
+        assert oracle.check(*g, st) == (0, -1)
+        assert size == int(st.sum())
+    size, st = oracle.min_degree_greedy(*gg.star(9))
+    assert size == 9 and st[0] == 0
