@@ -1,0 +1,220 @@
+/*
+ * tcmis.h -- C ABI of the GB300 (sm_103a) TC-MIS library, libtcmis.so.
+ *
+ * The library computes a maximal independent set (MIS) of an undirected,
+ * unweighted graph with the round-synchronous, priority-based iteration of
+ * TC-MIS (Nijhara & Banerjee), Algorithm 2:
+ *
+ *   priorities   P(v) = d / (d + deg(v) - eps(v))                  (Eq. 1, Sec. 2)
+ *                d = average degree, eps(v) in [0, 1) a hashed perturbation;
+ *                assigned once per solve and reused every round (Sec. 2).
+ *   while A != {}:                                                 (Algorithm 2)
+ *     Phase 1  C(v) = [P(v) > max over alive neighbours u of P(u)]  (selection test)
+ *     Phase 2  N_c = A x C                                         (exclusion test)
+ *     Phase 3  v joins the set if C(v) = 1; v leaves A if C(v) = 1 or N_c(v) > 0.
+ *
+ * Every phase of one round reads the state at the start of that round (the
+ * H3 ordering of Sec. 3.3).  The result is therefore unique for a given
+ * (graph, seed): it is the set that sequential greedy in decreasing priority
+ * order produces.  Every path of the library (CSR kernel, tile kernels,
+ * tensor-core kernel, batched and served solves) returns exactly that set.
+ *
+ * Exact priority rule (binary32, round-to-nearest, no FMA contraction):
+ *   d      = float(row_ptr[n]) / float(n)        (arcs counted in both directions)
+ *   h      = high 32 bits of mix(mix(seed) XOR v), mix = splitmix64 finaliser
+ *   eps    = float(h >> 8) * 2^-24
+ *   P      = d / ((d + float(deg(v))) - eps)
+ *   ties in P are broken by the larger vertex id.
+ *
+ * Graph input contract (checked by mis_create*, violations give MIS_EINVAL):
+ *   0 <= n < 2^31; row_ptr has n+1 entries, row_ptr[0] = 0, non-decreasing,
+ *   row_ptr[n] < 2^31; every col_idx entry in [0, n); no self-loop; each row
+ *   strictly increasing (sorted, no duplicates); symmetric (u in row v iff
+ *   v in row u), because the paper's graphs are undirected (Sec. 4.1.2).
+ *   n = 0 is valid and gives an empty result.
+ *
+ * Threading: every entry point may be called from any host thread.  Calls on
+ * the same mis_graph are serialised by the library.  The serving entry points
+ * (mis_submit / mis_poll / mis_wait) are driven by one scheduler thread per
+ * process that the library starts on first use.
+ *
+ * Errors: functions returning int give MIS_OK (0) or a negative MIS_E* code;
+ * functions returning a pointer give NULL on error.  In both cases
+ * mis_last_error() returns the code and a message for the calling thread.
+ */
+#ifndef TCMIS_H
+#define TCMIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MIS_OK = 0,
+    MIS_EINVAL = -1,     /* bad argument or graph violating the input contract */
+    MIS_ENOMEM = -2,     /* device or host allocation failed, or HBM budget exceeded */
+    MIS_EBUSY = -3,      /* no serving slot free / object in use */
+    MIS_ETIMEDOUT = -4,  /* a bounded device-side wait gave up, or mis_wait timed out */
+    MIS_EDEVICE = -5,    /* CUDA runtime error */
+    MIS_EINTERNAL = -6,  /* internal invariant broken (e.g. round cap exceeded) */
+    MIS_ENOTREADY = -7   /* request still in flight */
+};
+
+/* Which round kernel runs a solve. */
+enum {
+    MIS_PATH_AUTO = 0,     /* autotuner's choice, cached per density class */
+    MIS_PATH_CSR = 1,      /* warp-per-row CSR kernel on CUDA cores */
+    MIS_PATH_TILE = 2,     /* tile-CSR kernel, bitmask payload, popc on CUDA cores */
+    MIS_PATH_TILE_TC = 3   /* tile-CSR kernel, exclusion test as tensor-core MMA */
+};
+
+typedef struct mis_graph mis_graph;
+typedef int64_t mis_ticket;
+
+typedef struct mis_options {
+    int32_t path;            /* MIS_PATH_*; default MIS_PATH_AUTO */
+    int32_t threads_per_row; /* CSR path: 0 = auto, else 4, 8, 16 or 32 */
+    int32_t check_symmetry;  /* 1 (default) = verify symmetry at create, 0 = trust */
+    int32_t build_tiles;     /* 1 = build tile-CSR at create; -1 (default) = when the
+                                autotuner or a forced tile path needs it; 0 = never */
+    int64_t spin_cap;        /* device barrier spin limit in polls; 0 = default
+                                (about one second); the test suite uses small values */
+    int32_t device;          /* CUDA device ordinal; default 0 */
+    int32_t max_slots;       /* serving: concurrent solves per step; 0 = default (64) */
+    int64_t hbm_budget;      /* serving: bytes of per-solve workspace admitted at
+                                once; 0 = default (half of free device memory) */
+} mis_options;
+
+/* Per-solve statistics of the last completed solve on a graph. */
+typedef struct mis_stats {
+    int32_t rounds;          /* while-loop iterations of Algorithm 2 */
+    int32_t path;            /* MIS_PATH_* that ran */
+    int32_t threads_per_row; /* CSR path: lanes per row */
+    int32_t status;          /* MIS_OK or the error of that solve */
+    int64_t alive_sum;       /* sum over rounds of |A| at round start */
+    int64_t mis_size;        /* |M| */
+    int64_t alive_per_round[64]; /* |A| at the start of rounds 0..63 (0 beyond) */
+} mis_stats;
+
+/* Fill *opt with the defaults listed above. */
+void mis_options_init(mis_options *opt);
+
+/*
+ * Create a graph handle from a CSR graph in HOST memory (copied to the device;
+ * the caller may free its arrays when the call returns).  Validates the input
+ * contract on the device.  Returns NULL on error (see mis_last_error).
+ *   n        number of vertices
+ *   row_ptr  int32[n+1] row offsets
+ *   col_idx  int32[row_ptr[n]] neighbour ids
+ */
+mis_graph *mis_create(int32_t n, const int32_t *row_ptr, const int32_t *col_idx);
+
+/*
+ * As mis_create, with options, and with row_ptr / col_idx either host
+ * pointers (on_device = 0) or device pointers (on_device = 1; copied device
+ * to device).  `stream` is a cudaStream_t (NULL = legacy default stream); the
+ * call returns after the graph is resident.  `opt` may be NULL (defaults).
+ */
+mis_graph *mis_create_ex(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                         int32_t on_device, const mis_options *opt, void *stream);
+
+/*
+ * Block-diagonal disjoint union of `count` graphs, solved together in one
+ * persistent launch.  Graph g (host CSR arrays ns[g], row_ptrs[g],
+ * col_idxs[g]) keeps its own vertex ids, its own average degree d and its own
+ * seed for Eq. 1, so its part of the result equals a standalone solve of g.
+ * Vertex offsets inside the union are padded to multiples of 16.
+ */
+mis_graph *mis_create_batch(int32_t count, const int32_t *ns, const int32_t *const *row_ptrs,
+                            const int32_t *const *col_idxs, const mis_options *opt);
+
+/* Number of graphs in a handle (1 unless made by mis_create_batch) and the
+ * total number of result bytes (sum of the graphs' n). */
+int32_t mis_graph_count(const mis_graph *g);
+int64_t mis_result_size(const mis_graph *g);
+
+/*
+ * Solve with seed `seed` and write the result to HOST memory:
+ * out_status[v] = 1 if v is in the MIS, else 0 (n bytes; for a batch, the
+ * graphs' results one after another, each graph's seed = seed + its index).
+ * Blocks until done.
+ */
+int mis_solve(mis_graph *g, uint64_t seed, uint8_t *out_status);
+
+/*
+ * Asynchronous solve on `stream` (a cudaStream_t; NULL = legacy default).
+ * `seeds` holds one seed per graph of the handle (mis_graph_count entries).
+ * `out_status` is a DEVICE pointer to mis_result_size bytes.  Returns after
+ * enqueueing; errors found on the device are reported by mis_get_stats (which
+ * synchronises the stream).  The graph's device workspace is reused by the
+ * next solve on the same handle, so solves on one handle must be ordered on
+ * one stream.
+ */
+int mis_solve_ex(mis_graph *g, const uint64_t *seeds, uint8_t *out_status, void *stream);
+
+/* Statistics of the last solve on `g`; synchronises that solve's stream and
+ * returns its device-side status (MIS_OK, MIS_ETIMEDOUT, MIS_EINTERNAL). */
+int mis_get_stats(mis_graph *g, mis_stats *stats);
+
+/*
+ * Priority keys of Eq. 1 as computed by the device (for testing): writes
+ * uint32 key[v] = bit pattern of binary32 P(v) for deg(v) >= 1 and
+ * 0xFFFFFFFF for isolated vertices, into the DEVICE buffer out_key
+ * (mis_result_size entries).  Runs on `stream`.
+ */
+int mis_keys_ex(mis_graph *g, const uint64_t *seeds, uint32_t *out_key, void *stream);
+
+/* Select the round kernel (MIS_PATH_*) and lanes per row for later solves. */
+int mis_set_path(mis_graph *g, int32_t path, int32_t threads_per_row);
+
+/* Bytes of device memory held by the handle (graph + workspace). */
+int64_t mis_footprint(const mis_graph *g);
+
+/*
+ * Release the handle.  If served requests on it are still in flight the
+ * release is deferred until they finish.
+ */
+void mis_destroy(mis_graph *g);
+
+/* ---------------------------------------------------------------- serving
+ *
+ * Continuous batching over resident graphs.  mis_submit queues a request
+ * (graph, seed, HOST output buffer of n bytes that must stay valid until the
+ * request completes).  A scheduler thread admits queued requests into free
+ * slots while their workspace fits the HBM budget, and runs steps: one step
+ * advances every admitted request by one round of Algorithm 2 in a single
+ * launch, so requests that arrive while others run share the device.  A
+ * finished request's result is copied to its output buffer before it is
+ * reported done.
+ */
+int mis_submit(mis_graph *g, uint64_t seed, uint8_t *out_status, mis_ticket *ticket);
+
+/* MIS_OK if the request finished (and its ticket is released), MIS_ENOTREADY
+ * if still pending, or the negative error it finished with. */
+int mis_poll(mis_ticket ticket);
+
+/* Wait up to timeout_us microseconds (negative = forever); same returns as
+ * mis_poll, MIS_ETIMEDOUT when the wait expires first. */
+int mis_wait(mis_ticket ticket, int64_t timeout_us);
+
+/* Configure the serving scheduler (before the first submit; opt as in
+ * mis_create_ex: max_slots, hbm_budget, spin_cap, device). */
+int mis_serve_configure(const mis_options *opt);
+
+/* Stop the scheduler thread after draining in-flight requests. */
+void mis_serve_shutdown(void);
+
+/* Thread-local code and message of the last failing call on this thread. */
+int mis_last_error(const char **msg);
+
+/* Library version string. */
+const char *mis_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TCMIS_H */

@@ -1,0 +1,573 @@
+// api.cu -- the C ABI (include/tcmis.h): graph handles, solves, statistics.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "graph.h"
+#include "internal.h"
+#include "tcmis.h"
+
+namespace tcmis {
+
+namespace {
+thread_local int t_err_code = 0;
+thread_local std::string t_err_msg;
+constexpr long long kDefaultSpinCap = 20000000;  // polls of ~64 ns: about a second or more
+}  // namespace
+
+int set_error(int code, const std::string& msg) {
+    t_err_code = code;
+    t_err_msg = msg;
+    return code;
+}
+
+int set_cuda_error(cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();  // clear a sticky launch error on this thread
+    return set_error(e == cudaErrorMemoryAllocation ? MIS_ENOMEM : MIS_EDEVICE, m);
+}
+
+void clear_error() {
+    t_err_code = 0;
+    t_err_msg.clear();
+}
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(T** p, int64_t count, int64_t* footprint) {
+    const size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(count, 1);
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e == cudaSuccess && footprint) *footprint += (int64_t)bytes;
+    return e;
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+// Lanes per row from the average degree (the autotuner may override).
+int auto_tpr(double avg_deg) {
+    if (avg_deg <= 12.0) return 4;
+    if (avg_deg <= 40.0) return 8;
+    if (avg_deg <= 120.0) return 16;
+    return 32;
+}
+
+int pick_grid(mis_graph* g) {
+    const int maxb = csr_max_coresident_blocks(g->tpr, g->d.device);
+    if (maxb <= 0) return 0;
+    const int rows_per_pass = (csr_block_size() / 32) * (32 / g->tpr);
+    long long want = ((long long)g->d.n + 2LL * rows_per_pass - 1) / (2LL * rows_per_pass);
+    if (want < 1) want = 1;
+    return (int)std::min<long long>(want, maxb);
+}
+
+// Allocate the per-solve workspace and choose the launch shape.
+int finish_create(mis_graph* g) {
+    GraphData& d = g->d;
+    cudaError_t e;
+    if ((e = dalloc(&d.word, d.n, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.wl0, d.n, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.wl1, d.n, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.ctl, 1, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.out, d.result_bytes, &d.footprint)) != cudaSuccess)
+        return set_cuda_error(e, "workspace allocation");
+    if ((e = cudaMallocHost((void**)&d.ctl_host, sizeof(Ctl))) != cudaSuccess)
+        return set_cuda_error(e, "pinned allocation");
+    std::memset(d.ctl_host, 0, sizeof(Ctl));
+    const double avg = d.n ? (double)d.arcs / (double)d.n : 0.0;
+    g->tpr = g->opt.threads_per_row ? g->opt.threads_per_row : auto_tpr(avg);
+    g->path = MIS_PATH_CSR;
+    g->grid = pick_grid(g);
+    if (g->grid <= 0) return set_error(MIS_EDEVICE, "no co-resident blocks for the round kernel");
+    return MIS_OK;
+}
+
+int validate_device(mis_graph* g, cudaStream_t s) {
+    GraphData& d = g->d;
+    cudaError_t e = cudaMemsetAsync(d.flags, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess)
+        e = launch_validate(d.rp, d.col, d.n, d.arcs, g->opt.check_symmetry, d.flags, s);
+    unsigned f = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&f, d.flags, sizeof(unsigned),
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_cuda_error(e, "graph validation");
+    if (f) {
+        std::string why;
+        if (f & kBadRowPtr) why += " row_ptr not monotone from 0 to arcs;";
+        if (f & kBadColRange) why += " col_idx out of [0, n);";
+        if (f & kBadSelfLoop) why += " self-loop;";
+        if (f & kBadOrder) why += " row not strictly increasing (unsorted or duplicate);";
+        if (f & kBadSymmetry) why += " not symmetric;";
+        return set_error(MIS_EINVAL, "invalid graph:" + why);
+    }
+    return MIS_OK;
+}
+
+SolveArgs make_args(mis_graph* g) {
+    GraphData& d = g->d;
+    SolveArgs a;
+    a.rp = d.rp;
+    a.col = d.col;
+    a.n = d.n;
+    a.word = d.word;
+    a.wl0 = d.wl0;
+    a.wl1 = d.wl1;
+    a.ctl = d.ctl;
+    a.seg.count = d.count;
+    a.seg.blk_seg = d.blk_seg;
+    a.seg.voff = d.voff;
+    a.seg.nv = d.nv;
+    a.seg.arcs = d.garcs;
+    a.seg.roff = d.roff;
+    a.seg.seed = d.seeds;
+    a.spin_cap = g->opt.spin_cap > 0 ? g->opt.spin_cap : kDefaultSpinCap;
+    a.max_rounds = d.n + 2;
+    a.trp = d.trp;
+    a.tcol = d.tcol;
+    a.tbits = d.tbits;
+    return a;
+}
+
+}  // namespace
+
+void free_graph(mis_graph* g) {
+    if (!g) return;
+    GraphData& d = g->d;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(d.device);
+    if (g->own_stream) cudaStreamSynchronize(g->own_stream);
+    if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+    dfree(d.rp);
+    dfree(d.col);
+    dfree(d.blk_seg);
+    dfree(d.voff);
+    dfree(d.nv);
+    dfree(d.garcs);
+    dfree(d.roff);
+    dfree(d.seeds);
+    if (d.seeds_host) cudaFreeHost(d.seeds_host);
+    dfree(d.trp);
+    dfree(d.tcol);
+    dfree(d.tbits);
+    dfree(d.word);
+    dfree(d.wl0);
+    dfree(d.wl1);
+    dfree(d.ctl);
+    if (d.ctl_host) cudaFreeHost(d.ctl_host);
+    dfree(d.out);
+    dfree(d.flags);
+    if (g->own_stream) cudaStreamDestroy(g->own_stream);
+    cudaSetDevice(prev);
+    delete g;
+}
+
+// Enqueue one solve on stream s; results (bytes) into out_dev if non-null.
+int solve_async(mis_graph* g, const uint64_t* seeds, uint8_t* out_dev, cudaStream_t s) {
+    GraphData& d = g->d;
+    cudaError_t e = cudaSetDevice(d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    SolveArgs a = make_args(g);
+    a.out = out_dev;
+    if (d.count == 0) {
+        a.seed0 = seeds[0];
+    } else {
+        std::memcpy(d.seeds_host, seeds, sizeof(uint64_t) * (size_t)d.count);
+        e = cudaMemcpyAsync(d.seeds, d.seeds_host, sizeof(uint64_t) * (size_t)d.count,
+                            cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return set_cuda_error(e, "seed upload");
+    }
+    e = cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), s);
+    if (e != cudaSuccess) return set_cuda_error(e, "control reset");
+    if (d.n > 0) {
+        e = launch_csr_solve(a, g->tpr, g->grid, s);
+        if (e != cudaSuccess) return set_cuda_error(e, "round kernel launch");
+    }
+    g->last_stream = s;
+    g->last_path = MIS_PATH_CSR;
+    return MIS_OK;
+}
+
+}  // namespace tcmis
+
+using namespace tcmis;
+
+extern "C" {
+
+void mis_options_init(mis_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->path = MIS_PATH_AUTO;
+    opt->threads_per_row = 0;
+    opt->check_symmetry = 1;
+    opt->build_tiles = -1;
+    opt->spin_cap = 0;
+    opt->device = 0;
+    opt->max_slots = 0;
+    opt->hbm_budget = 0;
+}
+
+int mis_last_error(const char** msg) {
+    if (msg) *msg = t_err_msg.c_str();
+    return t_err_code;
+}
+
+const char* mis_version(void) { return "tcmis-gb300 0.1 (sm_103a)"; }
+
+static bool valid_tpr(int t) { return t == 0 || t == 4 || t == 8 || t == 16 || t == 32; }
+
+mis_graph* mis_create_ex(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                         int32_t on_device, const mis_options* opt, void* stream) {
+    clear_error();
+    if (n < 0 || (n > 0 && !row_ptr)) {
+        set_error(MIS_EINVAL, "n must be >= 0 and row_ptr non-null");
+        return nullptr;
+    }
+    mis_options o;
+    mis_options_init(&o);
+    if (opt) o = *opt;
+    if (!valid_tpr(o.threads_per_row)) {
+        set_error(MIS_EINVAL, "threads_per_row must be 0, 4, 8, 16 or 32");
+        return nullptr;
+    }
+    cudaError_t e = cudaSetDevice(o.device);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "cudaSetDevice");
+        return nullptr;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t arcs = 0;
+    if (n > 0) {
+        int32_t last = 0;
+        if (on_device) {
+            e = cudaMemcpyAsync(&last, row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                set_cuda_error(e, "reading row_ptr[n]");
+                return nullptr;
+            }
+        } else {
+            last = row_ptr[n];
+        }
+        arcs = last;
+        if (arcs < 0) {
+            set_error(MIS_EINVAL, "row_ptr[n] must be >= 0");
+            return nullptr;
+        }
+        if (arcs > 0 && !col_idx) {
+            set_error(MIS_EINVAL, "col_idx is null");
+            return nullptr;
+        }
+    }
+    mis_graph* g = new mis_graph();
+    g->opt = o;
+    GraphData& d = g->d;
+    d.device = o.device;
+    d.n = n;
+    d.arcs = arcs;
+    d.result_bytes = n;
+    const int64_t col_alloc = ((arcs + 3) / 4) * 4 + 4;
+    if ((e = dalloc(&d.rp, (int64_t)n + 1, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.col, col_alloc, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.flags, 1, &d.footprint)) != cudaSuccess) {
+        set_cuda_error(e, "graph allocation");
+        free_graph(g);
+        return nullptr;
+    }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    e = cudaMemsetAsync(d.col, 0, sizeof(int32_t) * (size_t)col_alloc, s);
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync(d.rp, row_ptr, sizeof(int32_t) * ((size_t)n + 1), kind, s);
+    if (e == cudaSuccess && n == 0) e = cudaMemsetAsync(d.rp, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess && arcs > 0)
+        e = cudaMemcpyAsync(d.col, col_idx, sizeof(int32_t) * (size_t)arcs, kind, s);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "graph upload");
+        free_graph(g);
+        return nullptr;
+    }
+    if (n > 0 && validate_device(g, s) != MIS_OK) {
+        free_graph(g);
+        return nullptr;
+    }
+    if (finish_create(g) != MIS_OK) {
+        free_graph(g);
+        return nullptr;
+    }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        set_cuda_error(e, "create");
+        free_graph(g);
+        return nullptr;
+    }
+    return g;
+}
+
+mis_graph* mis_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx) {
+    return mis_create_ex(n, row_ptr, col_idx, 0, nullptr, nullptr);
+}
+
+mis_graph* mis_create_batch(int32_t count, const int32_t* ns, const int32_t* const* row_ptrs,
+                            const int32_t* const* col_idxs, const mis_options* opt) {
+    clear_error();
+    if (count < 1 || !ns || !row_ptrs || !col_idxs) {
+        set_error(MIS_EINVAL, "count must be >= 1 with non-null arrays");
+        return nullptr;
+    }
+    mis_options o;
+    mis_options_init(&o);
+    if (opt) o = *opt;
+    if (!valid_tpr(o.threads_per_row)) {
+        set_error(MIS_EINVAL, "threads_per_row must be 0, 4, 8, 16 or 32");
+        return nullptr;
+    }
+    std::vector<int32_t> voff(count), nv(count), garcs(count);
+    std::vector<int64_t> roff(count);
+    int64_t N = 0, A = 0, R = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        if (ns[i] < 0 || (ns[i] > 0 && !row_ptrs[i])) {
+            set_error(MIS_EINVAL, "graph " + std::to_string(i) + ": bad n or row_ptr");
+            return nullptr;
+        }
+        const int64_t a = ns[i] ? row_ptrs[i][ns[i]] : 0;
+        if (a < 0 || (a > 0 && !col_idxs[i]) || (ns[i] > 0 && row_ptrs[i][0] != 0)) {
+            set_error(MIS_EINVAL, "graph " + std::to_string(i) + ": bad row_ptr or col_idx");
+            return nullptr;
+        }
+        voff[i] = (int32_t)N;
+        nv[i] = ns[i];
+        garcs[i] = (int32_t)a;
+        roff[i] = R;
+        N += ((int64_t)ns[i] + 15) / 16 * 16;
+        A += a;
+        R += ns[i];
+        if (N > INT32_MAX - 16 || A > INT32_MAX - 16) {
+            set_error(MIS_EINVAL, "batch exceeds 2^31 vertices or arcs");
+            return nullptr;
+        }
+    }
+    cudaError_t e = cudaSetDevice(o.device);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "cudaSetDevice");
+        return nullptr;
+    }
+    mis_graph* g = new mis_graph();
+    g->opt = o;
+    GraphData& d = g->d;
+    d.device = o.device;
+    d.n = (int32_t)N;
+    d.arcs = A;
+    d.count = count;
+    d.result_bytes = R;
+    d.h_nv = nv;
+    if ((e = cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        set_cuda_error(e, "stream");
+        free_graph(g);
+        return nullptr;
+    }
+    cudaStream_t s = g->own_stream;
+    const int64_t col_alloc = ((A + 3) / 4) * 4 + 4;
+    const int64_t nblk = N / 16;
+    if ((e = dalloc(&d.rp, N + 1, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.col, col_alloc, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.flags, 1, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.blk_seg, nblk, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.voff, count, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.nv, count, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.garcs, count, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.roff, count, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.seeds, count, &d.footprint)) != cudaSuccess ||
+        (e = cudaMallocHost((void**)&d.seeds_host, sizeof(uint64_t) * (size_t)count)) !=
+            cudaSuccess) {
+        set_cuda_error(e, "batch allocation");
+        free_graph(g);
+        return nullptr;
+    }
+    e = cudaMemsetAsync(d.col, 0, sizeof(int32_t) * (size_t)col_alloc, s);
+    int64_t aoff = 0;
+    for (int32_t i = 0; i < count && e == cudaSuccess; ++i) {
+        const int32_t ni = ns[i];
+        const int32_t ai = garcs[i];
+        if (ni > 0)
+            e = cudaMemcpyAsync(d.rp + voff[i], row_ptrs[i], sizeof(int32_t) * (size_t)ni,
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && ai > 0)
+            e = cudaMemcpyAsync(d.col + aoff, col_idxs[i], sizeof(int32_t) * (size_t)ai,
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = launch_relocate(d.rp + voff[i], d.col + aoff, ni, ai, voff[i], (int32_t)aoff, s);
+        const int32_t pad_to = (i + 1 < count) ? voff[i + 1] : (int32_t)N;
+        if (e == cudaSuccess)
+            e = launch_pad_rows(d.rp, voff[i] + ni, pad_to + (i + 1 == count ? 1 : 0),
+                                (int32_t)(aoff + ai), s);
+        aoff += ai;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d.voff, voff.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice,
+                            s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d.nv, nv.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d.garcs, garcs.data(), sizeof(int32_t) * count,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d.roff, roff.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice,
+                            s);
+    if (e == cudaSuccess) e = launch_fill_seg(d.blk_seg, d.voff, count, (int32_t)nblk, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "batch upload");
+        free_graph(g);
+        return nullptr;
+    }
+    // each graph must stay inside its own vertex range
+    for (int32_t i = 0; i < count; ++i) {
+        const int32_t* rp = row_ptrs[i];
+        const int32_t* col = col_idxs[i];
+        for (int32_t v = 0; v < ns[i]; ++v)
+            if (rp[v] > rp[v + 1]) {
+                set_error(MIS_EINVAL, "graph " + std::to_string(i) + ": row_ptr not monotone");
+                free_graph(g);
+                return nullptr;
+            }
+        for (int32_t p = 0; p < garcs[i]; ++p)
+            if (col[p] < 0 || col[p] >= ns[i]) {
+                set_error(MIS_EINVAL, "graph " + std::to_string(i) + ": col_idx out of range");
+                free_graph(g);
+                return nullptr;
+            }
+    }
+    if (N > 0 && validate_device(g, s) != MIS_OK) {
+        free_graph(g);
+        return nullptr;
+    }
+    if (finish_create(g) != MIS_OK) {
+        free_graph(g);
+        return nullptr;
+    }
+    return g;
+}
+
+int32_t mis_graph_count(const mis_graph* g) { return g ? (g->d.count ? g->d.count : 1) : 0; }
+
+int64_t mis_result_size(const mis_graph* g) { return g ? g->d.result_bytes : 0; }
+
+int64_t mis_footprint(const mis_graph* g) { return g ? g->d.footprint : 0; }
+
+int mis_set_path(mis_graph* g, int32_t path, int32_t threads_per_row) {
+    clear_error();
+    if (!g) return set_error(MIS_EINVAL, "null graph");
+    if (!valid_tpr(threads_per_row)) return set_error(MIS_EINVAL, "bad threads_per_row");
+    if (path != MIS_PATH_AUTO && path != MIS_PATH_CSR)
+        return set_error(MIS_EINVAL, "path not available");
+    std::lock_guard<std::mutex> lk(g->mu);
+    const double avg = g->d.n ? (double)g->d.arcs / (double)g->d.n : 0.0;
+    g->tpr = threads_per_row ? threads_per_row : auto_tpr(avg);
+    g->path = MIS_PATH_CSR;
+    cudaSetDevice(g->d.device);
+    g->grid = pick_grid(g);
+    return MIS_OK;
+}
+
+int mis_solve_ex(mis_graph* g, const uint64_t* seeds, uint8_t* out_status, void* stream) {
+    clear_error();
+    if (!g || !seeds) return set_error(MIS_EINVAL, "null graph or seeds");
+    if (g->d.result_bytes > 0 && !out_status) return set_error(MIS_EINVAL, "null out_status");
+    std::lock_guard<std::mutex> lk(g->mu);
+    return solve_async(g, seeds, out_status, (cudaStream_t)stream);
+}
+
+int mis_solve(mis_graph* g, uint64_t seed, uint8_t* out_status) {
+    clear_error();
+    if (!g) return set_error(MIS_EINVAL, "null graph");
+    if (g->d.result_bytes > 0 && !out_status) return set_error(MIS_EINVAL, "null out_status");
+    std::lock_guard<std::mutex> lk(g->mu);
+    cudaError_t e = cudaSetDevice(g->d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    if (!g->own_stream) {
+        e = cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return set_cuda_error(e, "stream");
+    }
+    std::vector<uint64_t> seeds((size_t)std::max(1, g->d.count));
+    for (size_t i = 0; i < seeds.size(); ++i) seeds[i] = seed + i;
+    int rc = solve_async(g, seeds.data(), g->d.out, g->own_stream);
+    if (rc != MIS_OK) return rc;
+    if (g->d.result_bytes > 0) {
+        e = cudaMemcpyAsync(out_status, g->d.out, (size_t)g->d.result_bytes,
+                            cudaMemcpyDeviceToHost, g->own_stream);
+        if (e != cudaSuccess) return set_cuda_error(e, "result download");
+    }
+    e = cudaMemcpyAsync(g->d.ctl_host, g->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
+                        g->own_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->own_stream);
+    if (e != cudaSuccess) return set_cuda_error(e, "solve");
+    if (g->d.ctl_host->err == kErrTimedOut)
+        return set_error(MIS_ETIMEDOUT, "device barrier wait exceeded its spin limit");
+    if (g->d.ctl_host->err != 0)
+        return set_error(MIS_EINTERNAL, "round cap exceeded");
+    return MIS_OK;
+}
+
+int mis_get_stats(mis_graph* g, mis_stats* st) {
+    clear_error();
+    if (!g || !st) return set_error(MIS_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(g->mu);
+    cudaError_t e = cudaSetDevice(g->d.device);
+    if (e == cudaSuccess && g->last_stream) e = cudaStreamSynchronize(g->last_stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->d.ctl_host, g->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_cuda_error(e, "stats");
+    const Ctl& c = *g->d.ctl_host;
+    std::memset(st, 0, sizeof(*st));
+    st->rounds = c.rounds;
+    st->path = g->last_path;
+    st->threads_per_row = g->tpr;
+    st->alive_sum = (int64_t)c.alive_sum;
+    st->mis_size = (int64_t)c.mis_size;
+    for (int r = 0; r < 64 && r < kStatRounds; ++r) st->alive_per_round[r] = c.alive[r];
+    st->status = c.err == 0 ? MIS_OK : (c.err == kErrTimedOut ? MIS_ETIMEDOUT : MIS_EINTERNAL);
+    if (st->status != MIS_OK)
+        return set_error(st->status, st->status == MIS_ETIMEDOUT
+                                         ? "device barrier wait exceeded its spin limit"
+                                         : "round cap exceeded");
+    return MIS_OK;
+}
+
+int mis_keys_ex(mis_graph* g, const uint64_t* seeds, uint32_t* out_key, void* stream) {
+    clear_error();
+    if (!g || !seeds || (g->d.result_bytes > 0 && !out_key))
+        return set_error(MIS_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(g->mu);
+    GraphData& d = g->d;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(d.device);
+    SolveArgs a = make_args(g);
+    if (d.count == 0) {
+        a.seed0 = seeds[0];
+    } else if (e == cudaSuccess) {
+        std::memcpy(d.seeds_host, seeds, sizeof(uint64_t) * (size_t)d.count);
+        e = cudaMemcpyAsync(d.seeds, d.seeds_host, sizeof(uint64_t) * (size_t)d.count,
+                            cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = launch_keys(a, out_key, s);
+    if (e != cudaSuccess) return set_cuda_error(e, "keys");
+    g->last_stream = s;
+    return MIS_OK;
+}
+
+void mis_destroy(mis_graph* g) {
+    if (!g) return;
+    if (g->inflight.load() > 0) {
+        g->destroy_pending.store(true);
+        serve_release_graph(g);
+        return;
+    }
+    free_graph(g);
+}
+
+}  // extern "C"

@@ -1,0 +1,158 @@
+// common.cuh -- device-side building blocks shared by the round kernels.
+//
+// Per-vertex state is one packed 32-bit word, read by every neighbour test:
+//
+//   bits 31..29  state    001 = undecided (alive), 111 = in the MIS, 000 = out
+//   bits 28..0   the low 29 bits of the priority key
+//
+// The priority key is the bit pattern of the binary32 priority P of Eq. 1.
+// For any valid graph P lies in [1/(n+1), 1], so its exponent field is in
+// [95, 127]: bits 31 and 30 of the key are 0 and bit 29 is 1.  An undecided
+// word is therefore exactly the key, an out word is any value below 2^29 (we
+// store 0) and an in word is the key with bits 31..30 set.  One unsigned
+// compare then decides both neighbour tests of a round:
+//
+//   selection test (Phase 1, Algorithm 2): u blocks v when
+//       word(u) > word(v)  or  (word(u) == word(v) and u > v)
+//     out words never block; undecided words compare by key then id; an in
+//     word (a candidate chosen earlier in the same phase) always blocks, which
+//     is exactly what the round-start snapshot says, because a candidate
+//     outranks every undecided neighbour.
+//   exclusion test (Phase 2): v has a candidate neighbour when word(u) >= 0xE0000000.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tcmis {
+
+constexpr uint32_t kWordInMin = 0xE0000000u;  // words >= this are in the MIS
+constexpr uint32_t kWordInSet = 0xC0000000u;  // OR'd into an undecided word
+constexpr uint32_t kWordOut = 0u;             // out of the MIS
+constexpr uint32_t kKeyIsolated = 0x3F800000u; // key used for deg-0 vertices (P = 1)
+
+// error codes written by kernels into Ctl::err (match the MIS_E* values)
+constexpr int kErrTimedOut = -4;
+constexpr int kErrInternal = -6;
+
+constexpr int kStatRounds = 64;
+
+// Control block of one solve in device memory; zeroed before every launch.
+struct Ctl {
+    unsigned bar_count;   // grid barrier: arrivals
+    unsigned bar_gen;     // grid barrier: generation
+    int err;              // first error (0 = none)
+    int rounds;           // rounds completed
+    int cnt[4];           // worklist sizes, ring indexed by round & 3
+    unsigned long long alive_sum;
+    unsigned long long mis_size;
+    int alive[kStatRounds];
+    unsigned grab[4];     // dynamic work counters, ring indexed by phase & 3
+    int pad[24];
+};
+
+// ---------------------------------------------------------------- Eq. 1
+
+// splitmix64 finaliser (Steele, Lea, Flood, OOPSLA 2014).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+
+// Average degree d of Eq. 1: arcs / n in binary32, round-to-nearest.
+__device__ __forceinline__ float average_degree(int32_t arcs, int32_t n) {
+    return __fdiv_rn(__int2float_rn(arcs), __int2float_rn(n));
+}
+
+// Eq. 1 key of a vertex with deg >= 1: bits of d / ((d + deg) - eps), each
+// operation binary32 round-to-nearest (explicit intrinsics: no contraction).
+// seed_mix = mix64(seed); eps = (hi32(mix64(seed_mix ^ id)) >> 8) * 2^-24.
+__device__ __forceinline__ uint32_t eq1_key(float dbar, int32_t deg, uint64_t seed_mix,
+                                            uint32_t local_id) {
+    const uint32_t h = (uint32_t)(mix64(seed_mix ^ (uint64_t)local_id) >> 32);
+    const float eps = __fmul_rn(__uint2float_rn(h >> 8), 0x1p-24f);
+    const float den = __fsub_rn(__fadd_rn(dbar, __int2float_rn(deg)), eps);
+    return __float_as_uint(__fdiv_rn(dbar, den));
+}
+
+// ---------------------------------------------------------------- memory helpers
+
+__device__ __forceinline__ uint32_t ld_word(const uint32_t* p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_acquire_int(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------- grid barrier
+//
+// Software barrier over all blocks of a cooperative launch (co-residency is
+// guaranteed by the launch).  Every wait is bounded: after `spin_cap` polls
+// the block records kErrTimedOut and leaves; a block that sees an error while
+// waiting leaves too, so a failed barrier never hangs the device.  The last
+// block to arrive may run `leader` (a functor called by one thread) before it
+// releases the others.  Returns false when the launch must stop.
+template <class Leader>
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, long long spin_cap,
+                                             Leader leader) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen = ld_acquire(&ctl->bar_gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+        if (arrived == nblocks - 1) {
+            leader();
+            ctl->bar_count = 0;
+            __threadfence();
+            st_release(&ctl->bar_gen, gen + 1);
+        } else {
+            long long polls = 0;
+            while (ld_acquire(&ctl->bar_gen) == gen) {
+                if (++polls > spin_cap || ld_acquire_int(&ctl->err) != 0) {
+                    atomicCAS(&ctl->err, 0, kErrTimedOut);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (ld_acquire_int(&ctl->err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+struct NoLeader {
+    __device__ void operator()() const {}
+};
+
+// ---------------------------------------------------------------- warp helpers
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace tcmis

@@ -1,0 +1,82 @@
+// graph.h -- the library's graph handle and host-side helpers (host code only).
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "tcmis.h"
+
+namespace tcmis {
+
+// Records code + message for the calling thread and returns the code.
+int set_error(int code, const std::string& msg);
+int set_cuda_error(cudaError_t e, const char* what);
+void clear_error();
+
+// Device buffers of one graph (or one block-diagonal union of graphs) plus
+// the workspace of one solve at a time.
+struct GraphData {
+    int device = 0;
+    int32_t n = 0;          // vertices (union size, padding included)
+    int64_t arcs = 0;       // stored arcs
+    int32_t* rp = nullptr;  // n + 1
+    int32_t* col = nullptr; // arcs, padded to a multiple of 4 plus 4
+    // batch segments (count == 0 for a single graph)
+    int32_t count = 0;
+    int32_t* blk_seg = nullptr;
+    int32_t* voff = nullptr;
+    int32_t* nv = nullptr;
+    int32_t* garcs = nullptr;
+    int64_t* roff = nullptr;
+    uint64_t* seeds = nullptr;       // device, count entries
+    uint64_t* seeds_host = nullptr;  // pinned staging, count entries
+    std::vector<int32_t> h_nv;       // per graph vertices (host copy)
+    int64_t result_bytes = 0;        // sum of the graphs' n
+    // tile-CSR (built on demand)
+    int32_t* trp = nullptr;
+    int32_t* tcol = nullptr;
+    uint64_t* tbits = nullptr;
+    int64_t ntiles = 0;
+    // workspace of one solve
+    uint32_t* word = nullptr;
+    int32_t* wl0 = nullptr;
+    int32_t* wl1 = nullptr;
+    Ctl* ctl = nullptr;
+    Ctl* ctl_host = nullptr;  // pinned
+    uint8_t* out = nullptr;   // device result for host-output solves
+    unsigned* flags = nullptr;
+    int64_t footprint = 0;
+};
+
+}  // namespace tcmis
+
+struct mis_graph {
+    tcmis::GraphData d;
+    mis_options opt{};
+    int32_t path = MIS_PATH_CSR;  // resolved path
+    int32_t tpr = 8;              // resolved threads per row
+    int32_t grid = 0;             // persistent grid size
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t last_stream = nullptr;
+    int32_t last_path = 0;
+    std::mutex mu;
+    std::atomic<int> inflight{0};       // served requests not yet finished
+    std::atomic<bool> destroy_pending{false};
+};
+
+namespace tcmis {
+
+// api.cu
+int solve_async(mis_graph* g, const uint64_t* seeds, uint8_t* out_dev, cudaStream_t s);
+void free_graph(mis_graph* g);
+
+// serve.cu
+void serve_release_graph(mis_graph* g);
+
+}  // namespace tcmis

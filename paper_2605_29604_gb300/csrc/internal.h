@@ -1,0 +1,72 @@
+// internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tcmis {
+
+struct Ctl;
+
+// Per-graph parameters of Eq. 1 for a block-diagonal union (count == 0: one
+// graph, seed in `seed0`, average degree from row_ptr[n] / n).
+struct SegTable {
+    int32_t count = 0;
+    const int32_t* blk_seg = nullptr;  // per 16-vertex block of the union: graph index
+    const int32_t* voff = nullptr;     // per graph: first vertex in the union
+    const int32_t* nv = nullptr;       // per graph: vertices
+    const int32_t* arcs = nullptr;     // per graph: arcs (its own row_ptr[n])
+    const int64_t* roff = nullptr;     // per graph: first byte of its result
+    const uint64_t* seed = nullptr;    // per graph: seed
+};
+
+// Everything one persistent solve launch needs.
+struct SolveArgs {
+    const int32_t* rp = nullptr;   // row_ptr, n+1
+    const int32_t* col = nullptr;  // col_idx, padded by >= 4 entries
+    int32_t n = 0;                 // vertices (of the union for a batch)
+    uint32_t* word = nullptr;      // packed per-vertex state, n
+    int32_t* wl0 = nullptr;        // worklists, n each
+    int32_t* wl1 = nullptr;
+    Ctl* ctl = nullptr;            // control block (zeroed before launch)
+    uint8_t* out = nullptr;        // result bytes (device), nullable
+    SegTable seg;                  // batch segments
+    uint64_t seed0 = 0;            // single-graph seed
+    long long spin_cap = 0;        // barrier poll limit
+    int32_t max_rounds = 0;        // round cap (error beyond)
+    // tile-CSR (used by the tile kernels only)
+    const int32_t* trp = nullptr;  // tile row-block pointer
+    const int32_t* tcol = nullptr; // tile column-block index
+    const uint64_t* tbits = nullptr; // 8x8 bitmask payloads
+};
+
+// Launch configuration chosen by the host.
+struct LaunchCfg {
+    int grid = 0;
+    int block = 0;
+};
+
+// kernels_csr.cu
+cudaError_t launch_csr_solve(const SolveArgs& a, int threads_per_row, int grid, cudaStream_t s);
+int csr_max_coresident_blocks(int threads_per_row, int device);
+int csr_block_size();
+
+// kernels_util.cu
+cudaError_t launch_validate(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs,
+                            int check_symmetry, unsigned* d_flags, cudaStream_t s);
+cudaError_t launch_keys(const SolveArgs& a, uint32_t* out_key, cudaStream_t s);
+cudaError_t launch_fill_seg(int32_t* blk_seg, const int32_t* voff, int32_t count,
+                            int32_t nblk, cudaStream_t s);
+cudaError_t launch_relocate(int32_t* rp, int32_t* col, int32_t n, int32_t arcs, int32_t voff,
+                            int32_t aoff, cudaStream_t s);
+cudaError_t launch_pad_rows(int32_t* dst_rp, int32_t from, int32_t to, int32_t value,
+                            cudaStream_t s);
+
+// validation flag bits
+constexpr unsigned kBadRowPtr = 1u;
+constexpr unsigned kBadColRange = 2u;
+constexpr unsigned kBadSelfLoop = 4u;
+constexpr unsigned kBadOrder = 8u;
+constexpr unsigned kBadSymmetry = 16u;
+
+}  // namespace tcmis

@@ -1,0 +1,71 @@
+"""The C-ABI library loads and exports every entry point include/tcmis.h declares.
+
+CPU only: no call here touches a GPU.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2605_29604_gb300 import build as nbuild
+from paper_2605_29604_gb300 import native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    nbuild.build()
+    return native.lib()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "tcmis.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(mis_[a-z_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["mis_create", "mis_solve", "mis_submit", "mis_poll", "mis_destroy",
+                     "mis_last_error", "mis_wait"]:
+        assert required in names
+    assert sorted(native.EXPORTED) == names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_options_defaults_and_version(lib):
+    o = native.options()
+    assert o.path == native.MIS_PATH_AUTO
+    assert o.check_symmetry == 1
+    assert o.build_tiles == -1
+    assert b"sm_103a" in lib.mis_version()
+
+
+def test_null_arguments_rejected_without_device(lib):
+    # argument checks happen before any CUDA call
+    assert lib.mis_solve(None, 1, None) == native.MIS_EINVAL
+    code, msg = native.last_error()
+    assert code == native.MIS_EINVAL and msg
+    assert lib.mis_create_ex(-1, None, None, 0, None, None) is None
+    assert native.last_error()[0] == native.MIS_EINVAL
+    o = native.options(threads_per_row=3)
+    assert lib.mis_create_ex(0, None, None, 0, ctypes.byref(o), None) is None
+    assert native.last_error()[0] == native.MIS_EINVAL
+
+
+def test_product_package_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_2605_29604_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "tcmis_oracle" not in text and "liboracle" not in text, f

@@ -1,0 +1,201 @@
+"""GPU parity of the CSR round kernel against the CPU oracle.
+
+Every comparison is bit-exact on the vertex set (the result is unique for a
+given graph and seed), and the round structure of Algorithm 2 (rounds, alive
+set size per round) must match too.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_29604_gb300 import graphgen as gg
+from paper_2605_29604_gb300 import native
+
+from gpu_util import assert_same, create, ensure_built, gpu_keys, gpu_solve, oracle_solve
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    torch.cuda.set_device(0)
+
+
+FAMILIES = {
+    "er_small": lambda: gg.er_gnm(3000, 12000, 4),
+    "er_10k": lambda: gg.er_10k_deg8(1),
+    "rmat14": lambda: gg.rmat(14, 16, 0.57, 0.19, 0.19, 9, permute=True),
+    "rmat14_natural": lambda: gg.rmat(14, 16, 0.57, 0.19, 0.19, 9, permute=False),
+    "grid": lambda: gg.grid_diag(127, 0.05, 2),
+    "grid_perm": lambda: gg.grid_diag(127, 0.05, 2, permute=True),
+    "rgg": lambda: gg.rgg(20000, 10.0, 3),
+    "dense": lambda: gg.random_small(700, 0.3, 6),
+    "star_hub": lambda: gg.disjoint_union([gg.star(150000), gg.er_gnm(5000, 20000, 3)]),
+    "path": lambda: gg.path(5001),
+    "cycle": lambda: gg.cycle(4099),
+    "complete": lambda: gg.complete(300),
+    "k_ab": lambda: gg.complete_bipartite(40, 900),
+    "empty": lambda: gg.empty(1234),
+    "single": lambda: gg.empty(1),
+    "edge": lambda: gg.path(2),
+}
+
+_cache = {}
+
+
+def graph(name):
+    if name not in _cache:
+        _cache[name] = FAMILIES[name]()
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", sorted(FAMILIES))
+def test_keys_bit_exact(name):
+    g = graph(name)
+    n, rp, col = g
+    h = create(g)
+    try:
+        for seed in (1, 2**63 + 5):
+            got = gpu_keys(h, [seed])
+            want = oracle.keys(n, rp, seed)
+            assert np.array_equal(got, want)
+    finally:
+        native.mis_destroy(h)
+
+
+@pytest.mark.parametrize("name", sorted(FAMILIES))
+@pytest.mark.parametrize("tpr", [4, 8, 16, 32])
+def test_csr_solve_bit_exact(name, tpr):
+    g = graph(name)
+    h = create(g)
+    try:
+        for seed in (1, 7):
+            got, st = gpu_solve(h, [seed], native.MIS_PATH_CSR, tpr)
+            assert st.path == native.MIS_PATH_CSR and st.threads_per_row == tpr
+            assert_same(g, seed, got, st)
+    finally:
+        native.mis_destroy(h)
+
+
+def test_zero_vertices():
+    h = create((0, np.zeros(1, np.int32), np.zeros(0, np.int32)))
+    try:
+        got, st = gpu_solve(h, [1])
+        assert len(got) == 0 and st.rounds == 0
+    finally:
+        native.mis_destroy(h)
+
+
+def test_repeated_solves_reuse_workspace():
+    g = graph("rmat14")
+    h = create(g)
+    try:
+        for seed in range(10, 16):
+            got, st = gpu_solve(h, [seed])
+            assert_same(g, seed, got, st)
+    finally:
+        native.mis_destroy(h)
+
+
+def test_host_api_matches():
+    g = graph("er_10k")
+    n, rp, col = g
+    h = native.mis_create(n, rp, col)
+    try:
+        got = native.mis_solve(h, 1)
+        st = native.mis_get_stats(h)
+        assert_same(g, 1, got, st)
+    finally:
+        native.mis_destroy(h)
+
+
+def test_device_input_create():
+    import torch
+    g = graph("grid")
+    n, rp, col = g
+    drp = torch.from_numpy(rp).cuda()
+    dcol = torch.from_numpy(col).cuda()
+    s = torch.cuda.current_stream().cuda_stream
+    h = native.mis_create_ex(n, drp.data_ptr(), dcol.data_ptr(), 1, None, s)
+    try:
+        got, st = gpu_solve(h, [3])
+        assert_same(g, 3, got, st)
+    finally:
+        native.mis_destroy(h)
+
+
+BAD = {
+    "asymmetric": (3, [0, 1, 1, 1], [1]),
+    "self_loop": (2, [0, 2, 3], [0, 1, 0]),
+    "unsorted": (3, [0, 2, 3, 4], [2, 1, 0, 0]),
+    "duplicate": (2, [0, 2, 3], [1, 1, 0]),
+    "out_of_range": (2, [0, 1, 2], [5, 0]),
+    "negative_col": (2, [0, 1, 2], [-1, 0]),
+    "rowptr_decreasing": (3, [0, 2, 1, 2], [1, 2]),
+    "rowptr_start": (2, [1, 2, 2], [1, 0]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(BAD))
+def test_invalid_graph_rejected(name):
+    n, rp, col = BAD[name]
+    with pytest.raises(native.MisError) as ei:
+        create((n, np.array(rp, np.int32), np.array(col, np.int32)))
+    assert ei.value.code == native.MIS_EINVAL
+
+
+def test_unchecked_symmetry_accepted_when_disabled():
+    n, rp, col = BAD["asymmetric"]
+    h = create((n, np.array(rp, np.int32), np.array(col, np.int32)), check_symmetry=0)
+    native.mis_destroy(h)
+
+
+def test_barrier_timeout_reports_error_and_recovers():
+    # A spin limit of one poll makes a grid barrier give up almost surely:
+    # the kernel must record MIS_ETIMEDOUT and return, leaving the context
+    # usable for the next (normal) solve on the same graph.
+    g = graph("rmat14")
+    h = create(g, spin_cap=1)
+    try:
+        seen = False
+        for _ in range(5):
+            try:
+                gpu_solve(h, [1])
+            except native.MisError as e:
+                assert e.code == native.MIS_ETIMEDOUT
+                seen = True
+                break
+        assert seen
+    finally:
+        native.mis_destroy(h)
+    h = create(g)
+    try:
+        got, st = gpu_solve(h, [1])
+        assert_same(g, 1, got, st)
+    finally:
+        native.mis_destroy(h)
+
+
+@pytest.mark.parametrize("count", [1, 5, 64])
+def test_batch_union_equals_standalone(count):
+    parts = gg.batch_mixed(count, seed=100 + count, nmin=16, nmax=5000)
+    parts[0] = gg.empty(0) if count > 2 else parts[0]
+    h = native.mis_create_batch(parts)
+    try:
+        seeds = np.arange(1000, 1000 + count, dtype=np.uint64)
+        keys = gpu_keys(h, seeds)
+        got, st = gpu_solve(h, seeds)
+        off = 0
+        for g, s in zip(parts, seeds):
+            n = g[0]
+            assert np.array_equal(keys[off:off + n], oracle.keys(n, g[1], int(s)))
+            want = oracle_solve(g, int(s))
+            assert np.array_equal(got[off:off + n], want.status)
+            off += n
+        assert off == len(got)
+    finally:
+        native.mis_destroy(h)
