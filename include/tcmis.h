@@ -207,6 +207,37 @@ int mis_serve_configure(const mis_options *opt);
 /* Stop the scheduler thread after draining in-flight requests. */
 void mis_serve_shutdown(void);
 
+/* ---------------------------------------------------------------- no allocation
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory (code running inside a custom
+ * allocator, frameworks that reserve all device memory up front, loops that
+ * cannot afford an allocation's latency or implicit synchronisation).
+ *
+ * Solves one graph on the calling thread's current CUDA device without any
+ * allocation: no cudaMalloc, no cudaFree, no allocating library routine.
+ *   n           number of vertices, 0 <= n <= 262144 (larger n: MIS_EINVAL)
+ *   row_ptr     DEVICE int32[n+1]
+ *   col_idx     DEVICE int32[row_ptr[n]] (no padding or alignment needed)
+ *   seed        seed of Eq. 1's perturbation
+ *   out_status  DEVICE uint8[n]: 1 if the vertex is in the MIS, else 0
+ *   stream      cudaStream_t (NULL = legacy default stream)
+ * The result equals mis_solve's for the same graph and seed.  The call
+ * enqueues on `stream` and waits for it; it returns MIS_OK, MIS_EINVAL,
+ * MIS_ETIMEDOUT, MIS_EINTERNAL or MIS_EDEVICE.  The graph is NOT validated:
+ * a graph that breaks the input contract gives an unspecified set, but the
+ * kernel never reads or writes outside the buffers above.
+ *
+ * Scratch: the library holds one fixed array of 3 MiB + 512 B in device
+ * memory on every GPU that loads it, until the process exits.  The first
+ * call on a device looks up that array's device address (with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the array, so calls whose work overlaps on a GPU (different streams or
+ * threads) race and must be serialised by the caller.
+ */
+int mis_solve_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint64_t seed,
+                      uint8_t *out_status, void *stream);
+
 /* Thread-local code and message of the last failing call on this thread. */
 int mis_last_error(const char **msg);
 

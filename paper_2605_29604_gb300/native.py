@@ -109,6 +109,8 @@ def lib():
         L.mis_serve_configure.restype = ctypes.c_int
         L.mis_serve_shutdown.argtypes = []
         L.mis_serve_shutdown.restype = None
+        L.mis_solve_noalloc.argtypes = [i32, P, P, u64, P, P]
+        L.mis_solve_noalloc.restype = ctypes.c_int
         L.mis_last_error.argtypes = [ctypes.POINTER(ctypes.c_char_p)]
         L.mis_last_error.restype = ctypes.c_int
         L.mis_version.argtypes = []
@@ -123,6 +125,7 @@ EXPORTED = [
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
     "mis_set_path", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
+    "mis_solve_noalloc",
 ]
 
 
@@ -222,6 +225,14 @@ def mis_keys_ex(h, seeds, out_ptr, stream=None):
     s = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64).reshape(-1))
     return _check(lib().mis_keys_ex(h, _ptr(s), ctypes.c_void_p(out_ptr),
                                     ctypes.c_void_p(stream) if stream else None))
+
+
+def mis_solve_noalloc(n, row_ptr_ptr, col_idx_ptr, seed, out_ptr, stream=None):
+    """Allocation-free solve: device pointers in and out (see include/tcmis.h)."""
+    return _check(lib().mis_solve_noalloc(n, ctypes.c_void_p(row_ptr_ptr),
+                                          ctypes.c_void_p(col_idx_ptr), seed & (2**64 - 1),
+                                          ctypes.c_void_p(out_ptr),
+                                          ctypes.c_void_p(stream) if stream else None))
 
 
 def mis_set_path(h, path, threads_per_row=0):
