@@ -76,7 +76,10 @@ typedef int64_t mis_ticket;
 
 typedef struct mis_options {
     int32_t path;            /* MIS_PATH_*; default MIS_PATH_AUTO */
-    int32_t threads_per_row; /* CSR path: 0 = auto, else 4, 8, 16 or 32 */
+    int32_t threads_per_row; /* CSR path: 0 = degree bins (rows of degree <= 8 get
+                                one lane, <= 4096 four, <= 65536 a warp, beyond a
+                                whole block), else 1, 4, 16, 32 or 512 lanes for
+                                every row */
     int32_t check_symmetry;  /* 1 (default) = verify symmetry at create, 0 = trust */
     int32_t build_tiles;     /* 1 = build tile-CSR at create; -1 (default) = when the
                                 autotuner or a forced tile path needs it; 0 = never */
@@ -92,11 +95,16 @@ typedef struct mis_options {
 typedef struct mis_stats {
     int32_t rounds;          /* while-loop iterations of Algorithm 2 */
     int32_t path;            /* MIS_PATH_* that ran */
-    int32_t threads_per_row; /* CSR path: lanes per row */
+    int32_t threads_per_row; /* CSR path: lanes per row forced for every row, or 0
+                                when rows are binned by degree */
     int32_t status;          /* MIS_OK or the error of that solve */
     int64_t alive_sum;       /* sum over rounds of |A| at round start */
     int64_t mis_size;        /* |M| */
     int64_t alive_per_round[64]; /* |A| at the start of rounds 0..63 (0 beyond) */
+    int64_t init_ns;         /* device time of the priority initialisation (Eq. 1) */
+    int64_t select_ns[64];   /* device time of Phase 1 (selection test), rounds 0..63 */
+    int64_t exclude_ns[64];  /* device time of Phases 2+3 (exclusion test, state
+                                update, compaction), rounds 0..63 */
 } mis_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -167,8 +175,21 @@ int mis_get_stats(mis_graph *g, mis_stats *stats);
  */
 int mis_keys_ex(mis_graph *g, const uint64_t *seeds, uint32_t *out_key, void *stream);
 
-/* Select the round kernel (MIS_PATH_*) and lanes per row for later solves. */
+/* Select the round kernel (MIS_PATH_*) and lanes per row (as in mis_options)
+ * for later solves. */
 int mis_set_path(mis_graph *g, int32_t path, int32_t threads_per_row);
+
+/* CSR path with degree bins: bounds[0..3] are the inclusive upper degrees of
+ * bins 0..3 (1, 4, 16 and 32 lanes per row; bin 4, a block of 512 threads per
+ * row, takes the rest).  Non-decreasing; -1 empties a bin.  Used by the
+ * autotuner. */
+int mis_set_csr_bins(mis_graph *g, const int32_t *bounds);
+
+/* Blocks of the persistent round kernel for later solves on `g` (0 = default:
+ * one per 256 vertices), clamped to what can be co-resident on the device;
+ * mis_get_grid returns the value in use.  Used by the autotuner. */
+int mis_set_grid(mis_graph *g, int32_t blocks);
+int32_t mis_get_grid(const mis_graph *g);
 
 /* Bytes of device memory held by the handle (graph + workspace). */
 int64_t mis_footprint(const mis_graph *g);

@@ -49,21 +49,61 @@ void dfree(void* p) {
     if (p) cudaFree(p);
 }
 
-// Lanes per row from the average degree (the autotuner may override).
-int auto_tpr(double avg_deg) {
-    if (avg_deg <= 12.0) return 4;
-    if (avg_deg <= 40.0) return 8;
-    if (avg_deg <= 120.0) return 16;
-    return 32;
+// Default degree-bin bounds: bin 0 (one lane per row) up to degree 8, bin 1
+// (4 lanes) up to 4096, bin 2 (16 lanes) unused, bin 3 (a warp) up to 65536,
+// bin 4 (a block per row) beyond.  Narrow groups win because most scans stop
+// at their first few arcs; the autotuner refines the bounds per graph.
+constexpr int32_t kDefaultThr[4] = {8, 4096, 4096, 65536};
+
+// Bin bounds that force every vertex into the bin of `tpr` lanes
+// (0 = default bins; 512 = a whole block per row).
+bool thresholds_for(int tpr, int32_t thr[4]) {
+    const int32_t none = -1, all = INT32_MAX;
+    int force;
+    switch (tpr) {
+        case 0:
+            for (int k = 0; k < 4; ++k) thr[k] = kDefaultThr[k];
+            return true;
+        case 1: force = 0; break;
+        case 4: force = 1; break;
+        case 16: force = 2; break;
+        case 32: force = 3; break;
+        case 512: force = 4; break;
+        default: return false;
+    }
+    for (int k = 0; k < 4; ++k) thr[k] = k < force ? none : all;
+    return true;
 }
 
-int pick_grid(mis_graph* g) {
-    const int maxb = csr_max_coresident_blocks(g->tpr, g->d.device);
+// Persistent grid: one block per 256 vertices, at most the co-resident limit
+// (3 blocks of 512 threads per SM); `request` > 0 overrides (clamped).
+int pick_grid(mis_graph* g, int request = 0) {
+    const int maxb = csr_max_coresident_blocks(g->d.device);
     if (maxb <= 0) return 0;
-    const int rows_per_pass = (csr_block_size() / 32) * (32 / g->tpr);
-    long long want = ((long long)g->d.n + 2LL * rows_per_pass - 1) / (2LL * rows_per_pass);
+    long long want = request > 0 ? request : ((long long)g->d.n + 255) / 256;
     if (want < 1) want = 1;
     return (int)std::min<long long>(want, maxb);
+}
+
+SegTable seg_of(const GraphData& d) {
+    SegTable t;
+    t.count = d.count;
+    t.blk_seg = d.blk_seg;
+    t.voff = d.voff;
+    t.nv = d.nv;
+    t.arcs = d.garcs;
+    t.roff = d.roff;
+    t.seed = d.seeds;
+    return t;
+}
+
+// (Re)build the round-0 list grouped by degree bin for thresholds thr.
+int rebin(mis_graph* g, const int32_t thr[4], cudaStream_t s) {
+    GraphData& d = g->d;
+    for (int j = 0; j < 4; ++j) d.thr[j] = thr[j];
+    cudaError_t e = build_bins(d.rp, d.n, seg_of(d), d.thr, d.order0, d.bin_off, s);
+    if (e != cudaSuccess) return set_cuda_error(e, "degree binning");
+    return MIS_OK;
 }
 
 // Allocate the per-solve workspace and choose the launch shape.
@@ -73,18 +113,27 @@ int finish_create(mis_graph* g) {
     if ((e = dalloc(&d.word, d.n, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.wl0, d.n, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.wl1, d.n, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.stage, d.n, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.order0, d.n, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.ctl, 1, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.times, 1, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.out, d.result_bytes, &d.footprint)) != cudaSuccess)
         return set_cuda_error(e, "workspace allocation");
-    if ((e = cudaMallocHost((void**)&d.ctl_host, sizeof(Ctl))) != cudaSuccess)
+    if ((e = cudaMallocHost((void**)&d.ctl_host, sizeof(Ctl))) != cudaSuccess ||
+        (e = cudaMallocHost((void**)&d.times_host, sizeof(PhaseTimes))) != cudaSuccess)
         return set_cuda_error(e, "pinned allocation");
     std::memset(d.ctl_host, 0, sizeof(Ctl));
-    const double avg = d.n ? (double)d.arcs / (double)d.n : 0.0;
-    g->tpr = g->opt.threads_per_row ? g->opt.threads_per_row : auto_tpr(avg);
+    g->tpr = g->opt.threads_per_row;
     g->path = MIS_PATH_CSR;
     g->grid = pick_grid(g);
     if (g->grid <= 0) return set_error(MIS_EDEVICE, "no co-resident blocks for the round kernel");
-    return MIS_OK;
+    int32_t thr[4];
+    thresholds_for(g->tpr, thr);
+    if (!g->own_stream) {
+        e = cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return set_cuda_error(e, "stream");
+    }
+    return rebin(g, thr, g->own_stream);
 }
 
 int validate_device(mis_graph* g, cudaStream_t s) {
@@ -118,14 +167,12 @@ SolveArgs make_args(mis_graph* g) {
     a.word = d.word;
     a.wl0 = d.wl0;
     a.wl1 = d.wl1;
+    a.stage = d.stage;
+    a.order0 = d.order0;
+    for (int j = 0; j < 6; ++j) a.bin_off[j] = d.bin_off[j];
     a.ctl = d.ctl;
-    a.seg.count = d.count;
-    a.seg.blk_seg = d.blk_seg;
-    a.seg.voff = d.voff;
-    a.seg.nv = d.nv;
-    a.seg.arcs = d.garcs;
-    a.seg.roff = d.roff;
-    a.seg.seed = d.seeds;
+    a.times = d.times;
+    a.seg = seg_of(d);
     a.spin_cap = g->opt.spin_cap > 0 ? g->opt.spin_cap : kDefaultSpinCap;
     a.max_rounds = d.n + 2;
     a.trp = d.trp;
@@ -159,8 +206,12 @@ void free_graph(mis_graph* g) {
     dfree(d.word);
     dfree(d.wl0);
     dfree(d.wl1);
+    dfree(d.stage);
+    dfree(d.order0);
     dfree(d.ctl);
     if (d.ctl_host) cudaFreeHost(d.ctl_host);
+    dfree(d.times);
+    if (d.times_host) cudaFreeHost(d.times_host);
     dfree(d.out);
     dfree(d.flags);
     if (g->own_stream) cudaStreamDestroy(g->own_stream);
@@ -184,9 +235,10 @@ int solve_async(mis_graph* g, const uint64_t* seeds, uint8_t* out_dev, cudaStrea
         if (e != cudaSuccess) return set_cuda_error(e, "seed upload");
     }
     e = cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.times, 0, sizeof(PhaseTimes), s);
     if (e != cudaSuccess) return set_cuda_error(e, "control reset");
     if (d.n > 0) {
-        e = launch_csr_solve(a, g->tpr, g->grid, s);
+        e = launch_csr_solve(a, g->grid, s);
         if (e != cudaSuccess) return set_cuda_error(e, "round kernel launch");
     }
     g->last_stream = s;
@@ -220,7 +272,9 @@ int mis_last_error(const char** msg) {
 
 const char* mis_version(void) { return "tcmis-gb300 0.1 (sm_103a)"; }
 
-static bool valid_tpr(int t) { return t == 0 || t == 4 || t == 8 || t == 16 || t == 32; }
+static bool valid_tpr(int t) {
+    return t == 0 || t == 1 || t == 4 || t == 16 || t == 32 || t == 512;
+}
 
 mis_graph* mis_create_ex(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
                          int32_t on_device, const mis_options* opt, void* stream) {
@@ -233,7 +287,7 @@ mis_graph* mis_create_ex(int32_t n, const int32_t* row_ptr, const int32_t* col_i
     mis_options_init(&o);
     if (opt) o = *opt;
     if (!valid_tpr(o.threads_per_row)) {
-        set_error(MIS_EINVAL, "threads_per_row must be 0, 4, 8, 16 or 32");
+        set_error(MIS_EINVAL, "threads_per_row must be 0, 1, 4, 16, 32 or 512");
         return nullptr;
     }
     cudaError_t e = cudaSetDevice(o.device);
@@ -323,7 +377,7 @@ mis_graph* mis_create_batch(int32_t count, const int32_t* ns, const int32_t* con
     mis_options_init(&o);
     if (opt) o = *opt;
     if (!valid_tpr(o.threads_per_row)) {
-        set_error(MIS_EINVAL, "threads_per_row must be 0, 4, 8, 16 or 32");
+        set_error(MIS_EINVAL, "threads_per_row must be 0, 1, 4, 16, 32 or 512");
         return nullptr;
     }
     std::vector<int32_t> voff(count), nv(count), garcs(count);
@@ -466,13 +520,42 @@ int mis_set_path(mis_graph* g, int32_t path, int32_t threads_per_row) {
     if (path != MIS_PATH_AUTO && path != MIS_PATH_CSR)
         return set_error(MIS_EINVAL, "path not available");
     std::lock_guard<std::mutex> lk(g->mu);
-    const double avg = g->d.n ? (double)g->d.arcs / (double)g->d.n : 0.0;
-    g->tpr = threads_per_row ? threads_per_row : auto_tpr(avg);
+    cudaError_t e = cudaSetDevice(g->d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
     g->path = MIS_PATH_CSR;
-    cudaSetDevice(g->d.device);
-    g->grid = pick_grid(g);
-    return MIS_OK;
+    if (threads_per_row == g->tpr) return MIS_OK;
+    g->tpr = threads_per_row;
+    int32_t thr[4];
+    thresholds_for(g->tpr, thr);
+    if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+    return rebin(g, thr, g->own_stream);
 }
+
+int mis_set_csr_bins(mis_graph* g, const int32_t* bounds) {
+    clear_error();
+    if (!g || !bounds) return set_error(MIS_EINVAL, "null argument");
+    if (!(bounds[0] <= bounds[1] && bounds[1] <= bounds[2] && bounds[2] <= bounds[3]))
+        return set_error(MIS_EINVAL, "bin bounds must be non-decreasing");
+    std::lock_guard<std::mutex> lk(g->mu);
+    cudaError_t e = cudaSetDevice(g->d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+    g->tpr = 0;
+    g->path = MIS_PATH_CSR;
+    return rebin(g, bounds, g->own_stream);
+}
+
+int mis_set_grid(mis_graph* g, int32_t blocks) {
+    clear_error();
+    if (!g || blocks < 0) return set_error(MIS_EINVAL, "null graph or negative block count");
+    std::lock_guard<std::mutex> lk(g->mu);
+    cudaError_t e = cudaSetDevice(g->d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    g->grid = pick_grid(g, blocks);
+    return g->grid > 0 ? MIS_OK : set_error(MIS_EDEVICE, "no co-resident blocks");
+}
+
+int32_t mis_get_grid(const mis_graph* g) { return g ? g->grid : 0; }
 
 int mis_solve_ex(mis_graph* g, const uint64_t* seeds, uint8_t* out_status, void* stream) {
     clear_error();
@@ -521,8 +604,11 @@ int mis_get_stats(mis_graph* g, mis_stats* st) {
     if (e == cudaSuccess && g->last_stream) e = cudaStreamSynchronize(g->last_stream);
     if (e == cudaSuccess)
         e = cudaMemcpy(g->d.ctl_host, g->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->d.times_host, g->d.times, sizeof(PhaseTimes), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return set_cuda_error(e, "stats");
     const Ctl& c = *g->d.ctl_host;
+    const PhaseTimes& tm = *g->d.times_host;
     std::memset(st, 0, sizeof(*st));
     st->rounds = c.rounds;
     st->path = g->last_path;
@@ -530,6 +616,15 @@ int mis_get_stats(mis_graph* g, mis_stats* st) {
     st->alive_sum = (int64_t)c.alive_sum;
     st->mis_size = (int64_t)c.mis_size;
     for (int r = 0; r < 64 && r < kStatRounds; ++r) st->alive_per_round[r] = c.alive[r];
+    auto span = [&](int a, int b) -> int64_t {
+        return (tm.t[a] && tm.t[b] && tm.t[b] >= tm.t[a]) ? (int64_t)(tm.t[b] - tm.t[a]) : 0;
+    };
+    st->init_ns = span(0, 1);
+    for (int r = 0; r < 64 && r < kStatRounds && r < c.rounds; ++r) {
+        const int start = r == 0 ? 1 : 2 + kStatRounds + r - 1;
+        st->select_ns[r] = span(start, 2 + r);
+        st->exclude_ns[r] = span(2 + r, 2 + kStatRounds + r);
+    }
     st->status = c.err == 0 ? MIS_OK : (c.err == kErrTimedOut ? MIS_ETIMEDOUT : MIS_EINTERNAL);
     if (st->status != MIS_OK)
         return set_error(st->status, st->status == MIS_ETIMEDOUT

@@ -36,6 +36,7 @@ constexpr int kErrTimedOut = -4;
 constexpr int kErrInternal = -6;
 
 constexpr int kStatRounds = 64;
+constexpr int kBins = 5;  // degree bins of the CSR round kernel
 
 // Control block of one solve in device memory; zeroed before every launch.
 struct Ctl {
@@ -47,9 +48,24 @@ struct Ctl {
     unsigned long long alive_sum;
     unsigned long long mis_size;
     int alive[kStatRounds];
-    unsigned grab[4];     // dynamic work counters, ring indexed by phase & 3
-    int pad[24];
+    unsigned grab[4][kBins];  // per-bin work counters, ring indexed by round & 3
+    int bcnt[4][kBins];       // per-bin worklist sizes, ring indexed by round & 3
+    int alive_acc[4];         // |A| at round start, ring indexed by round & 3
 };
+
+// Phase timestamps of one solve (device %globaltimer, ns), written by the
+// last block to reach each grid barrier: t[0] kernel start, t[1] end of the
+// priority init, t[2 + r] end of Phase 1 of round r, t[2 + kStatRounds + r]
+// end of Phases 2+3 of round r (rounds beyond kStatRounds are not recorded).
+struct PhaseTimes {
+    unsigned long long t[2 * kStatRounds + 2];
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // ---------------------------------------------------------------- Eq. 1
 
@@ -82,6 +98,12 @@ __device__ __forceinline__ uint32_t eq1_key(float dbar, int32_t deg, uint64_t se
 // ---------------------------------------------------------------- memory helpers
 
 __device__ __forceinline__ uint32_t ld_word(const uint32_t* p) { return __ldcg(p); }
+
+// Word load through L1.  Safe for the round kernels: the L1 is invalidated by
+// the acquire in every grid barrier, and inside one round a stale copy can only
+// hide a change that does not alter any test of that round (see the state
+// notes of the CSR kernel).
+__device__ __forceinline__ uint32_t ld_word_l1(const uint32_t* p) { return *p; }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;

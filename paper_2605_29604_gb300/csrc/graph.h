@@ -47,8 +47,14 @@ struct GraphData {
     uint32_t* word = nullptr;
     int32_t* wl0 = nullptr;
     int32_t* wl1 = nullptr;
+    int32_t* stage = nullptr;
+    int32_t* order0 = nullptr;
+    int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};
+    int32_t thr[4] = {0, 0, 0, 0};
     Ctl* ctl = nullptr;
     Ctl* ctl_host = nullptr;  // pinned
+    PhaseTimes* times = nullptr;
+    PhaseTimes* times_host = nullptr;  // pinned
     uint8_t* out = nullptr;   // device result for host-output solves
     unsigned* flags = nullptr;
     int64_t footprint = 0;
@@ -60,7 +66,7 @@ struct mis_graph {
     tcmis::GraphData d;
     mis_options opt{};
     int32_t path = MIS_PATH_CSR;  // resolved path
-    int32_t tpr = 8;              // resolved threads per row
+    int32_t tpr = 0;              // forced lanes per row (0 = degree bins)
     int32_t grid = 0;             // persistent grid size
     cudaStream_t own_stream = nullptr;
     cudaStream_t last_stream = nullptr;

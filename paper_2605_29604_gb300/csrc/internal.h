@@ -7,6 +7,7 @@
 namespace tcmis {
 
 struct Ctl;
+struct PhaseTimes;
 
 // Per-graph parameters of Eq. 1 for a block-diagonal union (count == 0: one
 // graph, seed in `seed0`, average degree from row_ptr[n] / n).
@@ -29,11 +30,16 @@ struct SolveArgs {
     int32_t* wl0 = nullptr;        // worklists, n each
     int32_t* wl1 = nullptr;
     Ctl* ctl = nullptr;            // control block (zeroed before launch)
+    PhaseTimes* times = nullptr;   // phase timestamps (nullable)
     uint8_t* out = nullptr;        // result bytes (device), nullable
     SegTable seg;                  // batch segments
     uint64_t seed0 = 0;            // single-graph seed
     long long spin_cap = 0;        // barrier poll limit
     int32_t max_rounds = 0;        // round cap (error beyond)
+    // degree bins of the CSR kernel
+    const int32_t* order0 = nullptr;  // round-0 list: real vertices grouped by bin
+    int32_t* stage = nullptr;         // per-block staging of survivors, n
+    int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};  // bin j occupies [bin_off[j], bin_off[j+1])
     // tile-CSR (used by the tile kernels only)
     const int32_t* trp = nullptr;  // tile row-block pointer
     const int32_t* tcol = nullptr; // tile column-block index
@@ -47,9 +53,12 @@ struct LaunchCfg {
 };
 
 // kernels_csr.cu
-cudaError_t launch_csr_solve(const SolveArgs& a, int threads_per_row, int grid, cudaStream_t s);
-int csr_max_coresident_blocks(int threads_per_row, int device);
+cudaError_t launch_csr_solve(const SolveArgs& a, int grid, cudaStream_t s);
+int csr_max_coresident_blocks(int device);
 int csr_block_size();
+// Round-0 list grouped by degree bin (thr: inclusive upper degree of bins 0..3).
+cudaError_t build_bins(const int32_t* rp, int32_t n, const SegTable& seg, const int32_t thr[4],
+                       int32_t* order0, int32_t bin_off[6], cudaStream_t s);
 
 // kernels_util.cu
 cudaError_t launch_validate(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs,

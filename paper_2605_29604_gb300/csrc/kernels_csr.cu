@@ -4,24 +4,32 @@
 //
 //   init      Eq. 1 priority of every vertex into its packed word (Sec. 2:
 //             priorities assigned once and reused every round)
-//   rounds    Algorithm 2's while-loop.  Each round has two phases separated
-//             by a grid barrier, both over the worklist of undecided vertices:
+//   rounds    Algorithm 2's while-loop; each round has two phases over the
+//             worklist W_r of undecided vertices, separated by grid barriers:
 //               Phase 1  selection test: v is a candidate when no undecided
 //                        neighbour outranks it (C(v) = [P(v) > Max_Np(v)]);
 //                        candidates are marked in the MIS in place.
 //               Phase 2+3 exclusion test and state update: an undecided
-//                        non-candidate with a candidate neighbour
-//                        (N_c(v) > 0) is marked out; the rest are appended to
-//                        the next round's worklist (compaction).
+//                        non-candidate with a candidate neighbour (N_c(v) > 0)
+//                        is marked out; the others form W_{r+1} (compaction).
 //             Both phases read only what the round-start snapshot fixes (see
-//             common.cuh), so the rounds match Algorithm 2 exactly.
+//             common.cuh), so rounds and alive-set sizes match Algorithm 2.
 //   output    result bytes out[v] = [v in the MIS].
 //
-// Rows are scanned by groups of TPR lanes (4, 8, 16 or 32), each lane
-// loading 16-byte aligned int4 slices of col_idx and gathering the four
-// neighbour words; a group stops at the first neighbour that decides its
-// test (a blocker in Phase 1, a candidate in Phase 2).
+// Worklists are split into degree bins (fixed at create time, degrees do not
+// change): bin j holds the vertices with deg in (thr[j-1], thr[j]].  Bins 0..3
+// are scanned by groups of 1, 4, 16 and 32 lanes, bin 4 (hubs) by a whole
+// block.  Warps take chunks of a bin's list through an atomic counter (heavy
+// bins first; the chunk shrinks when a bin is small so that the chunks spread
+// over all warps).  In Phase 2 a chunk is first triaged one vertex per lane
+// (candidates need no scan), the remaining vertices are scanned by groups,
+// and survivors are staged in shared memory and appended to the next list
+// with one atomic per chunk.  Each lane loads 16-byte aligned int4 slices of
+// col_idx and gathers the four neighbour words; scans stop at the first
+// neighbour that decides the test.
+#include <algorithm>
 #include <cstdio>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -29,10 +37,24 @@
 namespace tcmis {
 
 constexpr int kCsrBlock = 512;
+constexpr int kCsrMinBlocksPerSm = 3;
+constexpr int kWarps = kCsrBlock / 32;
 
-// Any neighbour of the row [b, e) satisfying the phase's test, for the group
-// of TPR lanes this lane belongs to.  Warp-uniform control flow: every lane of
-// the warp runs the loop until no group in the warp has work left.
+// Rows per chunk taken by one warp, per bin (bin 4 is taken a row at a time
+// by a whole block).
+constexpr int kChunk0 = 256, kChunk1 = 128, kChunk2 = 64, kChunk3 = 32;
+constexpr int kStageMax = 256;
+
+// Does u outrank v in the selection test?  `wu` is u's word, `wv` v's
+// (undecided, so wv is v's key): out words never outrank, undecided ones
+// compare by key then id, an in word (a candidate of this round) always does.
+__device__ __forceinline__ bool outranks(uint32_t wu, int u, uint32_t wv, int v) {
+    return wu > wv || (wu == wv && u > v);
+}
+
+// Scan of the row [b, e) of v by the group of TPR lanes of this lane; kSelect:
+// is there a neighbour that outranks v, else: is there an in neighbour.
+// Warp-uniform loop: every lane of the warp iterates until no group has work.
 template <int TPR, bool kSelect>
 __device__ __forceinline__ bool group_scan(const int32_t* __restrict__ col,
                                            const uint32_t* __restrict__ word, int b, int e,
@@ -44,14 +66,13 @@ __device__ __forceinline__ bool group_scan(const int32_t* __restrict__ col,
         bool hit = false;
         if (!found && p0 < e) {
             const int4 c = __ldg(reinterpret_cast<const int4*>(col + p0));
-            const uint32_t w0 = (p0 >= b) ? ld_word(word + c.x) : 0u;
-            const uint32_t w1 = (p0 + 1 >= b && p0 + 1 < e) ? ld_word(word + c.y) : 0u;
-            const uint32_t w2 = (p0 + 2 >= b && p0 + 2 < e) ? ld_word(word + c.z) : 0u;
-            const uint32_t w3 = (p0 + 3 >= b && p0 + 3 < e) ? ld_word(word + c.w) : 0u;
+            const uint32_t w0 = (p0 >= b) ? ld_word_l1(word + c.x) : 0u;
+            const uint32_t w1 = (p0 + 1 >= b && p0 + 1 < e) ? ld_word_l1(word + c.y) : 0u;
+            const uint32_t w2 = (p0 + 2 >= b && p0 + 2 < e) ? ld_word_l1(word + c.z) : 0u;
+            const uint32_t w3 = (p0 + 3 >= b && p0 + 3 < e) ? ld_word_l1(word + c.w) : 0u;
             if (kSelect) {
-                hit = (w0 > wv) | (w1 > wv) | (w2 > wv) | (w3 > wv) |
-                      ((w0 == wv) & (c.x > v)) | ((w1 == wv) & (c.y > v)) |
-                      ((w2 == wv) & (c.z > v)) | ((w3 == wv) & (c.w > v));
+                hit = outranks(w0, c.x, wv, v) | outranks(w1, c.y, wv, v) |
+                      outranks(w2, c.z, wv, v) | outranks(w3, c.w, wv, v);
             } else {
                 hit = max(max(w0, w1), max(w2, w3)) >= kWordInMin;
             }
@@ -65,19 +86,178 @@ __device__ __forceinline__ bool group_scan(const int32_t* __restrict__ col,
     return found;
 }
 
-template <int TPR>
-__global__ void __launch_bounds__(kCsrBlock, 2) csr_solve_kernel(const SolveArgs a) {
-    constexpr int G = 32 / TPR;  // rows per warp pass
+// Chunk size for a bin of `cnt` rows: at most CH, fewer when the bin is
+// small so that the chunks spread over all warps; a multiple of G.
+template <int G, int CH>
+__device__ __forceinline__ int chunk_of(int cnt) {
+    const long long nwarps = (long long)gridDim.x * (blockDim.x / 32);
+    long long per = (cnt + nwarps - 1) / nwarps;
+    per = ((per + G - 1) / G) * G;
+    if (per < G) per = G;
+    return per < CH ? (int)per : CH;
+}
+
+__device__ __forceinline__ long long global_warp() {
+    return (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+}
+
+// Phase 1, bins 0..3: selection test of every row of the bin's list.
+template <int TPR, int CH>
+__device__ __forceinline__ void select_bin(const SolveArgs& a, const int32_t* __restrict__ list,
+                                           int cnt, unsigned* grab) {
+    constexpr int G = 32 / TPR;
+    if (cnt <= 0) return;
     const unsigned lane = lane_id();
     const unsigned glane = lane % TPR;
     const unsigned gid = lane / TPR;
     const unsigned gshift = gid * TPR;
+    const int ch = chunk_of<G, CH>(cnt);
+    if (global_warp() >= (cnt + ch - 1) / ch) return;
+    for (;;) {
+        int c0 = 0;
+        if (lane == 0) c0 = (int)atomicAdd(grab, (unsigned)ch);
+        c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
+        if (c0 >= cnt) break;
+        const int c1 = min(c0 + ch, cnt);
+        for (int base = c0; base < c1; base += G) {
+            const int item = base + (int)gid;
+            const bool valid = item < c1;
+            const int v = valid ? list[item] : 0;
+            // every vertex of W_r is undecided and nothing else writes its
+            // word in this phase, so each lane may load it
+            const uint32_t wv = valid ? ld_word_l1(a.word + v) : 0u;
+            const int b = valid ? a.rp[v] : 0;
+            const int e = valid ? a.rp[v + 1] : 0;
+            const bool blocked = group_scan<TPR, true>(a.col, a.word, b, e, v, wv, glane, gshift);
+            if (valid && !blocked && glane == 0) a.word[v] = wv | kWordInSet;
+        }
+    }
+}
+
+// Phase 2+3, bins 0..3: triage, exclusion test, compaction.
+template <int TPR, int CH>
+__device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int32_t* __restrict__ list,
+                                            int cnt, unsigned* grab, int* next,
+                                            int32_t* __restrict__ dst, int32_t* wscan,
+                                            int32_t* wkeep) {
+    static_assert(CH <= kStageMax, "chunk exceeds the staging buffers");
+    constexpr int G = 32 / TPR;
+    if (cnt <= 0) return;
+    const unsigned lane = lane_id();
+    const unsigned glane = lane % TPR;
+    const unsigned gid = lane / TPR;
+    const unsigned gshift = gid * TPR;
+    const int ch = chunk_of<G, CH>(cnt);
+    if (global_warp() >= (cnt + ch - 1) / ch) return;
+    for (;;) {
+        int c0 = 0;
+        if (lane == 0) c0 = (int)atomicAdd(grab, (unsigned)ch);
+        c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
+        if (c0 >= cnt) break;
+        const int c1 = min(c0 + ch, cnt);
+        // triage, one vertex per lane: candidates of Phase 1 are done
+        int nscan = 0;
+        for (int base = c0; base < c1; base += 32) {
+            const int item = base + (int)lane;
+            const int v = item < c1 ? list[item] : -1;
+            const bool scan = v >= 0 && ld_word_l1(a.word + v) < kWordInMin;
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, scan);
+            if (scan) wscan[nscan + __popc(bal & lanemask_lt())] = v;
+            nscan += __popc(bal);
+        }
+        __syncwarp();
+        // exclusion test of the remaining (undecided) vertices
+        int nkeep = 0;
+        for (int base = 0; base < nscan; base += G) {
+            const int item = base + (int)gid;
+            const bool valid = item < nscan;
+            const int v = valid ? wscan[item] : 0;
+            const int b = valid ? a.rp[v] : 0;
+            const int e = valid ? a.rp[v + 1] : 0;
+            const bool excl = group_scan<TPR, false>(a.col, a.word, b, e, v, 0u, glane, gshift);
+            const bool lead = glane == 0;
+            if (valid && excl && lead) a.word[v] = kWordOut;
+            const bool keep = valid && !excl && lead;
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+            if (keep) wkeep[nkeep + __popc(bal & lanemask_lt())] = v;
+            nkeep += __popc(bal);
+        }
+        __syncwarp();
+        if (nkeep) {
+            int o = 0;
+            if (lane == 0) o = atomicAdd(next, nkeep);
+            o = __shfl_sync(0xFFFFFFFFu, o, 0);
+            for (int i = (int)lane; i < nkeep; i += 32) dst[o + i] = wkeep[i];
+        }
+        __syncwarp();
+    }
+}
+
+// Bin 4 (hubs): the whole block scans one row at a time.  kSelect: Phase 1,
+// else Phase 2+3 (survivors appended one by one: hub rows are few).
+template <bool kSelect>
+__device__ __forceinline__ void block_bin(const SolveArgs& a, const int32_t* __restrict__ list,
+                                          int cnt, unsigned* grab, int* next,
+                                          int32_t* __restrict__ dst) {
+    __shared__ int s_row;
+    if ((int)blockIdx.x >= cnt) return;  // no row left for this block
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_row = (int)atomicAdd(grab, 1u);
+        __syncthreads();
+        const int item = s_row;
+        if (item >= cnt) break;
+        const int v = list[item];
+        // the word of v does not change during this row's scan in either phase
+        const uint32_t wv = ld_word_l1(a.word + v);
+        if (!kSelect && wv >= kWordInMin) continue;  // a candidate: nothing to do
+        const int b = a.rp[v];
+        const int e = a.rp[v + 1];
+        bool found = false;
+        for (int base = b & ~3; base < e; base += 4 * (int)blockDim.x) {
+            const int p0 = base + 4 * (int)threadIdx.x;
+            bool hit = false;
+            if (p0 < e) {
+                const int4 c = __ldg(reinterpret_cast<const int4*>(a.col + p0));
+                const uint32_t w0 = (p0 >= b) ? ld_word_l1(a.word + c.x) : 0u;
+                const uint32_t w1 = (p0 + 1 >= b && p0 + 1 < e) ? ld_word_l1(a.word + c.y) : 0u;
+                const uint32_t w2 = (p0 + 2 >= b && p0 + 2 < e) ? ld_word_l1(a.word + c.z) : 0u;
+                const uint32_t w3 = (p0 + 3 >= b && p0 + 3 < e) ? ld_word_l1(a.word + c.w) : 0u;
+                if (kSelect)
+                    hit = outranks(w0, c.x, wv, v) | outranks(w1, c.y, wv, v) |
+                          outranks(w2, c.z, wv, v) | outranks(w3, c.w, wv, v);
+                else
+                    hit = max(max(w0, w1), max(w2, w3)) >= kWordInMin;
+            }
+            if (__syncthreads_or(hit)) {
+                found = true;
+                break;
+            }
+        }
+        if (threadIdx.x == 0) {
+            if (kSelect) {
+                if (!found) a.word[v] = wv | kWordInSet;
+            } else if (found) {
+                a.word[v] = kWordOut;
+            } else {
+                dst[atomicAdd(next, 1)] = v;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
+    csr_solve_kernel(const SolveArgs a) {
+    __shared__ int32_t s_scan[kWarps][kStageMax];
+    __shared__ int32_t s_keep[kWarps][kStageMax];
+    const unsigned lane = lane_id();
     const unsigned nblocks = gridDim.x;
-    const int wpb = blockDim.x / 32;
-    const long long gwarp = (long long)blockIdx.x * wpb + threadIdx.x / 32;
-    const long long nwarps = (long long)nblocks * wpb;
     Ctl* ctl = a.ctl;
+    PhaseTimes* times = a.times;
     const int32_t n = a.n;
+    int32_t* wscan = s_scan[threadIdx.x / 32];
+    int32_t* wkeep = s_keep[threadIdx.x / 32];
+    if (times && blockIdx.x == 0 && threadIdx.x == 0) times->t[0] = global_ns();
 
     // ---- init: Eq. 1 priorities
     {
@@ -109,61 +289,66 @@ __global__ void __launch_bounds__(kCsrBlock, 2) csr_solve_kernel(const SolveArgs
             a.word[v] = w;
         }
     }
-    if (!grid_barrier(ctl, nblocks, a.spin_cap, NoLeader())) return;
+    if (!grid_barrier(ctl, nblocks, a.spin_cap, [times]() {
+            if (times) times->t[1] = global_ns();
+        }))
+        return;
 
-    int count = n;  // round 0 works on the identity list
-    for (int r = 0;; ++r) {
-        const int32_t* wl_in = (r == 0) ? nullptr : ((r & 1) ? a.wl1 : a.wl0);
-        int32_t* wl_out = ((r + 1) & 1) ? a.wl1 : a.wl0;
-        int* next_cnt = &ctl->cnt[(r + 1) & 3];
+    int cnt[kBins];
+    int total = 0;
+    for (int j = 0; j < kBins; ++j) {
+        cnt[j] = a.bin_off[j + 1] - a.bin_off[j];
+        total += cnt[j];
+    }
+    const int* off = a.bin_off;
+    for (int r = 0; total > 0; ++r) {
+        const int32_t* src = (r == 0) ? a.order0 : ((r & 1) ? a.wl1 : a.wl0);
+        int32_t* dst = ((r + 1) & 1) ? a.wl1 : a.wl0;
+        int* next = ctl->bcnt[(r + 1) & 3];
 
         // ---- Phase 1: selection test
-        for (long long pass = gwarp; pass * G < count; pass += nwarps) {
-            const long long item = pass * G + gid;
-            const bool valid = item < count;
-            const int v = valid ? (wl_in ? wl_in[item] : (int)item) : 0;
-            const uint32_t wv = valid ? ld_word(a.word + v) : 0u;
-            const bool und = valid && (wv >> 29) == 1u;
-            const int b = und ? a.rp[v] : 0;
-            const int e = und ? a.rp[v + 1] : 0;
-            const bool blocked = group_scan<TPR, true>(a.col, a.word, b, e, v, wv, glane, gshift);
-            if (und && !blocked && glane == 0) a.word[v] = wv | kWordInSet;
-        }
-        if (!grid_barrier(ctl, nblocks, a.spin_cap, NoLeader())) return;
+        unsigned* grab = ctl->grab[(2 * r) & 3];
+        block_bin<true>(a, src + off[4], cnt[4], &grab[4], nullptr, nullptr);
+        select_bin<32, kChunk3>(a, src + off[3], cnt[3], &grab[3]);
+        select_bin<16, kChunk2>(a, src + off[2], cnt[2], &grab[2]);
+        select_bin<4, kChunk1>(a, src + off[1], cnt[1], &grab[1]);
+        select_bin<1, kChunk0>(a, src + off[0], cnt[0], &grab[0]);
+        const int rr = r;
+        if (!grid_barrier(ctl, nblocks, a.spin_cap, [ctl, times, rr]() {
+                if (times && rr < kStatRounds) times->t[2 + rr] = global_ns();
+                for (int j = 0; j < kBins; ++j) ctl->grab[(2 * rr + 2) & 3][j] = 0;
+            }))
+            return;
 
         // ---- Phase 2+3: exclusion test, state update, compaction
-        for (long long pass = gwarp; pass * G < count; pass += nwarps) {
-            const long long item = pass * G + gid;
-            const bool valid = item < count;
-            const int v = valid ? (wl_in ? wl_in[item] : (int)item) : 0;
-            const uint32_t wv = valid ? ld_word(a.word + v) : 0u;
-            const bool und = valid && (wv >> 29) == 1u;
-            const int b = und ? a.rp[v] : 0;
-            const int e = und ? a.rp[v + 1] : 0;
-            const bool excl = group_scan<TPR, false>(a.col, a.word, b, e, v, wv, glane, gshift);
-            const bool lead = glane == 0;
-            if (und && excl && lead) a.word[v] = kWordOut;
-            const bool keep = und && !excl && lead;
-            const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
-            if (bal) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(next_cnt, __popc(bal));
-                base = __shfl_sync(0xFFFFFFFFu, base, 0);
-                if (keep) wl_out[base + __popc(bal & lanemask_lt())] = v;
-            }
-        }
-        const int rr = r;
-        const int cur = count;
-        if (!grid_barrier(ctl, nblocks, a.spin_cap, [ctl, rr, cur]() {
+        grab = ctl->grab[(2 * r + 1) & 3];
+        block_bin<false>(a, src + off[4], cnt[4], &grab[4], &next[4], dst + off[4]);
+        exclude_bin<32, kChunk3>(a, src + off[3], cnt[3], &grab[3], &next[3], dst + off[3],
+                                 wscan, wkeep);
+        exclude_bin<16, kChunk2>(a, src + off[2], cnt[2], &grab[2], &next[2], dst + off[2],
+                                 wscan, wkeep);
+        exclude_bin<4, kChunk1>(a, src + off[1], cnt[1], &grab[1], &next[1], dst + off[1],
+                                wscan, wkeep);
+        exclude_bin<1, kChunk0>(a, src + off[0], cnt[0], &grab[0], &next[0], dst + off[0],
+                                wscan, wkeep);
+        const int cur = total;
+        if (!grid_barrier(ctl, nblocks, a.spin_cap, [ctl, times, rr, cur]() {
+                if (times && rr < kStatRounds) times->t[2 + kStatRounds + rr] = global_ns();
                 if (rr < kStatRounds) ctl->alive[rr] = cur;
                 ctl->alive_sum += (unsigned long long)cur;
                 ctl->rounds = rr + 1;
-                ctl->cnt[(rr + 2) & 3] = 0;
+                for (int j = 0; j < kBins; ++j) {
+                    ctl->grab[(2 * rr + 3) & 3][j] = 0;
+                    ctl->bcnt[(rr + 2) & 3][j] = 0;
+                }
             }))
             return;
-        count = ld_acquire_int(next_cnt);
-        if (count == 0) break;
-        if (r + 1 >= a.max_rounds) {
+        total = 0;
+        for (int j = 0; j < kBins; ++j) {
+            cnt[j] = ld_acquire_int(&next[j]);
+            total += cnt[j];
+        }
+        if (total > 0 && r + 1 >= a.max_rounds) {
             if (threadIdx.x == 0) atomicCAS(&ctl->err, 0, kErrInternal);
             return;
         }
@@ -190,40 +375,142 @@ __global__ void __launch_bounds__(kCsrBlock, 2) csr_solve_kernel(const SolveArgs
     }
 }
 
-template <int TPR>
-static cudaError_t launch_t(const SolveArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_csr_solve(const SolveArgs& a, int grid, cudaStream_t s) {
     void* args[] = {const_cast<SolveArgs*>(&a)};
-    return cudaLaunchCooperativeKernel((const void*)csr_solve_kernel<TPR>, dim3(grid),
+    return cudaLaunchCooperativeKernel((const void*)csr_solve_kernel, dim3(grid),
                                        dim3(kCsrBlock), args, 0, s);
-}
-
-cudaError_t launch_csr_solve(const SolveArgs& a, int tpr, int grid, cudaStream_t s) {
-    switch (tpr) {
-        case 4: return launch_t<4>(a, grid, s);
-        case 8: return launch_t<8>(a, grid, s);
-        case 16: return launch_t<16>(a, grid, s);
-        case 32: return launch_t<32>(a, grid, s);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 int csr_block_size() { return kCsrBlock; }
 
-int csr_max_coresident_blocks(int tpr, int device) {
+int csr_max_coresident_blocks(int device) {
     int per_sm = 0, sms = 0;
-    const void* fn = nullptr;
-    switch (tpr) {
-        case 4: fn = (const void*)csr_solve_kernel<4>; break;
-        case 8: fn = (const void*)csr_solve_kernel<8>; break;
-        case 16: fn = (const void*)csr_solve_kernel<16>; break;
-        case 32: fn = (const void*)csr_solve_kernel<32>; break;
-        default: return 0;
-    }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCsrBlock, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)csr_solve_kernel,
+                                                      kCsrBlock, 0) != cudaSuccess)
         return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return 0;
     return per_sm * sms;
+}
+
+// ---------------------------------------------------------------- degree bins
+//
+// order0 = the round-0 list: every real vertex (batch padding excluded),
+// grouped by bin, ascending id inside a bin.  Two kernels: per-block bin
+// counts, then (after the host turns the counts into offsets) a stable
+// scatter.  Blocks own contiguous vertex ranges.
+
+struct BinThr {
+    int32_t t[kBins - 1];
+};
+
+__device__ __forceinline__ int bin_of(int deg, const BinThr& thr) {
+    int j = 0;
+#pragma unroll
+    for (int k = 0; k < kBins - 1; ++k) j += deg > thr.t[k];
+    return j;
+}
+
+__device__ __forceinline__ bool is_real(const SegTable& seg, long long v) {
+    if (seg.count == 0) return true;
+    const int g = seg.blk_seg[v >> 4];
+    return (int)v - seg.voff[g] < seg.nv[g];
+}
+
+__global__ void bin_count_kernel(const int32_t* __restrict__ rp, int32_t n, const SegTable seg,
+                                 const BinThr thr, int32_t* __restrict__ blkcnt) {
+    __shared__ int c[kBins];
+    if (threadIdx.x < kBins) c[threadIdx.x] = 0;
+    __syncthreads();
+    const long long v0 = (long long)n * blockIdx.x / gridDim.x;
+    const long long v1 = (long long)n * (blockIdx.x + 1) / gridDim.x;
+    for (long long v = v0 + threadIdx.x; v < v1; v += blockDim.x)
+        if (is_real(seg, v)) atomicAdd(&c[bin_of(rp[v + 1] - rp[v], thr)], 1);
+    __syncthreads();
+    if (threadIdx.x < kBins) blkcnt[blockIdx.x * kBins + threadIdx.x] = c[threadIdx.x];
+}
+
+// blockDim.x must be 256
+__global__ void bin_scatter_kernel(const int32_t* __restrict__ rp, int32_t n, const SegTable seg,
+                                   const BinThr thr, const int32_t* __restrict__ blkoff,
+                                   int32_t* __restrict__ order0) {
+    __shared__ int wsum[8][kBins];
+    __shared__ int run[kBins];
+    const unsigned lane = lane_id();
+    const int w = threadIdx.x / 32;
+    if (threadIdx.x < kBins) run[threadIdx.x] = blkoff[blockIdx.x * kBins + threadIdx.x];
+    __syncthreads();
+    const long long v0 = (long long)n * blockIdx.x / gridDim.x;
+    const long long v1 = (long long)n * (blockIdx.x + 1) / gridDim.x;
+    for (long long c0 = v0; c0 < v1; c0 += blockDim.x) {
+        const long long v = c0 + threadIdx.x;
+        int j = -1;
+        if (v < v1 && is_real(seg, v)) j = bin_of(rp[v + 1] - rp[v], thr);
+        int rank = 0;
+        for (int b = 0; b < kBins; ++b) {
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, j == b);
+            if (j == b) rank = __popc(m & lanemask_lt());
+            if (lane == 0) wsum[w][b] = __popc(m);
+        }
+        __syncthreads();
+        if (j >= 0) {
+            int off = run[j];
+            for (int x = 0; x < w; ++x) off += wsum[x][j];
+            order0[off + rank] = (int32_t)v;
+        }
+        __syncthreads();
+        if (threadIdx.x < kBins) {
+            int t = 0;
+            for (int x = 0; x < 8; ++x) t += wsum[x][threadIdx.x];
+            run[threadIdx.x] += t;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t build_bins(const int32_t* rp, int32_t n, const SegTable& seg, const int32_t thr[4],
+                       int32_t* order0, int32_t bin_off[6], cudaStream_t s) {
+    for (int j = 0; j <= kBins; ++j) bin_off[j] = 0;
+    if (n == 0) return cudaSuccess;
+    const int blocks = (int)std::min<long long>(1024, ((long long)n + 255) / 256);
+    BinThr t;
+    for (int k = 0; k < kBins - 1; ++k) t.t[k] = thr[k];
+    int32_t* d_cnt = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d_cnt, sizeof(int32_t) * blocks * kBins);
+    if (e != cudaSuccess) return e;
+    std::vector<int32_t> h((size_t)blocks * kBins);
+    bin_count_kernel<<<blocks, 256, 0, s>>>(rp, n, seg, t, d_cnt);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), d_cnt, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+        int64_t tot[kBins] = {};
+        for (int b = 0; b < blocks; ++b)
+            for (int j = 0; j < kBins; ++j) tot[j] += h[(size_t)b * kBins + j];
+        int64_t acc = 0;
+        for (int j = 0; j < kBins; ++j) {
+            bin_off[j] = (int32_t)acc;
+            acc += tot[j];
+        }
+        bin_off[kBins] = (int32_t)acc;
+        int64_t run[kBins];
+        for (int j = 0; j < kBins; ++j) run[j] = bin_off[j];
+        for (int b = 0; b < blocks; ++b)
+            for (int j = 0; j < kBins; ++j) {
+                const int32_t c = h[(size_t)b * kBins + j];
+                h[(size_t)b * kBins + j] = (int32_t)run[j];
+                run[j] += c;
+            }
+        e = cudaMemcpyAsync(d_cnt, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) {
+        bin_scatter_kernel<<<blocks, 256, 0, s>>>(rp, n, seg, t, d_cnt, order0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_cnt);
+    return e;
 }
 
 }  // namespace tcmis

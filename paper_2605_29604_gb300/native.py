@@ -55,7 +55,8 @@ class mis_stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("threads_per_row", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("alive_sum", ctypes.c_int64), ("mis_size", ctypes.c_int64),
-                ("alive_per_round", ctypes.c_int64 * 64)]
+                ("alive_per_round", ctypes.c_int64 * 64), ("init_ns", ctypes.c_int64),
+                ("select_ns", ctypes.c_int64 * 64), ("exclude_ns", ctypes.c_int64 * 64)]
 
 
 _lock = threading.Lock()
@@ -97,6 +98,12 @@ def lib():
         L.mis_keys_ex.restype = ctypes.c_int
         L.mis_set_path.argtypes = [P, i32, i32]
         L.mis_set_path.restype = ctypes.c_int
+        L.mis_set_grid.argtypes = [P, i32]
+        L.mis_set_grid.restype = ctypes.c_int
+        L.mis_get_grid.argtypes = [P]
+        L.mis_get_grid.restype = i32
+        L.mis_set_csr_bins.argtypes = [P, P]
+        L.mis_set_csr_bins.restype = ctypes.c_int
         L.mis_destroy.argtypes = [P]
         L.mis_destroy.restype = None
         L.mis_submit.argtypes = [P, u64, P, ctypes.POINTER(i64)]
@@ -123,7 +130,7 @@ def lib():
 EXPORTED = [
     "mis_options_init", "mis_create", "mis_create_ex", "mis_create_batch", "mis_graph_count",
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
-    "mis_set_path", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_wait",
+    "mis_set_path", "mis_set_csr_bins", "mis_set_grid", "mis_get_grid", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
     "mis_solve_noalloc",
 ]
@@ -237,6 +244,19 @@ def mis_solve_noalloc(n, row_ptr_ptr, col_idx_ptr, seed, out_ptr, stream=None):
 
 def mis_set_path(h, path, threads_per_row=0):
     return _check(lib().mis_set_path(h, path, threads_per_row))
+
+
+def mis_set_csr_bins(h, bounds):
+    b = np.ascontiguousarray(np.asarray(bounds, dtype=np.int32))
+    return _check(lib().mis_set_csr_bins(h, _ptr(b)))
+
+
+def mis_set_grid(h, blocks):
+    return _check(lib().mis_set_grid(h, blocks))
+
+
+def mis_get_grid(h):
+    return lib().mis_get_grid(h)
 
 
 def mis_destroy(h):

@@ -56,7 +56,7 @@ def test_null_arguments_rejected_without_device(lib):
     assert code == native.MIS_EINVAL and msg
     assert lib.mis_create_ex(-1, None, None, 0, None, None) is None
     assert native.last_error()[0] == native.MIS_EINVAL
-    o = native.options(threads_per_row=3)
+    o = native.options(threads_per_row=8)
     assert lib.mis_create_ex(0, None, None, 0, ctypes.byref(o), None) is None
     assert native.last_error()[0] == native.MIS_EINVAL
 

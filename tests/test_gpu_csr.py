@@ -68,7 +68,7 @@ def test_keys_bit_exact(name):
 
 
 @pytest.mark.parametrize("name", sorted(FAMILIES))
-@pytest.mark.parametrize("tpr", [4, 8, 16, 32])
+@pytest.mark.parametrize("tpr", [0, 1, 4, 16, 32, 512])
 def test_csr_solve_bit_exact(name, tpr):
     g = graph(name)
     h = create(g)
@@ -79,6 +79,21 @@ def test_csr_solve_bit_exact(name, tpr):
             assert_same(g, seed, got, st)
     finally:
         native.mis_destroy(h)
+
+
+@pytest.mark.parametrize("bounds", [(2, 5, 9, 20), (-1, 3, 3, 3), (0, 0, 100000, 100000),
+                                    (1, 2, 3, 4), (-1, -1, -1, 2)])
+def test_csr_custom_bins(bounds):
+    for name in ("rmat14", "grid_perm", "star_hub"):
+        g = graph(name)
+        h = create(g)
+        try:
+            native.mis_set_csr_bins(h, bounds)
+            got, st = gpu_solve(h, [5])
+            assert st.threads_per_row == 0
+            assert_same(g, 5, got, st)
+        finally:
+            native.mis_destroy(h)
 
 
 def test_zero_vertices():
