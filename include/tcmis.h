@@ -81,8 +81,8 @@ typedef struct mis_options {
                                 whole block), else 1, 4, 16, 32 or 512 lanes for
                                 every row */
     int32_t check_symmetry;  /* 1 (default) = verify symmetry at create, 0 = trust */
-    int32_t build_tiles;     /* 1 = build tile-CSR at create; -1 (default) = when the
-                                autotuner or a forced tile path needs it; 0 = never */
+    int32_t build_tiles;     /* 1 = build the 16 x 16 tile-CSR at create; -1 (default)
+                                = when a tile path is first selected */
     int64_t spin_cap;        /* device barrier spin limit in polls; 0 = default
                                 (about one second); the test suite uses small values */
     int32_t device;          /* CUDA device ordinal; default 0 */
@@ -98,6 +98,9 @@ typedef struct mis_stats {
     int32_t threads_per_row; /* CSR path: lanes per row forced for every row, or 0
                                 when rows are binned by degree */
     int32_t status;          /* MIS_OK or the error of that solve */
+    int32_t tile;            /* tile size of the graph's tile-CSR (0 = not built) */
+    int32_t pad0;
+    int64_t ntiles;          /* non-empty tiles of that tile-CSR */
     int64_t alive_sum;       /* sum over rounds of |A| at round start */
     int64_t mis_size;        /* |M| */
     int64_t alive_per_round[64]; /* |A| at the start of rounds 0..63 (0 beyond) */
@@ -175,9 +178,12 @@ int mis_get_stats(mis_graph *g, mis_stats *stats);
  */
 int mis_keys_ex(mis_graph *g, const uint64_t *seeds, uint32_t *out_key, void *stream);
 
-/* Select the round kernel (MIS_PATH_*) and lanes per row (as in mis_options)
- * for later solves. */
-int mis_set_path(mis_graph *g, int32_t path, int32_t threads_per_row);
+/* Select the round kernel for later solves.  MIS_PATH_CSR (or AUTO): `param`
+ * is the lanes per row as in mis_options.threads_per_row.  MIS_PATH_TILE:
+ * `param` is the tile size, 8 or 16 (0 = 16); MIS_PATH_TILE_TC: 16 (or 0).
+ * The tile-CSR (non-empty tiles only, 0/1 bitmask payloads) is built on the
+ * device the first time a tile size is selected. */
+int mis_set_path(mis_graph *g, int32_t path, int32_t param);
 
 /* CSR path with degree bins: bounds[0..3] are the inclusive upper degrees of
  * bins 0..3 (1, 4, 16 and 32 lanes per row; bin 4, a block of 512 threads per
@@ -190,6 +196,12 @@ int mis_set_csr_bins(mis_graph *g, const int32_t *bounds);
  * mis_get_grid returns the value in use.  Used by the autotuner. */
 int mis_set_grid(mis_graph *g, int32_t blocks);
 int32_t mis_get_grid(const mis_graph *g);
+
+/* Copy the graph's tile-CSR into DEVICE buffers on `stream` (for testing):
+ * trp int32[nrb+1] (nrb = ceil(n / T)), tcol int32[ntiles], tbits uint64[ntiles
+ * * T * T / 64] (row-major bits: bit i*T + j of a tile is entry (i, j)).  Sizes
+ * come from mis_get_stats (tile, ntiles).  Any pointer may be NULL. */
+int mis_tiles_ex(mis_graph *g, int32_t *trp, int32_t *tcol, uint64_t *tbits, void *stream);
 
 /* Bytes of device memory held by the handle (graph + workspace). */
 int64_t mis_footprint(const mis_graph *g);

@@ -106,11 +106,61 @@ int rebin(mis_graph* g, const int32_t thr[4], cudaStream_t s) {
     return MIS_OK;
 }
 
+void free_tiles(GraphData& d) {
+    dfree(d.tiles.trp);
+    dfree(d.tiles.tcol);
+    dfree(d.tiles.tbits);
+    d.tiles = TileCsr();
+    d.footprint -= d.tile_footprint;
+    d.tile_footprint = 0;
+}
+
+// Switch to a tile path with T x T tiles, building the tile-CSR when needed.
+int use_tiles(mis_graph* g, int path, int T) {
+    GraphData& d = g->d;
+    if (T != 8 && T != 16) return set_error(MIS_EINVAL, "tile size must be 8 or 16");
+    if (path == MIS_PATH_TILE_TC && T != 16)
+        return set_error(MIS_EINVAL, "the tensor-core tile path uses 16 x 16 tiles");
+    cudaError_t e = cudaSuccess;
+    const int64_t npad = ((int64_t)d.n + 15) / 16 * 16;
+    if (!d.inbits) {
+        if ((e = dalloc(&d.inbits, npad / 32 + 1, &d.footprint)) != cudaSuccess ||
+            (e = dalloc(&d.rbl0, npad / 8, &d.footprint)) != cudaSuccess ||
+            (e = dalloc(&d.rbl1, npad / 8, &d.footprint)) != cudaSuccess)
+            return set_cuda_error(e, "tile workspace");
+    }
+    if (d.tiles.T != T) {
+        if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+        free_tiles(d);
+        e = build_tiles(d.rp, d.col, d.n, d.arcs, T, &d.tiles, g->own_stream);
+        if (e != cudaSuccess) {
+            free_tiles(d);
+            return set_cuda_error(e, "tile-CSR conversion");
+        }
+        const int words = T * T / 64;
+        d.tile_footprint = 4 * ((int64_t)d.tiles.nrb + 1) + 4 * d.tiles.ntiles +
+                           8 * (int64_t)words * d.tiles.ntiles;
+        d.footprint += d.tile_footprint;
+    }
+    const bool tc = path == MIS_PATH_TILE_TC;
+    // a row block with many tiles gets a whole warp of tile slots
+    const double per_rb = d.tiles.nrb ? (double)d.tiles.ntiles / d.tiles.nrb : 0.0;
+    g->tile_slots = per_rb > 12.0 ? 32 : 8;
+    const int maxb = tile_max_coresident_blocks(T, g->tile_slots, tc, d.device);
+    if (maxb <= 0) return set_error(MIS_EDEVICE, "no co-resident blocks for the tile kernel");
+    long long want = ((long long)d.tiles.nrb + 63) / 64;
+    if (want < 1) want = 1;
+    g->tile_grid = (int)std::min<long long>(want, maxb);
+    g->path = path;
+    return MIS_OK;
+}
+
 // Allocate the per-solve workspace and choose the launch shape.
 int finish_create(mis_graph* g) {
     GraphData& d = g->d;
     cudaError_t e;
-    if ((e = dalloc(&d.word, d.n, &d.footprint)) != cudaSuccess ||
+    const int64_t npad = ((int64_t)d.n + 15) / 16 * 16;  // tile kernels read whole blocks
+    if ((e = dalloc(&d.word, npad, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.wl0, d.n, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.wl1, d.n, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.stage, d.n, &d.footprint)) != cudaSuccess ||
@@ -133,7 +183,15 @@ int finish_create(mis_graph* g) {
         e = cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return set_cuda_error(e, "stream");
     }
-    return rebin(g, thr, g->own_stream);
+    const int brc = rebin(g, thr, g->own_stream);
+    if (brc != MIS_OK) return brc;
+    if (g->opt.build_tiles == 1 || g->opt.path == MIS_PATH_TILE || g->opt.path == MIS_PATH_TILE_TC) {
+        const int rc = use_tiles(g, g->opt.path == MIS_PATH_AUTO || g->opt.path == MIS_PATH_CSR
+                                        ? MIS_PATH_TILE : g->opt.path, 16);
+        if (rc != MIS_OK) return rc;
+        if (g->opt.path == MIS_PATH_AUTO || g->opt.path == MIS_PATH_CSR) g->path = MIS_PATH_CSR;
+    }
+    return MIS_OK;
 }
 
 int validate_device(mis_graph* g, cudaStream_t s) {
@@ -175,9 +233,13 @@ SolveArgs make_args(mis_graph* g) {
     a.seg = seg_of(d);
     a.spin_cap = g->opt.spin_cap > 0 ? g->opt.spin_cap : kDefaultSpinCap;
     a.max_rounds = d.n + 2;
-    a.trp = d.trp;
-    a.tcol = d.tcol;
-    a.tbits = d.tbits;
+    a.trp = d.tiles.trp;
+    a.tcol = d.tiles.tcol;
+    a.tbits = d.tiles.tbits;
+    a.nrb = d.tiles.nrb;
+    a.inbits = d.inbits;
+    a.rbl0 = d.rbl0;
+    a.rbl1 = d.rbl1;
     return a;
 }
 
@@ -200,9 +262,10 @@ void free_graph(mis_graph* g) {
     dfree(d.roff);
     dfree(d.seeds);
     if (d.seeds_host) cudaFreeHost(d.seeds_host);
-    dfree(d.trp);
-    dfree(d.tcol);
-    dfree(d.tbits);
+    free_tiles(d);
+    dfree(d.inbits);
+    dfree(d.rbl0);
+    dfree(d.rbl1);
     dfree(d.word);
     dfree(d.wl0);
     dfree(d.wl1);
@@ -238,11 +301,15 @@ int solve_async(mis_graph* g, const uint64_t* seeds, uint8_t* out_dev, cudaStrea
     if (e == cudaSuccess) e = cudaMemsetAsync(d.times, 0, sizeof(PhaseTimes), s);
     if (e != cudaSuccess) return set_cuda_error(e, "control reset");
     if (d.n > 0) {
-        e = launch_csr_solve(a, g->grid, s);
+        if (g->path == MIS_PATH_TILE || g->path == MIS_PATH_TILE_TC)
+            e = launch_tile_solve(a, d.tiles.T, g->tile_slots, g->path == MIS_PATH_TILE_TC,
+                                  g->tile_grid, s);
+        else
+            e = launch_csr_solve(a, g->grid, s);
         if (e != cudaSuccess) return set_cuda_error(e, "round kernel launch");
     }
     g->last_stream = s;
-    g->last_path = MIS_PATH_CSR;
+    g->last_path = g->path;
     return MIS_OK;
 }
 
@@ -516,12 +583,15 @@ int64_t mis_footprint(const mis_graph* g) { return g ? g->d.footprint : 0; }
 int mis_set_path(mis_graph* g, int32_t path, int32_t threads_per_row) {
     clear_error();
     if (!g) return set_error(MIS_EINVAL, "null graph");
-    if (!valid_tpr(threads_per_row)) return set_error(MIS_EINVAL, "bad threads_per_row");
-    if (path != MIS_PATH_AUTO && path != MIS_PATH_CSR)
-        return set_error(MIS_EINVAL, "path not available");
+    if ((path == MIS_PATH_CSR || path == MIS_PATH_AUTO) && !valid_tpr(threads_per_row))
+        return set_error(MIS_EINVAL, "bad threads_per_row");
+    if (path < MIS_PATH_AUTO || path > MIS_PATH_TILE_TC)
+        return set_error(MIS_EINVAL, "unknown path");
     std::lock_guard<std::mutex> lk(g->mu);
     cudaError_t e = cudaSetDevice(g->d.device);
     if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    if (path == MIS_PATH_TILE || path == MIS_PATH_TILE_TC)
+        return use_tiles(g, path, threads_per_row ? threads_per_row : 16);
     g->path = MIS_PATH_CSR;
     if (threads_per_row == g->tpr) return MIS_OK;
     g->tpr = threads_per_row;
@@ -556,6 +626,25 @@ int mis_set_grid(mis_graph* g, int32_t blocks) {
 }
 
 int32_t mis_get_grid(const mis_graph* g) { return g ? g->grid : 0; }
+
+int mis_tiles_ex(mis_graph* g, int32_t* trp, int32_t* tcol, uint64_t* tbits, void* stream) {
+    clear_error();
+    if (!g) return set_error(MIS_EINVAL, "null graph");
+    std::lock_guard<std::mutex> lk(g->mu);
+    const TileCsr& t = g->d.tiles;
+    if (t.T == 0) return set_error(MIS_EINVAL, "no tile-CSR built (select a tile path first)");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(g->d.device);
+    if (e == cudaSuccess && trp)
+        e = cudaMemcpyAsync(trp, t.trp, 4 * ((size_t)t.nrb + 1), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && tcol && t.ntiles)
+        e = cudaMemcpyAsync(tcol, t.tcol, 4 * (size_t)t.ntiles, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && tbits && t.ntiles)
+        e = cudaMemcpyAsync(tbits, t.tbits, 8 * (size_t)(t.T * t.T / 64) * (size_t)t.ntiles,
+                            cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return set_cuda_error(e, "tile export");
+    return MIS_OK;
+}
 
 int mis_solve_ex(mis_graph* g, const uint64_t* seeds, uint8_t* out_status, void* stream) {
     clear_error();
@@ -613,6 +702,8 @@ int mis_get_stats(mis_graph* g, mis_stats* st) {
     st->rounds = c.rounds;
     st->path = g->last_path;
     st->threads_per_row = g->tpr;
+    st->tile = g->d.tiles.T;
+    st->ntiles = g->d.tiles.ntiles;
     st->alive_sum = (int64_t)c.alive_sum;
     st->mis_size = (int64_t)c.mis_size;
     for (int r = 0; r < 64 && r < kStatRounds; ++r) st->alive_per_round[r] = c.alive[r];

@@ -39,10 +39,11 @@ struct GraphData {
     std::vector<int32_t> h_nv;       // per graph vertices (host copy)
     int64_t result_bytes = 0;        // sum of the graphs' n
     // tile-CSR (built on demand)
-    int32_t* trp = nullptr;
-    int32_t* tcol = nullptr;
-    uint64_t* tbits = nullptr;
-    int64_t ntiles = 0;
+    TileCsr tiles;
+    uint32_t* inbits = nullptr;  // in-set bit vector for the tile kernels
+    int32_t* rbl0 = nullptr;     // row-block worklists (sized for 8-row blocks)
+    int32_t* rbl1 = nullptr;
+    int64_t tile_footprint = 0;
     // workspace of one solve
     uint32_t* word = nullptr;
     int32_t* wl0 = nullptr;
@@ -67,7 +68,9 @@ struct mis_graph {
     mis_options opt{};
     int32_t path = MIS_PATH_CSR;  // resolved path
     int32_t tpr = 0;              // forced lanes per row (0 = degree bins)
-    int32_t grid = 0;             // persistent grid size
+    int32_t grid = 0;             // persistent grid size (CSR kernel)
+    int32_t tile_grid = 0;        // persistent grid size (tile kernels)
+    int32_t tile_slots = 8;       // tile kernels: lanes (tiles in flight) per row block
     cudaStream_t own_stream = nullptr;
     cudaStream_t last_stream = nullptr;
     int32_t last_path = 0;

@@ -1,0 +1,48 @@
+// init.cuh -- the priority initialisation shared by the round kernels.
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace tcmis {
+
+// Eq. 1 priority of every vertex v < n_words into its packed word (Sec. 2:
+// assigned once per solve).  Vertices at or beyond a.n (tile padding) and
+// batch padding vertices are out; isolated vertices get a fixed key (they
+// have no neighbour to compare with).  Grid-stride over the whole launch.
+__device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const int32_t n = a.n;
+    float dbar0 = 0.f;
+    uint64_t smix0 = 0;
+    if (a.seg.count == 0 && n > 0) {
+        dbar0 = average_degree(a.rp[n], n);
+        smix0 = mix64(a.seed0);
+    }
+    for (long long v = tid; v < n_words; v += nthreads) {
+        uint32_t w;
+        if (v >= n) {
+            w = kWordOut;
+        } else {
+            const int deg = a.rp[v + 1] - a.rp[v];
+            if (a.seg.count == 0) {
+                w = deg ? eq1_key(dbar0, deg, smix0, (uint32_t)v) : kKeyIsolated;
+            } else {
+                const int g = a.seg.blk_seg[v >> 4];
+                const int local = (int)v - a.seg.voff[g];
+                if (local >= a.seg.nv[g]) {
+                    w = kWordOut;  // padding vertex between two graphs
+                } else if (deg == 0) {
+                    w = kKeyIsolated;
+                } else {
+                    const float dbar = average_degree(a.seg.arcs[g], a.seg.nv[g]);
+                    w = eq1_key(dbar, deg, mix64(a.seg.seed[g]), (uint32_t)local);
+                }
+            }
+        }
+        a.word[v] = w;
+    }
+}
+
+}  // namespace tcmis

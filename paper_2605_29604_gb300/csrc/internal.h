@@ -41,9 +41,13 @@ struct SolveArgs {
     int32_t* stage = nullptr;         // per-block staging of survivors, n
     int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};  // bin j occupies [bin_off[j], bin_off[j+1])
     // tile-CSR (used by the tile kernels only)
-    const int32_t* trp = nullptr;  // tile row-block pointer
-    const int32_t* tcol = nullptr; // tile column-block index
-    const uint64_t* tbits = nullptr; // 8x8 bitmask payloads
+    const int32_t* trp = nullptr;    // row block rb owns tiles [trp[rb], trp[rb+1])
+    const int32_t* tcol = nullptr;   // column block of each tile
+    const uint64_t* tbits = nullptr; // T*T/64 words of row-major 0/1 bits per tile
+    int32_t nrb = 0;                 // row blocks = ceil(n / T)
+    uint32_t* inbits = nullptr;      // bit v set once v is in the MIS (nrb*T bits)
+    int32_t* rbl0 = nullptr;         // row-block worklists, nrb each
+    int32_t* rbl1 = nullptr;
 };
 
 // Launch configuration chosen by the host.
@@ -70,6 +74,26 @@ cudaError_t launch_relocate(int32_t* rp, int32_t* col, int32_t n, int32_t arcs, 
                             int32_t aoff, cudaStream_t s);
 cudaError_t launch_pad_rows(int32_t* dst_rp, int32_t from, int32_t to, int32_t value,
                             cudaStream_t s);
+
+// kernels_tile.cu
+struct TileCsr {
+    int T = 0;
+    int32_t nrb = 0;
+    int64_t ntiles = 0;
+    int32_t* trp = nullptr;
+    int32_t* tcol = nullptr;
+    uint64_t* tbits = nullptr;
+};
+// Non-empty T x T tiles of the adjacency (T = 8 or 16), bitmask payloads;
+// allocates out's arrays (the caller frees them with cudaFree).
+cudaError_t build_tiles(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs, int T,
+                        TileCsr* out, cudaStream_t s);
+// Persistent tile round kernel: T = 8 or 16 (tile size), S = 8 or 32 (lanes,
+// i.e. tiles in flight, per row block); tc = exclusion test on tensor cores
+// (T = 16 only).
+cudaError_t launch_tile_solve(const SolveArgs& a, int T, int S, bool tc, int grid,
+                              cudaStream_t s);
+int tile_max_coresident_blocks(int T, int S, bool tc, int device);
 
 // validation flag bits
 constexpr unsigned kBadRowPtr = 1u;

@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "init.cuh"
 #include "internal.h"
 
 namespace tcmis {
@@ -260,35 +261,7 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     if (times && blockIdx.x == 0 && threadIdx.x == 0) times->t[0] = global_ns();
 
     // ---- init: Eq. 1 priorities
-    {
-        const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-        const long long nthreads = (long long)nblocks * blockDim.x;
-        float dbar0 = 0.f;
-        uint64_t smix0 = 0;
-        if (a.seg.count == 0 && n > 0) {
-            dbar0 = average_degree(a.rp[n], n);
-            smix0 = mix64(a.seed0);
-        }
-        for (long long v = tid; v < n; v += nthreads) {
-            const int deg = a.rp[v + 1] - a.rp[v];
-            uint32_t w;
-            if (a.seg.count == 0) {
-                w = deg ? eq1_key(dbar0, deg, smix0, (uint32_t)v) : kKeyIsolated;
-            } else {
-                const int g = a.seg.blk_seg[v >> 4];
-                const int local = (int)v - a.seg.voff[g];
-                if (local >= a.seg.nv[g]) {
-                    w = kWordOut;  // padding vertex between two graphs
-                } else if (deg == 0) {
-                    w = kKeyIsolated;
-                } else {
-                    const float dbar = average_degree(a.seg.arcs[g], a.seg.nv[g]);
-                    w = eq1_key(dbar, deg, mix64(a.seg.seed[g]), (uint32_t)local);
-                }
-            }
-            a.word[v] = w;
-        }
-    }
+    init_words(a, a.n);
     if (!grid_barrier(ctl, nblocks, a.spin_cap, [times]() {
             if (times) times->t[1] = global_ns();
         }))

@@ -54,6 +54,7 @@ class mis_options(ctypes.Structure):
 class mis_stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("threads_per_row", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("pad0", ctypes.c_int32), ("ntiles", ctypes.c_int64),
                 ("alive_sum", ctypes.c_int64), ("mis_size", ctypes.c_int64),
                 ("alive_per_round", ctypes.c_int64 * 64), ("init_ns", ctypes.c_int64),
                 ("select_ns", ctypes.c_int64 * 64), ("exclude_ns", ctypes.c_int64 * 64)]
@@ -102,6 +103,8 @@ def lib():
         L.mis_set_grid.restype = ctypes.c_int
         L.mis_get_grid.argtypes = [P]
         L.mis_get_grid.restype = i32
+        L.mis_tiles_ex.argtypes = [P, P, P, P, P]
+        L.mis_tiles_ex.restype = ctypes.c_int
         L.mis_set_csr_bins.argtypes = [P, P]
         L.mis_set_csr_bins.restype = ctypes.c_int
         L.mis_destroy.argtypes = [P]
@@ -130,7 +133,7 @@ def lib():
 EXPORTED = [
     "mis_options_init", "mis_create", "mis_create_ex", "mis_create_batch", "mis_graph_count",
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
-    "mis_set_path", "mis_set_csr_bins", "mis_set_grid", "mis_get_grid", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_wait",
+    "mis_set_path", "mis_set_csr_bins", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
     "mis_solve_noalloc",
 ]
@@ -257,6 +260,12 @@ def mis_set_grid(h, blocks):
 
 def mis_get_grid(h):
     return lib().mis_get_grid(h)
+
+
+def mis_tiles_ex(h, trp_ptr, tcol_ptr, tbits_ptr, stream=None):
+    return _check(lib().mis_tiles_ex(h, ctypes.c_void_p(trp_ptr), ctypes.c_void_p(tcol_ptr),
+                                     ctypes.c_void_p(tbits_ptr),
+                                     ctypes.c_void_p(stream) if stream else None))
 
 
 def mis_destroy(h):
