@@ -49,6 +49,53 @@ void dfree(void* p) {
     if (p) cudaFree(p);
 }
 
+}  // namespace
+
+int64_t ws_bytes_for(int64_t n, int32_t count) {
+    const int64_t cap = (n + 15) / 16 * 16;
+    return 4 * cap * 3 + (cap / 32 + 1) * 4 + 2 * 4 * (cap / 8) + (int64_t)sizeof(Ctl) +
+           (int64_t)sizeof(PhaseTimes) + 8 * std::max<int64_t>(count, 1) + cap;
+}
+
+void ws_free(Workspace& w) {
+    dfree(w.word);
+    dfree(w.wl0);
+    dfree(w.wl1);
+    dfree(w.inbits);
+    dfree(w.rbl0);
+    dfree(w.rbl1);
+    dfree(w.ctl);
+    dfree(w.times);
+    dfree(w.seeds);
+    dfree(w.out);
+    w = Workspace();
+}
+
+cudaError_t ws_reserve(Workspace& w, int64_t n, int32_t count) {
+    const int64_t cap = (n + 15) / 16 * 16;
+    if (w.word && w.cap >= cap && w.seed_cap >= std::max(count, 1)) return cudaSuccess;
+    ws_free(w);
+    cudaError_t e;
+    int64_t b = 0;
+    if ((e = dalloc(&w.word, cap, &b)) != cudaSuccess || (e = dalloc(&w.wl0, cap, &b)) != cudaSuccess ||
+        (e = dalloc(&w.wl1, cap, &b)) != cudaSuccess ||
+        (e = dalloc(&w.inbits, cap / 32 + 1, &b)) != cudaSuccess ||
+        (e = dalloc(&w.rbl0, cap / 8, &b)) != cudaSuccess ||
+        (e = dalloc(&w.rbl1, cap / 8, &b)) != cudaSuccess ||
+        (e = dalloc(&w.ctl, 1, &b)) != cudaSuccess || (e = dalloc(&w.times, 1, &b)) != cudaSuccess ||
+        (e = dalloc(&w.seeds, std::max(count, 1), &b)) != cudaSuccess ||
+        (e = dalloc(&w.out, cap, &b)) != cudaSuccess) {
+        ws_free(w);
+        return e;
+    }
+    w.cap = cap;
+    w.seed_cap = std::max(count, 1);
+    w.bytes = b;
+    return cudaSuccess;
+}
+
+namespace {
+
 // Default degree-bin bounds: bin 0 (one lane per row) up to degree 8, bin 1
 // (4 lanes) up to 4096, bin 2 (16 lanes) unused, bin 3 (a warp) up to 65536,
 // bin 4 (a block per row) beyond.  Narrow groups win because most scans stop
@@ -93,7 +140,7 @@ SegTable seg_of(const GraphData& d) {
     t.nv = d.nv;
     t.arcs = d.garcs;
     t.roff = d.roff;
-    t.seed = d.seeds;
+    t.seed = nullptr;  // per-solve seeds live in the workspace
     return t;
 }
 
@@ -122,13 +169,6 @@ int use_tiles(mis_graph* g, int path, int T) {
     if (path == MIS_PATH_TILE_TC && T != 16)
         return set_error(MIS_EINVAL, "the tensor-core tile path uses 16 x 16 tiles");
     cudaError_t e = cudaSuccess;
-    const int64_t npad = ((int64_t)d.n + 15) / 16 * 16;
-    if (!d.inbits) {
-        if ((e = dalloc(&d.inbits, npad / 32 + 1, &d.footprint)) != cudaSuccess ||
-            (e = dalloc(&d.rbl0, npad / 8, &d.footprint)) != cudaSuccess ||
-            (e = dalloc(&d.rbl1, npad / 8, &d.footprint)) != cudaSuccess)
-            return set_cuda_error(e, "tile workspace");
-    }
     if (d.tiles.T != T) {
         if (g->last_stream) cudaStreamSynchronize(g->last_stream);
         free_tiles(d);
@@ -159,16 +199,10 @@ int use_tiles(mis_graph* g, int path, int T) {
 int finish_create(mis_graph* g) {
     GraphData& d = g->d;
     cudaError_t e;
-    const int64_t npad = ((int64_t)d.n + 15) / 16 * 16;  // tile kernels read whole blocks
-    if ((e = dalloc(&d.word, npad, &d.footprint)) != cudaSuccess ||
-        (e = dalloc(&d.wl0, d.n, &d.footprint)) != cudaSuccess ||
-        (e = dalloc(&d.wl1, d.n, &d.footprint)) != cudaSuccess ||
-        (e = dalloc(&d.stage, d.n, &d.footprint)) != cudaSuccess ||
-        (e = dalloc(&d.order0, d.n, &d.footprint)) != cudaSuccess ||
-        (e = dalloc(&d.ctl, 1, &d.footprint)) != cudaSuccess ||
-        (e = dalloc(&d.times, 1, &d.footprint)) != cudaSuccess ||
-        (e = dalloc(&d.out, d.result_bytes, &d.footprint)) != cudaSuccess)
+    if ((e = ws_reserve(d.ws, d.n, d.count)) != cudaSuccess ||
+        (e = dalloc(&d.order0, d.n, &d.footprint)) != cudaSuccess)
         return set_cuda_error(e, "workspace allocation");
+    d.footprint += d.ws.bytes;
     if ((e = cudaMallocHost((void**)&d.ctl_host, sizeof(Ctl))) != cudaSuccess ||
         (e = cudaMallocHost((void**)&d.times_host, sizeof(PhaseTimes))) != cudaSuccess)
         return set_cuda_error(e, "pinned allocation");
@@ -216,30 +250,30 @@ int validate_device(mis_graph* g, cudaStream_t s) {
     return MIS_OK;
 }
 
-SolveArgs make_args(mis_graph* g) {
+SolveArgs make_args(mis_graph* g, Workspace& w) {
     GraphData& d = g->d;
     SolveArgs a;
     a.rp = d.rp;
     a.col = d.col;
     a.n = d.n;
-    a.word = d.word;
-    a.wl0 = d.wl0;
-    a.wl1 = d.wl1;
-    a.stage = d.stage;
+    a.word = w.word;
+    a.wl0 = w.wl0;
+    a.wl1 = w.wl1;
     a.order0 = d.order0;
     for (int j = 0; j < 6; ++j) a.bin_off[j] = d.bin_off[j];
-    a.ctl = d.ctl;
-    a.times = d.times;
+    a.ctl = w.ctl;
+    a.times = w.times;
     a.seg = seg_of(d);
+    a.seg.seed = w.seeds;
     a.spin_cap = g->opt.spin_cap > 0 ? g->opt.spin_cap : kDefaultSpinCap;
     a.max_rounds = d.n + 2;
     a.trp = d.tiles.trp;
     a.tcol = d.tiles.tcol;
     a.tbits = d.tiles.tbits;
     a.nrb = d.tiles.nrb;
-    a.inbits = d.inbits;
-    a.rbl0 = d.rbl0;
-    a.rbl1 = d.rbl1;
+    a.inbits = w.inbits;
+    a.rbl0 = w.rbl0;
+    a.rbl1 = w.rbl1;
     return a;
 }
 
@@ -260,54 +294,54 @@ void free_graph(mis_graph* g) {
     dfree(d.nv);
     dfree(d.garcs);
     dfree(d.roff);
-    dfree(d.seeds);
     if (d.seeds_host) cudaFreeHost(d.seeds_host);
     free_tiles(d);
-    dfree(d.inbits);
-    dfree(d.rbl0);
-    dfree(d.rbl1);
-    dfree(d.word);
-    dfree(d.wl0);
-    dfree(d.wl1);
-    dfree(d.stage);
     dfree(d.order0);
-    dfree(d.ctl);
+    ws_free(d.ws);
     if (d.ctl_host) cudaFreeHost(d.ctl_host);
-    dfree(d.times);
     if (d.times_host) cudaFreeHost(d.times_host);
-    dfree(d.out);
     dfree(d.flags);
     if (g->own_stream) cudaStreamDestroy(g->own_stream);
     cudaSetDevice(prev);
     delete g;
 }
 
-// Enqueue one solve on stream s; results (bytes) into out_dev if non-null.
-int solve_async(mis_graph* g, const uint64_t* seeds, uint8_t* out_dev, cudaStream_t s) {
+int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_pinned,
+             uint8_t* out_dev, cudaStream_t s, bool single_block) {
     GraphData& d = g->d;
     cudaError_t e = cudaSetDevice(d.device);
     if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
-    SolveArgs a = make_args(g);
+    SolveArgs a = make_args(g, w);
     a.out = out_dev;
     if (d.count == 0) {
         a.seed0 = seeds[0];
     } else {
-        std::memcpy(d.seeds_host, seeds, sizeof(uint64_t) * (size_t)d.count);
-        e = cudaMemcpyAsync(d.seeds, d.seeds_host, sizeof(uint64_t) * (size_t)d.count,
+        std::memcpy(seeds_pinned, seeds, sizeof(uint64_t) * (size_t)d.count);
+        e = cudaMemcpyAsync(w.seeds, seeds_pinned, sizeof(uint64_t) * (size_t)d.count,
                             cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return set_cuda_error(e, "seed upload");
     }
-    e = cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.times, 0, sizeof(PhaseTimes), s);
+    e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.times, 0, sizeof(PhaseTimes), s);
     if (e != cudaSuccess) return set_cuda_error(e, "control reset");
     if (d.n > 0) {
-        if (g->path == MIS_PATH_TILE || g->path == MIS_PATH_TILE_TC)
+        const bool tile = g->path == MIS_PATH_TILE || g->path == MIS_PATH_TILE_TC;
+        if (tile)
             e = launch_tile_solve(a, d.tiles.T, g->tile_slots, g->path == MIS_PATH_TILE_TC,
-                                  g->tile_grid, s);
+                                  single_block ? 1 : g->tile_grid, s);
+        else if (single_block)
+            e = launch_csr_solve_single(a, s);
         else
             e = launch_csr_solve(a, g->grid, s);
         if (e != cudaSuccess) return set_cuda_error(e, "round kernel launch");
     }
+    return MIS_OK;
+}
+
+// Enqueue one solve on stream s in the handle's own workspace.
+int solve_async(mis_graph* g, const uint64_t* seeds, uint8_t* out_dev, cudaStream_t s) {
+    const int rc = solve_in(g, g->d.ws, seeds, g->d.seeds_host, out_dev, s, false);
+    if (rc != MIS_OK) return rc;
     g->last_stream = s;
     g->last_path = g->path;
     return MIS_OK;
@@ -502,7 +536,6 @@ mis_graph* mis_create_batch(int32_t count, const int32_t* ns, const int32_t* con
         (e = dalloc(&d.nv, count, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.garcs, count, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.roff, count, &d.footprint)) != cudaSuccess ||
-        (e = dalloc(&d.seeds, count, &d.footprint)) != cudaSuccess ||
         (e = cudaMallocHost((void**)&d.seeds_host, sizeof(uint64_t) * (size_t)count)) !=
             cudaSuccess) {
         set_cuda_error(e, "batch allocation");
@@ -588,6 +621,7 @@ int mis_set_path(mis_graph* g, int32_t path, int32_t threads_per_row) {
     if (path < MIS_PATH_AUTO || path > MIS_PATH_TILE_TC)
         return set_error(MIS_EINVAL, "unknown path");
     std::lock_guard<std::mutex> lk(g->mu);
+    if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
     cudaError_t e = cudaSetDevice(g->d.device);
     if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
     if (path == MIS_PATH_TILE || path == MIS_PATH_TILE_TC)
@@ -607,6 +641,7 @@ int mis_set_csr_bins(mis_graph* g, const int32_t* bounds) {
     if (!(bounds[0] <= bounds[1] && bounds[1] <= bounds[2] && bounds[2] <= bounds[3]))
         return set_error(MIS_EINVAL, "bin bounds must be non-decreasing");
     std::lock_guard<std::mutex> lk(g->mu);
+    if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
     cudaError_t e = cudaSetDevice(g->d.device);
     if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
     if (g->last_stream) cudaStreamSynchronize(g->last_stream);
@@ -667,14 +702,14 @@ int mis_solve(mis_graph* g, uint64_t seed, uint8_t* out_status) {
     }
     std::vector<uint64_t> seeds((size_t)std::max(1, g->d.count));
     for (size_t i = 0; i < seeds.size(); ++i) seeds[i] = seed + i;
-    int rc = solve_async(g, seeds.data(), g->d.out, g->own_stream);
+    int rc = solve_async(g, seeds.data(), g->d.ws.out, g->own_stream);
     if (rc != MIS_OK) return rc;
     if (g->d.result_bytes > 0) {
-        e = cudaMemcpyAsync(out_status, g->d.out, (size_t)g->d.result_bytes,
+        e = cudaMemcpyAsync(out_status, g->d.ws.out, (size_t)g->d.result_bytes,
                             cudaMemcpyDeviceToHost, g->own_stream);
         if (e != cudaSuccess) return set_cuda_error(e, "result download");
     }
-    e = cudaMemcpyAsync(g->d.ctl_host, g->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
+    e = cudaMemcpyAsync(g->d.ctl_host, g->d.ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
                         g->own_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->own_stream);
     if (e != cudaSuccess) return set_cuda_error(e, "solve");
@@ -692,9 +727,9 @@ int mis_get_stats(mis_graph* g, mis_stats* st) {
     cudaError_t e = cudaSetDevice(g->d.device);
     if (e == cudaSuccess && g->last_stream) e = cudaStreamSynchronize(g->last_stream);
     if (e == cudaSuccess)
-        e = cudaMemcpy(g->d.ctl_host, g->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(g->d.ctl_host, g->d.ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess)
-        e = cudaMemcpy(g->d.times_host, g->d.times, sizeof(PhaseTimes), cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(g->d.times_host, g->d.ws.times, sizeof(PhaseTimes), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return set_cuda_error(e, "stats");
     const Ctl& c = *g->d.ctl_host;
     const PhaseTimes& tm = *g->d.times_host;
@@ -732,12 +767,12 @@ int mis_keys_ex(mis_graph* g, const uint64_t* seeds, uint32_t* out_key, void* st
     GraphData& d = g->d;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(d.device);
-    SolveArgs a = make_args(g);
+    SolveArgs a = make_args(g, d.ws);
     if (d.count == 0) {
         a.seed0 = seeds[0];
     } else if (e == cudaSuccess) {
         std::memcpy(d.seeds_host, seeds, sizeof(uint64_t) * (size_t)d.count);
-        e = cudaMemcpyAsync(d.seeds, d.seeds_host, sizeof(uint64_t) * (size_t)d.count,
+        e = cudaMemcpyAsync(d.ws.seeds, d.seeds_host, sizeof(uint64_t) * (size_t)d.count,
                             cudaMemcpyHostToDevice, s);
     }
     if (e == cudaSuccess) e = launch_keys(a, out_key, s);
@@ -748,12 +783,7 @@ int mis_keys_ex(mis_graph* g, const uint64_t* seeds, uint32_t* out_key, void* st
 
 void mis_destroy(mis_graph* g) {
     if (!g) return;
-    if (g->inflight.load() > 0) {
-        g->destroy_pending.store(true);
-        serve_release_graph(g);
-        return;
-    }
-    free_graph(g);
+    serve_release_graph(g);  // frees now, or after its last served request
 }
 
 }  // extern "C"

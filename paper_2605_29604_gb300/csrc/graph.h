@@ -19,8 +19,33 @@ int set_error(int code, const std::string& msg);
 int set_cuda_error(cudaError_t e, const char* what);
 void clear_error();
 
+// Device buffers of one solve in flight: vertex words, worklists, the in-set
+// bits and row-block lists of the tile kernels, the control block, phase
+// timestamps, seeds (one per graph of a batch) and the result bytes.
+struct Workspace {
+    int64_t cap = 0;       // vertices held (a multiple of 16)
+    int32_t seed_cap = 0;  // seeds held
+    uint32_t* word = nullptr;
+    int32_t* wl0 = nullptr;
+    int32_t* wl1 = nullptr;
+    uint32_t* inbits = nullptr;
+    int32_t* rbl0 = nullptr;
+    int32_t* rbl1 = nullptr;
+    Ctl* ctl = nullptr;
+    PhaseTimes* times = nullptr;
+    uint64_t* seeds = nullptr;
+    uint8_t* out = nullptr;
+    int64_t bytes = 0;
+};
+
+// Allocate a workspace for graphs of up to n vertices and `count` seeds
+// (frees and reallocates when it is too small); returns the CUDA error.
+cudaError_t ws_reserve(Workspace& w, int64_t n, int32_t count);
+void ws_free(Workspace& w);
+int64_t ws_bytes_for(int64_t n, int32_t count);
+
 // Device buffers of one graph (or one block-diagonal union of graphs) plus
-// the workspace of one solve at a time.
+// the workspace of the handle's own solves.
 struct GraphData {
     int device = 0;
     int32_t n = 0;          // vertices (union size, padding included)
@@ -34,30 +59,21 @@ struct GraphData {
     int32_t* nv = nullptr;
     int32_t* garcs = nullptr;
     int64_t* roff = nullptr;
-    uint64_t* seeds = nullptr;       // device, count entries
     uint64_t* seeds_host = nullptr;  // pinned staging, count entries
     std::vector<int32_t> h_nv;       // per graph vertices (host copy)
     int64_t result_bytes = 0;        // sum of the graphs' n
     // tile-CSR (built on demand)
     TileCsr tiles;
-    uint32_t* inbits = nullptr;  // in-set bit vector for the tile kernels
-    int32_t* rbl0 = nullptr;     // row-block worklists (sized for 8-row blocks)
-    int32_t* rbl1 = nullptr;
     int64_t tile_footprint = 0;
-    // workspace of one solve
-    uint32_t* word = nullptr;
-    int32_t* wl0 = nullptr;
-    int32_t* wl1 = nullptr;
-    int32_t* stage = nullptr;
+    // degree bins of the CSR kernel
     int32_t* order0 = nullptr;
     int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};
     int32_t thr[4] = {0, 0, 0, 0};
-    Ctl* ctl = nullptr;
-    Ctl* ctl_host = nullptr;  // pinned
-    PhaseTimes* times = nullptr;
-    PhaseTimes* times_host = nullptr;  // pinned
-    uint8_t* out = nullptr;   // device result for host-output solves
     unsigned* flags = nullptr;
+    // workspace of the handle's own solves (mis_solve / mis_solve_ex)
+    Workspace ws;
+    Ctl* ctl_host = nullptr;           // pinned
+    PhaseTimes* times_host = nullptr;  // pinned
     int64_t footprint = 0;
 };
 
@@ -83,6 +99,11 @@ namespace tcmis {
 
 // api.cu
 int solve_async(mis_graph* g, const uint64_t* seeds, uint8_t* out_dev, cudaStream_t s);
+// One solve of g on stream s in workspace w; seeds (host, one per graph of
+// the handle) are staged through `seeds_pinned`; single_block: run the round
+// kernel as one block (ordinary launch, no cooperative co-scheduling needed).
+int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_pinned,
+             uint8_t* out_dev, cudaStream_t s, bool single_block);
 void free_graph(mis_graph* g);
 
 // serve.cu

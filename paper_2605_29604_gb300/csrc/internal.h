@@ -38,7 +38,6 @@ struct SolveArgs {
     int32_t max_rounds = 0;        // round cap (error beyond)
     // degree bins of the CSR kernel
     const int32_t* order0 = nullptr;  // round-0 list: real vertices grouped by bin
-    int32_t* stage = nullptr;         // per-block staging of survivors, n
     int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};  // bin j occupies [bin_off[j], bin_off[j+1])
     // tile-CSR (used by the tile kernels only)
     const int32_t* trp = nullptr;    // row block rb owns tiles [trp[rb], trp[rb+1])
@@ -58,6 +57,9 @@ struct LaunchCfg {
 
 // kernels_csr.cu
 cudaError_t launch_csr_solve(const SolveArgs& a, int grid, cudaStream_t s);
+// The same kernel as a single block through an ordinary launch (a lone block
+// needs no co-scheduling guarantee for its barriers).
+cudaError_t launch_csr_solve_single(const SolveArgs& a, cudaStream_t s);
 int csr_max_coresident_blocks(int device);
 int csr_block_size();
 // Round-0 list grouped by degree bin (thr: inclusive upper degree of bins 0..3).

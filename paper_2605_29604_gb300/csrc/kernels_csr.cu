@@ -354,6 +354,11 @@ cudaError_t launch_csr_solve(const SolveArgs& a, int grid, cudaStream_t s) {
                                        dim3(kCsrBlock), args, 0, s);
 }
 
+cudaError_t launch_csr_solve_single(const SolveArgs& a, cudaStream_t s) {
+    csr_solve_kernel<<<1, kCsrBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 int csr_block_size() { return kCsrBlock; }
 
 int csr_max_coresident_blocks(int device) {

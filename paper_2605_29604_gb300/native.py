@@ -11,6 +11,7 @@ buffers are numpy arrays.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 import threading
@@ -126,6 +127,8 @@ def lib():
         L.mis_version.argtypes = []
         L.mis_version.restype = ctypes.c_char_p
         _lib = L
+        # drain and stop the serving thread before the CUDA runtime unloads
+        atexit.register(L.mis_serve_shutdown)
         return L
 
 
@@ -279,11 +282,21 @@ def mis_submit(h, seed, out_status):
 
 
 def mis_poll(ticket):
+    """MIS_OK (done; ticket released), MIS_ENOTREADY, or a negative error."""
     return lib().mis_poll(ticket)
 
 
 def mis_wait(ticket, timeout_us=-1):
+    """Wait for a request; same returns as mis_poll, MIS_ETIMEDOUT on expiry."""
     return lib().mis_wait(ticket, timeout_us)
+
+
+def mis_serve_configure(opt=None):
+    return _check(lib().mis_serve_configure(ctypes.byref(opt) if opt is not None else None))
+
+
+def mis_serve_shutdown():
+    lib().mis_serve_shutdown()
 
 
 class Graph:
