@@ -4,14 +4,17 @@ A step is one full solve of the hot path -- Eq. 1 priorities, then every
 round of Algorithm 2 (selection test, exclusion test, state update,
 compaction) until the alive set is empty -- on a graph already resident in
 HBM.  value = arcs solved / device time of the K timed steps (CUDA events on
-the launching stream, L2 flushed between steps).
+the launching stream; a 256 MB write between steps flushes L2).
 
 Workloads (synthetic, seeded; stand-ins for the paper's SuiteSparse graphs):
   rmat22     R-MAT scale 22, edge factor 16, (0.57, 0.19, 0.19, 0.05), permuted (default)
   er10k      Erdos-Renyi G(10,000, 40,000)
   grid       2048 x 2048 grid + 5% random diagonals, natural ids
   grid_perm  the same grid, permuted ids
-  batch4096  4096 graphs (log-uniform 64..65,536 vertices, ER / random geometric) in one launch
+  batch4096  4096 graphs (log-uniform 64..65,536 vertices, ER / random geometric)
+             packed as one block-diagonal union and solved in one launch
+  serve      Poisson arrivals of solve requests over a resident pool of graphs
+             (continuous batching), graphs/s and p50/p99 vs sequential solves
 
 `--impl reference` times the CPU oracle (a plain sequential restatement of
 the same computation) on the host cores instead.
@@ -22,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -38,6 +42,7 @@ if ROOT not in sys.path:
 METRIC = "edges/s to full MIS on 1 GB300"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+PATH_NAMES = {1: "csr", 2: "tile", 3: "tile_tc"}
 
 
 def _peak_hbm():
@@ -119,29 +124,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(g, repeats=1):
-    """CPU oracle (keys + round simulation), sequential C on one host core."""
+def oracle_rate(g, min_seconds=0.0, max_repeats=1):
+    """CPU oracle (keys + round simulation), sequential C on one host core:
+    edges/s over `repeats` full solves of g (repeated until min_seconds)."""
     import oracle
     n, rp, col = g
     t0 = time.perf_counter()
-    for _ in range(repeats):
+    reps = 0
+    while True:
         res = oracle.solve(n, rp, col, 1)
-    dt = (time.perf_counter() - t0) / repeats
-    return int(rp[-1]) / dt, dt, res
+        reps += 1
+        if reps >= max_repeats and time.perf_counter() - t0 >= min_seconds:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return int(rp[-1]) / dt, dt, res, reps
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    name = args.workload if args.workload != "rmat22" else "rmat18"
+    name = {"rmat22": "rmat18", "batch4096": "er10k", "serve": "er10k"}.get(args.workload,
+                                                                             args.workload)
     g, desc = make_workload(name)
     n, rp, col = g
     for _ in range(args.warmup):
         oracle_rate(g)
     times = []
     for _ in range(args.steps):
-        _, dt, res = oracle_rate(g)
+        _, dt, res, _ = oracle_rate(g)
         times.append(dt)
     total = sum(times)
     value = args.steps * int(rp[-1]) / total
@@ -161,48 +172,58 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
+def _dist_setup():
     import torch
     import torch.distributed as dist
-
-    from paper_2605_29604_gb300 import native
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    return world, rank, local
 
-    g, desc = make_workload(args.workload)
-    n, rp, col = g
-    arcs = int(rp[-1])
-    stream = torch.cuda.current_stream().cuda_stream
-    opt = native.options(device=local, check_symmetry=1)
-    t_create = time.perf_counter()
-    h = native.mis_create_ex(n, rp, col, 0, opt, stream)
-    t_create = time.perf_counter() - t_create
-    if args.tpr:
-        native.mis_set_path(h, native.MIS_PATH_CSR, args.tpr)
-    out = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
-    seeds = np.array([1], dtype=np.uint64)
-    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)
+
+def _max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def time_device_steps(native, h, seeds, out_ptr, stream, steps, warmup, local, world):
+    """Per-step CUDA-event times (L2 flushed between steps), clocks sampled."""
+    import torch
+    import torch.distributed as dist
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
 
     def step():
-        native.mis_solve_ex(h, seeds, out.data_ptr(), stream)
+        native.mis_solve_ex(h, seeds, out_ptr, stream)
 
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         step()
-    st = native.mis_get_stats(h)
+    native.mis_get_stats(h)
     torch.cuda.synchronize()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for i in range(args.steps):
+        for i in range(steps):
             flush.add_(1.0)  # write 256 MB: evicts the previous step from L2
             starts[i].record()
             step()
@@ -211,11 +232,36 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    return step_ms, clk.summary()
+
+
+def run_single(args):
+    import torch
+
+    from paper_2605_29604_gb300 import native
+    world, rank, local = _dist_setup()
+    g, desc = make_workload(args.workload)
+    n, rp, col = g
+    arcs = int(rp[-1])
+    stream = torch.cuda.current_stream().cuda_stream
+    opt = native.options(device=local, check_symmetry=1)
+    t0 = time.perf_counter()
+    h = native.mis_create_ex(n, rp, col, 0, opt, stream)
+    t_create = time.perf_counter() - t0
+    tuning = None
+    if args.tpr is not None:
+        native.mis_set_path(h, native.MIS_PATH_CSR, args.tpr)
+    elif args.path:
+        native.mis_set_path(h, {"tile": 2, "tile_tc": 3}[args.path], args.tile)
+    else:
+        t0 = time.perf_counter()
+        tuning = native.mis_autotune(h, 3)
+        tune_s = time.perf_counter() - t0
+    out = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+    seeds = np.array([1], dtype=np.uint64)
+    step_ms, clocks = time_device_steps(native, h, seeds, out.data_ptr(), stream, args.steps,
+                                        args.warmup, local, world)
+    total_ms = _max_over_ranks(sum(step_ms), world)
     st = native.mis_get_stats(h)
     value = world * args.steps * arcs / (total_ms / 1e3)
 
@@ -234,48 +280,234 @@ def run_ours(args):
             native.mis_destroy(h2)
             if i:
                 times.append(time.perf_counter() - t0)
-        e2e = {"value": world * arcs * len(times) / sum(times), "unit": "edges/s",
+        e2e_s = _max_over_ranks(sum(times), world)
+        e2e = {"value": world * arcs * len(times) / e2e_s, "unit": "edges/s",
                "h2d_bytes_per_step": 4 * (n + 1) + 4 * arcs, "d2h_bytes_per_step": n,
-               "path": "mis_create_ex(host CSR, pinned) + mis_solve(host result) + mis_destroy"}
+               "path": "mis_create_ex(host CSR, pinned; creation-time validation and degree "
+                       "binning included) + mis_solve(host result) + mis_destroy"}
 
     peak, peak_kind = _peak_hbm()
     alg_bytes = 4 * arcs + 4 * (n + 1) + 4 * n + n
     launch_s = (total_ms / 1e3) / args.steps
     achieved = alg_bytes / launch_s / 1e9
+    path = PATH_NAMES.get(st.path, str(st.path))
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": args.workload, "graph": desc, "n": n, "arcs": arcs,
-                   "rounds": st.rounds, "path": "csr", "threads_per_row": st.threads_per_row,
-                   "mis_size": st.mis_size, "l2": "flushed between steps (256 MB write)",
+                   "rounds": st.rounds, "path": path, "threads_per_row": st.threads_per_row,
+                   "tile": st.tile, "mis_size": st.mis_size,
+                   "l2": "flushed between steps (256 MB write); graph (513 MB col_idx for rmat22) "
+                         "also exceeds L2",
                    "parallelism": f"replicas{world}", "create_s": t_create,
-                   "step_ms_p10_p50_p90": [float(np.percentile(step_ms, q)) for q in (10, 50, 90)]},
+                   "step_ms_p10_p50_p90": [float(np.percentile(step_ms, q)) for q in (10, 50, 90)],
+                   "phase_us": {"init": st.init_ns / 1e3,
+                                "select": [st.select_ns[r] / 1e3 for r in range(min(st.rounds, 64))],
+                                "exclude": [st.exclude_ns[r] / 1e3 for r in range(min(st.rounds, 64))]}},
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": args.traffic,
                      "peak_kind": f"{peak_kind} burst copy bandwidth",
                      "alg_bytes_per_launch": alg_bytes,
-                     "kernel": "csr_solve_kernel (one persistent launch per solve)"},
-        "clocks": clk.summary(),
+                     "alg_bytes_def": "4*arcs + 4*(n+1) (one read of the CSR) + 4*n (key words "
+                                      "written) + n (result bytes)",
+                     "kernel": f"{path} persistent round kernel (one launch per solve)"},
+        "clocks": clocks,
         "e2e": e2e,
     }
+    if tuning is not None:
+        line["config"]["autotune"] = {"path": PATH_NAMES.get(tuning.path), "param": tuning.param,
+                                      "bounds": list(tuning.bounds), "grid": tuning.grid,
+                                      "candidates": tuning.candidates, "seconds": tune_s,
+                                      "arcs_per_tile": tuning.arcs_per_tile}
     if rank == 0 and args.cpu_baseline:
         import oracle
-        sample_name = "rmat18" if args.workload == "rmat22" else args.workload
-        gs, sdesc = make_workload(sample_name) if sample_name != args.workload else (g, desc)
-        rate, dt, res = oracle_rate(gs)
-        mdg, _ = oracle.min_degree_greedy(*gs)
+        rate, dt, res, reps = oracle_rate(g, min_seconds=args.cpu_seconds)
+        mdg, _ = oracle.min_degree_greedy(*g)
         line["cpu_baseline"] = {"value": rate, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                                "sample": f"one oracle solve of {sdesc} ({dt:.2f} s)",
+                                "sample": f"{reps} full oracle solve(s) of the same graph "
+                                          f"({dt:.2f} s each)",
                                 "quality": {"mis_size": int(res.status.sum()),
-                                            "min_degree_greedy": mdg}}
+                                            "min_degree_greedy": mdg},
+                                "gpu_result_equals_oracle": bool(np.array_equal(
+                                    out[:n].cpu().numpy(), res.status))}
     native.mis_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
+        import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+def run_batch(args):
+    import torch
+
+    from paper_2605_29604_gb300 import graphgen as gg
+    from paper_2605_29604_gb300 import native
+    world, rank, local = _dist_setup()
+    t0 = time.perf_counter()
+    parts = gg.batch_mixed(args.batch_count, seed=4096, nmin=64, nmax=65536)
+    t_gen = time.perf_counter() - t0
+    arcs = int(sum(int(p[1][-1]) for p in parts))
+    nsum = int(sum(p[0] for p in parts))
+    t0 = time.perf_counter()
+    h = native.mis_create_batch(parts, native.options(device=local, check_symmetry=1))
+    t_create = time.perf_counter() - t0
+    tuning = native.mis_autotune(h, 3)
+    size = native.lib().mis_result_size(h)
+    out = torch.empty(max(size, 1), dtype=torch.uint8, device="cuda")
+    seeds = np.arange(1, len(parts) + 1, dtype=np.uint64)
+    stream = torch.cuda.current_stream().cuda_stream
+    step_ms, clocks = time_device_steps(native, h, seeds, out.data_ptr(), stream, args.steps,
+                                        args.warmup, local, world)
+    total_ms = _max_over_ranks(sum(step_ms), world)
+    st = native.mis_get_stats(h)
+    value = world * args.steps * arcs / (total_ms / 1e3)
+    peak, peak_kind = _peak_hbm()
+    alg_bytes = 4 * arcs + 4 * (nsum + 1) + 4 * nsum + nsum
+    achieved = alg_bytes / ((total_ms / 1e3) / args.steps) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "batch4096", "graphs": len(parts), "n_total": nsum, "arcs": arcs,
+                   "graphs_per_s": world * args.steps * len(parts) / (total_ms / 1e3),
+                   "rounds": st.rounds, "path": PATH_NAMES.get(st.path), "gen_s": t_gen,
+                   "create_s": t_create, "autotune": {"path": PATH_NAMES.get(tuning.path),
+                                                      "bounds": list(tuning.bounds),
+                                                      "grid": tuning.grid},
+                   "l2": "flushed between steps (256 MB write)"},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_kind": f"{peak_kind} burst copy bandwidth",
+                     "alg_bytes_per_launch": alg_bytes},
+        "clocks": clocks,
+    }
+    native.mis_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Continuous batching over a resident pool: saturated throughput, then
+    Poisson arrivals at fractions of it (p50/p99), vs sequential solves."""
+    import torch
+
+    from paper_2605_29604_gb300 import graphgen as gg
+    from paper_2605_29604_gb300 import native
+    world, rank, local = _dist_setup()
+    rng = np.random.default_rng(5)
+    specs = []
+    for i in range(args.pool):
+        n = int(round(math.exp(math.log(1000) + rng.random() * (math.log(2_000_000) - math.log(1000)))))
+        if i % 2 == 0:
+            scale = max(10, int(math.ceil(math.log2(n))))
+            specs.append(("rmat", scale, int(rng.integers(8, 33)), 100 + i))
+        else:
+            specs.append(("er", n, float(rng.uniform(4, 64)), 100 + i))
+
+    def gen(spec):
+        if spec[0] == "rmat":
+            return gg.rmat(spec[1], spec[2], 0.57, 0.19, 0.19, spec[3])
+        n, d, s = spec[1], spec[2], spec[3]
+        return gg.er_gnm(n, int(n * d / 2), s)
+
+    from concurrent.futures import ThreadPoolExecutor
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        graphs = list(ex.map(gen, specs))
+    t_gen = time.perf_counter() - t0
+    handles = [native.mis_create_ex(g[0], g[1], g[2], 0, native.options(device=local,
+                                                                          check_symmetry=0), None)
+               for g in graphs]
+    for h in handles:
+        native.mis_set_path(h, native.MIS_PATH_CSR, 0)
+    reqs = rng.integers(0, len(graphs), size=args.requests)
+    outs = [np.empty(g[0], dtype=np.uint8) for g in graphs]
+    arcs = np.array([int(g[1][-1]) for g in graphs])
+
+    # sequential plain solves of the same request list
+    t0 = time.perf_counter()
+    for k, i in enumerate(reqs[:args.seq_requests]):
+        native.mis_solve(handles[i], 1000 + k, outs[i])
+    seq_s = time.perf_counter() - t0
+    seq_rate = args.seq_requests / seq_s
+
+    def run(arrival_rate):
+        """Submit the request list (all at once if rate is None, else Poisson);
+        returns (graphs/s, latencies in ms)."""
+        n_req = len(reqs)
+        gaps = rng.exponential(1.0 / arrival_rate, size=n_req) if arrival_rate else np.zeros(n_req)
+        arrive = np.cumsum(gaps)
+        bufs = [np.empty(graphs[i][0], dtype=np.uint8) for i in reqs] if n_req <= 4000 else None
+        done_at = np.zeros(n_req)
+        tickets = {}
+        lock = threading.Lock()
+        finished = threading.Event()
+
+        def poller():
+            count = 0
+            while count < n_req:
+                with lock:
+                    items = list(tickets.items())
+                for k, t in items:
+                    rc = native.mis_poll(t)
+                    if rc == native.MIS_ENOTREADY:
+                        continue
+                    done_at[k] = time.perf_counter()
+                    with lock:
+                        del tickets[k]
+                    count += 1
+                time.sleep(0.00002)
+            finished.set()
+
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        t_start = time.perf_counter()
+        sub_at = np.zeros(n_req)
+        for k, i in enumerate(reqs):
+            target = t_start + arrive[k]
+            while time.perf_counter() < target:
+                pass
+            sub_at[k] = time.perf_counter()
+            buf = bufs[k] if bufs is not None else outs[i]
+            t = native.mis_submit(handles[i], 2000 + k, buf)
+            with lock:
+                tickets[k] = t
+        finished.wait()
+        total = done_at.max() - t_start
+        lat = (done_at - sub_at) * 1e3
+        return n_req / total, lat
+
+    cap, lat_sat = run(None)
+    results = {"saturated": {"graphs_per_s": cap, "p50_ms": float(np.percentile(lat_sat, 50)),
+                             "p99_ms": float(np.percentile(lat_sat, 99))}}
+    for frac in (0.5, 0.8):
+        rate, lat = run(frac * cap)
+        results[f"poisson_{frac}"] = {"offered_per_s": frac * cap, "graphs_per_s": rate,
+                                      "p50_ms": float(np.percentile(lat, 50)),
+                                      "p99_ms": float(np.percentile(lat, 99))}
+    native.mis_serve_shutdown()
+    line = {
+        "metric": "served graphs/s (continuous batching) vs sequential plain solves",
+        "value": cap, "unit": "graphs/s", "n_gpus": world, "steps": len(reqs), "warmup": 0,
+        "higher_is_better": True, "data": "synthetic", "dtype": "u32",
+        "config": {"workload": "serve", "pool": len(graphs),
+                   "pool_vertices_mean": float(np.mean([g[0] for g in graphs])),
+                   "pool_arcs_mean": float(arcs.mean()), "requests": len(reqs), "gen_s": t_gen,
+                   "sequential_graphs_per_s": seq_rate, "sequential_requests": args.seq_requests,
+                   "speedup_vs_sequential": cap / seq_rate, **results},
+    }
+    for h in handles:
+        native.mis_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -286,13 +518,26 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="rmat22")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--tpr", type=int, default=0)
+    ap.add_argument("--tpr", type=int, default=None, help="force the CSR path with these lanes")
+    ap.add_argument("--path", default=None, choices=["tile", "tile_tc"])
+    ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch from an ncu capture of this kernel")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--pool", type=int, default=48)
+    ap.add_argument("--requests", type=int, default=20000)
+    ap.add_argument("--seq-requests", type=int, default=2000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    return run_ours(args)
+    if args.workload == "batch4096":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
+    return run_single(args)
 
 
 if __name__ == "__main__":

@@ -191,6 +191,30 @@ int mis_set_path(mis_graph *g, int32_t path, int32_t param);
  * autotuner. */
 int mis_set_csr_bins(mis_graph *g, const int32_t *bounds);
 
+/* The autotuner's choice for a graph. */
+typedef struct mis_tuning {
+    int32_t path;        /* MIS_PATH_CSR, MIS_PATH_TILE or MIS_PATH_TILE_TC */
+    int32_t param;       /* CSR: forced lanes per row (0 = degree bins); tile: size */
+    int32_t bounds[4];   /* CSR degree-bin bounds (see mis_set_csr_bins) */
+    int32_t grid;        /* persistent blocks in use */
+    int32_t candidates;  /* configurations timed */
+    float ms;            /* median solve time of the choice, ms */
+    double arcs_per_tile;/* sampled arcs per non-empty 8 x 8 tile */
+} mis_tuning;
+
+/*
+ * Autotuner: times candidate configurations on `g` (median of `reps` solves
+ * each, reps <= 0 means 3) -- CSR degree-bin bounds and grid sizes, and the
+ * tile paths (8 x 8 and 16 x 16 popc, 16 x 16 tensor core) when sampled tiles
+ * hold enough arcs -- applies the fastest to `g` and caches it for the
+ * graph's density class (average degree, size, tile locality, device).  Graphs
+ * created later with path MIS_PATH_AUTO take the cached choice of their class.
+ * The cache lives in the process and, if the environment variable
+ * TCMIS_TUNE_CACHE names a file, in that file.  Blocks the calling thread;
+ * MIS_EBUSY while served requests on `g` are in flight.  `chosen` may be NULL.
+ */
+int mis_autotune(mis_graph *g, int32_t reps, mis_tuning *chosen);
+
 /* Blocks of the persistent round kernel for later solves on `g` (0 = default:
  * one per 256 vertices), clamped to what can be co-resident on the device;
  * mis_get_grid returns the value in use.  Used by the autotuner. */

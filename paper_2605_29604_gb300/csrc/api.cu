@@ -1,7 +1,12 @@
 // api.cu -- the C ABI (include/tcmis.h): graph handles, solves, statistics.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -11,6 +16,8 @@
 #include "tcmis.h"
 
 namespace tcmis {
+
+int apply_cached_choice(mis_graph* g);  // autotuner section below
 
 namespace {
 thread_local int t_err_code = 0;
@@ -219,6 +226,10 @@ int finish_create(mis_graph* g) {
     }
     const int brc = rebin(g, thr, g->own_stream);
     if (brc != MIS_OK) return brc;
+    if (g->opt.path == MIS_PATH_AUTO && g->opt.threads_per_row == 0) {
+        const int arc = apply_cached_choice(g);
+        if (arc != MIS_OK) return arc;
+    }
     if (g->opt.build_tiles == 1 || g->opt.path == MIS_PATH_TILE || g->opt.path == MIS_PATH_TILE_TC) {
         const int rc = use_tiles(g, g->opt.path == MIS_PATH_AUTO || g->opt.path == MIS_PATH_CSR
                                         ? MIS_PATH_TILE : g->opt.path, 16);
@@ -345,6 +356,262 @@ int solve_async(mis_graph* g, const uint64_t* seeds, uint8_t* out_dev, cudaStrea
     g->last_stream = s;
     g->last_path = g->path;
     return MIS_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+//
+// Chooses, per density class, the round kernel (CSR or tile), its lanes-per-
+// row bins or tile size, and the persistent grid, by timing candidate
+// configurations on the graph itself (median of a few solves, CUDA events).
+// Choices are cached per class (average-degree bucket, size bucket, tile
+// locality bucket, device name) in the process and, when TCMIS_TUNE_CACHE
+// names a file, on disk.
+
+namespace {
+
+struct TuneChoice {
+    int32_t path = MIS_PATH_CSR;
+    int32_t param = 0;   // CSR: forced lanes per row (0 = bins); tile: tile size
+    int32_t bounds[4] = {8, 4096, 4096, 65536};
+    int32_t grid = 0;    // CSR grid request (0 = default)
+    float ms = 0.f;
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune_cache;
+bool g_tune_loaded = false;
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* f = std::getenv("TCMIS_TUNE_CACHE");
+    if (!f) return;
+    std::ifstream in(f);
+    std::string line;
+    while (std::getline(in, line)) {
+        std::istringstream ss(line);
+        std::string key;
+        TuneChoice c;
+        if (ss >> key >> c.path >> c.param >> c.bounds[0] >> c.bounds[1] >> c.bounds[2] >>
+            c.bounds[3] >> c.grid >> c.ms)
+            g_tune_cache[key] = c;
+    }
+}
+
+void tune_save_locked() {
+    const char* f = std::getenv("TCMIS_TUNE_CACHE");
+    if (!f) return;
+    std::ofstream out(f, std::ios::trunc);
+    for (const auto& kv : g_tune_cache) {
+        const TuneChoice& c = kv.second;
+        out << kv.first << ' ' << c.path << ' ' << c.param << ' ' << c.bounds[0] << ' '
+            << c.bounds[1] << ' ' << c.bounds[2] << ' ' << c.bounds[3] << ' ' << c.grid << ' '
+            << c.ms << '\n';
+    }
+}
+
+// Distinct 8-column blocks of 8-row block rb: an 8-way merge of its sorted rows.
+__global__ void tile_sample_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                   int32_t n, const int32_t* __restrict__ rbs, int count,
+                                   unsigned long long* __restrict__ acc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int rb = rbs[k];
+    int cur[8], end[8];
+    long long arcs = 0;
+    for (int i = 0; i < 8; ++i) {
+        const int v = rb * 8 + i;
+        cur[i] = v < n ? rp[v] : 0;
+        end[i] = v < n ? rp[v + 1] : 0;
+        arcs += end[i] - cur[i];
+    }
+    long long tiles = 0;
+    for (;;) {
+        int cb = INT32_MAX;
+        for (int i = 0; i < 8; ++i)
+            if (cur[i] < end[i]) cb = min(cb, col[cur[i]] >> 3);
+        if (cb == INT32_MAX) break;
+        ++tiles;
+        for (int i = 0; i < 8; ++i)
+            while (cur[i] < end[i] && (col[cur[i]] >> 3) == cb) ++cur[i];
+    }
+    atomicAdd(&acc[0], (unsigned long long)arcs);
+    atomicAdd(&acc[1], (unsigned long long)tiles);
+}
+
+// Estimated arcs per non-empty 8 x 8 tile, from up to 2048 row blocks spread
+// evenly over the graph.
+double estimate_arcs_per_tile(mis_graph* g) {
+    GraphData& d = g->d;
+    const int32_t nrb = (d.n + 7) / 8;
+    if (nrb == 0 || d.arcs == 0) return 0.0;
+    const int count = std::min<int32_t>(nrb, 2048);
+    std::vector<int32_t> rbs((size_t)count);
+    for (int k = 0; k < count; ++k) rbs[(size_t)k] = (int32_t)((int64_t)k * nrb / count);
+    int32_t* d_rbs = nullptr;
+    unsigned long long* d_acc = nullptr;
+    unsigned long long h[2] = {0, 0};
+    cudaStream_t s = g->own_stream;
+    cudaError_t e = cudaMalloc((void**)&d_rbs, 4 * (size_t)count);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_acc, 16);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rbs, rbs.data(), 4 * (size_t)count,
+                                              cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_acc, 0, 16, s);
+    if (e == cudaSuccess) {
+        tile_sample_kernel<<<(count + 127) / 128, 128, 0, s>>>(d.rp, d.col, d.n, d_rbs, count,
+                                                               d_acc);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_acc, 16, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_rbs);
+    cudaFree(d_acc);
+    if (e != cudaSuccess || h[1] == 0) {
+        cudaGetLastError();
+        return 0.0;
+    }
+    return (double)h[0] / (double)h[1];
+}
+
+std::string density_class(mis_graph* g, double apt) {
+    const GraphData& d = g->d;
+    const double avg = d.n ? (double)d.arcs / d.n : 0.0;
+    int deg_b = 0;
+    while (deg_b < 20 && (1 << deg_b) <= avg) ++deg_b;
+    int size_b = 0;
+    while (size_b < 31 && (1ll << size_b) <= (long long)d.n) ++size_b;
+    const char loc = apt < 1.5 ? 's' : (apt < 3.0 ? 'm' : 'd');
+    cudaDeviceProp prop;
+    std::string dev = "gpu";
+    if (cudaGetDeviceProperties(&prop, d.device) == cudaSuccess) dev = prop.name;
+    for (char& c : dev)
+        if (c == ' ') c = '_';
+    return dev + ":d" + std::to_string(deg_b) + ":n" + std::to_string(size_b / 2) + ":" + loc +
+           (d.count ? ":batch" : "");
+}
+
+int apply_choice(mis_graph* g, const TuneChoice& c) {
+    if (c.path == MIS_PATH_TILE || c.path == MIS_PATH_TILE_TC) return use_tiles(g, c.path, c.param);
+    g->path = MIS_PATH_CSR;
+    int32_t thr[4];
+    if (c.param) {
+        thresholds_for(c.param, thr);
+    } else {
+        for (int k = 0; k < 4; ++k) thr[k] = c.bounds[k];
+    }
+    g->tpr = c.param;
+    if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+    const int rc = rebin(g, thr, g->own_stream);
+    if (rc != MIS_OK) return rc;
+    g->grid = pick_grid(g, c.grid);
+    return g->grid > 0 ? MIS_OK : set_error(MIS_EDEVICE, "no co-resident blocks");
+}
+
+// Median device time of `reps` solves (after one warm-up) in the handle's
+// own workspace, in ms; negative on error.
+float time_solves(mis_graph* g, int reps) {
+    std::vector<uint64_t> seeds((size_t)std::max(1, g->d.count), 1);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<float> ts;
+    for (int i = 0; i <= reps; ++i) {
+        cudaEventRecord(e0, g->own_stream);
+        if (solve_async(g, seeds.data(), g->d.ws.out, g->own_stream) != MIS_OK) break;
+        cudaEventRecord(e1, g->own_stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (i > 0) ts.push_back(ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaMemcpy(g->d.ctl_host, g->d.ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    if ((int)ts.size() != reps || g->d.ctl_host->err != 0) return -1.f;
+    std::sort(ts.begin(), ts.end());
+    return ts[ts.size() / 2];
+}
+
+}  // namespace
+
+int autotune(mis_graph* g, int reps, mis_tuning* out) {
+    if (reps < 1) reps = 3;
+    const double apt = estimate_arcs_per_tile(g);
+    std::vector<TuneChoice> cands;
+    auto bins = [&](int a, int b, int c, int d, int grid) {
+        TuneChoice t;
+        t.bounds[0] = a;
+        t.bounds[1] = b;
+        t.bounds[2] = c;
+        t.bounds[3] = d;
+        t.grid = grid;
+        cands.push_back(t);
+    };
+    const int maxg = csr_max_coresident_blocks(g->d.device);
+    bins(8, 4096, 4096, 65536, 0);
+    bins(8, 4096, 4096, 65536, maxg);
+    bins(4, 64, 1024, 65536, 0);
+    bins(16, 256, 4096, 65536, 0);
+    bins(12, 48, 256, 4096, 0);
+    bins(INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, 0);  // one lane per row
+    bins(-1, 65536, 65536, 65536, 0);                                     // four lanes per row
+    if (g->d.n <= 65536) bins(8, 4096, 4096, 65536, std::max(1, (g->d.n + 1023) / 1024));
+    if (apt >= 2.5) {
+        for (int T : {8, 16}) {
+            TuneChoice t;
+            t.path = MIS_PATH_TILE;
+            t.param = T;
+            cands.push_back(t);
+        }
+        TuneChoice t;
+        t.path = MIS_PATH_TILE_TC;
+        t.param = 16;
+        cands.push_back(t);
+    }
+    TuneChoice best;
+    best.ms = -1.f;
+    for (TuneChoice& c : cands) {
+        if (apply_choice(g, c) != MIS_OK) continue;
+        c.ms = time_solves(g, reps);
+        if (c.ms > 0.f && (best.ms < 0.f || c.ms < best.ms)) best = c;
+    }
+    if (best.ms < 0.f) return set_error(MIS_EINTERNAL, "autotuner found no working configuration");
+    const int rc = apply_choice(g, best);
+    if (rc != MIS_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        g_tune_cache[density_class(g, apt)] = best;
+        tune_save_locked();
+    }
+    if (out) {
+        out->path = best.path;
+        out->param = best.param;
+        for (int k = 0; k < 4; ++k) out->bounds[k] = best.bounds[k];
+        out->grid = g->path == MIS_PATH_CSR ? g->grid : g->tile_grid;
+        out->ms = best.ms;
+        out->arcs_per_tile = apt;
+        out->candidates = (int32_t)cands.size();
+    }
+    return MIS_OK;
+}
+
+// AUTO at create: the cached choice of the graph's class, if any.
+int apply_cached_choice(mis_graph* g) {
+    TuneChoice c;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        if (g_tune_cache.empty()) return MIS_OK;
+    }
+    const std::string key = density_class(g, estimate_arcs_per_tile(g));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it == g_tune_cache.end()) return MIS_OK;
+        c = it->second;
+    }
+    return apply_choice(g, c);
 }
 
 }  // namespace tcmis
@@ -648,6 +915,17 @@ int mis_set_csr_bins(mis_graph* g, const int32_t* bounds) {
     g->tpr = 0;
     g->path = MIS_PATH_CSR;
     return rebin(g, bounds, g->own_stream);
+}
+
+int mis_autotune(mis_graph* g, int32_t reps, mis_tuning* chosen) {
+    clear_error();
+    if (!g) return set_error(MIS_EINVAL, "null graph");
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
+    cudaError_t e = cudaSetDevice(g->d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    if (g->d.n == 0) return MIS_OK;
+    return autotune(g, reps, chosen);
 }
 
 int mis_set_grid(mis_graph* g, int32_t blocks) {

@@ -106,6 +106,8 @@ int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_
              uint8_t* out_dev, cudaStream_t s, bool single_block);
 void free_graph(mis_graph* g);
 
+int autotune(mis_graph* g, int reps, mis_tuning* out);
+
 // serve.cu
 void serve_release_graph(mis_graph* g);
 

@@ -61,6 +61,13 @@ class mis_stats(ctypes.Structure):
                 ("select_ns", ctypes.c_int64 * 64), ("exclude_ns", ctypes.c_int64 * 64)]
 
 
+class mis_tuning(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("param", ctypes.c_int32),
+                ("bounds", ctypes.c_int32 * 4), ("grid", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("arcs_per_tile", ctypes.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -100,6 +107,8 @@ def lib():
         L.mis_keys_ex.restype = ctypes.c_int
         L.mis_set_path.argtypes = [P, i32, i32]
         L.mis_set_path.restype = ctypes.c_int
+        L.mis_autotune.argtypes = [P, i32, ctypes.POINTER(mis_tuning)]
+        L.mis_autotune.restype = ctypes.c_int
         L.mis_set_grid.argtypes = [P, i32]
         L.mis_set_grid.restype = ctypes.c_int
         L.mis_get_grid.argtypes = [P]
@@ -136,7 +145,7 @@ def lib():
 EXPORTED = [
     "mis_options_init", "mis_create", "mis_create_ex", "mis_create_batch", "mis_graph_count",
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
-    "mis_set_path", "mis_set_csr_bins", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_wait",
+    "mis_set_path", "mis_set_csr_bins", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
     "mis_solve_noalloc",
 ]
@@ -255,6 +264,12 @@ def mis_set_path(h, path, threads_per_row=0):
 def mis_set_csr_bins(h, bounds):
     b = np.ascontiguousarray(np.asarray(bounds, dtype=np.int32))
     return _check(lib().mis_set_csr_bins(h, _ptr(b)))
+
+
+def mis_autotune(h, reps=3):
+    t = mis_tuning()
+    _check(lib().mis_autotune(h, reps, ctypes.byref(t)))
+    return t
 
 
 def mis_set_grid(h, blocks):
