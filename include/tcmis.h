@@ -89,6 +89,11 @@ typedef struct mis_options {
     int32_t max_slots;       /* serving: concurrent solves per step; 0 = default (64) */
     int64_t hbm_budget;      /* serving: bytes of per-solve workspace admitted at
                                 once; 0 = default (half of free device memory) */
+    int32_t serve_blocks;    /* serving: most blocks one served solve may use (graphs
+                                of up to 16384 vertices always use one); 0 = default
+                                (half the SMs), so that several large requests share
+                                the device */
+    int32_t pad0;
 } mis_options;
 
 /* Per-solve statistics of the last completed solve on a graph. */
@@ -256,6 +261,11 @@ int mis_poll(mis_ticket ticket);
 /* Wait up to timeout_us microseconds (negative = forever); same returns as
  * mis_poll, MIS_ETIMEDOUT when the wait expires first. */
 int mis_wait(mis_ticket ticket, int64_t timeout_us);
+
+/* As mis_poll; when the request is done, *latency_ns (if not NULL) receives
+ * the time from its mis_submit to the moment its result was in the caller's
+ * buffer, measured by the library (steady clock). */
+int mis_poll_ex(mis_ticket ticket, int64_t *latency_ns);
 
 /* Configure the serving scheduler (before the first submit; opt as in
  * mis_create_ex: max_slots, hbm_budget, spin_cap, device). */

@@ -318,7 +318,8 @@ void free_graph(mis_graph* g) {
 }
 
 int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_pinned,
-             uint8_t* out_dev, cudaStream_t s, bool single_block) {
+             uint8_t* out_dev, cudaStream_t s, int blocks) {
+    const bool single_block = blocks == 1;
     GraphData& d = g->d;
     cudaError_t e = cudaSetDevice(d.device);
     if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
@@ -339,11 +340,11 @@ int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_
         const bool tile = g->path == MIS_PATH_TILE || g->path == MIS_PATH_TILE_TC;
         if (tile)
             e = launch_tile_solve(a, d.tiles.T, g->tile_slots, g->path == MIS_PATH_TILE_TC,
-                                  single_block ? 1 : g->tile_grid, s);
+                                  blocks > 0 ? std::min(blocks, g->tile_grid) : g->tile_grid, s);
         else if (single_block)
             e = launch_csr_solve_single(a, s);
         else
-            e = launch_csr_solve(a, g->grid, s);
+            e = launch_csr_solve(a, blocks > 0 ? std::min(blocks, g->grid) : g->grid, s);
         if (e != cudaSuccess) return set_cuda_error(e, "round kernel launch");
     }
     return MIS_OK;
@@ -351,7 +352,7 @@ int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_
 
 // Enqueue one solve on stream s in the handle's own workspace.
 int solve_async(mis_graph* g, const uint64_t* seeds, uint8_t* out_dev, cudaStream_t s) {
-    const int rc = solve_in(g, g->d.ws, seeds, g->d.seeds_host, out_dev, s, false);
+    const int rc = solve_in(g, g->d.ws, seeds, g->d.seeds_host, out_dev, s, 0);
     if (rc != MIS_OK) return rc;
     g->last_stream = s;
     g->last_path = g->path;
@@ -631,6 +632,7 @@ void mis_options_init(mis_options* opt) {
     opt->device = 0;
     opt->max_slots = 0;
     opt->hbm_budget = 0;
+    opt->serve_blocks = 0;
 }
 
 int mis_last_error(const char** msg) {

@@ -100,10 +100,12 @@ namespace tcmis {
 // api.cu
 int solve_async(mis_graph* g, const uint64_t* seeds, uint8_t* out_dev, cudaStream_t s);
 // One solve of g on stream s in workspace w; seeds (host, one per graph of
-// the handle) are staged through `seeds_pinned`; single_block: run the round
-// kernel as one block (ordinary launch, no cooperative co-scheduling needed).
+// the handle) are staged through `seeds_pinned`.  blocks: 0 = the graph's own
+// persistent grid; 1 = the round kernel as one block through an ordinary
+// launch (a lone block needs no co-scheduling); > 1 = a cooperative grid of
+// at most that many blocks.
 int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_pinned,
-             uint8_t* out_dev, cudaStream_t s, bool single_block);
+             uint8_t* out_dev, cudaStream_t s, int blocks);
 void free_graph(mis_graph* g);
 
 int autotune(mis_graph* g, int reps, mis_tuning* out);

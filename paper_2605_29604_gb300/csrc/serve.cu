@@ -11,9 +11,9 @@
 //            budget (a request is always admitted when nothing runs);
 //   launch   each admitted request on its slot's stream: graphs of up to
 //            kSingleBlockMax vertices run the round kernel as one block
-//            through an ordinary launch, larger ones the cooperative
-//            persistent grid.  Requests admitted while others run share the
-//            device with them.
+//            through an ordinary launch, larger ones a cooperative grid of at
+//            most serve_blocks blocks (default: half the SMs), so that
+//            requests admitted while others run share the device with them.
 //
 // Graphs stay resident: a request names a graph created earlier with
 // mis_create*.  A graph destroyed while requests on it are in flight is freed
@@ -39,7 +39,15 @@ namespace {
 constexpr int32_t kSingleBlockMax = 16384;  // vertices solved by one block
 constexpr int kDefaultSlots = 64;
 
+int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
 struct Request {
+    int64_t t_submit = 0;
+    int64_t t_done = 0;
     mis_ticket id = 0;
     mis_graph* g = nullptr;
     uint64_t seed = 0;
@@ -79,6 +87,7 @@ class Server {
         device_ = d.device;
         max_slots_ = d.max_slots > 0 ? d.max_slots : kDefaultSlots;
         budget_ = d.hbm_budget;
+        serve_blocks_ = d.serve_blocks;
         return MIS_OK;
     }
 
@@ -92,6 +101,7 @@ class Server {
             if (rc != MIS_OK) return rc;
         }
         Request* r = new Request();
+        r->t_submit = now_ns();
         r->id = next_id_++;
         r->g = g;
         r->seed = seed;
@@ -104,9 +114,9 @@ class Server {
         return MIS_OK;
     }
 
-    int poll(mis_ticket t) {
+    int poll(mis_ticket t, int64_t* latency_ns = nullptr) {
         std::lock_guard<std::mutex> lk(mu_);
-        return finish_locked(t);
+        return finish_locked(t, latency_ns);
     }
 
     int wait(mis_ticket t, int64_t us) {
@@ -165,6 +175,8 @@ class Server {
     int start_locked() {
         cudaError_t e = cudaSetDevice(device_);
         if (e != cudaSuccess) return set_cuda_error(e, "serving: cudaSetDevice");
+        if (cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, device_) != cudaSuccess)
+            sms_ = 1;
         if (budget_ <= 0) {
             size_t free_b = 0, total_b = 0;
             e = cudaMemGetInfo(&free_b, &total_b);
@@ -178,12 +190,13 @@ class Server {
     }
 
     // Caller holds mu_.  Releases a finished request's ticket.
-    int finish_locked(mis_ticket t) {
+    int finish_locked(mis_ticket t, int64_t* latency_ns = nullptr) {
         auto it = reqs_.find(t);
         if (it == reqs_.end()) return set_error(MIS_EINVAL, "unknown ticket");
         Request* r = it->second;
         if (!r->done) return MIS_ENOTREADY;
         const int st = r->status;
+        if (latency_ns) *latency_ns = r->t_done - r->t_submit;
         reqs_.erase(it);
         delete r;
         if (st != MIS_OK) set_error(st, "served request failed");
@@ -224,8 +237,9 @@ class Server {
         int rc;
         {
             std::lock_guard<std::mutex> glk(g->mu);
-            rc = solve_in(g, s.ws, seeds.data(), s.seeds_pinned, s.ws.out, s.stream,
-                          d.n <= kSingleBlockMax);
+            int blocks = serve_blocks_ > 0 ? serve_blocks_ : std::max(1, sms_ / 2);
+            if (d.n <= kSingleBlockMax) blocks = 1;
+            rc = solve_in(g, s.ws, seeds.data(), s.seeds_pinned, s.ws.out, s.stream, blocks);
         }
         if (rc != MIS_OK) return rc;
         if (d.result_bytes > 0)
@@ -242,6 +256,7 @@ class Server {
 
     // Caller holds mu_ (released around the free of a destroyed graph).
     void complete_locked(std::unique_lock<std::mutex>& lk, Request* r, int status) {
+        r->t_done = now_ns();
         r->status = status;
         r->done = true;
         mis_graph* g = r->g;
@@ -338,6 +353,8 @@ class Server {
     int max_slots_ = kDefaultSlots;
     int64_t budget_ = 0;
     int64_t used_ = 0;
+    int serve_blocks_ = 0;
+    int sms_ = 1;
     mis_ticket next_id_ = 1;
 };
 
@@ -359,6 +376,11 @@ int mis_submit(mis_graph* g, uint64_t seed, uint8_t* out_status, mis_ticket* tic
 int mis_poll(mis_ticket t) {
     clear_error();
     return Server::get().poll(t);
+}
+
+int mis_poll_ex(mis_ticket t, int64_t* latency_ns) {
+    clear_error();
+    return Server::get().poll(t, latency_ns);
 }
 
 int mis_wait(mis_ticket t, int64_t timeout_us) {

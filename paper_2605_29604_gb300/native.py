@@ -49,7 +49,8 @@ class mis_options(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("threads_per_row", ctypes.c_int32),
                 ("check_symmetry", ctypes.c_int32), ("build_tiles", ctypes.c_int32),
                 ("spin_cap", ctypes.c_int64), ("device", ctypes.c_int32),
-                ("max_slots", ctypes.c_int32), ("hbm_budget", ctypes.c_int64)]
+                ("max_slots", ctypes.c_int32), ("hbm_budget", ctypes.c_int64),
+                ("serve_blocks", ctypes.c_int32), ("pad0", ctypes.c_int32)]
 
 
 class mis_stats(ctypes.Structure):
@@ -123,6 +124,8 @@ def lib():
         L.mis_submit.restype = ctypes.c_int
         L.mis_poll.argtypes = [i64]
         L.mis_poll.restype = ctypes.c_int
+        L.mis_poll_ex.argtypes = [i64, ctypes.POINTER(i64)]
+        L.mis_poll_ex.restype = ctypes.c_int
         L.mis_wait.argtypes = [i64, i64]
         L.mis_wait.restype = ctypes.c_int
         L.mis_serve_configure.argtypes = [ctypes.POINTER(mis_options)]
@@ -145,7 +148,7 @@ def lib():
 EXPORTED = [
     "mis_options_init", "mis_create", "mis_create_ex", "mis_create_batch", "mis_graph_count",
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
-    "mis_set_path", "mis_set_csr_bins", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_wait",
+    "mis_set_path", "mis_set_csr_bins", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
     "mis_solve_noalloc",
 ]
@@ -299,6 +302,13 @@ def mis_submit(h, seed, out_status):
 def mis_poll(ticket):
     """MIS_OK (done; ticket released), MIS_ENOTREADY, or a negative error."""
     return lib().mis_poll(ticket)
+
+
+def mis_poll_ex(ticket):
+    """(rc, latency_ns): rc as mis_poll; latency from submit to result (done only)."""
+    lat = ctypes.c_int64(0)
+    rc = lib().mis_poll_ex(ticket, ctypes.byref(lat))
+    return rc, lat.value
 
 
 def mis_wait(ticket, timeout_us=-1):

@@ -81,11 +81,12 @@ def test_poll_and_ticket_release(pool):
     out = np.empty(graphs[6][0], dtype=np.uint8)
     t = native.mis_submit(handles[6], 3, out)
     deadline = time.time() + 30
-    rc = native.mis_poll(t)
+    rc, lat = native.mis_poll_ex(t)
     while rc == native.MIS_ENOTREADY and time.time() < deadline:
         time.sleep(0.0002)
-        rc = native.mis_poll(t)
+        rc, lat = native.mis_poll_ex(t)
     assert rc == native.MIS_OK
+    assert 0 < lat < 30e9
     assert np.array_equal(out, _want(graphs[6], 3))
     assert native.mis_poll(t) == native.MIS_EINVAL  # released
     assert native.mis_wait(123456789, 0) == native.MIS_EINVAL
