@@ -155,7 +155,8 @@ SegTable seg_of(const GraphData& d) {
 int rebin(mis_graph* g, const int32_t thr[4], cudaStream_t s) {
     GraphData& d = g->d;
     for (int j = 0; j < 4; ++j) d.thr[j] = thr[j];
-    cudaError_t e = build_bins(d.rp, d.n, seg_of(d), d.thr, d.order0, d.bin_off, s);
+    cudaError_t e =
+        build_bins(d.rp, d.n, seg_of(d), d.thr, d.order0, d.bin_off, &d.n_isolated, s);
     if (e != cudaSuccess) return set_cuda_error(e, "degree binning");
     return MIS_OK;
 }
@@ -206,8 +207,11 @@ int use_tiles(mis_graph* g, int path, int T) {
 int finish_create(mis_graph* g) {
     GraphData& d = g->d;
     cudaError_t e;
+    const int64_t col_alloc = ((d.arcs + 3) / 4) * 4 + 4;
     if ((e = ws_reserve(d.ws, d.n, d.count)) != cudaSuccess ||
-        (e = dalloc(&d.order0, d.n, &d.footprint)) != cudaSuccess)
+        (e = dalloc(&d.order0, d.n, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.col_sel, col_alloc, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.split, d.n, &d.footprint)) != cudaSuccess)
         return set_cuda_error(e, "workspace allocation");
     d.footprint += d.ws.bytes;
     if ((e = cudaMallocHost((void**)&d.ctl_host, sizeof(Ctl))) != cudaSuccess ||
@@ -224,6 +228,11 @@ int finish_create(mis_graph* g) {
         e = cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return set_cuda_error(e, "stream");
     }
+    e = cudaMemsetAsync(d.col_sel, 0, sizeof(int32_t) * (size_t)col_alloc, g->own_stream);
+    if (e == cudaSuccess)
+        e = build_degree_order(d.rp, d.col, d.n, d.arcs, seg_of(d), d.col_sel, d.split,
+                               g->own_stream);
+    if (e != cudaSuccess) return set_cuda_error(e, "degree ordering");
     const int brc = rebin(g, thr, g->own_stream);
     if (brc != MIS_OK) return brc;
     if (g->opt.path == MIS_PATH_AUTO && g->opt.threads_per_row == 0) {
@@ -270,8 +279,11 @@ SolveArgs make_args(mis_graph* g, Workspace& w) {
     a.word = w.word;
     a.wl0 = w.wl0;
     a.wl1 = w.wl1;
+    a.col_sel = d.col_sel;
+    a.split = d.split;
     a.order0 = d.order0;
     for (int j = 0; j < 6; ++j) a.bin_off[j] = d.bin_off[j];
+    a.n_isolated = d.n_isolated;
     a.ctl = w.ctl;
     a.times = w.times;
     a.seg = seg_of(d);
@@ -308,6 +320,8 @@ void free_graph(mis_graph* g) {
     if (d.seeds_host) cudaFreeHost(d.seeds_host);
     free_tiles(d);
     dfree(d.order0);
+    dfree(d.col_sel);
+    dfree(d.split);
     ws_free(d.ws);
     if (d.ctl_host) cudaFreeHost(d.ctl_host);
     if (d.times_host) cudaFreeHost(d.times_host);

@@ -65,9 +65,12 @@ struct GraphData {
     // tile-CSR (built on demand)
     TileCsr tiles;
     int64_t tile_footprint = 0;
-    // degree bins of the CSR kernel
+    // degree-ordered rows and degree bins of the CSR kernel
+    int32_t* col_sel = nullptr;
+    int32_t* split = nullptr;
     int32_t* order0 = nullptr;
     int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};
+    int32_t n_isolated = 0;
     int32_t thr[4] = {0, 0, 0, 0};
     unsigned* flags = nullptr;
     // workspace of the handle's own solves (mis_solve / mis_solve_ex)

@@ -8,9 +8,14 @@ namespace tcmis {
 
 // Eq. 1 priority of every vertex v < n_words into its packed word (Sec. 2:
 // assigned once per solve).  Vertices at or beyond a.n (tile padding) and
-// batch padding vertices are out; isolated vertices get a fixed key (they
-// have no neighbour to compare with).  Grid-stride over the whole launch.
-__device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words) {
+// batch padding vertices are out.  Isolated vertices have no neighbour to
+// compare with, so every round-0 selection test accepts them: with
+// isolated_in they are written in the MIS right away (the CSR kernel keeps
+// them out of its worklists), else they get a fixed key and are decided in
+// round 0 like every other vertex.  Grid-stride over the whole launch.
+__device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
+                                           bool isolated_in) {
+    const uint32_t iso = isolated_in ? (kKeyIsolated | kWordInSet) : kKeyIsolated;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthreads = (long long)gridDim.x * blockDim.x;
     const int32_t n = a.n;
@@ -27,14 +32,14 @@ __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words) 
         } else {
             const int deg = a.rp[v + 1] - a.rp[v];
             if (a.seg.count == 0) {
-                w = deg ? eq1_key(dbar0, deg, smix0, (uint32_t)v) : kKeyIsolated;
+                w = deg ? eq1_key(dbar0, deg, smix0, (uint32_t)v) : iso;
             } else {
                 const int g = a.seg.blk_seg[v >> 4];
                 const int local = (int)v - a.seg.voff[g];
                 if (local >= a.seg.nv[g]) {
                     w = kWordOut;  // padding vertex between two graphs
                 } else if (deg == 0) {
-                    w = kKeyIsolated;
+                    w = iso;
                 } else {
                     const float dbar = average_degree(a.seg.arcs[g], a.seg.nv[g]);
                     w = eq1_key(dbar, deg, mix64(a.seg.seed[g]), (uint32_t)local);

@@ -37,8 +37,11 @@ struct SolveArgs {
     long long spin_cap = 0;        // barrier poll limit
     int32_t max_rounds = 0;        // round cap (error beyond)
     // degree bins of the CSR kernel
+    const int32_t* col_sel = nullptr; // rows sorted by neighbour degree (padded like col)
+    const int32_t* split = nullptr;   // neighbours of degree <= deg(v) + 1 (nullable)
     const int32_t* order0 = nullptr;  // round-0 list: real vertices grouped by bin
     int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};  // bin j occupies [bin_off[j], bin_off[j+1])
+    int32_t n_isolated = 0;           // real vertices of degree 0 (not in order0)
     // tile-CSR (used by the tile kernels only)
     const int32_t* trp = nullptr;    // row block rb owns tiles [trp[rb], trp[rb+1])
     const int32_t* tcol = nullptr;   // column block of each tile
@@ -62,9 +65,11 @@ cudaError_t launch_csr_solve(const SolveArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_csr_solve_single(const SolveArgs& a, cudaStream_t s);
 int csr_max_coresident_blocks(int device);
 int csr_block_size();
-// Round-0 list grouped by degree bin (thr: inclusive upper degree of bins 0..3).
+// Round-0 list grouped by degree bin (thr: inclusive upper degree of bins
+// 0..3); isolated vertices are left out and counted in *n_isolated.
 cudaError_t build_bins(const int32_t* rp, int32_t n, const SegTable& seg, const int32_t thr[4],
-                       int32_t* order0, int32_t bin_off[6], cudaStream_t s);
+                       int32_t* order0, int32_t bin_off[6], int32_t* n_isolated,
+                       cudaStream_t s);
 
 // kernels_util.cu
 cudaError_t launch_validate(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs,
@@ -76,6 +81,14 @@ cudaError_t launch_relocate(int32_t* rp, int32_t* col, int32_t n, int32_t arcs, 
                             int32_t aoff, cudaStream_t s);
 cudaError_t launch_pad_rows(int32_t* dst_rp, int32_t from, int32_t to, int32_t value,
                             cudaStream_t s);
+
+// kernels_order.cu
+// Rows of col sorted by neighbour degree into col_sel (same offsets) and
+// split[v] = neighbours of degree <= deg(v) + 1 (the whole row for very high
+// degrees): the only neighbours that can outrank v under Eq. 1.
+cudaError_t build_degree_order(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs,
+                               const SegTable& seg, int32_t* col_sel, int32_t* split,
+                               cudaStream_t s);
 
 // kernels_tile.cu
 struct TileCsr {

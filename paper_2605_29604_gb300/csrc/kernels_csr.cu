@@ -87,15 +87,37 @@ __device__ __forceinline__ bool group_scan(const int32_t* __restrict__ col,
     return found;
 }
 
-// Chunk size for a bin of `cnt` rows: at most CH, fewer when the bin is
-// small so that the chunks spread over all warps; a multiple of G.
+// Work split of a bin of `cnt` rows into chunks taken through one counter:
+// `nbig` chunks of `ch` rows (at most CH, fewer when the bin is small so that
+// the chunks spread over all warps) cover most of the bin, then chunks of one
+// warp pass (G rows) finish it, so that the last warps of a phase do not
+// wait long for a straggler.
+struct ChunkPlan {
+    int ch;
+    int nbig;
+    int total;  // chunks in all
+    __device__ __forceinline__ void range(int k, int cnt, int& c0, int& c1, int G) const {
+        if (k < nbig) {
+            c0 = k * ch;
+            c1 = c0 + ch;
+        } else {
+            c0 = nbig * ch + (k - nbig) * G;
+            c1 = min(c0 + G, cnt);
+        }
+    }
+};
+
 template <int G, int CH>
-__device__ __forceinline__ int chunk_of(int cnt) {
+__device__ __forceinline__ ChunkPlan plan_of(int cnt) {
     const long long nwarps = (long long)gridDim.x * (blockDim.x / 32);
     long long per = (cnt + nwarps - 1) / nwarps;
     per = ((per + G - 1) / G) * G;
     if (per < G) per = G;
-    return per < CH ? (int)per : CH;
+    ChunkPlan p;
+    p.ch = per < CH ? (int)per : CH;
+    p.nbig = (int)((long long)cnt * 7 / 8 / p.ch);
+    p.total = p.nbig + (cnt - p.nbig * p.ch + G - 1) / G;
+    return p;
 }
 
 __device__ __forceinline__ long long global_warp() {
@@ -112,14 +134,15 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int32_t* __
     const unsigned glane = lane % TPR;
     const unsigned gid = lane / TPR;
     const unsigned gshift = gid * TPR;
-    const int ch = chunk_of<G, CH>(cnt);
-    if (global_warp() >= (cnt + ch - 1) / ch) return;
+    const ChunkPlan plan = plan_of<G, CH>(cnt);
+    if (global_warp() >= plan.total) return;
     for (;;) {
-        int c0 = 0;
-        if (lane == 0) c0 = (int)atomicAdd(grab, (unsigned)ch);
-        c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
-        if (c0 >= cnt) break;
-        const int c1 = min(c0 + ch, cnt);
+        int k = 0;
+        if (lane == 0) k = (int)atomicAdd(grab, 1u);
+        k = __shfl_sync(0xFFFFFFFFu, k, 0);
+        if (k >= plan.total) break;
+        int c0, c1;
+        plan.range(k, cnt, c0, c1, G);
         for (int base = c0; base < c1; base += G) {
             const int item = base + (int)gid;
             const bool valid = item < c1;
@@ -128,8 +151,10 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int32_t* __
             // word in this phase, so each lane may load it
             const uint32_t wv = valid ? ld_word_l1(a.word + v) : 0u;
             const int b = valid ? a.rp[v] : 0;
-            const int e = valid ? a.rp[v + 1] : 0;
-            const bool blocked = group_scan<TPR, true>(a.col, a.word, b, e, v, wv, glane, gshift);
+            // only neighbours of degree <= deg(v) + 1 can outrank v
+            const int e = valid ? (a.split ? b + a.split[v] : a.rp[v + 1]) : 0;
+            const bool blocked =
+                group_scan<TPR, true>(a.col_sel, a.word, b, e, v, wv, glane, gshift);
             if (valid && !blocked && glane == 0) a.word[v] = wv | kWordInSet;
         }
     }
@@ -148,14 +173,15 @@ __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int32_t* _
     const unsigned glane = lane % TPR;
     const unsigned gid = lane / TPR;
     const unsigned gshift = gid * TPR;
-    const int ch = chunk_of<G, CH>(cnt);
-    if (global_warp() >= (cnt + ch - 1) / ch) return;
+    const ChunkPlan plan = plan_of<G, CH>(cnt);
+    if (global_warp() >= plan.total) return;
     for (;;) {
-        int c0 = 0;
-        if (lane == 0) c0 = (int)atomicAdd(grab, (unsigned)ch);
-        c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
-        if (c0 >= cnt) break;
-        const int c1 = min(c0 + ch, cnt);
+        int k = 0;
+        if (lane == 0) k = (int)atomicAdd(grab, 1u);
+        k = __shfl_sync(0xFFFFFFFFu, k, 0);
+        if (k >= plan.total) break;
+        int c0, c1;
+        plan.range(k, cnt, c0, c1, G);
         // triage, one vertex per lane: candidates of Phase 1 are done
         int nscan = 0;
         for (int base = c0; base < c1; base += 32) {
@@ -175,7 +201,7 @@ __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int32_t* _
             const int v = valid ? wscan[item] : 0;
             const int b = valid ? a.rp[v] : 0;
             const int e = valid ? a.rp[v + 1] : 0;
-            const bool excl = group_scan<TPR, false>(a.col, a.word, b, e, v, 0u, glane, gshift);
+            const bool excl = group_scan<TPR, false>(a.col_sel, a.word, b, e, v, 0u, glane, gshift);
             const bool lead = glane == 0;
             if (valid && excl && lead) a.word[v] = kWordOut;
             const bool keep = valid && !excl && lead;
@@ -213,13 +239,13 @@ __device__ __forceinline__ void block_bin(const SolveArgs& a, const int32_t* __r
         const uint32_t wv = ld_word_l1(a.word + v);
         if (!kSelect && wv >= kWordInMin) continue;  // a candidate: nothing to do
         const int b = a.rp[v];
-        const int e = a.rp[v + 1];
+        const int e = (kSelect && a.split) ? b + a.split[v] : a.rp[v + 1];
         bool found = false;
         for (int base = b & ~3; base < e; base += 4 * (int)blockDim.x) {
             const int p0 = base + 4 * (int)threadIdx.x;
             bool hit = false;
             if (p0 < e) {
-                const int4 c = __ldg(reinterpret_cast<const int4*>(a.col + p0));
+                const int4 c = __ldg(reinterpret_cast<const int4*>(a.col_sel + p0));
                 const uint32_t w0 = (p0 >= b) ? ld_word_l1(a.word + c.x) : 0u;
                 const uint32_t w1 = (p0 + 1 >= b && p0 + 1 < e) ? ld_word_l1(a.word + c.y) : 0u;
                 const uint32_t w2 = (p0 + 2 >= b && p0 + 2 < e) ? ld_word_l1(a.word + c.z) : 0u;
@@ -261,7 +287,7 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     if (times && blockIdx.x == 0 && threadIdx.x == 0) times->t[0] = global_ns();
 
     // ---- init: Eq. 1 priorities
-    init_words(a, a.n);
+    init_words(a, a.n, true);
     if (!grid_barrier(ctl, nblocks, a.spin_cap, [times]() {
             if (times) times->t[1] = global_ns();
         }))
@@ -273,19 +299,36 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
         cnt[j] = a.bin_off[j + 1] - a.bin_off[j];
         total += cnt[j];
     }
+    // isolated vertices were decided at init but belong to round 0's alive set
+    const int iso = a.n_isolated;
     const int* off = a.bin_off;
-    for (int r = 0; total > 0; ++r) {
+    // in rounds after the first, a bin with no more rows than warps gets one
+    // warp (or 4 lanes for short rows) per row: latency, not throughput
+    const int nwarps_all = (int)(nblocks * (blockDim.x / 32));
+    for (int r = 0; total > 0 || (r == 0 && iso > 0); ++r) {
         const int32_t* src = (r == 0) ? a.order0 : ((r & 1) ? a.wl1 : a.wl0);
         int32_t* dst = ((r + 1) & 1) ? a.wl1 : a.wl0;
         int* next = ctl->bcnt[(r + 1) & 3];
 
-        // ---- Phase 1: selection test
+        // ---- Phase 1: selection test.  Round 0 scans most rows only up to
+        // their first few arcs (a blocker turns up early); later rounds keep
+        // the rows that need long scans, so a small bin gets wider groups.
         unsigned* grab = ctl->grab[(2 * r) & 3];
         block_bin<true>(a, src + off[4], cnt[4], &grab[4], nullptr, nullptr);
-        select_bin<32, kChunk3>(a, src + off[3], cnt[3], &grab[3]);
-        select_bin<16, kChunk2>(a, src + off[2], cnt[2], &grab[2]);
-        select_bin<4, kChunk1>(a, src + off[1], cnt[1], &grab[1]);
-        select_bin<1, kChunk0>(a, src + off[0], cnt[0], &grab[0]);
+        if (r == 0) {
+            select_bin<32, kChunk3>(a, src + off[3], cnt[3], &grab[3]);
+            select_bin<16, kChunk2>(a, src + off[2], cnt[2], &grab[2]);
+            select_bin<4, kChunk1>(a, src + off[1], cnt[1], &grab[1]);
+            select_bin<1, kChunk0>(a, src + off[0], cnt[0], &grab[0]);
+        } else {
+            select_bin<32, kChunk3>(a, src + off[3], cnt[3], &grab[3]);
+            if (cnt[2] <= nwarps_all) select_bin<32, kChunk3>(a, src + off[2], cnt[2], &grab[2]);
+            else select_bin<16, kChunk2>(a, src + off[2], cnt[2], &grab[2]);
+            if (cnt[1] <= nwarps_all) select_bin<32, kChunk3>(a, src + off[1], cnt[1], &grab[1]);
+            else select_bin<4, kChunk1>(a, src + off[1], cnt[1], &grab[1]);
+            if (cnt[0] <= nwarps_all) select_bin<4, kChunk1>(a, src + off[0], cnt[0], &grab[0]);
+            else select_bin<1, kChunk0>(a, src + off[0], cnt[0], &grab[0]);
+        }
         const int rr = r;
         if (!grid_barrier(ctl, nblocks, a.spin_cap, [ctl, times, rr]() {
                 if (times && rr < kStatRounds) times->t[2 + rr] = global_ns();
@@ -296,15 +339,38 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
         // ---- Phase 2+3: exclusion test, state update, compaction
         grab = ctl->grab[(2 * r + 1) & 3];
         block_bin<false>(a, src + off[4], cnt[4], &grab[4], &next[4], dst + off[4]);
-        exclude_bin<32, kChunk3>(a, src + off[3], cnt[3], &grab[3], &next[3], dst + off[3],
-                                 wscan, wkeep);
-        exclude_bin<16, kChunk2>(a, src + off[2], cnt[2], &grab[2], &next[2], dst + off[2],
-                                 wscan, wkeep);
-        exclude_bin<4, kChunk1>(a, src + off[1], cnt[1], &grab[1], &next[1], dst + off[1],
-                                wscan, wkeep);
-        exclude_bin<1, kChunk0>(a, src + off[0], cnt[0], &grab[0], &next[0], dst + off[0],
-                                wscan, wkeep);
-        const int cur = total;
+        if (r == 0) {
+            exclude_bin<32, kChunk3>(a, src + off[3], cnt[3], &grab[3], &next[3], dst + off[3],
+                                     wscan, wkeep);
+            exclude_bin<16, kChunk2>(a, src + off[2], cnt[2], &grab[2], &next[2], dst + off[2],
+                                     wscan, wkeep);
+            exclude_bin<4, kChunk1>(a, src + off[1], cnt[1], &grab[1], &next[1], dst + off[1],
+                                    wscan, wkeep);
+            exclude_bin<1, kChunk0>(a, src + off[0], cnt[0], &grab[0], &next[0], dst + off[0],
+                                    wscan, wkeep);
+        } else {
+            exclude_bin<32, kChunk3>(a, src + off[3], cnt[3], &grab[3], &next[3], dst + off[3],
+                                     wscan, wkeep);
+            if (cnt[2] <= nwarps_all)
+                exclude_bin<32, kChunk3>(a, src + off[2], cnt[2], &grab[2], &next[2],
+                                         dst + off[2], wscan, wkeep);
+            else
+                exclude_bin<16, kChunk2>(a, src + off[2], cnt[2], &grab[2], &next[2],
+                                         dst + off[2], wscan, wkeep);
+            if (cnt[1] <= nwarps_all)
+                exclude_bin<32, kChunk3>(a, src + off[1], cnt[1], &grab[1], &next[1],
+                                         dst + off[1], wscan, wkeep);
+            else
+                exclude_bin<4, kChunk1>(a, src + off[1], cnt[1], &grab[1], &next[1],
+                                        dst + off[1], wscan, wkeep);
+            if (cnt[0] <= nwarps_all)
+                exclude_bin<4, kChunk1>(a, src + off[0], cnt[0], &grab[0], &next[0],
+                                        dst + off[0], wscan, wkeep);
+            else
+                exclude_bin<1, kChunk0>(a, src + off[0], cnt[0], &grab[0], &next[0],
+                                        dst + off[0], wscan, wkeep);
+        }
+        const int cur = total + (r == 0 ? iso : 0);
         if (!grid_barrier(ctl, nblocks, a.spin_cap, [ctl, times, rr, cur]() {
                 if (times && rr < kStatRounds) times->t[2 + kStatRounds + rr] = global_ns();
                 if (rr < kStatRounds) ctl->alive[rr] = cur;
@@ -395,17 +461,30 @@ __device__ __forceinline__ bool is_real(const SegTable& seg, long long v) {
     return (int)v - seg.voff[g] < seg.nv[g];
 }
 
+// A vertex of the round-0 list: real and not isolated.
+__device__ __forceinline__ bool listed(const SegTable& seg, const int32_t* rp, long long v) {
+    return is_real(seg, v) && rp[v + 1] > rp[v];
+}
+
 __global__ void bin_count_kernel(const int32_t* __restrict__ rp, int32_t n, const SegTable seg,
-                                 const BinThr thr, int32_t* __restrict__ blkcnt) {
+                                 const BinThr thr, int32_t* __restrict__ blkcnt,
+                                 int32_t* __restrict__ n_iso) {
     __shared__ int c[kBins];
+    __shared__ int iso;
     if (threadIdx.x < kBins) c[threadIdx.x] = 0;
+    if (threadIdx.x == 0) iso = 0;
     __syncthreads();
     const long long v0 = (long long)n * blockIdx.x / gridDim.x;
     const long long v1 = (long long)n * (blockIdx.x + 1) / gridDim.x;
-    for (long long v = v0 + threadIdx.x; v < v1; v += blockDim.x)
-        if (is_real(seg, v)) atomicAdd(&c[bin_of(rp[v + 1] - rp[v], thr)], 1);
+    for (long long v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        if (!is_real(seg, v)) continue;
+        const int deg = rp[v + 1] - rp[v];
+        if (deg == 0) atomicAdd(&iso, 1);
+        else atomicAdd(&c[bin_of(deg, thr)], 1);
+    }
     __syncthreads();
     if (threadIdx.x < kBins) blkcnt[blockIdx.x * kBins + threadIdx.x] = c[threadIdx.x];
+    if (threadIdx.x == 0 && iso) atomicAdd(n_iso, iso);
 }
 
 // blockDim.x must be 256
@@ -423,7 +502,7 @@ __global__ void bin_scatter_kernel(const int32_t* __restrict__ rp, int32_t n, co
     for (long long c0 = v0; c0 < v1; c0 += blockDim.x) {
         const long long v = c0 + threadIdx.x;
         int j = -1;
-        if (v < v1 && is_real(seg, v)) j = bin_of(rp[v + 1] - rp[v], thr);
+        if (v < v1 && listed(seg, rp, v)) j = bin_of(rp[v + 1] - rp[v], thr);
         int rank = 0;
         for (int b = 0; b < kBins; ++b) {
             const unsigned m = __ballot_sync(0xFFFFFFFFu, j == b);
@@ -447,21 +526,31 @@ __global__ void bin_scatter_kernel(const int32_t* __restrict__ rp, int32_t n, co
 }
 
 cudaError_t build_bins(const int32_t* rp, int32_t n, const SegTable& seg, const int32_t thr[4],
-                       int32_t* order0, int32_t bin_off[6], cudaStream_t s) {
+                       int32_t* order0, int32_t bin_off[6], int32_t* n_isolated,
+                       cudaStream_t s) {
     for (int j = 0; j <= kBins; ++j) bin_off[j] = 0;
+    *n_isolated = 0;
     if (n == 0) return cudaSuccess;
     const int blocks = (int)std::min<long long>(1024, ((long long)n + 255) / 256);
     BinThr t;
     for (int k = 0; k < kBins - 1; ++k) t.t[k] = thr[k];
     int32_t* d_cnt = nullptr;
-    cudaError_t e = cudaMalloc((void**)&d_cnt, sizeof(int32_t) * blocks * kBins);
+    cudaError_t e = cudaMalloc((void**)&d_cnt, sizeof(int32_t) * (blocks * kBins + 1));
     if (e != cudaSuccess) return e;
     std::vector<int32_t> h((size_t)blocks * kBins);
-    bin_count_kernel<<<blocks, 256, 0, s>>>(rp, n, seg, t, d_cnt);
-    e = cudaGetLastError();
+    int32_t iso = 0;
+    e = cudaMemsetAsync(d_cnt + blocks * kBins, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) {
+        bin_count_kernel<<<blocks, 256, 0, s>>>(rp, n, seg, t, d_cnt, d_cnt + blocks * kBins);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h.data(), d_cnt, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&iso, d_cnt + blocks * kBins, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *n_isolated = iso;
     if (e == cudaSuccess) {
         int64_t tot[kBins] = {};
         for (int b = 0; b < blocks; ++b)

@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(kTileBlock, 2) tile_solve_kernel(const SolveAr
 
     // ---- init: Eq. 1 priorities (tile padding out), empty in-set bits,
     // round-0 row-block list
-    init_words(a, nrb * T);
+    init_words(a, nrb * T, false);
     {
         const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
         const long long nthreads = (long long)nblocks * blockDim.x;

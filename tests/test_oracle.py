@@ -109,6 +109,25 @@ def test_keys_degree_monotone_and_isolated():
     assert abs(Fraction(float(key[v:v + 1].view(np.float32)[0])) - exact) <= 4 * exact / 2**24
 
 
+def test_keys_two_degrees_apart_are_strictly_ordered():
+    # The CSR kernel scans, in the selection test, only neighbours of degree
+    # <= deg(v) + 1: it relies on deg(u) >= deg(v) + 2 giving key(u) < key(v)
+    # strictly whenever dbar + deg(v) < 2^19.  Check it at the extremes of eps
+    # (0 and 1 - 2^-24) over a sweep of dbar and degrees, binary32 as the
+    # oracle evaluates Eq. 1.
+    rng = np.random.default_rng(7)
+    eps_hi = 1.0 - 2.0**-24
+    dbars = [float(np.float32(x)) for x in (0.01, 0.5, 1.0, 2.0, 7.3, 31.9, 250.0, 4095.5, 100000.0)]
+    for dbar in dbars:
+        degs = sorted(set([1, 2, 3, 10, 100, 1000] + list(rng.integers(1, 2**19 - int(dbar) - 3, 40))))
+        for d in degs:
+            if dbar + d + 2 >= 2**19:
+                continue
+            hi_u = oracle.priority(dbar, d + 2, eps_hi)   # largest key two degrees up
+            lo_v = oracle.priority(dbar, d, 0.0)          # smallest key at degree d
+            assert hi_u < lo_v, (dbar, d)
+
+
 # ---------------------------------------------------------------- round rule
 
 def test_worked_example_sec31():
