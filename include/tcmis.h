@@ -93,7 +93,13 @@ typedef struct mis_options {
                                 of up to 16384 vertices always use one); 0 = default
                                 (half the SMs), so that several large requests share
                                 the device */
-    int32_t pad0;
+    int32_t order_rows;      /* CSR kernel's copy of col_idx, made at create (seed-
+                                independent): 1 (default) = each row stably partitioned
+                                so that the neighbours able to outrank a vertex (degree
+                                <= its degree + 1) come first and the selection test
+                                scans only them; 2 = each row fully sorted by neighbour
+                                degree (slower create, shorter exclusion scans);
+                                0 = none (full rows) */
 } mis_options;
 
 /* Per-solve statistics of the last completed solve on a graph. */

@@ -47,14 +47,12 @@ namespace {
 template <class T>
 cudaError_t dalloc(T** p, int64_t count, int64_t* footprint) {
     const size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(count, 1);
-    cudaError_t e = cudaMalloc((void**)p, bytes);
+    cudaError_t e = dev_alloc((void**)p, bytes);
     if (e == cudaSuccess && footprint) *footprint += (int64_t)bytes;
     return e;
 }
 
-void dfree(void* p) {
-    if (p) cudaFree(p);
-}
+void dfree(void* p) { dev_free(p); }
 
 }  // namespace
 
@@ -92,6 +90,12 @@ cudaError_t ws_reserve(Workspace& w, int64_t n, int32_t count) {
         (e = dalloc(&w.ctl, 1, &b)) != cudaSuccess || (e = dalloc(&w.times, 1, &b)) != cudaSuccess ||
         (e = dalloc(&w.seeds, std::max(count, 1), &b)) != cudaSuccess ||
         (e = dalloc(&w.out, cap, &b)) != cudaSuccess) {
+        ws_free(w);
+        return e;
+    }
+    // pool memory is recycled: the control block must read as "no solve yet"
+    if ((e = cudaMemset(w.ctl, 0, sizeof(Ctl))) != cudaSuccess ||
+        (e = cudaMemset(w.times, 0, sizeof(PhaseTimes))) != cudaSuccess) {
         ws_free(w);
         return e;
     }
@@ -208,10 +212,11 @@ int finish_create(mis_graph* g) {
     GraphData& d = g->d;
     cudaError_t e;
     const int64_t col_alloc = ((d.arcs + 3) / 4) * 4 + 4;
+    const bool order = g->opt.order_rows != 0;
     if ((e = ws_reserve(d.ws, d.n, d.count)) != cudaSuccess ||
         (e = dalloc(&d.order0, d.n, &d.footprint)) != cudaSuccess ||
-        (e = dalloc(&d.col_sel, col_alloc, &d.footprint)) != cudaSuccess ||
-        (e = dalloc(&d.split, d.n, &d.footprint)) != cudaSuccess)
+        (order && (e = dalloc(&d.col_sel, col_alloc, &d.footprint)) != cudaSuccess) ||
+        (order && (e = dalloc(&d.split, d.n, &d.footprint)) != cudaSuccess))
         return set_cuda_error(e, "workspace allocation");
     d.footprint += d.ws.bytes;
     if ((e = cudaMallocHost((void**)&d.ctl_host, sizeof(Ctl))) != cudaSuccess ||
@@ -228,11 +233,16 @@ int finish_create(mis_graph* g) {
         e = cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return set_cuda_error(e, "stream");
     }
-    e = cudaMemsetAsync(d.col_sel, 0, sizeof(int32_t) * (size_t)col_alloc, g->own_stream);
-    if (e == cudaSuccess)
-        e = build_degree_order(d.rp, d.col, d.n, d.arcs, seg_of(d), d.col_sel, d.split,
-                               g->own_stream);
-    if (e != cudaSuccess) return set_cuda_error(e, "degree ordering");
+    if (order) {
+        e = cudaMemsetAsync(d.col_sel, 0, sizeof(int32_t) * (size_t)col_alloc, g->own_stream);
+        if (e == cudaSuccess)
+            e = g->opt.order_rows == 2
+                    ? build_degree_order(d.rp, d.col, d.n, d.arcs, seg_of(d), d.col_sel, d.split,
+                                         g->own_stream)
+                    : build_row_partition(d.rp, d.col, d.n, d.arcs, seg_of(d), d.col_sel,
+                                          d.split, g->own_stream);
+        if (e != cudaSuccess) return set_cuda_error(e, "degree ordering");
+    }
     const int brc = rebin(g, thr, g->own_stream);
     if (brc != MIS_OK) return brc;
     if (g->opt.path == MIS_PATH_AUTO && g->opt.threads_per_row == 0) {
@@ -279,7 +289,7 @@ SolveArgs make_args(mis_graph* g, Workspace& w) {
     a.word = w.word;
     a.wl0 = w.wl0;
     a.wl1 = w.wl1;
-    a.col_sel = d.col_sel;
+    a.col_sel = d.col_sel ? d.col_sel : d.col;
     a.split = d.split;
     a.order0 = d.order0;
     for (int j = 0; j < 6; ++j) a.bin_off[j] = d.bin_off[j];
@@ -467,8 +477,8 @@ double estimate_arcs_per_tile(mis_graph* g) {
     unsigned long long* d_acc = nullptr;
     unsigned long long h[2] = {0, 0};
     cudaStream_t s = g->own_stream;
-    cudaError_t e = cudaMalloc((void**)&d_rbs, 4 * (size_t)count);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_acc, 16);
+    cudaError_t e = dev_alloc((void**)&d_rbs, 4 * (size_t)count);
+    if (e == cudaSuccess) e = dev_alloc((void**)&d_acc, 16);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_rbs, rbs.data(), 4 * (size_t)count,
                                               cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_acc, 0, 16, s);
@@ -479,8 +489,8 @@ double estimate_arcs_per_tile(mis_graph* g) {
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_acc, 16, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(d_rbs);
-    cudaFree(d_acc);
+    dev_free(d_rbs);
+    dev_free(d_acc);
     if (e != cudaSuccess || h[1] == 0) {
         cudaGetLastError();
         return 0.0;
@@ -647,6 +657,7 @@ void mis_options_init(mis_options* opt) {
     opt->max_slots = 0;
     opt->hbm_budget = 0;
     opt->serve_blocks = 0;
+    opt->order_rows = 1;
 }
 
 int mis_last_error(const char** msg) {

@@ -25,6 +25,32 @@ __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
         dbar0 = average_degree(a.rp[n], n);
         smix0 = mix64(a.seed0);
     }
+    if (a.seg.count == 0 && (n_words & 3) == 0) {
+        // four vertices per thread: 16-byte loads of row_ptr, stores of words
+        for (long long v = 4 * tid; v < n_words; v += 4 * nthreads) {
+            int r[5];
+            if (v + 4 <= n) {
+                const int4 q = *reinterpret_cast<const int4*>(a.rp + v);
+                r[0] = q.x;
+                r[1] = q.y;
+                r[2] = q.z;
+                r[3] = q.w;
+                r[4] = a.rp[v + 4];
+            } else {
+                for (int k = 0; k < 5; ++k) r[k] = (v + k <= n) ? a.rp[v + k] : 0;
+            }
+            uint32_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long u = v + k;
+                const int deg = r[k + 1] - r[k];
+                w[k] = u >= n ? kWordOut
+                              : (deg ? eq1_key(dbar0, deg, smix0, (uint32_t)u) : iso);
+            }
+            *reinterpret_cast<uint4*>(a.word + v) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        return;
+    }
     for (long long v = tid; v < n_words; v += nthreads) {
         uint32_t w;
         if (v >= n) {

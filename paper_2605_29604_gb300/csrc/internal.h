@@ -52,6 +52,11 @@ struct SolveArgs {
     int32_t* rbl1 = nullptr;
 };
 
+// mem.cu: device memory from the stream-ordered pool (reused across
+// creates); callers synchronise their streams before dev_free.
+cudaError_t dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+
 // Launch configuration chosen by the host.
 struct LaunchCfg {
     int grid = 0;
@@ -89,6 +94,10 @@ cudaError_t launch_pad_rows(int32_t* dst_rp, int32_t from, int32_t to, int32_t v
 cudaError_t build_degree_order(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs,
                                const SegTable& seg, int32_t* col_sel, int32_t* split,
                                cudaStream_t s);
+// The same prefix by a stable partition of each row (cheaper than the sort).
+cudaError_t build_row_partition(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs,
+                                const SegTable& seg, int32_t* col_sel, int32_t* split,
+                                cudaStream_t s);
 
 // kernels_tile.cu
 struct TileCsr {

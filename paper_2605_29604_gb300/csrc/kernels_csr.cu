@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     if (times && blockIdx.x == 0 && threadIdx.x == 0) times->t[0] = global_ns();
 
     // ---- init: Eq. 1 priorities
-    init_words(a, a.n, true);
+    init_words(a, (a.n + 15) / 16 * 16, true);  // words are padded to 16
     if (!grid_barrier(ctl, nblocks, a.spin_cap, [times]() {
             if (times) times->t[1] = global_ns();
         }))
@@ -398,15 +398,34 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
         const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
         const long long nthreads = (long long)nblocks * blockDim.x;
         unsigned in_cnt = 0;
-        for (long long v = tid; v < n; v += nthreads) {
-            const bool in = ld_word(a.word + v) >= kWordInMin;
-            in_cnt += in;
-            if (a.seg.count == 0) {
-                a.out[v] = in;
-            } else {
-                const int g = a.seg.blk_seg[v >> 4];
-                const int local = (int)v - a.seg.voff[g];
-                if (local < a.seg.nv[g]) a.out[a.seg.roff[g] + local] = in;
+        if (a.seg.count == 0 && ((uintptr_t)a.out & 3) == 0) {
+            // four vertices per thread: 16-byte word loads, 4-byte result stores
+            for (long long v = 4 * tid; v < n; v += 4 * nthreads) {
+                const uint4 q = *reinterpret_cast<const uint4*>(a.word + v);
+                const uint32_t b0 = q.x >= kWordInMin, b1 = q.y >= kWordInMin;
+                const uint32_t b2 = q.z >= kWordInMin, b3 = q.w >= kWordInMin;
+                if (v + 4 <= n) {
+                    *reinterpret_cast<uint32_t*>(a.out + v) = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+                    in_cnt += b0 + b1 + b2 + b3;
+                } else {
+                    const uint32_t bb[4] = {b0, b1, b2, b3};
+                    for (int k = 0; k < 4 && v + k < n; ++k) {
+                        a.out[v + k] = (uint8_t)bb[k];
+                        in_cnt += bb[k];
+                    }
+                }
+            }
+        } else {
+            for (long long v = tid; v < n; v += nthreads) {
+                const bool in = ld_word(a.word + v) >= kWordInMin;
+                in_cnt += in;
+                if (a.seg.count == 0) {
+                    a.out[v] = in;
+                } else {
+                    const int g = a.seg.blk_seg[v >> 4];
+                    const int local = (int)v - a.seg.voff[g];
+                    if (local < a.seg.nv[g]) a.out[a.seg.roff[g] + local] = in;
+                }
             }
         }
         for (int o = 16; o; o >>= 1) in_cnt += __shfl_xor_sync(0xFFFFFFFFu, in_cnt, o);
@@ -535,7 +554,7 @@ cudaError_t build_bins(const int32_t* rp, int32_t n, const SegTable& seg, const 
     BinThr t;
     for (int k = 0; k < kBins - 1; ++k) t.t[k] = thr[k];
     int32_t* d_cnt = nullptr;
-    cudaError_t e = cudaMalloc((void**)&d_cnt, sizeof(int32_t) * (blocks * kBins + 1));
+    cudaError_t e = dev_alloc((void**)&d_cnt, sizeof(int32_t) * (blocks * kBins + 1));
     if (e != cudaSuccess) return e;
     std::vector<int32_t> h((size_t)blocks * kBins);
     int32_t iso = 0;
@@ -575,8 +594,9 @@ cudaError_t build_bins(const int32_t* rp, int32_t n, const SegTable& seg, const 
         bin_scatter_kernel<<<blocks, 256, 0, s>>>(rp, n, seg, t, d_cnt, order0);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(d_cnt);
+    const cudaError_t se = cudaStreamSynchronize(s);  // also on error: nothing may still run
+    if (e == cudaSuccess) e = se;
+    dev_free(d_cnt);
     return e;
 }
 

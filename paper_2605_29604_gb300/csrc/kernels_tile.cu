@@ -122,12 +122,12 @@ cudaError_t build_tiles(const int32_t* rp, const int32_t* col, int32_t n, int64_
     const int32_t nrb = (n + T - 1) / T;
     out->nrb = nrb;
     const int words = T * T / 64;
-    cudaError_t e = cudaMalloc((void**)&out->trp, sizeof(int32_t) * ((size_t)nrb + 1));
+    cudaError_t e = dev_alloc((void**)&out->trp, sizeof(int32_t) * ((size_t)nrb + 1));
     if (e != cudaSuccess) return e;
     if (arcs == 0) {
         e = cudaMemsetAsync(out->trp, 0, sizeof(int32_t) * ((size_t)nrb + 1), s);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&out->tcol, sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMalloc((void**)&out->tbits, sizeof(uint64_t) * words);
+        if (e == cudaSuccess) e = dev_alloc((void**)&out->tcol, sizeof(int32_t));
+        if (e == cudaSuccess) e = dev_alloc((void**)&out->tbits, sizeof(uint64_t) * words);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         return e;
     }
@@ -138,22 +138,23 @@ cudaError_t build_tiles(const int32_t* rp, const int32_t* col, int32_t n, int64_
     size_t temp_bytes = 0, scan_bytes = 0;
     const int key_bits = bits_for((uint64_t)nrb * (uint64_t)nrb);
     auto cleanup = [&]() {
-        cudaFree(k0);
-        cudaFree(k1);
-        cudaFree(v0);
-        cudaFree(v1);
-        cudaFree(flags);
-        cudaFree(tid);
-        cudaFree(trow);
-        cudaFree(temp);
+        cudaStreamSynchronize(s);  // no kernel may still use the temporaries
+        dev_free(k0);
+        dev_free(k1);
+        dev_free(v0);
+        dev_free(v1);
+        dev_free(flags);
+        dev_free(tid);
+        dev_free(trow);
+        dev_free(temp);
     };
     const size_t A = (size_t)arcs;
-    if ((e = cudaMalloc((void**)&k0, 8 * A)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&k1, 8 * A)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&v0, A)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&v1, A)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&flags, 4 * A)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&tid, 4 * A)) != cudaSuccess) {
+    if ((e = dev_alloc((void**)&k0, 8 * A)) != cudaSuccess ||
+        (e = dev_alloc((void**)&k1, 8 * A)) != cudaSuccess ||
+        (e = dev_alloc((void**)&v0, A)) != cudaSuccess ||
+        (e = dev_alloc((void**)&v1, A)) != cudaSuccess ||
+        (e = dev_alloc((void**)&flags, 4 * A)) != cudaSuccess ||
+        (e = dev_alloc((void**)&tid, 4 * A)) != cudaSuccess) {
         cleanup();
         return e;
     }
@@ -171,7 +172,7 @@ cudaError_t build_tiles(const int32_t* rp, const int32_t* col, int32_t n, int64_
     e = cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, dk, dv, arcs, 0, key_bits, s);
     if (e == cudaSuccess)
         e = cub::DeviceScan::InclusiveSum(nullptr, scan_bytes, flags, tid, arcs, s);
-    if (e == cudaSuccess) e = cudaMalloc(&temp, std::max(temp_bytes, scan_bytes));
+    if (e == cudaSuccess) e = dev_alloc(&temp, std::max(temp_bytes, scan_bytes));
     if (e == cudaSuccess)
         e = cub::DeviceRadixSort::SortPairs(temp, temp_bytes, dk, dv, arcs, 0, key_bits, s);
     const unsigned ablocks = (unsigned)((arcs + 255) / 256);
@@ -191,9 +192,9 @@ cudaError_t build_tiles(const int32_t* rp, const int32_t* col, int32_t n, int64_
     }
     const int64_t ntiles = (int64_t)last_tid;
     out->ntiles = ntiles;
-    if ((e = cudaMalloc((void**)&out->tcol, 4 * (size_t)ntiles)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&trow, 4 * (size_t)ntiles)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&out->tbits, 8 * (size_t)words * (size_t)ntiles)) != cudaSuccess) {
+    if ((e = dev_alloc((void**)&out->tcol, 4 * (size_t)ntiles)) != cudaSuccess ||
+        (e = dev_alloc((void**)&trow, 4 * (size_t)ntiles)) != cudaSuccess ||
+        (e = dev_alloc((void**)&out->tbits, 8 * (size_t)words * (size_t)ntiles)) != cudaSuccess) {
         cleanup();
         return e;
     }

@@ -50,7 +50,7 @@ class mis_options(ctypes.Structure):
                 ("check_symmetry", ctypes.c_int32), ("build_tiles", ctypes.c_int32),
                 ("spin_cap", ctypes.c_int64), ("device", ctypes.c_int32),
                 ("max_slots", ctypes.c_int32), ("hbm_budget", ctypes.c_int64),
-                ("serve_blocks", ctypes.c_int32), ("pad0", ctypes.c_int32)]
+                ("serve_blocks", ctypes.c_int32), ("order_rows", ctypes.c_int32)]
 
 
 class mis_stats(ctypes.Structure):

@@ -96,6 +96,19 @@ def test_csr_custom_bins(bounds):
             native.mis_destroy(h)
 
 
+@pytest.mark.parametrize("order_rows", [0, 1, 2])
+@pytest.mark.parametrize("name", ["rmat14", "grid_perm", "star_hub", "dense", "k_ab", "cycle"])
+def test_row_orderings_bit_exact(name, order_rows):
+    g = graph(name)
+    h = create(g, order_rows=order_rows)
+    try:
+        for tpr in (0, 1):
+            got, st = gpu_solve(h, [3], native.MIS_PATH_CSR, tpr)
+            assert_same(g, 3, got, st)
+    finally:
+        native.mis_destroy(h)
+
+
 def test_zero_vertices():
     h = create((0, np.zeros(1, np.int32), np.zeros(0, np.int32)))
     try:
