@@ -271,6 +271,8 @@ def run_single(args):
     tuning = None
     if args.tpr is not None:
         native.mis_set_path(h, native.MIS_PATH_CSR, args.tpr)
+        if args.csr_pending is not None:
+            native.mis_set_csr_pending(h, args.csr_pending)
     elif args.path:
         native.mis_set_path(h, {"tile": 2, "tile_tc": 3}[args.path], args.tile)
     else:
@@ -348,6 +350,7 @@ def run_single(args):
         line["config"]["autotune"] = {"path": PATH_NAMES.get(tuning.path), "param": tuning.param,
                                       "bounds": list(tuning.bounds), "grid": tuning.grid,
                                       "candidates": tuning.candidates, "seconds": tune_s,
+                                      "csr_pending": tuning.csr_pending,
                                       "arcs_per_tile": tuning.arcs_per_tile}
     if rank == 0 and args.cpu_baseline:
         import oracle
@@ -406,7 +409,8 @@ def run_batch(args):
                    "rounds": st.rounds, "path": PATH_NAMES.get(st.path), "gen_s": t_gen,
                    "create_s": t_create, "autotune": {"path": PATH_NAMES.get(tuning.path),
                                                       "bounds": list(tuning.bounds),
-                                                      "grid": tuning.grid},
+                                                      "grid": tuning.grid,
+                                                      "csr_pending": tuning.csr_pending},
                    "l2": "flushed between steps (256 MB write)"},
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -541,6 +545,8 @@ def main():
     ap.add_argument("--workload", default="rmat22")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tpr", type=int, default=None, help="force the CSR path with these lanes")
+    ap.add_argument("--csr-pending", type=int, default=None, choices=[0, 1],
+                    help="with --tpr: Phase 2 over Phase 1's pending list (1) or a triage (0)")
     ap.add_argument("--path", default=None, choices=["tile", "tile_tc"])
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=3)

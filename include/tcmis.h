@@ -110,7 +110,8 @@ typedef struct mis_stats {
                                 when rows are binned by degree */
     int32_t status;          /* MIS_OK or the error of that solve */
     int32_t tile;            /* tile size of the graph's tile-CSR (0 = not built) */
-    int32_t pad0;
+    int32_t csr_pending;     /* CSR path: 1 when Phase 1 listed its non-candidates
+                                for Phase 2, 0 when Phase 2 triaged the worklist */
     int64_t ntiles;          /* non-empty tiles of that tile-CSR */
     int64_t alive_sum;       /* sum over rounds of |A| at round start */
     int64_t mis_size;        /* |M| */
@@ -202,6 +203,15 @@ int mis_set_path(mis_graph *g, int32_t path, int32_t param);
  * autotuner. */
 int mis_set_csr_bins(mis_graph *g, const int32_t *bounds);
 
+/* CSR path: how Phase 2 finds the vertices to test (Sec. 3.1: the exclusion
+ * test concerns the undecided non-candidates of the round).  pending = 1:
+ * Phase 1 appends each non-candidate's row to a pending list that Phase 2
+ * scans; pending = 0 (default): Phase 2 reads the whole worklist and skips
+ * the candidates by their state.  Same result either way; the faster one
+ * depends on the graph (chosen by mis_autotune).  MIS_EINVAL for other
+ * values, MIS_EBUSY while served requests on `g` are in flight. */
+int mis_set_csr_pending(mis_graph *g, int32_t pending);
+
 /* The autotuner's choice for a graph. */
 typedef struct mis_tuning {
     int32_t path;        /* MIS_PATH_CSR, MIS_PATH_TILE or MIS_PATH_TILE_TC */
@@ -210,12 +220,14 @@ typedef struct mis_tuning {
     int32_t grid;        /* persistent blocks in use */
     int32_t candidates;  /* configurations timed */
     float ms;            /* median solve time of the choice, ms */
+    int32_t csr_pending; /* CSR: the mis_set_csr_pending mode of the choice */
     double arcs_per_tile;/* sampled arcs per non-empty 8 x 8 tile */
 } mis_tuning;
 
 /*
  * Autotuner: times candidate configurations on `g` (median of `reps` solves
- * each, reps <= 0 means 3) -- CSR degree-bin bounds and grid sizes, and the
+ * each, reps <= 0 means 3) -- CSR degree-bin bounds, grid sizes and both
+ * mis_set_csr_pending modes, and the
  * tile paths (8 x 8 and 16 x 16 popc, 16 x 16 tensor core) when sampled tiles
  * hold enough arcs -- applies the fastest to `g` and caches it for the
  * graph's density class (average degree, size, tile locality, device).  Graphs
@@ -301,7 +313,7 @@ void mis_serve_shutdown(void);
  * a graph that breaks the input contract gives an unspecified set, but the
  * kernel never reads or writes outside the buffers above.
  *
- * Scratch: the library holds one fixed array of 3 MiB + 512 B in device
+ * Scratch: the library holds one fixed array of 3 MiB + 1 KiB in device
  * memory on every GPU that loads it, until the process exits.  The first
  * call on a device looks up that array's device address (with that device
  * current); make that first call before any stream capture.  All calls share

@@ -58,7 +58,7 @@ void dfree(void* p) { dev_free(p); }
 
 int64_t ws_bytes_for(int64_t n, int32_t count) {
     const int64_t cap = (n + 15) / 16 * 16;
-    return 4 * cap * 3 + (cap / 32 + 1) * 4 + 2 * 4 * (cap / 8) + (int64_t)sizeof(Ctl) +
+    return 4 * cap + 16 * cap * 3 + (cap / 32 + 1) * 4 + 2 * 4 * (cap / 8) + (int64_t)sizeof(Ctl) +
            (int64_t)sizeof(PhaseTimes) + 8 * std::max<int64_t>(count, 1) + cap;
 }
 
@@ -66,6 +66,7 @@ void ws_free(Workspace& w) {
     dfree(w.word);
     dfree(w.wl0);
     dfree(w.wl1);
+    dfree(w.wlp);
     dfree(w.inbits);
     dfree(w.rbl0);
     dfree(w.rbl1);
@@ -84,6 +85,7 @@ cudaError_t ws_reserve(Workspace& w, int64_t n, int32_t count) {
     int64_t b = 0;
     if ((e = dalloc(&w.word, cap, &b)) != cudaSuccess || (e = dalloc(&w.wl0, cap, &b)) != cudaSuccess ||
         (e = dalloc(&w.wl1, cap, &b)) != cudaSuccess ||
+        (e = dalloc(&w.wlp, cap, &b)) != cudaSuccess ||
         (e = dalloc(&w.inbits, cap / 32 + 1, &b)) != cudaSuccess ||
         (e = dalloc(&w.rbl0, cap / 8, &b)) != cudaSuccess ||
         (e = dalloc(&w.rbl1, cap / 8, &b)) != cudaSuccess ||
@@ -160,7 +162,7 @@ int rebin(mis_graph* g, const int32_t thr[4], cudaStream_t s) {
     GraphData& d = g->d;
     for (int j = 0; j < 4; ++j) d.thr[j] = thr[j];
     cudaError_t e =
-        build_bins(d.rp, d.n, seg_of(d), d.thr, d.order0, d.bin_off, &d.n_isolated, s);
+        build_bins(d.rp, d.split, d.n, seg_of(d), d.thr, d.order0, d.bin_off, &d.n_isolated, s);
     if (e != cudaSuccess) return set_cuda_error(e, "degree binning");
     return MIS_OK;
 }
@@ -289,11 +291,13 @@ SolveArgs make_args(mis_graph* g, Workspace& w) {
     a.word = w.word;
     a.wl0 = w.wl0;
     a.wl1 = w.wl1;
+    a.wlp = w.wlp;
     a.col_sel = d.col_sel ? d.col_sel : d.col;
     a.split = d.split;
     a.order0 = d.order0;
     for (int j = 0; j < 6; ++j) a.bin_off[j] = d.bin_off[j];
     a.n_isolated = d.n_isolated;
+    a.pending = g->csr_pending;
     a.ctl = w.ctl;
     a.times = w.times;
     a.seg = seg_of(d);
@@ -400,6 +404,7 @@ struct TuneChoice {
     int32_t bounds[4] = {8, 4096, 4096, 65536};
     int32_t grid = 0;    // CSR grid request (0 = default)
     float ms = 0.f;
+    int32_t pending = 0; // CSR: Phase 1 lists its non-candidates for Phase 2
 };
 
 std::mutex g_tune_mu;
@@ -418,8 +423,10 @@ void tune_load_locked() {
         std::string key;
         TuneChoice c;
         if (ss >> key >> c.path >> c.param >> c.bounds[0] >> c.bounds[1] >> c.bounds[2] >>
-            c.bounds[3] >> c.grid >> c.ms)
+            c.bounds[3] >> c.grid >> c.ms) {
+            if (!(ss >> c.pending)) c.pending = 0;  // lines written before the field
             g_tune_cache[key] = c;
+        }
     }
 }
 
@@ -431,7 +438,7 @@ void tune_save_locked() {
         const TuneChoice& c = kv.second;
         out << kv.first << ' ' << c.path << ' ' << c.param << ' ' << c.bounds[0] << ' '
             << c.bounds[1] << ' ' << c.bounds[2] << ' ' << c.bounds[3] << ' ' << c.grid << ' '
-            << c.ms << '\n';
+            << c.ms << ' ' << c.pending << '\n';
     }
 }
 
@@ -525,6 +532,7 @@ int apply_choice(mis_graph* g, const TuneChoice& c) {
         for (int k = 0; k < 4; ++k) thr[k] = c.bounds[k];
     }
     g->tpr = c.param;
+    g->csr_pending = c.pending;
     if (g->last_stream) cudaStreamSynchronize(g->last_stream);
     const int rc = rebin(g, thr, g->own_stream);
     if (rc != MIS_OK) return rc;
@@ -570,7 +578,10 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
         t.bounds[2] = c;
         t.bounds[3] = d;
         t.grid = grid;
-        cands.push_back(t);
+        for (int pending : {0, 1}) {
+            t.pending = pending;
+            cands.push_back(t);
+        }
     };
     const int maxg = csr_max_coresident_blocks(g->d.device);
     bins(8, 4096, 4096, 65536, 0);
@@ -615,6 +626,7 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
         for (int k = 0; k < 4; ++k) out->bounds[k] = best.bounds[k];
         out->grid = g->path == MIS_PATH_CSR ? g->grid : g->tile_grid;
         out->ms = best.ms;
+        out->csr_pending = best.path == MIS_PATH_CSR ? best.pending : 0;
         out->arcs_per_tile = apt;
         out->candidates = (int32_t)cands.size();
     }
@@ -944,6 +956,16 @@ int mis_set_csr_bins(mis_graph* g, const int32_t* bounds) {
     return rebin(g, bounds, g->own_stream);
 }
 
+int mis_set_csr_pending(mis_graph* g, int32_t pending) {
+    clear_error();
+    if (!g) return set_error(MIS_EINVAL, "null graph");
+    if (pending != 0 && pending != 1) return set_error(MIS_EINVAL, "pending must be 0 or 1");
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
+    g->csr_pending = pending;
+    return MIS_OK;
+}
+
 int mis_autotune(mis_graph* g, int32_t reps, mis_tuning* chosen) {
     clear_error();
     if (!g) return set_error(MIS_EINVAL, "null graph");
@@ -1043,6 +1065,7 @@ int mis_get_stats(mis_graph* g, mis_stats* st) {
     st->path = g->last_path;
     st->threads_per_row = g->tpr;
     st->tile = g->d.tiles.T;
+    st->csr_pending = g->csr_pending;
     st->ntiles = g->d.tiles.ntiles;
     st->alive_sum = (int64_t)c.alive_sum;
     st->mis_size = (int64_t)c.mis_size;

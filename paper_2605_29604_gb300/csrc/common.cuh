@@ -50,6 +50,7 @@ struct Ctl {
     int alive[kStatRounds];
     unsigned grab[4][kBins];  // per-bin work counters, ring indexed by round & 3
     int bcnt[4][kBins];       // per-bin worklist sizes, ring indexed by round & 3
+    int pcnt[4][kBins];       // per-bin pending-list sizes, ring indexed by round & 3
     int alive_acc[4];         // |A| at round start, ring indexed by round & 3
 };
 
@@ -131,7 +132,18 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
 // releases the others.  Returns false when the launch must stop.
 template <class Leader>
 __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, long long spin_cap,
-                                             Leader leader) {
+                                             Leader leader);
+
+struct NoLeader {
+    __device__ void operator()() const {}
+};
+
+// As above; after the wait, thread 0 of every block also runs `after` (e.g.
+// to copy counters written before the barrier into shared memory, one load
+// per block instead of one per warp) before the block's threads go on.
+template <class Leader, class After>
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, long long spin_cap,
+                                             Leader leader, After after) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -157,15 +169,18 @@ __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, long lo
         }
         __threadfence();
         if (ld_acquire_int(&ctl->err) != 0) ok = 0;
+        if (ok) after();
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
 }
 
-struct NoLeader {
-    __device__ void operator()() const {}
-};
+template <class Leader>
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, long long spin_cap,
+                                             Leader leader) {
+    return grid_barrier(ctl, nblocks, spin_cap, leader, NoLeader());
+}
 
 // ---------------------------------------------------------------- warp helpers
 

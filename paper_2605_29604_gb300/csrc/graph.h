@@ -26,8 +26,9 @@ struct Workspace {
     int64_t cap = 0;       // vertices held (a multiple of 16)
     int32_t seed_cap = 0;  // seeds held
     uint32_t* word = nullptr;
-    int32_t* wl0 = nullptr;
-    int32_t* wl1 = nullptr;
+    int4* wl0 = nullptr;  // worklists of row records
+    int4* wl1 = nullptr;
+    int4* wlp = nullptr;
     uint32_t* inbits = nullptr;
     int32_t* rbl0 = nullptr;
     int32_t* rbl1 = nullptr;
@@ -68,7 +69,7 @@ struct GraphData {
     // degree-ordered rows and degree bins of the CSR kernel
     int32_t* col_sel = nullptr;
     int32_t* split = nullptr;
-    int32_t* order0 = nullptr;
+    int4* order0 = nullptr;       // round-0 row records grouped by bin
     int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};
     int32_t n_isolated = 0;
     int32_t thr[4] = {0, 0, 0, 0};
@@ -90,6 +91,7 @@ struct mis_graph {
     int32_t grid = 0;             // persistent grid size (CSR kernel)
     int32_t tile_grid = 0;        // persistent grid size (tile kernels)
     int32_t tile_slots = 8;       // tile kernels: lanes (tiles in flight) per row block
+    int32_t csr_pending = 0;      // CSR kernel: Phase 1 lists non-candidates for Phase 2
     cudaStream_t own_stream = nullptr;
     cudaStream_t last_stream = nullptr;
     int32_t last_path = 0;

@@ -27,8 +27,11 @@ struct SolveArgs {
     const int32_t* col = nullptr;  // col_idx, padded by >= 4 entries
     int32_t n = 0;                 // vertices (of the union for a batch)
     uint32_t* word = nullptr;      // packed per-vertex state, n
-    int32_t* wl0 = nullptr;        // worklists, n each
-    int32_t* wl1 = nullptr;
+    // Worklists hold row records {v, row begin, end of the selection prefix,
+    // row end} (int4), so that a scan needs no row_ptr lookup.
+    int4* wl0 = nullptr;           // worklists, n each
+    int4* wl1 = nullptr;
+    int4* wlp = nullptr;           // pending list of Phase 2 (non-candidates), n
     Ctl* ctl = nullptr;            // control block (zeroed before launch)
     PhaseTimes* times = nullptr;   // phase timestamps (nullable)
     uint8_t* out = nullptr;        // result bytes (device), nullable
@@ -39,9 +42,11 @@ struct SolveArgs {
     // degree bins of the CSR kernel
     const int32_t* col_sel = nullptr; // rows sorted by neighbour degree (padded like col)
     const int32_t* split = nullptr;   // neighbours of degree <= deg(v) + 1 (nullable)
-    const int32_t* order0 = nullptr;  // round-0 list: real vertices grouped by bin
+    const int4* order0 = nullptr;     // round-0 records: real non-isolated vertices by bin
     int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};  // bin j occupies [bin_off[j], bin_off[j+1])
     int32_t n_isolated = 0;           // real vertices of degree 0 (not in order0)
+    int32_t pending = 0;              // 1: Phase 1 lists its non-candidates for Phase 2
+                                      // (in wlp); 0: Phase 2 triages W_r itself
     // tile-CSR (used by the tile kernels only)
     const int32_t* trp = nullptr;    // row block rb owns tiles [trp[rb], trp[rb+1])
     const int32_t* tcol = nullptr;   // column block of each tile
@@ -70,11 +75,12 @@ cudaError_t launch_csr_solve(const SolveArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_csr_solve_single(const SolveArgs& a, cudaStream_t s);
 int csr_max_coresident_blocks(int device);
 int csr_block_size();
-// Round-0 list grouped by degree bin (thr: inclusive upper degree of bins
-// 0..3); isolated vertices are left out and counted in *n_isolated.
-cudaError_t build_bins(const int32_t* rp, int32_t n, const SegTable& seg, const int32_t thr[4],
-                       int32_t* order0, int32_t bin_off[6], int32_t* n_isolated,
-                       cudaStream_t s);
+// Round-0 row records grouped by degree bin (thr: inclusive upper degree of
+// bins 0..3; split: selection-prefix lengths, nullable = whole rows);
+// isolated vertices are left out and counted in *n_isolated.
+cudaError_t build_bins(const int32_t* rp, const int32_t* split, int32_t n, const SegTable& seg,
+                       const int32_t thr[4], int4* order0, int32_t bin_off[6],
+                       int32_t* n_isolated, cudaStream_t s);
 
 // kernels_util.cu
 cudaError_t launch_validate(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs,

@@ -16,17 +16,18 @@
 //             common.cuh), so rounds and alive-set sizes match Algorithm 2.
 //   output    result bytes out[v] = [v in the MIS].
 //
-// Worklists are split into degree bins (fixed at create time, degrees do not
+// Worklists hold row records {v, row begin, end of the selection prefix, row
+// end} and are split into degree bins (fixed at create time, degrees do not
 // change): bin j holds the vertices with deg in (thr[j-1], thr[j]].  Bins 0..3
-// are scanned by groups of 1, 4, 16 and 32 lanes, bin 4 (hubs) by a whole
-// block.  Warps take chunks of a bin's list through an atomic counter (heavy
-// bins first; the chunk shrinks when a bin is small so that the chunks spread
-// over all warps).  In Phase 2 a chunk is first triaged one vertex per lane
-// (candidates need no scan), the remaining vertices are scanned by groups,
-// and survivors are staged in shared memory and appended to the next list
-// with one atomic per chunk.  Each lane loads 16-byte aligned int4 slices of
-// col_idx and gathers the four neighbour words; scans stop at the first
-// neighbour that decides the test.
+// are scanned by groups of 1, 4, 16 and 32 lanes (a lane of a 1-lane group
+// scans several rows at once), bin 4 (hubs) by a whole block.  Each warp
+// takes its first chunk of a bin by its index and further chunks through the
+// bin's counter.  Phase 2 either scans a pending list of Phase 1's
+// non-candidates or triages W_r one vertex per lane (candidates need no scan);
+// survivors are staged in shared memory and appended to the next list with
+// one atomic per chunk.  Lanes load 16-byte aligned int4 slices of col_idx
+// and gather the four neighbour words; scans stop at the first neighbour that
+// decides the test.
 #include <algorithm>
 #include <cstdio>
 #include <vector>
@@ -39,6 +40,9 @@ namespace tcmis {
 
 constexpr int kCsrBlock = 512;
 constexpr int kCsrMinBlocksPerSm = 3;
+// Rows scanned at once by one lane when a row has one lane (the scans are
+// bound by load latency, so independent rows per lane add loads in flight).
+constexpr int kRowsPerLane = 2;
 constexpr int kWarps = kCsrBlock / 32;
 
 // Rows per chunk taken by one warp, per bin (bin 4 is taken a row at a time
@@ -53,13 +57,19 @@ __device__ __forceinline__ bool outranks(uint32_t wu, int u, uint32_t wv, int v)
     return wu > wv || (wu == wv && u > v);
 }
 
+// Neighbour words as they stand (through L1: see ld_word_l1).
+struct LiveWords {
+    const uint32_t* word;
+    __device__ __forceinline__ uint32_t operator()(int u) const { return ld_word_l1(word + u); }
+};
+
 // Scan of the row [b, e) of v by the group of TPR lanes of this lane; kSelect:
 // is there a neighbour that outranks v, else: is there an in neighbour.
 // Warp-uniform loop: every lane of the warp iterates until no group has work.
-template <int TPR, bool kSelect>
-__device__ __forceinline__ bool group_scan(const int32_t* __restrict__ col,
-                                           const uint32_t* __restrict__ word, int b, int e,
-                                           int v, uint32_t wv, unsigned glane, unsigned gshift) {
+template <int TPR, bool kSelect, class Words>
+__device__ __forceinline__ bool group_scan(const int32_t* __restrict__ col, Words nbw, int b,
+                                           int e, int v, uint32_t wv, unsigned glane,
+                                           unsigned gshift) {
     constexpr unsigned gbits = (TPR == 32) ? 0xFFFFFFFFu : ((1u << TPR) - 1u);
     bool found = false;
     int p0 = (b & ~3) + 4 * (int)glane;
@@ -67,10 +77,10 @@ __device__ __forceinline__ bool group_scan(const int32_t* __restrict__ col,
         bool hit = false;
         if (!found && p0 < e) {
             const int4 c = __ldg(reinterpret_cast<const int4*>(col + p0));
-            const uint32_t w0 = (p0 >= b) ? ld_word_l1(word + c.x) : 0u;
-            const uint32_t w1 = (p0 + 1 >= b && p0 + 1 < e) ? ld_word_l1(word + c.y) : 0u;
-            const uint32_t w2 = (p0 + 2 >= b && p0 + 2 < e) ? ld_word_l1(word + c.z) : 0u;
-            const uint32_t w3 = (p0 + 3 >= b && p0 + 3 < e) ? ld_word_l1(word + c.w) : 0u;
+            const uint32_t w0 = (p0 >= b) ? nbw(c.x) : 0u;
+            const uint32_t w1 = (p0 + 1 >= b && p0 + 1 < e) ? nbw(c.y) : 0u;
+            const uint32_t w2 = (p0 + 2 >= b && p0 + 2 < e) ? nbw(c.z) : 0u;
+            const uint32_t w3 = (p0 + 3 >= b && p0 + 3 < e) ? nbw(c.w) : 0u;
             if (kSelect) {
                 hit = outranks(w0, c.x, wv, v) | outranks(w1, c.y, wv, v) |
                       outranks(w2, c.z, wv, v) | outranks(w3, c.w, wv, v);
@@ -87,11 +97,63 @@ __device__ __forceinline__ bool group_scan(const int32_t* __restrict__ col,
     return found;
 }
 
-// Work split of a bin of `cnt` rows into chunks taken through one counter:
-// `nbig` chunks of `ch` rows (at most CH, fewer when the bin is small so that
-// the chunks spread over all warps) cover most of the bin, then chunks of one
-// warp pass (G rows) finish it, so that the last warps of a phase do not
-// wait long for a straggler.
+// Scans of R rows at once by one lane: the records list[idx[i]], i < R, of
+// the valid rows.  kSelect: flag[i] = some neighbour outranks the row's vertex
+// (only the prefix [b, es) of the row is read), else: flag[i] = some
+// neighbour is in the MIS.  All loads of one step are issued before any
+// test, so each lane keeps up to R gathers in flight.
+template <int R, bool kSelect, class Words>
+__device__ __forceinline__ void lane_rows(const int32_t* __restrict__ col, Words nbw,
+                                          const int4 (&rec)[R], const bool (&valid)[R],
+                                          const uint32_t (&wv)[R], bool (&flag)[R]) {
+    int p[R], e[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        e[i] = valid[i] ? (kSelect ? rec[i].z : rec[i].w) : 0;
+        p[i] = rec[i].y & ~3;
+        flag[i] = false;
+    }
+    for (;;) {
+        bool act[R];
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            act[i] = !flag[i] && p[i] < e[i];
+            any |= act[i];
+        }
+        if (!any) break;
+        int4 c[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+            c[i] = act[i] ? __ldg(reinterpret_cast<const int4*>(col + p[i])) : make_int4(0, 0, 0, 0);
+        uint32_t w[R][4];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int q = p[i], b = rec[i].y;
+            w[i][0] = (act[i] && q >= b) ? nbw(c[i].x) : 0u;
+            w[i][1] = (act[i] && q + 1 >= b && q + 1 < e[i]) ? nbw(c[i].y) : 0u;
+            w[i][2] = (act[i] && q + 2 >= b && q + 2 < e[i]) ? nbw(c[i].z) : 0u;
+            w[i][3] = (act[i] && q + 3 >= b && q + 3 < e[i]) ? nbw(c[i].w) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int v = rec[i].x;
+            bool hit;
+            if (kSelect)
+                hit = outranks(w[i][0], c[i].x, wv[i], v) | outranks(w[i][1], c[i].y, wv[i], v) |
+                      outranks(w[i][2], c[i].z, wv[i], v) | outranks(w[i][3], c[i].w, wv[i], v);
+            else
+                hit = max(max(w[i][0], w[i][1]), max(w[i][2], w[i][3])) >= kWordInMin;
+            flag[i] = flag[i] || (act[i] && hit);
+            p[i] += 4;
+        }
+    }
+}
+
+// Work split of a bin of `cnt` rows into chunks: `nbig` chunks of `ch` rows
+// (at most CH, fewer when the bin is small so that the chunks spread over all
+// warps) cover most of the bin, then chunks of one warp pass (G rows) finish
+// it, so that the last warps of a phase do not wait long for a straggler.
 struct ChunkPlan {
     int ch;
     int nbig;
@@ -108,9 +170,8 @@ struct ChunkPlan {
 };
 
 template <int G, int CH>
-__device__ __forceinline__ ChunkPlan plan_of(int cnt) {
-    const long long nwarps = (long long)gridDim.x * (blockDim.x / 32);
-    long long per = (cnt + nwarps - 1) / nwarps;
+__device__ __forceinline__ ChunkPlan plan_of(int cnt, int nwarps) {
+    long long per = ((long long)cnt + nwarps - 1) / nwarps;
     per = ((per + G - 1) / G) * G;
     if (per < G) per = G;
     ChunkPlan p;
@@ -120,126 +181,208 @@ __device__ __forceinline__ ChunkPlan plan_of(int cnt) {
     return p;
 }
 
-__device__ __forceinline__ long long global_warp() {
-    return (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+// Who takes which chunk.  Warp w of the grid starts on chunk (w - base) mod
+// nwarps of a bin (no atomic); the chunks past the first nwarps are handed out
+// through the bin's counter.  `base` moves on by each bin's share, so that
+// bins smaller than the grid land on different warps.
+struct WarpSched {
+    int gw;      // this warp's index in the grid
+    int nwarps;  // warps in the grid
+    int base;    // first warp of the next bin
+    __device__ __forceinline__ int first(int total) {
+        int k = gw - base;
+        if (k < 0) k += nwarps;
+        base += total < nwarps ? total : 0;
+        if (base >= nwarps) base -= nwarps;
+        return k;
+    }
+};
+
+__device__ __forceinline__ int next_chunk(int total, int nwarps, unsigned* grab) {
+    if (total <= nwarps) return total;  // every chunk was a first chunk
+    int k = 0;
+    if (lane_id() == 0) k = nwarps + (int)atomicAdd(grab, 1u);
+    return __shfl_sync(0xFFFFFFFFu, k, 0);
 }
 
-// Phase 1, bins 0..3: selection test of every row of the bin's list.
-template <int TPR, int CH>
-__device__ __forceinline__ void select_bin(const SolveArgs& a, const int32_t* __restrict__ list,
-                                           int cnt, unsigned* grab) {
+// Stages up to 32 list indices per call (the group leaders' `keep` flags) in
+// the warp's shared buffer; returns the new fill.
+__device__ __forceinline__ int stage_keep(bool keep, int idx, int32_t* wbuf, int fill) {
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+    if (keep) wbuf[fill + __popc(bal & lanemask_lt())] = idx;
+    return fill + __popc(bal);
+}
+
+// Appends the records list[wbuf[i]] of the warp's staged entries to `dst`
+// with one atomic on `next`.
+__device__ __forceinline__ void flush_stage(const int32_t* wbuf, int fill, const int4* list,
+                                            int* next, int4* __restrict__ dst) {
+    __syncwarp();
+    if (fill) {
+        const unsigned lane = lane_id();
+        int o = 0;
+        if (lane == 0) o = atomicAdd(next, fill);
+        o = __shfl_sync(0xFFFFFFFFu, o, 0);
+        for (int i = (int)lane; i < fill; i += 32) dst[o + i] = list[wbuf[i]];
+    }
+    __syncwarp();
+}
+
+// Phase 1, bins 0..3: selection test of every row of the bin's list W_r.
+// Candidates are marked in the MIS.  kPending: the others form the pending
+// list P_r of Phase 2 (appended to pdst, counted in *pnext).
+template <int TPR, int CH, bool kPending>
+__device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __restrict__ list, int cnt, WarpSched& ws,
+                                           unsigned* grab, int* pnext, int4* __restrict__ pdst,
+                                           int32_t* wbuf) {
+    static_assert(CH <= kStageMax, "chunk exceeds the staging buffer");
     constexpr int G = 32 / TPR;
     if (cnt <= 0) return;
     const unsigned lane = lane_id();
     const unsigned glane = lane % TPR;
     const unsigned gid = lane / TPR;
     const unsigned gshift = gid * TPR;
-    const ChunkPlan plan = plan_of<G, CH>(cnt);
-    if (global_warp() >= plan.total) return;
-    for (;;) {
-        int k = 0;
-        if (lane == 0) k = (int)atomicAdd(grab, 1u);
-        k = __shfl_sync(0xFFFFFFFFu, k, 0);
-        if (k >= plan.total) break;
+    const ChunkPlan plan = plan_of<G, CH>(cnt, ws.nwarps);
+    for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps, grab)) {
         int c0, c1;
         plan.range(k, cnt, c0, c1, G);
-        for (int base = c0; base < c1; base += G) {
-            const int item = base + (int)gid;
-            const bool valid = item < c1;
-            const int v = valid ? list[item] : 0;
-            // every vertex of W_r is undecided and nothing else writes its
-            // word in this phase, so each lane may load it
-            const uint32_t wv = valid ? ld_word_l1(a.word + v) : 0u;
-            const int b = valid ? a.rp[v] : 0;
-            // only neighbours of degree <= deg(v) + 1 can outrank v
-            const int e = valid ? (a.split ? b + a.split[v] : a.rp[v + 1]) : 0;
-            const bool blocked =
-                group_scan<TPR, true>(a.col_sel, a.word, b, e, v, wv, glane, gshift);
-            if (valid && !blocked && glane == 0) a.word[v] = wv | kWordInSet;
+        int fill = 0;
+        if constexpr (TPR == 1) {
+            for (int base = c0; base < c1; base += 32 * kRowsPerLane) {
+                int4 rec[kRowsPerLane];
+                bool valid[kRowsPerLane], blocked[kRowsPerLane];
+                uint32_t wv[kRowsPerLane];
+#pragma unroll
+                for (int i = 0; i < kRowsPerLane; ++i) {
+                    const int item = base + (int)lane + 32 * i;
+                    valid[i] = item < c1;
+                    rec[i] = valid[i] ? list[item] : make_int4(0, 0, 0, 0);
+                }
+#pragma unroll
+                for (int i = 0; i < kRowsPerLane; ++i)
+                    wv[i] = valid[i] ? ld_word_l1(a.word + rec[i].x) : 0u;
+                lane_rows<kRowsPerLane, true>(a.col_sel, LiveWords{a.word}, rec, valid, wv,
+                                              blocked);
+#pragma unroll
+                for (int i = 0; i < kRowsPerLane; ++i) {
+                    if (valid[i] && !blocked[i]) a.word[rec[i].x] = wv[i] | kWordInSet;
+                    if (kPending)
+                        fill = stage_keep(valid[i] && blocked[i], base + (int)lane + 32 * i, wbuf,
+                                          fill);
+                }
+            }
+        } else {
+            for (int base = c0; base < c1; base += G) {
+                const int item = base + (int)gid;
+                const bool valid = item < c1;
+                const int4 rec = valid ? list[item] : make_int4(0, 0, 0, 0);
+                // every vertex of W_r is undecided and nothing else writes its
+                // word in this phase, so each lane may load it
+                const uint32_t wv = valid ? ld_word_l1(a.word + rec.x) : 0u;
+                const int e = valid ? rec.z : 0;
+                const bool blocked = group_scan<TPR, true>(a.col_sel, LiveWords{a.word}, rec.y, e,
+                                                           rec.x, wv, glane, gshift);
+                const bool lead = glane == 0;
+                if (valid && !blocked && lead) a.word[rec.x] = wv | kWordInSet;
+                if (kPending) fill = stage_keep(valid && blocked && lead, item, wbuf, fill);
+            }
         }
+        if (kPending) flush_stage(wbuf, fill, list, pnext, pdst);
     }
 }
 
-// Phase 2+3, bins 0..3: triage, exclusion test, compaction.
-template <int TPR, int CH>
-__device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int32_t* __restrict__ list,
-                                            int cnt, unsigned* grab, int* next,
-                                            int32_t* __restrict__ dst, int32_t* wscan,
-                                            int32_t* wkeep) {
-    static_assert(CH <= kStageMax, "chunk exceeds the staging buffers");
+// Phase 2+3, bins 0..3: exclusion test, state update, compaction into
+// W_{r+1}.  kPending: `list` is the pending list P_r (undecided
+// non-candidates only); else it is W_r, and each chunk is first triaged one
+// vertex per lane (Phase 1 candidates need no scan) into `wscan`.
+template <int TPR, int CH, bool kPending>
+__device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __restrict__ list,
+                                            int cnt, WarpSched& ws, unsigned* grab, int* next,
+                                            int4* __restrict__ dst, int32_t* wbuf,
+                                            int32_t* wscan) {
+    static_assert(CH <= kStageMax, "chunk exceeds the staging buffer");
     constexpr int G = 32 / TPR;
     if (cnt <= 0) return;
     const unsigned lane = lane_id();
     const unsigned glane = lane % TPR;
     const unsigned gid = lane / TPR;
     const unsigned gshift = gid * TPR;
-    const ChunkPlan plan = plan_of<G, CH>(cnt);
-    if (global_warp() >= plan.total) return;
-    for (;;) {
-        int k = 0;
-        if (lane == 0) k = (int)atomicAdd(grab, 1u);
-        k = __shfl_sync(0xFFFFFFFFu, k, 0);
-        if (k >= plan.total) break;
+    const LiveWords nbw{a.word};
+    const ChunkPlan plan = plan_of<G, CH>(cnt, ws.nwarps);
+    for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps, grab)) {
         int c0, c1;
         plan.range(k, cnt, c0, c1, G);
-        // triage, one vertex per lane: candidates of Phase 1 are done
-        int nscan = 0;
-        for (int base = c0; base < c1; base += 32) {
-            const int item = base + (int)lane;
-            const int v = item < c1 ? list[item] : -1;
-            const bool scan = v >= 0 && ld_word_l1(a.word + v) < kWordInMin;
-            const unsigned bal = __ballot_sync(0xFFFFFFFFu, scan);
-            if (scan) wscan[nscan + __popc(bal & lanemask_lt())] = v;
-            nscan += __popc(bal);
+        if (!kPending) {
+            // triage: wscan gets the list indices of the undecided rows
+            int nscan = 0;
+            for (int base = c0; base < c1; base += 32) {
+                const int item = base + (int)lane;
+                const bool scan = item < c1 && ld_word_l1(a.word + list[item].x) < kWordInMin;
+                nscan = stage_keep(scan, item, wscan, nscan);
+            }
+            __syncwarp();
+            c0 = 0;
+            c1 = nscan;
         }
-        __syncwarp();
-        // exclusion test of the remaining (undecided) vertices
-        int nkeep = 0;
-        for (int base = 0; base < nscan; base += G) {
-            const int item = base + (int)gid;
-            const bool valid = item < nscan;
-            const int v = valid ? wscan[item] : 0;
-            const int b = valid ? a.rp[v] : 0;
-            const int e = valid ? a.rp[v + 1] : 0;
-            const bool excl = group_scan<TPR, false>(a.col_sel, a.word, b, e, v, 0u, glane, gshift);
-            const bool lead = glane == 0;
-            if (valid && excl && lead) a.word[v] = kWordOut;
-            const bool keep = valid && !excl && lead;
-            const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
-            if (keep) wkeep[nkeep + __popc(bal & lanemask_lt())] = v;
-            nkeep += __popc(bal);
+        // row i of the chunk: list[kPending ? i : wscan[i]]
+        int fill = 0;
+        if constexpr (TPR == 1) {
+            for (int base = c0; base < c1; base += 32 * kRowsPerLane) {
+                int4 rec[kRowsPerLane];
+                int idx[kRowsPerLane];
+                bool valid[kRowsPerLane], excl[kRowsPerLane];
+                const uint32_t unused[kRowsPerLane] = {};
+#pragma unroll
+                for (int i = 0; i < kRowsPerLane; ++i) {
+                    const int item = base + (int)lane + 32 * i;
+                    valid[i] = item < c1;
+                    idx[i] = valid[i] ? (kPending ? item : wscan[item]) : 0;
+                    rec[i] = valid[i] ? list[idx[i]] : make_int4(0, 0, 0, 0);
+                }
+                lane_rows<kRowsPerLane, false>(a.col_sel, nbw, rec, valid, unused, excl);
+#pragma unroll
+                for (int i = 0; i < kRowsPerLane; ++i) {
+                    if (valid[i] && excl[i]) a.word[rec[i].x] = kWordOut;
+                    fill = stage_keep(valid[i] && !excl[i], idx[i], wbuf, fill);
+                }
+            }
+        } else {
+            for (int base = c0; base < c1; base += G) {
+                const int item = base + (int)gid;
+                const bool valid = item < c1;
+                const int idx = valid ? (kPending ? item : wscan[item]) : 0;
+                const int4 rec = valid ? list[idx] : make_int4(0, 0, 0, 0);
+                const int e = valid ? rec.w : 0;
+                const bool excl =
+                    group_scan<TPR, false>(a.col_sel, nbw, rec.y, e, rec.x, 0u, glane, gshift);
+                const bool lead = glane == 0;
+                if (valid && excl && lead) a.word[rec.x] = kWordOut;
+                fill = stage_keep(valid && !excl && lead, idx, wbuf, fill);
+            }
         }
-        __syncwarp();
-        if (nkeep) {
-            int o = 0;
-            if (lane == 0) o = atomicAdd(next, nkeep);
-            o = __shfl_sync(0xFFFFFFFFu, o, 0);
-            for (int i = (int)lane; i < nkeep; i += 32) dst[o + i] = wkeep[i];
-        }
-        __syncwarp();
+        flush_stage(wbuf, fill, list, next, dst);
     }
 }
 
-// Bin 4 (hubs): the whole block scans one row at a time.  kSelect: Phase 1,
-// else Phase 2+3 (survivors appended one by one: hub rows are few).
-template <bool kSelect>
-__device__ __forceinline__ void block_bin(const SolveArgs& a, const int32_t* __restrict__ list,
-                                          int cnt, unsigned* grab, int* next,
-                                          int32_t* __restrict__ dst) {
+// Bin 4 (hubs): the whole block scans one row at a time.  kSelect: Phase 1
+// (kPending: non-candidates appended to the pending list), else Phase 2+3
+// (survivors appended to W_{r+1}); hub rows are few, so entries are appended
+// one by one.
+template <bool kSelect, bool kPending>
+__device__ __forceinline__ void block_bin(const SolveArgs& a, const int4* __restrict__ list, int cnt, unsigned* grab,
+                                          int* next, int4* __restrict__ dst) {
     __shared__ int s_row;
     if ((int)blockIdx.x >= cnt) return;  // no row left for this block
+    int item = (int)blockIdx.x;          // first row: no atomic
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_row = (int)atomicAdd(grab, 1u);
-        __syncthreads();
-        const int item = s_row;
         if (item >= cnt) break;
-        const int v = list[item];
+        const int4 rec = list[item];
+        const int v = rec.x;
         // the word of v does not change during this row's scan in either phase
         const uint32_t wv = ld_word_l1(a.word + v);
-        if (!kSelect && wv >= kWordInMin) continue;  // a candidate: nothing to do
-        const int b = a.rp[v];
-        const int e = (kSelect && a.split) ? b + a.split[v] : a.rp[v + 1];
+        const bool skip = !kSelect && !kPending && wv >= kWordInMin;  // a candidate
+        const int b = rec.y;
+        const int e = skip ? b : kSelect ? rec.z : rec.w;
         bool found = false;
         for (int base = b & ~3; base < e; base += 4 * (int)blockDim.x) {
             const int p0 = base + 4 * (int)threadIdx.x;
@@ -261,29 +404,141 @@ __device__ __forceinline__ void block_bin(const SolveArgs& a, const int32_t* __r
                 break;
             }
         }
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !skip) {
             if (kSelect) {
                 if (!found) a.word[v] = wv | kWordInSet;
+                else if (kPending) dst[atomicAdd(next, 1)] = rec;
             } else if (found) {
                 a.word[v] = kWordOut;
             } else {
-                dst[atomicAdd(next, 1)] = v;
+                dst[atomicAdd(next, 1)] = rec;
             }
         }
+        if (cnt <= (int)gridDim.x) break;  // every row was a first row
+        __syncthreads();
+        if (threadIdx.x == 0) s_row = (int)gridDim.x + (int)atomicAdd(grab, 1u);
+        __syncthreads();
+        item = s_row;
     }
 }
 
+// Phase 1 over the bins of one worklist: hubs first, then the bins of longer
+// rows.  In rounds after the first (`late`), a bin with no more rows than
+// warps gets one warp (or 4 lanes for short rows) per row: latency, not
+// throughput.
+template <bool kPending>
+__device__ __forceinline__ void select_phase(const SolveArgs& a, const int4* src, const int* cnt, bool late,
+                                             WarpSched& ws, unsigned* grab, int* pnext,
+                                             int4* pend, int32_t* wbuf) {
+    const int* off = a.bin_off;
+    const int nw = ws.nwarps;
+    block_bin<true, kPending>(a, src + off[4], cnt[4], &grab[4], &pnext[4],
+                                       pend + off[4]);
+    select_bin<32, kChunk3, kPending>(a, src + off[3], cnt[3], ws, &grab[3],
+                                               &pnext[3], pend + off[3], wbuf);
+    if (late && cnt[2] <= nw)
+        select_bin<32, kChunk3, kPending>(a, src + off[2], cnt[2], ws, &grab[2],
+                                                   &pnext[2], pend + off[2], wbuf);
+    else
+        select_bin<16, kChunk2, kPending>(a, src + off[2], cnt[2], ws, &grab[2],
+                                                   &pnext[2], pend + off[2], wbuf);
+    if (late && cnt[1] <= nw)
+        select_bin<32, kChunk3, kPending>(a, src + off[1], cnt[1], ws, &grab[1],
+                                                   &pnext[1], pend + off[1], wbuf);
+    else
+        select_bin<4, kChunk1, kPending>(a, src + off[1], cnt[1], ws, &grab[1],
+                                                  &pnext[1], pend + off[1], wbuf);
+    if (late && cnt[0] <= nw)
+        select_bin<4, kChunk1, kPending>(a, src + off[0], cnt[0], ws, &grab[0],
+                                                  &pnext[0], pend + off[0], wbuf);
+    else
+        select_bin<1, kChunk0, kPending>(a, src + off[0], cnt[0], ws, &grab[0],
+                                                  &pnext[0], pend + off[0], wbuf);
+}
+
+// Phase 2+3 over the bins of `list` (W_r, or P_r when kPending).
+template <bool kPending>
+__device__ __forceinline__ void exclude_phase(const SolveArgs& a, const int4* list,
+                                              const int* cnt, bool late, WarpSched& ws,
+                                              unsigned* grab, int* next, int4* dst,
+                                              int32_t* wbuf, int32_t* wscan) {
+    const int* off = a.bin_off;
+    const int nw = ws.nwarps;
+    block_bin<false, kPending>(a, list + off[4], cnt[4], &grab[4], &next[4],
+                                      dst + off[4]);
+    exclude_bin<32, kChunk3, kPending>(a, list + off[3], cnt[3], ws, &grab[3], &next[3],
+                                       dst + off[3], wbuf, wscan);
+    if (late && cnt[2] <= nw)
+        exclude_bin<32, kChunk3, kPending>(a, list + off[2], cnt[2], ws, &grab[2], &next[2],
+                                           dst + off[2], wbuf, wscan);
+    else
+        exclude_bin<16, kChunk2, kPending>(a, list + off[2], cnt[2], ws, &grab[2], &next[2],
+                                           dst + off[2], wbuf, wscan);
+    if (late && cnt[1] <= nw)
+        exclude_bin<32, kChunk3, kPending>(a, list + off[1], cnt[1], ws, &grab[1], &next[1],
+                                           dst + off[1], wbuf, wscan);
+    else
+        exclude_bin<4, kChunk1, kPending>(a, list + off[1], cnt[1], ws, &grab[1], &next[1],
+                                          dst + off[1], wbuf, wscan);
+    if (late && cnt[0] <= nw)
+        exclude_bin<4, kChunk1, kPending>(a, list + off[0], cnt[0], ws, &grab[0], &next[0],
+                                          dst + off[0], wbuf, wscan);
+    else
+        exclude_bin<1, kChunk0, kPending>(a, list + off[0], cnt[0], ws, &grab[0], &next[0],
+                                          dst + off[0], wbuf, wscan);
+}
+
+// Writes out[v] = [v in the MIS] and adds the MIS size to ctl->mis_size.
+__device__ __forceinline__ void output_pass(const SolveArgs& a) {
+    const int32_t n = a.n;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    unsigned in_cnt = 0;
+    if (a.seg.count == 0 && ((uintptr_t)a.out & 3) == 0) {
+        // four vertices per thread: 16-byte word loads, 4-byte result stores
+        for (long long v = 4 * tid; v < n; v += 4 * nthreads) {
+            const uint4 q = *reinterpret_cast<const uint4*>(a.word + v);
+            const uint32_t b0 = q.x >= kWordInMin, b1 = q.y >= kWordInMin;
+            const uint32_t b2 = q.z >= kWordInMin, b3 = q.w >= kWordInMin;
+            if (v + 4 <= n) {
+                *reinterpret_cast<uint32_t*>(a.out + v) = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+                in_cnt += b0 + b1 + b2 + b3;
+            } else {
+                const uint32_t bb[4] = {b0, b1, b2, b3};
+                for (int k = 0; k < 4 && v + k < n; ++k) {
+                    a.out[v + k] = (uint8_t)bb[k];
+                    in_cnt += bb[k];
+                }
+            }
+        }
+    } else {
+        for (long long v = tid; v < n; v += nthreads) {
+            const bool in = ld_word(a.word + v) >= kWordInMin;
+            in_cnt += in;
+            if (a.seg.count == 0) {
+                a.out[v] = in;
+            } else {
+                const int g = a.seg.blk_seg[v >> 4];
+                const int local = (int)v - a.seg.voff[g];
+                if (local < a.seg.nv[g]) a.out[a.seg.roff[g] + local] = in;
+            }
+        }
+    }
+    for (int o = 16; o; o >>= 1) in_cnt += __shfl_xor_sync(0xFFFFFFFFu, in_cnt, o);
+    if (lane_id() == 0 && in_cnt) atomicAdd(&a.ctl->mis_size, (unsigned long long)in_cnt);
+}
+
+template <bool kPending>
 __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     csr_solve_kernel(const SolveArgs a) {
-    __shared__ int32_t s_scan[kWarps][kStageMax];
-    __shared__ int32_t s_keep[kWarps][kStageMax];
-    const unsigned lane = lane_id();
+    __shared__ int32_t s_stage[kWarps][kStageMax];
+    __shared__ int32_t s_scan[kPending ? 1 : kWarps][kPending ? 1 : kStageMax];
+    __shared__ int s_cnt[kBins];
     const unsigned nblocks = gridDim.x;
     Ctl* ctl = a.ctl;
     PhaseTimes* times = a.times;
-    const int32_t n = a.n;
-    int32_t* wscan = s_scan[threadIdx.x / 32];
-    int32_t* wkeep = s_keep[threadIdx.x / 32];
+    int32_t* wbuf = s_stage[threadIdx.x / 32];
+    int32_t* wscan = kPending ? nullptr : &s_scan[kPending ? 0 : threadIdx.x / 32][0];
     if (times && blockIdx.x == 0 && threadIdx.x == 0) times->t[0] = global_ns();
 
     // ---- init: Eq. 1 priorities
@@ -301,90 +556,63 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     }
     // isolated vertices were decided at init but belong to round 0's alive set
     const int iso = a.n_isolated;
-    const int* off = a.bin_off;
-    // in rounds after the first, a bin with no more rows than warps gets one
-    // warp (or 4 lanes for short rows) per row: latency, not throughput
-    const int nwarps_all = (int)(nblocks * (blockDim.x / 32));
+    WarpSched ws;
+    ws.gw = (int)(blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32);
+    ws.nwarps = (int)(nblocks * (blockDim.x / 32));
+    ws.base = 0;
     for (int r = 0; total > 0 || (r == 0 && iso > 0); ++r) {
-        const int32_t* src = (r == 0) ? a.order0 : ((r & 1) ? a.wl1 : a.wl0);
-        int32_t* dst = ((r + 1) & 1) ? a.wl1 : a.wl0;
+        const int4* src = (r == 0) ? a.order0 : ((r & 1) ? a.wl1 : a.wl0);
+        int4* dst = ((r + 1) & 1) ? a.wl1 : a.wl0;
         int* next = ctl->bcnt[(r + 1) & 3];
-
-        // ---- Phase 1: selection test.  Round 0 scans most rows only up to
-        // their first few arcs (a blocker turns up early); later rounds keep
-        // the rows that need long scans, so a small bin gets wider groups.
-        unsigned* grab = ctl->grab[(2 * r) & 3];
-        block_bin<true>(a, src + off[4], cnt[4], &grab[4], nullptr, nullptr);
-        if (r == 0) {
-            select_bin<32, kChunk3>(a, src + off[3], cnt[3], &grab[3]);
-            select_bin<16, kChunk2>(a, src + off[2], cnt[2], &grab[2]);
-            select_bin<4, kChunk1>(a, src + off[1], cnt[1], &grab[1]);
-            select_bin<1, kChunk0>(a, src + off[0], cnt[0], &grab[0]);
-        } else {
-            select_bin<32, kChunk3>(a, src + off[3], cnt[3], &grab[3]);
-            if (cnt[2] <= nwarps_all) select_bin<32, kChunk3>(a, src + off[2], cnt[2], &grab[2]);
-            else select_bin<16, kChunk2>(a, src + off[2], cnt[2], &grab[2]);
-            if (cnt[1] <= nwarps_all) select_bin<32, kChunk3>(a, src + off[1], cnt[1], &grab[1]);
-            else select_bin<4, kChunk1>(a, src + off[1], cnt[1], &grab[1]);
-            if (cnt[0] <= nwarps_all) select_bin<4, kChunk1>(a, src + off[0], cnt[0], &grab[0]);
-            else select_bin<1, kChunk0>(a, src + off[0], cnt[0], &grab[0]);
-        }
+        int* pnext = ctl->pcnt[r & 3];
         const int rr = r;
-        if (!grid_barrier(ctl, nblocks, a.spin_cap, [ctl, times, rr]() {
-                if (times && rr < kStatRounds) times->t[2 + rr] = global_ns();
-                for (int j = 0; j < kBins; ++j) ctl->grab[(2 * rr + 2) & 3][j] = 0;
-            }))
+
+        // ---- Phase 1: selection test
+        select_phase<kPending>(a, src, cnt, r > 0, ws, ctl->grab[(2 * r) & 3], pnext, a.wlp,
+                               wbuf);
+        if (!grid_barrier(
+                ctl, nblocks, a.spin_cap,
+                [ctl, times, rr]() {
+                    if (times && rr < kStatRounds) times->t[2 + rr] = global_ns();
+                    for (int j = 0; j < kBins; ++j) ctl->grab[(2 * rr + 2) & 3][j] = 0;
+                },
+                [pnext]() {
+                    if (kPending)
+                        for (int j = 0; j < kBins; ++j) s_cnt[j] = __ldcg(pnext + j);
+                }))
             return;
 
         // ---- Phase 2+3: exclusion test, state update, compaction
-        grab = ctl->grab[(2 * r + 1) & 3];
-        block_bin<false>(a, src + off[4], cnt[4], &grab[4], &next[4], dst + off[4]);
-        if (r == 0) {
-            exclude_bin<32, kChunk3>(a, src + off[3], cnt[3], &grab[3], &next[3], dst + off[3],
-                                     wscan, wkeep);
-            exclude_bin<16, kChunk2>(a, src + off[2], cnt[2], &grab[2], &next[2], dst + off[2],
-                                     wscan, wkeep);
-            exclude_bin<4, kChunk1>(a, src + off[1], cnt[1], &grab[1], &next[1], dst + off[1],
-                                    wscan, wkeep);
-            exclude_bin<1, kChunk0>(a, src + off[0], cnt[0], &grab[0], &next[0], dst + off[0],
-                                    wscan, wkeep);
+        if (kPending) {
+            int pc[kBins];
+            for (int j = 0; j < kBins; ++j) pc[j] = s_cnt[j];
+            exclude_phase<true>(a, a.wlp, pc, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next, dst,
+                                wbuf, wscan);
         } else {
-            exclude_bin<32, kChunk3>(a, src + off[3], cnt[3], &grab[3], &next[3], dst + off[3],
-                                     wscan, wkeep);
-            if (cnt[2] <= nwarps_all)
-                exclude_bin<32, kChunk3>(a, src + off[2], cnt[2], &grab[2], &next[2],
-                                         dst + off[2], wscan, wkeep);
-            else
-                exclude_bin<16, kChunk2>(a, src + off[2], cnt[2], &grab[2], &next[2],
-                                         dst + off[2], wscan, wkeep);
-            if (cnt[1] <= nwarps_all)
-                exclude_bin<32, kChunk3>(a, src + off[1], cnt[1], &grab[1], &next[1],
-                                         dst + off[1], wscan, wkeep);
-            else
-                exclude_bin<4, kChunk1>(a, src + off[1], cnt[1], &grab[1], &next[1],
-                                        dst + off[1], wscan, wkeep);
-            if (cnt[0] <= nwarps_all)
-                exclude_bin<4, kChunk1>(a, src + off[0], cnt[0], &grab[0], &next[0],
-                                        dst + off[0], wscan, wkeep);
-            else
-                exclude_bin<1, kChunk0>(a, src + off[0], cnt[0], &grab[0], &next[0],
-                                        dst + off[0], wscan, wkeep);
+            exclude_phase<false>(a, src, cnt, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next, dst,
+                                 wbuf, wscan);
         }
         const int cur = total + (r == 0 ? iso : 0);
-        if (!grid_barrier(ctl, nblocks, a.spin_cap, [ctl, times, rr, cur]() {
-                if (times && rr < kStatRounds) times->t[2 + kStatRounds + rr] = global_ns();
-                if (rr < kStatRounds) ctl->alive[rr] = cur;
-                ctl->alive_sum += (unsigned long long)cur;
-                ctl->rounds = rr + 1;
-                for (int j = 0; j < kBins; ++j) {
-                    ctl->grab[(2 * rr + 3) & 3][j] = 0;
-                    ctl->bcnt[(rr + 2) & 3][j] = 0;
-                }
-            }))
+        if (!grid_barrier(
+                ctl, nblocks, a.spin_cap,
+                [ctl, times, rr, cur]() {
+                    if (times && rr < kStatRounds) times->t[2 + kStatRounds + rr] = global_ns();
+                    if (rr < kStatRounds) ctl->alive[rr] = cur;
+                    ctl->alive_sum += (unsigned long long)cur;
+                    ctl->rounds = rr + 1;
+                    for (int j = 0; j < kBins; ++j) {
+                        ctl->grab[(2 * rr + 3) & 3][j] = 0;
+                        ctl->bcnt[(rr + 2) & 3][j] = 0;
+                        ctl->pcnt[(rr + 2) & 3][j] = 0;
+                    }
+                },
+                [next]() {
+                    for (int j = 0; j < kBins; ++j) s_cnt[j] = __ldcg(next + j);
+                }))
             return;
         total = 0;
         for (int j = 0; j < kBins; ++j) {
-            cnt[j] = ld_acquire_int(&next[j]);
+            cnt[j] = s_cnt[j];
             total += cnt[j];
         }
         if (total > 0 && r + 1 >= a.max_rounds) {
@@ -394,74 +622,46 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     }
 
     // ---- output
-    if (a.out) {
-        const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-        const long long nthreads = (long long)nblocks * blockDim.x;
-        unsigned in_cnt = 0;
-        if (a.seg.count == 0 && ((uintptr_t)a.out & 3) == 0) {
-            // four vertices per thread: 16-byte word loads, 4-byte result stores
-            for (long long v = 4 * tid; v < n; v += 4 * nthreads) {
-                const uint4 q = *reinterpret_cast<const uint4*>(a.word + v);
-                const uint32_t b0 = q.x >= kWordInMin, b1 = q.y >= kWordInMin;
-                const uint32_t b2 = q.z >= kWordInMin, b3 = q.w >= kWordInMin;
-                if (v + 4 <= n) {
-                    *reinterpret_cast<uint32_t*>(a.out + v) = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
-                    in_cnt += b0 + b1 + b2 + b3;
-                } else {
-                    const uint32_t bb[4] = {b0, b1, b2, b3};
-                    for (int k = 0; k < 4 && v + k < n; ++k) {
-                        a.out[v + k] = (uint8_t)bb[k];
-                        in_cnt += bb[k];
-                    }
-                }
-            }
-        } else {
-            for (long long v = tid; v < n; v += nthreads) {
-                const bool in = ld_word(a.word + v) >= kWordInMin;
-                in_cnt += in;
-                if (a.seg.count == 0) {
-                    a.out[v] = in;
-                } else {
-                    const int g = a.seg.blk_seg[v >> 4];
-                    const int local = (int)v - a.seg.voff[g];
-                    if (local < a.seg.nv[g]) a.out[a.seg.roff[g] + local] = in;
-                }
-            }
-        }
-        for (int o = 16; o; o >>= 1) in_cnt += __shfl_xor_sync(0xFFFFFFFFu, in_cnt, o);
-        if (lane == 0 && in_cnt) atomicAdd(&ctl->mis_size, (unsigned long long)in_cnt);
-    }
+    if (a.out) output_pass(a);
 }
 
 cudaError_t launch_csr_solve(const SolveArgs& a, int grid, cudaStream_t s) {
     void* args[] = {const_cast<SolveArgs*>(&a)};
-    return cudaLaunchCooperativeKernel((const void*)csr_solve_kernel, dim3(grid),
-                                       dim3(kCsrBlock), args, 0, s);
+    const void* fn = a.pending ? (const void*)csr_solve_kernel<true>
+                               : (const void*)csr_solve_kernel<false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCsrBlock), args, 0, s);
 }
 
 cudaError_t launch_csr_solve_single(const SolveArgs& a, cudaStream_t s) {
-    csr_solve_kernel<<<1, kCsrBlock, 0, s>>>(a);
+    if (a.pending) csr_solve_kernel<true><<<1, kCsrBlock, 0, s>>>(a);
+    else csr_solve_kernel<false><<<1, kCsrBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 int csr_block_size() { return kCsrBlock; }
 
 int csr_max_coresident_blocks(int device) {
-    int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)csr_solve_kernel,
-                                                      kCsrBlock, 0) != cudaSuccess)
+    // both forms: the grid must fit whichever one a solve launches
+    int per_sm = 0, per_sm_p = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, (const void*)csr_solve_kernel<false>, kCsrBlock, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm_p, (const void*)csr_solve_kernel<true>, kCsrBlock, 0) != cudaSuccess)
         return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return 0;
-    return per_sm * sms;
+    return std::min(per_sm, per_sm_p) * sms;
 }
 
 // ---------------------------------------------------------------- degree bins
 //
-// order0 = the round-0 list: every real vertex (batch padding excluded),
-// grouped by bin, ascending id inside a bin.  Two kernels: per-block bin
-// counts, then (after the host turns the counts into offsets) a stable
-// scatter.  Blocks own contiguous vertex ranges.
+// order0 = the round-0 records: every real vertex of degree >= 1 (batch
+// padding excluded), grouped by bin, ascending id inside a bin.  Two kernels:
+// per-block class counts (the five bins, then isolated vertices), then (after
+// the host turns the counts into offsets) a stable scatter.  Blocks own
+// contiguous vertex ranges.
+
+constexpr int kClasses = kBins + 1;  // bins 0..4, then isolated
 
 struct BinThr {
     int32_t t[kBins - 1];
@@ -480,62 +680,61 @@ __device__ __forceinline__ bool is_real(const SegTable& seg, long long v) {
     return (int)v - seg.voff[g] < seg.nv[g];
 }
 
-// A vertex of the round-0 list: real and not isolated.
-__device__ __forceinline__ bool listed(const SegTable& seg, const int32_t* rp, long long v) {
-    return is_real(seg, v) && rp[v + 1] > rp[v];
+// Class of vertex v: its bin, kBins when isolated, -1 for batch padding.
+__device__ __forceinline__ int class_of(const SegTable& seg, const int32_t* rp, long long v,
+                                        const BinThr& thr) {
+    if (!is_real(seg, v)) return -1;
+    const int deg = rp[v + 1] - rp[v];
+    return deg == 0 ? kBins : bin_of(deg, thr);
 }
 
 __global__ void bin_count_kernel(const int32_t* __restrict__ rp, int32_t n, const SegTable seg,
-                                 const BinThr thr, int32_t* __restrict__ blkcnt,
-                                 int32_t* __restrict__ n_iso) {
-    __shared__ int c[kBins];
-    __shared__ int iso;
-    if (threadIdx.x < kBins) c[threadIdx.x] = 0;
-    if (threadIdx.x == 0) iso = 0;
+                                 const BinThr thr, int32_t* __restrict__ blkcnt) {
+    __shared__ int c[kClasses];
+    if (threadIdx.x < kClasses) c[threadIdx.x] = 0;
     __syncthreads();
     const long long v0 = (long long)n * blockIdx.x / gridDim.x;
     const long long v1 = (long long)n * (blockIdx.x + 1) / gridDim.x;
     for (long long v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-        if (!is_real(seg, v)) continue;
-        const int deg = rp[v + 1] - rp[v];
-        if (deg == 0) atomicAdd(&iso, 1);
-        else atomicAdd(&c[bin_of(deg, thr)], 1);
+        const int j = class_of(seg, rp, v, thr);
+        if (j >= 0) atomicAdd(&c[j], 1);
     }
     __syncthreads();
-    if (threadIdx.x < kBins) blkcnt[blockIdx.x * kBins + threadIdx.x] = c[threadIdx.x];
-    if (threadIdx.x == 0 && iso) atomicAdd(n_iso, iso);
+    if (threadIdx.x < kClasses) blkcnt[blockIdx.x * kClasses + threadIdx.x] = c[threadIdx.x];
 }
 
 // blockDim.x must be 256
-__global__ void bin_scatter_kernel(const int32_t* __restrict__ rp, int32_t n, const SegTable seg,
-                                   const BinThr thr, const int32_t* __restrict__ blkoff,
-                                   int32_t* __restrict__ order0) {
-    __shared__ int wsum[8][kBins];
-    __shared__ int run[kBins];
+__global__ void bin_scatter_kernel(const int32_t* __restrict__ rp,
+                                   const int32_t* __restrict__ split, int32_t n,
+                                   const SegTable seg, const BinThr thr,
+                                   const int32_t* __restrict__ blkoff,
+                                   int4* __restrict__ order0) {
+    __shared__ int wsum[8][kClasses];
+    __shared__ int run[kClasses];
     const unsigned lane = lane_id();
     const int w = threadIdx.x / 32;
-    if (threadIdx.x < kBins) run[threadIdx.x] = blkoff[blockIdx.x * kBins + threadIdx.x];
+    if (threadIdx.x < kClasses) run[threadIdx.x] = blkoff[blockIdx.x * kClasses + threadIdx.x];
     __syncthreads();
     const long long v0 = (long long)n * blockIdx.x / gridDim.x;
     const long long v1 = (long long)n * (blockIdx.x + 1) / gridDim.x;
     for (long long c0 = v0; c0 < v1; c0 += blockDim.x) {
         const long long v = c0 + threadIdx.x;
-        int j = -1;
-        if (v < v1 && listed(seg, rp, v)) j = bin_of(rp[v + 1] - rp[v], thr);
+        const int j = v < v1 ? class_of(seg, rp, v, thr) : -1;
         int rank = 0;
-        for (int b = 0; b < kBins; ++b) {
+        for (int b = 0; b < kClasses; ++b) {
             const unsigned m = __ballot_sync(0xFFFFFFFFu, j == b);
             if (j == b) rank = __popc(m & lanemask_lt());
             if (lane == 0) wsum[w][b] = __popc(m);
         }
         __syncthreads();
-        if (j >= 0) {
+        if (j >= 0 && j < kBins) {
             int off = run[j];
             for (int x = 0; x < w; ++x) off += wsum[x][j];
-            order0[off + rank] = (int32_t)v;
+            const int b = rp[v], e = rp[v + 1];
+            order0[off + rank] = make_int4((int)v, b, split ? b + split[v] : e, e);
         }
         __syncthreads();
-        if (threadIdx.x < kBins) {
+        if (threadIdx.x < kClasses) {
             int t = 0;
             for (int x = 0; x < 8; ++x) t += wsum[x][threadIdx.x];
             run[threadIdx.x] += t;
@@ -544,9 +743,9 @@ __global__ void bin_scatter_kernel(const int32_t* __restrict__ rp, int32_t n, co
     }
 }
 
-cudaError_t build_bins(const int32_t* rp, int32_t n, const SegTable& seg, const int32_t thr[4],
-                       int32_t* order0, int32_t bin_off[6], int32_t* n_isolated,
-                       cudaStream_t s) {
+cudaError_t build_bins(const int32_t* rp, const int32_t* split, int32_t n, const SegTable& seg,
+                       const int32_t thr[4], int4* order0, int32_t bin_off[6],
+                       int32_t* n_isolated, cudaStream_t s) {
     for (int j = 0; j <= kBins; ++j) bin_off[j] = 0;
     *n_isolated = 0;
     if (n == 0) return cudaSuccess;
@@ -554,44 +753,39 @@ cudaError_t build_bins(const int32_t* rp, int32_t n, const SegTable& seg, const 
     BinThr t;
     for (int k = 0; k < kBins - 1; ++k) t.t[k] = thr[k];
     int32_t* d_cnt = nullptr;
-    cudaError_t e = dev_alloc((void**)&d_cnt, sizeof(int32_t) * (blocks * kBins + 1));
+    cudaError_t e = dev_alloc((void**)&d_cnt, sizeof(int32_t) * blocks * kClasses);
     if (e != cudaSuccess) return e;
-    std::vector<int32_t> h((size_t)blocks * kBins);
-    int32_t iso = 0;
-    e = cudaMemsetAsync(d_cnt + blocks * kBins, 0, sizeof(int32_t), s);
-    if (e == cudaSuccess) {
-        bin_count_kernel<<<blocks, 256, 0, s>>>(rp, n, seg, t, d_cnt, d_cnt + blocks * kBins);
-        e = cudaGetLastError();
-    }
+    std::vector<int32_t> h((size_t)blocks * kClasses);
+    bin_count_kernel<<<blocks, 256, 0, s>>>(rp, n, seg, t, d_cnt);
+    e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h.data(), d_cnt, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&iso, d_cnt + blocks * kBins, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                            s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    *n_isolated = iso;
     if (e == cudaSuccess) {
-        int64_t tot[kBins] = {};
+        int64_t tot[kClasses] = {};
         for (int b = 0; b < blocks; ++b)
-            for (int j = 0; j < kBins; ++j) tot[j] += h[(size_t)b * kBins + j];
+            for (int j = 0; j < kClasses; ++j) tot[j] += h[(size_t)b * kClasses + j];
         int64_t acc = 0;
         for (int j = 0; j < kBins; ++j) {
             bin_off[j] = (int32_t)acc;
             acc += tot[j];
         }
         bin_off[kBins] = (int32_t)acc;
-        int64_t run[kBins];
+        *n_isolated = (int32_t)tot[kBins];
+        // running offsets per block into order0 (isolated vertices: not listed)
+        int64_t run[kClasses];
         for (int j = 0; j < kBins; ++j) run[j] = bin_off[j];
+        run[kBins] = 0;
         for (int b = 0; b < blocks; ++b)
-            for (int j = 0; j < kBins; ++j) {
-                const int32_t c = h[(size_t)b * kBins + j];
-                h[(size_t)b * kBins + j] = (int32_t)run[j];
+            for (int j = 0; j < kClasses; ++j) {
+                const int32_t c = h[(size_t)b * kClasses + j];
+                h[(size_t)b * kClasses + j] = (int32_t)run[j];
                 run[j] += c;
             }
         e = cudaMemcpyAsync(d_cnt, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice, s);
     }
     if (e == cudaSuccess) {
-        bin_scatter_kernel<<<blocks, 256, 0, s>>>(rp, n, seg, t, d_cnt, order0);
+        bin_scatter_kernel<<<blocks, 256, 0, s>>>(rp, split, n, seg, t, d_cnt, order0);
         e = cudaGetLastError();
     }
     const cudaError_t se = cudaStreamSynchronize(s);  // also on error: nothing may still run

@@ -512,6 +512,7 @@ template <int T, int S, bool kTC>
 __global__ void __launch_bounds__(kTileBlock, 2) tile_solve_kernel(const SolveArgs a) {
     __shared__ int32_t s_keep[kTileWarps][kTileChunk];
     __shared__ unsigned s_alive;
+    __shared__ int s_count;  // next worklist size, loaded once per block
     const unsigned lane = lane_id();
     const unsigned nblocks = gridDim.x;
     Ctl* ctl = a.ctl;
@@ -575,9 +576,10 @@ __global__ void __launch_bounds__(kTileBlock, 2) tile_solve_kernel(const SolveAr
                 ctl->grab[(2 * rr + 3) & 3][0] = 0;
                 ctl->bcnt[(rr + 2) & 3][0] = 0;
                 ctl->alive_acc[(rr + 2) & 3] = 0;
-            }))
+            },
+            [next]() { s_count = __ldcg(next); }))
             return;
-        count = ld_acquire_int(next);
+        count = s_count;
         if (count > 0 && r + 1 >= a.max_rounds) {
             if (threadIdx.x == 0) atomicCAS(&ctl->err, 0, kErrInternal);
             return;

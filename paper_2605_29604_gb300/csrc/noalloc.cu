@@ -31,10 +31,10 @@ namespace {
 constexpr int32_t kNoAllocMaxVertices = 262144;  // 2^18 vertices
 constexpr int kNoAllocTpr = 8;
 constexpr int kNoAllocBlock = 512;
-constexpr size_t kCtlBytes = 512;
+constexpr size_t kCtlBytes = 1024;
 constexpr size_t kVecBytes = sizeof(int32_t) * (size_t)kNoAllocMaxVertices;
 // layout: control block, words, worklist 0, worklist 1
-constexpr size_t kScratchBytes = kCtlBytes + 3 * kVecBytes;  // 3 MiB + 512 B
+constexpr size_t kScratchBytes = kCtlBytes + 3 * kVecBytes;  // 3 MiB + 1 KiB
 static_assert(sizeof(Ctl) <= kCtlBytes, "control block does not fit");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];

@@ -56,7 +56,7 @@ class mis_options(ctypes.Structure):
 class mis_stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("threads_per_row", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("tile", ctypes.c_int32), ("pad0", ctypes.c_int32), ("ntiles", ctypes.c_int64),
+                ("tile", ctypes.c_int32), ("csr_pending", ctypes.c_int32), ("ntiles", ctypes.c_int64),
                 ("alive_sum", ctypes.c_int64), ("mis_size", ctypes.c_int64),
                 ("alive_per_round", ctypes.c_int64 * 64), ("init_ns", ctypes.c_int64),
                 ("select_ns", ctypes.c_int64 * 64), ("exclude_ns", ctypes.c_int64 * 64)]
@@ -66,6 +66,7 @@ class mis_tuning(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("param", ctypes.c_int32),
                 ("bounds", ctypes.c_int32 * 4), ("grid", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("csr_pending", ctypes.c_int32),
                 ("arcs_per_tile", ctypes.c_double)]
 
 
@@ -118,6 +119,8 @@ def lib():
         L.mis_tiles_ex.restype = ctypes.c_int
         L.mis_set_csr_bins.argtypes = [P, P]
         L.mis_set_csr_bins.restype = ctypes.c_int
+        L.mis_set_csr_pending.argtypes = [P, i32]
+        L.mis_set_csr_pending.restype = ctypes.c_int
         L.mis_destroy.argtypes = [P]
         L.mis_destroy.restype = None
         L.mis_submit.argtypes = [P, u64, P, ctypes.POINTER(i64)]
@@ -148,7 +151,7 @@ def lib():
 EXPORTED = [
     "mis_options_init", "mis_create", "mis_create_ex", "mis_create_batch", "mis_graph_count",
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
-    "mis_set_path", "mis_set_csr_bins", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
+    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
     "mis_solve_noalloc",
 ]
@@ -267,6 +270,10 @@ def mis_set_path(h, path, threads_per_row=0):
 def mis_set_csr_bins(h, bounds):
     b = np.ascontiguousarray(np.asarray(bounds, dtype=np.int32))
     return _check(lib().mis_set_csr_bins(h, _ptr(b)))
+
+
+def mis_set_csr_pending(h, pending):
+    return _check(lib().mis_set_csr_pending(h, int(pending)))
 
 
 def mis_autotune(h, reps=3):

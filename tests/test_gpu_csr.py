@@ -81,6 +81,36 @@ def test_csr_solve_bit_exact(name, tpr):
         native.mis_destroy(h)
 
 
+@pytest.mark.parametrize("name", sorted(FAMILIES))
+@pytest.mark.parametrize("tpr", [0, 1, 4, 32, 512])
+def test_csr_pending_list_bit_exact(name, tpr):
+    """Phase 2 over Phase 1's pending list instead of a triage of W_r."""
+    g = graph(name)
+    h = create(g)
+    try:
+        native.mis_set_csr_pending(h, 1)
+        for seed in (1, 7):
+            got, st = gpu_solve(h, [seed], native.MIS_PATH_CSR, tpr)
+            assert st.csr_pending == 1
+            assert_same(g, seed, got, st)
+        native.mis_set_csr_pending(h, 0)
+        got, st = gpu_solve(h, [9], native.MIS_PATH_CSR, tpr)
+        assert st.csr_pending == 0
+        assert_same(g, 9, got, st)
+    finally:
+        native.mis_destroy(h)
+
+
+def test_csr_pending_rejects_bad_mode():
+    h = create(graph("path"))
+    try:
+        for bad in (-1, 2, 7):
+            with pytest.raises(RuntimeError):
+                native.mis_set_csr_pending(h, bad)
+    finally:
+        native.mis_destroy(h)
+
+
 @pytest.mark.parametrize("bounds", [(2, 5, 9, 20), (-1, 3, 3, 3), (0, 0, 100000, 100000),
                                     (1, 2, 3, 4), (-1, -1, -1, 2)])
 def test_csr_custom_bins(bounds):
@@ -102,9 +132,11 @@ def test_row_orderings_bit_exact(name, order_rows):
     g = graph(name)
     h = create(g, order_rows=order_rows)
     try:
-        for tpr in (0, 1):
-            got, st = gpu_solve(h, [3], native.MIS_PATH_CSR, tpr)
-            assert_same(g, 3, got, st)
+        for pending in (0, 1):
+            native.mis_set_csr_pending(h, pending)
+            for tpr in (0, 1):
+                got, st = gpu_solve(h, [3], native.MIS_PATH_CSR, tpr)
+                assert_same(g, 3, got, st)
     finally:
         native.mis_destroy(h)
 
@@ -216,14 +248,16 @@ def test_batch_union_equals_standalone(count):
     try:
         seeds = np.arange(1000, 1000 + count, dtype=np.uint64)
         keys = gpu_keys(h, seeds)
-        got, st = gpu_solve(h, seeds)
-        off = 0
-        for g, s in zip(parts, seeds):
-            n = g[0]
-            assert np.array_equal(keys[off:off + n], oracle.keys(n, g[1], int(s)))
-            want = oracle_solve(g, int(s))
-            assert np.array_equal(got[off:off + n], want.status)
-            off += n
-        assert off == len(got)
+        for pending in (0, 1):
+            native.mis_set_csr_pending(h, pending)
+            got, st = gpu_solve(h, seeds)
+            off = 0
+            for g, s in zip(parts, seeds):
+                n = g[0]
+                assert np.array_equal(keys[off:off + n], oracle.keys(n, g[1], int(s)))
+                want = oracle_solve(g, int(s))
+                assert np.array_equal(got[off:off + n], want.status)
+                off += n
+            assert off == len(got)
     finally:
         native.mis_destroy(h)
