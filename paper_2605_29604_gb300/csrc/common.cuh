@@ -40,8 +40,7 @@ constexpr int kBins = 5;  // degree bins of the CSR round kernel
 
 // Control block of one solve in device memory; zeroed before every launch.
 struct Ctl {
-    unsigned bar_count;   // grid barrier: arrivals
-    unsigned bar_gen;     // grid barrier: generation
+    unsigned long long bar_arrivals;  // grid barrier: block arrivals in this launch
     int err;              // first error (0 = none)
     int rounds;           // rounds completed
     int cnt[4];           // worklist sizes, ring indexed by round & 3
@@ -106,9 +105,9 @@ __device__ __forceinline__ uint32_t ld_word(const uint32_t* p) { return __ldcg(p
 // notes of the CSR kernel).
 __device__ __forceinline__ uint32_t ld_word_l1(const uint32_t* p) { return *p; }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -118,63 +117,74 @@ __device__ __forceinline__ int ld_acquire_int(const int* p) {
     return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 // ---------------------------------------------------------------- grid barrier
 //
 // Software barrier over all blocks of a cooperative launch (co-residency is
-// guaranteed by the launch).  Every wait is bounded: after `spin_cap` polls
-// the block records kErrTimedOut and leaves; a block that sees an error while
-// waiting leaves too, so a failed barrier never hangs the device.  The last
-// block to arrive may run `leader` (a functor called by one thread) before it
-// releases the others.  Returns false when the launch must stop.
-template <class Leader>
-__device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, long long spin_cap,
-                                             Leader leader);
+// guaranteed by the launch).  Ctl::bar_arrivals counts block arrivals over the
+// whole launch and is never reset: the k-th barrier of a launch is complete
+// once it reaches k * nblocks, so a block arrives with one atomic and waits by
+// polling that same counter (no generation flag, no reset, no release step).
+// The count of barriers a block has passed sits in shared memory (thread 0
+// alone uses it); a kernel calls grid_barrier_start() once before its first
+// barrier.
+//
+// The last block to arrive runs `leader` (one thread) but nobody waits for
+// it, so a leader may only write what other blocks read after the NEXT
+// barrier or after the launch (the round kernels' ring-indexed counters are
+// laid out for that).  After the wait, thread 0 of every block runs `after`
+// (e.g. to copy counters written before the barrier into shared memory, one
+// load per block instead of one per warp).
+//
+// Every wait is bounded: after `spin_cap` polls the block records
+// kErrTimedOut and leaves; a block that sees an error while waiting leaves
+// too, so a failed barrier never hangs the device.  Returns false when the
+// launch must stop.
+__shared__ unsigned s_bar_epoch;
 
-struct NoLeader {
-    __device__ void operator()() const {}
-};
+__device__ __forceinline__ void grid_barrier_start() {
+    if (threadIdx.x == 0) s_bar_epoch = 0;
+}
 
-// As above; after the wait, thread 0 of every block also runs `after` (e.g.
-// to copy counters written before the barrier into shared memory, one load
-// per block instead of one per warp) before the block's threads go on.
 template <class Leader, class After>
 __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, long long spin_cap,
                                              Leader leader, After after) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
+        const unsigned epoch = ++s_bar_epoch;
+        const unsigned long long target = (unsigned long long)epoch * nblocks;
         int ok = 1;
-        const unsigned gen = ld_acquire(&ctl->bar_gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-        if (arrived == nblocks - 1) {
+        __threadfence();  // the block's writes before its arrival
+        const unsigned long long arrived = atomicAdd(&ctl->bar_arrivals, 1ull) + 1ull;
+        if (arrived >= target) {
+            __threadfence();  // acquire: the other blocks' writes before theirs
             leader();
-            ctl->bar_count = 0;
-            __threadfence();
-            st_release(&ctl->bar_gen, gen + 1);
         } else {
             long long polls = 0;
-            while (ld_acquire(&ctl->bar_gen) == gen) {
-                if (++polls > spin_cap || ld_acquire_int(&ctl->err) != 0) {
+            while (ld_acquire_u64(&ctl->bar_arrivals) < target) {
+                if (++polls > spin_cap) {
                     atomicCAS(&ctl->err, 0, kErrTimedOut);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                if ((polls & 63) == 0 && ld_acquire_int(&ctl->err) != 0) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
             }
         }
-        __threadfence();
-        if (ld_acquire_int(&ctl->err) != 0) ok = 0;
         if (ok) after();
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
 }
+
+struct NoLeader {
+    __device__ void operator()() const {}
+};
 
 template <class Leader>
 __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, long long spin_cap,

@@ -45,10 +45,17 @@ constexpr int kCsrMinBlocksPerSm = 3;
 constexpr int kRowsPerLane = 2;
 constexpr int kWarps = kCsrBlock / 32;
 
-// Rows per chunk taken by one warp, per bin (bin 4 is taken a row at a time
-// by a whole block).
-constexpr int kChunk0 = 256, kChunk1 = 128, kChunk2 = 64, kChunk3 = 32;
-constexpr int kStageMax = 256;
+// Most rows per chunk taken by one warp, per bin (bin 4 is taken a row at a
+// time by a whole block).  A bin of up to nwarps * CH rows is split into equal
+// static chunks, one per warp, with no counter atomics; larger bins hand out
+// further chunks through the bin's counter.  Same-address atomics serialise in
+// L2, so few large chunks beat many small ones here.
+constexpr int kChunk0 = 1024, kChunk1 = 512, kChunk2 = 256, kChunk3 = 128;
+// Finish each bin with chunks of one warp pass (balance at the end of a
+// phase, at the price of more counter atomics): measured slower, off.
+constexpr bool kTailChunks = false;
+constexpr int kStageMax = 512;  // list entries staged per warp before an append
+constexpr int kScanMax = 256;   // rows triaged at once in Phase 2
 
 // Does u outrank v in the selection test?  `wu` is u's word, `wv` v's
 // (undecided, so wv is v's key): out words never outrank, undecided ones
@@ -161,7 +168,7 @@ struct ChunkPlan {
     __device__ __forceinline__ void range(int k, int cnt, int& c0, int& c1, int G) const {
         if (k < nbig) {
             c0 = k * ch;
-            c1 = c0 + ch;
+            c1 = min(c0 + ch, cnt);
         } else {
             c0 = nbig * ch + (k - nbig) * G;
             c1 = min(c0 + G, cnt);
@@ -176,8 +183,13 @@ __device__ __forceinline__ ChunkPlan plan_of(int cnt, int nwarps) {
     if (per < G) per = G;
     ChunkPlan p;
     p.ch = per < CH ? (int)per : CH;
-    p.nbig = (int)((long long)cnt * 7 / 8 / p.ch);
-    p.total = p.nbig + (cnt - p.nbig * p.ch + G - 1) / G;
+    if (kTailChunks) {
+        p.nbig = (int)((long long)cnt * 7 / 8 / p.ch);
+        p.total = p.nbig + (cnt - p.nbig * p.ch + G - 1) / G;
+    } else {
+        p.nbig = (cnt + p.ch - 1) / p.ch;  // the last one may be short
+        p.total = p.nbig;
+    }
     return p;
 }
 
@@ -228,27 +240,38 @@ __device__ __forceinline__ void flush_stage(const int32_t* wbuf, int fill, const
     __syncwarp();
 }
 
+// Appends the staged entries when another pass could overflow the buffer.
+__device__ __forceinline__ int flush_if_full(const int32_t* wbuf, int fill, int pass_rows,
+                                             const int4* list, int* next, int4* dst) {
+    if (fill > kStageMax - pass_rows) {
+        flush_stage(wbuf, fill, list, next, dst);
+        return 0;
+    }
+    return fill;
+}
+
 // Phase 1, bins 0..3: selection test of every row of the bin's list W_r.
 // Candidates are marked in the MIS.  kPending: the others form the pending
 // list P_r of Phase 2 (appended to pdst, counted in *pnext).
 template <int TPR, int CH, bool kPending>
-__device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __restrict__ list, int cnt, WarpSched& ws,
-                                           unsigned* grab, int* pnext, int4* __restrict__ pdst,
-                                           int32_t* wbuf) {
-    static_assert(CH <= kStageMax, "chunk exceeds the staging buffer");
+__device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __restrict__ list,
+                                           int cnt, WarpSched& ws, unsigned* grab, int* pnext,
+                                           int4* __restrict__ pdst, int32_t* wbuf) {
     constexpr int G = 32 / TPR;
+    constexpr int kPass = TPR == 1 ? 32 * kRowsPerLane : G;  // rows of one warp pass
+    static_assert(kPass <= kStageMax, "a warp pass exceeds the staging buffer");
     if (cnt <= 0) return;
     const unsigned lane = lane_id();
     const unsigned glane = lane % TPR;
     const unsigned gid = lane / TPR;
     const unsigned gshift = gid * TPR;
     const ChunkPlan plan = plan_of<G, CH>(cnt, ws.nwarps);
+    int fill = 0;
     for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps, grab)) {
         int c0, c1;
         plan.range(k, cnt, c0, c1, G);
-        int fill = 0;
-        if constexpr (TPR == 1) {
-            for (int base = c0; base < c1; base += 32 * kRowsPerLane) {
+        for (int base = c0; base < c1; base += kPass) {
+            if constexpr (TPR == 1) {
                 int4 rec[kRowsPerLane];
                 bool valid[kRowsPerLane], blocked[kRowsPerLane];
                 uint32_t wv[kRowsPerLane];
@@ -258,6 +281,8 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __res
                     valid[i] = item < c1;
                     rec[i] = valid[i] ? list[item] : make_int4(0, 0, 0, 0);
                 }
+                // every vertex of W_r is undecided and nothing else writes its
+                // word in this phase, so it may be read through L1
 #pragma unroll
                 for (int i = 0; i < kRowsPerLane; ++i)
                     wv[i] = valid[i] ? ld_word_l1(a.word + rec[i].x) : 0u;
@@ -270,14 +295,10 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __res
                         fill = stage_keep(valid[i] && blocked[i], base + (int)lane + 32 * i, wbuf,
                                           fill);
                 }
-            }
-        } else {
-            for (int base = c0; base < c1; base += G) {
+            } else {
                 const int item = base + (int)gid;
                 const bool valid = item < c1;
                 const int4 rec = valid ? list[item] : make_int4(0, 0, 0, 0);
-                // every vertex of W_r is undecided and nothing else writes its
-                // word in this phase, so each lane may load it
                 const uint32_t wv = valid ? ld_word_l1(a.word + rec.x) : 0u;
                 const int e = valid ? rec.z : 0;
                 const bool blocked = group_scan<TPR, true>(a.col_sel, LiveWords{a.word}, rec.y, e,
@@ -286,22 +307,26 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __res
                 if (valid && !blocked && lead) a.word[rec.x] = wv | kWordInSet;
                 if (kPending) fill = stage_keep(valid && blocked && lead, item, wbuf, fill);
             }
+            if (kPending) fill = flush_if_full(wbuf, fill, kPass, list, pnext, pdst);
         }
-        if (kPending) flush_stage(wbuf, fill, list, pnext, pdst);
     }
+    if (kPending) flush_stage(wbuf, fill, list, pnext, pdst);
 }
 
 // Phase 2+3, bins 0..3: exclusion test, state update, compaction into
 // W_{r+1}.  kPending: `list` is the pending list P_r (undecided
-// non-candidates only); else it is W_r, and each chunk is first triaged one
-// vertex per lane (Phase 1 candidates need no scan) into `wscan`.
+// non-candidates only); else it is W_r, and each chunk (at most kScanMax
+// rows) is first triaged one vertex per lane (Phase 1 candidates need no
+// scan) into `wscan`.
 template <int TPR, int CH, bool kPending>
 __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __restrict__ list,
                                             int cnt, WarpSched& ws, unsigned* grab, int* next,
                                             int4* __restrict__ dst, int32_t* wbuf,
                                             int32_t* wscan) {
-    static_assert(CH <= kStageMax, "chunk exceeds the staging buffer");
     constexpr int G = 32 / TPR;
+    constexpr int kPass = TPR == 1 ? 32 * kRowsPerLane : G;
+    static_assert(kPass <= kStageMax, "a warp pass exceeds the staging buffer");
+    static_assert(kPending || CH <= kScanMax, "a chunk exceeds the triage buffer");
     if (cnt <= 0) return;
     const unsigned lane = lane_id();
     const unsigned glane = lane % TPR;
@@ -309,11 +334,13 @@ __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __re
     const unsigned gshift = gid * TPR;
     const LiveWords nbw{a.word};
     const ChunkPlan plan = plan_of<G, CH>(cnt, ws.nwarps);
+    int fill = 0;
     for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps, grab)) {
         int c0, c1;
         plan.range(k, cnt, c0, c1, G);
         if (!kPending) {
             // triage: wscan gets the list indices of the undecided rows
+            __syncwarp();  // the previous chunk is done with wscan
             int nscan = 0;
             for (int base = c0; base < c1; base += 32) {
                 const int item = base + (int)lane;
@@ -325,9 +352,8 @@ __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __re
             c1 = nscan;
         }
         // row i of the chunk: list[kPending ? i : wscan[i]]
-        int fill = 0;
-        if constexpr (TPR == 1) {
-            for (int base = c0; base < c1; base += 32 * kRowsPerLane) {
+        for (int base = c0; base < c1; base += kPass) {
+            if constexpr (TPR == 1) {
                 int4 rec[kRowsPerLane];
                 int idx[kRowsPerLane];
                 bool valid[kRowsPerLane], excl[kRowsPerLane];
@@ -345,9 +371,7 @@ __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __re
                     if (valid[i] && excl[i]) a.word[rec[i].x] = kWordOut;
                     fill = stage_keep(valid[i] && !excl[i], idx[i], wbuf, fill);
                 }
-            }
-        } else {
-            for (int base = c0; base < c1; base += G) {
+            } else {
                 const int item = base + (int)gid;
                 const bool valid = item < c1;
                 const int idx = valid ? (kPending ? item : wscan[item]) : 0;
@@ -359,9 +383,10 @@ __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __re
                 if (valid && excl && lead) a.word[rec.x] = kWordOut;
                 fill = stage_keep(valid && !excl && lead, idx, wbuf, fill);
             }
+            fill = flush_if_full(wbuf, fill, kPass, list, next, dst);
         }
-        flush_stage(wbuf, fill, list, next, dst);
     }
+    flush_stage(wbuf, fill, list, next, dst);
 }
 
 // Bin 4 (hubs): the whole block scans one row at a time.  kSelect: Phase 1
@@ -464,27 +489,32 @@ __device__ __forceinline__ void exclude_phase(const SolveArgs& a, const int4* li
                                               int32_t* wbuf, int32_t* wscan) {
     const int* off = a.bin_off;
     const int nw = ws.nwarps;
+    // a triaged chunk must fit the triage buffer
+    constexpr int kX0 = (kPending || kChunk0 <= kScanMax) ? kChunk0 : kScanMax;
+    constexpr int kX1 = (kPending || kChunk1 <= kScanMax) ? kChunk1 : kScanMax;
+    constexpr int kX2 = (kPending || kChunk2 <= kScanMax) ? kChunk2 : kScanMax;
+    constexpr int kX3 = (kPending || kChunk3 <= kScanMax) ? kChunk3 : kScanMax;
     block_bin<false, kPending>(a, list + off[4], cnt[4], &grab[4], &next[4],
                                       dst + off[4]);
-    exclude_bin<32, kChunk3, kPending>(a, list + off[3], cnt[3], ws, &grab[3], &next[3],
+    exclude_bin<32, kX3, kPending>(a, list + off[3], cnt[3], ws, &grab[3], &next[3],
                                        dst + off[3], wbuf, wscan);
     if (late && cnt[2] <= nw)
-        exclude_bin<32, kChunk3, kPending>(a, list + off[2], cnt[2], ws, &grab[2], &next[2],
+        exclude_bin<32, kX3, kPending>(a, list + off[2], cnt[2], ws, &grab[2], &next[2],
                                            dst + off[2], wbuf, wscan);
     else
-        exclude_bin<16, kChunk2, kPending>(a, list + off[2], cnt[2], ws, &grab[2], &next[2],
+        exclude_bin<16, kX2, kPending>(a, list + off[2], cnt[2], ws, &grab[2], &next[2],
                                            dst + off[2], wbuf, wscan);
     if (late && cnt[1] <= nw)
-        exclude_bin<32, kChunk3, kPending>(a, list + off[1], cnt[1], ws, &grab[1], &next[1],
+        exclude_bin<32, kX3, kPending>(a, list + off[1], cnt[1], ws, &grab[1], &next[1],
                                            dst + off[1], wbuf, wscan);
     else
-        exclude_bin<4, kChunk1, kPending>(a, list + off[1], cnt[1], ws, &grab[1], &next[1],
+        exclude_bin<4, kX1, kPending>(a, list + off[1], cnt[1], ws, &grab[1], &next[1],
                                           dst + off[1], wbuf, wscan);
     if (late && cnt[0] <= nw)
-        exclude_bin<4, kChunk1, kPending>(a, list + off[0], cnt[0], ws, &grab[0], &next[0],
+        exclude_bin<4, kX1, kPending>(a, list + off[0], cnt[0], ws, &grab[0], &next[0],
                                           dst + off[0], wbuf, wscan);
     else
-        exclude_bin<1, kChunk0, kPending>(a, list + off[0], cnt[0], ws, &grab[0], &next[0],
+        exclude_bin<1, kX0, kPending>(a, list + off[0], cnt[0], ws, &grab[0], &next[0],
                                           dst + off[0], wbuf, wscan);
 }
 
@@ -532,13 +562,18 @@ template <bool kPending>
 __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     csr_solve_kernel(const SolveArgs a) {
     __shared__ int32_t s_stage[kWarps][kStageMax];
-    __shared__ int32_t s_scan[kPending ? 1 : kWarps][kPending ? 1 : kStageMax];
+    __shared__ int32_t s_scan[kPending ? 1 : kWarps][kPending ? 1 : kScanMax];
+    // per-bin sizes of W_r and of P_r, copied once per block after each
+    // barrier (kept in shared memory, out of the scans' registers)
     __shared__ int s_cnt[kBins];
+    __shared__ int s_pcnt[kBins];
     const unsigned nblocks = gridDim.x;
     Ctl* ctl = a.ctl;
     PhaseTimes* times = a.times;
     int32_t* wbuf = s_stage[threadIdx.x / 32];
     int32_t* wscan = kPending ? nullptr : &s_scan[kPending ? 0 : threadIdx.x / 32][0];
+    grid_barrier_start();
+    if (threadIdx.x < kBins) s_cnt[threadIdx.x] = a.bin_off[threadIdx.x + 1] - a.bin_off[threadIdx.x];
     if (times && blockIdx.x == 0 && threadIdx.x == 0) times->t[0] = global_ns();
 
     // ---- init: Eq. 1 priorities
@@ -548,19 +583,20 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
         }))
         return;
 
-    int cnt[kBins];
-    int total = 0;
-    for (int j = 0; j < kBins; ++j) {
-        cnt[j] = a.bin_off[j + 1] - a.bin_off[j];
-        total += cnt[j];
-    }
     // isolated vertices were decided at init but belong to round 0's alive set
     const int iso = a.n_isolated;
     WarpSched ws;
     ws.gw = (int)(blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32);
     ws.nwarps = (int)(nblocks * (blockDim.x / 32));
     ws.base = 0;
-    for (int r = 0; total > 0 || (r == 0 && iso > 0); ++r) {
+    for (int r = 0;; ++r) {
+        int total = 0;
+        for (int j = 0; j < kBins; ++j) total += s_cnt[j];
+        if (!(total > 0 || (r == 0 && iso > 0))) break;
+        if (r >= a.max_rounds) {
+            if (threadIdx.x == 0) atomicCAS(&ctl->err, 0, kErrInternal);
+            return;
+        }
         const int4* src = (r == 0) ? a.order0 : ((r & 1) ? a.wl1 : a.wl0);
         int4* dst = ((r + 1) & 1) ? a.wl1 : a.wl0;
         int* next = ctl->bcnt[(r + 1) & 3];
@@ -568,7 +604,7 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
         const int rr = r;
 
         // ---- Phase 1: selection test
-        select_phase<kPending>(a, src, cnt, r > 0, ws, ctl->grab[(2 * r) & 3], pnext, a.wlp,
+        select_phase<kPending>(a, src, s_cnt, r > 0, ws, ctl->grab[(2 * r) & 3], pnext, a.wlp,
                                wbuf);
         if (!grid_barrier(
                 ctl, nblocks, a.spin_cap,
@@ -578,20 +614,17 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
                 },
                 [pnext]() {
                     if (kPending)
-                        for (int j = 0; j < kBins; ++j) s_cnt[j] = __ldcg(pnext + j);
+                        for (int j = 0; j < kBins; ++j) s_pcnt[j] = __ldcg(pnext + j);
                 }))
             return;
 
         // ---- Phase 2+3: exclusion test, state update, compaction
-        if (kPending) {
-            int pc[kBins];
-            for (int j = 0; j < kBins; ++j) pc[j] = s_cnt[j];
-            exclude_phase<true>(a, a.wlp, pc, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next, dst,
-                                wbuf, wscan);
-        } else {
-            exclude_phase<false>(a, src, cnt, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next, dst,
+        if (kPending)
+            exclude_phase<true>(a, a.wlp, s_pcnt, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next,
+                                dst, wbuf, wscan);
+        else
+            exclude_phase<false>(a, src, s_cnt, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next, dst,
                                  wbuf, wscan);
-        }
         const int cur = total + (r == 0 ? iso : 0);
         if (!grid_barrier(
                 ctl, nblocks, a.spin_cap,
@@ -610,15 +643,6 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
                     for (int j = 0; j < kBins; ++j) s_cnt[j] = __ldcg(next + j);
                 }))
             return;
-        total = 0;
-        for (int j = 0; j < kBins; ++j) {
-            cnt[j] = s_cnt[j];
-            total += cnt[j];
-        }
-        if (total > 0 && r + 1 >= a.max_rounds) {
-            if (threadIdx.x == 0) atomicCAS(&ctl->err, 0, kErrInternal);
-            return;
-        }
     }
 
     // ---- output

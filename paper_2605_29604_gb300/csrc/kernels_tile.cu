@@ -520,6 +520,7 @@ __global__ void __launch_bounds__(kTileBlock, 2) tile_solve_kernel(const SolveAr
     const int32_t n = a.n;
     const int32_t nrb = a.nrb;
     int32_t* wkeep = s_keep[threadIdx.x / 32];
+    grid_barrier_start();
     if (times && blockIdx.x == 0 && threadIdx.x == 0) times->t[0] = global_ns();
 
     // ---- init: Eq. 1 priorities (tile padding out), empty in-set bits,

@@ -85,6 +85,8 @@ __global__ void __launch_bounds__(kNoAllocBlock, 2)
     const int wpb = blockDim.x / 32;
     const long long gwarp = (long long)blockIdx.x * wpb + threadIdx.x / 32;
     const long long nwarps = (long long)nblocks * wpb;
+    grid_barrier_start();
+    __shared__ int s_count;        // next worklist size, loaded once per block
     const int arcs = max(0, rp[n]);
     auto row = [&](int v, int& b, int& e) {
         b = min(max(rp[v], 0), arcs);
@@ -152,9 +154,10 @@ __global__ void __launch_bounds__(kNoAllocBlock, 2)
                 ctl->alive_sum += (unsigned long long)cur;
                 ctl->rounds = rr + 1;
                 ctl->cnt[(rr + 2) & 3] = 0;
-            }))
+            },
+            [next_cnt]() { s_count = __ldcg(next_cnt); }))
             return;
-        count = ld_acquire_int(next_cnt);
+        count = s_count;
         if (count == 0) break;
         if (r + 1 >= n + 2) {
             if (threadIdx.x == 0) atomicCAS(&ctl->err, 0, kErrInternal);
