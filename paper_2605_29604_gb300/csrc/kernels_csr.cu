@@ -447,38 +447,68 @@ __device__ __forceinline__ void block_bin(const SolveArgs& a, const int4* __rest
     }
 }
 
+// Lanes per row of a bin whose base width is BASE: in rounds after the first
+// (`late`) the rows are the survivors of earlier rounds, which need the
+// longest scans, and there are few of them, so a bin takes the widest group
+// (up to a warp) at which all its rows still fit in one pass of the grid's
+// lanes: latency, not throughput.
+template <int BASE>
+__device__ __forceinline__ int lanes_per_row(int cnt, bool late, int nwarps) {
+    if (!late) return BASE;
+    const long long lanes = 32LL * nwarps;
+    if (BASE < 32 && 32LL * cnt <= lanes) return 32;
+    if (BASE < 16 && 16LL * cnt <= lanes) return 16;
+    if (BASE < 4 && 4LL * cnt <= lanes) return 4;
+    return BASE;
+}
+
+// Phase 1 of bin j (base width BASE, chunk CH) at the width lanes_per_row picks.
+template <int BASE, int CH, bool kPending>
+__device__ __forceinline__ void select_bin_at(const SolveArgs& a, const int4* list, int cnt,
+                                              bool late, WarpSched& ws, unsigned* grab,
+                                              int* pnext, int4* pend, int32_t* wbuf) {
+    switch (lanes_per_row<BASE>(cnt, late, ws.nwarps)) {
+        case 32: select_bin<32, kChunk3, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf); break;
+        case 16: select_bin<16, kChunk2, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf); break;
+        case 4: select_bin<4, kChunk1, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf); break;
+        default: select_bin<BASE, CH, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf);
+    }
+}
+
+// Phase 2+3 of one bin, likewise.  A triaged chunk must fit the triage buffer.
+template <int BASE, int CH, bool kPending>
+__device__ __forceinline__ void exclude_bin_at(const SolveArgs& a, const int4* list, int cnt,
+                                               bool late, WarpSched& ws, unsigned* grab,
+                                               int* next, int4* dst, int32_t* wbuf,
+                                               int32_t* wscan) {
+    constexpr int kX3 = (kPending || kChunk3 <= kScanMax) ? kChunk3 : kScanMax;
+    constexpr int kX2 = (kPending || kChunk2 <= kScanMax) ? kChunk2 : kScanMax;
+    constexpr int kX1 = (kPending || kChunk1 <= kScanMax) ? kChunk1 : kScanMax;
+    constexpr int kX = (kPending || CH <= kScanMax) ? CH : kScanMax;
+    switch (lanes_per_row<BASE>(cnt, late, ws.nwarps)) {
+        case 32: exclude_bin<32, kX3, kPending>(a, list, cnt, ws, grab, next, dst, wbuf, wscan); break;
+        case 16: exclude_bin<16, kX2, kPending>(a, list, cnt, ws, grab, next, dst, wbuf, wscan); break;
+        case 4: exclude_bin<4, kX1, kPending>(a, list, cnt, ws, grab, next, dst, wbuf, wscan); break;
+        default: exclude_bin<BASE, kX, kPending>(a, list, cnt, ws, grab, next, dst, wbuf, wscan);
+    }
+}
+
 // Phase 1 over the bins of one worklist: hubs first, then the bins of longer
-// rows.  In rounds after the first (`late`), a bin with no more rows than
-// warps gets one warp (or 4 lanes for short rows) per row: latency, not
-// throughput.
+// rows.
 template <bool kPending>
-__device__ __forceinline__ void select_phase(const SolveArgs& a, const int4* src, const int* cnt, bool late,
-                                             WarpSched& ws, unsigned* grab, int* pnext,
-                                             int4* pend, int32_t* wbuf) {
+__device__ __forceinline__ void select_phase(const SolveArgs& a, const int4* src, const int* cnt,
+                                             bool late, WarpSched& ws, unsigned* grab,
+                                             int* pnext, int4* pend, int32_t* wbuf) {
     const int* off = a.bin_off;
-    const int nw = ws.nwarps;
-    block_bin<true, kPending>(a, src + off[4], cnt[4], &grab[4], &pnext[4],
-                                       pend + off[4]);
-    select_bin<32, kChunk3, kPending>(a, src + off[3], cnt[3], ws, &grab[3],
-                                               &pnext[3], pend + off[3], wbuf);
-    if (late && cnt[2] <= nw)
-        select_bin<32, kChunk3, kPending>(a, src + off[2], cnt[2], ws, &grab[2],
-                                                   &pnext[2], pend + off[2], wbuf);
-    else
-        select_bin<16, kChunk2, kPending>(a, src + off[2], cnt[2], ws, &grab[2],
-                                                   &pnext[2], pend + off[2], wbuf);
-    if (late && cnt[1] <= nw)
-        select_bin<32, kChunk3, kPending>(a, src + off[1], cnt[1], ws, &grab[1],
-                                                   &pnext[1], pend + off[1], wbuf);
-    else
-        select_bin<4, kChunk1, kPending>(a, src + off[1], cnt[1], ws, &grab[1],
-                                                  &pnext[1], pend + off[1], wbuf);
-    if (late && cnt[0] <= nw)
-        select_bin<4, kChunk1, kPending>(a, src + off[0], cnt[0], ws, &grab[0],
-                                                  &pnext[0], pend + off[0], wbuf);
-    else
-        select_bin<1, kChunk0, kPending>(a, src + off[0], cnt[0], ws, &grab[0],
-                                                  &pnext[0], pend + off[0], wbuf);
+    block_bin<true, kPending>(a, src + off[4], cnt[4], &grab[4], &pnext[4], pend + off[4]);
+    select_bin_at<32, kChunk3, kPending>(a, src + off[3], cnt[3], late, ws, &grab[3], &pnext[3],
+                                         pend + off[3], wbuf);
+    select_bin_at<16, kChunk2, kPending>(a, src + off[2], cnt[2], late, ws, &grab[2], &pnext[2],
+                                         pend + off[2], wbuf);
+    select_bin_at<4, kChunk1, kPending>(a, src + off[1], cnt[1], late, ws, &grab[1], &pnext[1],
+                                        pend + off[1], wbuf);
+    select_bin_at<1, kChunk0, kPending>(a, src + off[0], cnt[0], late, ws, &grab[0], &pnext[0],
+                                        pend + off[0], wbuf);
 }
 
 // Phase 2+3 over the bins of `list` (W_r, or P_r when kPending).
@@ -488,34 +518,15 @@ __device__ __forceinline__ void exclude_phase(const SolveArgs& a, const int4* li
                                               unsigned* grab, int* next, int4* dst,
                                               int32_t* wbuf, int32_t* wscan) {
     const int* off = a.bin_off;
-    const int nw = ws.nwarps;
-    // a triaged chunk must fit the triage buffer
-    constexpr int kX0 = (kPending || kChunk0 <= kScanMax) ? kChunk0 : kScanMax;
-    constexpr int kX1 = (kPending || kChunk1 <= kScanMax) ? kChunk1 : kScanMax;
-    constexpr int kX2 = (kPending || kChunk2 <= kScanMax) ? kChunk2 : kScanMax;
-    constexpr int kX3 = (kPending || kChunk3 <= kScanMax) ? kChunk3 : kScanMax;
-    block_bin<false, kPending>(a, list + off[4], cnt[4], &grab[4], &next[4],
-                                      dst + off[4]);
-    exclude_bin<32, kX3, kPending>(a, list + off[3], cnt[3], ws, &grab[3], &next[3],
-                                       dst + off[3], wbuf, wscan);
-    if (late && cnt[2] <= nw)
-        exclude_bin<32, kX3, kPending>(a, list + off[2], cnt[2], ws, &grab[2], &next[2],
-                                           dst + off[2], wbuf, wscan);
-    else
-        exclude_bin<16, kX2, kPending>(a, list + off[2], cnt[2], ws, &grab[2], &next[2],
-                                           dst + off[2], wbuf, wscan);
-    if (late && cnt[1] <= nw)
-        exclude_bin<32, kX3, kPending>(a, list + off[1], cnt[1], ws, &grab[1], &next[1],
-                                           dst + off[1], wbuf, wscan);
-    else
-        exclude_bin<4, kX1, kPending>(a, list + off[1], cnt[1], ws, &grab[1], &next[1],
-                                          dst + off[1], wbuf, wscan);
-    if (late && cnt[0] <= nw)
-        exclude_bin<4, kX1, kPending>(a, list + off[0], cnt[0], ws, &grab[0], &next[0],
-                                          dst + off[0], wbuf, wscan);
-    else
-        exclude_bin<1, kX0, kPending>(a, list + off[0], cnt[0], ws, &grab[0], &next[0],
-                                          dst + off[0], wbuf, wscan);
+    block_bin<false, kPending>(a, list + off[4], cnt[4], &grab[4], &next[4], dst + off[4]);
+    exclude_bin_at<32, kChunk3, kPending>(a, list + off[3], cnt[3], late, ws, &grab[3],
+                                          &next[3], dst + off[3], wbuf, wscan);
+    exclude_bin_at<16, kChunk2, kPending>(a, list + off[2], cnt[2], late, ws, &grab[2],
+                                          &next[2], dst + off[2], wbuf, wscan);
+    exclude_bin_at<4, kChunk1, kPending>(a, list + off[1], cnt[1], late, ws, &grab[1],
+                                         &next[1], dst + off[1], wbuf, wscan);
+    exclude_bin_at<1, kChunk0, kPending>(a, list + off[0], cnt[0], late, ws, &grab[0],
+                                         &next[0], dst + off[0], wbuf, wscan);
 }
 
 // Writes out[v] = [v in the MIS] and adds the MIS size to ctl->mis_size.
