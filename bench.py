@@ -222,14 +222,19 @@ def _sum_over_ranks(x, world):
     return float(t.item())
 
 
-def time_device_steps(native, h, seeds, out_ptr, stream, steps, warmup, local, world):
-    """Per-step CUDA-event times (L2 flushed between steps), clocks sampled."""
+def time_device_steps(native, h, seeds, out_ptr, stream, steps, warmup, local, world,
+                      replay=None):
+    """Per-step CUDA-event times (L2 flushed between steps), clocks sampled.
+    With `replay` (from mis_capture) each step replays the captured solve."""
     import torch
     import torch.distributed as dist
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
 
     def step():
-        native.mis_solve_ex(h, seeds, out_ptr, stream)
+        if replay is not None:
+            native.mis_replay_launch(replay, stream)
+        else:
+            native.mis_solve_ex(h, seeds, out_ptr, stream)
 
     for _ in range(max(warmup, 3)):
         step()
@@ -391,10 +396,13 @@ def run_batch(args):
     out = torch.empty(max(size, 1), dtype=torch.uint8, device="cuda")
     seeds = np.arange(1, len(parts) + 1, dtype=np.uint64)
     stream = torch.cuda.current_stream().cuda_stream
+    # one persistent launch per step, replayed from a captured CUDA graph
+    replay = native.mis_capture(h, seeds, out.data_ptr())
     step_ms, clocks = time_device_steps(native, h, seeds, out.data_ptr(), stream, args.steps,
-                                        args.warmup, local, world)
+                                        args.warmup, local, world, replay=replay)
     total_ms = _max_over_ranks(sum(step_ms), world)
     st = native.mis_get_stats(h)
+    native.mis_replay_destroy(replay)
     value = world * args.steps * arcs / (total_ms / 1e3)
     peak, peak_kind = _peak_hbm()
     alg_bytes = 4 * arcs + 4 * (nsum + 1) + 4 * nsum + nsum
@@ -411,6 +419,10 @@ def run_batch(args):
                                                       "bounds": list(tuning.bounds),
                                                       "grid": tuning.grid,
                                                       "csr_pending": tuning.csr_pending},
+                   "launch": "captured CUDA graph replay (mis_capture, mis_replay_launch)",
+                   "phase_us": {"init": st.init_ns / 1e3,
+                                "select": [x / 1e3 for x in st.select_ns[:st.rounds]],
+                                "exclude": [x / 1e3 for x in st.exclude_ns[:st.rounds]]},
                    "l2": "flushed between steps (256 MB write)"},
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

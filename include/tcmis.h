@@ -72,6 +72,7 @@ enum {
 };
 
 typedef struct mis_graph mis_graph;
+typedef struct mis_replay mis_replay;
 typedef int64_t mis_ticket;
 
 typedef struct mis_options {
@@ -120,6 +121,11 @@ typedef struct mis_stats {
     int64_t select_ns[64];   /* device time of Phase 1 (selection test), rounds 0..63 */
     int64_t exclude_ns[64];  /* device time of Phases 2+3 (exclusion test, state
                                 update, compaction), rounds 0..63 */
+    int64_t sure_in;         /* CSR path: vertices known at create time to be round-0
+                                candidates (every neighbour has degree >= deg + 2),
+                                put in the MIS at init without a test */
+    int64_t sure_out;        /* CSR path: neighbours of those, excluded in round 0
+                                without a test */
 } mis_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -177,6 +183,25 @@ int mis_solve(mis_graph *g, uint64_t seed, uint8_t *out_status);
  * one stream.
  */
 int mis_solve_ex(mis_graph *g, const uint64_t *seeds, uint8_t *out_status, void *stream);
+
+/*
+ * Captured solves (no counterpart in the paper: launch-overhead removal for
+ * repeated solves, e.g. a batched union solved again and again).
+ * mis_capture records what mis_solve_ex(g, seeds, out_status, stream) enqueues
+ * -- control-block reset, seed upload, the one persistent round-kernel launch
+ * -- into an executable CUDA graph; mis_replay_launch launches that graph on
+ * `stream` (a cudaStream_t).  Each replay is a complete solve with the captured seeds
+ * (copied at capture time) into the captured DEVICE buffer `out_status`, and
+ * the captured path, bins and grid.  Replays use the handle's workspace like
+ * mis_solve_ex: order them with the handle's other solves on one stream;
+ * mis_get_stats reports the last one.  Destroy every replay of a handle
+ * before the handle.  Errors: MIS_EINVAL (null or bad arguments), MIS_EBUSY
+ * (served requests in flight on `g`), MIS_EDEVICE (capture or instantiation
+ * refused by the driver), MIS_ENOMEM.
+ */
+int mis_capture(mis_graph *g, const uint64_t *seeds, uint8_t *out_status, mis_replay **replay);
+int mis_replay_launch(mis_replay *replay, void *stream);
+void mis_replay_destroy(mis_replay *replay);
 
 /* Statistics of the last solve on `g`; synchronises that solve's stream and
  * returns its device-side status (MIS_OK, MIS_ETIMEDOUT, MIS_EINTERNAL). */

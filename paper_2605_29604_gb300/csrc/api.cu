@@ -161,9 +161,14 @@ SegTable seg_of(const GraphData& d) {
 int rebin(mis_graph* g, const int32_t thr[4], cudaStream_t s) {
     GraphData& d = g->d;
     for (int j = 0; j < 4; ++j) d.thr[j] = thr[j];
-    cudaError_t e =
-        build_bins(d.rp, d.split, d.n, seg_of(d), d.thr, d.order0, d.bin_off, &d.n_isolated, s);
+    Round0Plan plan;
+    cudaError_t e = build_bins(d.rp, d.split, d.r0class, d.n, seg_of(d), d.thr, d.order0,
+                               d.sure_out, &plan, s);
     if (e != cudaSuccess) return set_cuda_error(e, "degree binning");
+    for (int j = 0; j < 6; ++j) d.bin_off[j] = plan.bin_off[j];
+    d.n_isolated = plan.n_isolated;
+    d.n_sure_in = plan.n_sure_in;
+    d.n_sure_out = plan.n_sure_out;
     return MIS_OK;
 }
 
@@ -217,6 +222,8 @@ int finish_create(mis_graph* g) {
     const bool order = g->opt.order_rows != 0;
     if ((e = ws_reserve(d.ws, d.n, d.count)) != cudaSuccess ||
         (e = dalloc(&d.order0, d.n, &d.footprint)) != cudaSuccess ||
+        (order && (e = dalloc(&d.r0class, d.n, &d.footprint)) != cudaSuccess) ||
+        (order && (e = dalloc(&d.sure_out, d.n, &d.footprint)) != cudaSuccess) ||
         (order && (e = dalloc(&d.col_sel, col_alloc, &d.footprint)) != cudaSuccess) ||
         (order && (e = dalloc(&d.split, d.n, &d.footprint)) != cudaSuccess))
         return set_cuda_error(e, "workspace allocation");
@@ -243,6 +250,9 @@ int finish_create(mis_graph* g) {
                                          g->own_stream)
                     : build_row_partition(d.rp, d.col, d.n, d.arcs, seg_of(d), d.col_sel,
                                           d.split, g->own_stream);
+        if (e == cudaSuccess)
+            e = build_round0_classes(d.rp, d.col_sel, d.split, d.n, seg_of(d), d.r0class,
+                                     g->own_stream);
         if (e != cudaSuccess) return set_cuda_error(e, "degree ordering");
     }
     const int brc = rebin(g, thr, g->own_stream);
@@ -297,6 +307,10 @@ SolveArgs make_args(mis_graph* g, Workspace& w) {
     a.order0 = d.order0;
     for (int j = 0; j < 6; ++j) a.bin_off[j] = d.bin_off[j];
     a.n_isolated = d.n_isolated;
+    a.r0class = d.r0class;
+    a.sure_out = d.sure_out;
+    a.n_sure_in = d.n_sure_in;
+    a.n_sure_out = d.n_sure_out;
     a.pending = g->csr_pending;
     a.ctl = w.ctl;
     a.times = w.times;
@@ -334,6 +348,8 @@ void free_graph(mis_graph* g) {
     if (d.seeds_host) cudaFreeHost(d.seeds_host);
     free_tiles(d);
     dfree(d.order0);
+    dfree(d.r0class);
+    dfree(d.sure_out);
     dfree(d.col_sel);
     dfree(d.split);
     ws_free(d.ws);
@@ -1066,6 +1082,9 @@ int mis_get_stats(mis_graph* g, mis_stats* st) {
     st->threads_per_row = g->tpr;
     st->tile = g->d.tiles.T;
     st->csr_pending = g->csr_pending;
+    const bool csr = g->last_path != MIS_PATH_TILE && g->last_path != MIS_PATH_TILE_TC;
+    st->sure_in = csr ? g->d.n_sure_in : 0;
+    st->sure_out = csr ? g->d.n_sure_out : 0;
     st->ntiles = g->d.tiles.ntiles;
     st->alive_sum = (int64_t)c.alive_sum;
     st->mis_size = (int64_t)c.mis_size;
@@ -1107,6 +1126,76 @@ int mis_keys_ex(mis_graph* g, const uint64_t* seeds, uint32_t* out_key, void* st
     if (e != cudaSuccess) return set_cuda_error(e, "keys");
     g->last_stream = s;
     return MIS_OK;
+}
+
+int mis_capture(mis_graph* g, const uint64_t* seeds, uint8_t* out_status, mis_replay** replay) {
+    clear_error();
+    if (!g || !seeds || !replay) return set_error(MIS_EINVAL, "null argument");
+    if (g->d.result_bytes > 0 && !out_status) return set_error(MIS_EINVAL, "null out_status");
+    *replay = nullptr;
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
+    cudaError_t e = cudaSetDevice(g->d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    auto* r = new (std::nothrow) mis_replay();
+    if (!r) return set_error(MIS_ENOMEM, "replay");
+    r->g = g;
+    r->path = g->path;
+    const int count = std::max(1, g->d.count);
+    cudaStream_t cs = nullptr;
+    e = cudaMallocHost((void**)&r->seeds_pinned, sizeof(uint64_t) * (size_t)count);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        mis_replay_destroy(r);
+        return set_cuda_error(e, "capture setup");
+    }
+    // the graph's memcpy node reads this private pinned copy at every replay
+    std::memcpy(r->seeds_pinned, seeds, sizeof(uint64_t) * (size_t)count);
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int rc = MIS_OK;
+    if (e == cudaSuccess) {
+        rc = solve_in(g, g->d.ws, r->seeds_pinned, r->seeds_pinned, out_status, cs, 0);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+        r->graph = graph;
+        if (rc == MIS_OK && ee != cudaSuccess) rc = set_cuda_error(ee, "stream capture");
+    } else {
+        rc = set_cuda_error(e, "stream capture");
+    }
+    if (rc == MIS_OK) {
+        e = cudaGraphInstantiate(&r->exec, r->graph, 0);
+        if (e != cudaSuccess) rc = set_cuda_error(e, "graph instantiation");
+    }
+    cudaStreamDestroy(cs);
+    if (rc != MIS_OK) {
+        mis_replay_destroy(r);
+        return rc;
+    }
+    *replay = r;
+    return MIS_OK;
+}
+
+int mis_replay_launch(mis_replay* r, void* stream) {
+    clear_error();
+    if (!r || !r->exec) return set_error(MIS_EINVAL, "null replay");
+    mis_graph* g = r->g;
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
+    cudaError_t e = cudaSetDevice(g->d.device);
+    if (e == cudaSuccess) e = cudaGraphLaunch(r->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_cuda_error(e, "graph launch");
+    g->last_stream = (cudaStream_t)stream;
+    g->last_path = r->path;
+    return MIS_OK;
+}
+
+void mis_replay_destroy(mis_replay* r) {
+    if (!r) return;
+    if (r->g) cudaSetDevice(r->g->d.device);
+    if (r->exec) cudaGraphExecDestroy(r->exec);
+    if (r->graph) cudaGraphDestroy(r->graph);
+    if (r->seeds_pinned) cudaFreeHost(r->seeds_pinned);
+    delete r;
 }
 
 void mis_destroy(mis_graph* g) {

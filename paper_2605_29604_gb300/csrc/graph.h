@@ -70,6 +70,10 @@ struct GraphData {
     int32_t* col_sel = nullptr;
     int32_t* split = nullptr;
     int4* order0 = nullptr;       // round-0 row records grouped by bin
+    uint8_t* r0class = nullptr;   // round-0 classes (with a degree-ordered adjacency)
+    int32_t* sure_out = nullptr;  // sure round-0 exclusions
+    int32_t n_sure_in = 0;
+    int32_t n_sure_out = 0;
     int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};
     int32_t n_isolated = 0;
     int32_t thr[4] = {0, 0, 0, 0};
@@ -98,6 +102,15 @@ struct mis_graph {
     std::mutex mu;
     std::atomic<int> inflight{0};       // served requests not yet finished
     std::atomic<bool> destroy_pending{false};
+};
+
+// A captured solve (mis_capture): an executable CUDA graph of one solve.
+struct mis_replay {
+    mis_graph* g = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t* seeds_pinned = nullptr;  // the captured seeds, read by every replay
+    int32_t path = 0;                  // round kernel captured
 };
 
 namespace tcmis {

@@ -11,10 +11,12 @@ namespace tcmis {
 // batch padding vertices are out.  Isolated vertices have no neighbour to
 // compare with, so every round-0 selection test accepts them: with
 // isolated_in they are written in the MIS right away (the CSR kernel keeps
-// them out of its worklists), else they get a fixed key and are decided in
-// round 0 like every other vertex.  Grid-stride over the whole launch.
+// them out of its worklists), and so are the sure round-0 candidates of
+// a.r0class (class 1); else isolated vertices get a fixed key and are decided
+// in round 0 like every other vertex.  Grid-stride over the whole launch.
 __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
                                            bool isolated_in) {
+    const uint8_t* r0class = isolated_in ? a.r0class : nullptr;
     const uint32_t iso = isolated_in ? (kKeyIsolated | kWordInSet) : kKeyIsolated;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthreads = (long long)gridDim.x * blockDim.x;
@@ -39,6 +41,16 @@ __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
             } else {
                 for (int k = 0; k < 5; ++k) r[k] = (v + k <= n) ? a.rp[v + k] : 0;
             }
+            // class-1 flags of the four vertices (bytes of one aligned word)
+            uint32_t sure = 0;
+            if (r0class) {
+                if (v + 4 <= n) {
+                    sure = *reinterpret_cast<const uint32_t*>(r0class + v);
+                } else {
+                    for (int k = 0; k < 4; ++k)
+                        if (v + k < n) sure |= (uint32_t)r0class[v + k] << (8 * k);
+                }
+            }
             uint32_t w[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -46,6 +58,7 @@ __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
                 const int deg = r[k + 1] - r[k];
                 w[k] = u >= n ? kWordOut
                               : (deg ? eq1_key(dbar0, deg, smix0, (uint32_t)u) : iso);
+                if (((sure >> (8 * k)) & 0xFFu) == 1u) w[k] |= kWordInSet;
             }
             *reinterpret_cast<uint4*>(a.word + v) = make_uint4(w[0], w[1], w[2], w[3]);
         }
@@ -71,6 +84,7 @@ __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
                     w = eq1_key(dbar, deg, mix64(a.seg.seed[g]), (uint32_t)local);
                 }
             }
+            if (r0class && r0class[v] == 1) w |= kWordInSet;
         }
         a.word[v] = w;
     }

@@ -45,6 +45,14 @@ struct SolveArgs {
     const int4* order0 = nullptr;     // round-0 records: real non-isolated vertices by bin
     int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};  // bin j occupies [bin_off[j], bin_off[j+1])
     int32_t n_isolated = 0;           // real vertices of degree 0 (not in order0)
+    // Round-0 decisions known at create time (see build_round0_classes):
+    // r0class[v] = 1 marks a sure round-0 candidate (written in the MIS at
+    // init), sure_out lists the sure round-0 exclusions (written out in
+    // round 0's Phase 2); neither is in order0.  Null / 0 when unused.
+    const uint8_t* r0class = nullptr;
+    const int32_t* sure_out = nullptr;
+    int32_t n_sure_in = 0;
+    int32_t n_sure_out = 0;
     int32_t pending = 0;              // 1: Phase 1 lists its non-candidates for Phase 2
                                       // (in wlp); 0: Phase 2 triages W_r itself
     // tile-CSR (used by the tile kernels only)
@@ -75,12 +83,29 @@ cudaError_t launch_csr_solve(const SolveArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_csr_solve_single(const SolveArgs& a, cudaStream_t s);
 int csr_max_coresident_blocks(int device);
 int csr_block_size();
+// Where round 0's vertices go: order0 bins, or decided without a test.
+struct Round0Plan {
+    int32_t bin_off[6];   // order0 bin j occupies [bin_off[j], bin_off[j+1])
+    int32_t n_isolated;   // degree 0: in the MIS at init
+    int32_t n_sure_in;    // r0class 1: in the MIS at init
+    int32_t n_sure_out;   // r0class 2: listed in sure_out
+};
+
 // Round-0 row records grouped by degree bin (thr: inclusive upper degree of
-// bins 0..3; split: selection-prefix lengths, nullable = whole rows);
-// isolated vertices are left out and counted in *n_isolated.
-cudaError_t build_bins(const int32_t* rp, const int32_t* split, int32_t n, const SegTable& seg,
-                       const int32_t thr[4], int4* order0, int32_t bin_off[6],
-                       int32_t* n_isolated, cudaStream_t s);
+// bins 0..3; split: selection-prefix lengths, nullable = whole rows).
+// Isolated vertices and the classes of r0class (nullable) are left out of
+// order0; the sure exclusions are listed in sure_out.
+cudaError_t build_bins(const int32_t* rp, const int32_t* split, const uint8_t* r0class,
+                       int32_t n, const SegTable& seg, const int32_t thr[4], int4* order0,
+                       int32_t* sure_out, Round0Plan* plan, cudaStream_t s);
+
+// Create-time round-0 classes from the degree-ordered rows (col_sel, split):
+// 1 = sure candidate (empty selection prefix: every neighbour has degree >=
+// deg + 2, so none can outrank it, whatever the seed); 2 = sure exclusion (not
+// class 1, with a class-1 neighbour); 0 = the rest (tested in round 0).
+cudaError_t build_round0_classes(const int32_t* rp, const int32_t* col_sel, const int32_t* split,
+                                 int32_t n, const SegTable& seg, uint8_t* r0class,
+                                 cudaStream_t s);
 
 // kernels_util.cu
 cudaError_t launch_validate(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs,

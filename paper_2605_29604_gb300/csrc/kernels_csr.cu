@@ -594,8 +594,9 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
         }))
         return;
 
-    // isolated vertices were decided at init but belong to round 0's alive set
-    const int iso = a.n_isolated;
+    // vertices decided without a test (isolated ones and sure candidates at
+    // init, sure exclusions in round 0's Phase 2) belong to round 0's alive set
+    const int decided0 = a.n_isolated + a.n_sure_in + a.n_sure_out;
     WarpSched ws;
     ws.gw = (int)(blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32);
     ws.nwarps = (int)(nblocks * (blockDim.x / 32));
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     for (int r = 0;; ++r) {
         int total = 0;
         for (int j = 0; j < kBins; ++j) total += s_cnt[j];
-        if (!(total > 0 || (r == 0 && iso > 0))) break;
+        if (!(total > 0 || (r == 0 && decided0 > 0))) break;
         if (r >= a.max_rounds) {
             if (threadIdx.x == 0) atomicCAS(&ctl->err, 0, kErrInternal);
             return;
@@ -630,13 +631,19 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
             return;
 
         // ---- Phase 2+3: exclusion test, state update, compaction
+        if (r == 0) {
+            // the sure exclusions: neighbours of sure candidates
+            const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+            const long long nthreads = (long long)nblocks * blockDim.x;
+            for (long long i = tid; i < a.n_sure_out; i += nthreads) a.word[a.sure_out[i]] = kWordOut;
+        }
         if (kPending)
             exclude_phase<true>(a, a.wlp, s_pcnt, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next,
                                 dst, wbuf, wscan);
         else
             exclude_phase<false>(a, src, s_cnt, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next, dst,
                                  wbuf, wscan);
-        const int cur = total + (r == 0 ? iso : 0);
+        const int cur = total + (r == 0 ? decided0 : 0);
         if (!grid_barrier(
                 ctl, nblocks, a.spin_cap,
                 [ctl, times, rr, cur]() {
@@ -691,12 +698,14 @@ int csr_max_coresident_blocks(int device) {
 // ---------------------------------------------------------------- degree bins
 //
 // order0 = the round-0 records: every real vertex of degree >= 1 (batch
-// padding excluded), grouped by bin, ascending id inside a bin.  Two kernels:
-// per-block class counts (the five bins, then isolated vertices), then (after
-// the host turns the counts into offsets) a stable scatter.  Blocks own
-// contiguous vertex ranges.
+// padding excluded) that round 0 has to test, grouped by bin, ascending id
+// inside a bin; sure_out = the sure round-0 exclusions, ascending.  Two
+// kernels: per-block class counts, then (after the host turns the counts into
+// offsets) a stable scatter.  Blocks own contiguous vertex ranges.
 
-constexpr int kClasses = kBins + 1;  // bins 0..4, then isolated
+// classes: bins 0..4, then isolated, sure candidates, sure exclusions
+constexpr int kIsolated = kBins, kSureIn = kBins + 1, kSureOut = kBins + 2;
+constexpr int kClasses = kBins + 3;
 
 struct BinThr {
     int32_t t[kBins - 1];
@@ -715,23 +724,27 @@ __device__ __forceinline__ bool is_real(const SegTable& seg, long long v) {
     return (int)v - seg.voff[g] < seg.nv[g];
 }
 
-// Class of vertex v: its bin, kBins when isolated, -1 for batch padding.
-__device__ __forceinline__ int class_of(const SegTable& seg, const int32_t* rp, long long v,
-                                        const BinThr& thr) {
+// Class of vertex v (-1 for batch padding).
+__device__ __forceinline__ int class_of(const SegTable& seg, const int32_t* rp,
+                                        const uint8_t* r0class, long long v, const BinThr& thr) {
     if (!is_real(seg, v)) return -1;
     const int deg = rp[v + 1] - rp[v];
-    return deg == 0 ? kBins : bin_of(deg, thr);
+    if (deg == 0) return kIsolated;
+    if (r0class && r0class[v] == 1) return kSureIn;
+    if (r0class && r0class[v] == 2) return kSureOut;
+    return bin_of(deg, thr);
 }
 
-__global__ void bin_count_kernel(const int32_t* __restrict__ rp, int32_t n, const SegTable seg,
-                                 const BinThr thr, int32_t* __restrict__ blkcnt) {
+__global__ void bin_count_kernel(const int32_t* __restrict__ rp, const uint8_t* __restrict__ r0class,
+                                 int32_t n, const SegTable seg, const BinThr thr,
+                                 int32_t* __restrict__ blkcnt) {
     __shared__ int c[kClasses];
     if (threadIdx.x < kClasses) c[threadIdx.x] = 0;
     __syncthreads();
     const long long v0 = (long long)n * blockIdx.x / gridDim.x;
     const long long v1 = (long long)n * (blockIdx.x + 1) / gridDim.x;
     for (long long v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-        const int j = class_of(seg, rp, v, thr);
+        const int j = class_of(seg, rp, r0class, v, thr);
         if (j >= 0) atomicAdd(&c[j], 1);
     }
     __syncthreads();
@@ -740,10 +753,11 @@ __global__ void bin_count_kernel(const int32_t* __restrict__ rp, int32_t n, cons
 
 // blockDim.x must be 256
 __global__ void bin_scatter_kernel(const int32_t* __restrict__ rp,
-                                   const int32_t* __restrict__ split, int32_t n,
+                                   const int32_t* __restrict__ split,
+                                   const uint8_t* __restrict__ r0class, int32_t n,
                                    const SegTable seg, const BinThr thr,
                                    const int32_t* __restrict__ blkoff,
-                                   int4* __restrict__ order0) {
+                                   int4* __restrict__ order0, int32_t* __restrict__ sure_out) {
     __shared__ int wsum[8][kClasses];
     __shared__ int run[kClasses];
     const unsigned lane = lane_id();
@@ -754,7 +768,7 @@ __global__ void bin_scatter_kernel(const int32_t* __restrict__ rp,
     const long long v1 = (long long)n * (blockIdx.x + 1) / gridDim.x;
     for (long long c0 = v0; c0 < v1; c0 += blockDim.x) {
         const long long v = c0 + threadIdx.x;
-        const int j = v < v1 ? class_of(seg, rp, v, thr) : -1;
+        const int j = v < v1 ? class_of(seg, rp, r0class, v, thr) : -1;
         int rank = 0;
         for (int b = 0; b < kClasses; ++b) {
             const unsigned m = __ballot_sync(0xFFFFFFFFu, j == b);
@@ -762,11 +776,15 @@ __global__ void bin_scatter_kernel(const int32_t* __restrict__ rp,
             if (lane == 0) wsum[w][b] = __popc(m);
         }
         __syncthreads();
-        if (j >= 0 && j < kBins) {
+        if (j >= 0 && (j < kBins || j == kSureOut)) {
             int off = run[j];
             for (int x = 0; x < w; ++x) off += wsum[x][j];
-            const int b = rp[v], e = rp[v + 1];
-            order0[off + rank] = make_int4((int)v, b, split ? b + split[v] : e, e);
+            if (j == kSureOut) {
+                sure_out[off + rank] = (int32_t)v;
+            } else {
+                const int b = rp[v], e = rp[v + 1];
+                order0[off + rank] = make_int4((int)v, b, split ? b + split[v] : e, e);
+            }
         }
         __syncthreads();
         if (threadIdx.x < kClasses) {
@@ -778,11 +796,10 @@ __global__ void bin_scatter_kernel(const int32_t* __restrict__ rp,
     }
 }
 
-cudaError_t build_bins(const int32_t* rp, const int32_t* split, int32_t n, const SegTable& seg,
-                       const int32_t thr[4], int4* order0, int32_t bin_off[6],
-                       int32_t* n_isolated, cudaStream_t s) {
-    for (int j = 0; j <= kBins; ++j) bin_off[j] = 0;
-    *n_isolated = 0;
+cudaError_t build_bins(const int32_t* rp, const int32_t* split, const uint8_t* r0class,
+                       int32_t n, const SegTable& seg, const int32_t thr[4], int4* order0,
+                       int32_t* sure_out, Round0Plan* plan, cudaStream_t s) {
+    *plan = Round0Plan{};
     if (n == 0) return cudaSuccess;
     const int blocks = (int)std::min<long long>(1024, ((long long)n + 255) / 256);
     BinThr t;
@@ -791,7 +808,7 @@ cudaError_t build_bins(const int32_t* rp, const int32_t* split, int32_t n, const
     cudaError_t e = dev_alloc((void**)&d_cnt, sizeof(int32_t) * blocks * kClasses);
     if (e != cudaSuccess) return e;
     std::vector<int32_t> h((size_t)blocks * kClasses);
-    bin_count_kernel<<<blocks, 256, 0, s>>>(rp, n, seg, t, d_cnt);
+    bin_count_kernel<<<blocks, 256, 0, s>>>(rp, r0class, n, seg, t, d_cnt);
     e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h.data(), d_cnt, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost, s);
@@ -802,15 +819,17 @@ cudaError_t build_bins(const int32_t* rp, const int32_t* split, int32_t n, const
             for (int j = 0; j < kClasses; ++j) tot[j] += h[(size_t)b * kClasses + j];
         int64_t acc = 0;
         for (int j = 0; j < kBins; ++j) {
-            bin_off[j] = (int32_t)acc;
+            plan->bin_off[j] = (int32_t)acc;
             acc += tot[j];
         }
-        bin_off[kBins] = (int32_t)acc;
-        *n_isolated = (int32_t)tot[kBins];
-        // running offsets per block into order0 (isolated vertices: not listed)
-        int64_t run[kClasses];
-        for (int j = 0; j < kBins; ++j) run[j] = bin_off[j];
-        run[kBins] = 0;
+        plan->bin_off[kBins] = (int32_t)acc;
+        plan->n_isolated = (int32_t)tot[kIsolated];
+        plan->n_sure_in = (int32_t)tot[kSureIn];
+        plan->n_sure_out = (int32_t)tot[kSureOut];
+        // running offsets per block: bins into order0, sure exclusions into
+        // sure_out (isolated vertices and sure candidates are not listed)
+        int64_t run[kClasses] = {};
+        for (int j = 0; j < kBins; ++j) run[j] = plan->bin_off[j];
         for (int b = 0; b < blocks; ++b)
             for (int j = 0; j < kClasses; ++j) {
                 const int32_t c = h[(size_t)b * kClasses + j];
@@ -820,13 +839,71 @@ cudaError_t build_bins(const int32_t* rp, const int32_t* split, int32_t n, const
         e = cudaMemcpyAsync(d_cnt, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice, s);
     }
     if (e == cudaSuccess) {
-        bin_scatter_kernel<<<blocks, 256, 0, s>>>(rp, split, n, seg, t, d_cnt, order0);
+        bin_scatter_kernel<<<blocks, 256, 0, s>>>(rp, split, r0class, n, seg, t, d_cnt, order0,
+                                                  sure_out);
         e = cudaGetLastError();
     }
     const cudaError_t se = cudaStreamSynchronize(s);  // also on error: nothing may still run
     if (e == cudaSuccess) e = se;
     dev_free(d_cnt);
     return e;
+}
+
+// ---------------------------------------------------------------- round-0 classes
+//
+// Eq. 1 ranks a vertex of degree <= deg(v) - 2 strictly above v for every
+// seed (the order kept by the degree-ordered rows, see kernels_order.cu).
+// So a vertex whose selection prefix is empty outranks all its neighbours: it
+// is a candidate of round 0 whatever the seed (class 1).  A vertex of another
+// class with a class-1 neighbour is outranked by it and has a candidate
+// neighbour: it is excluded in round 0 (class 2).  Such a neighbour has degree
+// <= deg(v) - 2, so it lies in v's selection prefix; a warp scans the prefix
+// and stops at the first one.  Round counts and alive sets are unchanged:
+// these vertices are decided in round 0 exactly as the tests would decide
+// them, only without running the tests.
+
+__global__ void round0_class_kernel(const int32_t* __restrict__ rp,
+                                    const int32_t* __restrict__ col_sel,
+                                    const int32_t* __restrict__ split, int32_t n,
+                                    const SegTable seg, uint8_t* __restrict__ r0class) {
+    const long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const unsigned lane = lane_id();
+    if (v >= n) return;
+    const int b = rp[v];
+    const int deg = rp[v + 1] - b;
+    const int pre = split[v];
+    uint8_t c = 0;
+    if (deg > 0 && is_real(seg, v)) {
+        if (pre == 0) {
+            c = 1;
+        } else {
+            for (int p0 = b; p0 < b + pre; p0 += 32) {
+                const int p = p0 + (int)lane;
+                bool hit = false;
+                if (p < b + pre) {
+                    const int u = col_sel[p];
+                    hit = split[u] == 0 && rp[u + 1] > rp[u];
+                }
+                if (__any_sync(0xFFFFFFFFu, hit)) {
+                    c = 2;
+                    break;
+                }
+            }
+        }
+    }
+    if (lane == 0) r0class[v] = c;
+}
+
+cudaError_t build_round0_classes(const int32_t* rp, const int32_t* col_sel, const int32_t* split,
+                                 int32_t n, const SegTable& seg, uint8_t* r0class,
+                                 cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const long long threads = 32LL * n;
+    round0_class_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(rp, col_sel, split, n,
+                                                                         seg, r0class);
+    cudaError_t e = cudaGetLastError();
+    const cudaError_t se = cudaStreamSynchronize(s);
+    return e != cudaSuccess ? e : se;
 }
 
 }  // namespace tcmis

@@ -59,7 +59,8 @@ class mis_stats(ctypes.Structure):
                 ("tile", ctypes.c_int32), ("csr_pending", ctypes.c_int32), ("ntiles", ctypes.c_int64),
                 ("alive_sum", ctypes.c_int64), ("mis_size", ctypes.c_int64),
                 ("alive_per_round", ctypes.c_int64 * 64), ("init_ns", ctypes.c_int64),
-                ("select_ns", ctypes.c_int64 * 64), ("exclude_ns", ctypes.c_int64 * 64)]
+                ("select_ns", ctypes.c_int64 * 64), ("exclude_ns", ctypes.c_int64 * 64),
+                ("sure_in", ctypes.c_int64), ("sure_out", ctypes.c_int64)]
 
 
 class mis_tuning(ctypes.Structure):
@@ -119,6 +120,12 @@ def lib():
         L.mis_tiles_ex.restype = ctypes.c_int
         L.mis_set_csr_bins.argtypes = [P, P]
         L.mis_set_csr_bins.restype = ctypes.c_int
+        L.mis_capture.argtypes = [P, P, P, ctypes.POINTER(P)]
+        L.mis_capture.restype = ctypes.c_int
+        L.mis_replay_launch.argtypes = [P, P]
+        L.mis_replay_launch.restype = ctypes.c_int
+        L.mis_replay_destroy.argtypes = [P]
+        L.mis_replay_destroy.restype = None
         L.mis_set_csr_pending.argtypes = [P, i32]
         L.mis_set_csr_pending.restype = ctypes.c_int
         L.mis_destroy.argtypes = [P]
@@ -151,7 +158,7 @@ def lib():
 EXPORTED = [
     "mis_options_init", "mis_create", "mis_create_ex", "mis_create_batch", "mis_graph_count",
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
-    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
+    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
     "mis_solve_noalloc",
 ]
@@ -270,6 +277,24 @@ def mis_set_path(h, path, threads_per_row=0):
 def mis_set_csr_bins(h, bounds):
     b = np.ascontiguousarray(np.asarray(bounds, dtype=np.int32))
     return _check(lib().mis_set_csr_bins(h, _ptr(b)))
+
+
+def mis_capture(h, seeds, out_status_dev):
+    """Capture one solve of `h` (seeds: one per graph; out_status_dev: device
+    pointer) into a replayable CUDA graph; returns the replay handle."""
+    s = np.ascontiguousarray(np.atleast_1d(np.asarray(seeds, dtype=np.uint64)))
+    r = ctypes.c_void_p()
+    _check(lib().mis_capture(h, _ptr(s), ctypes.c_void_p(out_status_dev) if out_status_dev else None,
+                             ctypes.byref(r)))
+    return r
+
+
+def mis_replay_launch(r, stream):
+    return _check(lib().mis_replay_launch(r, ctypes.c_void_p(stream) if stream else None))
+
+
+def mis_replay_destroy(r):
+    lib().mis_replay_destroy(r)
 
 
 def mis_set_csr_pending(h, pending):

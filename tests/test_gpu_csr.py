@@ -111,6 +111,45 @@ def test_csr_pending_rejects_bad_mode():
         native.mis_destroy(h)
 
 
+def _sure_sets(g):
+    """Round-0 decisions that need no test, from their definition: a vertex
+    whose neighbours all have degree >= deg + 2 outranks every neighbour under
+    Eq. 1 (sure candidate); a vertex with such a neighbour is excluded."""
+    n, rp, col = g
+    rp = rp.astype(np.int64)
+    deg = np.diff(rp)
+    if len(col) == 0:
+        return 0, 0
+    src = np.repeat(np.arange(n), deg)
+    outranked = (deg[col] >= deg[src] + 2)
+    nz = deg > 0
+    all_lower = np.zeros(n, dtype=bool)
+    all_lower[nz] = np.logical_and.reduceat(outranked, rp[:-1][nz])
+    sure_in = nz & all_lower
+    has = np.zeros(n, dtype=bool)
+    has[nz] = np.logical_or.reduceat(sure_in[col], rp[:-1][nz])
+    sure_out = nz & ~sure_in & has
+    return int(sure_in.sum()), int(sure_out.sum())
+
+
+@pytest.mark.parametrize("order_rows", [0, 1, 2])
+@pytest.mark.parametrize("name", ["rmat14", "star_hub", "er_10k", "k_ab", "grid", "path", "empty"])
+def test_round0_sure_sets(name, order_rows):
+    """Vertices decided at create time: counts match their definition, and
+    the result, rounds and alive sets still match Algorithm 2."""
+    g = graph(name)
+    h = create(g, order_rows=order_rows)
+    try:
+        for pending in (0, 1):
+            native.mis_set_csr_pending(h, pending)
+            got, st = gpu_solve(h, [13], native.MIS_PATH_CSR, 0)
+            assert_same(g, 13, got, st)
+            want = _sure_sets(g) if order_rows else (0, 0)
+            assert (st.sure_in, st.sure_out) == want
+    finally:
+        native.mis_destroy(h)
+
+
 @pytest.mark.parametrize("bounds", [(2, 5, 9, 20), (-1, 3, 3, 3), (0, 0, 100000, 100000),
                                     (1, 2, 3, 4), (-1, -1, -1, 2)])
 def test_csr_custom_bins(bounds):
