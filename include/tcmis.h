@@ -185,6 +185,22 @@ int mis_solve(mis_graph *g, uint64_t seed, uint8_t *out_status);
 int mis_solve_ex(mis_graph *g, const uint64_t *seeds, uint8_t *out_status, void *stream);
 
 /*
+ * Several solves of one graph in one launch: k solves (1 <= k <= 8) with
+ * seeds[0..k-1] (HOST array).  Each solve's result is the set mis_solve_ex
+ * with that seed gives; solve s is written to out_status + s * n (DEVICE
+ * buffer of k * n bytes).  The k solves share the graph and one worklist and
+ * run their rounds of Algorithm 2 in lock step: with k right-hand sides the
+ * exclusion product of Sec. 3.1 (Phase 2, N_c = A x C) becomes A x [C_1 ..
+ * C_k], and every neighbour gather serves all k solves.  mis_get_stats then
+ * reports rounds = the largest round count of the k solves, alive sets and
+ * MIS sizes summed over the solves.  Single-graph handles only (MIS_EINVAL for
+ * a batch, or k outside [1, 8]); MIS_EBUSY while served requests on `g` are in
+ * flight; the extra device memory (32 bytes per vertex) is kept by the handle.
+ */
+int mis_solve_multi_ex(mis_graph *g, int32_t k, const uint64_t *seeds, uint8_t *out_status,
+                       void *stream);
+
+/*
  * Captured solves (no counterpart in the paper: launch-overhead removal for
  * repeated solves, e.g. a batched union solved again and again).
  * mis_capture records what mis_solve_ex(g, seeds, out_status, stream) enqueues

@@ -348,6 +348,7 @@ void free_graph(mis_graph* g) {
     if (d.seeds_host) cudaFreeHost(d.seeds_host);
     free_tiles(d);
     dfree(d.order0);
+    dfree(d.word8);
     dfree(d.r0class);
     dfree(d.sure_out);
     dfree(d.col_sel);
@@ -395,6 +396,30 @@ int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_
 }
 
 // Enqueue one solve on stream s in the handle's own workspace.
+int solve_multi_in(mis_graph* g, Workspace& w, uint32_t* word8, int k, const uint64_t* seeds,
+                   uint8_t* out_dev, cudaStream_t s, int blocks) {
+    GraphData& d = g->d;
+    cudaError_t e = cudaSetDevice(d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    MultiSeeds ms{};
+    for (int i = 0; i < k; ++i) ms.seed[i] = seeds[i];
+    SolveArgs a = make_args(g, w);
+    a.out = out_dev;
+    e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.times, 0, sizeof(PhaseTimes), s);
+    if (e != cudaSuccess) return set_cuda_error(e, "control reset");
+    if (d.n > 0) {
+        const int maxb = multi_max_coresident_blocks(d.device);
+        if (maxb <= 0) return set_error(MIS_EDEVICE, "no co-resident blocks for the multi kernel");
+        long long grid = ((long long)d.n + 255) / 256;
+        if (blocks > 0) grid = std::min<long long>(grid, blocks);
+        grid = std::max<long long>(1, std::min<long long>(grid, maxb));
+        e = launch_multi_solve(a, word8, k, ms, (int)grid, s);
+        if (e != cudaSuccess) return set_cuda_error(e, "multi-seed kernel launch");
+    }
+    return MIS_OK;
+}
+
 int solve_async(mis_graph* g, const uint64_t* seeds, uint8_t* out_dev, cudaStream_t s) {
     const int rc = solve_in(g, g->d.ws, seeds, g->d.seeds_host, out_dev, s, 0);
     if (rc != MIS_OK) return rc;
@@ -1125,6 +1150,31 @@ int mis_keys_ex(mis_graph* g, const uint64_t* seeds, uint32_t* out_key, void* st
     if (e == cudaSuccess) e = launch_keys(a, out_key, s);
     if (e != cudaSuccess) return set_cuda_error(e, "keys");
     g->last_stream = s;
+    return MIS_OK;
+}
+
+int mis_solve_multi_ex(mis_graph* g, int32_t k, const uint64_t* seeds, uint8_t* out_status,
+                       void* stream) {
+    clear_error();
+    if (!g || !seeds) return set_error(MIS_EINVAL, "null graph or seeds");
+    if (k < 1 || k > kMaxMulti) return set_error(MIS_EINVAL, "k must be in [1, 8]");
+    if (g->d.count != 0) return set_error(MIS_EINVAL, "multi-seed solves take a single graph");
+    if (g->d.n > 0 && !out_status) return set_error(MIS_EINVAL, "null out_status");
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
+    GraphData& d = g->d;
+    cudaError_t e = cudaSetDevice(d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    if (!d.word8) {
+        if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+        const int64_t cap = (d.n + 15) / 16 * 16;
+        if ((e = dalloc(&d.word8, (int64_t)kMaxMulti * cap, &d.footprint)) != cudaSuccess)
+            return set_cuda_error(e, "multi-seed workspace");
+    }
+    const int rc = solve_multi_in(g, d.ws, d.word8, k, seeds, out_status, (cudaStream_t)stream, 0);
+    if (rc != MIS_OK) return rc;
+    g->last_stream = (cudaStream_t)stream;
+    g->last_path = MIS_PATH_CSR;
     return MIS_OK;
 }
 

@@ -51,6 +51,8 @@ struct Ctl {
     int bcnt[4][kBins];       // per-bin worklist sizes, ring indexed by round & 3
     int pcnt[4][kBins];       // per-bin pending-list sizes, ring indexed by round & 3
     int alive_acc[4];         // |A| at round start, ring indexed by round & 3
+    unsigned long long alive_acc64[4];  // the same, summed over the solves of a
+                                        // multi-seed launch, ring indexed
 };
 
 // Phase timestamps of one solve (device %globaltimer, ns), written by the

@@ -72,6 +72,7 @@ struct GraphData {
     int4* order0 = nullptr;       // round-0 row records grouped by bin
     uint8_t* r0class = nullptr;   // round-0 classes (with a degree-ordered adjacency)
     int32_t* sure_out = nullptr;  // sure round-0 exclusions
+    uint32_t* word8 = nullptr;    // multi-seed solves: 8 words per vertex (lazily)
     int32_t n_sure_in = 0;
     int32_t n_sure_out = 0;
     int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};
@@ -124,6 +125,10 @@ int solve_async(mis_graph* g, const uint64_t* seeds, uint8_t* out_dev, cudaStrea
 // at most that many blocks.
 int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_pinned,
              uint8_t* out_dev, cudaStream_t s, int blocks);
+// k multi-seed solves of single graph g on stream s in workspace w (word8:
+// kMaxMulti words per vertex; out_dev: k * n bytes); blocks as for solve_in.
+int solve_multi_in(mis_graph* g, Workspace& w, uint32_t* word8, int k, const uint64_t* seeds,
+                   uint8_t* out_dev, cudaStream_t s, int blocks);
 void free_graph(mis_graph* g);
 
 int autotune(mis_graph* g, int reps, mis_tuning* out);

@@ -21,6 +21,13 @@ struct SegTable {
     const uint64_t* seed = nullptr;    // per graph: seed
 };
 
+// Solves of one graph in one multi-seed launch (kernels_multi.cu): at most
+// kMaxMulti, one seed each.
+constexpr int kMaxMulti = 8;
+struct MultiSeeds {
+    uint64_t seed[kMaxMulti];
+};
+
 // Everything one persistent solve launch needs.
 struct SolveArgs {
     const int32_t* rp = nullptr;   // row_ptr, n+1
@@ -106,6 +113,13 @@ cudaError_t build_bins(const int32_t* rp, const int32_t* split, const uint8_t* r
 cudaError_t build_round0_classes(const int32_t* rp, const int32_t* col_sel, const int32_t* split,
                                  int32_t n, const SegTable& seg, uint8_t* r0class,
                                  cudaStream_t s);
+
+// kernels_multi.cu: k <= kMaxMulti solves of the graph of `a` (a.seg unused);
+// word8 holds kMaxMulti words per vertex (n padded to 16); a.out receives
+// k * n result bytes, solve s at a.out + s * n.
+cudaError_t launch_multi_solve(const SolveArgs& a, uint32_t* word8, int k,
+                               const MultiSeeds& seeds, int grid, cudaStream_t s);
+int multi_max_coresident_blocks(int device);
 
 // kernels_util.cu
 cudaError_t launch_validate(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs,

@@ -1,0 +1,403 @@
+// kernels_multi.cu -- K <= 8 solves of one graph in one persistent launch.
+//
+// The solves differ only in their seed, so they share the graph, its
+// degree-ordered rows, its round-0 classes (which do not depend on the seed)
+// and one worklist: a vertex stays on it while any solve has it undecided.
+// Each vertex holds one packed word per solve (the layout of common.cuh),
+// the K words of a vertex side by side in one 32-byte sector, so a neighbour
+// gather fetches the state of every solve at once and one row scan decides
+// the selection test (Phase 1) or the exclusion test (Phase 2) of Algorithm 2
+// for all solves that still have the vertex undecided.  Rounds run in lock
+// step; a solve that has finished has no undecided vertex and drops out of
+// every test.  The result of each solve is the one a single solve with its
+// seed gives (the rounds of each solve are exactly its own).
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+#include "worklist.cuh"
+
+namespace tcmis {
+
+namespace {
+
+constexpr int kMultiBlock = 512;
+constexpr int kMultiMinBlocksPerSm = 2;
+constexpr int kMultiWarps = kMultiBlock / 32;
+// rows per chunk, per lane-group width (1, 4, 16, 32 lanes per row)
+constexpr int kMChunk1 = 512, kMChunk4 = 256, kMChunk16 = 128, kMChunk32 = 64;
+
+// The eight words of vertex v (solves beyond K hold "out" and never count).
+__device__ __forceinline__ void load8(const uint32_t* word8, int v, uint32_t (&w)[kMaxMulti]) {
+    const uint4* p = reinterpret_cast<const uint4*>(word8 + (size_t)kMaxMulti * v);
+    const uint4 a = p[0], b = p[1];
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+}
+
+__device__ __forceinline__ void store8(uint32_t* word8, int v, const uint32_t (&w)[kMaxMulti]) {
+    uint4* p = reinterpret_cast<uint4*>(word8 + (size_t)kMaxMulti * v);
+    p[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    p[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// Solves with v undecided.
+__device__ __forceinline__ unsigned undecided_mask(const uint32_t (&w)[kMaxMulti]) {
+    unsigned m = 0;
+#pragma unroll
+    for (int s = 0; s < kMaxMulti; ++s) m |= ((w[s] >> 29) == 1u ? 1u : 0u) << s;
+    return m;
+}
+
+// Solves in which u (words wu) decides v's test: kSelect: u outranks v
+// (words wv; out words never do, in words always do), else: u is in the MIS.
+template <bool kSelect>
+__device__ __forceinline__ unsigned decides(const uint32_t (&wu)[kMaxMulti], int u,
+                                            const uint32_t (&wv)[kMaxMulti], int v) {
+    unsigned m = 0;
+#pragma unroll
+    for (int s = 0; s < kMaxMulti; ++s) {
+        const bool hit = kSelect ? (wu[s] > wv[s] || (wu[s] == wv[s] && u > v))
+                                 : wu[s] >= kWordInMin;
+        m |= (hit ? 1u : 0u) << s;
+    }
+    return m;
+}
+
+// Scan of the row [b, e) of v by the group of TPR lanes of this lane, for the
+// solves in `act` (the same for the whole group).  Returns the solves in
+// which some neighbour decides the test.  Warp-uniform loop.
+template <int TPR, bool kSelect>
+__device__ __forceinline__ unsigned group_scan8(const int32_t* __restrict__ col,
+                                                const uint32_t* __restrict__ word8, int b, int e,
+                                                int v, const uint32_t (&wv)[kMaxMulti],
+                                                unsigned act, unsigned glane) {
+    unsigned found = 0;
+    int p0 = (b & ~3) + 4 * (int)glane;
+    for (;;) {
+        unsigned hit = 0;
+        if ((act & ~found) != 0u && p0 < e) {
+            const int4 c = __ldg(reinterpret_cast<const int4*>(col + p0));
+            const int cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (p0 + q >= b && p0 + q < e) {
+                    uint32_t wu[kMaxMulti];
+                    load8(word8, cc[q], wu);
+                    hit |= decides<kSelect>(wu, cc[q], wv, v);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < TPR; o <<= 1) hit |= __shfl_xor_sync(0xFFFFFFFFu, hit, o);
+        found |= hit & act;
+        p0 += 4 * TPR;
+        const bool more = (act & ~found) != 0u && (p0 - 4 * (int)glane) < e;
+        if (!__any_sync(0xFFFFFFFFu, more)) break;
+    }
+    return found;
+}
+
+struct MultiCtx {
+    const SolveArgs& a;
+    uint32_t* word8;
+    int32_t* wbuf;
+};
+
+// Phase 1 over one bin at TPR lanes per row: for every row, the selection
+// test in each solve that has the row undecided; candidates are marked in.
+// Counts the undecided (vertex, solve) pairs into *alive.
+template <int TPR, int CH>
+__device__ __forceinline__ void select_bin8(const MultiCtx& x, const int4* __restrict__ list,
+                                            int cnt, WarpSched& ws, unsigned* grab,
+                                            unsigned long long* alive) {
+    constexpr int G = 32 / TPR;
+    if (cnt <= 0) return;
+    const unsigned lane = lane_id();
+    const unsigned glane = lane % TPR;
+    const unsigned gid = lane / TPR;
+    const ChunkPlan plan = plan_of<G, CH>(cnt, ws.nwarps);
+    unsigned count = 0;
+    for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps, grab)) {
+        int c0, c1;
+        plan.range(k, cnt, c0, c1, G);
+        for (int base = c0; base < c1; base += G) {
+            const int item = base + (int)gid;
+            const bool valid = item < c1;
+            const int4 rec = valid ? list[item] : make_int4(0, 0, 0, 0);
+            uint32_t wv[kMaxMulti];
+            unsigned act = 0;
+            if (valid) {
+                load8(x.word8, rec.x, wv);
+                act = undecided_mask(wv);
+            } else {
+#pragma unroll
+                for (int s = 0; s < kMaxMulti; ++s) wv[s] = 0u;
+            }
+            const unsigned blocked =
+                group_scan8<TPR, true>(x.a.col_sel, x.word8, rec.y, valid ? rec.z : 0, rec.x, wv,
+                                       act, glane);
+            const unsigned cand = act & ~blocked;
+            if (glane == 0 && valid) {
+                count += __popc(act);
+                if (cand) {
+#pragma unroll
+                    for (int s = 0; s < kMaxMulti; ++s)
+                        if ((cand >> s) & 1u) wv[s] |= kWordInSet;
+                    store8(x.word8, rec.x, wv);
+                }
+            }
+        }
+    }
+    for (int o = 16; o; o >>= 1) count += __shfl_xor_sync(0xFFFFFFFFu, count, o);
+    if (lane == 0 && count) atomicAdd(alive, (unsigned long long)count);
+}
+
+// Phase 2+3 over one bin: in each solve that still has the row undecided (a
+// non-candidate), the exclusion test; the row stays on the worklist while
+// some solve keeps it undecided.
+template <int TPR, int CH>
+__device__ __forceinline__ void exclude_bin8(const MultiCtx& x, const int4* __restrict__ list,
+                                             int cnt, WarpSched& ws, unsigned* grab, int* next,
+                                             int4* __restrict__ dst) {
+    constexpr int G = 32 / TPR;
+    if (cnt <= 0) return;
+    const unsigned lane = lane_id();
+    const unsigned glane = lane % TPR;
+    const unsigned gid = lane / TPR;
+    const ChunkPlan plan = plan_of<G, CH>(cnt, ws.nwarps);
+    int fill = 0;
+    for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps, grab)) {
+        int c0, c1;
+        plan.range(k, cnt, c0, c1, G);
+        for (int base = c0; base < c1; base += G) {
+            const int item = base + (int)gid;
+            const bool valid = item < c1;
+            const int4 rec = valid ? list[item] : make_int4(0, 0, 0, 0);
+            uint32_t wv[kMaxMulti];
+            unsigned und = 0;
+            if (valid) {
+                load8(x.word8, rec.x, wv);
+                und = undecided_mask(wv);
+            } else {
+#pragma unroll
+                for (int s = 0; s < kMaxMulti; ++s) wv[s] = 0u;
+            }
+            const unsigned excl = group_scan8<TPR, false>(x.a.col_sel, x.word8, rec.y,
+                                                          valid ? rec.w : 0, rec.x, wv, und, glane);
+            const bool lead = glane == 0 && valid;
+            if (lead && excl) {
+#pragma unroll
+                for (int s = 0; s < kMaxMulti; ++s)
+                    if ((excl >> s) & 1u) wv[s] = kWordOut;
+                store8(x.word8, rec.x, wv);
+            }
+            fill = stage_keep(lead && (und & ~excl) != 0u, item, x.wbuf, fill);
+            fill = flush_if_full(x.wbuf, fill, G, list, next, dst);
+        }
+    }
+    flush_stage(x.wbuf, fill, list, next, dst);
+}
+
+// Lanes per row of a bin of base width BASE (as in the single-solve kernel:
+// from round 1 on, the widest group at which the bin fits one grid pass).
+template <int BASE>
+__device__ __forceinline__ int multi_lanes(int cnt, bool late, int nwarps) {
+    if (!late) return BASE;
+    const long long lanes = 32LL * nwarps;
+    if (BASE < 32 && 32LL * cnt <= lanes) return 32;
+    if (BASE < 16 && 16LL * cnt <= lanes) return 16;
+    if (BASE < 4 && 4LL * cnt <= lanes) return 4;
+    return BASE;
+}
+
+template <int BASE, int CH>
+__device__ __forceinline__ void select_at8(const MultiCtx& x, const int4* list, int cnt, bool late,
+                                           WarpSched& ws, unsigned* grab,
+                                           unsigned long long* alive) {
+    switch (multi_lanes<BASE>(cnt, late, ws.nwarps)) {
+        case 32: select_bin8<32, kMChunk32>(x, list, cnt, ws, grab, alive); break;
+        case 16: select_bin8<16, kMChunk16>(x, list, cnt, ws, grab, alive); break;
+        case 4: select_bin8<4, kMChunk4>(x, list, cnt, ws, grab, alive); break;
+        default: select_bin8<BASE, CH>(x, list, cnt, ws, grab, alive);
+    }
+}
+
+template <int BASE, int CH>
+__device__ __forceinline__ void exclude_at8(const MultiCtx& x, const int4* list, int cnt,
+                                            bool late, WarpSched& ws, unsigned* grab, int* next,
+                                            int4* dst) {
+    switch (multi_lanes<BASE>(cnt, late, ws.nwarps)) {
+        case 32: exclude_bin8<32, kMChunk32>(x, list, cnt, ws, grab, next, dst); break;
+        case 16: exclude_bin8<16, kMChunk16>(x, list, cnt, ws, grab, next, dst); break;
+        case 4: exclude_bin8<4, kMChunk4>(x, list, cnt, ws, grab, next, dst); break;
+        default: exclude_bin8<BASE, CH>(x, list, cnt, ws, grab, next, dst);
+    }
+}
+
+// Eq. 1 words of every vertex for the K seeds (solves beyond K: out); the
+// round-0 decisions known at create time are written here too (isolated and
+// sure candidates: in, in every solve).
+__device__ __forceinline__ void init_words8(const SolveArgs& a, uint32_t* word8, int k,
+                                            const uint64_t (&smix)[kMaxMulti]) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const int32_t n = a.n;
+    const int32_t n_words = (n + 15) / 16 * 16;
+    const float dbar = n > 0 ? average_degree(a.rp[n], n) : 0.f;
+    for (long long v = tid; v < n_words; v += nthreads) {
+        uint32_t w[kMaxMulti];
+        const int deg = v < n ? a.rp[v + 1] - a.rp[v] : 0;
+        // in at init in every solve: an in word blocks and excludes whatever
+        // its key bits, so these words need no key
+        const bool in0 = v < n && (deg == 0 || (a.r0class && a.r0class[v] == 1));
+#pragma unroll
+        for (int s = 0; s < kMaxMulti; ++s) {
+            if (v >= n || s >= k) w[s] = kWordOut;
+            else if (in0) w[s] = kWordInMin;
+            else w[s] = eq1_key(dbar, deg, smix[s], (uint32_t)v);
+        }
+        store8(word8, (int)v, w);
+    }
+}
+
+__global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
+    multi_solve_kernel(const SolveArgs a, uint32_t* word8, int k, const MultiSeeds seeds) {
+    __shared__ int32_t s_stage[kMultiWarps][kStageMax];
+    __shared__ int s_cnt[kBins];
+    const unsigned nblocks = gridDim.x;
+    Ctl* ctl = a.ctl;
+    PhaseTimes* times = a.times;
+    const MultiCtx x{a, word8, s_stage[threadIdx.x / 32]};
+    grid_barrier_start();
+    if (threadIdx.x < kBins) s_cnt[threadIdx.x] = a.bin_off[threadIdx.x + 1] - a.bin_off[threadIdx.x];
+    if (times && blockIdx.x == 0 && threadIdx.x == 0) times->t[0] = global_ns();
+
+    // ---- init: Eq. 1 priorities of every solve
+    {
+        uint64_t smix[kMaxMulti];
+#pragma unroll
+        for (int s = 0; s < kMaxMulti; ++s) smix[s] = mix64(seeds.seed[s]);
+        init_words8(a, word8, k, smix);
+    }
+    if (!grid_barrier(ctl, nblocks, a.spin_cap, [times]() {
+            if (times) times->t[1] = global_ns();
+        }))
+        return;
+
+    const int decided0 = a.n_isolated + a.n_sure_in + a.n_sure_out;
+    WarpSched ws;
+    ws.gw = (int)(blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32);
+    ws.nwarps = (int)(nblocks * (blockDim.x / 32));
+    ws.base = 0;
+    const int* off = a.bin_off;
+    for (int r = 0;; ++r) {
+        int total = 0;
+        for (int j = 0; j < kBins; ++j) total += s_cnt[j];
+        if (!(total > 0 || (r == 0 && decided0 > 0))) break;
+        if (r >= a.max_rounds) {
+            if (threadIdx.x == 0) atomicCAS(&ctl->err, 0, kErrInternal);
+            return;
+        }
+        const int4* src = (r == 0) ? a.order0 : ((r & 1) ? a.wl1 : a.wl0);
+        int4* dst = ((r + 1) & 1) ? a.wl1 : a.wl0;
+        int* next = ctl->bcnt[(r + 1) & 3];
+        unsigned long long* acc = &ctl->alive_acc64[r & 3];
+        const int rr = r;
+        const bool late = r > 0;
+
+        // ---- Phase 1: selection test of every solve; hubs take a warp per row
+        unsigned* grab = ctl->grab[(2 * r) & 3];
+        select_at8<32, kMChunk32>(x, src + off[4], s_cnt[4], late, ws, &grab[4], acc);
+        select_at8<32, kMChunk32>(x, src + off[3], s_cnt[3], late, ws, &grab[3], acc);
+        select_at8<16, kMChunk16>(x, src + off[2], s_cnt[2], late, ws, &grab[2], acc);
+        select_at8<4, kMChunk4>(x, src + off[1], s_cnt[1], late, ws, &grab[1], acc);
+        select_at8<1, kMChunk1>(x, src + off[0], s_cnt[0], late, ws, &grab[0], acc);
+        if (!grid_barrier(ctl, nblocks, a.spin_cap, [ctl, times, rr]() {
+                if (times && rr < kStatRounds) times->t[2 + rr] = global_ns();
+                for (int j = 0; j < kBins; ++j) ctl->grab[(2 * rr + 2) & 3][j] = 0;
+            }))
+            return;
+
+        // ---- Phase 2+3: exclusion test, state update, compaction
+        if (r == 0) {
+            const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+            const long long nthreads = (long long)nblocks * blockDim.x;
+            const uint4 out4 = make_uint4(kWordOut, kWordOut, kWordOut, kWordOut);
+            for (long long i = tid; i < a.n_sure_out; i += nthreads) {
+                uint4* p = reinterpret_cast<uint4*>(word8 + (size_t)kMaxMulti * a.sure_out[i]);
+                p[0] = out4;
+                p[1] = out4;
+            }
+        }
+        grab = ctl->grab[(2 * r + 1) & 3];
+        exclude_at8<32, kMChunk32>(x, src + off[4], s_cnt[4], late, ws, &grab[4], &next[4], dst + off[4]);
+        exclude_at8<32, kMChunk32>(x, src + off[3], s_cnt[3], late, ws, &grab[3], &next[3], dst + off[3]);
+        exclude_at8<16, kMChunk16>(x, src + off[2], s_cnt[2], late, ws, &grab[2], &next[2], dst + off[2]);
+        exclude_at8<4, kMChunk4>(x, src + off[1], s_cnt[1], late, ws, &grab[1], &next[1], dst + off[1]);
+        exclude_at8<1, kMChunk1>(x, src + off[0], s_cnt[0], late, ws, &grab[0], &next[0], dst + off[0]);
+        const long long extra = r == 0 ? (long long)k * decided0 : 0;
+        if (!grid_barrier(
+                ctl, nblocks, a.spin_cap,
+                [ctl, times, rr, extra]() {
+                    // Phase 1 of this round summed its undecided pairs into
+                    // alive_acc64[rr & 3] before the previous barrier
+                    const unsigned long long cur = ctl->alive_acc64[rr & 3] + (unsigned long long)extra;
+                    ctl->alive_acc64[(rr + 2) & 3] = 0;
+                    if (times && rr < kStatRounds) times->t[2 + kStatRounds + rr] = global_ns();
+                    if (rr < kStatRounds) ctl->alive[rr] = (int)cur;
+                    ctl->alive_sum += cur;
+                    ctl->rounds = rr + 1;
+                    for (int j = 0; j < kBins; ++j) {
+                        ctl->grab[(2 * rr + 3) & 3][j] = 0;
+                        ctl->bcnt[(rr + 2) & 3][j] = 0;
+                    }
+                },
+                [next]() {
+                    for (int j = 0; j < kBins; ++j) s_cnt[j] = __ldcg(next + j);
+                }))
+            return;
+    }
+
+    // ---- output: out[s * n + v] = [v in the MIS of solve s]
+    if (a.out) {
+        const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        const long long nthreads = (long long)nblocks * blockDim.x;
+        unsigned in_cnt = 0;
+        for (long long v = tid; v < a.n; v += nthreads) {
+            uint32_t w[kMaxMulti];
+            load8(word8, (int)v, w);
+#pragma unroll
+            for (int s = 0; s < kMaxMulti; ++s) {
+                if (s < k) {
+                    const bool in = w[s] >= kWordInMin;
+                    a.out[(long long)s * a.n + v] = in;
+                    in_cnt += in;
+                }
+            }
+        }
+        for (int o = 16; o; o >>= 1) in_cnt += __shfl_xor_sync(0xFFFFFFFFu, in_cnt, o);
+        if (lane_id() == 0 && in_cnt) atomicAdd(&ctl->mis_size, (unsigned long long)in_cnt);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_multi_solve(const SolveArgs& a, uint32_t* word8, int k,
+                               const MultiSeeds& seeds, int grid, cudaStream_t s) {
+    void* args[] = {const_cast<SolveArgs*>(&a), &word8, &k, const_cast<MultiSeeds*>(&seeds)};
+    return cudaLaunchCooperativeKernel((const void*)multi_solve_kernel, dim3(grid),
+                                       dim3(kMultiBlock), args, 0, s);
+}
+
+int multi_max_coresident_blocks(int device) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)multi_solve_kernel,
+                                                      kMultiBlock, 0) != cudaSuccess)
+        return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return 0;
+    return per_sm * sms;
+}
+
+}  // namespace tcmis

@@ -9,9 +9,14 @@
 //   admit    queued requests, oldest first, while a slot is free and the
 //            workspace bytes of all admitted requests stay within the HBM
 //            budget (a request is always admitted when nothing runs);
-//   launch   each admitted request on its slot's stream: graphs of up to
-//            kSingleBlockMax vertices run the round kernel as one block
-//            through an ordinary launch, larger ones a cooperative grid of at
+//   group    queued requests on the same single graph (CSR path) ride one
+//            slot together, up to 8: one multi-seed launch solves them all
+//            (kernels_multi.cu), every neighbour gather serving each of them;
+//            only requests already queued are grouped, nothing waits for a
+//            group to fill;
+//   launch   each admitted request (or group) on its slot's stream: on a graph
+//            of up to kSingleBlockMax vertices as one block (a lone request
+//            through an ordinary launch), else as a cooperative grid of at
 //            most serve_blocks blocks (default: half the SMs), so that
 //            requests admitted while others run share the device with them.
 //
@@ -23,6 +28,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <list>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -38,6 +44,7 @@ namespace {
 
 constexpr int32_t kSingleBlockMax = 16384;  // vertices solved by one block
 constexpr int kDefaultSlots = 64;
+constexpr int kGroupScan = 1024;  // queue entries searched for a request's group
 
 int64_t now_ns() {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -65,7 +72,12 @@ struct Slot {
     uint64_t* seeds_pinned = nullptr;
     int32_t seeds_cap = 0;
     Ctl* ctl_pinned = nullptr;
-    Request* req = nullptr;
+    uint32_t* word8 = nullptr;     // multi-seed state, kMaxMulti words per vertex
+    int64_t word8_cap = 0;         // vertices
+    uint8_t* out_multi = nullptr;  // multi-seed results, kMaxMulti * n bytes
+    int64_t out_multi_cap = 0;     // bytes
+    Request* reqs[kMaxMulti] = {};
+    int nreq = 0;                  // requests riding this slot (0 = free)
     int64_t charge = 0;
 };
 
@@ -160,6 +172,8 @@ class Server {
         for (Slot& s : slots_) {
             if (s.stream) cudaStreamSynchronize(s.stream);
             ws_free(s.ws);
+            if (s.word8) cudaFree(s.word8);
+            if (s.out_multi) cudaFree(s.out_multi);
             if (s.pinned_out) cudaFreeHost(s.pinned_out);
             if (s.seeds_pinned) cudaFreeHost(s.seeds_pinned);
             if (s.ctl_pinned) cudaFreeHost(s.ctl_pinned);
@@ -203,10 +217,19 @@ class Server {
         return st;
     }
 
-    // Caller holds mu_.  Starts request r on slot s; MIS_OK or an error (the
-    // request is then finished with that error by the caller).
-    int launch_locked(Slot& s, Request* r) {
-        mis_graph* g = r->g;
+    // Bytes a slot holds for k requests on graph d.
+    static int64_t charge_for(const GraphData& d, int k) {
+        int64_t b = ws_bytes_for(d.n, d.count) + d.result_bytes;
+        if (k > 1) b += 4 * (int64_t)kMaxMulti * ((d.n + 15) / 16 * 16) + k * d.result_bytes;
+        return b;
+    }
+
+    // Starts the k requests rs (all on the same graph, taken off the queue
+    // and assigned to slot s) on slot s; MIS_OK or an error (the requests are
+    // then finished with that error by the caller).  Called by the scheduler
+    // thread without mu_: only that thread touches the slots.
+    int launch_unlocked(Slot& s, Request* const* rs, int k) {
+        mis_graph* g = rs[0]->g;
         GraphData& d = g->d;
         cudaError_t e = cudaSuccess;
         if (!s.stream) {
@@ -217,41 +240,94 @@ class Server {
         }
         if ((e = ws_reserve(s.ws, d.n, d.count)) != cudaSuccess)
             return set_cuda_error(e, "serving: workspace");
-        if (s.pinned_cap < d.result_bytes) {
+        const int64_t out_bytes = (int64_t)k * d.result_bytes;
+        if (s.pinned_cap < out_bytes) {
             if (s.pinned_out) cudaFreeHost(s.pinned_out);
             s.pinned_out = nullptr;
-            if ((e = cudaMallocHost((void**)&s.pinned_out, (size_t)d.result_bytes)) != cudaSuccess)
+            s.pinned_cap = 0;
+            if ((e = cudaMallocHost((void**)&s.pinned_out, (size_t)out_bytes)) != cudaSuccess)
                 return set_cuda_error(e, "serving: pinned result");
-            s.pinned_cap = d.result_bytes;
+            s.pinned_cap = out_bytes;
         }
         const int32_t count = std::max(1, d.count);
         if (s.seeds_cap < count) {
             if (s.seeds_pinned) cudaFreeHost(s.seeds_pinned);
             s.seeds_pinned = nullptr;
+            s.seeds_cap = 0;
             if ((e = cudaMallocHost((void**)&s.seeds_pinned, 8 * (size_t)count)) != cudaSuccess)
                 return set_cuda_error(e, "serving: pinned seeds");
             s.seeds_cap = count;
         }
-        std::vector<uint64_t> seeds((size_t)count);
-        for (int32_t i = 0; i < count; ++i) seeds[(size_t)i] = r->seed + (uint64_t)i;
+        uint8_t* dev_out = s.ws.out;
+        if (k > 1) {
+            const int64_t cap = (d.n + 15) / 16 * 16;
+            if (s.word8_cap < cap) {
+                if (s.word8) cudaFree(s.word8);
+                s.word8 = nullptr;
+                s.word8_cap = 0;
+                if ((e = cudaMalloc((void**)&s.word8, 4 * (size_t)kMaxMulti * cap)) != cudaSuccess)
+                    return set_cuda_error(e, "serving: multi-seed state");
+                s.word8_cap = cap;
+            }
+            if (s.out_multi_cap < out_bytes) {
+                if (s.out_multi) cudaFree(s.out_multi);
+                s.out_multi = nullptr;
+                s.out_multi_cap = 0;
+                if ((e = cudaMalloc((void**)&s.out_multi, (size_t)out_bytes)) != cudaSuccess)
+                    return set_cuda_error(e, "serving: multi-seed results");
+                s.out_multi_cap = out_bytes;
+            }
+            dev_out = s.out_multi;
+        }
         int rc;
         {
             std::lock_guard<std::mutex> glk(g->mu);
             int blocks = serve_blocks_ > 0 ? serve_blocks_ : std::max(1, sms_ / 2);
             if (d.n <= kSingleBlockMax) blocks = 1;
-            rc = solve_in(g, s.ws, seeds.data(), s.seeds_pinned, s.ws.out, s.stream, blocks);
+            if (k > 1) {
+                uint64_t seeds[kMaxMulti];
+                for (int i = 0; i < k; ++i) seeds[i] = rs[i]->seed;
+                rc = solve_multi_in(g, s.ws, s.word8, k, seeds, dev_out, s.stream, blocks);
+            } else {
+                std::vector<uint64_t> seeds((size_t)count);
+                for (int32_t i = 0; i < count; ++i) seeds[(size_t)i] = rs[0]->seed + (uint64_t)i;
+                rc = solve_in(g, s.ws, seeds.data(), s.seeds_pinned, dev_out, s.stream, blocks);
+            }
         }
         if (rc != MIS_OK) return rc;
-        if (d.result_bytes > 0)
-            e = cudaMemcpyAsync(s.pinned_out, s.ws.out, (size_t)d.result_bytes,
-                                cudaMemcpyDeviceToHost, s.stream);
+        if (out_bytes > 0)
+            e = cudaMemcpyAsync(s.pinned_out, dev_out, (size_t)out_bytes, cudaMemcpyDeviceToHost,
+                                s.stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(s.ctl_pinned, s.ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
                                 s.stream);
         if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.stream);
         if (e != cudaSuccess) return set_cuda_error(e, "serving: enqueue");
-        s.req = r;
         return MIS_OK;
+    }
+
+    // Caller holds mu_.  Takes the oldest queued request and, when its graph
+    // can be solved by the multi-seed kernel, up to kmax - 1 more queued
+    // requests on the same graph (searching kGroupScan entries).
+    int take_group_locked(Request** rs, int kmax) {
+        Request* r = queue_.front();
+        queue_.pop_front();
+        rs[0] = r;
+        int k = 1;
+        const GraphData& d = r->g->d;
+        const bool groupable = d.count == 0 && d.n > 0 && r->g->path == MIS_PATH_CSR;
+        if (!groupable) return k;
+        int scanned = 0;
+        for (auto it = queue_.begin(); it != queue_.end() && k < kmax && scanned < kGroupScan;
+             ++scanned) {
+            if ((*it)->g == r->g) {
+                rs[k++] = *it;
+                it = queue_.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        return k;
     }
 
     // Caller holds mu_ (released around the free of a destroyed graph).
@@ -269,22 +345,33 @@ class Server {
         cv_done_.notify_all();
     }
 
+    struct Job {
+        Slot* slot = nullptr;
+        Request* rs[kMaxMulti] = {};
+        int k = 0;
+        int64_t need = 0;
+        int rc = MIS_OK;
+    };
+
     void loop() {
         cudaSetDevice(device_);
+        std::vector<Job> jobs;
         std::unique_lock<std::mutex> lk(mu_);
         for (;;) {
             bool progressed = false;
             int busy = 0;
             // retire
             for (Slot& s : slots_) {
-                if (!s.req) continue;
+                if (s.nreq == 0) continue;
                 const cudaError_t q = cudaEventQuery(s.ev);
                 if (q == cudaErrorNotReady) {
                     ++busy;
                     continue;
                 }
-                Request* r = s.req;
-                s.req = nullptr;
+                const int k = s.nreq;
+                Request* rs[kMaxMulti];
+                for (int i = 0; i < k; ++i) rs[i] = s.reqs[i];
+                s.nreq = 0;
                 used_ -= s.charge;
                 s.charge = 0;
                 int st = MIS_OK;
@@ -292,19 +379,23 @@ class Server {
                     cudaGetLastError();
                     st = MIS_EDEVICE;
                 } else {
-                    if (r->g->d.result_bytes > 0)
-                        std::memcpy(r->host_out, s.pinned_out, (size_t)r->g->d.result_bytes);
                     if (s.ctl_pinned->err == kErrTimedOut) st = MIS_ETIMEDOUT;
                     else if (s.ctl_pinned->err != 0) st = MIS_EINTERNAL;
                 }
-                complete_locked(lk, r, st);
+                const int64_t nb = rs[0]->g->d.result_bytes;
+                for (int i = 0; i < k; ++i) {
+                    if (st == MIS_OK && nb > 0)
+                        std::memcpy(rs[i]->host_out, s.pinned_out + i * nb, (size_t)nb);
+                    complete_locked(lk, rs[i], st);
+                }
                 progressed = true;
             }
-            // admit and launch
+            // admit: choose slots and groups under the lock ...
+            jobs.clear();
             while (!queue_.empty()) {
                 Slot* free_slot = nullptr;
                 for (Slot& s : slots_)
-                    if (!s.req) {
+                    if (s.nreq == 0) {
                         free_slot = &s;
                         break;
                     }
@@ -313,18 +404,37 @@ class Server {
                     free_slot = &slots_.back();
                 }
                 if (!free_slot) break;
-                Request* r = queue_.front();
-                const GraphData& d = r->g->d;
-                const int64_t need = ws_bytes_for(d.n, d.count) + d.result_bytes;
-                if (used_ > 0 && used_ + need > budget_) break;  // admission by HBM footprint
-                queue_.pop_front();
-                const int rc = launch_locked(*free_slot, r);
-                if (rc != MIS_OK) {
-                    complete_locked(lk, r, rc);
-                } else {
-                    free_slot->charge = need;
-                    used_ += need;
-                    ++busy;
+                const GraphData& d = queue_.front()->g->d;
+                // admission by HBM footprint (a lone request always fits)
+                if (used_ > 0 && used_ + charge_for(d, 1) > budget_) break;
+                // the largest group that fits the budget
+                int kmax = kMaxMulti;
+                while (kmax > 1 && used_ > 0 && used_ + charge_for(d, kmax) > budget_) --kmax;
+                Job j;
+                j.slot = free_slot;
+                j.k = take_group_locked(j.rs, kmax);
+                j.need = charge_for(d, j.k);
+                free_slot->nreq = j.k;
+                for (int i = 0; i < j.k; ++i) free_slot->reqs[i] = j.rs[i];
+                free_slot->charge = j.need;
+                used_ += j.need;
+                jobs.push_back(j);
+            }
+            // ... and launch without it, so that submitters and pollers are not
+            // held up by the CUDA calls (the requests taken are off the queue)
+            if (!jobs.empty()) {
+                lk.unlock();
+                for (Job& j : jobs) j.rc = launch_unlocked(*j.slot, j.rs, j.k);
+                lk.lock();
+                for (Job& j : jobs) {
+                    if (j.rc != MIS_OK) {
+                        j.slot->nreq = 0;
+                        used_ -= j.need;
+                        j.slot->charge = 0;
+                        for (int i = 0; i < j.k; ++i) complete_locked(lk, j.rs[i], j.rc);
+                    } else {
+                        ++busy;
+                    }
                 }
                 progressed = true;
             }
@@ -343,7 +453,7 @@ class Server {
 
     std::mutex mu_;
     std::condition_variable cv_work_, cv_done_;
-    std::deque<Request*> queue_;
+    std::list<Request*> queue_;  // list: grouping erases from the middle
     std::unordered_map<mis_ticket, Request*> reqs_;
     std::deque<Slot> slots_;  // deque: slots never move once created
     std::thread thread_;

@@ -120,6 +120,8 @@ def lib():
         L.mis_tiles_ex.restype = ctypes.c_int
         L.mis_set_csr_bins.argtypes = [P, P]
         L.mis_set_csr_bins.restype = ctypes.c_int
+        L.mis_solve_multi_ex.argtypes = [P, i32, P, P, P]
+        L.mis_solve_multi_ex.restype = ctypes.c_int
         L.mis_capture.argtypes = [P, P, P, ctypes.POINTER(P)]
         L.mis_capture.restype = ctypes.c_int
         L.mis_replay_launch.argtypes = [P, P]
@@ -158,7 +160,7 @@ def lib():
 EXPORTED = [
     "mis_options_init", "mis_create", "mis_create_ex", "mis_create_batch", "mis_graph_count",
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
-    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
+    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
     "mis_solve_noalloc",
 ]
@@ -277,6 +279,15 @@ def mis_set_path(h, path, threads_per_row=0):
 def mis_set_csr_bins(h, bounds):
     b = np.ascontiguousarray(np.asarray(bounds, dtype=np.int32))
     return _check(lib().mis_set_csr_bins(h, _ptr(b)))
+
+
+def mis_solve_multi_ex(h, seeds, out_ptr, stream=None):
+    """k = len(seeds) solves of one graph in one launch; solve s's result at
+    out_ptr + s * n (device)."""
+    s = np.ascontiguousarray(np.atleast_1d(np.asarray(seeds, dtype=np.uint64)))
+    return _check(lib().mis_solve_multi_ex(h, len(s), _ptr(s),
+                                           ctypes.c_void_p(out_ptr) if out_ptr else None,
+                                           ctypes.c_void_p(stream) if stream else None))
 
 
 def mis_capture(h, seeds, out_status_dev):

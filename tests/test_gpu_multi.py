@@ -1,0 +1,122 @@
+"""Several solves of one graph in one launch (mis_solve_multi_ex): each
+solve's set is bit-identical to the oracle's for its seed, and the summed
+round statistics match the oracle's per-seed rounds."""
+import numpy as np
+import pytest
+
+from paper_2605_29604_gb300 import graphgen as gg
+from paper_2605_29604_gb300 import native
+
+from gpu_util import create, ensure_built, oracle_solve
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    torch.cuda.set_device(0)
+
+
+FAMILIES = {
+    "er_10k": lambda: gg.er_10k_deg8(1),
+    "rmat14": lambda: gg.rmat(14, 16, 0.57, 0.19, 0.19, 9, permute=True),
+    "rmat14_natural": lambda: gg.rmat(14, 16, 0.57, 0.19, 0.19, 9, permute=False),
+    "grid": lambda: gg.grid_diag(127, 0.05, 2),
+    "grid_perm": lambda: gg.grid_diag(127, 0.05, 2, permute=True),
+    "star_hub": lambda: gg.disjoint_union([gg.star(150000), gg.er_gnm(5000, 20000, 3)]),
+    "dense": lambda: gg.random_small(700, 0.3, 6),
+    "k_ab": lambda: gg.complete_bipartite(40, 900),
+    "path": lambda: gg.path(5001),
+    "empty": lambda: gg.empty(1234),
+    "edge": lambda: gg.path(2),
+}
+
+_cache = {}
+
+
+def graph(name):
+    if name not in _cache:
+        _cache[name] = FAMILIES[name]()
+    return _cache[name]
+
+
+def multi_solve(h, n, seeds):
+    import torch
+    k = len(seeds)
+    out = torch.full((max(k * n, 1),), 7, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    native.mis_solve_multi_ex(h, np.asarray(seeds, dtype=np.uint64), out.data_ptr(), stream)
+    st = native.mis_get_stats(h)
+    return out[:k * n].cpu().numpy().reshape(k, n), st
+
+
+def check(g, seeds, got, st):
+    n = g[0]
+    wants = [oracle_solve(g, int(s)) for s in seeds]
+    for s, want, row in zip(seeds, wants, got):
+        bad = np.flatnonzero(row != want.status)
+        assert len(bad) == 0, f"seed {s}: {len(bad)} vertices differ, first {bad[:10]}"
+    rounds = max(w.rounds for w in wants)
+    assert st.rounds == rounds
+    alive = np.zeros(rounds, dtype=np.int64)
+    for w in wants:
+        alive[:w.rounds] += np.asarray(w.alive_per_round[:w.rounds], dtype=np.int64)
+    r = min(rounds, 64)
+    assert list(st.alive_per_round[:r]) == [int(x) for x in alive[:r]]
+    assert st.alive_sum == int(sum(w.alive_sum for w in wants))
+    assert st.mis_size == int(sum(int(w.status.sum()) for w in wants))
+
+
+@pytest.mark.parametrize("name", sorted(FAMILIES))
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_multi_bit_exact(name, k):
+    g = graph(name)
+    h = create(g)
+    try:
+        seeds = [1 + 977 * i for i in range(k)]
+        got, st = multi_solve(h, g[0], seeds)
+        check(g, seeds, got, st)
+    finally:
+        native.mis_destroy(h)
+
+
+@pytest.mark.parametrize("order_rows", [0, 2])
+def test_multi_orderings_and_repeats(order_rows):
+    g = graph("rmat14")
+    h = create(g, order_rows=order_rows)
+    try:
+        seeds = [5, 5, 2**63 + 11, 0, 17]
+        got, st = multi_solve(h, g[0], seeds)
+        check(g, seeds, got, st)
+        assert np.array_equal(got[0], got[1])
+        # the handle's plain solves still work after a multi-seed solve
+        import torch
+        out = torch.empty(g[0], dtype=torch.uint8, device="cuda")
+        native.mis_solve_ex(h, [17], out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        native.mis_get_stats(h)
+        assert np.array_equal(out.cpu().numpy(), got[4])
+    finally:
+        native.mis_destroy(h)
+
+
+def test_multi_rejects_bad_arguments():
+    import torch
+    g = graph("path")
+    h = create(g)
+    out = torch.empty(9 * g[0], dtype=torch.uint8, device="cuda")
+    try:
+        for seeds in ([], list(range(9))):
+            with pytest.raises(native.MisError):
+                native.mis_solve_multi_ex(h, np.asarray(seeds, dtype=np.uint64), out.data_ptr())
+    finally:
+        native.mis_destroy(h)
+    hb = native.mis_create_batch([gg.path(10), gg.path(20)])
+    try:
+        with pytest.raises(native.MisError):
+            native.mis_solve_multi_ex(hb, np.asarray([1, 2], dtype=np.uint64), out.data_ptr())
+    finally:
+        native.mis_destroy(hb)

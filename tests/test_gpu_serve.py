@@ -160,3 +160,29 @@ def test_served_barrier_timeout_is_reported():
         assert np.array_equal(out, _want(g2, 5))
     finally:
         native.mis_destroy(h2)
+
+
+def test_same_graph_requests_ride_together():
+    """Requests queued on the same large graph are solved together (several
+    seeds per launch); each result must still be its own seed's set, and a
+    graph on the tile path (solved alone) must not be affected."""
+    g = gg.rmat(15, 16, 0.57, 0.19, 0.19, 21)
+    gt = gg.grid_diag(150, 0.05, 8)
+    h = create(g)
+    ht = create(gt)
+    native.mis_set_path(ht, native.MIS_PATH_TILE, 8)
+    try:
+        reqs = []
+        seeds = [1000 + k for k in range(20)] + [1003, 1003, 2**64 - 1, 0]
+        for k, s in enumerate(seeds):
+            out = np.full(g[0], 9, dtype=np.uint8)
+            reqs.append((native.mis_submit(h, s, out), g, s, out))
+            if k % 6 == 0:
+                o2 = np.full(gt[0], 9, dtype=np.uint8)
+                reqs.append((native.mis_submit(ht, s, o2), gt, s, o2))
+        for t, gg_, s, out in reqs:
+            assert native.mis_wait(t, -1) == native.MIS_OK
+            assert np.array_equal(out, _want(gg_, s)), s
+    finally:
+        native.mis_destroy(h)
+        native.mis_destroy(ht)
