@@ -292,6 +292,30 @@ def run_single(args):
     st = native.mis_get_stats(h)
     value = world * args.steps * arcs / (total_ms / 1e3)
 
+    # several seeds of the same resident graph per launch (mis_solve_multi_ex)
+    multi = None
+    if args.multi > 0 and args.path is None:
+        kk = min(args.multi, 8)
+        mout = torch.empty(max(kk * n, 1), dtype=torch.uint8, device="cuda")
+        mseeds = np.arange(1, kk + 1, dtype=np.uint64)
+        flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
+        for _ in range(max(args.warmup, 3)):
+            native.mis_solve_multi_ex(h, mseeds, mout.data_ptr(), stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for e0, e1 in ev:
+            flush.add_(1.0)  # L2 flushed between launches, as for the single solves
+            e0.record()
+            native.mis_solve_multi_ex(h, mseeds, mout.data_ptr(), stream)
+            e1.record()
+        torch.cuda.synchronize()
+        mst = native.mis_get_stats(h)
+        mt = float(np.median([e0.elapsed_time(e1) for e0, e1 in ev]))
+        multi = {"k": kk, "launch_ms_p50": mt, "per_solve_ms": mt / kk,
+                 "edges_per_s_aggregate": kk * arcs / (mt / 1e3), "rounds": mst.rounds,
+                 "kernel": "multi_solve_kernel (k seeds of the graph per persistent launch)"}
+
     # end to end through the C ABI with host buffers: pinned CSR in, result out
     e2e = None
     if args.e2e_steps > 0:
@@ -321,7 +345,7 @@ def run_single(args):
     launch_s = (total_ms / 1e3) / args.steps
     traffic = args.traffic
     if traffic is None and args.workload == "rmat22" and st.path == 1:
-        traffic = profiled_traffic(["kernels_csr.cu", "common.cuh", "init.cuh"],
+        traffic = profiled_traffic(["kernels_csr.cu", "common.cuh", "init.cuh", "worklist.cuh"],
                                    "csr_solve_rmat22.md")
     achieved = alg_bytes / launch_s / 1e9
     path = PATH_NAMES.get(st.path, str(st.path))
@@ -351,6 +375,8 @@ def run_single(args):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if multi is not None:
+        line["config"]["multi_seed"] = multi
     if tuning is not None:
         line["config"]["autotune"] = {"path": PATH_NAMES.get(tuning.path), "param": tuning.param,
                                       "bounds": list(tuning.bounds), "grid": tuning.grid,
@@ -586,6 +612,8 @@ def main():
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--seq-requests", type=int, default=2000)
     ap.add_argument("--serve-blocks", type=int, default=0)
+    ap.add_argument("--multi", type=int, default=8,
+                    help="also time this many seeds of the graph per launch (0 = off)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
