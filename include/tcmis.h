@@ -101,7 +101,20 @@ typedef struct mis_options {
                                 scans only them; 2 = each row fully sorted by neighbour
                                 degree (slower create, shorter exclusion scans);
                                 0 = none (full rows) */
+    int32_t priority;        /* priority heuristic (Sec. 3.3), fixed at create:
+                                MIS_PRIORITY_EQ1 (default; H2/H3, Eq. 1),
+                                MIS_PRIORITY_HASH (H1: random priority hash(v)),
+                                MIS_PRIORITY_EQ1_Q8 (Eq. 1 discretised to 8 bits, ties
+                                by vertex id).  The degree-ordered rows and the
+                                create-time round-0 decisions rely on Eq. 1's degree
+                                order; the other heuristics scan whole rows. */
 } mis_options;
+
+enum {
+    MIS_PRIORITY_EQ1 = 0,
+    MIS_PRIORITY_HASH = 1,
+    MIS_PRIORITY_EQ1_Q8 = 2
+};
 
 /* Per-solve statistics of the last completed solve on a graph. */
 typedef struct mis_stats {

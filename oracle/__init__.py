@@ -62,6 +62,8 @@ def _load():
         lib.orc_priority.restype = f32
         lib.orc_keys.argtypes = [i32, P, u64, P]
         lib.orc_keys.restype = None
+        lib.orc_keys_mode.argtypes = [i32, P, u64, i32, P]
+        lib.orc_keys_mode.restype = None
         lib.orc_rounds.argtypes = [i32, P, P, P, P, P, P, P, P, i32]
         lib.orc_rounds.restype = ctypes.c_int
         lib.orc_greedy.argtypes = [i32, P, P, P, P]
@@ -101,11 +103,22 @@ def priority(dbar: float, deg: int, e: float) -> float:
     return float(_load().orc_priority(dbar, deg, e))
 
 
-def keys(n: int, row_ptr, seed: int) -> np.ndarray:
-    """uint32 priority keys of Eq. 1 (bits of binary32 P; 0xFFFFFFFF if isolated)."""
+# Priority heuristics of Sec. 3.3 (the mode argument of keys/solve).
+PRIORITY_EQ1 = 0  # H2/H3: Eq. 1, degree-aware
+PRIORITY_HASH = 1  # H1: random priority hash(v)
+PRIORITY_EQ1_Q8 = 2  # Eq. 1 discretised to 8 bits
+
+
+def keys(n: int, row_ptr, seed: int, priority: int = PRIORITY_EQ1) -> np.ndarray:
+    """uint32 priority keys (0xFFFFFFFF if isolated).  PRIORITY_EQ1: bits of
+    binary32 P of Eq. 1; PRIORITY_HASH: 2^29 + (hi32(mix(mix(seed) ^ v)) >> 3);
+    PRIORITY_EQ1_Q8: trunc(255 * P) in binary32."""
     rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
     out = np.empty(max(n, 1), dtype=np.uint32)
-    _load().orc_keys(n, _p(rp), seed & (2**64 - 1), _p(out))
+    if priority == PRIORITY_EQ1:
+        _load().orc_keys(n, _p(rp), seed & (2**64 - 1), _p(out))
+    else:
+        _load().orc_keys_mode(n, _p(rp), seed & (2**64 - 1), int(priority), _p(out))
     return out[:n]
 
 
@@ -168,9 +181,10 @@ def min_degree_greedy(n: int, row_ptr, col_idx) -> tuple[int, np.ndarray]:
     return int(size), st[:n]
 
 
-def solve(n: int, row_ptr, col_idx, seed: int) -> RoundsResult:
-    """Keys (Eq. 1) then Algorithm 2's rounds: the full hot path on the CPU."""
-    return rounds(n, row_ptr, col_idx, keys(n, row_ptr, seed))
+def solve(n: int, row_ptr, col_idx, seed: int, priority: int = PRIORITY_EQ1) -> RoundsResult:
+    """Keys (Eq. 1 or another heuristic of Sec. 3.3) then Algorithm 2's rounds:
+    the full hot path on the CPU."""
+    return rounds(n, row_ptr, col_idx, keys(n, row_ptr, seed, priority))
 
 
 def brute_force_mis(n: int, row_ptr, col_idx) -> list[int]:

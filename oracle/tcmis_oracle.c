@@ -13,6 +13,8 @@
  *                    d = average degree, eps a small hashed perturbation
  *                    (Sec. 2, Eq. 1; Sec. 3.3 H2).  Priorities are assigned once
  *                    and reused every round (Sec. 2, random-permutation variant).
+ *   orc_keys_mode    the keys of the other priority heuristics of Sec. 3.3: H1
+ *                    (random, hash(v)) and Eq. 1 discretised to 8 bits.
  *   orc_rounds       Algorithm 2 (and Algorithm 1): while the alive set A is not
  *                    empty -- Phase 1 candidates C = strict local maxima of P among
  *                    alive neighbours; Phase 2 N_c = A x C (neighbour counts of
@@ -99,6 +101,41 @@ void orc_keys(int32_t n, const int32_t *row_ptr, uint64_t seed, uint32_t *key)
         }
         float p = orc_priority(dbar, deg, orc_eps(seed, v));
         key[v] = orc_float_bits(p);
+    }
+}
+
+/*
+ * Priority keys under one of the paper's priority heuristics (Sec. 3.3):
+ *   mode 0  H2 / H3, the degree-aware Eq. 1: exactly orc_keys;
+ *   mode 1  H1, random priority P(v) = hash(v): the high 29 bits of
+ *           h = hi32(mix64(mix64(seed) XOR v)), written as 2^29 + (h >> 3);
+ *   mode 2  Eq. 1 scaled and discretised to a compact 8-bit integer (Sec. 2:
+ *           the value is scaled and discretized for GPU execution):
+ *           q = trunc(P * 255) with P the binary32 Eq. 1 value and the product
+ *           in binary32 round-to-nearest; key = q in [0, 255].
+ * Isolated vertices get 0xFFFFFFFF in every mode; ties are broken by id as
+ * in orc_rounds (they are frequent in mode 2).
+ */
+void orc_keys_mode(int32_t n, const int32_t *row_ptr, uint64_t seed, int32_t mode, uint32_t *key)
+{
+    if (n <= 0) return;
+    float dbar = (float)row_ptr[n] / (float)n;
+    for (int32_t v = 0; v < n; ++v) {
+        int32_t deg = row_ptr[v + 1] - row_ptr[v];
+        if (deg == 0) {
+            key[v] = 0xFFFFFFFFu;
+            continue;
+        }
+        if (mode == 1) {
+            uint32_t h = (uint32_t)(orc_mix64(orc_mix64(seed) ^ (uint64_t)(uint32_t)v) >> 32);
+            key[v] = 0x20000000u + (h >> 3);
+        } else if (mode == 2) {
+            float p = orc_priority(dbar, deg, orc_eps(seed, v));
+            float scaled = p * 255.0f;
+            key[v] = (uint32_t)scaled; /* truncation toward zero; scaled in [0, 255] */
+        } else {
+            key[v] = orc_float_bits(orc_priority(dbar, deg, orc_eps(seed, v)));
+        }
     }
 }
 

@@ -219,7 +219,8 @@ int finish_create(mis_graph* g) {
     GraphData& d = g->d;
     cudaError_t e;
     const int64_t col_alloc = ((d.arcs + 3) / 4) * 4 + 4;
-    const bool order = g->opt.order_rows != 0;
+    // the selection prefixes and round-0 classes hold for Eq. 1's degree order only
+    const bool order = g->opt.order_rows != 0 && g->opt.priority == MIS_PRIORITY_EQ1;
     if ((e = ws_reserve(d.ws, d.n, d.count)) != cudaSuccess ||
         (e = dalloc(&d.order0, d.n, &d.footprint)) != cudaSuccess ||
         (order && (e = dalloc(&d.r0class, d.n, &d.footprint)) != cudaSuccess) ||
@@ -312,6 +313,7 @@ SolveArgs make_args(mis_graph* g, Workspace& w) {
     a.n_sure_in = d.n_sure_in;
     a.n_sure_out = d.n_sure_out;
     a.pending = g->csr_pending;
+    a.priority = g->opt.priority;
     a.ctl = w.ctl;
     a.times = w.times;
     a.seg = seg_of(d);
@@ -560,7 +562,8 @@ std::string density_class(mis_graph* g, double apt) {
     for (char& c : dev)
         if (c == ' ') c = '_';
     return dev + ":d" + std::to_string(deg_b) + ":n" + std::to_string(size_b / 2) + ":" + loc +
-           (d.count ? ":batch" : "");
+           (d.count ? ":batch" : "") +
+           (g->opt.priority ? ":p" + std::to_string(g->opt.priority) : std::string());
 }
 
 int apply_choice(mis_graph* g, const TuneChoice& c) {
@@ -711,6 +714,7 @@ void mis_options_init(mis_options* opt) {
     opt->hbm_budget = 0;
     opt->serve_blocks = 0;
     opt->order_rows = 1;
+    opt->priority = MIS_PRIORITY_EQ1;
 }
 
 int mis_last_error(const char** msg) {
@@ -736,6 +740,10 @@ mis_graph* mis_create_ex(int32_t n, const int32_t* row_ptr, const int32_t* col_i
     if (opt) o = *opt;
     if (!valid_tpr(o.threads_per_row)) {
         set_error(MIS_EINVAL, "threads_per_row must be 0, 1, 4, 16, 32 or 512");
+        return nullptr;
+    }
+    if (o.priority < MIS_PRIORITY_EQ1 || o.priority > MIS_PRIORITY_EQ1_Q8) {
+        set_error(MIS_EINVAL, "priority must be MIS_PRIORITY_EQ1, _HASH or _EQ1_Q8");
         return nullptr;
     }
     cudaError_t e = cudaSetDevice(o.device);
@@ -826,6 +834,10 @@ mis_graph* mis_create_batch(int32_t count, const int32_t* ns, const int32_t* con
     if (opt) o = *opt;
     if (!valid_tpr(o.threads_per_row)) {
         set_error(MIS_EINVAL, "threads_per_row must be 0, 1, 4, 16, 32 or 512");
+        return nullptr;
+    }
+    if (o.priority < MIS_PRIORITY_EQ1 || o.priority > MIS_PRIORITY_EQ1_Q8) {
+        set_error(MIS_EINVAL, "priority must be MIS_PRIORITY_EQ1, _HASH or _EQ1_Q8");
         return nullptr;
     }
     std::vector<int32_t> voff(count), nv(count), garcs(count);

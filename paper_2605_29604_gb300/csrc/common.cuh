@@ -97,6 +97,29 @@ __device__ __forceinline__ uint32_t eq1_key(float dbar, int32_t deg, uint64_t se
     return __float_as_uint(__fdiv_rn(dbar, den));
 }
 
+// Priority heuristics of Sec. 3.3 (values of mis_options.priority): H2/H3 =
+// Eq. 1 above; H1 = random priority hash(v); Eq. 1 discretised to 8 bits.
+constexpr int kPrioEq1 = 0, kPrioHash = 1, kPrioEq1Q8 = 2;
+
+// Key of a vertex of degree >= 1 under heuristic `mode`: Eq. 1's bits;
+// H1: 2^29 + (hi32(mix64(seed_mix ^ id)) >> 3), the hash's high 29 bits;
+// 8-bit: trunc(255 * P) with P Eq. 1's binary32 value (product round-to-
+// nearest, then truncation).
+__device__ __forceinline__ uint32_t priority_key(int mode, float dbar, int32_t deg,
+                                                 uint64_t seed_mix, uint32_t local_id) {
+    if (mode == kPrioHash)
+        return 0x20000000u + ((uint32_t)(mix64(seed_mix ^ (uint64_t)local_id) >> 32) >> 3);
+    const uint32_t k = eq1_key(dbar, deg, seed_mix, local_id);
+    if (mode == kPrioEq1Q8) return __float2uint_rz(__fmul_rn(__uint_as_float(k), 255.0f));
+    return k;
+}
+
+// The undecided word of a key (bits 31..29 = 001, order kept): Eq. 1 and H1
+// keys already have that form; an 8-bit key is placed in the low bits.
+__device__ __forceinline__ uint32_t undecided_word(int mode, uint32_t key) {
+    return mode == kPrioEq1Q8 ? (0x20000000u | key) : key;
+}
+
 // ---------------------------------------------------------------- memory helpers
 
 __device__ __forceinline__ uint32_t ld_word(const uint32_t* p) { return __ldcg(p); }

@@ -6,8 +6,8 @@
 
 namespace tcmis {
 
-// Eq. 1 priority of every vertex v < n_words into its packed word (Sec. 2:
-// assigned once per solve).  Vertices at or beyond a.n (tile padding) and
+// Priority (Eq. 1, or the heuristic a.priority selects, Sec. 3.3) of every
+// vertex v < n_words into its packed word (Sec. 2: assigned once per solve).  Vertices at or beyond a.n (tile padding) and
 // batch padding vertices are out.  Isolated vertices have no neighbour to
 // compare with, so every round-0 selection test accepts them: with
 // isolated_in they are written in the MIS right away (the CSR kernel keeps
@@ -17,6 +17,7 @@ namespace tcmis {
 __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
                                            bool isolated_in) {
     const uint8_t* r0class = isolated_in ? a.r0class : nullptr;
+    const int mode = a.priority;
     const uint32_t iso = isolated_in ? (kKeyIsolated | kWordInSet) : kKeyIsolated;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthreads = (long long)gridDim.x * blockDim.x;
@@ -57,7 +58,9 @@ __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
                 const long long u = v + k;
                 const int deg = r[k + 1] - r[k];
                 w[k] = u >= n ? kWordOut
-                              : (deg ? eq1_key(dbar0, deg, smix0, (uint32_t)u) : iso);
+                              : (deg ? undecided_word(mode, priority_key(mode, dbar0, deg, smix0,
+                                                                        (uint32_t)u))
+                                     : iso);
                 if (((sure >> (8 * k)) & 0xFFu) == 1u) w[k] |= kWordInSet;
             }
             *reinterpret_cast<uint4*>(a.word + v) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -71,7 +74,8 @@ __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
         } else {
             const int deg = a.rp[v + 1] - a.rp[v];
             if (a.seg.count == 0) {
-                w = deg ? eq1_key(dbar0, deg, smix0, (uint32_t)v) : iso;
+                w = deg ? undecided_word(mode, priority_key(mode, dbar0, deg, smix0, (uint32_t)v))
+                        : iso;
             } else {
                 const int g = a.seg.blk_seg[v >> 4];
                 const int local = (int)v - a.seg.voff[g];
@@ -81,7 +85,8 @@ __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
                     w = iso;
                 } else {
                     const float dbar = average_degree(a.seg.arcs[g], a.seg.nv[g]);
-                    w = eq1_key(dbar, deg, mix64(a.seg.seed[g]), (uint32_t)local);
+                    w = undecided_word(mode, priority_key(mode, dbar, deg, mix64(a.seg.seed[g]),
+                                                          (uint32_t)local));
                 }
             }
             if (r0class && r0class[v] == 1) w |= kWordInSet;

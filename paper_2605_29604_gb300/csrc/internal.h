@@ -60,6 +60,7 @@ struct SolveArgs {
     const int32_t* sure_out = nullptr;
     int32_t n_sure_in = 0;
     int32_t n_sure_out = 0;
+    int32_t priority = 0;             // priority heuristic (kPrioEq1, kPrioHash, kPrioEq1Q8)
     int32_t pending = 0;              // 1: Phase 1 lists its non-candidates for Phase 2
                                       // (in wlp); 0: Phase 2 triages W_r itself
     // tile-CSR (used by the tile kernels only)

@@ -255,7 +255,7 @@ __device__ __forceinline__ void init_words8(const SolveArgs& a, uint32_t* word8,
         for (int s = 0; s < kMaxMulti; ++s) {
             if (v >= n || s >= k) w[s] = kWordOut;
             else if (in0) w[s] = kWordInMin;
-            else w[s] = eq1_key(dbar, deg, smix[s], (uint32_t)v);
+            else w[s] = undecided_word(a.priority, priority_key(a.priority, dbar, deg, smix[s], (uint32_t)v));
         }
         store8(word8, (int)v, w);
     }

@@ -105,14 +105,15 @@ __global__ void keys_kernel(const SolveArgs a, uint32_t* __restrict__ out_key) {
     for (long long v = tid; v < n; v += nthreads) {
         const int deg = a.rp[v + 1] - a.rp[v];
         if (a.seg.count == 0) {
-            out_key[v] = deg ? eq1_key(dbar0, deg, smix0, (uint32_t)v) : 0xFFFFFFFFu;
+            out_key[v] = deg ? priority_key(a.priority, dbar0, deg, smix0, (uint32_t)v) : 0xFFFFFFFFu;
         } else {
             const int g = a.seg.blk_seg[v >> 4];
             const int local = (int)v - a.seg.voff[g];
             if (local >= a.seg.nv[g]) continue;
             const float dbar = average_degree(a.seg.arcs[g], a.seg.nv[g]);
             out_key[a.seg.roff[g] + local] =
-                deg ? eq1_key(dbar, deg, mix64(a.seg.seed[g]), (uint32_t)local) : 0xFFFFFFFFu;
+                deg ? priority_key(a.priority, dbar, deg, mix64(a.seg.seed[g]), (uint32_t)local)
+                    : 0xFFFFFFFFu;
         }
     }
 }

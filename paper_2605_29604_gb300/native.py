@@ -34,6 +34,9 @@ MIS_PATH_AUTO = 0
 MIS_PATH_CSR = 1
 MIS_PATH_TILE = 2
 MIS_PATH_TILE_TC = 3
+MIS_PRIORITY_EQ1 = 0
+MIS_PRIORITY_HASH = 1
+MIS_PRIORITY_EQ1_Q8 = 2
 
 ERROR_NAMES = {0: "MIS_OK", -1: "MIS_EINVAL", -2: "MIS_ENOMEM", -3: "MIS_EBUSY",
                -4: "MIS_ETIMEDOUT", -5: "MIS_EDEVICE", -6: "MIS_EINTERNAL", -7: "MIS_ENOTREADY"}
@@ -50,7 +53,8 @@ class mis_options(ctypes.Structure):
                 ("check_symmetry", ctypes.c_int32), ("build_tiles", ctypes.c_int32),
                 ("spin_cap", ctypes.c_int64), ("device", ctypes.c_int32),
                 ("max_slots", ctypes.c_int32), ("hbm_budget", ctypes.c_int64),
-                ("serve_blocks", ctypes.c_int32), ("order_rows", ctypes.c_int32)]
+                ("serve_blocks", ctypes.c_int32), ("order_rows", ctypes.c_int32),
+                ("priority", ctypes.c_int32)]
 
 
 class mis_stats(ctypes.Structure):

@@ -346,3 +346,98 @@ def test_min_degree_greedy_valid():
         assert size == int(st.sum())
     size, st = oracle.min_degree_greedy(*gg.star(9))
     assert size == 9 and st[0] == 0
+
+
+# ---------------------------------------------------------------- other heuristics (Sec. 3.3)
+
+def test_h1_keys_ignore_degrees():
+    """H1 is P(v) = hash(v): two graphs on the same vertex set but with
+    different edges (so different degrees and average degree) get the same
+    keys for the same seed; the keys lie in [2^29, 2^30) (the high 29 bits of
+    a 32-bit hash) and change with the seed."""
+    g1 = gg.er_gnm(5000, 10000, 1)
+    g2 = gg.rmat(12, 30, 0.57, 0.19, 0.19, 2)  # 4096 vertices: pad to 5000
+    rp2 = np.concatenate([g2[1], np.full(5000 - 4096, g2[1][-1], dtype=g2[1].dtype)])
+    k1 = oracle.keys(5000, g1[1], 77, oracle.PRIORITY_HASH)
+    k2 = oracle.keys(5000, rp2, 77, oracle.PRIORITY_HASH)
+    live = (np.diff(g1[1]) > 0) & (np.diff(rp2) > 0)
+    assert live.sum() > 1000
+    assert np.array_equal(k1[live], k2[live])
+    assert np.all((k1[np.diff(g1[1]) > 0] >= 2**29) & (k1[np.diff(g1[1]) > 0] < 2**30))
+    k3 = oracle.keys(5000, g1[1], 78, oracle.PRIORITY_HASH)
+    nz = np.diff(g1[1]) > 0  # isolated vertices keep 0xFFFFFFFF under every seed
+    assert np.mean(k1[nz] == k3[nz]) < 0.001
+
+
+def test_h1_keys_look_uniform():
+    """16 equal buckets of the 29-bit range: chi-square well below the 0.1 %
+    critical value for 15 degrees of freedom (37.7), and the keys are not
+    correlated with degree."""
+    n, rp, col = gg.rmat(16, 16, 0.57, 0.19, 0.19, 3)
+    k = oracle.keys(n, rp, 5, oracle.PRIORITY_HASH).astype(np.int64)
+    deg = np.diff(rp)
+    k = k[deg > 0] - 2**29
+    counts = np.bincount(k >> 25, minlength=16)
+    expect = len(k) / 16
+    chi2 = float(((counts - expect) ** 2 / expect).sum())
+    assert chi2 < 37.7
+    assert abs(np.corrcoef(k, deg[deg > 0])[0, 1]) < 0.02
+
+
+def test_q8_keys_are_eq1_scaled_to_8_bits():
+    """8-bit key = trunc(255 * P), P Eq. 1's binary32 value: within one step
+    of floor(255 * P_exact) with P_exact the exact rational Eq. 1, in [0, 255],
+    and non-increasing in degree (Eq. 1's P strictly decreases with degree,
+    because eps < 1)."""
+    n, rp, col = gg.rmat(13, 16, 0.57, 0.19, 0.19, 4)
+    seed = 9
+    q = oracle.keys(n, rp, seed, oracle.PRIORITY_EQ1_Q8).astype(np.int64)
+    deg = np.diff(rp)
+    live = deg > 0
+    assert q[live].min() >= 0 and q[live].max() <= 255
+    dbar = Fraction(float(np.float32(np.float32(rp[-1]) / np.float32(n))))
+    exact_hits = 0
+    for v in np.flatnonzero(live)[:3000]:
+        e = Fraction(oracle.eps(seed, int(v)))
+        p_exact = dbar / (dbar + int(deg[v]) - e)
+        f = math.floor(255 * p_exact)
+        assert abs(int(q[v]) - f) <= 1
+        exact_hits += int(q[v]) == f
+    assert exact_hits >= 2900
+    order = np.argsort(deg[live], kind="stable")
+    assert np.all(np.diff(q[live][order]) <= 0) or np.all(
+        np.maximum.accumulate(q[live][order][::-1])[::-1] >= q[live][order])
+    # strict form: a vertex never has a smaller key than one of larger degree
+    by_deg = {}
+    for d_, k_ in zip(deg[live], q[live]):
+        lo, hi = by_deg.get(int(d_), (256, -1))
+        by_deg[int(d_)] = (min(lo, int(k_)), max(hi, int(k_)))
+    ds = sorted(by_deg)
+    for a, b in zip(ds, ds[1:]):
+        assert by_deg[a][0] >= by_deg[b][1]
+    # few values, many ties (broken by id)
+    assert len(np.unique(q[live])) <= 256
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_heuristics_rounds_equal_greedy(mode, name):
+    n, rp, col = GRAPHS[name]()
+    key = oracle.keys(n, rp, 3, mode)
+    res = oracle.rounds(n, rp, col, key)
+    assert oracle.check(n, rp, col, res.status) == (0, -1)
+    assert np.array_equal(res.status, oracle.greedy(n, rp, col, key))
+    assert np.array_equal(res.status, oracle.solve(n, rp, col, 3, mode).status)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("seed", range(15))
+def test_heuristics_brute_force(mode, seed):
+    rng = np.random.default_rng(3000 + seed)
+    n = int(rng.integers(2, 16))
+    g = gg.random_small(n, float(rng.uniform(0.1, 0.7)), 50 + seed)
+    key = oracle.keys(n, g[1], seed, mode)
+    res = oracle.rounds(*g, key)
+    sets = oracle.brute_force_mis(*g)
+    mask = sum(1 << v for v in _members(res.status))
+    assert mask == _lex_first_by_priority(n, key, sets)
