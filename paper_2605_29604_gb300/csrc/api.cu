@@ -293,6 +293,54 @@ int validate_device(mis_graph* g, cudaStream_t s) {
     return MIS_OK;
 }
 
+// Host CSR without the symmetry check: col_idx goes up in pieces on the
+// handle's own stream while each landed piece is checked on `s`, so the
+// checks hide behind the copy (host-to-device bandwidth bounds a create).
+constexpr int64_t kUploadPiece = 16 << 20;  // arcs per piece
+
+int upload_checked(mis_graph* g, const int32_t* col_idx, cudaStream_t s) {
+    GraphData& d = g->d;
+    cudaError_t e = cudaSuccess;
+    if (!g->own_stream) e = cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.flags, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = launch_validate_rowptr(d.rp, d.n, d.arcs, d.flags, s);
+    unsigned f = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&f, d.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the arc checks trust row_ptr
+    if (e != cudaSuccess) return set_cuda_error(e, "graph upload");
+    if (f) return set_error(MIS_EINVAL, "invalid graph: row_ptr not monotone from 0 to arcs;");
+    std::vector<cudaEvent_t> evs;
+    for (int64_t a0 = 0; a0 < d.arcs && e == cudaSuccess; a0 += kUploadPiece) {
+        const int64_t a1 = std::min(d.arcs, a0 + kUploadPiece);
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) break;
+        evs.push_back(ev);
+        e = cudaMemcpyAsync(d.col + a0, col_idx + a0, sizeof(int32_t) * (size_t)(a1 - a0),
+                            cudaMemcpyHostToDevice, g->own_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, g->own_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+        // the order check of the first arc of a piece reads the previous
+        // piece's last arc, which the copy stream has landed before
+        if (e == cudaSuccess) e = launch_validate_arcs(d.rp, d.col, d.n, a0, a1, 0, d.flags, s);
+    }
+    f = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&f, d.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    const cudaError_t se = cudaStreamSynchronize(s);
+    const cudaError_t ce = cudaStreamSynchronize(g->own_stream);  // nothing may still run
+    for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+    if (e == cudaSuccess) e = se != cudaSuccess ? se : ce;
+    if (e != cudaSuccess) return set_cuda_error(e, "graph upload");
+    if (f) {
+        std::string why;
+        if (f & kBadColRange) why += " col_idx out of [0, n);";
+        if (f & kBadSelfLoop) why += " self-loop;";
+        if (f & kBadOrder) why += " row not strictly increasing (unsorted or duplicate);";
+        return set_error(MIS_EINVAL, "invalid graph:" + why);
+    }
+    return MIS_OK;
+}
+
 SolveArgs make_args(mis_graph* g, Workspace& w) {
     GraphData& d = g->d;
     SolveArgs a;
@@ -485,7 +533,11 @@ void tune_save_locked() {
     }
 }
 
-// Distinct 8-column blocks of 8-row block rb: an 8-way merge of its sorted rows.
+// Distinct 8-column blocks of 8-row block rb: an 8-way merge of its sorted
+// rows, stopped after kSampleArcs arcs (a hub row would make one thread walk
+// it all); the tiles of the rest are extrapolated at the same rate.
+constexpr int kSampleArcs = 256;
+
 __global__ void tile_sample_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                    int32_t n, const int32_t* __restrict__ rbs, int count,
                                    unsigned long long* __restrict__ acc) {
@@ -500,16 +552,20 @@ __global__ void tile_sample_kernel(const int32_t* __restrict__ rp, const int32_t
         end[i] = v < n ? rp[v + 1] : 0;
         arcs += end[i] - cur[i];
     }
-    long long tiles = 0;
-    for (;;) {
+    long long tiles = 0, seen = 0;
+    while (seen < kSampleArcs) {
         int cb = INT32_MAX;
         for (int i = 0; i < 8; ++i)
             if (cur[i] < end[i]) cb = min(cb, col[cur[i]] >> 3);
         if (cb == INT32_MAX) break;
         ++tiles;
         for (int i = 0; i < 8; ++i)
-            while (cur[i] < end[i] && (col[cur[i]] >> 3) == cb) ++cur[i];
+            while (cur[i] < end[i] && (col[cur[i]] >> 3) == cb) {
+                ++cur[i];
+                ++seen;
+            }
     }
+    if (seen > 0 && seen < arcs) tiles = (tiles * arcs + seen - 1) / seen;
     atomicAdd(&acc[0], (unsigned long long)arcs);
     atomicAdd(&acc[1], (unsigned long long)tiles);
 }
@@ -791,20 +847,34 @@ mis_graph* mis_create_ex(int32_t n, const int32_t* row_ptr, const int32_t* col_i
         return nullptr;
     }
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    e = cudaMemsetAsync(d.col, 0, sizeof(int32_t) * (size_t)col_alloc, s);
+    // only the padding after the last arc needs zeros (int4 loads read it)
+    e = cudaMemsetAsync(d.col + arcs, 0, sizeof(int32_t) * (size_t)(col_alloc - arcs), s);
     if (e == cudaSuccess && n > 0)
         e = cudaMemcpyAsync(d.rp, row_ptr, sizeof(int32_t) * ((size_t)n + 1), kind, s);
     if (e == cudaSuccess && n == 0) e = cudaMemsetAsync(d.rp, 0, sizeof(int32_t), s);
-    if (e == cudaSuccess && arcs > 0)
-        e = cudaMemcpyAsync(d.col, col_idx, sizeof(int32_t) * (size_t)arcs, kind, s);
     if (e != cudaSuccess) {
         set_cuda_error(e, "graph upload");
         free_graph(g);
         return nullptr;
     }
-    if (n > 0 && validate_device(g, s) != MIS_OK) {
-        free_graph(g);
-        return nullptr;
+    const bool pipelined = !on_device && !o.check_symmetry && arcs >= kUploadPiece;
+    if (pipelined) {
+        if (upload_checked(g, col_idx, s) != MIS_OK) {
+            free_graph(g);
+            return nullptr;
+        }
+    } else {
+        if (arcs > 0)
+            e = cudaMemcpyAsync(d.col, col_idx, sizeof(int32_t) * (size_t)arcs, kind, s);
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "graph upload");
+            free_graph(g);
+            return nullptr;
+        }
+        if (n > 0 && validate_device(g, s) != MIS_OK) {
+            free_graph(g);
+            return nullptr;
+        }
     }
     if (finish_create(g) != MIS_OK) {
         free_graph(g);

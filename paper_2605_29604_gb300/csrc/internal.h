@@ -125,6 +125,13 @@ int multi_max_coresident_blocks(int device);
 // kernels_util.cu
 cudaError_t launch_validate(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs,
                             int check_symmetry, unsigned* d_flags, cudaStream_t s);
+// The two halves of launch_validate: row pointers, then the arcs [a0, a1)
+// (which trust the row pointers).  Flags are ORed into *d_flags.
+cudaError_t launch_validate_rowptr(const int32_t* rp, int32_t n, int64_t arcs, unsigned* d_flags,
+                                   cudaStream_t s);
+cudaError_t launch_validate_arcs(const int32_t* rp, const int32_t* col, int32_t n, int64_t a0,
+                                 int64_t a1, int check_symmetry, unsigned* d_flags,
+                                 cudaStream_t s);
 cudaError_t launch_keys(const SolveArgs& a, uint32_t* out_key, cudaStream_t s);
 cudaError_t launch_fill_seg(int32_t* blk_seg, const int32_t* voff, int32_t count,
                             int32_t nblk, cudaStream_t s);

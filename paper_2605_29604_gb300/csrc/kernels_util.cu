@@ -25,13 +25,14 @@ __global__ void validate_rowptr_kernel(const int32_t* __restrict__ rp, int32_t n
 // arc by binary search over row_ptr and walks forward from there.
 constexpr int kArcsPerThread = 16;
 
+// Checks the arcs [a0, a1) (all of them: a0 = 0, a1 = arcs).
 __global__ void validate_arcs_kernel(const int32_t* __restrict__ rp,
-                                     const int32_t* __restrict__ col, int32_t n, int64_t arcs,
-                                     int check_symmetry, unsigned* flags) {
+                                     const int32_t* __restrict__ col, int32_t n, int64_t a0,
+                                     int64_t a1, int check_symmetry, unsigned* flags) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t p0 = t * kArcsPerThread;
-    if (p0 >= arcs) return;
-    const int64_t p1 = (arcs < p0 + kArcsPerThread) ? arcs : p0 + kArcsPerThread;
+    const int64_t p0 = a0 + t * kArcsPerThread;
+    if (p0 >= a1) return;
+    const int64_t p1 = (a1 < p0 + kArcsPerThread) ? a1 : p0 + kArcsPerThread;
     // row = last v with rp[v] <= p0
     int lo = 0, hi = n;  // invariant rp[lo] <= p0 < rp[hi]
     while (hi - lo > 1) {
@@ -83,10 +84,28 @@ cudaError_t launch_validate(const int32_t* rp, const int32_t* col, int32_t n, in
     e = cudaMemcpyAsync(&hflags, d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess || hflags || arcs == 0) return e;
-    const long long work = (arcs + kArcsPerThread - 1) / kArcsPerThread;
+    return launch_validate_arcs(rp, col, n, 0, arcs, check_symmetry, d_flags, s);
+}
+
+cudaError_t launch_validate_rowptr(const int32_t* rp, int32_t n, int64_t arcs, unsigned* d_flags,
+                                   cudaStream_t s) {
+    const int threads = 256;
+    long long blocks = (n + threads - 1) / threads;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 65535) blocks = 65535;
+    validate_rowptr_kernel<<<(unsigned)blocks, threads, 0, s>>>(rp, n, arcs, d_flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_arcs(const int32_t* rp, const int32_t* col, int32_t n, int64_t a0,
+                                 int64_t a1, int check_symmetry, unsigned* d_flags,
+                                 cudaStream_t s) {
+    if (a1 <= a0) return cudaSuccess;
+    const int threads = 256;
+    const long long work = (a1 - a0 + kArcsPerThread - 1) / kArcsPerThread;
     const long long ablocks = (work + threads - 1) / threads;
-    validate_arcs_kernel<<<(unsigned)ablocks, threads, 0, s>>>(rp, col, n, arcs, check_symmetry,
-                                                                d_flags);
+    validate_arcs_kernel<<<(unsigned)ablocks, threads, 0, s>>>(rp, col, n, a0, a1,
+                                                                check_symmetry, d_flags);
     return cudaGetLastError();
 }
 

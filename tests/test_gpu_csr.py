@@ -300,3 +300,31 @@ def test_batch_union_equals_standalone(count):
             assert off == len(got)
     finally:
         native.mis_destroy(h)
+
+
+def test_large_host_upload_checks_every_piece():
+    """Host graphs of many arcs go up in pieces, each checked as it lands
+    (symmetry check off): a defect in the last piece is still rejected, and
+    a clean copy solves to a valid maximal independent set."""
+    n, rp, col = gg.rmat(20, 16, 0.57, 0.19, 0.19, 41, permute=True)
+    assert rp[-1] > (16 << 20)  # at least two pieces
+    for kind in ("range", "self", "order"):
+        bad = col.copy()
+        v = int(np.searchsorted(rp, len(col) - 1, side="right") - 1)  # row of the last arc
+        if kind == "range":
+            bad[-1] = n
+        elif kind == "self":
+            bad[-1] = v
+        else:
+            bad[-1] = bad[-2] if rp[v + 1] - rp[v] >= 2 else bad[-1]
+            if rp[v + 1] - rp[v] < 2:
+                continue
+        with pytest.raises(native.MisError):
+            native.mis_create_ex(n, rp, bad, 0, native.options(check_symmetry=0), None)
+    h = native.mis_create_ex(n, rp, col, 0, native.options(check_symmetry=0), None)
+    try:
+        got, st = gpu_solve(h, [5])
+        assert oracle.check(n, rp, col, got) == (0, -1)
+        assert st.mis_size == int(got.sum())
+    finally:
+        native.mis_destroy(h)
