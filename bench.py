@@ -191,35 +191,46 @@ def run_reference(args):
 
 
 def _dist_setup():
+    """World size, rank and local rank from the torchrun environment: one
+    process per GPU over NCCL, or gloo on a host without a GPU."""
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
     return world, rank, local
 
 
-def _max_over_ranks(x, world):
+def _reduce_over_ranks(x, world, op):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], device="cuda", dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def _max_over_ranks(x, world):
+    import torch.distributed as dist
+    return _reduce_over_ranks(x, world, dist.ReduceOp.MAX)
 
 
 def _sum_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], device="cuda", dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce_over_ranks(x, world, dist.ReduceOp.SUM)
+
+
+def replica_throughput(world, steps, units_per_step, max_total_ms):
+    """Whole-job throughput of `world` independent replicas (weak scaling):
+    every rank processes steps * units_per_step, the job takes the slowest
+    rank's time."""
+    return world * steps * units_per_step / (max_total_ms / 1e3)
 
 
 def time_device_steps(native, h, seeds, out_ptr, stream, steps, warmup, local, world,
@@ -290,7 +301,7 @@ def run_single(args):
                                         args.warmup, local, world)
     total_ms = _max_over_ranks(sum(step_ms), world)
     st = native.mis_get_stats(h)
-    value = world * args.steps * arcs / (total_ms / 1e3)
+    value = replica_throughput(world, args.steps, arcs, total_ms)
 
     # several seeds of the same resident graph per launch (mis_solve_multi_ex)
     multi = None
@@ -431,7 +442,7 @@ def run_batch(args):
     total_ms = _max_over_ranks(sum(step_ms), world)
     st = native.mis_get_stats(h)
     native.mis_replay_destroy(replay)
-    value = world * args.steps * arcs / (total_ms / 1e3)
+    value = replica_throughput(world, args.steps, arcs, total_ms)
     peak, peak_kind = _peak_hbm()
     alg_bytes = 4 * arcs + 4 * (nsum + 1) + 4 * nsum + nsum
     achieved = alg_bytes / ((total_ms / 1e3) / args.steps) / 1e9
