@@ -202,9 +202,11 @@ int use_tiles(mis_graph* g, int path, int T) {
         d.footprint += d.tile_footprint;
     }
     const bool tc = path == MIS_PATH_TILE_TC;
-    // a row block with many tiles gets a whole warp of tile slots
+    // a row block with many tiles gets a whole warp of tile slots; 8 x 8 row
+    // blocks with few tiles are taken one per lane (32 row blocks per warp
+    // pass: the selection test is latency-bound), 16 x 16 ones by 8 lanes
     const double per_rb = d.tiles.nrb ? (double)d.tiles.ntiles / d.tiles.nrb : 0.0;
-    g->tile_slots = per_rb > 12.0 ? 32 : 8;
+    g->tile_slots = per_rb > 12.0 ? 32 : (T == 8 ? 1 : 8);
     const int maxb = tile_max_coresident_blocks(T, g->tile_slots, tc, d.device);
     if (maxb <= 0) return set_error(MIS_EDEVICE, "no co-resident blocks for the tile kernel");
     long long want = ((long long)d.tiles.nrb + 63) / 64;

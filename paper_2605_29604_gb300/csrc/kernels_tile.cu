@@ -610,6 +610,11 @@ __global__ void __launch_bounds__(kTileBlock, 2) tile_solve_kernel(const SolveAr
 
 const void* tile_kernel_fn(int T, int S, bool tc) {
     if (tc) return T == 16 ? (const void*)tile_solve_kernel<16, 8, true> : nullptr;
+    if (T == 8 && S == 1) return (const void*)tile_solve_kernel<8, 1, false>;
+    if (T == 8 && S == 2) return (const void*)tile_solve_kernel<8, 2, false>;
+    if (T == 8 && S == 4) return (const void*)tile_solve_kernel<8, 4, false>;
+    if (T == 16 && S == 1) return (const void*)tile_solve_kernel<16, 1, false>;
+    if (T == 16 && S == 4) return (const void*)tile_solve_kernel<16, 4, false>;
     if (T == 8 && S == 8) return (const void*)tile_solve_kernel<8, 8, false>;
     if (T == 8 && S == 32) return (const void*)tile_solve_kernel<8, 32, false>;
     if (T == 16 && S == 8) return (const void*)tile_solve_kernel<16, 8, false>;
