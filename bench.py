@@ -428,7 +428,8 @@ def run_batch(args):
     arcs = int(sum(int(p[1][-1]) for p in parts))
     nsum = int(sum(p[0] for p in parts))
     t0 = time.perf_counter()
-    h = native.mis_create_batch(parts, native.options(device=local, check_symmetry=1))
+    h = native.mis_create_batch(parts, native.options(device=local, check_symmetry=1,
+                                                      order_rows=args.batch_order))
     t_create = time.perf_counter() - t0
     tuning = native.mis_autotune(h, 3)
     size = native.lib().mis_result_size(h)
@@ -621,6 +622,8 @@ def main():
                     help="DRAM bytes per launch from an ncu capture of this kernel")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-order", type=int, default=2, choices=[0, 1, 2],
+                    help="create-time row ordering of the batched union (mis_options.order_rows)")
     ap.add_argument("--pool", type=int, default=48)
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--seq-requests", type=int, default=2000)

@@ -28,9 +28,22 @@ __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
         dbar0 = average_degree(a.rp[n], n);
         smix0 = mix64(a.seed0);
     }
-    if (a.seg.count == 0 && (n_words & 3) == 0) {
-        // four vertices per thread: 16-byte loads of row_ptr, stores of words
+    if ((n_words & 3) == 0) {
+        // four vertices per thread: 16-byte loads of row_ptr, stores of words.
+        // In a batch the four share one 16-vertex block, hence one graph
+        // (offsets are multiples of 16): its parameters are looked up once.
         for (long long v = 4 * tid; v < n_words; v += 4 * nthreads) {
+            float dbar = dbar0;
+            uint64_t smix = smix0;
+            long long first = 0;  // the graph's first vertex in the union
+            long long limit = n;  // its vertices
+            if (a.seg.count != 0 && v < n) {
+                const int g = a.seg.blk_seg[v >> 4];
+                first = a.seg.voff[g];
+                limit = a.seg.nv[g];
+                dbar = average_degree(a.seg.arcs[g], a.seg.nv[g]);
+                smix = mix64(a.seg.seed[g]);
+            }
             int r[5];
             if (v + 4 <= n) {
                 const int4 q = *reinterpret_cast<const int4*>(a.rp + v);
@@ -56,12 +69,16 @@ __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const long long u = v + k;
+                const long long local = u - first;
                 const int deg = r[k + 1] - r[k];
-                w[k] = u >= n ? kWordOut
-                              : (deg ? undecided_word(mode, priority_key(mode, dbar0, deg, smix0,
-                                                                        (uint32_t)u))
-                                     : iso);
-                if (((sure >> (8 * k)) & 0xFFu) == 1u) w[k] |= kWordInSet;
+                if (u >= n || local >= limit) {
+                    w[k] = kWordOut;  // beyond n, or padding between two graphs
+                } else {
+                    w[k] = deg ? undecided_word(mode, priority_key(mode, dbar, deg, smix,
+                                                                   (uint32_t)local))
+                               : iso;
+                    if (((sure >> (8 * k)) & 0xFFu) == 1u) w[k] |= kWordInSet;
+                }
             }
             *reinterpret_cast<uint4*>(a.word + v) = make_uint4(w[0], w[1], w[2], w[3]);
         }
