@@ -42,7 +42,7 @@ if ROOT not in sys.path:
 METRIC = "edges/s to full MIS on 1 GB300"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-PATH_NAMES = {1: "csr", 2: "tile", 3: "tile_tc"}
+PATH_NAMES = {1: "csr", 2: "tile", 3: "tile_tc", 4: "push"}
 
 
 def _peak_hbm():
@@ -290,7 +290,8 @@ def run_single(args):
         if args.csr_pending is not None:
             native.mis_set_csr_pending(h, args.csr_pending)
     elif args.path:
-        native.mis_set_path(h, {"tile": 2, "tile_tc": 3}[args.path], args.tile)
+        native.mis_set_path(h, {"tile": 2, "tile_tc": 3, "push": 4}[args.path],
+                            args.tile if args.path != "push" else 0)
     else:
         t0 = time.perf_counter()
         tuning = native.mis_autotune(h, 3)
@@ -614,7 +615,7 @@ def main():
     ap.add_argument("--tpr", type=int, default=None, help="force the CSR path with these lanes")
     ap.add_argument("--csr-pending", type=int, default=None, choices=[0, 1],
                     help="with --tpr: Phase 2 over Phase 1's pending list (1) or a triage (0)")
-    ap.add_argument("--path", default=None, choices=["tile", "tile_tc"])
+    ap.add_argument("--path", default=None, choices=["tile", "tile_tc", "push"])
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

@@ -68,7 +68,10 @@ enum {
     MIS_PATH_AUTO = 0,     /* autotuner's choice, cached per density class */
     MIS_PATH_CSR = 1,      /* warp-per-row CSR kernel on CUDA cores */
     MIS_PATH_TILE = 2,     /* tile-CSR kernel, bitmask payload, popc on CUDA cores */
-    MIS_PATH_TILE_TC = 3   /* tile-CSR kernel, exclusion test as tensor-core MMA */
+    MIS_PATH_TILE_TC = 3,  /* tile-CSR kernel, exclusion test as tensor-core MMA */
+    MIS_PATH_PUSH = 4      /* CSR, work-efficient push/decrement rounds: a count of
+                              undecided higher neighbours per vertex, decremented
+                              as they are excluded; every arc read O(1) times */
 };
 
 typedef struct mis_graph mis_graph;

@@ -435,7 +435,13 @@ int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_
     if (e != cudaSuccess) return set_cuda_error(e, "control reset");
     if (d.n > 0) {
         const bool tile = g->path == MIS_PATH_TILE || g->path == MIS_PATH_TILE_TC;
-        if (tile)
+        if (g->path == MIS_PATH_PUSH) {
+            const int maxb = push_max_coresident_blocks(d.device);
+            if (maxb <= 0) return set_error(MIS_EDEVICE, "no co-resident blocks for the push kernel");
+            long long grid = std::min<long long>(maxb, std::max<long long>(1, (d.n + 255) / 256));
+            if (blocks > 0) grid = std::min<long long>(grid, blocks);
+            e = launch_push_solve(a, (int)grid, s);
+        } else if (tile)
             e = launch_tile_solve(a, d.tiles.T, g->tile_slots, g->path == MIS_PATH_TILE_TC,
                                   blocks > 0 ? std::min(blocks, g->tile_grid) : g->tile_grid, s);
         else if (single_block)
@@ -626,6 +632,10 @@ std::string density_class(mis_graph* g, double apt) {
 
 int apply_choice(mis_graph* g, const TuneChoice& c) {
     if (c.path == MIS_PATH_TILE || c.path == MIS_PATH_TILE_TC) return use_tiles(g, c.path, c.param);
+    if (c.path == MIS_PATH_PUSH) {
+        g->path = MIS_PATH_PUSH;
+        return MIS_OK;
+    }
     g->path = MIS_PATH_CSR;
     int32_t thr[4];
     if (c.param) {
@@ -694,6 +704,11 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
     bins(INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, 0);  // one lane per row
     bins(-1, 65536, 65536, 65536, 0);                                     // four lanes per row
     if (g->d.n <= 65536) bins(8, 4096, 4096, 65536, std::max(1, (g->d.n + 1023) / 1024));
+    {
+        TuneChoice t;
+        t.path = MIS_PATH_PUSH;
+        cands.push_back(t);
+    }
     if (apt >= 2.5) {
         for (int T : {8, 16}) {
             TuneChoice t;
@@ -1049,7 +1064,7 @@ int mis_set_path(mis_graph* g, int32_t path, int32_t threads_per_row) {
     if (!g) return set_error(MIS_EINVAL, "null graph");
     if ((path == MIS_PATH_CSR || path == MIS_PATH_AUTO) && !valid_tpr(threads_per_row))
         return set_error(MIS_EINVAL, "bad threads_per_row");
-    if (path < MIS_PATH_AUTO || path > MIS_PATH_TILE_TC)
+    if (path < MIS_PATH_AUTO || path > MIS_PATH_PUSH)
         return set_error(MIS_EINVAL, "unknown path");
     std::lock_guard<std::mutex> lk(g->mu);
     if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
@@ -1057,6 +1072,10 @@ int mis_set_path(mis_graph* g, int32_t path, int32_t threads_per_row) {
     if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
     if (path == MIS_PATH_TILE || path == MIS_PATH_TILE_TC)
         return use_tiles(g, path, threads_per_row ? threads_per_row : 16);
+    if (path == MIS_PATH_PUSH) {
+        g->path = MIS_PATH_PUSH;
+        return MIS_OK;
+    }
     g->path = MIS_PATH_CSR;
     if (threads_per_row == g->tpr) return MIS_OK;
     g->tpr = threads_per_row;
@@ -1191,7 +1210,7 @@ int mis_get_stats(mis_graph* g, mis_stats* st) {
     st->threads_per_row = g->tpr;
     st->tile = g->d.tiles.T;
     st->csr_pending = g->csr_pending;
-    const bool csr = g->last_path != MIS_PATH_TILE && g->last_path != MIS_PATH_TILE_TC;
+    const bool csr = g->last_path == MIS_PATH_CSR;
     st->sure_in = csr ? g->d.n_sure_in : 0;
     st->sure_out = csr ? g->d.n_sure_out : 0;
     st->ntiles = g->d.tiles.ntiles;

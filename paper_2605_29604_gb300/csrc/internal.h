@@ -122,6 +122,11 @@ cudaError_t launch_multi_solve(const SolveArgs& a, uint32_t* word8, int k,
                                const MultiSeeds& seeds, int grid, cudaStream_t s);
 int multi_max_coresident_blocks(int device);
 
+// kernels_push.cu: the push/decrement form of the rounds (uses the worklist
+// buffers of `a` for its ready and excluded lists and per-vertex counts).
+cudaError_t launch_push_solve(const SolveArgs& a, int grid, cudaStream_t s);
+int push_max_coresident_blocks(int device);
+
 // kernels_util.cu
 cudaError_t launch_validate(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs,
                             int check_symmetry, unsigned* d_flags, cudaStream_t s);

@@ -34,6 +34,7 @@ MIS_PATH_AUTO = 0
 MIS_PATH_CSR = 1
 MIS_PATH_TILE = 2
 MIS_PATH_TILE_TC = 3
+MIS_PATH_PUSH = 4
 MIS_PRIORITY_EQ1 = 0
 MIS_PRIORITY_HASH = 1
 MIS_PRIORITY_EQ1_Q8 = 2
