@@ -142,6 +142,11 @@ typedef struct mis_stats {
                                 put in the MIS at init without a test */
     int64_t sure_out;        /* CSR path: neighbours of those, excluded in round 0
                                 without a test */
+    int64_t tested_arcs;     /* CSR path: arcs among the vertices neither of the
+                                above nor isolated (the tested subgraph), whose
+                                rows all scans but round 0's selection test read;
+                                -1 when the graph keeps no copy of them (more
+                                than half of the arcs) */
 } mis_stats;
 
 /* Fill *opt with the defaults listed above. */

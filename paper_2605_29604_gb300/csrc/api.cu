@@ -163,7 +163,7 @@ int rebin(mis_graph* g, const int32_t thr[4], cudaStream_t s) {
     for (int j = 0; j < 4; ++j) d.thr[j] = thr[j];
     Round0Plan plan;
     cudaError_t e = build_bins(d.rp, d.split, d.r0class, d.n, seg_of(d), d.thr, d.order0,
-                               d.sure_out, &plan, s);
+                               d.sure_out, d.s0_rp, d.s0_pre, d.order0_s0, &plan, s);
     if (e != cudaSuccess) return set_cuda_error(e, "degree binning");
     for (int j = 0; j < 6; ++j) d.bin_off[j] = plan.bin_off[j];
     d.n_isolated = plan.n_isolated;
@@ -256,6 +256,17 @@ int finish_create(mis_graph* g) {
         if (e == cudaSuccess)
             e = build_round0_classes(d.rp, d.col_sel, d.split, d.n, seg_of(d), d.r0class,
                                      g->own_stream);
+        // the tested subgraph, when it holds at most half of the arcs
+        int64_t s0_arcs = 0;
+        if (e == cudaSuccess)
+            e = build_s0_graph(d.rp, d.col_sel, d.split, d.r0class, d.n, d.arcs / 2, &d.s0_rp,
+                               &d.s0_col, &d.s0_pre, &s0_arcs, g->own_stream);
+        if (e == cudaSuccess && d.s0_rp) {
+            e = dalloc(&d.order0_s0, d.n, &d.footprint);
+            d.s0_arcs = s0_arcs;
+            d.s0_bytes = 4 * (2 * (int64_t)d.n + 1) + 4 * (((s0_arcs + 3) / 4) * 4 + 4);
+            d.footprint += d.s0_bytes;
+        }
         if (e != cudaSuccess) return set_cuda_error(e, "degree ordering");
     }
     const int brc = rebin(g, thr, g->own_stream);
@@ -360,6 +371,8 @@ SolveArgs make_args(mis_graph* g, Workspace& w) {
     a.n_isolated = d.n_isolated;
     a.r0class = d.r0class;
     a.sure_out = d.sure_out;
+    a.col_s0 = d.s0_col ? d.s0_col : a.col_sel;
+    a.order0_s0 = d.s0_col ? d.order0_s0 : nullptr;
     a.n_sure_in = d.n_sure_in;
     a.n_sure_out = d.n_sure_out;
     a.pending = g->csr_pending;
@@ -403,6 +416,10 @@ void free_graph(mis_graph* g) {
     dfree(d.word8);
     dfree(d.r0class);
     dfree(d.sure_out);
+    dfree(d.s0_rp);
+    dfree(d.s0_col);
+    dfree(d.s0_pre);
+    dfree(d.order0_s0);
     dfree(d.col_sel);
     dfree(d.split);
     ws_free(d.ws);
@@ -1213,6 +1230,7 @@ int mis_get_stats(mis_graph* g, mis_stats* st) {
     const bool csr = g->last_path == MIS_PATH_CSR;
     st->sure_in = csr ? g->d.n_sure_in : 0;
     st->sure_out = csr ? g->d.n_sure_out : 0;
+    st->tested_arcs = !csr ? 0 : g->d.s0_col ? g->d.s0_arcs : -1;
     st->ntiles = g->d.tiles.ntiles;
     st->alive_sum = (int64_t)c.alive_sum;
     st->mis_size = (int64_t)c.mis_size;

@@ -73,6 +73,12 @@ struct GraphData {
     uint8_t* r0class = nullptr;   // round-0 classes (with a degree-ordered adjacency)
     int32_t* sure_out = nullptr;  // sure round-0 exclusions
     uint32_t* word8 = nullptr;    // multi-seed solves: 8 words per vertex (lazily)
+    int32_t* s0_rp = nullptr;     // the tested subgraph (when it is small)
+    int32_t* s0_col = nullptr;
+    int32_t* s0_pre = nullptr;
+    int4* order0_s0 = nullptr;
+    int64_t s0_bytes = 0;
+    int64_t s0_arcs = 0;
     int32_t n_sure_in = 0;
     int32_t n_sure_out = 0;
     int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};

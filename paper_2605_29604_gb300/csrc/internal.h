@@ -58,6 +58,11 @@ struct SolveArgs {
     // round 0's Phase 2); neither is in order0.  Null / 0 when unused.
     const uint8_t* r0class = nullptr;
     const int32_t* sure_out = nullptr;
+    // The adjacency of every scan but round 0's selection test: the tested
+    // subgraph's rows where the graph has one (order0_s0[i] is then
+    // order0[i]'s row in it), else col_sel itself (order0_s0 null).
+    const int32_t* col_s0 = nullptr;
+    const int4* order0_s0 = nullptr;
     int32_t n_sure_in = 0;
     int32_t n_sure_out = 0;
     int32_t priority = 0;             // priority heuristic (kPrioEq1, kPrioHash, kPrioEq1Q8)
@@ -105,7 +110,19 @@ struct Round0Plan {
 // order0; the sure exclusions are listed in sure_out.
 cudaError_t build_bins(const int32_t* rp, const int32_t* split, const uint8_t* r0class,
                        int32_t n, const SegTable& seg, const int32_t thr[4], int4* order0,
-                       int32_t* sure_out, Round0Plan* plan, cudaStream_t s);
+                       int32_t* sure_out, const int32_t* s0_rp, const int32_t* s0_pre,
+                       int4* order0_s0, Round0Plan* plan, cudaStream_t s);
+// (with s0_rp, s0_pre and order0_s0 non-null, order0_s0[i] is order0[i]'s row
+// in the tested subgraph below)
+
+// The tested subgraph: the class-0 vertices' adjacency restricted to class-0
+// neighbours, each row in col_sel's order (s0_pre = its selection-prefix
+// length).  Built only when it has at most max_arcs arcs (else all outputs
+// null); the caller owns what it returns.
+cudaError_t build_s0_graph(const int32_t* rp, const int32_t* col_sel, const int32_t* split,
+                           const uint8_t* r0class, int32_t n, int64_t max_arcs, int32_t** s0_rp,
+                           int32_t** s0_col, int32_t** s0_pre, int64_t* s0_arcs,
+                           cudaStream_t s);
 
 // Create-time round-0 classes from the degree-ordered rows (col_sel, split):
 // 1 = sure candidate (empty selection prefix: every neighbour has degree >=

@@ -29,6 +29,8 @@
 // and gather the four neighbour words; scans stop at the first neighbour that
 // decides the test.
 #include <algorithm>
+
+#include <cub/cub.cuh>
 #include <cstdio>
 #include <vector>
 
@@ -154,13 +156,29 @@ __device__ __forceinline__ void lane_rows(const int32_t* __restrict__ col, Words
     }
 }
 
+// The adjacency the scans read.  Round 0's selection test reads the full
+// rows (col_sel); every other scan reads col_s0 (the tested subgraph's rows
+// where the graph has one, else col_sel).  Both come from the kernel
+// parameters, so they cost no registers across a phase.
+__device__ __forceinline__ const int32_t* select_col(const SolveArgs& a, bool late) {
+    return late ? a.col_s0 : a.col_sel;
+}
+__device__ __forceinline__ const int32_t* exclude_col(const SolveArgs& a) { return a.col_s0; }
+// The records of Phase 2 for the rows of `list` (a slice of W_r): in round 0
+// with a tested subgraph, the same rows of order0_s0.
+__device__ __forceinline__ const int4* pending_view(const SolveArgs& a, const int4* list,
+                                                    bool late) {
+    return (!late && a.order0_s0) ? a.order0_s0 + (list - a.order0) : list;
+}
+
 // Phase 1, bins 0..3: selection test of every row of the bin's list W_r.
 // Candidates are marked in the MIS.  kPending: the others form the pending
-// list P_r of Phase 2 (appended to pdst, counted in *pnext).
+// list P_r of Phase 2 (appended to pdst, counted in *pnext), each entry the
+// row's record in the adjacency Phase 2 scans.
 template <int TPR, int CH, bool kPending>
 __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __restrict__ list,
                                            int cnt, WarpSched& ws, unsigned* grab, int* pnext,
-                                           int4* __restrict__ pdst, int32_t* wbuf) {
+                                           int4* __restrict__ pdst, int32_t* wbuf, bool late) {
     constexpr int G = 32 / TPR;
     constexpr int kPass = TPR == 1 ? 32 * kRowsPerLane : G;  // rows of one warp pass
     static_assert(kPass <= kStageMax, "a warp pass exceeds the staging buffer");
@@ -190,8 +208,7 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __res
 #pragma unroll
                 for (int i = 0; i < kRowsPerLane; ++i)
                     wv[i] = valid[i] ? ld_word_l1(a.word + rec[i].x) : 0u;
-                lane_rows<kRowsPerLane, true>(a.col_sel, LiveWords{a.word}, rec, valid, wv,
-                                              blocked);
+                lane_rows<kRowsPerLane, true>(select_col(a, late), LiveWords{a.word}, rec, valid, wv, blocked);
 #pragma unroll
                 for (int i = 0; i < kRowsPerLane; ++i) {
                     if (valid[i] && !blocked[i]) a.word[rec[i].x] = wv[i] | kWordInSet;
@@ -205,16 +222,17 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __res
                 const int4 rec = valid ? list[item] : make_int4(0, 0, 0, 0);
                 const uint32_t wv = valid ? ld_word_l1(a.word + rec.x) : 0u;
                 const int e = valid ? rec.z : 0;
-                const bool blocked = group_scan<TPR, true>(a.col_sel, LiveWords{a.word}, rec.y, e,
-                                                           rec.x, wv, glane, gshift);
+                const bool blocked =
+                    group_scan<TPR, true>(select_col(a, late), LiveWords{a.word}, rec.y, e, rec.x, wv, glane, gshift);
                 const bool lead = glane == 0;
                 if (valid && !blocked && lead) a.word[rec.x] = wv | kWordInSet;
                 if (kPending) fill = stage_keep(valid && blocked && lead, item, wbuf, fill);
             }
-            if (kPending) fill = flush_if_full(wbuf, fill, kPass, list, pnext, pdst);
+            if (kPending)
+                fill = flush_if_full(wbuf, fill, kPass, pending_view(a, list, late), pnext, pdst);
         }
     }
-    if (kPending) flush_stage(wbuf, fill, list, pnext, pdst);
+    if (kPending) flush_stage(wbuf, fill, pending_view(a, list, late), pnext, pdst);
 }
 
 // Phase 2+3, bins 0..3: exclusion test, state update, compaction into
@@ -269,7 +287,7 @@ __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __re
                     idx[i] = valid[i] ? (kPending ? item : wscan[item]) : 0;
                     rec[i] = valid[i] ? list[idx[i]] : make_int4(0, 0, 0, 0);
                 }
-                lane_rows<kRowsPerLane, false>(a.col_sel, nbw, rec, valid, unused, excl);
+                lane_rows<kRowsPerLane, false>(exclude_col(a), nbw, rec, valid, unused, excl);
 #pragma unroll
                 for (int i = 0; i < kRowsPerLane; ++i) {
                     if (valid[i] && excl[i]) a.word[rec[i].x] = kWordOut;
@@ -282,7 +300,7 @@ __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __re
                 const int4 rec = valid ? list[idx] : make_int4(0, 0, 0, 0);
                 const int e = valid ? rec.w : 0;
                 const bool excl =
-                    group_scan<TPR, false>(a.col_sel, nbw, rec.y, e, rec.x, 0u, glane, gshift);
+                    group_scan<TPR, false>(exclude_col(a), nbw, rec.y, e, rec.x, 0u, glane, gshift);
                 const bool lead = glane == 0;
                 if (valid && excl && lead) a.word[rec.x] = kWordOut;
                 fill = stage_keep(valid && !excl && lead, idx, wbuf, fill);
@@ -298,8 +316,10 @@ __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __re
 // (survivors appended to W_{r+1}); hub rows are few, so entries are appended
 // one by one.
 template <bool kSelect, bool kPending>
-__device__ __forceinline__ void block_bin(const SolveArgs& a, const int4* __restrict__ list, int cnt, unsigned* grab,
-                                          int* next, int4* __restrict__ dst) {
+__device__ __forceinline__ void block_bin(const SolveArgs& a, const int4* __restrict__ list,
+                                          int cnt, unsigned* grab, int* next,
+                                          int4* __restrict__ dst, bool late) {
+    const int32_t* __restrict__ col = kSelect ? select_col(a, late) : exclude_col(a);
     __shared__ int s_row;
     if ((int)blockIdx.x >= cnt) return;  // no row left for this block
     int item = (int)blockIdx.x;          // first row: no atomic
@@ -317,7 +337,7 @@ __device__ __forceinline__ void block_bin(const SolveArgs& a, const int4* __rest
             const int p0 = base + 4 * (int)threadIdx.x;
             bool hit = false;
             if (p0 < e) {
-                const int4 c = __ldg(reinterpret_cast<const int4*>(a.col_sel + p0));
+                const int4 c = __ldg(reinterpret_cast<const int4*>(col + p0));
                 const uint32_t w0 = (p0 >= b) ? ld_word_l1(a.word + c.x) : 0u;
                 const uint32_t w1 = (p0 + 1 >= b && p0 + 1 < e) ? ld_word_l1(a.word + c.y) : 0u;
                 const uint32_t w2 = (p0 + 2 >= b && p0 + 2 < e) ? ld_word_l1(a.word + c.z) : 0u;
@@ -336,7 +356,7 @@ __device__ __forceinline__ void block_bin(const SolveArgs& a, const int4* __rest
         if (threadIdx.x == 0 && !skip) {
             if (kSelect) {
                 if (!found) a.word[v] = wv | kWordInSet;
-                else if (kPending) dst[atomicAdd(next, 1)] = rec;
+                else if (kPending) dst[atomicAdd(next, 1)] = pending_view(a, list, late)[item];
             } else if (found) {
                 a.word[v] = kWordOut;
             } else {
@@ -372,10 +392,14 @@ __device__ __forceinline__ void select_bin_at(const SolveArgs& a, const int4* li
                                               bool late, WarpSched& ws, unsigned* grab,
                                               int* pnext, int4* pend, int32_t* wbuf) {
     switch (lanes_per_row<BASE>(cnt, late, ws.nwarps)) {
-        case 32: select_bin<32, kChunk3, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf); break;
-        case 16: select_bin<16, kChunk2, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf); break;
-        case 4: select_bin<4, kChunk1, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf); break;
-        default: select_bin<BASE, CH, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf);
+        case 32:
+            select_bin<32, kChunk3, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf, late);
+            break;
+        case 16:
+            select_bin<16, kChunk2, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf, late);
+            break;
+        case 4: select_bin<4, kChunk1, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf, late); break;
+        default: select_bin<BASE, CH, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf, late);
     }
 }
 
@@ -404,7 +428,7 @@ __device__ __forceinline__ void select_phase(const SolveArgs& a, const int4* src
                                              bool late, WarpSched& ws, unsigned* grab,
                                              int* pnext, int4* pend, int32_t* wbuf) {
     const int* off = a.bin_off;
-    block_bin<true, kPending>(a, src + off[4], cnt[4], &grab[4], &pnext[4], pend + off[4]);
+    block_bin<true, kPending>(a, src + off[4], cnt[4], &grab[4], &pnext[4], pend + off[4], late);
     select_bin_at<32, kChunk3, kPending>(a, src + off[3], cnt[3], late, ws, &grab[3], &pnext[3],
                                          pend + off[3], wbuf);
     select_bin_at<16, kChunk2, kPending>(a, src + off[2], cnt[2], late, ws, &grab[2], &pnext[2],
@@ -422,7 +446,7 @@ __device__ __forceinline__ void exclude_phase(const SolveArgs& a, const int4* li
                                               unsigned* grab, int* next, int4* dst,
                                               int32_t* wbuf, int32_t* wscan) {
     const int* off = a.bin_off;
-    block_bin<false, kPending>(a, list + off[4], cnt[4], &grab[4], &next[4], dst + off[4]);
+    block_bin<false, kPending>(a, list + off[4], cnt[4], &grab[4], &next[4], dst + off[4], late);
     exclude_bin_at<32, kChunk3, kPending>(a, list + off[3], cnt[3], late, ws, &grab[3],
                                           &next[3], dst + off[3], wbuf, wscan);
     exclude_bin_at<16, kChunk2, kPending>(a, list + off[2], cnt[2], late, ws, &grab[2],
@@ -544,9 +568,9 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
         if (kPending)
             exclude_phase<true>(a, a.wlp, s_pcnt, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next,
                                 dst, wbuf, wscan);
-        else
-            exclude_phase<false>(a, src, s_cnt, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next, dst,
-                                 wbuf, wscan);
+        else  // W_r's rows in the adjacency Phase 2 scans
+            exclude_phase<false>(a, pending_view(a, src, r > 0), s_cnt, r > 0, ws,
+                                 ctl->grab[(2 * r + 1) & 3], next, dst, wbuf, wscan);
         const int cur = total + (r == 0 ? decided0 : 0);
         if (!grid_barrier(
                 ctl, nblocks, a.spin_cap,
@@ -661,7 +685,10 @@ __global__ void bin_scatter_kernel(const int32_t* __restrict__ rp,
                                    const uint8_t* __restrict__ r0class, int32_t n,
                                    const SegTable seg, const BinThr thr,
                                    const int32_t* __restrict__ blkoff,
-                                   int4* __restrict__ order0, int32_t* __restrict__ sure_out) {
+                                   int4* __restrict__ order0, int32_t* __restrict__ sure_out,
+                                   const int32_t* __restrict__ s0_rp,
+                                   const int32_t* __restrict__ s0_pre,
+                                   int4* __restrict__ order0_s0) {
     __shared__ int wsum[8][kClasses];
     __shared__ int run[kClasses];
     const unsigned lane = lane_id();
@@ -688,6 +715,9 @@ __global__ void bin_scatter_kernel(const int32_t* __restrict__ rp,
             } else {
                 const int b = rp[v], e = rp[v + 1];
                 order0[off + rank] = make_int4((int)v, b, split ? b + split[v] : e, e);
+                if (order0_s0)  // the same row in the tested subgraph
+                    order0_s0[off + rank] =
+                        make_int4((int)v, s0_rp[v], s0_rp[v] + s0_pre[v], s0_rp[v + 1]);
             }
         }
         __syncthreads();
@@ -702,7 +732,8 @@ __global__ void bin_scatter_kernel(const int32_t* __restrict__ rp,
 
 cudaError_t build_bins(const int32_t* rp, const int32_t* split, const uint8_t* r0class,
                        int32_t n, const SegTable& seg, const int32_t thr[4], int4* order0,
-                       int32_t* sure_out, Round0Plan* plan, cudaStream_t s) {
+                       int32_t* sure_out, const int32_t* s0_rp, const int32_t* s0_pre,
+                       int4* order0_s0, Round0Plan* plan, cudaStream_t s) {
     *plan = Round0Plan{};
     if (n == 0) return cudaSuccess;
     const int blocks = (int)std::min<long long>(1024, ((long long)n + 255) / 256);
@@ -744,7 +775,7 @@ cudaError_t build_bins(const int32_t* rp, const int32_t* split, const uint8_t* r
     }
     if (e == cudaSuccess) {
         bin_scatter_kernel<<<blocks, 256, 0, s>>>(rp, split, r0class, n, seg, t, d_cnt, order0,
-                                                  sure_out);
+                                                  sure_out, s0_rp, s0_pre, order0_s0);
         e = cudaGetLastError();
     }
     const cudaError_t se = cudaStreamSynchronize(s);  // also on error: nothing may still run
@@ -808,6 +839,124 @@ cudaError_t build_round0_classes(const int32_t* rp, const int32_t* col_sel, cons
     cudaError_t e = cudaGetLastError();
     const cudaError_t se = cudaStreamSynchronize(s);
     return e != cudaSuccess ? e : se;
+}
+
+// ---------------------------------------------------------------- the tested subgraph
+//
+// S0 = the vertices of degree >= 1 that round 0 has to test (class 0).  An S0
+// vertex has no class-1 neighbour (else it would be class 2), so in round 0
+// its exclusion test can only be decided by an S0 candidate; and after round
+// 0 every vertex outside S0 is decided (class 1 in, class 2 out), so in every
+// later round both tests only need the S0 neighbours.  Round 0's selection
+// test is the one exception (class-2 neighbours are still undecided then) and
+// keeps the full rows.  Where S0 is small (power-law graphs), its internal
+// adjacency -- each row in col_sel's order, selection prefix first -- makes
+// those scans short.
+
+__device__ __forceinline__ bool in_s0(const uint8_t* r0class, const int32_t* rp, long long v) {
+    return r0class[v] == 0 && rp[v + 1] > rp[v];
+}
+
+// One warp per vertex: S0 neighbours of an S0 row, in its selection prefix
+// (pre) and in all (tot); 0 for the other vertices.
+__global__ void s0_count_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col_sel,
+                                const int32_t* __restrict__ split,
+                                const uint8_t* __restrict__ r0class, int32_t n,
+                                int32_t* __restrict__ tot, int32_t* __restrict__ pre) {
+    const long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const unsigned lane = lane_id();
+    if (v >= n) return;
+    int ct = 0, cp = 0;
+    if (in_s0(r0class, rp, v)) {
+        const int b = rp[v], e = rp[v + 1], es = b + split[v];
+        for (int p = b + (int)lane; p < e; p += 32) {
+            const bool hit = in_s0(r0class, rp, col_sel[p]);
+            ct += hit;
+            cp += hit && p < es;
+        }
+        for (int o = 16; o; o >>= 1) {
+            ct += __shfl_xor_sync(0xFFFFFFFFu, ct, o);
+            cp += __shfl_xor_sync(0xFFFFFFFFu, cp, o);
+        }
+    }
+    if (lane == 0) {
+        tot[v] = ct;
+        pre[v] = cp;
+    }
+}
+
+// One warp per S0 row: its S0 neighbours, in order, to s0_col[s0_rp[v] ...].
+__global__ void s0_scatter_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col_sel,
+                                  const uint8_t* __restrict__ r0class, int32_t n,
+                                  const int32_t* __restrict__ s0_rp, int32_t* __restrict__ s0_col) {
+    const long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const unsigned lane = lane_id();
+    if (v >= n || !in_s0(r0class, rp, v)) return;
+    const int b = rp[v], e = rp[v + 1];
+    int out = s0_rp[v];
+    for (int p0 = b; p0 < e; p0 += 32) {
+        const int p = p0 + (int)lane;
+        const int u = p < e ? col_sel[p] : 0;
+        const bool hit = p < e && in_s0(r0class, rp, u);
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, hit);
+        if (hit) s0_col[out + __popc(bal & lanemask_lt())] = u;
+        out += __popc(bal);
+    }
+}
+
+cudaError_t build_s0_graph(const int32_t* rp, const int32_t* col_sel, const int32_t* split,
+                           const uint8_t* r0class, int32_t n, int64_t max_arcs, int32_t** s0_rp,
+                           int32_t** s0_col, int32_t** s0_pre, int64_t* s0_arcs,
+                           cudaStream_t s) {
+    *s0_rp = *s0_col = *s0_pre = nullptr;
+    *s0_arcs = 0;
+    if (n == 0) return cudaSuccess;
+    int32_t *tot = nullptr, *rpo = nullptr, *pre = nullptr, *colo = nullptr;
+    void* temp = nullptr;
+    size_t temp_bytes = 0;
+    const unsigned blocks = (unsigned)((32LL * n + 255) / 256);
+    cudaError_t e = dev_alloc((void**)&tot, sizeof(int32_t) * ((size_t)n + 1));
+    if (e == cudaSuccess) e = dev_alloc((void**)&rpo, sizeof(int32_t) * ((size_t)n + 1));
+    if (e == cudaSuccess) e = dev_alloc((void**)&pre, sizeof(int32_t) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tot + n, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) {
+        s0_count_kernel<<<blocks, 256, 0, s>>>(rp, col_sel, split, r0class, n, tot, pre);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cub::DeviceScan::ExclusiveSum(nullptr, temp_bytes, tot, rpo, n + 1, s);
+    if (e == cudaSuccess) e = dev_alloc(&temp, temp_bytes ? temp_bytes : 1);
+    if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(temp, temp_bytes, tot, rpo, n + 1, s);
+    int32_t total = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&total, rpo + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const bool worth = e == cudaSuccess && (int64_t)total <= max_arcs;
+    if (worth) {
+        // padded like col_idx: 16-byte slices may read up to 3 entries past a row
+        const size_t alloc = ((size_t)total + 3) / 4 * 4 + 4;
+        e = dev_alloc((void**)&colo, sizeof(int32_t) * alloc);
+        if (e == cudaSuccess) e = cudaMemsetAsync(colo, 0, sizeof(int32_t) * alloc, s);
+        if (e == cudaSuccess) {
+            s0_scatter_kernel<<<blocks, 256, 0, s>>>(rp, col_sel, r0class, n, rpo, colo);
+            e = cudaGetLastError();
+        }
+    }
+    const cudaError_t se = cudaStreamSynchronize(s);  // also on error: nothing may still run
+    if (e == cudaSuccess) e = se;
+    dev_free(tot);
+    dev_free(temp);
+    if (e != cudaSuccess || !worth) {
+        dev_free(rpo);
+        dev_free(pre);
+        dev_free(colo);
+        return e;
+    }
+    *s0_rp = rpo;
+    *s0_col = colo;
+    *s0_pre = pre;
+    *s0_arcs = total;
+    return cudaSuccess;
 }
 
 }  // namespace tcmis

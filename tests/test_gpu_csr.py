@@ -132,6 +132,26 @@ def _sure_sets(g):
     return int(sure_in.sum()), int(sure_out.sum())
 
 
+def _tested_arcs(g):
+    """Arcs between vertices that are neither isolated nor decided at create
+    time: the only ones the round-0 exclusion test and every later round can
+    need, since every other vertex is decided by the end of round 0."""
+    n, rp, col = g
+    rp = rp.astype(np.int64)
+    deg = np.diff(rp)
+    if len(col) == 0:
+        return 0
+    src = np.repeat(np.arange(n), deg)
+    outranked = (deg[col] >= deg[src] + 2)
+    nz = deg > 0
+    all_lower = np.zeros(n, dtype=bool)
+    all_lower[nz] = np.logical_and.reduceat(outranked, rp[:-1][nz])
+    has = np.zeros(n, dtype=bool)
+    has[nz] = np.logical_or.reduceat(all_lower[col], rp[:-1][nz])
+    tested = nz & ~has & ~all_lower
+    return int((tested[src] & tested[col]).sum())
+
+
 @pytest.mark.parametrize("order_rows", [0, 1, 2])
 @pytest.mark.parametrize("name", ["rmat14", "star_hub", "er_10k", "k_ab", "grid", "path", "empty"])
 def test_round0_sure_sets(name, order_rows):
@@ -146,6 +166,10 @@ def test_round0_sure_sets(name, order_rows):
             assert_same(g, 13, got, st)
             want = _sure_sets(g) if order_rows else (0, 0)
             assert (st.sure_in, st.sure_out) == want
+            # the tested subgraph is kept when it holds at most half the arcs
+            t = _tested_arcs(g)
+            want_t = t if order_rows and 2 * t <= len(g[2]) and g[0] > 0 else -1
+            assert st.tested_arcs == want_t
     finally:
         native.mis_destroy(h)
 
