@@ -147,6 +147,10 @@ typedef struct mis_stats {
                                 rows all scans but round 0's selection test read;
                                 -1 when the graph keeps no copy of them (more
                                 than half of the arcs) */
+    int64_t keyed;           /* CSR path: vertices whose Eq. 1 key a solve computes
+                                when the graph has a tested subgraph (its
+                                vertices and those of their selection prefixes;
+                                no other word is read); -1 = every vertex */
 } mis_stats;
 
 /* Fill *opt with the defaults listed above. */

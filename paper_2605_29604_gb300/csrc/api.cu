@@ -267,6 +267,11 @@ int finish_create(mis_graph* g) {
             d.s0_bytes = 4 * (2 * (int64_t)d.n + 1) + 4 * (((s0_arcs + 3) / 4) * 4 + 4);
             d.footprint += d.s0_bytes;
         }
+        if (e == cudaSuccess && d.s0_col && d.count == 0) {
+            e = build_keyed(d.rp, d.col_sel, d.split, d.r0class, d.n, &d.keyed, &d.n_keyed,
+                            &d.out0, g->own_stream);
+            d.footprint += 8 * ((int64_t)d.n_keyed + 1) + ((int64_t)d.n + 15) / 16 * 16;
+        }
         if (e != cudaSuccess) return set_cuda_error(e, "degree ordering");
     }
     const int brc = rebin(g, thr, g->own_stream);
@@ -373,6 +378,10 @@ SolveArgs make_args(mis_graph* g, Workspace& w) {
     a.sure_out = d.sure_out;
     a.col_s0 = d.s0_col ? d.s0_col : a.col_sel;
     a.order0_s0 = d.s0_col ? d.order0_s0 : nullptr;
+    a.direct = d.count == 0 ? 1 : 0;
+    a.keyed = d.keyed;
+    a.out0 = d.out0;
+    a.n_keyed = d.n_keyed;
     a.n_sure_in = d.n_sure_in;
     a.n_sure_out = d.n_sure_out;
     a.pending = g->csr_pending;
@@ -420,6 +429,8 @@ void free_graph(mis_graph* g) {
     dfree(d.s0_col);
     dfree(d.s0_pre);
     dfree(d.order0_s0);
+    dfree(d.keyed);
+    dfree(d.out0);
     dfree(d.col_sel);
     dfree(d.split);
     ws_free(d.ws);
@@ -1231,6 +1242,7 @@ int mis_get_stats(mis_graph* g, mis_stats* st) {
     st->sure_in = csr ? g->d.n_sure_in : 0;
     st->sure_out = csr ? g->d.n_sure_out : 0;
     st->tested_arcs = !csr ? 0 : g->d.s0_col ? g->d.s0_arcs : -1;
+    st->keyed = !csr ? 0 : g->d.out0 ? g->d.n_keyed : -1;
     st->ntiles = g->d.tiles.ntiles;
     st->alive_sum = (int64_t)c.alive_sum;
     st->mis_size = (int64_t)c.mis_size;

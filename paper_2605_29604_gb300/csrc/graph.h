@@ -79,6 +79,9 @@ struct GraphData {
     int4* order0_s0 = nullptr;
     int64_t s0_bytes = 0;
     int64_t s0_arcs = 0;
+    int2* keyed = nullptr;        // vertices whose words a solve reads (with s0_col)
+    uint8_t* out0 = nullptr;      // result bytes decided at create time
+    int32_t n_keyed = 0;
     int32_t n_sure_in = 0;
     int32_t n_sure_out = 0;
     int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};

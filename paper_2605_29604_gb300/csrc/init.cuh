@@ -13,9 +13,12 @@ namespace tcmis {
 // isolated_in they are written in the MIS right away (the CSR kernel keeps
 // them out of its worklists), and so are the sure round-0 candidates of
 // a.r0class (class 1); else isolated vertices get a fixed key and are decided
-// in round 0 like every other vertex.  Grid-stride over the whole launch.
+// in round 0 like every other vertex.  With `out` (a single graph), the
+// result byte of every vertex < n is written too: 1 for those put in the MIS
+// here, 0 for the rest until a round selects them.  Grid-stride over the
+// whole launch.
 __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
-                                           bool isolated_in) {
+                                           bool isolated_in, uint8_t* out = nullptr) {
     const uint8_t* r0class = isolated_in ? a.r0class : nullptr;
     const int mode = a.priority;
     const uint32_t iso = isolated_in ? (kKeyIsolated | kWordInSet) : kKeyIsolated;
@@ -81,6 +84,16 @@ __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
                 }
             }
             *reinterpret_cast<uint4*>(a.word + v) = make_uint4(w[0], w[1], w[2], w[3]);
+            if (out && v < n) {
+                uint32_t b = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) b |= (uint32_t)(w[k] >= kWordInMin) << (8 * k);
+                if (v + 4 <= n && ((uintptr_t)(out + v) & 3) == 0) {
+                    *reinterpret_cast<uint32_t*>(out + v) = b;
+                } else {
+                    for (int k = 0; k < 4 && v + k < n; ++k) out[v + k] = (uint8_t)(b >> (8 * k));
+                }
+            }
         }
         return;
     }
@@ -107,6 +120,7 @@ __device__ __forceinline__ void init_words(const SolveArgs& a, int32_t n_words,
                 }
             }
             if (r0class && r0class[v] == 1) w |= kWordInSet;
+            if (out) out[v] = w >= kWordInMin;
         }
         a.word[v] = w;
     }

@@ -63,6 +63,17 @@ struct SolveArgs {
     // order0[i]'s row in it), else col_sel itself (order0_s0 null).
     const int32_t* col_s0 = nullptr;
     const int4* order0_s0 = nullptr;
+    // With these (single graphs with a tested subgraph): the solve computes
+    // the keys of keyed[0 .. n_keyed) only, starts the result from out0 and
+    // marks its candidates in it as it selects them (no output pass).
+    const int2* keyed = nullptr;
+    const uint8_t* out0 = nullptr;
+    int32_t n_keyed = 0;
+    // 1 (single graphs): the CSR kernel writes the result as it decides --
+    // the create-time part at init, candidates as they are selected -- and
+    // counts the MIS size on the way, so it needs no output pass and a small
+    // last worklist can be finished by one block
+    int32_t direct = 0;
     int32_t n_sure_in = 0;
     int32_t n_sure_out = 0;
     int32_t priority = 0;             // priority heuristic (kPrioEq1, kPrioHash, kPrioEq1Q8)
@@ -123,6 +134,14 @@ cudaError_t build_s0_graph(const int32_t* rp, const int32_t* col_sel, const int3
                            const uint8_t* r0class, int32_t n, int64_t max_arcs, int32_t** s0_rp,
                            int32_t** s0_col, int32_t** s0_pre, int64_t* s0_arcs,
                            cudaStream_t s);
+// The keyed vertices of a graph with a tested subgraph (S0 and the vertices
+// of S0 rows' selection prefixes; {vertex, degree}, sorted by vertex) and the
+// result bytes known at create time (out0[v] = 1 for isolated vertices and
+// sure candidates; padded to a multiple of 16).  Device arrays, owned by the
+// caller.
+cudaError_t build_keyed(const int32_t* rp, const int32_t* col_sel, const int32_t* split,
+                        const uint8_t* r0class, int32_t n, int2** keyed, int32_t* n_keyed,
+                        uint8_t** out0, cudaStream_t s);
 
 // Create-time round-0 classes from the degree-ordered rows (col_sel, split):
 // 1 = sure candidate (empty selection prefix: every neighbour has degree >=

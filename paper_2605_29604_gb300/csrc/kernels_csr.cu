@@ -47,6 +47,14 @@ constexpr int kCsrMinBlocksPerSm = 3;
 // bound by load latency, so independent rows per lane add loads in flight).
 constexpr int kRowsPerLane = 2;
 constexpr int kWarps = kCsrBlock / 32;
+// A worklist of at most this many rows (after round 0) is finished by one
+// block: its rounds then cost two block-wide barriers instead of two grid
+// barriers, which on a grid of hundreds of blocks take microseconds each.
+constexpr int kSoloRows = 512;
+// ... in the triage form of the kernel; the pending form keeps the grid (at
+// its register budget the switch costs it spills in the scans).
+template <bool kPending>
+constexpr bool kSoloPath = !kPending;
 
 // Most rows per chunk taken by one warp, per bin (bin 4 is taken a row at a
 // time by a whole block).  A bin of up to nwarps * CH rows is split into equal
@@ -171,13 +179,49 @@ __device__ __forceinline__ const int4* pending_view(const SolveArgs& a, const in
     return (!late && a.order0_s0) ? a.order0_s0 + (list - a.order0) : list;
 }
 
+// Warps taking part in the rounds: the grid's, or block 0's once it finishes
+// the rounds alone (kept in shared memory so that the switch costs the
+// scans no register).
+__shared__ int s_nwarps;
+
+// Static first chunks of each bin, one per warp, rotating over the warps
+// from bin to bin (the chunk plan of the worklists), over s_nwarps warps.
+struct RoundSched {
+    int gw;    // this warp's index among the warps taking part
+    int base;  // first warp of the next bin
+    __device__ __forceinline__ int nwarps() const { return s_nwarps; }
+    __device__ __forceinline__ int first(int total) {
+        const int n = nwarps();
+        int k = gw - base;
+        if (k < 0) k += n;
+        base += total < n ? total : 0;
+        if (base >= n) base -= n;
+        return k;
+    }
+};
+
+// Candidates this block selected (with a.direct: the MIS size is counted as
+// vertices are selected, there is no output pass).
+__shared__ unsigned s_selected;
+// 1 while block 0 finishes a small worklist alone (its hub bin then takes
+// every row itself)
+__shared__ int s_solo;
+
+// Puts v (a Phase 1 candidate, word already marked) in the result.
+__device__ __forceinline__ void mark_selected(const SolveArgs& a, int v) {
+    if (a.direct) {
+        if (a.out) a.out[v] = 1;
+        atomicAdd(&s_selected, 1u);
+    }
+}
+
 // Phase 1, bins 0..3: selection test of every row of the bin's list W_r.
 // Candidates are marked in the MIS.  kPending: the others form the pending
 // list P_r of Phase 2 (appended to pdst, counted in *pnext), each entry the
 // row's record in the adjacency Phase 2 scans.
 template <int TPR, int CH, bool kPending>
 __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __restrict__ list,
-                                           int cnt, WarpSched& ws, unsigned* grab, int* pnext,
+                                           int cnt, RoundSched& ws, unsigned* grab, int* pnext,
                                            int4* __restrict__ pdst, int32_t* wbuf, bool late) {
     constexpr int G = 32 / TPR;
     constexpr int kPass = TPR == 1 ? 32 * kRowsPerLane : G;  // rows of one warp pass
@@ -187,9 +231,9 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __res
     const unsigned glane = lane % TPR;
     const unsigned gid = lane / TPR;
     const unsigned gshift = gid * TPR;
-    const ChunkPlan plan = plan_of<G, CH>(cnt, ws.nwarps);
+    const ChunkPlan plan = plan_of<G, CH>(cnt, ws.nwarps());
     int fill = 0;
-    for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps, grab)) {
+    for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps(), grab)) {
         int c0, c1;
         plan.range(k, cnt, c0, c1, G);
         for (int base = c0; base < c1; base += kPass) {
@@ -211,7 +255,10 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __res
                 lane_rows<kRowsPerLane, true>(select_col(a, late), LiveWords{a.word}, rec, valid, wv, blocked);
 #pragma unroll
                 for (int i = 0; i < kRowsPerLane; ++i) {
-                    if (valid[i] && !blocked[i]) a.word[rec[i].x] = wv[i] | kWordInSet;
+                    if (valid[i] && !blocked[i]) {
+                        a.word[rec[i].x] = wv[i] | kWordInSet;
+                        mark_selected(a, rec[i].x);
+                    }
                     if (kPending)
                         fill = stage_keep(valid[i] && blocked[i], base + (int)lane + 32 * i, wbuf,
                                           fill);
@@ -225,7 +272,10 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __res
                 const bool blocked =
                     group_scan<TPR, true>(select_col(a, late), LiveWords{a.word}, rec.y, e, rec.x, wv, glane, gshift);
                 const bool lead = glane == 0;
-                if (valid && !blocked && lead) a.word[rec.x] = wv | kWordInSet;
+                if (valid && !blocked && lead) {
+                    a.word[rec.x] = wv | kWordInSet;
+                    mark_selected(a, rec.x);
+                }
                 if (kPending) fill = stage_keep(valid && blocked && lead, item, wbuf, fill);
             }
             if (kPending)
@@ -242,7 +292,7 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __res
 // scan) into `wscan`.
 template <int TPR, int CH, bool kPending>
 __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __restrict__ list,
-                                            int cnt, WarpSched& ws, unsigned* grab, int* next,
+                                            int cnt, RoundSched& ws, unsigned* grab, int* next,
                                             int4* __restrict__ dst, int32_t* wbuf,
                                             int32_t* wscan) {
     constexpr int G = 32 / TPR;
@@ -255,9 +305,9 @@ __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __re
     const unsigned gid = lane / TPR;
     const unsigned gshift = gid * TPR;
     const LiveWords nbw{a.word};
-    const ChunkPlan plan = plan_of<G, CH>(cnt, ws.nwarps);
+    const ChunkPlan plan = plan_of<G, CH>(cnt, ws.nwarps());
     int fill = 0;
-    for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps, grab)) {
+    for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps(), grab)) {
         int c0, c1;
         plan.range(k, cnt, c0, c1, G);
         if (!kPending) {
@@ -355,7 +405,10 @@ __device__ __forceinline__ void block_bin(const SolveArgs& a, const int4* __rest
         }
         if (threadIdx.x == 0 && !skip) {
             if (kSelect) {
-                if (!found) a.word[v] = wv | kWordInSet;
+                if (!found) {
+                    a.word[v] = wv | kWordInSet;
+                    mark_selected(a, v);
+                }
                 else if (kPending) dst[atomicAdd(next, 1)] = pending_view(a, list, late)[item];
             } else if (found) {
                 a.word[v] = kWordOut;
@@ -363,9 +416,10 @@ __device__ __forceinline__ void block_bin(const SolveArgs& a, const int4* __rest
                 dst[atomicAdd(next, 1)] = rec;
             }
         }
-        if (cnt <= (int)gridDim.x) break;  // every row was a first row
+        const int nb = (kSoloPath<kPending> && s_solo) ? 1 : (int)gridDim.x;
+        if (cnt <= nb) break;  // every row was a first row
         __syncthreads();
-        if (threadIdx.x == 0) s_row = (int)gridDim.x + (int)atomicAdd(grab, 1u);
+        if (threadIdx.x == 0) s_row = nb + (int)atomicAdd(grab, 1u);
         __syncthreads();
         item = s_row;
     }
@@ -389,9 +443,9 @@ __device__ __forceinline__ int lanes_per_row(int cnt, bool late, int nwarps) {
 // Phase 1 of bin j (base width BASE, chunk CH) at the width lanes_per_row picks.
 template <int BASE, int CH, bool kPending>
 __device__ __forceinline__ void select_bin_at(const SolveArgs& a, const int4* list, int cnt,
-                                              bool late, WarpSched& ws, unsigned* grab,
+                                              bool late, RoundSched& ws, unsigned* grab,
                                               int* pnext, int4* pend, int32_t* wbuf) {
-    switch (lanes_per_row<BASE>(cnt, late, ws.nwarps)) {
+    switch (lanes_per_row<BASE>(cnt, late, ws.nwarps())) {
         case 32:
             select_bin<32, kChunk3, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf, late);
             break;
@@ -406,14 +460,14 @@ __device__ __forceinline__ void select_bin_at(const SolveArgs& a, const int4* li
 // Phase 2+3 of one bin, likewise.  A triaged chunk must fit the triage buffer.
 template <int BASE, int CH, bool kPending>
 __device__ __forceinline__ void exclude_bin_at(const SolveArgs& a, const int4* list, int cnt,
-                                               bool late, WarpSched& ws, unsigned* grab,
+                                               bool late, RoundSched& ws, unsigned* grab,
                                                int* next, int4* dst, int32_t* wbuf,
                                                int32_t* wscan) {
     constexpr int kX3 = (kPending || kChunk3 <= kScanMax) ? kChunk3 : kScanMax;
     constexpr int kX2 = (kPending || kChunk2 <= kScanMax) ? kChunk2 : kScanMax;
     constexpr int kX1 = (kPending || kChunk1 <= kScanMax) ? kChunk1 : kScanMax;
     constexpr int kX = (kPending || CH <= kScanMax) ? CH : kScanMax;
-    switch (lanes_per_row<BASE>(cnt, late, ws.nwarps)) {
+    switch (lanes_per_row<BASE>(cnt, late, ws.nwarps())) {
         case 32: exclude_bin<32, kX3, kPending>(a, list, cnt, ws, grab, next, dst, wbuf, wscan); break;
         case 16: exclude_bin<16, kX2, kPending>(a, list, cnt, ws, grab, next, dst, wbuf, wscan); break;
         case 4: exclude_bin<4, kX1, kPending>(a, list, cnt, ws, grab, next, dst, wbuf, wscan); break;
@@ -425,7 +479,7 @@ __device__ __forceinline__ void exclude_bin_at(const SolveArgs& a, const int4* l
 // rows.
 template <bool kPending>
 __device__ __forceinline__ void select_phase(const SolveArgs& a, const int4* src, const int* cnt,
-                                             bool late, WarpSched& ws, unsigned* grab,
+                                             bool late, RoundSched& ws, unsigned* grab,
                                              int* pnext, int4* pend, int32_t* wbuf) {
     const int* off = a.bin_off;
     block_bin<true, kPending>(a, src + off[4], cnt[4], &grab[4], &pnext[4], pend + off[4], late);
@@ -442,7 +496,7 @@ __device__ __forceinline__ void select_phase(const SolveArgs& a, const int4* src
 // Phase 2+3 over the bins of `list` (W_r, or P_r when kPending).
 template <bool kPending>
 __device__ __forceinline__ void exclude_phase(const SolveArgs& a, const int4* list,
-                                              const int* cnt, bool late, WarpSched& ws,
+                                              const int* cnt, bool late, RoundSched& ws,
                                               unsigned* grab, int* next, int4* dst,
                                               int32_t* wbuf, int32_t* wscan) {
     const int* off = a.bin_off;
@@ -455,6 +509,46 @@ __device__ __forceinline__ void exclude_phase(const SolveArgs& a, const int4* li
                                          &next[1], dst + off[1], wbuf, wscan);
     exclude_bin_at<1, kChunk0, kPending>(a, list + off[0], cnt[0], late, ws, &grab[0],
                                          &next[0], dst + off[0], wbuf, wscan);
+}
+
+// Initialisation with the keyed list (a.out0 set): the result starts as the
+// create-time bytes out0 (16-byte copies where out is aligned) and only the
+// keyed vertices get their Eq. 1 words; no other word is read by any test.
+__device__ __forceinline__ void init_keyed(const SolveArgs& a) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const int32_t n = a.n;
+    if (a.out) {
+        long long done = 0;
+        if (((uintptr_t)a.out & 15) == 0) {
+            const long long nq = n / 16;
+            const uint4* src = reinterpret_cast<const uint4*>(a.out0);
+            uint4* dst = reinterpret_cast<uint4*>(a.out);
+            for (long long i = tid; i < nq; i += nthreads) dst[i] = __ldg(src + i);
+            done = nq * 16;
+        }
+        for (long long v = done + tid; v < n; v += nthreads) a.out[v] = a.out0[v];
+    }
+    const int mode = a.priority;
+    const float dbar = average_degree(a.rp[n], n);
+    const uint64_t smix = mix64(a.seed0);
+    for (long long i = tid; i < a.n_keyed; i += nthreads) {
+        const int2 k = __ldg(a.keyed + i);
+        a.word[k.x] = undecided_word(mode, priority_key(mode, dbar, k.y, smix, (uint32_t)k.x));
+    }
+}
+
+// The barrier of a block finishing the rounds alone: the same hooks as
+// grid_barrier (leader bookkeeping, then `after`), run by thread 0 between
+// two block-wide barriers, which also order the block's global writes.
+template <class Leader, class After>
+__device__ __forceinline__ void block_sync(Leader leader, After after) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        leader();
+        after();
+    }
+    __syncthreads();
 }
 
 // Writes out[v] = [v in the MIS] and adds the MIS size to ctl->mis_size.
@@ -497,15 +591,34 @@ __device__ __forceinline__ void output_pass(const SolveArgs& a) {
     if (lane_id() == 0 && in_cnt) atomicAdd(&a.ctl->mis_size, (unsigned long long)in_cnt);
 }
 
+// per-bin sizes of W_r and of P_r, copied once per block after each barrier
+// (kept in shared memory, out of the scans' registers)
+__shared__ int s_cnt[kBins];
+__shared__ int s_pcnt[kBins];
+
+// The barrier of a round: the grid's, or block 0's alone once it finishes
+// the rounds by itself (s_solo).  The round's bookkeeping (`book`: stats,
+// timestamps, resetting the ring counters of the round after next) is done
+// by block 0 once past the barrier, not by the last block to arrive, so
+// block 0 is the only block that ever writes those counters outside a
+// phase -- which is what lets it carry on alone at any round.
+template <bool kPending, class Book, class After>
+__device__ __forceinline__ bool round_barrier(const SolveArgs& a, Book book, After after) {
+    if (kSoloPath<kPending> && s_solo) {
+        block_sync(book, after);
+        return true;
+    }
+    return grid_barrier(a.ctl, gridDim.x, a.spin_cap, NoLeader(), [&]() {
+        if (blockIdx.x == 0) book();
+        after();
+    });
+}
+
 template <bool kPending>
 __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     csr_solve_kernel(const SolveArgs a) {
     __shared__ int32_t s_stage[kWarps][kStageMax];
     __shared__ int32_t s_scan[kPending ? 1 : kWarps][kPending ? 1 : kScanMax];
-    // per-bin sizes of W_r and of P_r, copied once per block after each
-    // barrier (kept in shared memory, out of the scans' registers)
-    __shared__ int s_cnt[kBins];
-    __shared__ int s_pcnt[kBins];
     const unsigned nblocks = gridDim.x;
     Ctl* ctl = a.ctl;
     PhaseTimes* times = a.times;
@@ -513,21 +626,29 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     int32_t* wscan = kPending ? nullptr : &s_scan[kPending ? 0 : threadIdx.x / 32][0];
     grid_barrier_start();
     if (threadIdx.x < kBins) s_cnt[threadIdx.x] = a.bin_off[threadIdx.x + 1] - a.bin_off[threadIdx.x];
+    if (threadIdx.x == 0) {
+        s_selected = 0;
+        s_solo = 0;
+        s_nwarps = (int)(nblocks * (blockDim.x / 32));
+    }
     if (times && blockIdx.x == 0 && threadIdx.x == 0) times->t[0] = global_ns();
 
-    // ---- init: Eq. 1 priorities
-    init_words(a, (a.n + 15) / 16 * 16, true);  // words are padded to 16
-    if (!grid_barrier(ctl, nblocks, a.spin_cap, [times]() {
-            if (times) times->t[1] = global_ns();
-        }))
+    // ---- init: Eq. 1 priorities (and, direct, the create-time result bytes)
+    if (a.out0) init_keyed(a);
+    else init_words(a, (a.n + 15) / 16 * 16, true, a.direct ? a.out : nullptr);  // padded to 16
+    if (!round_barrier<kPending>(
+            a,
+            [times]() {
+                if (times) times->t[1] = global_ns();
+            },
+            []() {}))
         return;
 
     // vertices decided without a test (isolated ones and sure candidates at
     // init, sure exclusions in round 0's Phase 2) belong to round 0's alive set
     const int decided0 = a.n_isolated + a.n_sure_in + a.n_sure_out;
-    WarpSched ws;
+    RoundSched ws;
     ws.gw = (int)(blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32);
-    ws.nwarps = (int)(nblocks * (blockDim.x / 32));
     ws.base = 0;
     for (int r = 0;; ++r) {
         int total = 0;
@@ -536,6 +657,24 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
         if (r >= a.max_rounds) {
             if (threadIdx.x == 0) atomicCAS(&ctl->err, 0, kErrInternal);
             return;
+        }
+        // A small worklist is finished by block 0 alone, with block-level
+        // barriers: every block reads the same total, so all see the switch;
+        // the others are done (the result is written as vertices are
+        // decided).  Block 0 keeps the ring counters, which it alone resets,
+        // and its warps keep their indices.  Worklists only shrink, so once
+        // switched every later round switches again (idempotent).
+        if constexpr (kSoloPath<kPending>) {
+            if (a.direct && r > 0 && total <= kSoloRows) {
+                if (blockIdx.x != 0) break;
+                __syncthreads();  // every thread has read the shared state of the last round
+                if (threadIdx.x == 0) {
+                    s_solo = 1;
+                    s_nwarps = (int)(blockDim.x / 32);
+                }
+                __syncthreads();
+                ws.base = 0;  // first() needs base < nwarps
+            }
         }
         const int4* src = (r == 0) ? a.order0 : ((r & 1) ? a.wl1 : a.wl0);
         int4* dst = ((r + 1) & 1) ? a.wl1 : a.wl0;
@@ -546,8 +685,8 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
         // ---- Phase 1: selection test
         select_phase<kPending>(a, src, s_cnt, r > 0, ws, ctl->grab[(2 * r) & 3], pnext, a.wlp,
                                wbuf);
-        if (!grid_barrier(
-                ctl, nblocks, a.spin_cap,
+        if (!round_barrier<kPending>(
+                a,
                 [ctl, times, rr]() {
                     if (times && rr < kStatRounds) times->t[2 + rr] = global_ns();
                     for (int j = 0; j < kBins; ++j) ctl->grab[(2 * rr + 2) & 3][j] = 0;
@@ -559,8 +698,9 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
             return;
 
         // ---- Phase 2+3: exclusion test, state update, compaction
-        if (r == 0) {
-            // the sure exclusions: neighbours of sure candidates
+        if (r == 0 && !a.out0) {
+            // the sure exclusions: neighbours of sure candidates (with the
+            // keyed list no test reads their words, and out0 has them out)
             const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
             const long long nthreads = (long long)nblocks * blockDim.x;
             for (long long i = tid; i < a.n_sure_out; i += nthreads) a.word[a.sure_out[i]] = kWordOut;
@@ -572,8 +712,8 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
             exclude_phase<false>(a, pending_view(a, src, r > 0), s_cnt, r > 0, ws,
                                  ctl->grab[(2 * r + 1) & 3], next, dst, wbuf, wscan);
         const int cur = total + (r == 0 ? decided0 : 0);
-        if (!grid_barrier(
-                ctl, nblocks, a.spin_cap,
+        if (!round_barrier<kPending>(
+                a,
                 [ctl, times, rr, cur]() {
                     if (times && rr < kStatRounds) times->t[2 + kStatRounds + rr] = global_ns();
                     if (rr < kStatRounds) ctl->alive[rr] = cur;
@@ -592,7 +732,18 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     }
 
     // ---- output
-    if (a.out) output_pass(a);
+    if (!a.direct) {
+        if (a.out) output_pass(a);
+        return;
+    }
+    // the result is complete; the MIS size is the create-time part plus the
+    // candidates every block selected
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long c = s_selected;
+        if (blockIdx.x == 0) c += (unsigned long long)a.n_isolated + (unsigned long long)a.n_sure_in;
+        if (c) atomicAdd(&ctl->mis_size, c);
+    }
 }
 
 cudaError_t launch_csr_solve(const SolveArgs& a, int grid, cudaStream_t s) {
@@ -956,6 +1107,99 @@ cudaError_t build_s0_graph(const int32_t* rp, const int32_t* col_sel, const int3
     *s0_col = colo;
     *s0_pre = pre;
     *s0_arcs = total;
+    return cudaSuccess;
+}
+
+// ---- the keyed vertices and the create-time result bytes
+//
+// With the tested subgraph, a solve only ever reads the words of two sets of
+// vertices: those of S0 (every scan) and the vertices in an S0 row's
+// selection prefix (round 0's selection test; they are S0 or class-2
+// vertices, since class 1 has no S0 neighbour).  Every other vertex is
+// decided before any test and no scan reads its word: isolated vertices and
+// class 1 are in the MIS, class 2 is out.  So the solve computes keys for the
+// keyed list alone (sorted by vertex, with each degree), copies the result
+// bytes of the vertices decided at create time from out0 (1: isolated or
+// class 1), and marks its own candidates in the result as it selects them.
+
+// One warp per vertex: flag an S0 vertex and every vertex of its selection
+// prefix (benign duplicate writes of 1).
+__global__ void keyed_mark_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col_sel,
+                                  const int32_t* __restrict__ split,
+                                  const uint8_t* __restrict__ r0class, int32_t n,
+                                  int32_t* __restrict__ need) {
+    const long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const unsigned lane = lane_id();
+    if (v >= n || !in_s0(r0class, rp, v)) return;
+    if (lane == 0) need[v] = 1;
+    const int b = rp[v], es = b + split[v];
+    for (int p = b + (int)lane; p < es; p += 32) need[col_sel[p]] = 1;
+}
+
+// keyed[pos[v]] = {v, degree of v} for every flagged v; out0[v] = 1 for the
+// isolated vertices and class 1.
+__global__ void keyed_pack_kernel(const int32_t* __restrict__ rp,
+                                  const uint8_t* __restrict__ r0class, int32_t n,
+                                  const int32_t* __restrict__ need,
+                                  const int32_t* __restrict__ pos, int2* __restrict__ keyed,
+                                  uint8_t* __restrict__ out0) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int deg = rp[v + 1] - rp[v];
+    if (need[v]) keyed[pos[v]] = make_int2((int)v, deg);
+    out0[v] = (deg == 0 || r0class[v] == 1) ? 1 : 0;
+}
+
+cudaError_t build_keyed(const int32_t* rp, const int32_t* col_sel, const int32_t* split,
+                        const uint8_t* r0class, int32_t n, int2** keyed, int32_t* n_keyed,
+                        uint8_t** out0, cudaStream_t s) {
+    *keyed = nullptr;
+    *out0 = nullptr;
+    *n_keyed = 0;
+    if (n == 0) return cudaSuccess;
+    int32_t *need = nullptr, *pos = nullptr;
+    int2* kd = nullptr;
+    uint8_t* o0 = nullptr;
+    void* temp = nullptr;
+    size_t temp_bytes = 0;
+    cudaError_t e = dev_alloc((void**)&need, sizeof(int32_t) * ((size_t)n + 1));
+    if (e == cudaSuccess) e = dev_alloc((void**)&pos, sizeof(int32_t) * ((size_t)n + 1));
+    // result bytes padded to 16 for the solve's 16-byte copies
+    if (e == cudaSuccess) e = dev_alloc((void**)&o0, ((size_t)n + 15) / 16 * 16);
+    if (e == cudaSuccess) e = cudaMemsetAsync(need, 0, sizeof(int32_t) * ((size_t)n + 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(o0, 0, ((size_t)n + 15) / 16 * 16, s);
+    if (e == cudaSuccess) {
+        keyed_mark_kernel<<<(unsigned)((32LL * n + 255) / 256), 256, 0, s>>>(rp, col_sel, split,
+                                                                          r0class, n, need);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cub::DeviceScan::ExclusiveSum(nullptr, temp_bytes, need, pos, n + 1, s);
+    if (e == cudaSuccess) e = dev_alloc(&temp, temp_bytes ? temp_bytes : 1);
+    if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(temp, temp_bytes, need, pos, n + 1, s);
+    int32_t total = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&total, pos + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&kd, sizeof(int2) * ((size_t)total + 1));
+    if (e == cudaSuccess) {
+        keyed_pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rp, r0class, n, need, pos,
+                                                                      kd, o0);
+        e = cudaGetLastError();
+    }
+    const cudaError_t se = cudaStreamSynchronize(s);  // also on error: nothing may still run
+    if (e == cudaSuccess) e = se;
+    dev_free(need);
+    dev_free(pos);
+    dev_free(temp);
+    if (e != cudaSuccess) {
+        dev_free(kd);
+        dev_free(o0);
+        return e;
+    }
+    *keyed = kd;
+    *n_keyed = total;
+    *out0 = o0;
     return cudaSuccess;
 }
 

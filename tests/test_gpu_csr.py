@@ -174,6 +174,58 @@ def test_round0_sure_sets(name, order_rows):
         native.mis_destroy(h)
 
 
+def _keyed_count(g):
+    """Vertices whose words a solve with the tested subgraph reads: the
+    tested vertices and every vertex in one of their selection prefixes
+    (neighbours of degree <= deg + 1)."""
+    n, rp, col = g
+    rp = rp.astype(np.int64)
+    deg = np.diff(rp)
+    src = np.repeat(np.arange(n), deg)
+    outranked = (deg[col] >= deg[src] + 2)
+    nz = deg > 0
+    all_lower = np.zeros(n, dtype=bool)
+    all_lower[nz] = np.logical_and.reduceat(outranked, rp[:-1][nz])
+    has = np.zeros(n, dtype=bool)
+    has[nz] = np.logical_or.reduceat(all_lower[col], rp[:-1][nz])
+    tested = nz & ~has & ~all_lower
+    need = tested.copy()
+    need[col[tested[src] & ~outranked]] = True
+    return int(need.sum())
+
+
+@pytest.mark.parametrize("offset", [0, 1, 3, 16])
+def test_keyed_result_any_alignment(offset):
+    """With the keyed list a solve starts its result from create-time bytes
+    and writes candidates as it selects them: every byte of the result is
+    written at any alignment of the buffer, none around it, and successive
+    seeds on one handle (stale words of vertices no test reads) agree with
+    the oracle."""
+    import torch
+    for name in ("rmat14", "star_hub", "k_ab"):
+        g = graph(name)
+        n = g[0]
+        h = create(g, order_rows=2)
+        try:
+            native.mis_set_path(h, native.MIS_PATH_CSR, 0)
+            buf = torch.empty(n + 64, dtype=torch.uint8, device="cuda")
+            stream = torch.cuda.current_stream().cuda_stream
+            for pending in (0, 1):
+                native.mis_set_csr_pending(h, pending)
+                for seed in (5, 6, 2**63 + 1):
+                    buf.fill_(7)
+                    native.mis_solve_ex(h, np.array([seed], dtype=np.uint64),
+                                        buf.data_ptr() + offset, stream)
+                    st = native.mis_get_stats(h)
+                    host = buf.cpu().numpy()
+                    assert_same(g, seed, host[offset:offset + n], st)
+                    assert (host[:offset] == 7).all() and (host[offset + n:] == 7).all()
+                    if st.tested_arcs >= 0:
+                        assert st.keyed == _keyed_count(g)
+        finally:
+            native.mis_destroy(h)
+
+
 @pytest.mark.parametrize("bounds", [(2, 5, 9, 20), (-1, 3, 3, 3), (0, 0, 100000, 100000),
                                     (1, 2, 3, 4), (-1, -1, -1, 2)])
 def test_csr_custom_bins(bounds):
