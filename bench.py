@@ -355,8 +355,26 @@ def run_single(args):
                        "mis_destroy"}
 
     peak, peak_kind = _peak_hbm()
-    alg_bytes = 4 * arcs + 4 * (n + 1) + 4 * n + n
+    # B0: one read of the CSR plus the key words and result bytes -- the
+    # lower bound of a solve that starts from the CSR alone
+    b0 = 4 * arcs + 4 * (n + 1) + 4 * n + n
     launch_s = (total_ms / 1e3) / args.steps
+    # With the create-time tested subgraph and keyed list, a solve starts from
+    # those structures instead: its algorithmic bytes are one pass over each
+    # of them (neighbour word gathers stay in L2 and are not counted)
+    if st.path == 1 and st.keyed >= 0:
+        alg_bytes = (12 * st.keyed + 2 * n + 32 * st.tested_rows
+                     + 4 * st.tested_prefix_arcs + 4 * st.tested_arcs)
+        alg_def = ("12*keyed (keyed list read, dense key words written) + 2*n (create-time result "
+                   "bytes read, result written) + 32*tested_rows (round-0 row records, full and "
+                   "tested-subgraph) + 4*tested_prefix_arcs (round-0 selection prefixes) + "
+                   "4*tested_arcs (the tested subgraph); neighbour words are L2-resident")
+        alg_counts = {"keyed": st.keyed, "tested_rows": st.tested_rows,
+                      "tested_prefix_arcs": st.tested_prefix_arcs, "tested_arcs": st.tested_arcs}
+    else:
+        alg_bytes = b0
+        alg_def = "4*arcs + 4*(n+1) (one read of the CSR) + 4*n (key words written) + n (result)"
+        alg_counts = None
     traffic = args.traffic
     if traffic is None and args.workload == "rmat22" and st.path == 1:
         traffic = profiled_traffic(["kernels_csr.cu", "common.cuh", "init.cuh", "worklist.cuh"],
@@ -382,9 +400,12 @@ def run_single(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} burst copy bandwidth",
-                     "alg_bytes_per_launch": alg_bytes,
-                     "alg_bytes_def": "4*arcs + 4*(n+1) (one read of the CSR) + 4*n (key words "
-                                      "written) + n (result bytes)",
+                     "alg_bytes_per_launch": alg_bytes, "alg_bytes_def": alg_def,
+                     "alg_counts": alg_counts,
+                     "b0_bytes": b0, "b0_per_s_frac": b0 / launch_s / 1e9 / peak,
+                     "b0_def": "4*arcs + 4*(n+1) + 4*n + n: one read of the CSR, key words and "
+                               "result; b0_per_s_frac is that volume per launch time over the "
+                               "peak (an edges/s equivalent, not a bandwidth)",
                      "kernel": f"{path} persistent round kernel (one launch per solve)"},
         "clocks": clocks,
         "e2e": e2e,

@@ -151,6 +151,11 @@ typedef struct mis_stats {
                                 when the graph has a tested subgraph (its
                                 vertices and those of their selection prefixes;
                                 no other word is read); -1 = every vertex */
+    int64_t tested_rows;     /* CSR path, with a tested subgraph: its vertices (the
+                                rows round 0 tests); -1 without one */
+    int64_t tested_prefix_arcs; /* ... and the arcs of their selection prefixes
+                                (neighbours of degree <= deg + 1), which round
+                                0's selection test reads; -1 without one */
 } mis_stats;
 
 /* Fill *opt with the defaults listed above. */

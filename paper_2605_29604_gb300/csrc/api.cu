@@ -269,7 +269,7 @@ int finish_create(mis_graph* g) {
         }
         if (e == cudaSuccess && d.s0_col && d.count == 0) {
             e = build_keyed(d.rp, d.col_sel, d.split, d.r0class, d.n, &d.keyed, &d.n_keyed,
-                            &d.out0, g->own_stream);
+                            &d.out0, &d.n_tested, &d.tested_prefix_arcs, g->own_stream);
             d.footprint += 8 * ((int64_t)d.n_keyed + 1) + ((int64_t)d.n + 15) / 16 * 16;
         }
         if (e != cudaSuccess) return set_cuda_error(e, "degree ordering");
@@ -1243,6 +1243,8 @@ int mis_get_stats(mis_graph* g, mis_stats* st) {
     st->sure_out = csr ? g->d.n_sure_out : 0;
     st->tested_arcs = !csr ? 0 : g->d.s0_col ? g->d.s0_arcs : -1;
     st->keyed = !csr ? 0 : g->d.out0 ? g->d.n_keyed : -1;
+    st->tested_rows = !csr ? 0 : g->d.out0 ? g->d.n_tested : -1;
+    st->tested_prefix_arcs = !csr ? 0 : g->d.out0 ? g->d.tested_prefix_arcs : -1;
     st->ntiles = g->d.tiles.ntiles;
     st->alive_sum = (int64_t)c.alive_sum;
     st->mis_size = (int64_t)c.mis_size;

@@ -82,6 +82,8 @@ struct GraphData {
     int2* keyed = nullptr;        // vertices whose words a solve reads (with s0_col)
     uint8_t* out0 = nullptr;      // result bytes decided at create time
     int32_t n_keyed = 0;
+    int32_t n_tested = 0;             // vertices of the tested subgraph
+    int64_t tested_prefix_arcs = 0;   // arcs of their selection prefixes
     int32_t n_sure_in = 0;
     int32_t n_sure_out = 0;
     int32_t bin_off[6] = {0, 0, 0, 0, 0, 0};

@@ -138,10 +138,12 @@ cudaError_t build_s0_graph(const int32_t* rp, const int32_t* col_sel, const int3
 // of S0 rows' selection prefixes; {vertex, degree}, sorted by vertex) and the
 // result bytes known at create time (out0[v] = 1 for isolated vertices and
 // sure candidates; padded to a multiple of 16).  Device arrays, owned by the
-// caller.
+// caller.  Also counts the tested vertices and the arcs of their selection
+// prefixes.
 cudaError_t build_keyed(const int32_t* rp, const int32_t* col_sel, const int32_t* split,
                         const uint8_t* r0class, int32_t n, int2** keyed, int32_t* n_keyed,
-                        uint8_t** out0, cudaStream_t s);
+                        uint8_t** out0, int32_t* n_tested, int64_t* prefix_arcs,
+                        cudaStream_t s);
 
 // Create-time round-0 classes from the degree-ordered rows (col_sel, split):
 // 1 = sure candidate (empty selection prefix: every neighbour has degree >=

@@ -1123,15 +1123,20 @@ cudaError_t build_s0_graph(const int32_t* rp, const int32_t* col_sel, const int3
 // class 1), and marks its own candidates in the result as it selects them.
 
 // One warp per vertex: flag an S0 vertex and every vertex of its selection
-// prefix (benign duplicate writes of 1).
+// prefix (benign duplicate writes of 1); count S0 rows and prefix arcs.
 __global__ void keyed_mark_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col_sel,
                                   const int32_t* __restrict__ split,
                                   const uint8_t* __restrict__ r0class, int32_t n,
-                                  int32_t* __restrict__ need) {
+                                  int32_t* __restrict__ need,
+                                  unsigned long long* __restrict__ sums) {
     const long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const unsigned lane = lane_id();
     if (v >= n || !in_s0(r0class, rp, v)) return;
-    if (lane == 0) need[v] = 1;
+    if (lane == 0) {
+        need[v] = 1;
+        atomicAdd(&sums[0], 1ull);
+        atomicAdd(&sums[1], (unsigned long long)split[v]);
+    }
     const int b = rp[v], es = b + split[v];
     for (int p = b + (int)lane; p < es; p += 32) need[col_sel[p]] = 1;
 }
@@ -1152,12 +1157,17 @@ __global__ void keyed_pack_kernel(const int32_t* __restrict__ rp,
 
 cudaError_t build_keyed(const int32_t* rp, const int32_t* col_sel, const int32_t* split,
                         const uint8_t* r0class, int32_t n, int2** keyed, int32_t* n_keyed,
-                        uint8_t** out0, cudaStream_t s) {
+                        uint8_t** out0, int32_t* n_tested, int64_t* prefix_arcs,
+                        cudaStream_t s) {
     *keyed = nullptr;
     *out0 = nullptr;
     *n_keyed = 0;
+    *n_tested = 0;
+    *prefix_arcs = 0;
     if (n == 0) return cudaSuccess;
     int32_t *need = nullptr, *pos = nullptr;
+    unsigned long long* sums = nullptr;
+    unsigned long long hsums[2] = {0, 0};
     int2* kd = nullptr;
     uint8_t* o0 = nullptr;
     void* temp = nullptr;
@@ -1166,11 +1176,13 @@ cudaError_t build_keyed(const int32_t* rp, const int32_t* col_sel, const int32_t
     if (e == cudaSuccess) e = dev_alloc((void**)&pos, sizeof(int32_t) * ((size_t)n + 1));
     // result bytes padded to 16 for the solve's 16-byte copies
     if (e == cudaSuccess) e = dev_alloc((void**)&o0, ((size_t)n + 15) / 16 * 16);
+    if (e == cudaSuccess) e = dev_alloc((void**)&sums, sizeof(hsums));
     if (e == cudaSuccess) e = cudaMemsetAsync(need, 0, sizeof(int32_t) * ((size_t)n + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(o0, 0, ((size_t)n + 15) / 16 * 16, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, sizeof(hsums), s);
     if (e == cudaSuccess) {
-        keyed_mark_kernel<<<(unsigned)((32LL * n + 255) / 256), 256, 0, s>>>(rp, col_sel, split,
-                                                                          r0class, n, need);
+        keyed_mark_kernel<<<(unsigned)((32LL * n + 255) / 256), 256, 0, s>>>(
+            rp, col_sel, split, r0class, n, need, sums);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
@@ -1180,6 +1192,8 @@ cudaError_t build_keyed(const int32_t* rp, const int32_t* col_sel, const int32_t
     int32_t total = 0;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&total, pos + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hsums, sums, sizeof(hsums), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = dev_alloc((void**)&kd, sizeof(int2) * ((size_t)total + 1));
     if (e == cudaSuccess) {
@@ -1192,6 +1206,7 @@ cudaError_t build_keyed(const int32_t* rp, const int32_t* col_sel, const int32_t
     dev_free(need);
     dev_free(pos);
     dev_free(temp);
+    dev_free(sums);
     if (e != cudaSuccess) {
         dev_free(kd);
         dev_free(o0);
@@ -1200,6 +1215,8 @@ cudaError_t build_keyed(const int32_t* rp, const int32_t* col_sel, const int32_t
     *keyed = kd;
     *n_keyed = total;
     *out0 = o0;
+    *n_tested = (int32_t)hsums[0];
+    *prefix_arcs = (int64_t)hsums[1];
     return cudaSuccess;
 }
 

@@ -66,7 +66,8 @@ class mis_stats(ctypes.Structure):
                 ("alive_per_round", ctypes.c_int64 * 64), ("init_ns", ctypes.c_int64),
                 ("select_ns", ctypes.c_int64 * 64), ("exclude_ns", ctypes.c_int64 * 64),
                 ("sure_in", ctypes.c_int64), ("sure_out", ctypes.c_int64),
-                ("tested_arcs", ctypes.c_int64), ("keyed", ctypes.c_int64)]
+                ("tested_arcs", ctypes.c_int64), ("keyed", ctypes.c_int64),
+                ("tested_rows", ctypes.c_int64), ("tested_prefix_arcs", ctypes.c_int64)]
 
 
 class mis_tuning(ctypes.Structure):

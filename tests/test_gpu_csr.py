@@ -190,8 +190,9 @@ def _keyed_count(g):
     has[nz] = np.logical_or.reduceat(all_lower[col], rp[:-1][nz])
     tested = nz & ~has & ~all_lower
     need = tested.copy()
-    need[col[tested[src] & ~outranked]] = True
-    return int(need.sum())
+    in_prefix = tested[src] & ~outranked
+    need[col[in_prefix]] = True
+    return int(need.sum()), int(tested.sum()), int(in_prefix.sum())
 
 
 @pytest.mark.parametrize("offset", [0, 1, 3, 16])
@@ -221,7 +222,7 @@ def test_keyed_result_any_alignment(offset):
                     assert_same(g, seed, host[offset:offset + n], st)
                     assert (host[:offset] == 7).all() and (host[offset + n:] == 7).all()
                     if st.tested_arcs >= 0:
-                        assert st.keyed == _keyed_count(g)
+                        assert (st.keyed, st.tested_rows, st.tested_prefix_arcs) == _keyed_count(g)
         finally:
             native.mis_destroy(h)
 
