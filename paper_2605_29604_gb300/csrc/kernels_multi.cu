@@ -11,6 +11,13 @@
 // step; a solve that has finished has no undecided vertex and drops out of
 // every test.  The result of each solve is the one a single solve with its
 // seed gives (the rounds of each solve are exactly its own).
+//
+// With the tested subgraph and the keyed vertices of a single graph (see
+// kernels_csr.cu), the launch works as the single-solve kernel does: the
+// words of the keyed vertices only (one 32-byte sector each), round 0's
+// exclusion test and every later round on the tested subgraph, and results
+// written as vertices are decided (from the create-time bytes out0), with no
+// output pass.
 #include <algorithm>
 
 #include "common.cuh"
@@ -102,7 +109,11 @@ struct MultiCtx {
     const SolveArgs& a;
     uint32_t* word8;
     int32_t* wbuf;
+    int k;  // solves in the launch
 };
+
+// Candidates marked in the results by this block (with the keyed vertices).
+__shared__ unsigned s_msel;
 
 // Phase 1 over one bin at TPR lanes per row: for every row, the selection
 // test in each solve that has the row undecided; candidates are marked in.
@@ -110,7 +121,7 @@ struct MultiCtx {
 template <int TPR, int CH>
 __device__ __forceinline__ void select_bin8(const MultiCtx& x, const int4* __restrict__ list,
                                             int cnt, WarpSched& ws, unsigned* grab,
-                                            unsigned long long* alive) {
+                                            unsigned long long* alive, bool late) {
     constexpr int G = 32 / TPR;
     if (cnt <= 0) return;
     const unsigned lane = lane_id();
@@ -134,9 +145,11 @@ __device__ __forceinline__ void select_bin8(const MultiCtx& x, const int4* __res
 #pragma unroll
                 for (int s = 0; s < kMaxMulti; ++s) wv[s] = 0u;
             }
+            // round 0 reads the full selection prefixes, later rounds the
+            // tested subgraph's rows (col_s0 is col_sel without one)
             const unsigned blocked =
-                group_scan8<TPR, true>(x.a.col_sel, x.word8, rec.y, valid ? rec.z : 0, rec.x, wv,
-                                       act, glane);
+                group_scan8<TPR, true>(late ? x.a.col_s0 : x.a.col_sel, x.word8, rec.y,
+                                       valid ? rec.z : 0, rec.x, wv, act, glane);
             const unsigned cand = act & ~blocked;
             if (glane == 0 && valid) {
                 count += __popc(act);
@@ -145,6 +158,12 @@ __device__ __forceinline__ void select_bin8(const MultiCtx& x, const int4* __res
                     for (int s = 0; s < kMaxMulti; ++s)
                         if ((cand >> s) & 1u) wv[s] |= kWordInSet;
                     store8(x.word8, rec.x, wv);
+                    if (x.a.out0) {  // results written as decided
+                        if (x.a.out)
+                            for (int s = 0; s < x.k; ++s)
+                                if ((cand >> s) & 1u) x.a.out[(long long)s * x.a.n + rec.x] = 1;
+                        atomicAdd(&s_msel, (unsigned)__popc(cand));
+                    }
                 }
             }
         }
@@ -183,7 +202,7 @@ __device__ __forceinline__ void exclude_bin8(const MultiCtx& x, const int4* __re
 #pragma unroll
                 for (int s = 0; s < kMaxMulti; ++s) wv[s] = 0u;
             }
-            const unsigned excl = group_scan8<TPR, false>(x.a.col_sel, x.word8, rec.y,
+            const unsigned excl = group_scan8<TPR, false>(x.a.col_s0, x.word8, rec.y,
                                                           valid ? rec.w : 0, rec.x, wv, und, glane);
             const bool lead = glane == 0 && valid;
             if (lead && excl) {
@@ -216,10 +235,10 @@ __device__ __forceinline__ void select_at8(const MultiCtx& x, const int4* list, 
                                            WarpSched& ws, unsigned* grab,
                                            unsigned long long* alive) {
     switch (multi_lanes<BASE>(cnt, late, ws.nwarps)) {
-        case 32: select_bin8<32, kMChunk32>(x, list, cnt, ws, grab, alive); break;
-        case 16: select_bin8<16, kMChunk16>(x, list, cnt, ws, grab, alive); break;
-        case 4: select_bin8<4, kMChunk4>(x, list, cnt, ws, grab, alive); break;
-        default: select_bin8<BASE, CH>(x, list, cnt, ws, grab, alive);
+        case 32: select_bin8<32, kMChunk32>(x, list, cnt, ws, grab, alive, late); break;
+        case 16: select_bin8<16, kMChunk16>(x, list, cnt, ws, grab, alive, late); break;
+        case 4: select_bin8<4, kMChunk4>(x, list, cnt, ws, grab, alive, late); break;
+        default: select_bin8<BASE, CH>(x, list, cnt, ws, grab, alive, late);
     }
 }
 
@@ -261,6 +280,40 @@ __device__ __forceinline__ void init_words8(const SolveArgs& a, uint32_t* word8,
     }
 }
 
+// With the keyed vertices: their eight words only (the only words any test
+// reads), and each solve's result started from the create-time bytes out0.
+__device__ __forceinline__ void init_keyed8(const SolveArgs& a, uint32_t* word8, int k,
+                                            const uint64_t (&smix)[kMaxMulti]) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const int32_t n = a.n;
+    if (a.out) {
+        for (int s = 0; s < k; ++s) {
+            uint8_t* out = a.out + (long long)s * n;
+            long long done = 0;
+            if (((uintptr_t)out & 15) == 0) {
+                const long long nq = n / 16;
+                const uint4* src = reinterpret_cast<const uint4*>(a.out0);
+                for (long long i = tid; i < nq; i += nthreads)
+                    reinterpret_cast<uint4*>(out)[i] = __ldg(src + i);
+                done = nq * 16;
+            }
+            for (long long v = done + tid; v < n; v += nthreads) out[v] = a.out0[v];
+        }
+    }
+    const float dbar = average_degree(a.rp[n], n);
+    for (long long i = tid; i < a.n_keyed; i += nthreads) {
+        const int2 kv = __ldg(a.keyed + i);
+        uint32_t w[kMaxMulti];
+#pragma unroll
+        for (int s = 0; s < kMaxMulti; ++s)
+            w[s] = s < k ? undecided_word(a.priority, priority_key(a.priority, dbar, kv.y, smix[s],
+                                                                   (uint32_t)kv.x))
+                         : kWordOut;
+        store8(word8, kv.x, w);
+    }
+}
+
 __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
     multi_solve_kernel(const SolveArgs a, uint32_t* word8, int k, const MultiSeeds seeds) {
     __shared__ int32_t s_stage[kMultiWarps][kStageMax];
@@ -268,9 +321,10 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
     const unsigned nblocks = gridDim.x;
     Ctl* ctl = a.ctl;
     PhaseTimes* times = a.times;
-    const MultiCtx x{a, word8, s_stage[threadIdx.x / 32]};
+    const MultiCtx x{a, word8, s_stage[threadIdx.x / 32], k};
     grid_barrier_start();
     if (threadIdx.x < kBins) s_cnt[threadIdx.x] = a.bin_off[threadIdx.x + 1] - a.bin_off[threadIdx.x];
+    if (threadIdx.x == 0) s_msel = 0;
     if (times && blockIdx.x == 0 && threadIdx.x == 0) times->t[0] = global_ns();
 
     // ---- init: Eq. 1 priorities of every solve
@@ -278,7 +332,8 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
         uint64_t smix[kMaxMulti];
 #pragma unroll
         for (int s = 0; s < kMaxMulti; ++s) smix[s] = mix64(seeds.seed[s]);
-        init_words8(a, word8, k, smix);
+        if (a.out0) init_keyed8(a, word8, k, smix);
+        else init_words8(a, word8, k, smix);
     }
     if (!grid_barrier(ctl, nblocks, a.spin_cap, [times]() {
             if (times) times->t[1] = global_ns();
@@ -320,7 +375,7 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
             return;
 
         // ---- Phase 2+3: exclusion test, state update, compaction
-        if (r == 0) {
+        if (r == 0 && !a.out0) {  // (no test reads these words with the keyed vertices)
             const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
             const long long nthreads = (long long)nblocks * blockDim.x;
             const uint4 out4 = make_uint4(kWordOut, kWordOut, kWordOut, kWordOut);
@@ -331,6 +386,8 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
             }
         }
         grab = ctl->grab[(2 * r + 1) & 3];
+        // round 0's rows in the tested subgraph, where the graph has one
+        if (r == 0 && a.order0_s0) src = a.order0_s0;
         exclude_at8<32, kMChunk32>(x, src + off[4], s_cnt[4], late, ws, &grab[4], &next[4], dst + off[4]);
         exclude_at8<32, kMChunk32>(x, src + off[3], s_cnt[3], late, ws, &grab[3], &next[3], dst + off[3]);
         exclude_at8<16, kMChunk16>(x, src + off[2], s_cnt[2], late, ws, &grab[2], &next[2], dst + off[2]);
@@ -359,6 +416,18 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
             return;
     }
 
+    // ---- with the keyed vertices the results are complete: the MIS sizes are
+    // the create-time part of each solve plus the candidates marked
+    if (a.out0) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long c = s_msel;
+            if (blockIdx.x == 0)
+                c += (unsigned long long)k * ((unsigned long long)a.n_isolated + a.n_sure_in);
+            if (c) atomicAdd(&ctl->mis_size, c);
+        }
+        return;
+    }
     // ---- output: out[s * n + v] = [v in the MIS of solve s]
     if (a.out) {
         const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
