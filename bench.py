@@ -289,6 +289,10 @@ def run_single(args):
         native.mis_set_path(h, native.MIS_PATH_CSR, args.tpr)
         if args.csr_pending is not None:
             native.mis_set_csr_pending(h, args.csr_pending)
+        if args.bins:
+            native.mis_set_csr_bins(h, [int(x) for x in args.bins.split(",")])
+        if args.grid:
+            native.mis_set_grid(h, args.grid)
     elif args.path:
         native.mis_set_path(h, {"tile": 2, "tile_tc": 3, "push": 4}[args.path],
                             args.tile if args.path != "push" else 0)
@@ -636,6 +640,10 @@ def main():
     ap.add_argument("--tpr", type=int, default=None, help="force the CSR path with these lanes")
     ap.add_argument("--csr-pending", type=int, default=None, choices=[0, 1],
                     help="with --tpr: Phase 2 over Phase 1's pending list (1) or a triage (0)")
+    ap.add_argument("--bins", default=None,
+                    help="with --tpr 0: the CSR kernel's four degree-bin bounds, comma separated")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="with --tpr: blocks of the persistent CSR launch (0 = all co-resident)")
     ap.add_argument("--path", default=None, choices=["tile", "tile_tc", "push"])
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=3)

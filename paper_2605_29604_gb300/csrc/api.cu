@@ -730,6 +730,13 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
     bins(16, 256, 4096, 65536, 0);
     bins(12, 48, 256, 4096, 0);
     bins(INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, 0);  // one lane per row
+    // smaller grids: fewer arrivals per grid barrier, for barrier-bound solves
+    // (two and one blocks per SM at the kernel's three)
+    if (maxg >= 3) {
+        bins(8, 4096, 4096, 65536, maxg * 2 / 3);
+        bins(8, 4096, 4096, 65536, maxg / 3);
+        bins(INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, maxg * 2 / 3);
+    }
     bins(-1, 65536, 65536, 65536, 0);                                     // four lanes per row
     if (g->d.n <= 65536) bins(8, 4096, 4096, 65536, std::max(1, (g->d.n + 1023) / 1024));
     {
