@@ -324,6 +324,44 @@ int mis_tiles_ex(mis_graph *g, int32_t *trp, int32_t *tcol, uint64_t *tbits, voi
 /* Bytes of device memory held by the handle (graph + workspace). */
 int64_t mis_footprint(const mis_graph *g);
 
+/* ---------------------------------------------------------------- dynamic graphs
+ *
+ * The dynamic setting (edge insertions and deletions) that the paper's
+ * conclusion names as future work.  Single graphs only (not a batch).
+ *
+ * mis_update_edges applies n_ins insertions and n_del deletions of undirected
+ * edges to the resident graph.  ins and del are HOST arrays of vertex pairs
+ * (u0, v0, u1, v1, ...), each with 0 <= u, v < n and u != v, else MIS_EINVAL.
+ * Inserting an edge that exists, or deleting one that does not, changes
+ * nothing.  The graph is rebuilt on the device (sorted, duplicate-free,
+ * symmetric) with every create-time structure, as mis_create_ex builds them
+ * from the new CSR; the handle keeps its options and its resolved path.
+ * Synchronises `stream`.  MIS_EBUSY while served requests of the handle are
+ * in flight; on any error the handle keeps its old graph.
+ */
+int mis_update_edges(mis_graph *g, int64_t n_ins, const int32_t *ins, int64_t n_del,
+                     const int32_t *del, void *stream);
+
+/*
+ * mis_repair turns out_status (DEVICE, n bytes), the result of a solve with
+ * `seed` of the graph as it was before some edge changes, into the result of
+ * the same solve of the graph as it is now -- bit-identical to mis_solve_ex
+ * with that seed -- by re-deciding only the vertices whose state can change.
+ * changed: HOST pairs (u, v) of every edge inserted or deleted since
+ * out_status was computed (a superset is fine).  Algorithm 2 with fixed keys
+ * yields the greedy MIS in priority order, where a vertex's state depends
+ * only on its higher-priority neighbours; so only the downstream closure of
+ * the lower endpoints of the changed edges can change, and the rounds run on
+ * that closure alone, the other vertices fixed.  Requires MIS_PRIORITY_HASH
+ * (H1, Sec. 3.3), whose keys do not depend on the graph: Eq. 1's keys divide
+ * by the average degree, so an edge change moves every key (MIS_EINVAL: solve
+ * again instead).  mis_size and rounds (nullable) receive |M| and the rounds
+ * run on the closure.  Uses the handle's workspace (not concurrently with its
+ * other solves); synchronises `stream`.
+ */
+int mis_repair(mis_graph *g, uint64_t seed, int64_t n_changed, const int32_t *changed,
+               uint8_t *out_status, int64_t *mis_size, int32_t *rounds, void *stream);
+
 /*
  * Release the handle.  If served requests on it are still in flight the
  * release is deferred until they finish.

@@ -1,0 +1,436 @@
+// dynamic.cu -- edge updates of a resident graph, and incremental repair of
+// an MIS after them: the dynamic setting (edge insertions and deletions) that
+// the paper's conclusion names as future work.
+//
+// mis_update_edges rebuilds the graph on the device: the arcs become 64-bit
+// keys (row << 32 | column), deleted ones are dropped, inserted ones (both
+// directions) appended, and a radix sort plus a unique pass give the new
+// sorted, duplicate-free, symmetric CSR, from which every create-time
+// structure is rebuilt exactly as mis_create_ex builds it.
+//
+// mis_repair turns the MIS of the graph before a set of edge changes into
+// the MIS of the graph after them, equal to a full solve of the new graph.
+// It relies on a fact of Algorithm 2 with fixed priorities: its result is the
+// greedy MIS in priority order, in which a vertex's state depends only on
+// its higher-priority neighbours.  So a changed edge {a, b} can only change
+// the state of its lower endpoint directly, and a changed vertex only that of
+// its lower-priority neighbours: the vertices whose state may change are the
+// downstream closure ("cone") of the lower endpoints.  Every vertex outside
+// the cone keeps its state; the rounds of Algorithm 2 then run on the cone
+// alone, with the vertices outside it fixed in or out.  This needs priorities
+// that do not depend on the graph: the H1 hash keys (Sec. 3.3).  Eq. 1's key
+// divides by the average degree d-bar, so any edge change moves every key and
+// a repair would be a full solve.
+#include <algorithm>
+#include <vector>
+
+#include <cub/cub.cuh>
+
+#include "common.cuh"
+#include "graph.h"
+#include "internal.h"
+
+namespace tcmis {
+
+namespace {
+
+constexpr unsigned long long kGone = ~0ull;  // key of a deleted arc (sorts last)
+
+// One warp per row: the 64-bit key of every arc, kGone for the arcs listed
+// (sorted) in del.
+__global__ void arc_keys_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                int32_t n, const unsigned long long* __restrict__ del,
+                                int64_t ndel, unsigned long long* __restrict__ keys) {
+    const long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (v >= n) return;
+    const int b = rp[v], e = rp[v + 1];
+    for (int p = b + (int)lane_id(); p < e; p += 32) {
+        const unsigned long long k = ((unsigned long long)v << 32) | (unsigned)col[p];
+        long long lo = 0, hi = ndel;  // first del entry >= k
+        while (lo < hi) {
+            const long long mid = (lo + hi) / 2;
+            if (del[mid] < k) lo = mid + 1;
+            else hi = mid;
+        }
+        keys[p] = (lo < ndel && del[lo] == k) ? kGone : k;
+    }
+}
+
+// rp[v] = the first arc of row v among the sorted keys; col = their low words.
+__global__ void csr_of_keys_kernel(const unsigned long long* __restrict__ keys, int64_t arcs,
+                                   int32_t n, int32_t* __restrict__ rp,
+                                   int32_t* __restrict__ col) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < arcs) col[i] = (int32_t)(keys[i] & 0xFFFFFFFFull);
+    if (i <= n) {
+        const unsigned long long k = (unsigned long long)i << 32;
+        long long lo = 0, hi = arcs;
+        while (lo < hi) {
+            const long long mid = (lo + hi) / 2;
+            if (keys[mid] < k) lo = mid + 1;
+            else hi = mid;
+        }
+        rp[i] = (int32_t)lo;
+    }
+}
+
+// ---- repair
+
+// H1 key of v for the seed (seed_mix = mix64(seed), as in every solve).
+__device__ __forceinline__ uint32_t hash_key(uint64_t seed, int v) {
+    return priority_key(kPrioHash, 0.f, 1, mix64(seed), (uint32_t)v);
+}
+
+// Does u outrank v (fixed keys; ties to the larger id, as in the rounds)?
+__device__ __forceinline__ bool above(uint32_t ku, int u, uint32_t kv, int v) {
+    return ku > kv || (ku == kv && u > v);
+}
+
+// Every vertex keeps its state for now: word = in or out from out[].
+__global__ void fixed_words_kernel(const uint8_t* __restrict__ out, int32_t n,
+                                   uint32_t* __restrict__ word) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) word[v] = out[v] ? kWordInMin : kWordOut;
+}
+
+// Puts v in the cone (once) and on the queue.
+__device__ __forceinline__ void claim(int v, int* __restrict__ in_cone, int32_t* __restrict__ queue,
+                                      int* __restrict__ qlen) {
+    if (atomicExch(in_cone + v, 1) == 0) queue[atomicAdd(qlen, 1)] = v;
+}
+
+// The lower endpoint of each changed edge starts the cone.
+__global__ void seed_cone_kernel(const int32_t* __restrict__ pairs, int64_t m, uint64_t seed,
+                                 int* __restrict__ in_cone, int32_t* __restrict__ queue,
+                                 int* __restrict__ qlen) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int a = pairs[2 * i], b = pairs[2 * i + 1];
+    claim(above(hash_key(seed, a), a, hash_key(seed, b), b) ? b : a, in_cone, queue, qlen);
+}
+
+// One warp per vertex w of the frontier queue[f0 .. f1): every neighbour that
+// w outranks joins the cone.
+__global__ void expand_cone_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                   uint64_t seed, int f0, int f1, int* __restrict__ in_cone,
+                                   int32_t* __restrict__ queue, int* __restrict__ qlen) {
+    const long long i = f0 + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (i >= f1) return;
+    const int w = queue[i];
+    const uint32_t kw = hash_key(seed, w);
+    for (int p = rp[w] + (int)lane_id(); p < rp[w + 1]; p += 32) {
+        const int u = col[p];
+        if (above(kw, w, hash_key(seed, u), u)) claim(u, in_cone, queue, qlen);
+    }
+}
+
+// The cone is undecided again: its keys, and 0 in the result.
+__global__ void open_cone_kernel(const int32_t* __restrict__ queue, int len, uint64_t seed,
+                                 uint32_t* __restrict__ word, uint8_t* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    const int v = queue[i];
+    word[v] = undecided_word(kPrioHash, hash_key(seed, v));
+    out[v] = 0;
+}
+
+// Phase 1 over W (one warp per vertex): v is a candidate when no neighbour's
+// word outranks its own (an in word outranks every key); candidates go in.
+__global__ void repair_select_kernel(const int32_t* __restrict__ rp,
+                                     const int32_t* __restrict__ col,
+                                     const int32_t* __restrict__ wl, int len,
+                                     uint32_t* __restrict__ word, uint8_t* __restrict__ out) {
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (i >= len) return;
+    const int v = wl[i];
+    const uint32_t wv = word[v];
+    bool blocked = false;
+    for (int p0 = rp[v]; p0 < rp[v + 1] && !blocked; p0 += 32) {
+        const int p = p0 + (int)lane_id();
+        bool hit = false;
+        if (p < rp[v + 1]) {
+            const int u = col[p];
+            const uint32_t wu = __ldcg(word + u);
+            hit = wu > wv || (wu == wv && u > v);
+        }
+        blocked = __any_sync(0xFFFFFFFFu, hit);
+    }
+    if (!blocked && lane_id() == 0) {
+        word[v] = wv | kWordInSet;
+        out[v] = 1;
+    }
+}
+
+// Phases 2+3 over W (one warp per vertex): a non-candidate with an in
+// neighbour goes out; the others stay, compacted into the next list.
+__global__ void repair_exclude_kernel(const int32_t* __restrict__ rp,
+                                      const int32_t* __restrict__ col,
+                                      const int32_t* __restrict__ wl, int len,
+                                      uint32_t* __restrict__ word, int32_t* __restrict__ next,
+                                      int* __restrict__ next_len) {
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (i >= len) return;
+    const int v = wl[i];
+    if (word[v] >= kWordInMin) return;  // a candidate of this round
+    bool excl = false;
+    for (int p0 = rp[v]; p0 < rp[v + 1] && !excl; p0 += 32) {
+        const int p = p0 + (int)lane_id();
+        excl = __any_sync(0xFFFFFFFFu, p < rp[v + 1] && __ldcg(word + col[p]) >= kWordInMin);
+    }
+    if (lane_id() == 0) {
+        if (excl) word[v] = kWordOut;
+        else next[atomicAdd(next_len, 1)] = v;
+    }
+}
+
+__global__ void count_in_kernel(const uint8_t* __restrict__ out, int32_t n,
+                                unsigned long long* __restrict__ total) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    unsigned c = 0;
+    for (long long v = tid; v < n; v += nthreads) c += out[v] != 0;
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if (lane_id() == 0 && c) atomicAdd(total, (unsigned long long)c);
+}
+
+unsigned warp_blocks(long long items) { return (unsigned)((32LL * items + 255) / 256); }
+unsigned thread_blocks(long long items) { return (unsigned)((items + 255) / 256); }
+
+// Checks pairs of vertex ids: 0 <= u, v < n, u != v.
+bool pairs_ok(const int32_t* pairs, int64_t m, int32_t n) {
+    for (int64_t i = 0; i < m; ++i) {
+        const int32_t u = pairs[2 * i], v = pairs[2 * i + 1];
+        if (u < 0 || v < 0 || u >= n || v >= n || u == v) return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+}  // namespace tcmis
+
+using namespace tcmis;
+
+extern "C" {
+
+int mis_update_edges(mis_graph* g, int64_t n_ins, const int32_t* ins, int64_t n_del,
+                     const int32_t* del, void* stream) {
+    clear_error();
+    if (!g || n_ins < 0 || n_del < 0 || (n_ins > 0 && !ins) || (n_del > 0 && !del))
+        return set_error(MIS_EINVAL, "mis_update_edges: null graph, negative count or null pairs");
+    if (g->d.count != 0) return set_error(MIS_EINVAL, "mis_update_edges: a batch cannot be updated");
+    if (g->inflight.load() != 0)
+        return set_error(MIS_EBUSY, "mis_update_edges: served requests of this graph in flight");
+    const int32_t n = g->d.n;
+    if (!pairs_ok(ins, n_ins, n) || !pairs_ok(del, n_del, n))
+        return set_error(MIS_EINVAL, "mis_update_edges: a pair is out of range or a self-loop");
+    const int64_t arcs = g->d.arcs;
+    const int64_t total = arcs + 2 * n_ins;
+    if (total > (int64_t)INT32_MAX - 16)
+        return set_error(MIS_EINVAL, "mis_update_edges: more than 2^31 arcs");
+    cudaError_t e = cudaSetDevice(g->d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // deletions (both directions, sorted) and insertions as arc keys
+    std::vector<unsigned long long> hdel, hins;
+    hdel.reserve(2 * n_del);
+    for (int64_t i = 0; i < n_del; ++i) {
+        const unsigned long long u = (unsigned)del[2 * i], v = (unsigned)del[2 * i + 1];
+        hdel.push_back(u << 32 | v);
+        hdel.push_back(v << 32 | u);
+    }
+    std::sort(hdel.begin(), hdel.end());
+    hins.reserve(2 * n_ins);
+    for (int64_t i = 0; i < n_ins; ++i) {
+        const unsigned long long u = (unsigned)ins[2 * i], v = (unsigned)ins[2 * i + 1];
+        hins.push_back(u << 32 | v);
+        hins.push_back(v << 32 | u);
+    }
+
+    unsigned long long *keys = nullptr, *sorted = nullptr, *dd = nullptr;
+    int32_t *rp = nullptr, *col = nullptr;
+    int* nsel = nullptr;
+    void* temp = nullptr;
+    size_t tb_sort = 0, tb_uniq = 0;
+    const size_t tot = (size_t)std::max<int64_t>(total, 1);
+    e = dev_alloc((void**)&keys, sizeof(unsigned long long) * tot);
+    if (e == cudaSuccess) e = dev_alloc((void**)&sorted, sizeof(unsigned long long) * tot);
+    if (e == cudaSuccess) e = dev_alloc((void**)&dd, sizeof(unsigned long long) * (hdel.size() + 1));
+    if (e == cudaSuccess) e = dev_alloc((void**)&nsel, sizeof(int));
+    if (e == cudaSuccess && !hdel.empty())
+        e = cudaMemcpyAsync(dd, hdel.data(), sizeof(unsigned long long) * hdel.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !hins.empty())
+        e = cudaMemcpyAsync(keys + arcs, hins.data(), sizeof(unsigned long long) * hins.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n > 0 && arcs > 0) {
+        arc_keys_kernel<<<warp_blocks(n), 256, 0, s>>>(g->d.rp, g->d.col, n, dd,
+                                                       (int64_t)hdel.size(), keys);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cub::DeviceRadixSort::SortKeys(nullptr, tb_sort, keys, sorted, (int)total, 0, 64, s);
+    if (e == cudaSuccess)
+        e = cub::DeviceSelect::Unique(nullptr, tb_uniq, sorted, keys, nsel, (int)total, s);
+    if (e == cudaSuccess) e = dev_alloc(&temp, std::max<size_t>(std::max(tb_sort, tb_uniq), 1));
+    if (e == cudaSuccess && total > 0)
+        e = cub::DeviceRadixSort::SortKeys(temp, tb_sort, keys, sorted, (int)total, 0, 64, s);
+    if (e == cudaSuccess && total > 0)
+        e = cub::DeviceSelect::Unique(temp, tb_uniq, sorted, keys, nsel, (int)total, s);
+    int hn = 0;
+    unsigned long long last = 0;
+    if (e == cudaSuccess && total > 0)
+        e = cudaMemcpyAsync(&hn, nsel, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && hn > 0)
+        e = cudaMemcpyAsync(&last, keys + hn - 1, sizeof(last), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const int64_t new_arcs = hn - (hn > 0 && last == kGone ? 1 : 0);
+    if (e == cudaSuccess) e = dev_alloc((void**)&rp, sizeof(int32_t) * ((size_t)n + 1));
+    if (e == cudaSuccess) e = dev_alloc((void**)&col, sizeof(int32_t) * ((size_t)new_arcs + 1));
+    if (e == cudaSuccess) {
+        csr_of_keys_kernel<<<thread_blocks(std::max<int64_t>(new_arcs, (int64_t)n + 1)), 256, 0,
+                             s>>>(keys, new_arcs, n, rp, col);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(keys);
+    dev_free(sorted);
+    dev_free(dd);
+    dev_free(nsel);
+    dev_free(temp);
+    if (e != cudaSuccess) {
+        dev_free(rp);
+        dev_free(col);
+        return set_cuda_error(e, "mis_update_edges");
+    }
+    // the new graph, built by the same create path; the handle takes its data
+    mis_options o = g->opt;
+    o.check_symmetry = 0;  // symmetric by construction
+    mis_graph* g2 = mis_create_ex(n, rp, col, 1, &o, stream);
+    dev_free(rp);
+    dev_free(col);
+    if (!g2) return MIS_EDEVICE;  // the error is already recorded
+    std::swap(g->d, g2->d);
+    g->path = g2->path;
+    g->tpr = g2->tpr;
+    g->grid = g2->grid;
+    g->tile_grid = g2->tile_grid;
+    g->tile_slots = g2->tile_slots;
+    g->csr_pending = g2->csr_pending;
+    mis_destroy(g2);  // frees the old graph's data
+    return MIS_OK;
+}
+
+int mis_repair(mis_graph* g, uint64_t seed, int64_t n_changed, const int32_t* changed,
+               uint8_t* out_status, int64_t* mis_size, int32_t* rounds, void* stream) {
+    clear_error();
+    if (!g || n_changed < 0 || (n_changed > 0 && !changed) || (!out_status && g && g->d.n > 0))
+        return set_error(MIS_EINVAL, "mis_repair: null graph, pairs or result");
+    if (g->d.count != 0) return set_error(MIS_EINVAL, "mis_repair: not for a batch");
+    if (g->opt.priority != MIS_PRIORITY_HASH)
+        return set_error(MIS_EINVAL,
+                         "mis_repair needs MIS_PRIORITY_HASH: Eq. 1 keys depend on the average "
+                         "degree, so an edge change moves every key (solve again instead)");
+    const int32_t n = g->d.n;
+    if (!pairs_ok(changed, n_changed, n))
+        return set_error(MIS_EINVAL, "mis_repair: a pair is out of range or a self-loop");
+    cudaError_t e = cudaSetDevice(g->d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (rounds) *rounds = 0;
+    if (mis_size) *mis_size = 0;
+    if (n == 0) return MIS_OK;
+    Workspace& w = g->d.ws;
+    uint32_t* word = w.word;
+    int32_t* wa = reinterpret_cast<int32_t*>(w.wl0);  // int4[cap] each: room for n ints
+    int32_t* wb = reinterpret_cast<int32_t*>(w.wl1);
+
+    int *in_cone = nullptr, *cnt = nullptr;
+    int32_t* queue = nullptr;
+    int32_t* dpairs = nullptr;
+    unsigned long long* dsum = nullptr;
+    e = dev_alloc((void**)&in_cone, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = dev_alloc((void**)&queue, sizeof(int32_t) * (size_t)n);
+    if (e == cudaSuccess) e = dev_alloc((void**)&cnt, 2 * sizeof(int));
+    if (e == cudaSuccess) e = dev_alloc((void**)&dsum, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dev_alloc((void**)&dpairs, sizeof(int32_t) * (2 * (size_t)n_changed + 2));
+    if (e == cudaSuccess) e = cudaMemsetAsync(in_cone, 0, sizeof(int) * (size_t)n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess && n_changed > 0)
+        e = cudaMemcpyAsync(dpairs, changed, sizeof(int32_t) * 2 * (size_t)n_changed,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        fixed_words_kernel<<<thread_blocks(n), 256, 0, s>>>(out_status, n, word);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && n_changed > 0) {
+        seed_cone_kernel<<<thread_blocks(n_changed), 256, 0, s>>>(dpairs, n_changed, seed,
+                                                                   in_cone, queue, cnt);
+        e = cudaGetLastError();
+    }
+    // the cone: breadth-first, each frontier a segment of the queue
+    int f0 = 0, f1 = 0;
+    while (e == cudaSuccess) {
+        e = cudaMemcpyAsync(&f1, cnt, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess || f1 == f0) break;
+        expand_cone_kernel<<<warp_blocks(f1 - f0), 256, 0, s>>>(g->d.rp, g->d.col, seed, f0, f1,
+                                                                in_cone, queue, cnt);
+        e = cudaGetLastError();
+        f0 = f1;
+    }
+    const int cone = f1;
+    if (e == cudaSuccess && cone > 0) {
+        open_cone_kernel<<<thread_blocks(cone), 256, 0, s>>>(queue, cone, seed, word, out_status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && cone > 0)
+        e = cudaMemcpyAsync(wa, queue, sizeof(int32_t) * (size_t)cone, cudaMemcpyDeviceToDevice, s);
+    // Algorithm 2's rounds on the cone
+    int len = cone, r = 0;
+    while (e == cudaSuccess && len > 0) {
+        if (r > n + 1) {
+            e = cudaErrorUnknown;
+            break;
+        }
+        e = cudaMemsetAsync(cnt + 1, 0, sizeof(int), s);
+        if (e == cudaSuccess) {
+            repair_select_kernel<<<warp_blocks(len), 256, 0, s>>>(g->d.rp, g->d.col, wa, len, word,
+                                                                  out_status);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            repair_exclude_kernel<<<warp_blocks(len), 256, 0, s>>>(g->d.rp, g->d.col, wa, len, word,
+                                                                   wb, cnt + 1);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&len, cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        std::swap(wa, wb);
+        ++r;
+    }
+    unsigned long long hsum = 0;
+    if (e == cudaSuccess && mis_size) {
+        count_in_kernel<<<std::min<unsigned>(thread_blocks(n), 1024), 256, 0, s>>>(out_status, n,
+                                                                                    dsum);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&hsum, dsum, sizeof(hsum), cudaMemcpyDeviceToHost, s);
+    }
+    const cudaError_t se = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = se;
+    dev_free(in_cone);
+    dev_free(queue);
+    dev_free(cnt);
+    dev_free(dsum);
+    dev_free(dpairs);
+    if (e != cudaSuccess) return set_cuda_error(e, "mis_repair");
+    if (rounds) *rounds = r;
+    if (mis_size) *mis_size = (int64_t)hsum;
+    return MIS_OK;
+}
+
+}  // extern "C"

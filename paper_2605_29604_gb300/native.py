@@ -139,6 +139,10 @@ def lib():
         L.mis_set_csr_pending.restype = ctypes.c_int
         L.mis_destroy.argtypes = [P]
         L.mis_destroy.restype = None
+        L.mis_update_edges.argtypes = [P, i64, P, i64, P, P]
+        L.mis_update_edges.restype = ctypes.c_int
+        L.mis_repair.argtypes = [P, u64, i64, P, P, ctypes.POINTER(i64), ctypes.POINTER(i32), P]
+        L.mis_repair.restype = ctypes.c_int
         L.mis_submit.argtypes = [P, u64, P, ctypes.POINTER(i64)]
         L.mis_submit.restype = ctypes.c_int
         L.mis_poll.argtypes = [i64]
@@ -169,7 +173,7 @@ EXPORTED = [
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
     "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
-    "mis_solve_noalloc",
+    "mis_solve_noalloc", "mis_update_edges", "mis_repair",
 ]
 
 
@@ -295,6 +299,32 @@ def mis_solve_multi_ex(h, seeds, out_ptr, stream=None):
     return _check(lib().mis_solve_multi_ex(h, len(s), _ptr(s),
                                            ctypes.c_void_p(out_ptr) if out_ptr else None,
                                            ctypes.c_void_p(stream) if stream else None))
+
+
+def _pairs(p):
+    a = np.ascontiguousarray(np.asarray(p, dtype=np.int32).reshape(-1, 2))
+    return a, len(a)
+
+
+def mis_update_edges(h, ins=(), dels=(), stream=None):
+    """Insert and delete undirected edges (host (m, 2) arrays of vertex pairs)."""
+    a, na = _pairs(ins)
+    d, nd = _pairs(dels)
+    return _check(lib().mis_update_edges(h, na, _ptr(a) if na else None, nd,
+                                         _ptr(d) if nd else None,
+                                         ctypes.c_void_p(stream) if stream else None))
+
+
+def mis_repair(h, seed, changed, out_ptr, stream=None):
+    """Repair the device result at out_ptr (a solve with `seed` before the
+    edges in `changed` were inserted or deleted); returns (|M|, rounds)."""
+    c, nc = _pairs(changed)
+    size = ctypes.c_int64()
+    rounds = ctypes.c_int32()
+    _check(lib().mis_repair(h, ctypes.c_uint64(int(seed)), nc, _ptr(c) if nc else None,
+                            ctypes.c_void_p(out_ptr) if out_ptr else None, ctypes.byref(size),
+                            ctypes.byref(rounds), ctypes.c_void_p(stream) if stream else None))
+    return size.value, rounds.value
 
 
 def mis_capture(h, seeds, out_status_dev):
