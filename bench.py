@@ -15,6 +15,8 @@ Workloads (synthetic, seeded; stand-ins for the paper's SuiteSparse graphs):
              packed as one block-diagonal union and solved in one launch
   serve      Poisson arrivals of solve requests over a resident pool of graphs
              (continuous batching), graphs/s and p50/p99 vs sequential solves
+  dynamic    batches of edge insertions/deletions on the resident R-MAT scale 22
+             graph, each applied and the MIS repaired (H1 priority), vs a full solve
 
 `--impl reference` times the CPU oracle (a plain sequential restatement of
 the same computation) on the host cores instead.
@@ -162,8 +164,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    name = {"rmat22": "rmat18", "batch4096": "er10k", "serve": "er10k"}.get(args.workload,
-                                                                             args.workload)
+    name = {"rmat22": "rmat18", "batch4096": "er10k", "serve": "er10k",
+            "dynamic": "rmat18"}.get(args.workload, args.workload)
     g, desc = make_workload(name)
     n, rp, col = g
     for _ in range(args.warmup):
@@ -503,6 +505,74 @@ def run_batch(args):
     return 0
 
 
+def run_dynamic(args):
+    """Dynamic graphs: batches of edge insertions and deletions on the
+    resident R-MAT scale 22 graph, each applied (mis_update_edges) and the
+    MIS repaired (mis_repair, H1 priority), against a full solve."""
+    import torch
+
+    from paper_2605_29604_gb300 import native
+    world, rank, local = _dist_setup()
+    (n, rp, col), desc = make_workload("rmat22")
+    arcs = int(rp[-1])
+    stream = torch.cuda.current_stream().cuda_stream
+    h = native.mis_create_ex(n, rp, col, 0, native.options(device=local, check_symmetry=0,
+                                                           priority=native.MIS_PRIORITY_HASH),
+                             stream)
+    native.mis_set_path(h, native.MIS_PATH_CSR, 0)
+    seed = 1
+    out = torch.empty(n, dtype=torch.uint8, device="cuda")
+    seeds = np.array([seed], dtype=np.uint64)
+    step_ms, clocks = time_device_steps(native, h, seeds, out.data_ptr(), stream, args.steps,
+                                        args.warmup, local, world)
+    solve_ms = float(np.median(step_ms))
+    native.mis_solve_ex(h, seeds, out.data_ptr(), stream)
+    rng = np.random.default_rng(2605)
+    src = np.repeat(np.arange(n, dtype=np.int32), np.diff(rp))
+    half = args.dyn_edges // 2
+    upd, rep, sizes, rounds = [], [], [], []
+    for _ in range(args.dyn_steps):
+        pick = rng.integers(0, arcs, size=half)  # existing arcs (either direction)
+        dels = np.stack([src[pick], col[pick]], axis=1).astype(np.int32)
+        u = rng.integers(0, n, size=half)
+        ins = np.stack([u, (u + rng.integers(1, n, size=half)) % n], axis=1).astype(np.int32)
+        t0 = time.perf_counter()
+        native.mis_update_edges(h, ins, dels, stream)
+        t1 = time.perf_counter()
+        size, r = native.mis_repair(h, seed, np.concatenate([ins, dels]), out.data_ptr(), stream)
+        t2 = time.perf_counter()
+        upd.append(t1 - t0)
+        rep.append(t2 - t1)
+        sizes.append(size)
+        rounds.append(r)
+    # the repaired result against a full solve of the updated graph
+    full = torch.empty(n, dtype=torch.uint8, device="cuda")
+    native.mis_solve_ex(h, seeds, full.data_ptr(), stream)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(full, out))
+    rep_ms = 1e3 * float(np.median(rep))
+    upd_ms = 1e3 * float(np.median(upd))
+    line = {
+        "metric": "edge changes applied and repaired per second", "impl": "ours",
+        "value": args.dyn_edges / ((rep_ms + upd_ms) / 1e3), "unit": "edge changes/s",
+        "n_gpus": world, "steps": args.dyn_steps, "warmup": max(args.warmup, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "dynamic", "graph": desc + ", H1 priority", "n": n, "arcs": arcs,
+                   "edges_per_batch": args.dyn_edges, "insert_delete_split": "half and half",
+                   "full_solve_ms": solve_ms, "repair_ms_p50": rep_ms, "update_ms_p50": upd_ms,
+                   "repair_rounds": rounds, "mis_sizes": sizes,
+                   "repair_equals_full_solve": same,
+                   "timing": "full solve: CUDA events, L2 flushed; update and repair: host "
+                             "wall clock (both synchronise their stream)"},
+        "clocks": clocks,
+    }
+    native.mis_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0 if same else 1
+
+
 def run_serve(args):
     """Continuous batching over a resident pool: saturated throughput, then
     Poisson arrivals at fractions of it (p50/p99), vs sequential solves."""
@@ -658,6 +728,9 @@ def main():
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--seq-requests", type=int, default=2000)
     ap.add_argument("--serve-blocks", type=int, default=0)
+    ap.add_argument("--dyn-edges", type=int, default=1000,
+                    help="dynamic workload: edge changes per batch (half inserted, half deleted)")
+    ap.add_argument("--dyn-steps", type=int, default=5)
     ap.add_argument("--multi", type=int, default=8,
                     help="also time this many seeds of the graph per launch (0 = off)")
     args = ap.parse_args()
@@ -667,6 +740,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "dynamic":
+        return run_dynamic(args)
     return run_single(args)
 
 

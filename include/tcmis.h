@@ -349,14 +349,15 @@ int mis_update_edges(mis_graph *g, int64_t n_ins, const int32_t *ins, int64_t n_
  * with that seed -- by re-deciding only the vertices whose state can change.
  * changed: HOST pairs (u, v) of every edge inserted or deleted since
  * out_status was computed (a superset is fine).  Algorithm 2 with fixed keys
- * yields the greedy MIS in priority order, where a vertex's state depends
- * only on its higher-priority neighbours; so only the downstream closure of
- * the lower endpoints of the changed edges can change, and the rounds run on
- * that closure alone, the other vertices fixed.  Requires MIS_PRIORITY_HASH
+ * yields the greedy MIS in priority order, where a vertex is in exactly when
+ * no neighbour that outranks it is in; so the repair re-decides the lower
+ * endpoints of the changed edges, then, pass by pass, the lower-priority
+ * neighbours of every vertex that flipped, until nothing flips; the other
+ * vertices keep their state.  Requires MIS_PRIORITY_HASH
  * (H1, Sec. 3.3), whose keys do not depend on the graph: Eq. 1's keys divide
  * by the average degree, so an edge change moves every key (MIS_EINVAL: solve
  * again instead).  mis_size and rounds (nullable) receive |M| and the rounds
- * run on the closure.  Uses the handle's workspace (not concurrently with its
+ * run over all passes.  Uses the handle's workspace (not concurrently with its
  * other solves); synchronises `stream`.
  */
 int mis_repair(mis_graph *g, uint64_t seed, int64_t n_changed, const int32_t *changed,

@@ -429,6 +429,8 @@ void free_graph(mis_graph* g) {
     dfree(d.s0_col);
     dfree(d.s0_pre);
     dfree(d.order0_s0);
+    dfree(d.dyn_mark);
+    dfree(d.dyn_cnt);
     dfree(d.keyed);
     dfree(d.out0);
     dfree(d.col_sel);

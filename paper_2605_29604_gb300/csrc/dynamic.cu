@@ -11,16 +11,17 @@
 // mis_repair turns the MIS of the graph before a set of edge changes into
 // the MIS of the graph after them, equal to a full solve of the new graph.
 // It relies on a fact of Algorithm 2 with fixed priorities: its result is the
-// greedy MIS in priority order, in which a vertex's state depends only on
-// its higher-priority neighbours.  So a changed edge {a, b} can only change
-// the state of its lower endpoint directly, and a changed vertex only that of
-// its lower-priority neighbours: the vertices whose state may change are the
-// downstream closure ("cone") of the lower endpoints.  Every vertex outside
-// the cone keeps its state; the rounds of Algorithm 2 then run on the cone
-// alone, with the vertices outside it fixed in or out.  This needs priorities
-// that do not depend on the graph: the H1 hash keys (Sec. 3.3).  Eq. 1's key
-// divides by the average degree d-bar, so any edge change moves every key and
-// a repair would be a full solve.
+// greedy MIS in priority order, where a vertex is in exactly when no
+// neighbour that outranks it is in.  So a changed edge {a, b} can only change
+// the state of its lower endpoint directly, and a vertex whose state flips
+// only that of the neighbours it outranks.  The repair runs in passes: the
+// first re-decides the lower endpoints, every other vertex fixed; each next
+// pass re-decides the lower-priority neighbours of the vertices that flipped,
+// until nothing flips.  Within a pass the rounds apply the greedy rule to the
+// listed vertices.  This needs priorities that do not depend on the graph:
+// the H1 hash keys (Sec. 3.3).  Eq. 1's key divides by the average degree
+// d-bar, so any edge change moves every key and a repair would be a full
+// solve.
 #include <algorithm>
 #include <vector>
 
@@ -93,93 +94,92 @@ __global__ void fixed_words_kernel(const uint8_t* __restrict__ out, int32_t n,
     if (v < n) word[v] = out[v] ? kWordInMin : kWordOut;
 }
 
-// Puts v in the cone (once) and on the queue.
-__device__ __forceinline__ void claim(int v, int* __restrict__ in_cone, int32_t* __restrict__ queue,
-                                      int* __restrict__ qlen) {
-    if (atomicExch(in_cone + v, 1) == 0) queue[atomicAdd(qlen, 1)] = v;
+// Puts v on a pass's list, once: mark[v] holds the stamp of the last pass
+// that listed it.
+__device__ __forceinline__ void enlist(int v, int stamp, int* __restrict__ mark,
+                                       int32_t* __restrict__ list, int* __restrict__ len) {
+    if (atomicExch(mark + v, stamp) != stamp) list[atomicAdd(len, 1)] = v;
 }
 
-// The lower endpoint of each changed edge starts the cone.
-__global__ void seed_cone_kernel(const int32_t* __restrict__ pairs, int64_t m, uint64_t seed,
-                                 int* __restrict__ in_cone, int32_t* __restrict__ queue,
-                                 int* __restrict__ qlen) {
+// The first pass: the lower endpoint of each changed edge.
+__global__ void seed_dirty_kernel(const int32_t* __restrict__ pairs, int64_t m, uint64_t seed,
+                                  int stamp, int* __restrict__ mark, int32_t* __restrict__ list,
+                                  int* __restrict__ len) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const int a = pairs[2 * i], b = pairs[2 * i + 1];
-    claim(above(hash_key(seed, a), a, hash_key(seed, b), b) ? b : a, in_cone, queue, qlen);
+    enlist(above(hash_key(seed, a), a, hash_key(seed, b), b) ? b : a, stamp, mark, list, len);
 }
 
-// One warp per vertex w of the frontier queue[f0 .. f1): every neighbour that
-// w outranks joins the cone.
-__global__ void expand_cone_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                   uint64_t seed, int f0, int f1, int* __restrict__ in_cone,
-                                   int32_t* __restrict__ queue, int* __restrict__ qlen) {
-    const long long i = f0 + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-    if (i >= f1) return;
-    const int w = queue[i];
-    const uint32_t kw = hash_key(seed, w);
-    for (int p = rp[w] + (int)lane_id(); p < rp[w + 1]; p += 32) {
-        const int u = col[p];
-        if (above(kw, w, hash_key(seed, u), u)) claim(u, in_cone, queue, qlen);
-    }
-}
-
-// The cone is undecided again: its keys, and 0 in the result.
-__global__ void open_cone_kernel(const int32_t* __restrict__ queue, int len, uint64_t seed,
-                                 uint32_t* __restrict__ word, uint8_t* __restrict__ out) {
+// The pass's vertices are undecided again: their keys, 0 in the result, and
+// their previous state kept in old[i].
+__global__ void open_dirty_kernel(const int32_t* __restrict__ list, int len, uint64_t seed,
+                                  uint32_t* __restrict__ word, uint8_t* __restrict__ out,
+                                  uint8_t* __restrict__ old) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= len) return;
-    const int v = queue[i];
+    const int v = list[i];
+    old[i] = out[v];
     word[v] = undecided_word(kPrioHash, hash_key(seed, v));
     out[v] = 0;
 }
 
-// Phase 1 over W (one warp per vertex): v is a candidate when no neighbour's
-// word outranks its own (an in word outranks every key); candidates go in.
-__global__ void repair_select_kernel(const int32_t* __restrict__ rp,
-                                     const int32_t* __restrict__ col,
-                                     const int32_t* __restrict__ wl, int len,
-                                     uint32_t* __restrict__ word, uint8_t* __restrict__ out) {
+// One warp per vertex of the pass: if its state flipped, every neighbour it
+// outranks goes on the next pass's list.
+__global__ void propagate_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                 const int32_t* __restrict__ list, int len, uint64_t seed,
+                                 const uint8_t* __restrict__ out, const uint8_t* __restrict__ old,
+                                 int stamp, int* __restrict__ mark, int32_t* __restrict__ next,
+                                 int* __restrict__ next_len) {
     const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     if (i >= len) return;
-    const int v = wl[i];
-    const uint32_t wv = word[v];
-    bool blocked = false;
-    for (int p0 = rp[v]; p0 < rp[v + 1] && !blocked; p0 += 32) {
-        const int p = p0 + (int)lane_id();
-        bool hit = false;
-        if (p < rp[v + 1]) {
-            const int u = col[p];
-            const uint32_t wu = __ldcg(word + u);
-            hit = wu > wv || (wu == wv && u > v);
-        }
-        blocked = __any_sync(0xFFFFFFFFu, hit);
-    }
-    if (!blocked && lane_id() == 0) {
-        word[v] = wv | kWordInSet;
-        out[v] = 1;
+    const int v = list[i];
+    if (out[v] == old[i]) return;
+    const uint32_t kv = hash_key(seed, v);
+    for (int p = rp[v] + (int)lane_id(); p < rp[v + 1]; p += 32) {
+        const int u = col[p];
+        if (above(kv, v, hash_key(seed, u), u)) enlist(u, stamp, mark, next, next_len);
     }
 }
 
-// Phases 2+3 over W (one warp per vertex): a non-candidate with an in
-// neighbour goes out; the others stay, compacted into the next list.
-__global__ void repair_exclude_kernel(const int32_t* __restrict__ rp,
-                                      const int32_t* __restrict__ col,
-                                      const int32_t* __restrict__ wl, int len,
-                                      uint32_t* __restrict__ word, int32_t* __restrict__ next,
-                                      int* __restrict__ next_len) {
+// One round over W (one warp per vertex), by the greedy rule the rounds of
+// Algorithm 2 compute: v goes out when a neighbour that outranks it is in,
+// goes in when every neighbour that outranks it is out, and stays otherwise.
+// Neighbours below v do not matter (those of the vertices that flip are
+// re-decided in the next pass).  A state, once decided, is final, so reading
+// one decided in the same round by another warp is safe.
+__global__ void repair_round_kernel(const int32_t* __restrict__ rp,
+                                    const int32_t* __restrict__ col,
+                                    const int32_t* __restrict__ wl, int len, uint64_t seed,
+                                    uint32_t* __restrict__ word, uint8_t* __restrict__ out,
+                                    int32_t* __restrict__ next, int* __restrict__ next_len) {
     const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     if (i >= len) return;
     const int v = wl[i];
-    if (word[v] >= kWordInMin) return;  // a candidate of this round
-    bool excl = false;
-    for (int p0 = rp[v]; p0 < rp[v + 1] && !excl; p0 += 32) {
+    const uint32_t kv = hash_key(seed, v);
+    bool in_above = false, open_above = false;
+    for (int p0 = rp[v]; p0 < rp[v + 1] && !in_above; p0 += 32) {
         const int p = p0 + (int)lane_id();
-        excl = __any_sync(0xFFFFFFFFu, p < rp[v + 1] && __ldcg(word + col[p]) >= kWordInMin);
+        bool in_u = false, open_u = false;
+        if (p < rp[v + 1]) {
+            const int u = col[p];
+            if (above(hash_key(seed, u), u, kv, v)) {
+                const uint32_t wu = __ldcg(word + u);
+                in_u = wu >= kWordInMin;
+                open_u = (wu >> 29) == 1u;
+            }
+        }
+        in_above = __any_sync(0xFFFFFFFFu, in_u);
+        open_above = open_above || __any_sync(0xFFFFFFFFu, open_u);
     }
-    if (lane_id() == 0) {
-        if (excl) word[v] = kWordOut;
-        else next[atomicAdd(next_len, 1)] = v;
+    if (lane_id() != 0) return;
+    if (in_above) {
+        word[v] = kWordOut;
+    } else if (!open_above) {
+        word[v] = kWordInMin | kv;
+        out[v] = 1;
+    } else {
+        next[atomicAdd(next_len, 1)] = v;
     }
 }
 
@@ -342,23 +342,36 @@ int mis_repair(mis_graph* g, uint64_t seed, int64_t n_changed, const int32_t* ch
     if (rounds) *rounds = 0;
     if (mis_size) *mis_size = 0;
     if (n == 0) return MIS_OK;
-    Workspace& w = g->d.ws;
+    GraphData& d = g->d;
+    // per-graph scratch: the pass stamps of every vertex, and four counters
+    if (!d.dyn_mark) {
+        if ((e = dev_alloc((void**)&d.dyn_mark, sizeof(int) * (size_t)n)) != cudaSuccess ||
+            (e = dev_alloc((void**)&d.dyn_cnt, 4 * sizeof(int))) != cudaSuccess ||
+            (e = cudaMemsetAsync(d.dyn_mark, 0, sizeof(int) * (size_t)n, s)) != cudaSuccess)
+            return set_cuda_error(e, "mis_repair: scratch");
+        d.dyn_stamp = 0;
+        d.footprint += 4 * (int64_t)n + 16;
+    }
+    if (d.dyn_stamp > INT32_MAX - 2 * (n + 2)) {  // stamps would wrap: start over
+        if ((e = cudaMemsetAsync(d.dyn_mark, 0, sizeof(int) * (size_t)n, s)) != cudaSuccess)
+            return set_cuda_error(e, "mis_repair: scratch");
+        d.dyn_stamp = 0;
+    }
+    Workspace& w = d.ws;
     uint32_t* word = w.word;
-    int32_t* wa = reinterpret_cast<int32_t*>(w.wl0);  // int4[cap] each: room for n ints
+    // lists in the workspace (each int4 array holds 4 ints per vertex)
+    int32_t* wa = reinterpret_cast<int32_t*>(w.wl0);
     int32_t* wb = reinterpret_cast<int32_t*>(w.wl1);
-
-    int *in_cone = nullptr, *cnt = nullptr;
-    int32_t* queue = nullptr;
+    int32_t* list = reinterpret_cast<int32_t*>(w.wlp);
+    int32_t* next = list + w.cap;
+    uint8_t* old = reinterpret_cast<uint8_t*>(list + 2 * w.cap);
+    int* cnt = d.dyn_cnt;  // [0] list length, [1] next round's length
     int32_t* dpairs = nullptr;
     unsigned long long* dsum = nullptr;
-    e = dev_alloc((void**)&in_cone, sizeof(int) * (size_t)n);
-    if (e == cudaSuccess) e = dev_alloc((void**)&queue, sizeof(int32_t) * (size_t)n);
-    if (e == cudaSuccess) e = dev_alloc((void**)&cnt, 2 * sizeof(int));
+    e = dev_alloc((void**)&dpairs, sizeof(int32_t) * (2 * (size_t)n_changed + 2));
     if (e == cudaSuccess) e = dev_alloc((void**)&dsum, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = dev_alloc((void**)&dpairs, sizeof(int32_t) * (2 * (size_t)n_changed + 2));
-    if (e == cudaSuccess) e = cudaMemsetAsync(in_cone, 0, sizeof(int) * (size_t)n, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 2 * sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 4 * sizeof(int), s);
     if (e == cudaSuccess && n_changed > 0)
         e = cudaMemcpyAsync(dpairs, changed, sizeof(int32_t) * 2 * (size_t)n_changed,
                             cudaMemcpyHostToDevice, s);
@@ -366,51 +379,55 @@ int mis_repair(mis_graph* g, uint64_t seed, int64_t n_changed, const int32_t* ch
         fixed_words_kernel<<<thread_blocks(n), 256, 0, s>>>(out_status, n, word);
         e = cudaGetLastError();
     }
+    int stamp = ++d.dyn_stamp;
     if (e == cudaSuccess && n_changed > 0) {
-        seed_cone_kernel<<<thread_blocks(n_changed), 256, 0, s>>>(dpairs, n_changed, seed,
-                                                                   in_cone, queue, cnt);
+        seed_dirty_kernel<<<thread_blocks(n_changed), 256, 0, s>>>(dpairs, n_changed, seed, stamp,
+                                                                    d.dyn_mark, list, cnt);
         e = cudaGetLastError();
     }
-    // the cone: breadth-first, each frontier a segment of the queue
-    int f0 = 0, f1 = 0;
-    while (e == cudaSuccess) {
-        e = cudaMemcpyAsync(&f1, cnt, sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess || f1 == f0) break;
-        expand_cone_kernel<<<warp_blocks(f1 - f0), 256, 0, s>>>(g->d.rp, g->d.col, seed, f0, f1,
-                                                                in_cone, queue, cnt);
-        e = cudaGetLastError();
-        f0 = f1;
-    }
-    const int cone = f1;
-    if (e == cudaSuccess && cone > 0) {
-        open_cone_kernel<<<thread_blocks(cone), 256, 0, s>>>(queue, cone, seed, word, out_status);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess && cone > 0)
-        e = cudaMemcpyAsync(wa, queue, sizeof(int32_t) * (size_t)cone, cudaMemcpyDeviceToDevice, s);
-    // Algorithm 2's rounds on the cone
-    int len = cone, r = 0;
+    // passes: re-decide the listed vertices with every other vertex fixed;
+    // the lower-priority neighbours of those that flipped form the next pass
+    int len = 0, r = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&len, cnt, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     while (e == cudaSuccess && len > 0) {
-        if (r > n + 1) {
-            e = cudaErrorUnknown;
-            break;
+        open_dirty_kernel<<<thread_blocks(len), 256, 0, s>>>(list, len, seed, word, out_status, old);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(wa, list, sizeof(int32_t) * (size_t)len, cudaMemcpyDeviceToDevice, s);
+        // Algorithm 2's rounds on the listed vertices
+        int wl = len;
+        int32_t *x = wa, *y = wb;
+        while (e == cudaSuccess && wl > 0) {
+            if (r > 2 * n + 2) {
+                e = cudaErrorUnknown;
+                break;
+            }
+            e = cudaMemsetAsync(cnt + 1, 0, sizeof(int), s);
+            if (e == cudaSuccess) {
+                repair_round_kernel<<<warp_blocks(wl), 256, 0, s>>>(d.rp, d.col, x, wl, seed, word,
+                                                                    out_status, y, cnt + 1);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&wl, cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            std::swap(x, y);
+            ++r;
         }
-        e = cudaMemsetAsync(cnt + 1, 0, sizeof(int), s);
+        // the flips, and the next pass
+        stamp = ++d.dyn_stamp;
+        if (e == cudaSuccess) e = cudaMemsetAsync(cnt + 2, 0, sizeof(int), s);
         if (e == cudaSuccess) {
-            repair_select_kernel<<<warp_blocks(len), 256, 0, s>>>(g->d.rp, g->d.col, wa, len, word,
-                                                                  out_status);
+            propagate_kernel<<<warp_blocks(len), 256, 0, s>>>(d.rp, d.col, list, len, seed,
+                                                              out_status, old, stamp, d.dyn_mark,
+                                                              next, cnt + 2);
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) {
-            repair_exclude_kernel<<<warp_blocks(len), 256, 0, s>>>(g->d.rp, g->d.col, wa, len, word,
-                                                                   wb, cnt + 1);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&len, cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&len, cnt + 2, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        std::swap(wa, wb);
-        ++r;
+        std::swap(list, next);
     }
     unsigned long long hsum = 0;
     if (e == cudaSuccess && mis_size) {
@@ -422,9 +439,6 @@ int mis_repair(mis_graph* g, uint64_t seed, int64_t n_changed, const int32_t* ch
     }
     const cudaError_t se = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = se;
-    dev_free(in_cone);
-    dev_free(queue);
-    dev_free(cnt);
     dev_free(dsum);
     dev_free(dpairs);
     if (e != cudaSuccess) return set_cuda_error(e, "mis_repair");

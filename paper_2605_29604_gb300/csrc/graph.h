@@ -83,6 +83,9 @@ struct GraphData {
     uint8_t* out0 = nullptr;      // result bytes decided at create time
     int32_t n_keyed = 0;
     int32_t n_tested = 0;             // vertices of the tested subgraph
+    int32_t* dyn_mark = nullptr;      // mis_repair: pass stamp of each vertex (lazily)
+    int* dyn_cnt = nullptr;           // mis_repair: list counters
+    int32_t dyn_stamp = 0;            // mis_repair: last pass stamp issued
     int64_t tested_prefix_arcs = 0;   // arcs of their selection prefixes
     int32_t n_sure_in = 0;
     int32_t n_sure_out = 0;
