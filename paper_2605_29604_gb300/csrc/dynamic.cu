@@ -3,9 +3,9 @@
 // the paper's conclusion names as future work.
 //
 // mis_update_edges rebuilds the graph on the device: the arcs become 64-bit
-// keys (row << 32 | column), deleted ones are dropped, inserted ones (both
-// directions) appended, and a radix sort plus a unique pass give the new
-// sorted, duplicate-free, symmetric CSR, from which every create-time
+// keys (row << 32 | column), already sorted; the deleted ones are dropped,
+// the sorted insertions (both directions) merged in, and a unique pass gives
+// the new sorted, duplicate-free, symmetric CSR, from which every create-time
 // structure is rebuilt exactly as mis_create_ex builds it.
 //
 // mis_repair turns the MIS of the graph before a set of edge changes into
@@ -35,7 +35,11 @@ namespace tcmis {
 
 namespace {
 
-constexpr unsigned long long kGone = ~0ull;  // key of a deleted arc (sorts last)
+constexpr unsigned long long kGone = ~0ull;  // key of a deleted arc
+
+struct NotGone {
+    __host__ __device__ bool operator()(const unsigned long long& k) const { return k != kGone; }
+};
 
 // One warp per row: the 64-bit key of every arc, kGone for the arcs listed
 // (sorted) in del.
@@ -247,57 +251,75 @@ int mis_update_edges(mis_graph* g, int64_t n_ins, const int32_t* ins, int64_t n_
         hins.push_back(u << 32 | v);
         hins.push_back(v << 32 | u);
     }
+    std::sort(hins.begin(), hins.end());
+    hins.erase(std::unique(hins.begin(), hins.end()), hins.end());
+    const int64_t nins = (int64_t)hins.size();
 
-    unsigned long long *keys = nullptr, *sorted = nullptr, *dd = nullptr;
+    // The old arcs are sorted keys already (rows ascending, columns ascending
+    // within a row): drop the deleted ones, merge in the sorted insertions,
+    // and drop the insertions of edges that exist -- three linear passes.
+    unsigned long long *keys = nullptr, *work = nullptr, *dd = nullptr, *ik = nullptr;
     int32_t *rp = nullptr, *col = nullptr;
     int* nsel = nullptr;
     void* temp = nullptr;
-    size_t tb_sort = 0, tb_uniq = 0;
+    size_t tb_sel = 0, tb_merge = 0, tb_uniq = 0;
     const size_t tot = (size_t)std::max<int64_t>(total, 1);
     e = dev_alloc((void**)&keys, sizeof(unsigned long long) * tot);
-    if (e == cudaSuccess) e = dev_alloc((void**)&sorted, sizeof(unsigned long long) * tot);
+    if (e == cudaSuccess) e = dev_alloc((void**)&work, sizeof(unsigned long long) * tot);
     if (e == cudaSuccess) e = dev_alloc((void**)&dd, sizeof(unsigned long long) * (hdel.size() + 1));
-    if (e == cudaSuccess) e = dev_alloc((void**)&nsel, sizeof(int));
+    if (e == cudaSuccess) e = dev_alloc((void**)&ik, sizeof(unsigned long long) * (size_t)(nins + 1));
+    if (e == cudaSuccess) e = dev_alloc((void**)&nsel, 2 * sizeof(int));
     if (e == cudaSuccess && !hdel.empty())
         e = cudaMemcpyAsync(dd, hdel.data(), sizeof(unsigned long long) * hdel.size(),
                             cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && !hins.empty())
-        e = cudaMemcpyAsync(keys + arcs, hins.data(), sizeof(unsigned long long) * hins.size(),
+    if (e == cudaSuccess && nins > 0)
+        e = cudaMemcpyAsync(ik, hins.data(), sizeof(unsigned long long) * (size_t)nins,
                             cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && n > 0 && arcs > 0) {
         arc_keys_kernel<<<warp_blocks(n), 256, 0, s>>>(g->d.rp, g->d.col, n, dd,
                                                        (int64_t)hdel.size(), keys);
         e = cudaGetLastError();
     }
+    const NotGone kept_op;
     if (e == cudaSuccess)
-        e = cub::DeviceRadixSort::SortKeys(nullptr, tb_sort, keys, sorted, (int)total, 0, 64, s);
+        e = cub::DeviceSelect::If(nullptr, tb_sel, keys, work, nsel, (int)std::max<int64_t>(arcs, 1),
+                                  kept_op, s);
     if (e == cudaSuccess)
-        e = cub::DeviceSelect::Unique(nullptr, tb_uniq, sorted, keys, nsel, (int)total, s);
-    if (e == cudaSuccess) e = dev_alloc(&temp, std::max<size_t>(std::max(tb_sort, tb_uniq), 1));
-    if (e == cudaSuccess && total > 0)
-        e = cub::DeviceRadixSort::SortKeys(temp, tb_sort, keys, sorted, (int)total, 0, 64, s);
-    if (e == cudaSuccess && total > 0)
-        e = cub::DeviceSelect::Unique(temp, tb_uniq, sorted, keys, nsel, (int)total, s);
+        e = cub::DeviceMerge::MergeKeys(nullptr, tb_merge, work, (int64_t)arcs, ik, nins, keys,
+                                        ::cuda::std::less<unsigned long long>{}, s);
+    if (e == cudaSuccess)
+        e = cub::DeviceSelect::Unique(nullptr, tb_uniq, keys, work, nsel + 1, (int)tot, s);
+    if (e == cudaSuccess)
+        e = dev_alloc(&temp, std::max<size_t>(std::max(tb_sel, std::max(tb_merge, tb_uniq)), 1));
+    int nkept = 0;
+    if (e == cudaSuccess && arcs > 0)
+        e = cub::DeviceSelect::If(temp, tb_sel, keys, work, nsel, (int)arcs, kept_op, s);
+    if (e == cudaSuccess && arcs > 0)
+        e = cudaMemcpyAsync(&nkept, nsel, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const int64_t merged = nkept + nins;
+    if (e == cudaSuccess && merged > 0)
+        e = cub::DeviceMerge::MergeKeys(temp, tb_merge, work, (int64_t)nkept, ik, nins, keys,
+                                        ::cuda::std::less<unsigned long long>{}, s);
     int hn = 0;
-    unsigned long long last = 0;
-    if (e == cudaSuccess && total > 0)
-        e = cudaMemcpyAsync(&hn, nsel, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && merged > 0)
+        e = cub::DeviceSelect::Unique(temp, tb_uniq, keys, work, nsel + 1, (int)merged, s);
+    if (e == cudaSuccess && merged > 0)
+        e = cudaMemcpyAsync(&hn, nsel + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess && hn > 0)
-        e = cudaMemcpyAsync(&last, keys + hn - 1, sizeof(last), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    const int64_t new_arcs = hn - (hn > 0 && last == kGone ? 1 : 0);
+    const int64_t new_arcs = hn;
     if (e == cudaSuccess) e = dev_alloc((void**)&rp, sizeof(int32_t) * ((size_t)n + 1));
     if (e == cudaSuccess) e = dev_alloc((void**)&col, sizeof(int32_t) * ((size_t)new_arcs + 1));
     if (e == cudaSuccess) {
         csr_of_keys_kernel<<<thread_blocks(std::max<int64_t>(new_arcs, (int64_t)n + 1)), 256, 0,
-                             s>>>(keys, new_arcs, n, rp, col);
+                             s>>>(work, new_arcs, n, rp, col);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     dev_free(keys);
-    dev_free(sorted);
+    dev_free(work);
     dev_free(dd);
+    dev_free(ik);
     dev_free(nsel);
     dev_free(temp);
     if (e != cudaSuccess) {
