@@ -59,6 +59,11 @@ def test_null_arguments_rejected_without_device(lib):
     o = native.options(threads_per_row=8)
     assert lib.mis_create_ex(0, None, None, 0, ctypes.byref(o), None) is None
     assert native.last_error()[0] == native.MIS_EINVAL
+    # the dynamic-graph entry points check their arguments first too
+    assert lib.mis_update_edges(None, 0, None, 0, None, None) == native.MIS_EINVAL
+    assert lib.mis_update_edges(None, -1, None, 0, None, None) == native.MIS_EINVAL
+    assert lib.mis_repair(None, 1, 0, None, None, None, None, None) == native.MIS_EINVAL
+    assert native.last_error()[0] == native.MIS_EINVAL
 
 
 def test_product_package_does_not_import_oracle():
