@@ -337,7 +337,8 @@ int64_t mis_footprint(const mis_graph *g);
  * symmetric) with every create-time structure, as mis_create_ex builds them
  * from the new CSR; the handle keeps its options and its resolved path.
  * Synchronises `stream`.  MIS_EBUSY while served requests of the handle are
- * in flight; on any error the handle keeps its old graph.
+ * in flight or captured solves of it (mis_capture) exist, since both hold its
+ * device memory; on any error the handle keeps its old graph.
  */
 int mis_update_edges(mis_graph *g, int64_t n_ins, const int32_t *ins, int64_t n_del,
                      const int32_t *del, void *stream);

@@ -1365,6 +1365,8 @@ int mis_capture(mis_graph* g, const uint64_t* seeds, uint8_t* out_status, mis_re
         mis_replay_destroy(r);
         return rc;
     }
+    r->counted = true;
+    g->replays.fetch_add(1);
     *replay = r;
     return MIS_OK;
 }
@@ -1389,6 +1391,7 @@ void mis_replay_destroy(mis_replay* r) {
     if (r->exec) cudaGraphExecDestroy(r->exec);
     if (r->graph) cudaGraphDestroy(r->graph);
     if (r->seeds_pinned) cudaFreeHost(r->seeds_pinned);
+    if (r->counted && r->g) r->g->replays.fetch_sub(1);
     delete r;
 }
 

@@ -225,6 +225,9 @@ int mis_update_edges(mis_graph* g, int64_t n_ins, const int32_t* ins, int64_t n_
     if (g->d.count != 0) return set_error(MIS_EINVAL, "mis_update_edges: a batch cannot be updated");
     if (g->inflight.load() != 0)
         return set_error(MIS_EBUSY, "mis_update_edges: served requests of this graph in flight");
+    if (g->replays.load() != 0)
+        return set_error(MIS_EBUSY, "mis_update_edges: captured solves of this graph exist "
+                                    "(they hold its device memory; destroy them first)");
     const int32_t n = g->d.n;
     if (!pairs_ok(ins, n_ins, n) || !pairs_ok(del, n_del, n))
         return set_error(MIS_EINVAL, "mis_update_edges: a pair is out of range or a self-loop");

@@ -117,6 +117,7 @@ struct mis_graph {
     std::mutex mu;
     std::atomic<int> inflight{0};       // served requests not yet finished
     std::atomic<bool> destroy_pending{false};
+    std::atomic<int> replays{0};        // live captured solves (they hold device pointers)
 };
 
 // A captured solve (mis_capture): an executable CUDA graph of one solve.
@@ -126,6 +127,7 @@ struct mis_replay {
     cudaGraphExec_t exec = nullptr;
     uint64_t* seeds_pinned = nullptr;  // the captured seeds, read by every replay
     int32_t path = 0;                  // round kernel captured
+    bool counted = false;              // counted in g->replays
 };
 
 namespace tcmis {

@@ -180,6 +180,13 @@ def test_dynamic_rejects_bad_input():
         # a failed update leaves the graph as it was
         got, st = gpu_solve(h, [4])
         assert np.array_equal(got, oracle.solve(g[0], g[1], g[2], 4, HASH).status)
+        torch.cuda.synchronize()
+        # nor a graph with a captured solve, until the replay is destroyed
+        r = native.mis_capture(h, [3], out.data_ptr())
+        with pytest.raises(RuntimeError):
+            native.mis_update_edges(h, [[0, 1]], ())
+        native.mis_replay_destroy(r)
+        native.mis_update_edges(h, [[0, 1]], ())
         # a batch cannot be updated
         b = native.mis_create_batch([g, g])
         try:
