@@ -344,6 +344,18 @@ int mis_update_edges(mis_graph *g, int64_t n_ins, const int32_t *ins, int64_t n_
                      const int32_t *del, void *stream);
 
 /*
+ * mis_add_vertices appends k isolated vertices, ids n .. n+k-1 (n grows to
+ * n+k; result buffers then need n+k bytes).  An isolated vertex is in every
+ * maximal independent set, so the result of the grown graph is the old
+ * result followed by k ones, and edges to the new vertices then go through
+ * mis_update_edges and mis_repair.  A vertex is removed from the set problem
+ * by deleting its edges (it is then isolated, hence in).  Same conditions as
+ * mis_update_edges (single graph, no served request in flight, no captured
+ * solve); synchronises `stream`.
+ */
+int mis_add_vertices(mis_graph *g, int32_t k, void *stream);
+
+/*
  * mis_repair turns out_status (DEVICE, n bytes), the result of a solve with
  * `seed` of the graph as it was before some edge changes, into the result of
  * the same solve of the graph as it is now -- bit-identical to mis_solve_ex

@@ -200,6 +200,30 @@ __global__ void count_in_kernel(const uint8_t* __restrict__ out, int32_t n,
 unsigned warp_blocks(long long items) { return (unsigned)((32LL * items + 255) / 256); }
 unsigned thread_blocks(long long items) { return (unsigned)((items + 255) / 256); }
 
+__global__ void fill_kernel(int32_t* __restrict__ p, int32_t count, int32_t value) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) p[i] = value;
+}
+
+// The handle takes the graph (n, rp, col: device CSR, valid and symmetric),
+// built by the same create path as mis_create_ex with its options; its old
+// data is freed.  On error the handle keeps its old graph.
+int adopt_csr(mis_graph* g, int32_t n, const int32_t* rp, const int32_t* col, void* stream) {
+    mis_options o = g->opt;
+    o.check_symmetry = 0;  // symmetric by construction
+    mis_graph* g2 = mis_create_ex(n, rp, col, 1, &o, stream);
+    if (!g2) return MIS_EDEVICE;  // the error is already recorded
+    std::swap(g->d, g2->d);
+    g->path = g2->path;
+    g->tpr = g2->tpr;
+    g->grid = g2->grid;
+    g->tile_grid = g2->tile_grid;
+    g->tile_slots = g2->tile_slots;
+    g->csr_pending = g2->csr_pending;
+    mis_destroy(g2);  // frees the old graph's data
+    return MIS_OK;
+}
+
 // Checks pairs of vertex ids: 0 <= u, v < n, u != v.
 bool pairs_ok(const int32_t* pairs, int64_t m, int32_t n) {
     for (int64_t i = 0; i < m; ++i) {
@@ -330,22 +354,49 @@ int mis_update_edges(mis_graph* g, int64_t n_ins, const int32_t* ins, int64_t n_
         dev_free(col);
         return set_cuda_error(e, "mis_update_edges");
     }
-    // the new graph, built by the same create path; the handle takes its data
-    mis_options o = g->opt;
-    o.check_symmetry = 0;  // symmetric by construction
-    mis_graph* g2 = mis_create_ex(n, rp, col, 1, &o, stream);
+    const int rc = adopt_csr(g, n, rp, col, stream);
     dev_free(rp);
     dev_free(col);
-    if (!g2) return MIS_EDEVICE;  // the error is already recorded
-    std::swap(g->d, g2->d);
-    g->path = g2->path;
-    g->tpr = g2->tpr;
-    g->grid = g2->grid;
-    g->tile_grid = g2->tile_grid;
-    g->tile_slots = g2->tile_slots;
-    g->csr_pending = g2->csr_pending;
-    mis_destroy(g2);  // frees the old graph's data
-    return MIS_OK;
+    return rc;
+}
+
+int mis_add_vertices(mis_graph* g, int32_t k, void* stream) {
+    clear_error();
+    if (!g || k < 0) return set_error(MIS_EINVAL, "mis_add_vertices: null graph or k < 0");
+    if (g->d.count != 0) return set_error(MIS_EINVAL, "mis_add_vertices: not for a batch");
+    if (g->inflight.load() != 0)
+        return set_error(MIS_EBUSY, "mis_add_vertices: served requests of this graph in flight");
+    if (g->replays.load() != 0)
+        return set_error(MIS_EBUSY, "mis_add_vertices: captured solves of this graph exist "
+                                    "(they hold its device memory; destroy them first)");
+    const int32_t n = g->d.n;
+    if ((int64_t)n + k > (int64_t)INT32_MAX - 16)
+        return set_error(MIS_EINVAL, "mis_add_vertices: more than 2^31 vertices");
+    if (k == 0) return MIS_OK;
+    cudaError_t e = cudaSetDevice(g->d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    // the same arcs; the new rows are empty: row_ptr[n + 1 ..] = arcs
+    const int32_t n2 = n + k;
+    int32_t *rp = nullptr, *col = nullptr;
+    e = dev_alloc((void**)&rp, sizeof(int32_t) * ((size_t)n2 + 1));
+    if (e == cudaSuccess) e = dev_alloc((void**)&col, sizeof(int32_t) * ((size_t)g->d.arcs + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rp, g->d.rp, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice,
+                            s);
+    if (e == cudaSuccess) {
+        fill_kernel<<<thread_blocks(k), 256, 0, s>>>(rp + n + 1, k, (int32_t)g->d.arcs);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && g->d.arcs > 0)
+        e = cudaMemcpyAsync(col, g->d.col, sizeof(int32_t) * (size_t)g->d.arcs,
+                            cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int rc = e == cudaSuccess ? adopt_csr(g, n2, rp, col, stream)
+                              : set_cuda_error(e, "mis_add_vertices");
+    dev_free(rp);
+    dev_free(col);
+    return rc;
 }
 
 int mis_repair(mis_graph* g, uint64_t seed, int64_t n_changed, const int32_t* changed,

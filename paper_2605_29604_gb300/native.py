@@ -143,6 +143,9 @@ def lib():
         L.mis_update_edges.restype = ctypes.c_int
         L.mis_repair.argtypes = [P, u64, i64, P, P, ctypes.POINTER(i64), ctypes.POINTER(i32), P]
         L.mis_repair.restype = ctypes.c_int
+        L.mis_add_vertices.argtypes = [P, i32, P]
+        L.mis_add_vertices.restype = ctypes.c_int
+        L.mis_repair.restype = ctypes.c_int
         L.mis_submit.argtypes = [P, u64, P, ctypes.POINTER(i64)]
         L.mis_submit.restype = ctypes.c_int
         L.mis_poll.argtypes = [i64]
@@ -173,7 +176,7 @@ EXPORTED = [
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
     "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
-    "mis_solve_noalloc", "mis_update_edges", "mis_repair",
+    "mis_solve_noalloc", "mis_update_edges", "mis_repair", "mis_add_vertices",
 ]
 
 
@@ -313,6 +316,11 @@ def mis_update_edges(h, ins=(), dels=(), stream=None):
     return _check(lib().mis_update_edges(h, na, _ptr(a) if na else None, nd,
                                          _ptr(d) if nd else None,
                                          ctypes.c_void_p(stream) if stream else None))
+
+
+def mis_add_vertices(h, k, stream=None):
+    """Append k isolated vertices (ids n .. n+k-1)."""
+    return _check(lib().mis_add_vertices(h, int(k), ctypes.c_void_p(stream) if stream else None))
 
 
 def mis_repair(h, seed, changed, out_ptr, stream=None):

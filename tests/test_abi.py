@@ -63,6 +63,7 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.mis_update_edges(None, 0, None, 0, None, None) == native.MIS_EINVAL
     assert lib.mis_update_edges(None, -1, None, 0, None, None) == native.MIS_EINVAL
     assert lib.mis_repair(None, 1, 0, None, None, None, None, None) == native.MIS_EINVAL
+    assert lib.mis_add_vertices(None, 1, None) == native.MIS_EINVAL
     assert native.last_error()[0] == native.MIS_EINVAL
 
 

@@ -158,6 +158,46 @@ def test_repair_isolates_and_reconnects():
         native.mis_destroy(h)
 
 
+@pytest.mark.parametrize("priority", [native.MIS_PRIORITY_EQ1, HASH])
+def test_add_vertices_then_connect(priority):
+    """Added vertices are isolated (in); once connected by inserted edges, a
+    solve -- and, with H1 keys, a repair of the grown result -- equals the
+    oracle's on the grown graph."""
+    import torch
+    rng = np.random.default_rng(5)
+    g = gg.rmat(12, 8, 0.57, 0.19, 0.19, 4, permute=True)
+    n, rp, col = g
+    seed = 77
+    h = create(g, priority=priority)
+    try:
+        out = _device_solve(h, n, seed)
+        k = 300
+        native.mis_add_vertices(h, k)
+        assert native.lib().mis_result_size(h) == n + k
+        grown = (n + k, np.concatenate([rp, np.full(k, rp[-1], dtype=rp.dtype)]), col)
+        got, st = gpu_solve(h, [seed])
+        assert np.array_equal(got, oracle.solve(*grown, seed, priority).status)
+        assert (got[n:] == 1).all()
+        # connect every new vertex to two old ones and to the next new one
+        new = np.arange(n, n + k)
+        ins = np.concatenate([np.stack([new, rng.integers(0, n, k)], 1),
+                              np.stack([new, rng.integers(0, n, k)], 1),
+                              np.stack([new[:-1], new[1:]], 1)]).astype(np.int32)
+        native.mis_update_edges(h, ins, ())
+        g2 = apply_changes(grown, ins, np.zeros((0, 2), np.int32))
+        want = oracle.solve(g2[0], g2[1], g2[2], seed, priority)
+        got, st = gpu_solve(h, [seed])
+        assert np.array_equal(got, want.status)
+        if priority == HASH:
+            buf = torch.ones(n + k, dtype=torch.uint8, device="cuda")
+            buf[:n] = out[:n]
+            native.mis_repair(h, seed, ins, buf.data_ptr(),
+                              torch.cuda.current_stream().cuda_stream)
+            assert np.array_equal(buf.cpu().numpy(), want.status)
+    finally:
+        native.mis_destroy(h)
+
+
 def test_dynamic_rejects_bad_input():
     import torch
     g = gg.er_10k_deg8(1)
@@ -192,6 +232,8 @@ def test_dynamic_rejects_bad_input():
         try:
             with pytest.raises(RuntimeError):
                 native.mis_update_edges(b, [[0, 1]], ())
+            with pytest.raises(RuntimeError):
+                native.mis_add_vertices(b, 3)
         finally:
             native.mis_destroy(b)
     finally:
