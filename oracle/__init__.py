@@ -16,6 +16,10 @@ What is here (each function cites the part of the paper it follows):
 - ``brute_force_mis`` every maximal independent set of a graph with n <= 20.
 - ``eps`` / ``priority`` / ``splitmix64_mix``  the pieces of Eq. 1, exposed
                       so that tests can pin them separately.
+- ``rounds_parallel`` / ``solve_parallel``  not the oracle: a second CPU
+                      baseline, the same rounds over worklists on all host
+                      cores (``cpu_parallel.c``, OpenMP), checked against
+                      ``rounds`` by the tests and timed beside it by bench.py.
 
 The arithmetic lives in ``tcmis_oracle.c`` (plain C, one thread, binary32
 round-to-nearest with no FMA contraction); the brute force is pure Python.
@@ -185,6 +189,69 @@ def solve(n: int, row_ptr, col_idx, seed: int, priority: int = PRIORITY_EQ1) -> 
     """Keys (Eq. 1 or another heuristic of Sec. 3.3) then Algorithm 2's rounds:
     the full hot path on the CPU."""
     return rounds(n, row_ptr, col_idx, keys(n, row_ptr, seed, priority))
+
+
+# ---- the second CPU baseline (cpu_parallel.c): the same rounds on all cores
+
+_PAR_SRC = os.path.join(_HERE, "cpu_parallel.c")
+_PAR_LIB = os.path.join(_HERE, "libcpupar.so")
+_par = None
+
+
+def build_parallel(force: bool = False) -> str:
+    """Compile cpu_parallel.c with OpenMP where gcc has it, else without."""
+    if (force or not os.path.exists(_PAR_LIB)
+            or os.path.getmtime(_PAR_LIB) < os.path.getmtime(_PAR_SRC)):
+        tmp = _PAR_LIB + f".tmp{os.getpid()}"
+        base = ["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-o", tmp, _PAR_SRC]
+        if subprocess.call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
+        os.replace(tmp, _PAR_LIB)
+    return _PAR_LIB
+
+
+def _load_parallel():
+    global _par
+    with _lock:
+        if _par is None:
+            lib = ctypes.CDLL(build_parallel())
+            P = ctypes.c_void_p
+            lib.par_rounds.argtypes = [ctypes.c_int32, P, P, P, P, P, P, P, ctypes.c_int32,
+                                       ctypes.c_int32]
+            lib.par_rounds.restype = ctypes.c_int
+            lib.par_threads.argtypes = []
+            lib.par_threads.restype = ctypes.c_int
+            _par = lib
+        return _par
+
+
+def parallel_threads() -> int:
+    return int(_load_parallel().par_threads())
+
+
+def rounds_parallel(n: int, row_ptr, col_idx, key, threads: int = 0) -> RoundsResult:
+    """Algorithm 2's rounds on all host cores (cpu_parallel.c); the same
+    result, rounds and alive sets as rounds().  work is not counted (0)."""
+    rp, col = _csr(row_ptr, col_idx)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    if n == 0:
+        return RoundsResult(np.zeros(0, np.uint8), 0, 0, 0, np.zeros(0, np.int64))
+    cap = n + 1
+    st = np.empty(n, dtype=np.uint8)
+    r = ctypes.c_int32()
+    a = ctypes.c_int64()
+    per = np.zeros(cap, dtype=np.int64)
+    rc = _load_parallel().par_rounds(n, _p(rp), _p(col), _p(k), _p(st), ctypes.byref(r),
+                                     ctypes.byref(a), _p(per), cap, int(threads))
+    if rc != 0:
+        raise RuntimeError("parallel round simulation did not terminate within the round cap")
+    return RoundsResult(st, r.value, 0, a.value, per[:r.value].copy())
+
+
+def solve_parallel(n: int, row_ptr, col_idx, seed: int, priority: int = PRIORITY_EQ1,
+                   threads: int = 0) -> RoundsResult:
+    """keys() (sequential), then the rounds on all host cores."""
+    return rounds_parallel(n, row_ptr, col_idx, keys(n, row_ptr, seed, priority), threads)
 
 
 def brute_force_mis(n: int, row_ptr, col_idx) -> list[int]:

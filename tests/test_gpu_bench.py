@@ -48,5 +48,7 @@ def test_single_graph_line():
     c = d["cpu_baseline"]
     assert c["kind"] == "oracle" and c["cores"] >= 1 and c["value"] > 0
     assert c["gpu_result_equals_oracle"] is True
+    par = d["cpu_parallel"]
+    assert par["value"] > 0 and par["cores"] >= 1 and par["result_equals_oracle"] is True
     assert d["gpu_launches"] == 3
     assert d["config"]["multi_seed"]["k"] == 2
