@@ -1,0 +1,103 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times (create-time degree order, autotuned kernel, persistent launch; the
+batch as a captured and replayed launch).  The oracle solves these graphs in
+seconds, so every output is compared, with the round structure; independence
+and maximality are checked on top."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_29604_gb300 import graphgen as gg
+from paper_2605_29604_gb300 import native
+
+from gpu_util import assert_same, ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    torch.cuda.set_device(0)
+
+
+def _bench_handle(g):
+    n, rp, col = g
+    h = native.mis_create_ex(n, rp, col, 0, native.options(check_symmetry=1, order_rows=2), None)
+    native.mis_autotune(h, 3)
+    return h
+
+
+def _solve(h, n, seeds):
+    import torch
+    out = torch.full((max(n, 1),), 7, dtype=torch.uint8, device="cuda")
+    native.mis_solve_ex(h, np.asarray(seeds, dtype=np.uint64), out.data_ptr(),
+                        torch.cuda.current_stream().cuda_stream)
+    return out[:n].cpu().numpy(), native.mis_get_stats(h)
+
+
+@pytest.mark.parametrize("name", ["rmat22", "grid", "grid_perm"])
+def test_full_size_single_graph(name):
+    g = {"rmat22": lambda: gg.rmat22(seed=22),
+         "grid": lambda: gg.grid2048(seed=3),
+         "grid_perm": lambda: gg.grid2048(seed=3, permute_ids=True)}[name]()
+    n, rp, col = g
+    h = _bench_handle(g)
+    try:
+        for seed in (1, 2**63 + 11):
+            got, st = _solve(h, n, [seed])
+            assert_same(g, seed, got, st)
+            assert oracle.check(n, rp, col, got)[0] == 0
+    finally:
+        native.mis_destroy(h)
+
+
+def test_full_size_multi_seed_rmat22():
+    """Eight seeds of R-MAT scale 22 in one launch: each equals its oracle solve."""
+    import torch
+    g = gg.rmat22(seed=22)
+    n, rp, col = g
+    h = _bench_handle(g)
+    try:
+        seeds = np.arange(1, 9, dtype=np.uint64)
+        out = torch.empty(8 * n, dtype=torch.uint8, device="cuda")
+        native.mis_solve_multi_ex(h, seeds, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        host = out.cpu().numpy()
+        for s in (0, 7):
+            want = oracle.solve(n, rp, col, int(seeds[s]))
+            assert np.array_equal(host[s * n:(s + 1) * n], want.status), s
+    finally:
+        native.mis_destroy(h)
+
+
+def test_full_size_batch4096_replayed():
+    """The 4096-graph batch as bench.py times it: one captured launch,
+    replayed; every graph's result equals its own oracle solve."""
+    import torch
+    parts = gg.batch_mixed(4096, seed=4096, nmin=64, nmax=65536)
+    h = native.mis_create_batch(parts, native.options(check_symmetry=1, order_rows=2))
+    try:
+        native.mis_autotune(h, 3)
+        size = native.lib().mis_result_size(h)
+        out = torch.full((size,), 7, dtype=torch.uint8, device="cuda")
+        seeds = np.arange(1, len(parts) + 1, dtype=np.uint64)
+        r = native.mis_capture(h, seeds, out.data_ptr())
+        try:
+            s = torch.cuda.current_stream().cuda_stream
+            native.mis_replay_launch(r, s)
+            out.fill_(7)
+            native.mis_replay_launch(r, s)  # the second replay must redo everything
+            host = out.cpu().numpy()
+        finally:
+            native.mis_replay_destroy(r)
+        off = 0
+        for i, (n, rp, col) in enumerate(parts):
+            want = oracle.solve(n, rp, col, int(seeds[i])).status
+            assert np.array_equal(host[off:off + n], want), i
+            off += n
+        assert off == size
+    finally:
+        native.mis_destroy(h)
