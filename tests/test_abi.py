@@ -75,3 +75,29 @@ def test_product_package_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "tcmis_oracle" not in text and "liboracle" not in text, f
+
+
+def _header_fields(struct):
+    text = open(os.path.join(ROOT, "include", "tcmis.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (struct, struct), text, flags=re.S)
+    assert body, struct
+    sizes = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+             "float": ctypes.c_float, "double": ctypes.c_double}
+    out = []
+    for ty, name, _, count in re.findall(
+            r"(int32_t|int64_t|uint64_t|float|double)\s+(\w+)(\[(\d+)\])?;", body.group(1)):
+        out.append((name, sizes[ty] * int(count) if count else sizes[ty]))
+    return out
+
+
+@pytest.mark.parametrize("struct", ["mis_options", "mis_stats", "mis_tuning"])
+def test_binding_structs_match_the_header(struct):
+    """The ctypes mirrors have the header's fields, in order, with its types
+    (so offsets and sizes agree on every platform ctypes knows)."""
+    want = _header_fields(struct)
+    got = getattr(native, struct)._fields_
+    assert [n for n, _ in got] == [n for n, _ in want]
+    for (n, t), (_, w) in zip(got, want):
+        assert ctypes.sizeof(t) == ctypes.sizeof(w), n
+        assert getattr(t, "_type_", t) == getattr(w, "_type_", w), n
