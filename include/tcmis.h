@@ -386,12 +386,19 @@ void mis_destroy(mis_graph *g);
  *
  * Continuous batching over resident graphs.  mis_submit queues a request
  * (graph, seed, HOST output buffer of n bytes that must stay valid until the
- * request completes).  A scheduler thread admits queued requests into free
- * slots while their workspace fits the HBM budget, and runs steps: one step
- * advances every admitted request by one round of Algorithm 2 in a single
- * launch, so requests that arrive while others run share the device.  A
- * finished request's result is copied to its output buffer before it is
- * reported done.
+ * request completes).  One scheduler thread per process owns up to max_slots
+ * solve slots, each with its own CUDA stream and workspace, and loops:
+ *   retire  slots whose solve finished: the result is copied to the caller's
+ *           buffer, then the request is reported done;
+ *   admit   queued requests, oldest first, while a slot is free and the
+ *           workspace bytes of the admitted requests fit the HBM budget;
+ *   group   queued requests on the same single graph ride one slot together,
+ *           up to 8, solved by one multi-seed launch (see mis_solve_multi_ex);
+ *   launch  each admitted request or group as a whole solve on its slot's
+ *           stream: one block for graphs of up to 16384 vertices, else a
+ *           cooperative grid of at most serve_blocks blocks.
+ * Requests that arrive while others run are admitted as slots and memory
+ * free up, and their solves run on the device at the same time as the others'.
  */
 int mis_submit(mis_graph *g, uint64_t seed, uint8_t *out_status, mis_ticket *ticket);
 
@@ -426,22 +433,26 @@ void mis_serve_shutdown(void);
  * allocation: no cudaMalloc, no cudaFree, no allocating library routine.
  *   n           number of vertices, 0 <= n <= 262144 (larger n: MIS_EINVAL)
  *   row_ptr     DEVICE int32[n+1]
- *   col_idx     DEVICE int32[row_ptr[n]] (no padding or alignment needed)
- *   seed        seed of Eq. 1's perturbation
+ *   col_idx     DEVICE int32[row_ptr[n]] (no padding or alignment needed);
+ *               may be NULL only when row_ptr[n] = 0 (else MIS_EINVAL)
+ *   seed        seed of the hashed priority perturbation; the same meaning
+ *               as mis_solve's seed
  *   out_status  DEVICE uint8[n]: 1 if the vertex is in the MIS, else 0
  *   stream      cudaStream_t (NULL = legacy default stream)
  * The result equals mis_solve's for the same graph and seed.  The call
- * enqueues on `stream` and waits for it; it returns MIS_OK, MIS_EINVAL,
- * MIS_ETIMEDOUT, MIS_EINTERNAL or MIS_EDEVICE.  The graph is NOT validated:
- * a graph that breaks the input contract gives an unspecified set, but the
- * kernel never reads or writes outside the buffers above.
+ * enqueues on `stream` and waits for it before it returns; it returns MIS_OK,
+ * MIS_EINVAL, MIS_ETIMEDOUT, MIS_EINTERNAL or MIS_EDEVICE.  The graph is NOT
+ * validated: a graph that breaks the input contract gives an unspecified
+ * set, but the kernel never reads or writes outside the buffers above.
  *
  * Scratch: the library holds one fixed array of 3 MiB + 1 KiB in device
- * memory on every GPU that loads it, until the process exits.  The first
- * call on a device looks up that array's device address (with that device
- * current); make that first call before any stream capture.  All calls share
- * the array, so calls whose work overlaps on a GPU (different streams or
- * threads) race and must be serialised by the caller.
+ * memory on every GPU that loads it, until the process exits.  Each call
+ * looks up that array's device address on the current device; the first
+ * call on a device also loads the library's device code there, so make it
+ * before any stream capture begins on that device.  All calls share the
+ * array, and each call clears the part that must start at zero; calls whose
+ * work overlaps on a GPU (different streams or threads) race and must be
+ * serialised by the caller.
  */
 int mis_solve_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint64_t seed,
                       uint8_t *out_status, void *stream);

@@ -17,7 +17,6 @@
 // the input contract yields an unspecified set but no out-of-bounds access.
 // The graph is not validated.
 #include <cstddef>
-#include <mutex>
 
 #include "common.cuh"
 #include "graph.h"
@@ -38,10 +37,6 @@ constexpr size_t kScratchBytes = kCtlBytes + 3 * kVecBytes;  // 3 MiB + 1 KiB
 static_assert(sizeof(Ctl) <= kCtlBytes, "control block does not fit");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {};
 
 template <bool kSelect>
 __device__ __forceinline__ bool scan_scalar(const int32_t* __restrict__ col,
@@ -87,7 +82,9 @@ __global__ void __launch_bounds__(kNoAllocBlock, 2)
     const long long nwarps = (long long)nblocks * wpb;
     grid_barrier_start();
     __shared__ int s_count;        // next worklist size, loaded once per block
-    const int arcs = max(0, rp[n]);
+    // a null col_idx reads as a graph without arcs (the host rejects it when
+    // row_ptr[n] > 0), so no scan ever dereferences it
+    const int arcs = col ? max(0, rp[n]) : 0;
     auto row = [&](int v, int& b, int& e) {
         b = min(max(rp[v], 0), arcs);
         e = min(max(rp[v + 1], b), arcs);
@@ -187,24 +184,26 @@ extern "C" int mis_solve_noalloc(int32_t n, const int32_t* row_ptr, const int32_
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_cuda_error(e, "mis_solve_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices)
-        return set_error(MIS_EINVAL, "mis_solve_noalloc: device ordinal beyond 63");
+    // The scratch array's address as the current device sees it, looked up on
+    // every call: the first lookup on a device loads the module there, later
+    // ones are table lookups.  Not cached, because a context that is torn
+    // down and created again (cudaDeviceReset) may place the array elsewhere.
     void* base = nullptr;
-    {
-        // once per device, with that device current: the address of the
-        // scratch array as the device sees it
-        std::lock_guard<std::mutex> lk(g_setup_mu);
-        if (!g_scratch_addr[dev]) {
-            e = cudaGetSymbolAddress(&g_scratch_addr[dev], g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                g_scratch_addr[dev] = nullptr;
-                return set_cuda_error(e, "mis_solve_noalloc: cudaGetSymbolAddress");
-            }
-        }
-        base = g_scratch_addr[dev];
-    }
+    e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+    if (e != cudaSuccess || !base)
+        return set_cuda_error(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                              "mis_solve_noalloc: cudaGetSymbolAddress");
     if (n == 0) return MIS_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (!col_idx) {
+        // col_idx may be null only for a graph without arcs
+        int32_t arcs = 0;
+        e = cudaMemcpyAsync(&arcs, row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return set_cuda_error(e, "mis_solve_noalloc: read row_ptr[n]");
+        if (arcs != 0)
+            return set_error(MIS_EINVAL, "mis_solve_noalloc: null col_idx with row_ptr[n] > 0");
+    }
     // the control block must start at zero; words and worklists are written
     // before they are read
     e = cudaMemsetAsync(base, 0, kCtlBytes, s);

@@ -67,6 +67,26 @@ def test_eps_uses_high_bits_of_double_mix():
         assert oracle.eps(seed, v) == top24 / 2**24
 
 
+def test_h1_key_uses_high_bits_of_double_mix():
+    # H1 (Sec. 3.3): P(v) = hash(v), read as the high 29 bits of the high
+    # word of mix(mix(seed) ^ v), stored above 2^29 so that the packed state
+    # prefix stays 001.  Built here from the vector-pinned finaliser by bit
+    # fields; a slip to the low 32 bits, or to the low 29 bits of the high
+    # word, changes the key of almost every vertex.
+    n = 64
+    rp = np.arange(0, 2 * n + 1, 2, dtype=np.int32)  # every vertex has degree 2
+    for seed in (0, 1, 12345, 2**63 + 11):
+        got = oracle.keys(n, rp, seed, oracle.PRIORITY_HASH)
+        mixed = oracle.splitmix64_mix(seed)
+        for v in range(n):
+            h = oracle.splitmix64_mix(mixed ^ v)
+            hi32 = h >> 32
+            assert int(got[v]) == (1 << 29) + (hi32 >> 3), (seed, v)
+            lo32 = h & 0xFFFFFFFF
+            if (lo32 >> 3) != (hi32 >> 3):
+                assert int(got[v]) != (1 << 29) + (lo32 >> 3)
+
+
 @pytest.mark.parametrize("seed", [1, 99, 2024])
 def test_priority_is_eq1_within_binary32_rounding(seed):
     # Exact rational value of Eq. 1 at the binary32 inputs, versus the

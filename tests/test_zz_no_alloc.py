@@ -82,3 +82,44 @@ def test_noalloc_limit_and_empty():
                                  dummy.data_ptr())
     assert ei.value.code == native.MIS_EINVAL
     assert "262144" in str(ei.value)
+
+
+def test_noalloc_allocates_nothing():
+    # what the entry point exists for: after a warm-up call (which loads the
+    # library's device code, the fixed array included), further calls leave
+    # the device's free memory and the torch pool's bytes exactly as they were
+    import torch
+    g = gg.rmat(14, 16, 0.57, 0.19, 0.19, 9, permute=True)
+    n, rp, col = g
+    drp = torch.from_numpy(rp).cuda()
+    dcol = torch.from_numpy(col).cuda()
+    out = torch.empty(n, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    native.mis_solve_noalloc(n, drp.data_ptr(), dcol.data_ptr(), 1, out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    allocated0 = torch.cuda.memory_allocated()
+    for seed in (2, 3, 4):
+        native.mis_solve_noalloc(n, drp.data_ptr(), dcol.data_ptr(), seed, out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_reserved() == reserved0
+    assert torch.cuda.memory_allocated() == allocated0
+    assert np.array_equal(out.cpu().numpy(), _regular(g, 4))
+
+
+def test_noalloc_null_col_idx():
+    import torch
+    # a graph without arcs may pass a null col_idx: every vertex is isolated
+    n = 37
+    drp = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    out = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    native.mis_solve_noalloc(n, drp.data_ptr(), 0, 5, out.data_ptr())
+    assert int(out.sum()) == n
+    # with arcs, a null col_idx is refused before any launch
+    rp = torch.from_numpy(np.arange(0, 2 * n + 1, 2, dtype=np.int32)).cuda()
+    with pytest.raises(native.MisError) as ei:
+        native.mis_solve_noalloc(n, rp.data_ptr(), 0, 5, out.data_ptr())
+    assert ei.value.code == native.MIS_EINVAL
