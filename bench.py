@@ -4,16 +4,21 @@ A step is one full solve of the hot path -- Eq. 1 priorities, then every
 round of Algorithm 2 (selection test, exclusion test, state update,
 compaction) until the alive set is empty -- on a graph already resident in
 HBM.  value = arcs solved / device time of the K timed steps (CUDA events on
-the launching stream; a 256 MB write between steps flushes L2).
+the launching stream; a 256 MB write between steps flushes L2).  The timed
+graph is created with no create-time decisions (order_rows = 0), so each
+solve starts from the CSR; the same solve on a graph whose create-time
+structures decide the seed-independent round-0 vertices is reported beside
+it as `amortized`, with create times and create + first solve.
 
 Workloads (synthetic, seeded; stand-ins for the paper's SuiteSparse graphs):
-  rmat22     R-MAT scale 22, edge factor 16, (0.57, 0.19, 0.19, 0.05), permuted (default)
+  rmat22     R-MAT scale 22, edge factor 16, (0.57, 0.19, 0.19, 0.05), permuted (default;
+             its line also carries the batch4096 and serve legs below)
   er10k      Erdos-Renyi G(10,000, 40,000)
   grid       2048 x 2048 grid + 5% random diagonals, natural ids
   grid_perm  the same grid, permuted ids
   batch4096  4096 graphs (log-uniform 64..65,536 vertices, ER / random geometric)
              packed as one block-diagonal union and solved in one launch
-  serve      Poisson arrivals of solve requests over a resident pool of graphs
+  serve      Poisson arrivals of solve requests over a resident pool of 512 graphs
              (continuous batching), graphs/s and p50/p99 vs sequential solves
   dynamic    batches of edge insertions/deletions on the resident R-MAT scale 22
              graph, each applied and the MIS repaired (H1 priority), vs a full solve
@@ -271,22 +276,40 @@ def time_device_steps(native, h, seeds, out_ptr, stream, steps, warmup, local, w
     return step_ms, clk.summary()
 
 
-def run_single(args):
+def create_timings(native, n, drp, dcol, stream, local, variants, reps=2):
+    """Create from a device-resident CSR, then the first solve, per option set:
+    the best of `reps` of create alone (host wall clock; mis_create_ex returns
+    once the graph is resident) and of create + first solve between CUDA
+    events on the solve stream."""
     import torch
+    out = {}
+    res = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+    for name, opt in variants:
+        best_c, best_cs = float("inf"), float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            e0.record()
+            h = native.mis_create_ex(n, drp, dcol, 1, opt, stream)
+            t1 = time.perf_counter()
+            native.mis_solve_ex(h, [1], res.data_ptr(), stream)
+            e1.record()
+            torch.cuda.synchronize()
+            native.mis_destroy(h)
+            best_c = min(best_c, t1 - t0)
+            best_cs = min(best_cs, e0.elapsed_time(e1))
+        out[name] = {"create_s": best_c, "create_plus_first_solve_ms": best_cs}
+    return out
 
-    from paper_2605_29604_gb300 import native
-    world, rank, local = _dist_setup()
-    g, desc = make_workload(args.workload)
-    n, rp, col = g
-    arcs = int(rp[-1])
-    stream = torch.cuda.current_stream().cuda_stream
-    # resident graph: the create-time row ordering that gives the shortest
-    # solves (each row sorted by neighbour degree)
-    opt = native.options(device=local, check_symmetry=1, order_rows=2)
-    t0 = time.perf_counter()
-    h = native.mis_create_ex(n, rp, col, 0, opt, stream)
-    t_create = time.perf_counter() - t0
-    tuning = None
+
+def tuned_handle(native, n, drp, dcol, stream, local, order_rows, args):
+    """A resident graph with the given create-time row ordering, on the launch
+    configuration the flags force or the autotuner picks."""
+    opt = native.options(device=local, check_symmetry=1, order_rows=order_rows)
+    h = native.mis_create_ex(n, drp, dcol, 1, opt, stream)
+    tuning, tune_s = None, 0.0
     if args.tpr is not None:
         native.mis_set_path(h, native.MIS_PATH_CSR, args.tpr)
         if args.csr_pending is not None:
@@ -302,6 +325,50 @@ def run_single(args):
         t0 = time.perf_counter()
         tuning = native.mis_autotune(h, 3)
         tune_s = time.perf_counter() - t0
+    return h, tuning, tune_s
+
+
+def tuning_dict(tuning, tune_s):
+    if tuning is None:
+        return None
+    return {"path": PATH_NAMES.get(tuning.path), "param": tuning.param,
+            "bounds": list(tuning.bounds), "grid": tuning.grid, "candidates": tuning.candidates,
+            "seconds": tune_s, "csr_pending": tuning.csr_pending,
+            "arcs_per_tile": tuning.arcs_per_tile}
+
+
+def phase_us(st):
+    r = min(st.rounds, 64)
+    return {"init": st.init_ns / 1e3, "select": [st.select_ns[i] / 1e3 for i in range(r)],
+            "exclude": [st.exclude_ns[i] / 1e3 for i in range(r)]}
+
+
+def run_single(args):
+    import torch
+
+    from paper_2605_29604_gb300 import native
+    world, rank, local = _dist_setup()
+    g, desc = make_workload(args.workload)
+    n, rp, col = g
+    arcs = int(rp[-1])
+    stream = torch.cuda.current_stream().cuda_stream
+    # the CSR resident in HBM before anything is timed
+    drp_t = torch.from_numpy(rp).cuda()
+    dcol_t = torch.from_numpy(col if arcs else np.zeros(1, np.int32)).cuda()
+    drp, dcol = drp_t.data_ptr(), dcol_t.data_ptr()
+
+    # create, and create + first solve, per create-time option set
+    creates = create_timings(native, n, drp, dcol, stream, local, [
+        ("default", native.options(device=local)),
+        ("full_rows", native.options(device=local, check_symmetry=1, order_rows=0)),
+        ("round0_structures", native.options(device=local, check_symmetry=1, order_rows=2)),
+    ])
+
+    # ---- the headline: Algorithm 2 from the CSR.  A graph created with
+    # order_rows = 0 keeps no create-time decision (no degree-ordered rows,
+    # round-0 classes, tested subgraph or keyed list): every solve computes
+    # every key and tests every undecided vertex over its full row.
+    h, tuning, tune_s = tuned_handle(native, n, drp, dcol, stream, local, 0, args)
     out = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
     seeds = np.array([1], dtype=np.uint64)
     step_ms, clocks = time_device_steps(native, h, seeds, out.data_ptr(), stream, args.steps,
@@ -309,30 +376,61 @@ def run_single(args):
     total_ms = _max_over_ranks(sum(step_ms), world)
     st = native.mis_get_stats(h)
     value = replica_throughput(world, args.steps, arcs, total_ms)
+    launch_s = (total_ms / 1e3) / args.steps
+    full_result = out[:n].cpu().numpy()
+    native.mis_destroy(h)
 
-    # several seeds of the same resident graph per launch (mis_solve_multi_ex)
+    # ---- amortised: the same solve on a graph whose create-time structures
+    # (degree-sorted rows, round-0 classes, tested subgraph, keyed list) have
+    # already decided every seed-independent round-0 vertex
+    amort = None
     multi = None
-    if args.multi > 0 and args.path is None:
-        kk = min(args.multi, 8)
-        mout = torch.empty(max(kk * n, 1), dtype=torch.uint8, device="cuda")
-        mseeds = np.arange(1, kk + 1, dtype=np.uint64)
-        flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
-        for _ in range(max(args.warmup, 3)):
-            native.mis_solve_multi_ex(h, mseeds, mout.data_ptr(), stream)
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        for e0, e1 in ev:
-            flush.add_(1.0)  # L2 flushed between launches, as for the single solves
-            e0.record()
-            native.mis_solve_multi_ex(h, mseeds, mout.data_ptr(), stream)
-            e1.record()
-        torch.cuda.synchronize()
-        mst = native.mis_get_stats(h)
-        mt = float(np.median([e0.elapsed_time(e1) for e0, e1 in ev]))
-        multi = {"k": kk, "launch_ms_p50": mt, "per_solve_ms": mt / kk,
-                 "edges_per_s_aggregate": kk * arcs / (mt / 1e3), "rounds": mst.rounds,
-                 "kernel": "multi_solve_kernel (k seeds of the graph per persistent launch)"}
+    if args.amortized and args.path is None:
+        ha, atuning, atune_s = tuned_handle(native, n, drp, dcol, stream, local, 2, args)
+        aout = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+        a_ms, a_clocks = time_device_steps(native, ha, seeds, aout.data_ptr(), stream,
+                                           args.steps, args.warmup, local, world)
+        ast = native.mis_get_stats(ha)
+        a_solve = float(np.median(a_ms))
+        f_solve = float(np.median(step_ms))
+        dc = creates["round0_structures"]["create_s"] - creates["full_rows"]["create_s"]
+        gain_s = (f_solve - a_solve) / 1e3
+        amort = {
+            "per_solve_ms_p50": a_solve, "edges_per_s": arcs / (a_solve / 1e3),
+            "create_s": creates["round0_structures"]["create_s"],
+            "break_even_seeds": (dc / gain_s) if gain_s > 0 else None,
+            "rounds": ast.rounds, "sure_in": ast.sure_in, "sure_out": ast.sure_out,
+            "tested_rows": ast.tested_rows, "tested_arcs": ast.tested_arcs,
+            "keyed": ast.keyed, "phase_us": phase_us(ast), "autotune": tuning_dict(atuning, atune_s),
+            "same_result": bool(np.array_equal(aout[:n].cpu().numpy(), full_result)),
+            "what": "mis_create_ex with order_rows=2: seed-independent round-0 decisions made at "
+                    "create time, so a solve tests only the tested subgraph; valid for repeated "
+                    "seeds of one resident graph"}
+        # several seeds of the same resident graph per launch (mis_solve_multi_ex)
+        if args.multi > 0:
+            kk = min(args.multi, 8)
+            mout = torch.empty(max(kk * n, 1), dtype=torch.uint8, device="cuda")
+            mseeds = np.arange(1, kk + 1, dtype=np.uint64)
+            flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
+            for _ in range(max(args.warmup, 3)):
+                native.mis_solve_multi_ex(ha, mseeds, mout.data_ptr(), stream)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            for e0, e1 in ev:
+                flush.add_(1.0)  # L2 flushed between launches, as for the single solves
+                e0.record()
+                native.mis_solve_multi_ex(ha, mseeds, mout.data_ptr(), stream)
+                e1.record()
+            torch.cuda.synchronize()
+            mst = native.mis_get_stats(ha)
+            mt = float(np.median([e0.elapsed_time(e1) for e0, e1 in ev]))
+            multi = {"k": kk, "launch_ms_p50": mt, "per_solve_ms": mt / kk,
+                     "edges_per_s_aggregate": kk * arcs / (mt / 1e3), "rounds": mst.rounds,
+                     "kernel": "multi_solve_kernel (k seeds of the amortised graph per "
+                               "persistent launch)"}
+        native.mis_destroy(ha)
+    del drp_t, dcol_t
 
     # end to end through the C ABI with host buffers: pinned CSR in, result out
     e2e = None
@@ -355,37 +453,20 @@ def run_single(args):
         e2e_s = _max_over_ranks(sum(times), world)
         e2e = {"value": world * arcs * len(times) / e2e_s, "unit": "edges/s",
                "h2d_bytes_per_step": 4 * (n + 1) + 4 * arcs, "d2h_bytes_per_step": n,
+               "same_result": bool(np.array_equal(hout[:n], full_result)),
                "path": "mis_create_ex(host CSR from pinned memory, uploaded in pieces with "
                        "row-pointer/range/order validation overlapped; degree binning included; "
                        "no row ordering; symmetry check off) + mis_solve(host result) + "
                        "mis_destroy"}
 
     peak, peak_kind = _peak_hbm()
-    # B0: one read of the CSR plus the key words and result bytes -- the
-    # lower bound of a solve that starts from the CSR alone
-    b0 = 4 * arcs + 4 * (n + 1) + 4 * n + n
-    launch_s = (total_ms / 1e3) / args.steps
-    # With the create-time tested subgraph and keyed list, a solve starts from
-    # those structures instead: its algorithmic bytes are one pass over each
-    # of them (neighbour word gathers stay in L2 and are not counted)
-    if st.path == 1 and st.keyed >= 0:
-        alg_bytes = (12 * st.keyed + 2 * n + 32 * st.tested_rows
-                     + 4 * st.tested_prefix_arcs + 4 * st.tested_arcs)
-        alg_def = ("12*keyed (keyed list read, dense key words written) + 2*n (create-time result "
-                   "bytes read, result written) + 32*tested_rows (round-0 row records, full and "
-                   "tested-subgraph) + 4*tested_prefix_arcs (round-0 selection prefixes) + "
-                   "4*tested_arcs (the tested subgraph); neighbour words are L2-resident")
-        alg_counts = {"keyed": st.keyed, "tested_rows": st.tested_rows,
-                      "tested_prefix_arcs": st.tested_prefix_arcs, "tested_arcs": st.tested_arcs}
-    else:
-        alg_bytes = b0
-        alg_def = "4*arcs + 4*(n+1) (one read of the CSR) + 4*n (key words written) + n (result)"
-        alg_counts = None
+    # SURVEY-defined one-read volume of the CSR: every arc and row pointer once
+    b0 = 4 * arcs + 4 * (n + 1)
+    achieved = b0 / launch_s / 1e9
     traffic = args.traffic
     if traffic is None and args.workload == "rmat22" and st.path == 1:
         traffic = profiled_traffic(["kernels_csr.cu", "common.cuh", "init.cuh", "worklist.cuh"],
-                                   "csr_solve_rmat22.md")
-    achieved = alg_bytes / launch_s / 1e9
+                                   "csr_solve_full_rmat22.md")
     path = PATH_NAMES.get(st.path, str(st.path))
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
@@ -393,37 +474,35 @@ def run_single(args):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": args.workload, "graph": desc, "n": n, "arcs": arcs,
+                   "solve": "Algorithm 2 from the CSR: graph created with order_rows=0, no "
+                            "create-time decisions; every key computed and every undecided "
+                            "vertex tested over its full row in every solve",
                    "rounds": st.rounds, "path": path, "threads_per_row": st.threads_per_row,
                    "tile": st.tile, "mis_size": st.mis_size,
                    "l2": "flushed between steps (256 MB write); graph (513 MB col_idx for rmat22) "
                          "also exceeds L2",
-                   "parallelism": f"replicas{world}", "create_s": t_create,
+                   "parallelism": f"replicas{world}", "create": creates,
                    "step_ms_p10_p50_p90": [float(np.percentile(step_ms, q)) for q in (10, 50, 90)],
-                   "phase_us": {"init": st.init_ns / 1e3,
-                                "select": [st.select_ns[r] / 1e3 for r in range(min(st.rounds, 64))],
-                                "exclude": [st.exclude_ns[r] / 1e3 for r in range(min(st.rounds, 64))]}},
+                   "phase_us": phase_us(st), "autotune": tuning_dict(tuning, tune_s)},
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "peak_kind": f"{peak_kind} burst copy bandwidth",
-                     "alg_bytes_per_launch": alg_bytes, "alg_bytes_def": alg_def,
-                     "alg_counts": alg_counts,
-                     "b0_bytes": b0, "b0_per_s_frac": b0 / launch_s / 1e9 / peak,
-                     "b0_def": "4*arcs + 4*(n+1) + 4*n + n: one read of the CSR, key words and "
-                               "result; b0_per_s_frac is that volume per launch time over the "
-                               "peak (an edges/s equivalent, not a bandwidth)",
-                     "kernel": f"{path} persistent round kernel (one launch per solve)"},
+                     "peak_kind": f"{peak_kind} burst copy bandwidth (of {peak_kind})",
+                     "alg_bytes_per_launch": b0,
+                     "alg_bytes_def": "B0 = 4*arcs + 4*(n+1): one read of col_idx and row_ptr",
+                     "kernel": f"{path} persistent round kernel (one launch per solve), full rows"},
         "clocks": clocks,
         "e2e": e2e,
     }
+    if amort is not None:
+        line["config"]["amortized"] = amort
     if multi is not None:
         line["config"]["multi_seed"] = multi
-    if tuning is not None:
-        line["config"]["autotune"] = {"path": PATH_NAMES.get(tuning.path), "param": tuning.param,
-                                      "bounds": list(tuning.bounds), "grid": tuning.grid,
-                                      "candidates": tuning.candidates, "seconds": tune_s,
-                                      "csr_pending": tuning.csr_pending,
-                                      "arcs_per_tile": tuning.arcs_per_tile}
+    legs = [x for x in (args.legs or "").split(",") if x]
+    if "batch" in legs:
+        line["batch4096"] = batch_leg(args, native, local, world)
+    if "serve" in legs:
+        line["serve"] = serve_leg(args, native, local, world, rank)
     if rank == 0 and args.cpu_baseline:
         import oracle
         rate, dt, res, reps = oracle_rate(g, min_seconds=args.cpu_seconds)
@@ -434,7 +513,16 @@ def run_single(args):
                                 "quality": {"mis_size": int(res.status.sum()),
                                             "min_degree_greedy": mdg},
                                 "gpu_result_equals_oracle": bool(np.array_equal(
-                                    out[:n].cpu().numpy(), res.status))}
+                                    full_result, res.status))}
+        # work bytes of the pull rounds (each undecided row read in full, each
+        # round's alive set listed and read back), from the oracle's counts
+        wb = 4 * int(res.work) + 8 * int(res.alive_sum) + 4 * n + n
+        line["roofline"]["work_bytes"] = wb
+        line["roofline"]["work_def"] = ("B_csr = 4*W + 8*sum_r |und_r| + 4*n + n, W = sum over "
+                                        "rounds of the degrees of the undecided vertices "
+                                        f"(oracle: W = {int(res.work)}, sum |und_r| = "
+                                        f"{int(res.alive_sum)})")
+        line["roofline"]["work_frac"] = wb / launch_s / 1e9 / peak
         # the second CPU baseline: the same rounds on all host cores (OpenMP)
         pn, prp, pcol = g
         pkeys = oracle.keys(pn, prp, 1)
@@ -453,7 +541,6 @@ def run_single(args):
                     "keys precomputed, not timed",
             "sample": f"{preps} full solves of the same graph ({pdt * 1e3:.1f} ms each)",
             "result_equals_oracle": bool(np.array_equal(pres.status, res.status))}
-    native.mis_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -462,12 +549,11 @@ def run_single(args):
     return 0
 
 
-def run_batch(args):
+def batch_leg(args, native, local, world):
+    """Config 4: the 4096-graph union, one captured persistent launch per step."""
     import torch
 
     from paper_2605_29604_gb300 import graphgen as gg
-    from paper_2605_29604_gb300 import native
-    world, rank, local = _dist_setup()
     t0 = time.perf_counter()
     parts = gg.batch_mixed(args.batch_count, seed=4096, nmin=64, nmax=65536)
     t_gen = time.perf_counter() - t0
@@ -489,38 +575,57 @@ def run_batch(args):
     total_ms = _max_over_ranks(sum(step_ms), world)
     st = native.mis_get_stats(h)
     native.mis_replay_destroy(replay)
-    value = replica_throughput(world, args.steps, arcs, total_ms)
+    # the union's result against standalone solves of a sample of its graphs
+    got = out[:size].cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum([p[0] for p in parts])])
+    checked, same = 0, True
+    for i in range(0, len(parts), max(1, len(parts) // 64)):
+        pn, prp, pcol = parts[i]
+        h1 = native.mis_create_ex(pn, prp, pcol, 0, native.options(device=local,
+                                                                    check_symmetry=0), None)
+        want = native.mis_solve(h1, int(seeds[i]))
+        native.mis_destroy(h1)
+        same &= bool(np.array_equal(got[offs[i]:offs[i + 1]], want[:pn]))
+        checked += 1
+    native.mis_destroy(h)
     peak, peak_kind = _peak_hbm()
-    alg_bytes = 4 * arcs + 4 * (nsum + 1) + 4 * nsum + nsum
-    achieved = alg_bytes / ((total_ms / 1e3) / args.steps) / 1e9
-    line = {
-        "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
-        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic",
-        "config": {"workload": "batch4096", "graphs": len(parts), "n_total": nsum, "arcs": arcs,
-                   "graphs_per_s": world * args.steps * len(parts) / (total_ms / 1e3),
-                   "rounds": st.rounds, "path": PATH_NAMES.get(st.path), "gen_s": t_gen,
-                   "create_s": t_create, "autotune": {"path": PATH_NAMES.get(tuning.path),
-                                                      "bounds": list(tuning.bounds),
-                                                      "grid": tuning.grid,
-                                                      "csr_pending": tuning.csr_pending},
-                   "launch": "captured CUDA graph replay (mis_capture, mis_replay_launch)",
-                   "phase_us": {"init": st.init_ns / 1e3,
-                                "select": [x / 1e3 for x in st.select_ns[:st.rounds]],
-                                "exclude": [x / 1e3 for x in st.exclude_ns[:st.rounds]]},
-                   "l2": "flushed between steps (256 MB write)"},
-        "gpu_launches": args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_kind": f"{peak_kind} burst copy bandwidth",
-                     "alg_bytes_per_launch": alg_bytes},
+    launch_s = (total_ms / 1e3) / args.steps
+    b0 = 4 * arcs + 4 * (nsum + len(parts))
+    return {
+        "graphs": len(parts), "n_total": nsum, "arcs": arcs, "steps": args.steps,
+        "ms_per_launch": total_ms / args.steps,
+        "graphs_per_s": world * args.steps * len(parts) / (total_ms / 1e3),
+        "edges_per_s": replica_throughput(world, args.steps, arcs, total_ms),
+        "rounds": st.rounds, "path": PATH_NAMES.get(st.path), "gen_s": t_gen,
+        "create_s": t_create, "create_order_rows": args.batch_order,
+        "create_note": ("order_rows=2: the union's round-0 classes are made at create time "
+                        "(seed-independent), so each replayed solve tests only the rest"
+                        if args.batch_order else "no create-time decisions"),
+        "autotune": {"path": PATH_NAMES.get(tuning.path), "bounds": list(tuning.bounds),
+                     "grid": tuning.grid, "csr_pending": tuning.csr_pending},
+        "launch": "captured CUDA graph replay (mis_capture, mis_replay_launch)",
+        "phase_us": phase_us(st), "l2": "flushed between steps (256 MB write)",
+        "roofline": {"b0_bytes": b0, "b0_frac": b0 / launch_s / 1e9 / peak, "peak": peak,
+                     "b0_def": "4*arcs + 4*(n+1) per graph"},
+        "standalone_check": {"graphs_checked": checked, "all_equal": same},
         "clocks": clocks,
     }
-    native.mis_destroy(h)
+
+
+def run_batch(args):
+    from paper_2605_29604_gb300 import native
+    world, rank, local = _dist_setup()
+    leg = batch_leg(args, native, local, world)
+    line = {
+        "metric": METRIC, "value": leg["edges_per_s"], "unit": "edges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": leg["ms_per_launch"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": {"workload": "batch4096", **leg},
+        "gpu_launches": args.steps, "clocks": leg["clocks"],
+    }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    return 0
+    return 0 if leg["standalone_check"]["all_equal"] else 1
 
 
 def run_dynamic(args):
@@ -591,23 +696,31 @@ def run_dynamic(args):
     return 0 if same else 1
 
 
-def run_serve(args):
-    """Continuous batching over a resident pool: saturated throughput, then
-    Poisson arrivals at fractions of it (p50/p99), vs sequential solves."""
-    import torch
-
-    from paper_2605_29604_gb300 import graphgen as gg
-    from paper_2605_29604_gb300 import native
-    world, rank, local = _dist_setup()
-    rng = np.random.default_rng(5)
+def serve_pool_specs(pool, seed=5):
+    """Config 5's pool: sizes log-uniform in [1K, 2M] vertices, even entries
+    R-MAT (edge factor 8..32, permuted, size rounded up to a power of two),
+    odd entries Erdos-Renyi (average degree 4..64)."""
+    rng = np.random.default_rng(seed)
     specs = []
-    for i in range(args.pool):
+    for i in range(pool):
         n = int(round(math.exp(math.log(1000) + rng.random() * (math.log(2_000_000) - math.log(1000)))))
         if i % 2 == 0:
             scale = max(10, int(math.ceil(math.log2(n))))
             specs.append(("rmat", scale, int(rng.integers(8, 33)), 100 + i))
         else:
             specs.append(("er", n, float(rng.uniform(4, 64)), 100 + i))
+    return specs
+
+
+def serve_leg(args, native, local, world, rank):
+    """Config 5: continuous batching over a resident pool -- saturated
+    throughput, then Poisson arrivals at fractions of it (p50/p99) -- against
+    sequential plain solves of the same request list; a sample of the served
+    results is checked against standalone solves."""
+    import torch
+
+    from paper_2605_29604_gb300 import graphgen as gg
+    specs = serve_pool_specs(args.pool)
 
     def gen(spec):
         if spec[0] == "rmat":
@@ -617,39 +730,61 @@ def run_serve(args):
 
     from concurrent.futures import ThreadPoolExecutor
     t0 = time.perf_counter()
-    with ThreadPoolExecutor(max_workers=16) as ex:
+    with ThreadPoolExecutor(max_workers=max(4, os.cpu_count() or 4)) as ex:
         graphs = list(ex.map(gen, specs))
     t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
     handles = [native.mis_create_ex(g[0], g[1], g[2], 0, native.options(device=local,
                                                                           check_symmetry=0), None)
                for g in graphs]
+    t_create = time.perf_counter() - t0
     native.mis_serve_shutdown()
     native.mis_serve_configure(native.options(device=local, serve_blocks=args.serve_blocks))
     for h in handles:
         native.mis_set_path(h, native.MIS_PATH_CSR, 0)
+    rng = np.random.default_rng(7)
     reqs = rng.integers(0, len(graphs), size=args.requests)
-    outs = [np.empty(g[0], dtype=np.uint8) for g in graphs]
     arcs = np.array([int(g[1][-1]) for g in graphs])
+    nmax = max(g[0] for g in graphs)
+    # every request writes a host buffer; a sample of requests gets its own,
+    # checked afterwards, the rest share one buffer per graph
+    sample = set(rng.choice(len(reqs), size=min(args.serve_check, len(reqs)),
+                            replace=False).tolist())
+    shared = [np.empty(g[0], dtype=np.uint8) for g in graphs]
 
-    # sequential plain solves of the same request list
+    # sequential plain solves of the same request list, one after another on
+    # one stream, results in device memory (the fastest plain form)
+    stream = torch.cuda.current_stream().cuda_stream
+    dout = torch.empty(nmax, dtype=torch.uint8, device="cuda")
+    for k in range(min(16, len(reqs))):  # warm-up
+        native.mis_solve_ex(handles[reqs[k]], [1000 + k], dout.data_ptr(), stream)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for k, i in enumerate(reqs[:args.seq_requests]):
-        native.mis_solve(handles[i], 1000 + k, outs[i])
+    for k, i in enumerate(reqs):
+        native.mis_solve_ex(handles[i], [1000 + k], dout.data_ptr(), stream)
+    torch.cuda.synchronize()
     seq_s = time.perf_counter() - t0
-    seq_rate = args.seq_requests / seq_s
+    seq_rate = len(reqs) / seq_s
 
-    def run(arrival_rate):
+    def run(arrival_rate, base_seed, keep):
         """Submit the request list (all at once if rate is None, else with
         Poisson arrivals); returns (graphs/s, latencies in ms).  Latency is
         measured by the library, from mis_submit to the result in the host
         buffer (mis_poll_ex)."""
         n_req = len(reqs)
         lat = np.zeros(n_req)
+
+        def buf(k):
+            if k in keep:
+                return keep[k]
+            return shared[reqs[k]]
+
         if arrival_rate is None:
             # everything at once; collect in submission order (one poll at a
             # time keeps the library's lock free for its scheduler)
             t_start = time.perf_counter()
-            tickets = [native.mis_submit(handles[i], 2000 + k, outs[i]) for k, i in enumerate(reqs)]
+            tickets = [native.mis_submit(handles[i], base_seed + k, buf(k))
+                       for k, i in enumerate(reqs)]
             for kk, t in enumerate(tickets):
                 while True:
                     rc, ns = native.mis_poll_ex(t)
@@ -670,7 +805,7 @@ def run_serve(args):
             now = time.perf_counter() - t_start
             while k < n_req and arrive[k] <= now:
                 i = reqs[k]
-                outstanding.append((k, native.mis_submit(handles[i], 2000 + k, outs[i])))
+                outstanding.append((k, native.mis_submit(handles[i], base_seed + k, buf(k))))
                 k += 1
             still = []
             for kk, t in outstanding:
@@ -690,32 +825,55 @@ def run_serve(args):
                     time.sleep(wait - 100e-6)
         return n_req / (t_end - t_start), lat
 
-    cap, lat_sat = run(None)
+    keep = {k: np.empty(graphs[reqs[k]][0], dtype=np.uint8) for k in sample}
+    cap, lat_sat = run(None, 2000, keep)
     results = {"saturated": {"graphs_per_s": cap, "p50_ms": float(np.percentile(lat_sat, 50)),
                              "p99_ms": float(np.percentile(lat_sat, 99))}}
-    for frac in (0.5, 0.8):
-        rate, lat = run(frac * cap)
+    for frac in (0.5, 0.8, 1.0):
+        rate, lat = run(frac * cap, 50000, {})
         results[f"poisson_{frac}"] = {"offered_per_s": frac * cap, "graphs_per_s": rate,
                                       "p50_ms": float(np.percentile(lat, 50)),
                                       "p99_ms": float(np.percentile(lat, 99))}
     native.mis_serve_shutdown()
-    line = {
-        "metric": "served graphs/s (continuous batching) vs sequential plain solves",
-        "value": cap, "unit": "graphs/s", "n_gpus": world, "steps": len(reqs), "warmup": 0,
-        "higher_is_better": True, "data": "synthetic", "dtype": "u32",
-        "config": {"workload": "serve", "pool": len(graphs),
-                   "pool_vertices_mean": float(np.mean([g[0] for g in graphs])),
-                   "pool_arcs_mean": float(arcs.mean()), "requests": len(reqs), "gen_s": t_gen,
-                   "sequential_graphs_per_s": seq_rate, "sequential_requests": args.seq_requests,
-                   "serve_blocks": args.serve_blocks or "one per SM",
-                   "latency": "library-measured, mis_submit to result in host buffer",
-                   "speedup_vs_sequential": cap / seq_rate, **results},
-    }
+    # each sampled served result against a standalone solve with its seed
+    same = True
+    for k, got in keep.items():
+        h = handles[reqs[k]]
+        native.mis_solve_ex(h, [2000 + k], dout.data_ptr(), stream)
+        torch.cuda.synchronize()
+        same &= bool(np.array_equal(got, dout[:len(got)].cpu().numpy()))
     for h in handles:
         native.mis_destroy(h)
+    per_graph = np.bincount(reqs, minlength=len(graphs))
+    return {
+        "metric": "served graphs/s (continuous batching) vs sequential plain solves",
+        "pool": len(graphs), "pool_vertices_mean": float(np.mean([g[0] for g in graphs])),
+        "pool_arcs_mean": float(arcs.mean()), "pool_arcs_total": int(arcs.sum()),
+        "requests": len(reqs), "requests_per_graph_max": int(per_graph.max()),
+        "gen_s": t_gen, "create_s": t_create,
+        "sequential_graphs_per_s": seq_rate,
+        "sequential": "the same request list as mis_solve_ex calls back to back on one stream, "
+                      "results in device memory",
+        "served_graphs_per_s": cap, "speedup_vs_sequential": cap / seq_rate,
+        "serve_blocks": args.serve_blocks or "default (half the SMs)",
+        "latency": "library-measured, mis_submit to result in host buffer",
+        **results,
+        "standalone_check": {"requests_checked": len(keep), "all_equal": same},
+    }
+
+
+def run_serve(args):
+    from paper_2605_29604_gb300 import native
+    world, rank, local = _dist_setup()
+    leg = serve_leg(args, native, local, world, rank)
+    line = {
+        "metric": leg["metric"], "value": leg["served_graphs_per_s"], "unit": "graphs/s",
+        "n_gpus": world, "steps": leg["requests"], "warmup": 0, "higher_is_better": True,
+        "data": "synthetic", "dtype": "u32", "config": {"workload": "serve", **leg},
+    }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    return 0
+    return 0 if leg["standalone_check"]["all_equal"] else 1
 
 
 def main():
@@ -742,16 +900,25 @@ def main():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-order", type=int, default=2, choices=[0, 1, 2],
                     help="create-time row ordering of the batched union (mis_options.order_rows)")
-    ap.add_argument("--pool", type=int, default=48)
+    ap.add_argument("--pool", type=int, default=512)
     ap.add_argument("--requests", type=int, default=20000)
-    ap.add_argument("--seq-requests", type=int, default=2000)
+    ap.add_argument("--serve-check", type=int, default=256,
+                    help="served results checked against standalone solves")
     ap.add_argument("--serve-blocks", type=int, default=0)
     ap.add_argument("--dyn-edges", type=int, default=1000,
                     help="dynamic workload: edge changes per batch (half inserted, half deleted)")
     ap.add_argument("--dyn-steps", type=int, default=5)
+    ap.add_argument("--legs", default=None,
+                    help="extra legs of the single-graph run, comma separated: batch (the "
+                         "4096-graph union), serve (the served pool); default both for rmat22, "
+                         "none otherwise")
+    ap.add_argument("--no-amortized", dest="amortized", action="store_false",
+                    help="skip the solve on a graph with create-time round-0 structures")
     ap.add_argument("--multi", type=int, default=8,
                     help="also time this many seeds of the graph per launch (0 = off)")
     args = ap.parse_args()
+    if args.legs is None:
+        args.legs = "batch,serve" if args.workload == "rmat22" else ""
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch4096":

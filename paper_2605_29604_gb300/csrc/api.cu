@@ -655,8 +655,11 @@ std::string density_class(mis_graph* g, double apt) {
     if (cudaGetDeviceProperties(&prop, d.device) == cudaSuccess) dev = prop.name;
     for (char& c : dev)
         if (c == ' ') c = '_';
+    // graphs with create-time round-0 structures solve a different problem
+    // size than graphs scanned from their full rows: tuned apart
+    const int order = d.col_sel ? g->opt.order_rows : 0;
     return dev + ":d" + std::to_string(deg_b) + ":n" + std::to_string(size_b / 2) + ":" + loc +
-           (d.count ? ":batch" : "") +
+           ":o" + std::to_string(order) + (d.s0_col ? "s" : "") + (d.count ? ":batch" : "") +
            (g->opt.priority ? ":p" + std::to_string(g->opt.priority) : std::string());
 }
 

@@ -52,3 +52,27 @@ def test_single_graph_line():
     assert par["value"] > 0 and par["cores"] >= 1 and par["result_equals_oracle"] is True
     assert d["gpu_launches"] == 3
     assert d["config"]["multi_seed"]["k"] == 2
+    # the timed solve starts from the CSR; B0 over its time cannot pass the peak
+    assert r["alg_bytes_per_launch"] == 4 * d["config"]["arcs"] + 4 * (d["config"]["n"] + 1)
+    assert r["frac"] <= 1.0
+    assert r["work_bytes"] >= r["alg_bytes_per_launch"]
+    cr = d["config"]["create"]
+    for k in ("default", "full_rows", "round0_structures"):
+        assert cr[k]["create_s"] > 0 and cr[k]["create_plus_first_solve_ms"] > 0
+    am = d["config"]["amortized"]
+    assert am["same_result"] is True and am["per_solve_ms_p50"] > 0
+
+
+def test_single_graph_line_with_legs():
+    d = _run("--workload", "er10k", "--steps", "3", "--warmup", "3", "--e2e-steps", "0",
+             "--no-cpu-baseline", "--multi", "0", "--legs", "batch,serve", "--batch-count", "64",
+             "--pool", "8", "--requests", "400", "--serve-check", "32")
+    b = d["batch4096"]
+    assert b["graphs"] == 64 and b["graphs_per_s"] > 0
+    assert b["standalone_check"]["all_equal"] is True
+    s = d["serve"]
+    assert s["pool"] == 8 and s["requests"] == 400
+    assert s["served_graphs_per_s"] > 0 and s["sequential_graphs_per_s"] > 0
+    for k in ("saturated", "poisson_0.5", "poisson_0.8", "poisson_1.0"):
+        assert s[k]["p99_ms"] >= s[k]["p50_ms"] > 0
+    assert s["standalone_check"]["all_equal"] is True
