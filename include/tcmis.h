@@ -283,6 +283,15 @@ int mis_set_csr_bins(mis_graph *g, const int32_t *bounds);
  * values, MIS_EBUSY while served requests on `g` are in flight. */
 int mis_set_csr_pending(mis_graph *g, int32_t pending);
 
+/* CSR path, graphs created without the round-0 classes (order_rows = 0 or a
+ * priority other than Eq. 1): how round 0 (Algorithm 2's first iteration,
+ * every vertex alive) reaches the rows of degree bin 0.  on = 1 (default):
+ * the warps split the vertex range and read row_ptr in sequence, one lane per
+ * light row; on = 0: from the bin's create-time list of 16-byte row records.
+ * Same result either way (chosen by mis_autotune).  MIS_EINVAL for other
+ * values, MIS_EBUSY while served requests on `g` are in flight. */
+int mis_set_csr_range0(mis_graph *g, int32_t on);
+
 /* The autotuner's choice for a graph. */
 typedef struct mis_tuning {
     int32_t path;        /* MIS_PATH_CSR, MIS_PATH_TILE or MIS_PATH_TILE_TC */
@@ -293,6 +302,8 @@ typedef struct mis_tuning {
     float ms;            /* median solve time of the choice, ms */
     int32_t csr_pending; /* CSR: the mis_set_csr_pending mode of the choice */
     double arcs_per_tile;/* sampled arcs per non-empty 8 x 8 tile */
+    int32_t csr_range0;  /* CSR: the mis_set_csr_range0 mode of the choice (0 when
+                            the graph has round-0 classes) */
 } mis_tuning;
 
 /*

@@ -385,6 +385,7 @@ SolveArgs make_args(mis_graph* g, Workspace& w) {
     a.n_sure_in = d.n_sure_in;
     a.n_sure_out = d.n_sure_out;
     a.pending = g->csr_pending;
+    a.range0_max = (g->csr_range0 && !d.r0class && d.thr[0] >= 1) ? d.thr[0] : 0;
     a.priority = g->opt.priority;
     a.ctl = w.ctl;
     a.times = w.times;
@@ -534,6 +535,7 @@ struct TuneChoice {
     int32_t grid = 0;    // CSR grid request (0 = default)
     float ms = 0.f;
     int32_t pending = 0; // CSR: Phase 1 lists its non-candidates for Phase 2
+    int32_t range0 = 1;  // CSR: round 0 takes bin 0 by vertex ranges
 };
 
 std::mutex g_tune_mu;
@@ -554,6 +556,7 @@ void tune_load_locked() {
         if (ss >> key >> c.path >> c.param >> c.bounds[0] >> c.bounds[1] >> c.bounds[2] >>
             c.bounds[3] >> c.grid >> c.ms) {
             if (!(ss >> c.pending)) c.pending = 0;  // lines written before the field
+            if (!(ss >> c.range0)) c.range0 = 1;
             g_tune_cache[key] = c;
         }
     }
@@ -567,7 +570,7 @@ void tune_save_locked() {
         const TuneChoice& c = kv.second;
         out << kv.first << ' ' << c.path << ' ' << c.param << ' ' << c.bounds[0] << ' '
             << c.bounds[1] << ' ' << c.bounds[2] << ' ' << c.bounds[3] << ' ' << c.grid << ' '
-            << c.ms << ' ' << c.pending << '\n';
+            << c.ms << ' ' << c.pending << ' ' << c.range0 << '\n';
     }
 }
 
@@ -678,6 +681,7 @@ int apply_choice(mis_graph* g, const TuneChoice& c) {
     }
     g->tpr = c.param;
     g->csr_pending = c.pending;
+    g->csr_range0 = c.range0;
     if (g->last_stream) cudaStreamSynchronize(g->last_stream);
     const int rc = rebin(g, thr, g->own_stream);
     if (rc != MIS_OK) return rc;
@@ -743,6 +747,17 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
         bins(INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, maxg * 2 / 3);
     }
     bins(-1, 65536, 65536, 65536, 0);                                     // four lanes per row
+    // without round-0 classes, round 0 can take bin 0 by vertex ranges (the
+    // candidates above) or from its list
+    if (!g->d.r0class) {
+        const size_t k0 = cands.size();
+        bins(8, 4096, 4096, 65536, 0);
+        bins(4, 64, 1024, 65536, 0);
+        bins(16, 256, 4096, 65536, 0);
+        bins(32, 4096, 4096, 65536, 0);
+        for (size_t k = k0; k < cands.size(); ++k) cands[k].range0 = 0;
+        if (maxg >= 3) bins(8, 4096, 4096, 65536, maxg * 2 / 3);
+    }
     if (g->d.n <= 65536) bins(8, 4096, 4096, 65536, std::max(1, (g->d.n + 1023) / 1024));
     {
         TuneChoice t;
@@ -784,6 +799,7 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
         out->grid = g->path == MIS_PATH_CSR ? g->grid : g->tile_grid;
         out->ms = best.ms;
         out->csr_pending = best.path == MIS_PATH_CSR ? best.pending : 0;
+        out->csr_range0 = (best.path == MIS_PATH_CSR && !g->d.r0class) ? best.range0 : 0;
         out->arcs_per_tile = apt;
         out->candidates = (int32_t)cands.size();
     }
@@ -1147,6 +1163,16 @@ int mis_set_csr_pending(mis_graph* g, int32_t pending) {
     std::lock_guard<std::mutex> lk(g->mu);
     if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
     g->csr_pending = pending;
+    return MIS_OK;
+}
+
+int mis_set_csr_range0(mis_graph* g, int32_t on) {
+    clear_error();
+    if (!g) return set_error(MIS_EINVAL, "null graph");
+    if (on != 0 && on != 1) return set_error(MIS_EINVAL, "range0 must be 0 or 1");
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
+    g->csr_range0 = on;
     return MIS_OK;
 }
 

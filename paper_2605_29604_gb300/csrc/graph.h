@@ -111,6 +111,8 @@ struct mis_graph {
     int32_t tile_grid = 0;        // persistent grid size (tile kernels)
     int32_t tile_slots = 8;       // tile kernels: lanes (tiles in flight) per row block
     int32_t csr_pending = 0;      // CSR kernel: Phase 1 lists non-candidates for Phase 2
+    int32_t csr_range0 = 1;       // CSR kernel: round 0 tests bin 0 by vertex ranges
+                                  // (graphs without round-0 classes only)
     cudaStream_t own_stream = nullptr;
     cudaStream_t last_stream = nullptr;
     int32_t last_path = 0;

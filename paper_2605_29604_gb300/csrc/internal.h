@@ -77,6 +77,9 @@ struct SolveArgs {
     int32_t n_sure_in = 0;
     int32_t n_sure_out = 0;
     int32_t priority = 0;             // priority heuristic (kPrioEq1, kPrioHash, kPrioEq1Q8)
+    // > 0: round 0 tests bin 0 (degree 1 .. range0_max) by vertex ranges over
+    // row_ptr instead of its order0 list (graphs without round-0 classes)
+    int32_t range0_max = 0;
     int32_t pending = 0;              // 1: Phase 1 lists its non-candidates for Phase 2
                                       // (in wlp); 0: Phase 2 triages W_r itself
     // tile-CSR (used by the tile kernels only)

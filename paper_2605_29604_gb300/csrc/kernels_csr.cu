@@ -361,6 +361,121 @@ __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __re
     flush_stage(wbuf, fill, list, next, dst);
 }
 
+// Round 0 of bin 0 without its list (a.range0_max > 0; graphs with no
+// create-time round-0 classes): the warps split the vertex range [0, n) into
+// contiguous slices and each lane takes kRowsPerLane vertices of a 64-vertex
+// pass, reading row_ptr in sequence instead of 16-byte row records.  Lanes
+// whose vertex is isolated or heavier than the bin (degree > range0_max) sit
+// the pass out; those rows are in the lists of bins 1..4.
+__device__ __forceinline__ void range0_slice(const SolveArgs& a, const RoundSched& ws, int& v0,
+                                             int& v1) {
+    constexpr int kPass = 32 * kRowsPerLane;
+    const int nw = ws.nwarps();
+    int per = (int)(((long long)a.n + nw - 1) / nw);
+    per = (int)(((long long)per + kPass - 1) / kPass * kPass);
+    const long long b = (long long)ws.gw * per;
+    v0 = (int)min(b, (long long)a.n);
+    v1 = (int)min(b + per, (long long)a.n);
+}
+
+// The record {v, row begin, prefix end, row end} of vertex v < n, and
+// whether v is a light row (1 <= degree <= range0_max).  Graphs without
+// round-0 classes have no selection prefixes either (both come with Eq. 1's
+// degree-ordered rows), so the prefix is the whole row.
+__device__ __forceinline__ bool range0_record(const SolveArgs& a, int v, int4& rec) {
+    const int b = __ldg(a.rp + v);
+    const int e = __ldg(a.rp + v + 1);
+    rec = make_int4(v, b, e, e);
+    return (unsigned)(e - b - 1) < (unsigned)a.range0_max;
+}
+
+// Appends the staged vertices' records to `dst` with one atomic on `next`.
+__device__ __forceinline__ void flush_stage_v(const SolveArgs& a, const int32_t* wbuf, int fill,
+                                              int* next, int4* __restrict__ dst) {
+    __syncwarp();
+    if (fill) {
+        const unsigned lane = lane_id();
+        int o = 0;
+        if (lane == 0) o = atomicAdd(next, fill);
+        o = __shfl_sync(0xFFFFFFFFu, o, 0);
+        for (int i = (int)lane; i < fill; i += 32) {
+            int4 rec;
+            range0_record(a, wbuf[i], rec);
+            dst[o + i] = rec;
+        }
+    }
+    __syncwarp();
+}
+
+// Phase 1 of round 0, bin 0, by vertex ranges.  Candidates are marked in the
+// MIS; the non-candidates are found again by Phase 2's range pass (no
+// pending list).
+__device__ __forceinline__ void select_range0(const SolveArgs& a, const RoundSched& ws) {
+    constexpr int R = kRowsPerLane;
+    const unsigned lane = lane_id();
+    int v0, v1;
+    range0_slice(a, ws, v0, v1);
+    for (int base = v0; base < v1; base += 32 * R) {
+        int4 rec[R];
+        bool valid[R], blocked[R];
+        uint32_t wv[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const unsigned v = (unsigned)base + lane + 32u * i;  // no overflow: base < 2^31
+            valid[i] = v < (unsigned)v1 && range0_record(a, (int)v, rec[i]);
+            if (!valid[i]) rec[i] = make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) wv[i] = valid[i] ? ld_word_l1(a.word + rec[i].x) : 0u;
+        lane_rows<R, true>(a.col_sel, LiveWords{a.word}, rec, valid, wv, blocked);
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+            if (valid[i] && !blocked[i]) {
+                a.word[rec[i].x] = wv[i] | kWordInSet;
+                mark_selected(a, rec[i].x);
+            }
+    }
+}
+
+// Phase 2+3 of round 0, bin 0, by vertex ranges: the light rows still
+// undecided after Phase 1 are tested for a selected neighbour; the others
+// are staged and appended to bin 0 of W_1 as records.
+__device__ __forceinline__ void exclude_range0(const SolveArgs& a, const RoundSched& ws,
+                                               int* next, int4* __restrict__ dst,
+                                               int32_t* wbuf) {
+    constexpr int R = kRowsPerLane;
+    constexpr int kPass = 32 * R;
+    const unsigned lane = lane_id();
+    int v0, v1;
+    range0_slice(a, ws, v0, v1);
+    const uint32_t unused[R] = {};
+    int fill = 0;
+    for (int base = v0; base < v1; base += kPass) {
+        int4 rec[R];
+        bool valid[R], excl[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const unsigned v = (unsigned)base + lane + 32u * i;  // no overflow: base < 2^31
+            valid[i] = v < (unsigned)v1 && range0_record(a, (int)v, rec[i]);
+            if (!valid[i]) rec[i] = make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i)  // undecided non-candidates only
+            valid[i] = valid[i] && (ld_word_l1(a.word + rec[i].x) >> 29) == 1u;
+        lane_rows<R, false>(exclude_col(a), LiveWords{a.word}, rec, valid, unused, excl);
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (valid[i] && excl[i]) a.word[rec[i].x] = kWordOut;
+            fill = stage_keep(valid[i] && !excl[i], rec[i].x, wbuf, fill);
+        }
+        if (fill > kStageMax - kPass) {
+            flush_stage_v(a, wbuf, fill, next, dst);
+            fill = 0;
+        }
+    }
+    flush_stage_v(a, wbuf, fill, next, dst);
+}
+
 // Bin 4 (hubs): the whole block scans one row at a time.  kSelect: Phase 1
 // (kPending: non-candidates appended to the pending list), else Phase 2+3
 // (survivors appended to W_{r+1}); hub rows are few, so entries are appended
@@ -477,7 +592,7 @@ __device__ __forceinline__ void exclude_bin_at(const SolveArgs& a, const int4* l
 
 // Phase 1 over the bins of one worklist: hubs first, then the bins of longer
 // rows.
-template <bool kPending>
+template <bool kPending, bool kRange0>
 __device__ __forceinline__ void select_phase(const SolveArgs& a, const int4* src, const int* cnt,
                                              bool late, RoundSched& ws, unsigned* grab,
                                              int* pnext, int4* pend, int32_t* wbuf) {
@@ -489,12 +604,15 @@ __device__ __forceinline__ void select_phase(const SolveArgs& a, const int4* src
                                          pend + off[2], wbuf);
     select_bin_at<4, kChunk1, kPending>(a, src + off[1], cnt[1], late, ws, &grab[1], &pnext[1],
                                         pend + off[1], wbuf);
-    select_bin_at<1, kChunk0, kPending>(a, src + off[0], cnt[0], late, ws, &grab[0], &pnext[0],
-                                        pend + off[0], wbuf);
+    if (kRange0 && !late)
+        select_range0(a, ws);
+    else
+        select_bin_at<1, kChunk0, kPending>(a, src + off[0], cnt[0], late, ws, &grab[0],
+                                            &pnext[0], pend + off[0], wbuf);
 }
 
 // Phase 2+3 over the bins of `list` (W_r, or P_r when kPending).
-template <bool kPending>
+template <bool kPending, bool kRange0>
 __device__ __forceinline__ void exclude_phase(const SolveArgs& a, const int4* list,
                                               const int* cnt, bool late, RoundSched& ws,
                                               unsigned* grab, int* next, int4* dst,
@@ -507,8 +625,11 @@ __device__ __forceinline__ void exclude_phase(const SolveArgs& a, const int4* li
                                           &next[2], dst + off[2], wbuf, wscan);
     exclude_bin_at<4, kChunk1, kPending>(a, list + off[1], cnt[1], late, ws, &grab[1],
                                          &next[1], dst + off[1], wbuf, wscan);
-    exclude_bin_at<1, kChunk0, kPending>(a, list + off[0], cnt[0], late, ws, &grab[0],
-                                         &next[0], dst + off[0], wbuf, wscan);
+    if (kRange0 && !late)
+        exclude_range0(a, ws, &next[0], dst + off[0], wbuf);
+    else
+        exclude_bin_at<1, kChunk0, kPending>(a, list + off[0], cnt[0], late, ws, &grab[0],
+                                             &next[0], dst + off[0], wbuf, wscan);
 }
 
 // Initialisation with the keyed list (a.out0 set): the result starts as the
@@ -614,7 +735,9 @@ __device__ __forceinline__ bool round_barrier(const SolveArgs& a, Book book, Aft
     });
 }
 
-template <bool kPending>
+// kRange0: round 0 takes bin 0 by vertex ranges (a.range0_max > 0); a
+// separate instance, so that the list form keeps its register budget.
+template <bool kPending, bool kRange0>
 __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     csr_solve_kernel(const SolveArgs a) {
     __shared__ int32_t s_stage[kWarps][kStageMax];
@@ -683,7 +806,7 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
         const int rr = r;
 
         // ---- Phase 1: selection test
-        select_phase<kPending>(a, src, s_cnt, r > 0, ws, ctl->grab[(2 * r) & 3], pnext, a.wlp,
+        select_phase<kPending, kRange0>(a, src, s_cnt, r > 0, ws, ctl->grab[(2 * r) & 3], pnext, a.wlp,
                                wbuf);
         if (!round_barrier<kPending>(
                 a,
@@ -706,10 +829,10 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
             for (long long i = tid; i < a.n_sure_out; i += nthreads) a.word[a.sure_out[i]] = kWordOut;
         }
         if (kPending)
-            exclude_phase<true>(a, a.wlp, s_pcnt, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next,
+            exclude_phase<true, kRange0>(a, a.wlp, s_pcnt, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next,
                                 dst, wbuf, wscan);
         else  // W_r's rows in the adjacency Phase 2 scans
-            exclude_phase<false>(a, pending_view(a, src, r > 0), s_cnt, r > 0, ws,
+            exclude_phase<false, kRange0>(a, pending_view(a, src, r > 0), s_cnt, r > 0, ws,
                                  ctl->grab[(2 * r + 1) & 3], next, dst, wbuf, wscan);
         const int cur = total + (r == 0 ? decided0 : 0);
         if (!round_barrier<kPending>(
@@ -746,32 +869,43 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     }
 }
 
+const void* csr_kernel_fn(const SolveArgs& a) {
+    const bool range0 = a.range0_max > 0;
+    if (a.pending)
+        return range0 ? (const void*)csr_solve_kernel<true, true>
+                      : (const void*)csr_solve_kernel<true, false>;
+    return range0 ? (const void*)csr_solve_kernel<false, true>
+                  : (const void*)csr_solve_kernel<false, false>;
+}
+
 cudaError_t launch_csr_solve(const SolveArgs& a, int grid, cudaStream_t s) {
     void* args[] = {const_cast<SolveArgs*>(&a)};
-    const void* fn = a.pending ? (const void*)csr_solve_kernel<true>
-                               : (const void*)csr_solve_kernel<false>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCsrBlock), args, 0, s);
+    return cudaLaunchCooperativeKernel(csr_kernel_fn(a), dim3(grid), dim3(kCsrBlock), args, 0, s);
 }
 
 cudaError_t launch_csr_solve_single(const SolveArgs& a, cudaStream_t s) {
-    if (a.pending) csr_solve_kernel<true><<<1, kCsrBlock, 0, s>>>(a);
-    else csr_solve_kernel<false><<<1, kCsrBlock, 0, s>>>(a);
-    return cudaGetLastError();
+    void* args[] = {const_cast<SolveArgs*>(&a)};
+    return cudaLaunchKernel(csr_kernel_fn(a), dim3(1), dim3(kCsrBlock), args, 0, s);
 }
 
 int csr_block_size() { return kCsrBlock; }
 
 int csr_max_coresident_blocks(int device) {
-    // both forms: the grid must fit whichever one a solve launches
-    int per_sm = 0, per_sm_p = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, (const void*)csr_solve_kernel<false>, kCsrBlock, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm_p, (const void*)csr_solve_kernel<true>, kCsrBlock, 0) != cudaSuccess)
-        return 0;
+    // every form: the grid must fit whichever one a solve launches
+    const void* fns[] = {(const void*)csr_solve_kernel<false, false>,
+                         (const void*)csr_solve_kernel<true, false>,
+                         (const void*)csr_solve_kernel<false, true>,
+                         (const void*)csr_solve_kernel<true, true>};
+    int per_sm = 1 << 30, sms = 0;
+    for (const void* fn : fns) {
+        int p = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, fn, kCsrBlock, 0) != cudaSuccess)
+            return 0;
+        per_sm = std::min(per_sm, p);
+    }
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return 0;
-    return std::min(per_sm, per_sm_p) * sms;
+    return per_sm * sms;
 }
 
 // ---------------------------------------------------------------- degree bins

@@ -75,7 +75,7 @@ class mis_tuning(ctypes.Structure):
                 ("bounds", ctypes.c_int32 * 4), ("grid", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("ms", ctypes.c_float),
                 ("csr_pending", ctypes.c_int32),
-                ("arcs_per_tile", ctypes.c_double)]
+                ("arcs_per_tile", ctypes.c_double), ("csr_range0", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -137,6 +137,8 @@ def lib():
         L.mis_replay_destroy.restype = None
         L.mis_set_csr_pending.argtypes = [P, i32]
         L.mis_set_csr_pending.restype = ctypes.c_int
+        L.mis_set_csr_range0.argtypes = [P, i32]
+        L.mis_set_csr_range0.restype = ctypes.c_int
         L.mis_destroy.argtypes = [P]
         L.mis_destroy.restype = None
         L.mis_update_edges.argtypes = [P, i64, P, i64, P, P]
@@ -174,7 +176,7 @@ def lib():
 EXPORTED = [
     "mis_options_init", "mis_create", "mis_create_ex", "mis_create_batch", "mis_graph_count",
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
-    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
+    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_set_csr_range0", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
     "mis_solve_noalloc", "mis_update_edges", "mis_repair", "mis_add_vertices",
 ]
@@ -355,6 +357,10 @@ def mis_replay_destroy(r):
 
 def mis_set_csr_pending(h, pending):
     return _check(lib().mis_set_csr_pending(h, int(pending)))
+
+
+def mis_set_csr_range0(h, on):
+    return _check(lib().mis_set_csr_range0(h, int(on)))
 
 
 def mis_autotune(h, reps=3):

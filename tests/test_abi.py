@@ -23,7 +23,7 @@ def lib():
 def _declared():
     text = open(os.path.join(ROOT, "include", "tcmis.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"\b(mis_[a-z_]+)\s*\(", text)
+    names = re.findall(r"\b(mis_[a-z_0-9]+)\s*\(", text)
     return sorted(set(names))
 
 

@@ -257,6 +257,40 @@ def test_row_orderings_bit_exact(name, order_rows):
         native.mis_destroy(h)
 
 
+@pytest.mark.parametrize("name", sorted(FAMILIES))
+@pytest.mark.parametrize("priority", [0, 1, 2])
+def test_range_round0_bit_exact(name, priority):
+    """Graphs without round-0 classes (order_rows = 0, or H1 / 8-bit keys):
+    round 0 reaches bin 0 by vertex ranges or through its list, with and
+    without the pending list, at several bin-0 bounds (including every row
+    in bin 0, hubs too)."""
+    g = graph(name)
+    h = create(g, order_rows=0, priority=priority)
+    try:
+        seed = 11
+        want = oracle.solve(g[0], g[1], g[2], seed, priority)
+        for bounds in ((8, 4096, 4096, 65536), (1, 2, 3, 4), (32, 64, 64, 64),
+                       (2**31 - 2,) * 4):
+            native.mis_set_csr_bins(h, bounds)
+            for range0 in (1, 0):
+                native.mis_set_csr_range0(h, range0)
+                for pending in (0, 1):
+                    native.mis_set_csr_pending(h, pending)
+                    got, st = gpu_solve(h, [seed])
+                    assert_same(g, seed, got, st, want)
+    finally:
+        native.mis_destroy(h)
+
+
+def test_range_round0_rejects_bad_mode():
+    h = create(graph("path"), order_rows=0)
+    try:
+        with pytest.raises(native.MisError):
+            native.mis_set_csr_range0(h, 2)
+    finally:
+        native.mis_destroy(h)
+
+
 def test_zero_vertices():
     h = create((0, np.zeros(1, np.int32), np.zeros(0, np.int32)))
     try:
