@@ -778,9 +778,18 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
     }
     TuneChoice best;
     best.ms = -1.f;
+    // TCMIS_TUNE_LOG set: every candidate's time on stderr
+    const bool log = std::getenv("TCMIS_TUNE_LOG") != nullptr;
     for (TuneChoice& c : cands) {
         if (apply_choice(g, c) != MIS_OK) continue;
         c.ms = time_solves(g, reps);
+        if (log)
+            std::fprintf(stderr,
+                         "tcmis tune: path %d param %d bounds %d %d %d %d grid %d pending %d "
+                         "range0 %d: %.4f ms\n",
+                         c.path, c.param, c.bounds[0], c.bounds[1], c.bounds[2], c.bounds[3],
+                         c.path == MIS_PATH_CSR ? g->grid : g->tile_grid, c.pending, c.range0,
+                         c.ms);
         if (c.ms > 0.f && (best.ms < 0.f || c.ms < best.ms)) best = c;
     }
     if (best.ms < 0.f) return set_error(MIS_EINTERNAL, "autotuner found no working configuration");
