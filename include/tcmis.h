@@ -68,7 +68,8 @@ enum {
     MIS_PATH_AUTO = 0,     /* autotuner's choice, cached per density class */
     MIS_PATH_CSR = 1,      /* warp-per-row CSR kernel on CUDA cores */
     MIS_PATH_TILE = 2,     /* tile-CSR kernel, bitmask payload, popc on CUDA cores */
-    MIS_PATH_TILE_TC = 3,  /* tile-CSR kernel, exclusion test as tensor-core MMA */
+    MIS_PATH_TILE_TC = 3,  /* tile-CSR kernel, exclusion test as tensor-core MMA
+                              (payload form: mis_set_tile_payload) */
     MIS_PATH_PUSH = 4      /* CSR, work-efficient push/decrement rounds: a count of
                               undecided higher neighbours per vertex, decremented
                               as they are excluded; every arc read O(1) times */
@@ -156,6 +157,8 @@ typedef struct mis_stats {
     int64_t tested_prefix_arcs; /* ... and the arcs of their selection prefixes
                                 (neighbours of degree <= deg + 1), which round
                                 0's selection test reads; -1 without one */
+    int32_t tile_payload;    /* MIS_PATH_TILE_TC: the MIS_TILE_* form that ran; -1
+                                on other paths */
 } mis_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -226,6 +229,11 @@ int mis_solve_ex(mis_graph *g, const uint64_t *seeds, uint8_t *out_status, void 
  * MIS sizes summed over the solves.  Single-graph handles only (MIS_EINVAL for
  * a batch, or k outside [1, 8]); MIS_EBUSY while served requests on `g` are in
  * flight; the extra device memory (32 bytes per vertex) is kept by the handle.
+ * On a graph whose path is MIS_PATH_TILE_TC the solves run on its 16 x 16
+ * tiles and the product A x [C_1 .. C_k] is a tensor-core MMA with the k
+ * solves as k of its eight columns, in the graph's tile payload form
+ * (mis_set_tile_payload); on any other path, on the CSR kernel's rows with
+ * CUDA cores.  mis_get_stats reports the path that ran.
  */
 int mis_solve_multi_ex(mis_graph *g, int32_t k, const uint64_t *seeds, uint8_t *out_status,
                        void *stream);
@@ -283,6 +291,45 @@ int mis_set_csr_bins(mis_graph *g, const int32_t *bounds);
  * values, MIS_EBUSY while served requests on `g` are in flight. */
 int mis_set_csr_pending(mis_graph *g, int32_t pending);
 
+/* Tile payload forms of the tensor-core exclusion (MIS_PATH_TILE_TC), i.e.
+ * of the product N_c = A x C of Sec. 3.1 Phase 2 over the non-empty 16 x 16
+ * tiles.  The selection test always reads the tiles' bitmasks; the forms
+ * differ in what the tensor cores read:
+ *   MIS_TILE_BITS     the bitmask, expanded to fp16 0/1 fragments in registers
+ *                     (mma m16n8k16, fp32 accumulation, one tile per MMA)
+ *   MIS_TILE_BITS_B1  the bitmask itself on the single-bit MMA: AND, then
+ *                     population count, int32 accumulation (m16n8k128, eight
+ *                     tiles per MMA)
+ *   MIS_TILE_INT8     stored 16 x 16 int8 0/1 tiles, 256 bytes each (m16n8k32,
+ *                     int32 accumulation, two tiles per MMA)
+ *   MIS_TILE_FP16     stored 16 x 16 fp16 0/1 tiles, 512 bytes each, the
+ *                     paper's format (Sec. 3.2, Listing 1; m16n8k16, fp32)
+ * All are exact (0/1 entries, sums below 2^24).  A stored payload is built on
+ * the device from the bitmask the first time its form runs and is kept by the
+ * handle (mis_footprint counts it). */
+enum {
+    MIS_TILE_BITS = 0,
+    MIS_TILE_BITS_B1 = 1,
+    MIS_TILE_INT8 = 2,
+    MIS_TILE_FP16 = 3
+};
+
+/* The payload form of the tensor-core tile path for later solves (and for
+ * the exclusion of multi-seed solves on that path); switches a graph already
+ * on MIS_PATH_TILE_TC at once, building its stored payload if needed.
+ * MIS_EINVAL for other values, MIS_ENOMEM when the payload does not fit,
+ * MIS_EBUSY while served requests on `g` are in flight. */
+int mis_set_tile_payload(mis_graph *g, int32_t payload);
+
+/* The 16 x 16 tiles' payload in form `payload` copied into the DEVICE buffer
+ * `out` on `stream` (for testing): MIS_TILE_BITS / MIS_TILE_BITS_B1 give the
+ * bitmask (32 bytes per tile, as mis_tiles_ex), MIS_TILE_INT8 256 bytes per
+ * tile (entry (i, j) at byte 16 i + j), MIS_TILE_FP16 512 bytes per tile (at
+ * half 16 i + j); tiles in tile-CSR order (mis_get_stats: ntiles).  Builds
+ * the 16 x 16 tile-CSR and the stored payload if needed; out may be NULL
+ * (build only). */
+int mis_tile_payload_ex(mis_graph *g, int32_t payload, void *out, void *stream);
+
 /* CSR path, graphs created without the round-0 classes (order_rows = 0 or a
  * priority other than Eq. 1): how round 0 (Algorithm 2's first iteration,
  * every vertex alive) reaches the rows of degree bin 0.  on = 1 (default):
@@ -304,6 +351,8 @@ typedef struct mis_tuning {
     double arcs_per_tile;/* sampled arcs per non-empty 8 x 8 tile */
     int32_t csr_range0;  /* CSR: the mis_set_csr_range0 mode of the choice (0 when
                             the graph has round-0 classes) */
+    int32_t tile_payload;/* MIS_PATH_TILE_TC: the MIS_TILE_* form of the choice,
+                            else -1 */
 } mis_tuning;
 
 /*

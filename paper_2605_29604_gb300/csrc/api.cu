@@ -172,7 +172,15 @@ int rebin(mis_graph* g, const int32_t thr[4], cudaStream_t s) {
     return MIS_OK;
 }
 
+void free_payload(GraphData& d) {
+    if (d.tpay) d.footprint -= tile_payload_bytes(d.tiles.ntiles, d.tpay_kind);
+    dfree(d.tpay);
+    d.tpay = nullptr;
+    d.tpay_kind = -1;
+}
+
 void free_tiles(GraphData& d) {
+    free_payload(d);
     dfree(d.tiles.trp);
     dfree(d.tiles.tcol);
     dfree(d.tiles.tbits);
@@ -202,12 +210,24 @@ int use_tiles(mis_graph* g, int path, int T) {
         d.footprint += d.tile_footprint;
     }
     const bool tc = path == MIS_PATH_TILE_TC;
+    // the stored int8 / fp16 payload of a tensor-core form that reads one
+    const int pay = g->tile_payload;
+    if (tc && (pay == MIS_TILE_INT8 || pay == MIS_TILE_FP16) && d.tpay_kind != pay) {
+        if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+        free_payload(d);
+        void* p = nullptr;
+        e = build_tile_payload(d.tiles, pay, &p, g->own_stream);
+        if (e != cudaSuccess) return set_cuda_error(e, "tile payload");
+        d.tpay = p;
+        d.tpay_kind = pay;
+        d.footprint += tile_payload_bytes(d.tiles.ntiles, pay);
+    }
     // a row block with many tiles gets a whole warp of tile slots; 8 x 8 row
     // blocks with few tiles are taken one per lane (32 row blocks per warp
     // pass: the selection test is latency-bound), 16 x 16 ones by 8 lanes
     const double per_rb = d.tiles.nrb ? (double)d.tiles.ntiles / d.tiles.nrb : 0.0;
-    g->tile_slots = per_rb > 12.0 ? 32 : (T == 8 ? 1 : 8);
-    const int maxb = tile_max_coresident_blocks(T, g->tile_slots, tc, d.device);
+    g->tile_slots = tc ? 8 : (per_rb > 12.0 ? 32 : (T == 8 ? 1 : 8));
+    const int maxb = tile_max_coresident_blocks(T, g->tile_slots, tc ? pay : -1, d.device);
     if (maxb <= 0) return set_error(MIS_EDEVICE, "no co-resident blocks for the tile kernel");
     long long want = ((long long)d.tiles.nrb + 63) / 64;
     if (want < 1) want = 1;
@@ -396,6 +416,7 @@ SolveArgs make_args(mis_graph* g, Workspace& w) {
     a.trp = d.tiles.trp;
     a.tcol = d.tiles.tcol;
     a.tbits = d.tiles.tbits;
+    a.tpay = d.tpay;
     a.nrb = d.tiles.nrb;
     a.inbits = w.inbits;
     a.rbl0 = w.rbl0;
@@ -424,6 +445,7 @@ void free_graph(mis_graph* g) {
     free_tiles(d);
     dfree(d.order0);
     dfree(d.word8);
+    dfree(d.inb8);
     dfree(d.r0class);
     dfree(d.sure_out);
     dfree(d.s0_rp);
@@ -473,7 +495,8 @@ int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_
             if (blocks > 0) grid = std::min<long long>(grid, blocks);
             e = launch_push_solve(a, (int)grid, s);
         } else if (tile)
-            e = launch_tile_solve(a, d.tiles.T, g->tile_slots, g->path == MIS_PATH_TILE_TC,
+            e = launch_tile_solve(a, d.tiles.T, g->tile_slots,
+                                  g->path == MIS_PATH_TILE_TC ? g->tile_payload : -1,
                                   blocks > 0 ? std::min(blocks, g->tile_grid) : g->tile_grid, s);
         else if (single_block)
             e = launch_csr_solve_single(a, s);
@@ -536,6 +559,7 @@ struct TuneChoice {
     float ms = 0.f;
     int32_t pending = 0; // CSR: Phase 1 lists its non-candidates for Phase 2
     int32_t range0 = 1;  // CSR: round 0 takes bin 0 by vertex ranges
+    int32_t payload = 0; // tensor-core tile path: MIS_TILE_* form
 };
 
 std::mutex g_tune_mu;
@@ -557,6 +581,7 @@ void tune_load_locked() {
             c.bounds[3] >> c.grid >> c.ms) {
             if (!(ss >> c.pending)) c.pending = 0;  // lines written before the field
             if (!(ss >> c.range0)) c.range0 = 1;
+            if (!(ss >> c.payload)) c.payload = 0;
             g_tune_cache[key] = c;
         }
     }
@@ -570,7 +595,7 @@ void tune_save_locked() {
         const TuneChoice& c = kv.second;
         out << kv.first << ' ' << c.path << ' ' << c.param << ' ' << c.bounds[0] << ' '
             << c.bounds[1] << ' ' << c.bounds[2] << ' ' << c.bounds[3] << ' ' << c.grid << ' '
-            << c.ms << ' ' << c.pending << ' ' << c.range0 << '\n';
+            << c.ms << ' ' << c.pending << ' ' << c.range0 << ' ' << c.payload << '\n';
     }
 }
 
@@ -667,6 +692,7 @@ std::string density_class(mis_graph* g, double apt) {
 }
 
 int apply_choice(mis_graph* g, const TuneChoice& c) {
+    if (c.path == MIS_PATH_TILE_TC) g->tile_payload = c.payload;
     if (c.path == MIS_PATH_TILE || c.path == MIS_PATH_TILE_TC) return use_tiles(g, c.path, c.param);
     if (c.path == MIS_PATH_PUSH) {
         g->path = MIS_PATH_PUSH;
@@ -771,10 +797,21 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
             t.param = T;
             cands.push_back(t);
         }
-        TuneChoice t;
-        t.path = MIS_PATH_TILE_TC;
-        t.param = 16;
-        cands.push_back(t);
+        // the tensor-core forms; a stored payload only while it stays within
+        // a quarter of the free device memory
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        const int64_t est_tiles = (int64_t)((double)g->d.arcs / std::max(apt, 1.0));
+        for (int pay : {MIS_TILE_BITS, MIS_TILE_BITS_B1, MIS_TILE_INT8, MIS_TILE_FP16}) {
+            if ((pay == MIS_TILE_INT8 || pay == MIS_TILE_FP16) &&
+                tile_payload_bytes(est_tiles, pay) > (int64_t)(free_b / 4))
+                continue;
+            TuneChoice t;
+            t.path = MIS_PATH_TILE_TC;
+            t.param = 16;
+            t.payload = pay;
+            cands.push_back(t);
+        }
     }
     TuneChoice best;
     best.ms = -1.f;
@@ -786,10 +823,10 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
         if (log)
             std::fprintf(stderr,
                          "tcmis tune: path %d param %d bounds %d %d %d %d grid %d pending %d "
-                         "range0 %d: %.4f ms\n",
+                         "range0 %d payload %d: %.4f ms\n",
                          c.path, c.param, c.bounds[0], c.bounds[1], c.bounds[2], c.bounds[3],
                          c.path == MIS_PATH_CSR ? g->grid : g->tile_grid, c.pending, c.range0,
-                         c.ms);
+                         c.payload, c.ms);
         if (c.ms > 0.f && (best.ms < 0.f || c.ms < best.ms)) best = c;
     }
     if (best.ms < 0.f) return set_error(MIS_EINTERNAL, "autotuner found no working configuration");
@@ -809,6 +846,7 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
         out->ms = best.ms;
         out->csr_pending = best.path == MIS_PATH_CSR ? best.pending : 0;
         out->csr_range0 = (best.path == MIS_PATH_CSR && !g->d.r0class) ? best.range0 : 0;
+        out->tile_payload = best.path == MIS_PATH_TILE_TC ? best.payload : -1;
         out->arcs_per_tile = apt;
         out->candidates = (int32_t)cands.size();
     }
@@ -1175,6 +1213,58 @@ int mis_set_csr_pending(mis_graph* g, int32_t pending) {
     return MIS_OK;
 }
 
+int mis_tile_payload_ex(mis_graph* g, int32_t payload, void* out, void* stream) {
+    clear_error();
+    if (!g) return set_error(MIS_EINVAL, "null graph");
+    if (payload < MIS_TILE_BITS || payload > MIS_TILE_FP16)
+        return set_error(MIS_EINVAL, "unknown tile payload");
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
+    GraphData& d = g->d;
+    cudaError_t e = cudaSetDevice(d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    if (d.tiles.T != 16) {
+        const int32_t keep = g->path;
+        const int rc = use_tiles(g, MIS_PATH_TILE, 16);
+        if (rc != MIS_OK) return rc;
+        g->path = keep;
+    }
+    const bool stored = payload == MIS_TILE_INT8 || payload == MIS_TILE_FP16;
+    if (stored && d.tpay_kind != payload) {
+        if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+        free_payload(d);
+        void* p = nullptr;
+        e = build_tile_payload(d.tiles, payload, &p, g->own_stream);
+        if (e != cudaSuccess) return set_cuda_error(e, "tile payload");
+        d.tpay = p;
+        d.tpay_kind = payload;
+        d.footprint += tile_payload_bytes(d.tiles.ntiles, payload);
+    }
+    if (!out) return MIS_OK;
+    const int64_t bytes = stored ? tile_payload_bytes(d.tiles.ntiles, payload) : 32 * d.tiles.ntiles;
+    if (bytes > 0)
+        e = cudaMemcpyAsync(out, stored ? d.tpay : (const void*)d.tiles.tbits, (size_t)bytes,
+                            cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_cuda_error(e, "tile payload copy");
+    return MIS_OK;
+}
+
+int mis_set_tile_payload(mis_graph* g, int32_t payload) {
+    clear_error();
+    if (!g) return set_error(MIS_EINVAL, "null graph");
+    if (payload < MIS_TILE_BITS || payload > MIS_TILE_FP16)
+        return set_error(MIS_EINVAL, "unknown tile payload");
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
+    cudaError_t e = cudaSetDevice(g->d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    g->tile_payload = payload;
+    // a graph already on the tensor-core path switches now (and builds the
+    // stored payload if the form reads one)
+    if (g->path == MIS_PATH_TILE_TC) return use_tiles(g, MIS_PATH_TILE_TC, 16);
+    return MIS_OK;
+}
+
 int mis_set_csr_range0(mis_graph* g, int32_t on) {
     clear_error();
     if (!g) return set_error(MIS_EINVAL, "null graph");
@@ -1285,6 +1375,7 @@ int mis_get_stats(mis_graph* g, mis_stats* st) {
     st->threads_per_row = g->tpr;
     st->tile = g->d.tiles.T;
     st->csr_pending = g->csr_pending;
+    st->tile_payload = g->last_path == MIS_PATH_TILE_TC ? g->tile_payload : -1;
     const bool csr = g->last_path == MIS_PATH_CSR;
     st->sure_in = csr ? g->d.n_sure_in : 0;
     st->sure_out = csr ? g->d.n_sure_out : 0;
@@ -1352,6 +1443,34 @@ int mis_solve_multi_ex(mis_graph* g, int32_t k, const uint64_t* seeds, uint8_t* 
         const int64_t cap = (d.n + 15) / 16 * 16;
         if ((e = dalloc(&d.word8, (int64_t)kMaxMulti * cap, &d.footprint)) != cudaSuccess)
             return set_cuda_error(e, "multi-seed workspace");
+    }
+    if (g->path == MIS_PATH_TILE_TC) {
+        // the solves as right-hand sides of the tensor-core exclusion
+        const int32_t words = tile_multi_bitvector_words(d.tiles.nrb);
+        if (!d.inb8) {
+            if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+            if ((e = dalloc(&d.inb8, (int64_t)kMaxMulti * words, &d.footprint)) != cudaSuccess)
+                return set_cuda_error(e, "multi-seed workspace");
+        }
+        MultiSeeds ms{};
+        for (int i = 0; i < k; ++i) ms.seed[i] = seeds[i];
+        SolveArgs a = make_args(g, d.ws);
+        a.out = out_status;
+        cudaStream_t s = (cudaStream_t)stream;
+        e = cudaMemsetAsync(d.ws.ctl, 0, sizeof(Ctl), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.ws.times, 0, sizeof(PhaseTimes), s);
+        if (e != cudaSuccess) return set_cuda_error(e, "control reset");
+        if (d.n > 0) {
+            const int maxb = tile_multi_max_coresident_blocks(g->tile_payload, d.device);
+            if (maxb <= 0) return set_error(MIS_EDEVICE, "no co-resident blocks for the kernel");
+            const long long want = std::max<long long>(1, ((long long)d.tiles.nrb + 63) / 64);
+            e = launch_tile_multi_solve(a, d.word8, d.inb8, k, ms, g->tile_payload,
+                                        (int)std::min<long long>(want, maxb), s);
+            if (e != cudaSuccess) return set_cuda_error(e, "multi-seed tile kernel launch");
+        }
+        g->last_stream = s;
+        g->last_path = MIS_PATH_TILE_TC;
+        return MIS_OK;
     }
     const int rc = solve_multi_in(g, d.ws, d.word8, k, seeds, out_status, (cudaStream_t)stream, 0);
     if (rc != MIS_OK) return rc;

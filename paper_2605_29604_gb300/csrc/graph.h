@@ -66,6 +66,12 @@ struct GraphData {
     // tile-CSR (built on demand)
     TileCsr tiles;
     int64_t tile_footprint = 0;
+    // stored payload of the 16 x 16 tiles for a tensor-core form that reads
+    // one (int8 or fp16, built on first use; kind -1 = none)
+    void* tpay = nullptr;
+    int32_t tpay_kind = -1;
+    // multi-seed solves on the tiles: one in-set bit vector per solve
+    uint32_t* inb8 = nullptr;
     // degree-ordered rows and degree bins of the CSR kernel
     int32_t* col_sel = nullptr;
     int32_t* split = nullptr;
@@ -111,6 +117,7 @@ struct mis_graph {
     int32_t tile_grid = 0;        // persistent grid size (tile kernels)
     int32_t tile_slots = 8;       // tile kernels: lanes (tiles in flight) per row block
     int32_t csr_pending = 0;      // CSR kernel: Phase 1 lists non-candidates for Phase 2
+    int32_t tile_payload = 0;     // tensor-core tile path: payload form (MIS_TILE_*)
     int32_t csr_range0 = 1;       // CSR kernel: round 0 tests bin 0 by vertex ranges
                                   // (graphs without round-0 classes only)
     cudaStream_t own_stream = nullptr;

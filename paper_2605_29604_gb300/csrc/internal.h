@@ -86,6 +86,7 @@ struct SolveArgs {
     const int32_t* trp = nullptr;    // row block rb owns tiles [trp[rb], trp[rb+1])
     const int32_t* tcol = nullptr;   // column block of each tile
     const uint64_t* tbits = nullptr; // T*T/64 words of row-major 0/1 bits per tile
+    const void* tpay = nullptr;      // stored int8 / fp16 tile payload (tensor-core forms)
     int32_t nrb = 0;                 // row blocks = ceil(n / T)
     uint32_t* inbits = nullptr;      // bit v set once v is in the MIS (nrb*T bits)
     int32_t* rbl0 = nullptr;         // row-block worklists, nrb each
@@ -212,11 +213,28 @@ struct TileCsr {
 cudaError_t build_tiles(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs, int T,
                         TileCsr* out, cudaStream_t s);
 // Persistent tile round kernel: T = 8 or 16 (tile size), S = 8 or 32 (lanes,
-// i.e. tiles in flight, per row block); tc = exclusion test on tensor cores
-// (T = 16 only).
-cudaError_t launch_tile_solve(const SolveArgs& a, int T, int S, bool tc, int grid,
+// i.e. tiles in flight, per row block); tc_payload = the payload form of the
+// exclusion test on tensor cores (tile_tc.cuh; T = 16 only), -1 = popc on
+// CUDA cores.
+cudaError_t launch_tile_solve(const SolveArgs& a, int T, int S, int tc_payload, int grid,
                               cudaStream_t s);
-int tile_max_coresident_blocks(int T, int S, bool tc, int device);
+int tile_max_coresident_blocks(int T, int S, int tc_payload, int device);
+// kernels_tile_multi.cu: k <= kMaxMulti solves of the graph of `a` on its
+// 16 x 16 tiles (a.trp, a.tcol, a.tbits, a.tpay; a.rbl0/1 row-block lists),
+// the exclusion test on tensor cores in payload form `payload` with the k
+// solves as right-hand sides.  word8: kMaxMulti words per vertex (nrb * 16
+// vertices); inb8: kMaxMulti bit vectors of tile_multi_bitvector_words(nrb)
+// words each.  a.out receives solve s at a.out + s * n.
+int32_t tile_multi_bitvector_words(int32_t nrb);
+cudaError_t launch_tile_multi_solve(const SolveArgs& a, uint32_t* word8, uint32_t* inb8, int k,
+                                    const MultiSeeds& seeds, int payload, int grid,
+                                    cudaStream_t s);
+int tile_multi_max_coresident_blocks(int payload, int device);
+// The int8 (256 bytes per tile) or fp16 (512 bytes per tile) payload of a
+// 16 x 16 tile-CSR for the tensor-core exclusion, expanded from its bitmask
+// (tile_tc.cuh: kPayI8, kPayF16); allocates *out (freed with dev_free).
+int64_t tile_payload_bytes(int64_t ntiles, int P);
+cudaError_t build_tile_payload(const TileCsr& tiles, int P, void** out, cudaStream_t s);
 
 // validation flag bits
 constexpr unsigned kBadRowPtr = 1u;

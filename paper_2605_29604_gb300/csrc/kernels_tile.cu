@@ -35,6 +35,7 @@
 #include "common.cuh"
 #include "init.cuh"
 #include "internal.h"
+#include "tile_tc.cuh"
 
 namespace tcmis {
 
@@ -426,21 +427,18 @@ __device__ __forceinline__ void tile_exclude(const SolveArgs& a, const int32_t* 
     }
 }
 
-__device__ __forceinline__ uint32_t half2_bits(uint32_t lo, uint32_t hi) {
-    // fp16 1.0 is 0x3C00
-    return (lo ? 0x3C00u : 0u) | (hi ? 0x3C000000u : 0u);
-}
-
-// Phase 2+3 on tensor cores (T = 16): one warp per row block, one
-// mma.m16n8k16 per tile whose C segment is non-zero.
+// Phase 2+3 on tensor cores (T = 16): one warp per row block; N_c of its 16
+// rows by rowblock_nc in payload form P, with C (the in-set bits) as column 0
+// of the B operand.
+template <int P>
 __device__ __forceinline__ void tile_exclude_tc(const SolveArgs& a,
                                                 const int32_t* __restrict__ list, int cnt,
                                                 unsigned* grab, int* next,
                                                 int32_t* __restrict__ dst, int32_t* wkeep) {
     if (cnt <= 0) return;
     const unsigned lane = lane_id();
-    const int g = (int)(lane >> 2);  // fragment row group
-    const int q = (int)(lane & 3);   // fragment column pair
+    const bool col0 = (lane >> 2) == 0;  // this lane's B column is solve 0
+    const uint16_t* inseg = reinterpret_cast<const uint16_t*>(a.inbits);
     const int ch = tile_chunk<1>(cnt);
     if (tile_gwarp() >= (cnt + ch - 1) / ch) return;
     for (;;) {
@@ -452,43 +450,22 @@ __device__ __forceinline__ void tile_exclude_tc(const SolveArgs& a,
         int nkeep = 0;
         for (int item = c0; item < c1; ++item) {
             const int rb = list[item];
-            const int t0 = a.trp[rb];
-            const int t1 = a.trp[rb + 1];
-            float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-            for (int t = t0; t < t1; ++t) {
-                const int cb = __ldg(a.tcol + t);
-                const uint32_t seg = in_segment<16>(a.inbits, cb);
-                if (seg == 0u) continue;  // C segment empty: the tile adds nothing
-                const uint32_t r0 = tile_row<16>(a.tbits, t, g);
-                const uint32_t r8 = tile_row<16>(a.tbits, t, g + 8);
-                const uint32_t a0 = half2_bits((r0 >> (2 * q)) & 1u, (r0 >> (2 * q + 1)) & 1u);
-                const uint32_t a1 = half2_bits((r8 >> (2 * q)) & 1u, (r8 >> (2 * q + 1)) & 1u);
-                const uint32_t a2 =
-                    half2_bits((r0 >> (2 * q + 8)) & 1u, (r0 >> (2 * q + 9)) & 1u);
-                const uint32_t a3 =
-                    half2_bits((r8 >> (2 * q + 8)) & 1u, (r8 >> (2 * q + 9)) & 1u);
-                // B = the C segment as column 0 of a 16 x 8 operand
-                const uint32_t b0 =
-                    g == 0 ? half2_bits((seg >> (2 * q)) & 1u, (seg >> (2 * q + 1)) & 1u) : 0u;
-                const uint32_t b1 =
-                    g == 0 ? half2_bits((seg >> (2 * q + 8)) & 1u, (seg >> (2 * q + 9)) & 1u)
-                           : 0u;
-                asm volatile(
-                    "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
-                    "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
-                    : "+f"(acc0), "+f"(acc1), "+f"(acc2), "+f"(acc3)
-                    : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-            }
-            // N_c of rows g (acc0) and g + 8 (acc2) sit in column 0, lanes q == 0
-            const float nc_lo = __shfl_sync(0xFFFFFFFFu, acc0, (int)(lane & 7) * 4);
-            const float nc_hi = __shfl_sync(0xFFFFFFFFu, acc2, (int)(lane & 7) * 4);
+            int d[4];
+            rowblock_nc<P>(a.tbits, a.tpay, a.trp[rb], a.trp[rb + 1],
+                           [&](int t) -> uint32_t {
+                               return col0 ? (uint32_t)inseg[__ldg(a.tcol + t)] : 0u;
+                           },
+                           d);
+            // N_c of rows g (d[0]) and g + 8 (d[2]) sit in column 0, lanes q == 0
+            const int nc_lo = __shfl_sync(0xFFFFFFFFu, d[0], (int)(lane & 7) * 4);
+            const int nc_hi = __shfl_sync(0xFFFFFFFFu, d[2], (int)(lane & 7) * 4);
             bool keep_row = false;
             if (lane < 16) {
                 const int v = rb * 16 + (int)lane;
-                const float nc = lane < 8 ? nc_lo : nc_hi;
+                const int nc = lane < 8 ? nc_lo : nc_hi;
                 const uint32_t wv = ld_word_l1(a.word + v);
                 if ((wv >> 29) == 1u) {
-                    if (nc > 0.5f) a.word[v] = kWordOut;
+                    if (nc > 0) a.word[v] = kWordOut;
                     else keep_row = true;
                 }
             }
@@ -508,7 +485,9 @@ __device__ __forceinline__ void tile_exclude_tc(const SolveArgs& a,
     }
 }
 
-template <int T, int S, bool kTC>
+// P: the tensor-core payload form of Phase 2 (tile_tc.cuh), or -1 for the
+// CUDA-core popc form.
+template <int T, int S, int P>
 __global__ void __launch_bounds__(kTileBlock, 2) tile_solve_kernel(const SolveArgs a) {
     __shared__ int32_t s_keep[kTileWarps][kTileChunk];
     __shared__ unsigned s_alive;
@@ -564,8 +543,8 @@ __global__ void __launch_bounds__(kTileBlock, 2) tile_solve_kernel(const SolveAr
             return;
 
         // ---- Phase 2+3: exclusion test, state update, compaction
-        if (kTC)
-            tile_exclude_tc(a, src, count, &ctl->grab[(2 * r + 1) & 3][0], next, dst, wkeep);
+        if constexpr (P >= 0)
+            tile_exclude_tc<P>(a, src, count, &ctl->grab[(2 * r + 1) & 3][0], next, dst, wkeep);
         else
             tile_exclude<T, S>(a, src, count, &ctl->grab[(2 * r + 1) & 3][0], next, dst, wkeep);
         if (!grid_barrier(ctl, nblocks, a.spin_cap, [ctl, times, rr]() {
@@ -608,32 +587,41 @@ __global__ void __launch_bounds__(kTileBlock, 2) tile_solve_kernel(const SolveAr
     }
 }
 
-const void* tile_kernel_fn(int T, int S, bool tc) {
-    if (tc) return T == 16 ? (const void*)tile_solve_kernel<16, 8, true> : nullptr;
-    if (T == 8 && S == 1) return (const void*)tile_solve_kernel<8, 1, false>;
-    if (T == 8 && S == 2) return (const void*)tile_solve_kernel<8, 2, false>;
-    if (T == 8 && S == 4) return (const void*)tile_solve_kernel<8, 4, false>;
-    if (T == 16 && S == 1) return (const void*)tile_solve_kernel<16, 1, false>;
-    if (T == 16 && S == 4) return (const void*)tile_solve_kernel<16, 4, false>;
-    if (T == 8 && S == 8) return (const void*)tile_solve_kernel<8, 8, false>;
-    if (T == 8 && S == 32) return (const void*)tile_solve_kernel<8, 32, false>;
-    if (T == 16 && S == 8) return (const void*)tile_solve_kernel<16, 8, false>;
-    if (T == 16 && S == 32) return (const void*)tile_solve_kernel<16, 32, false>;
+const void* tile_kernel_fn(int T, int S, int P) {
+    if (P >= 0) {
+        if (T != 16) return nullptr;
+        switch (P) {
+            case kPayBitsF16: return (const void*)tile_solve_kernel<16, 8, kPayBitsF16>;
+            case kPayB1: return (const void*)tile_solve_kernel<16, 8, kPayB1>;
+            case kPayI8: return (const void*)tile_solve_kernel<16, 8, kPayI8>;
+            case kPayF16: return (const void*)tile_solve_kernel<16, 8, kPayF16>;
+            default: return nullptr;
+        }
+    }
+    if (T == 8 && S == 1) return (const void*)tile_solve_kernel<8, 1, -1>;
+    if (T == 8 && S == 2) return (const void*)tile_solve_kernel<8, 2, -1>;
+    if (T == 8 && S == 4) return (const void*)tile_solve_kernel<8, 4, -1>;
+    if (T == 16 && S == 1) return (const void*)tile_solve_kernel<16, 1, -1>;
+    if (T == 16 && S == 4) return (const void*)tile_solve_kernel<16, 4, -1>;
+    if (T == 8 && S == 8) return (const void*)tile_solve_kernel<8, 8, -1>;
+    if (T == 8 && S == 32) return (const void*)tile_solve_kernel<8, 32, -1>;
+    if (T == 16 && S == 8) return (const void*)tile_solve_kernel<16, 8, -1>;
+    if (T == 16 && S == 32) return (const void*)tile_solve_kernel<16, 32, -1>;
     return nullptr;
 }
 
 }  // namespace
 
-cudaError_t launch_tile_solve(const SolveArgs& a, int T, int S, bool tc, int grid,
+cudaError_t launch_tile_solve(const SolveArgs& a, int T, int S, int tc_payload, int grid,
                               cudaStream_t s) {
-    const void* fn = tile_kernel_fn(T, S, tc);
+    const void* fn = tile_kernel_fn(T, S, tc_payload);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {const_cast<SolveArgs*>(&a)};
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTileBlock), args, 0, s);
 }
 
-int tile_max_coresident_blocks(int T, int S, bool tc, int device) {
-    const void* fn = tile_kernel_fn(T, S, tc);
+int tile_max_coresident_blocks(int T, int S, int tc_payload, int device) {
+    const void* fn = tile_kernel_fn(T, S, tc_payload);
     if (!fn) return 0;
     int per_sm = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTileBlock, 0) != cudaSuccess)
@@ -641,6 +629,64 @@ int tile_max_coresident_blocks(int T, int S, bool tc, int device) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return 0;
     return per_sm * sms;
+}
+
+// ---------------------------------------------------------------- stored payloads
+//
+// The int8 and fp16 payload forms of the tensor-core exclusion, expanded from
+// the bitmask: tile t's entry (i, j) at byte (kPayI8) or half (kPayF16)
+// offset t * 256 + i * 16 + j.  One thread per tile row.
+
+namespace {
+
+__global__ void expand_payload_kernel(const uint64_t* __restrict__ tbits, int64_t ntiles, int P,
+                                      void* __restrict__ out) {
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= ntiles * 16) return;
+    const int t = (int)(x >> 4), i = (int)(x & 15);
+    const uint32_t r = tile_row16(tbits, t, i);
+    if (P == kPayI8) {
+        uint4 v;
+        v.x = bytes_of4(r & 0xFu);
+        v.y = bytes_of4((r >> 4) & 0xFu);
+        v.z = bytes_of4((r >> 8) & 0xFu);
+        v.w = bytes_of4((r >> 12) & 0xFu);
+        reinterpret_cast<uint4*>(out)[x] = v;
+    } else {
+        uint32_t h[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h[k] = half2_of((r >> (2 * k)) & 1u, (r >> (2 * k + 1)) & 1u);
+        uint4* o = reinterpret_cast<uint4*>(out) + 2 * x;
+        o[0] = make_uint4(h[0], h[1], h[2], h[3]);
+        o[1] = make_uint4(h[4], h[5], h[6], h[7]);
+    }
+}
+
+}  // namespace
+
+int64_t tile_payload_bytes(int64_t ntiles, int P) {
+    return P == kPayI8 ? 256 * ntiles : P == kPayF16 ? 512 * ntiles : 0;
+}
+
+cudaError_t build_tile_payload(const TileCsr& tiles, int P, void** out, cudaStream_t s) {
+    *out = nullptr;
+    if (tiles.T != 16 || (P != kPayI8 && P != kPayF16)) return cudaErrorInvalidValue;
+    const int64_t bytes = tile_payload_bytes(tiles.ntiles, P);
+    cudaError_t e = dev_alloc(out, (size_t)std::max<int64_t>(bytes, 16));
+    if (e != cudaSuccess) return e;
+    if (tiles.ntiles > 0) {
+        const long long rows = tiles.ntiles * 16;
+        expand_payload_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(tiles.tbits,
+                                                                            tiles.ntiles, P, *out);
+        e = cudaGetLastError();
+    }
+    const cudaError_t se = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = se;
+    if (e != cudaSuccess) {
+        dev_free(*out);
+        *out = nullptr;
+    }
+    return e;
 }
 
 }  // namespace tcmis

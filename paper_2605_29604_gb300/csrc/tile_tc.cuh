@@ -1,0 +1,161 @@
+// tile_tc.cuh -- the exclusion product of one 16-row block on tensor cores.
+//
+// Phase 2 of Algorithm 2 is the product N_c = A x C of the 0/1 adjacency A
+// with the 0/1 vector C of the round's candidates (Sec. 3.1); the paper runs
+// it as 16 x 16 fp16 tiles with fp32 accumulation (Listing 1).  With several
+// solves of one graph in one launch, C becomes [C_1 .. C_8] and the product
+// fills the eight columns of an m16n8 MMA.  rowblock_nc computes, for one
+// block of 16 rows and its non-empty tiles [t0, t1):
+//
+//   D[i][s] = sum over tiles t, columns j of A_t(i, j) * C_s(16 * tcol[t] + j)
+//
+// for 16 rows i and 8 right-hand sides s, in one of four payload forms:
+//
+//   kPayBitsF16  the tile's bitmask expanded to fp16 A fragments in registers,
+//                m16n8k16, one tile per MMA;
+//   kPayB1       the bitmask itself on the single-bit MMA (AND, then POPC,
+//                accumulated in int32), m16n8k128, eight tiles per MMA;
+//   kPayI8       stored 16 x 16 int8 0/1 tiles, m16n8k32 s8, two tiles per MMA;
+//   kPayF16      stored 16 x 16 fp16 0/1 tiles (the paper's format), m16n8k16.
+//
+// Every form is exact: entries are 0/1 and a row of one launch's product is at
+// most the row's degree (< 2^24, exact in fp32; int32 for the integer forms).
+// Fragment coordinates of a lane: g = lane / 4 (A rows g and g + 8, B and D
+// column g), q = lane % 4; the lane receives D[g][2q], D[g][2q + 1],
+// D[g + 8][2q], D[g + 8][2q + 1].  Groups of tiles whose C segments are zero
+// in every column add nothing and are skipped (the early exit of Sec. 3.2).
+#pragma once
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace tcmis {
+
+constexpr int kPayBitsF16 = 0;
+constexpr int kPayB1 = 1;
+constexpr int kPayI8 = 2;
+constexpr int kPayF16 = 3;
+
+// Row i's 16 bits of tile t (bit j = entry (i, j)); four 64-bit words per tile.
+__device__ __forceinline__ uint32_t tile_row16(const uint64_t* __restrict__ tbits, int t, int i) {
+    return (uint32_t)(__ldg(tbits + (long long)t * 4 + (i >> 2)) >> (16 * (i & 3))) & 0xFFFFu;
+}
+
+// fp16 pair {lo, hi} of two 0/1 values (1.0 = 0x3C00).
+__device__ __forceinline__ uint32_t half2_of(uint32_t lo, uint32_t hi) {
+    return (lo ? 0x3C00u : 0u) | (hi ? 0x3C000000u : 0u);
+}
+
+// Four int8 0/1 values from the low four bits (bit b -> byte b).
+__device__ __forceinline__ uint32_t bytes_of4(uint32_t bits) {
+    return (bits & 1u) | ((bits & 2u) << 7) | ((bits & 4u) << 14) | ((bits & 8u) << 21);
+}
+
+__device__ __forceinline__ void mma_f16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                        uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_s8(int (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                       uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+        : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_b1(int (&c)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k128.row.col.s32.b1.b1.s32.and.popc "
+        "{%0, %1, %2, %3}, {%4, %5}, {%6}, {%0, %1, %2, %3};\n"
+        : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
+        : "r"(a0), "r"(a1), "r"(b0));
+}
+
+// D of one row block (see above).  seg(t): the 16 C bits of this lane's
+// column g on tile t's column block (0 for columns beyond the solves).
+// pay: the stored int8 (256 bytes per tile) or fp16 (512 bytes per tile)
+// payload for kPayI8 / kPayF16, unused otherwise.  Warp-uniform: every lane
+// of the warp calls it for the same row block.
+template <int P, class Seg>
+__device__ __forceinline__ void rowblock_nc(const uint64_t* __restrict__ tbits,
+                                            const void* __restrict__ pay, int t0, int t1,
+                                            Seg seg, int (&d)[4]) {
+    const unsigned lane = lane_id();
+    const int g = (int)(lane >> 2), q = (int)(lane & 3);
+    if constexpr (P == kPayB1) {
+        int acc[4] = {0, 0, 0, 0};
+        for (int tb = t0; tb < t1; tb += 8) {
+            // this lane's 32 k-slots are tiles tb + 2q and tb + 2q + 1
+            const int ta = tb + 2 * q, tc = ta + 1;
+            uint32_t b0 = 0;
+            if (ta < t1) b0 = seg(ta);
+            if (tc < t1) b0 |= seg(tc) << 16;
+            if (!__any_sync(0xFFFFFFFFu, b0 != 0u)) continue;
+            uint32_t a0 = 0, a1 = 0;
+            if (ta < t1) {
+                a0 = tile_row16(tbits, ta, g);
+                a1 = tile_row16(tbits, ta, g + 8);
+            }
+            if (tc < t1) {
+                a0 |= tile_row16(tbits, tc, g) << 16;
+                a1 |= tile_row16(tbits, tc, g + 8) << 16;
+            }
+            mma_b1(acc, a0, a1, b0);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] = acc[k];
+    } else if constexpr (P == kPayI8) {
+        const uint32_t* p8 = reinterpret_cast<const uint32_t*>(pay);  // 64 words per tile
+        int acc[4] = {0, 0, 0, 0};
+        for (int tb = t0; tb < t1; tb += 2) {
+            const bool two = tb + 1 < t1;
+            const uint32_t s0 = seg(tb), s1 = two ? seg(tb + 1) : 0u;
+            if (!__any_sync(0xFFFFFFFFu, (s0 | s1) != 0u)) continue;
+            const uint32_t* pa = p8 + (long long)tb * 64;
+            const uint32_t a0 = __ldg(pa + g * 4 + q), a1 = __ldg(pa + (g + 8) * 4 + q);
+            uint32_t a2 = 0, a3 = 0;
+            if (two) {
+                a2 = __ldg(pa + 64 + g * 4 + q);
+                a3 = __ldg(pa + 64 + (g + 8) * 4 + q);
+            }
+            mma_s8(acc, a0, a1, a2, a3, bytes_of4((s0 >> (4 * q)) & 0xFu),
+                   bytes_of4((s1 >> (4 * q)) & 0xFu));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] = acc[k];
+    } else {
+        const uint32_t* p16 = reinterpret_cast<const uint32_t*>(pay);  // 128 words per tile
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int t = t0; t < t1; ++t) {
+            const uint32_t s = seg(t);
+            if (!__any_sync(0xFFFFFFFFu, s != 0u)) continue;
+            uint32_t a0, a1, a2, a3;
+            if constexpr (P == kPayF16) {
+                const uint32_t* pt = p16 + (long long)t * 128;
+                a0 = __ldg(pt + g * 8 + q);
+                a1 = __ldg(pt + (g + 8) * 8 + q);
+                a2 = __ldg(pt + g * 8 + q + 4);
+                a3 = __ldg(pt + (g + 8) * 8 + q + 4);
+            } else {
+                const uint32_t r0 = tile_row16(tbits, t, g), r8 = tile_row16(tbits, t, g + 8);
+                a0 = half2_of((r0 >> (2 * q)) & 1u, (r0 >> (2 * q + 1)) & 1u);
+                a1 = half2_of((r8 >> (2 * q)) & 1u, (r8 >> (2 * q + 1)) & 1u);
+                a2 = half2_of((r0 >> (2 * q + 8)) & 1u, (r0 >> (2 * q + 9)) & 1u);
+                a3 = half2_of((r8 >> (2 * q + 8)) & 1u, (r8 >> (2 * q + 9)) & 1u);
+            }
+            mma_f16(acc, a0, a1, a2, a3, half2_of((s >> (2 * q)) & 1u, (s >> (2 * q + 1)) & 1u),
+                    half2_of((s >> (2 * q + 8)) & 1u, (s >> (2 * q + 9)) & 1u));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] = (int)acc[k];
+    }
+}
+
+}  // namespace tcmis

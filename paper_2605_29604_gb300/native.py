@@ -67,7 +67,8 @@ class mis_stats(ctypes.Structure):
                 ("select_ns", ctypes.c_int64 * 64), ("exclude_ns", ctypes.c_int64 * 64),
                 ("sure_in", ctypes.c_int64), ("sure_out", ctypes.c_int64),
                 ("tested_arcs", ctypes.c_int64), ("keyed", ctypes.c_int64),
-                ("tested_rows", ctypes.c_int64), ("tested_prefix_arcs", ctypes.c_int64)]
+                ("tested_rows", ctypes.c_int64), ("tested_prefix_arcs", ctypes.c_int64),
+                ("tile_payload", ctypes.c_int32)]
 
 
 class mis_tuning(ctypes.Structure):
@@ -75,7 +76,8 @@ class mis_tuning(ctypes.Structure):
                 ("bounds", ctypes.c_int32 * 4), ("grid", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("ms", ctypes.c_float),
                 ("csr_pending", ctypes.c_int32),
-                ("arcs_per_tile", ctypes.c_double), ("csr_range0", ctypes.c_int32)]
+                ("arcs_per_tile", ctypes.c_double), ("csr_range0", ctypes.c_int32),
+                ("tile_payload", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -137,6 +139,10 @@ def lib():
         L.mis_replay_destroy.restype = None
         L.mis_set_csr_pending.argtypes = [P, i32]
         L.mis_set_csr_pending.restype = ctypes.c_int
+        L.mis_tile_payload_ex.argtypes = [P, i32, P, P]
+        L.mis_tile_payload_ex.restype = ctypes.c_int
+        L.mis_set_tile_payload.argtypes = [P, i32]
+        L.mis_set_tile_payload.restype = ctypes.c_int
         L.mis_set_csr_range0.argtypes = [P, i32]
         L.mis_set_csr_range0.restype = ctypes.c_int
         L.mis_destroy.argtypes = [P]
@@ -176,7 +182,7 @@ def lib():
 EXPORTED = [
     "mis_options_init", "mis_create", "mis_create_ex", "mis_create_batch", "mis_graph_count",
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
-    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_set_csr_range0", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
+    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_set_csr_range0", "mis_set_tile_payload", "mis_tile_payload_ex", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
     "mis_solve_noalloc", "mis_update_edges", "mis_repair", "mis_add_vertices",
 ]
@@ -357,6 +363,18 @@ def mis_replay_destroy(r):
 
 def mis_set_csr_pending(h, pending):
     return _check(lib().mis_set_csr_pending(h, int(pending)))
+
+
+MIS_TILE_BITS, MIS_TILE_BITS_B1, MIS_TILE_INT8, MIS_TILE_FP16 = 0, 1, 2, 3
+
+
+def mis_tile_payload_ex(h, payload, out_ptr, stream=None):
+    return _check(lib().mis_tile_payload_ex(h, int(payload), ctypes.c_void_p(out_ptr),
+                                            ctypes.c_void_p(stream) if stream else None))
+
+
+def mis_set_tile_payload(h, payload):
+    return _check(lib().mis_set_tile_payload(h, int(payload)))
 
 
 def mis_set_csr_range0(h, on):

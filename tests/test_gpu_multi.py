@@ -120,3 +120,31 @@ def test_multi_rejects_bad_arguments():
             native.mis_solve_multi_ex(hb, np.asarray([1, 2], dtype=np.uint64), out.data_ptr())
     finally:
         native.mis_destroy(hb)
+
+
+PAYLOADS = [native.MIS_TILE_BITS, native.MIS_TILE_BITS_B1, native.MIS_TILE_INT8,
+            native.MIS_TILE_FP16]
+
+
+@pytest.mark.parametrize("name", sorted(FAMILIES))
+@pytest.mark.parametrize("payload", PAYLOADS)
+@pytest.mark.parametrize("k", [1, 5, 8])
+def test_multi_on_tiles_tensor_cores_bit_exact(name, payload, k):
+    """The k solves as right-hand sides of the tensor-core exclusion on the
+    16 x 16 tiles, in every payload form: each solve's set equals the
+    oracle's, and the summed rounds match."""
+    g = graph(name)
+    h = create(g, order_rows=0)
+    try:
+        native.mis_set_tile_payload(h, payload)
+        native.mis_set_path(h, native.MIS_PATH_TILE_TC, 16)
+        seeds = [3 + 1013 * i for i in range(k)]
+        got, st = multi_solve(h, g[0], seeds)
+        assert st.path == native.MIS_PATH_TILE_TC
+        check(g, seeds, got, st)
+        # a second launch reuses the bit vectors and words
+        seeds2 = [s + 1 for s in seeds]
+        got2, st2 = multi_solve(h, g[0], seeds2)
+        check(g, seeds2, got2, st2)
+    finally:
+        native.mis_destroy(h)

@@ -94,6 +94,67 @@ def test_converter_matches_definition(name, T):
         native.mis_destroy(h)
 
 
+PAYLOADS = [native.MIS_TILE_BITS, native.MIS_TILE_BITS_B1, native.MIS_TILE_INT8,
+            native.MIS_TILE_FP16]
+
+
+@pytest.mark.parametrize("name", ["er_10k", "rmat14", "grid", "grid_perm", "path_ragged", "empty",
+                                  "complete"])
+@pytest.mark.parametrize("payload", PAYLOADS)
+def test_payload_matches_definition(name, payload):
+    """Each payload form of the 16 x 16 tiles against the tile-CSR built here
+    from the definition: the bitmask bit for bit, the int8 and fp16 forms
+    entry by entry (1 exactly where the arc is, 0 elsewhere)."""
+    import torch
+    g = graph(name)
+    n, rp, col = g
+    h = create(g)
+    try:
+        native.mis_tile_payload_ex(h, payload, 0)
+        st = native.mis_get_stats(h)
+        _, _, bits = numpy_tiles(n, rp, col, 16)
+        nt = st.ntiles
+        assert nt == len(bits) // 4
+        per = {native.MIS_TILE_INT8: 256, native.MIS_TILE_FP16: 512}.get(payload, 32)
+        buf = torch.zeros(max(nt * per, 16), dtype=torch.uint8, device="cuda")
+        native.mis_tile_payload_ex(h, payload, buf.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        got = buf.cpu().numpy()[:nt * per]
+        # entry (t, i, j) of the definition
+        ent = np.zeros((nt, 16, 16), dtype=np.uint8)
+        w = bits.reshape(nt, 4)
+        for i in range(16):
+            row = (w[:, i // 4] >> np.uint64(16 * (i % 4))) & np.uint64(0xFFFF)
+            for j in range(16):
+                ent[:, i, j] = ((row >> np.uint64(j)) & np.uint64(1)).astype(np.uint8)
+        if payload in (native.MIS_TILE_BITS, native.MIS_TILE_BITS_B1):
+            assert np.array_equal(got.view(np.uint64), bits)
+        elif payload == native.MIS_TILE_INT8:
+            assert np.array_equal(got.reshape(nt, 16, 16), ent)
+        else:
+            halves = got.view(np.float16).reshape(nt, 16, 16)
+            assert np.array_equal(halves, ent.astype(np.float16))
+        assert int(ent.sum()) == int(rp[-1])
+    finally:
+        native.mis_destroy(h)
+
+
+@pytest.mark.parametrize("name", sorted(FAMILIES))
+@pytest.mark.parametrize("payload", PAYLOADS)
+def test_tile_tc_payloads_bit_exact(name, payload):
+    """The tensor-core exclusion in every payload form."""
+    g = graph(name)
+    h = create(g)
+    try:
+        native.mis_set_tile_payload(h, payload)
+        for seed in (1, 9):
+            got, st = gpu_solve(h, [seed], native.MIS_PATH_TILE_TC, 16)
+            assert st.path == native.MIS_PATH_TILE_TC and st.tile_payload == payload
+            assert_same(g, seed, got, st)
+    finally:
+        native.mis_destroy(h)
+
+
 @pytest.mark.parametrize("name", sorted(FAMILIES))
 @pytest.mark.parametrize("path,T", [(native.MIS_PATH_TILE, 8), (native.MIS_PATH_TILE, 16),
                                     (native.MIS_PATH_TILE_TC, 16)])
