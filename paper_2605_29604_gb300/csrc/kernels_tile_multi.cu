@@ -9,17 +9,16 @@
 // eight words per vertex, side by side) and its own in-set bit vector, the B
 // operand: C_s's 16 bits on a tile's column block are one 16-bit load.
 //
-// A warp takes one row block (16 vertices).  Lane (g, q), g = lane / 4 and
-// q = lane % 4, owns rows g and g + 8 in solves 2q and 2q + 1 in both phases
-// -- exactly the four entries D[g][2q], D[g][2q+1], D[g+8][2q], D[g+8][2q+1]
-// of the MMA result it receives, so the exclusion needs no shuffle:
+// A warp takes one row block (16 vertices):
 //
-//   Phase 1  selection test (CUDA cores): for each tile, the lane's two rows'
-//            bits; each set bit j is a neighbour u = 16 tcol + j, whose words
-//            of the lane's two solves (8 bytes) are compared with the row's.
-//            Candidates are marked in their words and in C_s.
-//   Phase 2  exclusion test (tensor cores): D = sum over tiles of A_t x C;
-//            an undecided entry with D > 0 is marked out.
+//   Phase 1  selection test (CUDA cores): lane (i, h) owns row i in solves
+//            4h .. 4h + 3; each set bit j of the row in a tile is a neighbour
+//            u = 16 tcol + j, whose four words (16 bytes) are compared with
+//            the row's.  Candidates are marked in their words and in C_s.
+//   Phase 2  exclusion test (tensor cores): D = sum over tiles of A_t x C.
+//            Lane (g, q), g = lane / 4 and q = lane % 4, receives the MMA
+//            entries D[g][2q], D[g][2q+1], D[g+8][2q], D[g+8][2q+1] and owns
+//            those rows and solves: an undecided entry with D > 0 is out.
 //   Phase 3  the row block stays on the worklist while any of its 16 x K
 //            entries is undecided.
 //
@@ -65,12 +64,6 @@ __device__ __forceinline__ unsigned und4(uint2 w0, uint2 w1) {
            ((w1.x >> 29) == 1u ? 4u : 0u) | ((w1.y >> 29) == 1u ? 8u : 0u);
 }
 
-// Solves (two bits) in which neighbour u (words wu of the lane's two solves)
-// outranks vertex v (words wv).
-__device__ __forceinline__ unsigned blocks2(uint2 wu, int u, uint2 wv, int v) {
-    return (outranks_m(wu.x, u, wv.x, v) ? 1u : 0u) | (outranks_m(wu.y, u, wv.y, v) ? 2u : 0u);
-}
-
 struct TmArgs {
     uint32_t* word8;   // kMaxMulti words per vertex, nrb * 16 vertices
     uint32_t* inb8;    // kMaxMulti bit vectors of nrb * 16 bits, `words` words apart
@@ -79,13 +72,31 @@ struct TmArgs {
     MultiSeeds seeds;
 };
 
-// Phase 1 over the row-block list.
+// Phase 1 over the row-block list.  Here lane (i, h), i = lane / 2 and
+// h = lane % 2, owns row i in solves 4h .. 4h + 3.  The row block's tiles
+// are taken two at a time: their column blocks and the row's bits are
+// loaded together, then the first two neighbours of the row in each of the
+// two tiles (the usual case; more are taken one by one), so that the words
+// of up to four neighbours (16 bytes each: the lane's four solves) are
+// loaded at once instead of one after another.
+constexpr int kSelTiles = 2;  // tiles per step
+constexpr int kSelBits = 2;   // neighbours per tile-row loaded in the batch
+__device__ __forceinline__ unsigned und_quad(uint4 w) {
+    return ((w.x >> 29) == 1u ? 1u : 0u) | ((w.y >> 29) == 1u ? 2u : 0u) |
+           ((w.z >> 29) == 1u ? 4u : 0u) | ((w.w >> 29) == 1u ? 8u : 0u);
+}
+
+__device__ __forceinline__ unsigned blocks4(uint4 wu, int u, uint4 wv, int v) {
+    return (outranks_m(wu.x, u, wv.x, v) ? 1u : 0u) | (outranks_m(wu.y, u, wv.y, v) ? 2u : 0u) |
+           (outranks_m(wu.z, u, wv.z, v) ? 4u : 0u) | (outranks_m(wu.w, u, wv.w, v) ? 8u : 0u);
+}
+
 __device__ __forceinline__ void tm_select(const SolveArgs& a, const TmArgs& m,
                                           const int32_t* __restrict__ list, int cnt,
                                           unsigned* grab, unsigned long long& alive) {
     if (cnt <= 0) return;
     const unsigned lane = lane_id();
-    const int g = (int)(lane >> 2), q = (int)(lane & 3);
+    const int i = (int)(lane >> 1), h = (int)(lane & 1);
     const int ch = tm_chunk(cnt);
     const long long gw = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (gw >= (cnt + ch - 1) / ch) return;
@@ -95,61 +106,76 @@ __device__ __forceinline__ void tm_select(const SolveArgs& a, const TmArgs& m,
         c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
         if (c0 >= cnt) break;
         const int c1 = min(c0 + ch, cnt);
+        // the next row block's id and tile range are loaded one item ahead
+        int rb_n = list[c0];
+        int t0_n = a.trp[rb_n], t1_n = a.trp[rb_n + 1];
         for (int item = c0; item < c1; ++item) {
-            const int rb = list[item];
-            const int v0 = rb * 16 + g, v1 = v0 + 8;
-            uint2 w0 = ld_pair(m.word8, v0, q), w1 = ld_pair(m.word8, v1, q);
-            const unsigned und = und4(w0, w1);
+            const int rb = rb_n, t0 = t0_n, t1 = t1_n;
+            if (item + 1 < c1) {
+                rb_n = list[item + 1];
+                t0_n = a.trp[rb_n];
+                t1_n = a.trp[rb_n + 1];
+            }
+            const int v = rb * 16 + i;
+            uint4* wp = reinterpret_cast<uint4*>(m.word8 + (size_t)kMaxMulti * v + 4 * h);
+            uint4 w = *wp;
+            const unsigned und = und_quad(w);
             alive += __popc(und);
             unsigned blocked = ~und & 0xFu;
-            const int t0 = a.trp[rb], t1 = a.trp[rb + 1];
-            for (int t = t0; t < t1; t += 2) {
-                // two tiles at a time: their loads are independent
-                const bool two = t + 1 < t1;
-                const int cb0 = __ldg(a.tcol + t), cb1 = two ? __ldg(a.tcol + t + 1) : 0;
-                uint32_t r00 = tile_row16(a.tbits, t, g), r08 = tile_row16(a.tbits, t, g + 8);
-                uint32_t r10 = two ? tile_row16(a.tbits, t + 1, g) : 0u;
-                uint32_t r18 = two ? tile_row16(a.tbits, t + 1, g + 8) : 0u;
-                if ((blocked & 3u) == 3u) r00 = r10 = 0u;
-                if ((blocked & 12u) == 12u) r08 = r18 = 0u;
-                // neighbours of row g, then of row g + 8, over both tiles
-                uint32_t bits0 = r00 | (r10 << 16), bits8 = r08 | (r18 << 16);
-                while (bits0 && (blocked & 3u) != 3u) {
-                    const int j = __ffs(bits0) - 1;
-                    bits0 &= bits0 - 1;
-                    const int u = (j < 16 ? cb0 : cb1) * 16 + (j & 15);
-                    blocked |= blocks2(ld_pair(m.word8, u, q), u, w0, v0);
-                }
-                while (bits8 && (blocked & 12u) != 12u) {
-                    const int j = __ffs(bits8) - 1;
-                    bits8 &= bits8 - 1;
-                    const int u = (j < 16 ? cb0 : cb1) * 16 + (j & 15);
-                    blocked |= blocks2(ld_pair(m.word8, u, q), u, w1, v1) << 2;
-                }
+            const uint32_t* w8 = m.word8 + 4 * h;
+            for (int tb = t0; tb < t1; tb += kSelTiles) {
                 if (!__any_sync(0xFFFFFFFFu, blocked != 0xFu)) break;
+                int cb[kSelTiles];
+                uint32_t bits[kSelTiles];
+#pragma unroll
+                for (int k = 0; k < kSelTiles; ++k) {
+                    const bool ok = tb + k < t1 && blocked != 0xFu;
+                    cb[k] = ok ? __ldg(a.tcol + tb + k) : 0;
+                    bits[k] = ok ? tile_row16(a.tbits, tb + k, i) : 0u;
+                }
+                constexpr int kU = kSelTiles * kSelBits;
+                int u[kU];
+                bool has[kU];
+#pragma unroll
+                for (int k = 0; k < kSelTiles; ++k) {
+#pragma unroll
+                    for (int r = 0; r < kSelBits; ++r) {
+                        has[kSelBits * k + r] = bits[k] != 0u;
+                        u[kSelBits * k + r] =
+                            cb[k] * 16 + (has[kSelBits * k + r] ? __ffs(bits[k]) - 1 : 0);
+                        bits[k] &= bits[k] - 1;
+                    }
+                }
+                uint4 wu[kU];
+#pragma unroll
+                for (int k = 0; k < kU; ++k)
+                    wu[k] = has[k] ? *reinterpret_cast<const uint4*>(w8 + (size_t)kMaxMulti * u[k])
+                                   : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int k = 0; k < kU; ++k)
+                    if (has[k]) blocked |= blocks4(wu[k], u[k], w, v);
+                // rows with more neighbours in a tile
+#pragma unroll
+                for (int k = 0; k < kSelTiles; ++k) {
+                    while (bits[k] && blocked != 0xFu) {
+                        const int uu = cb[k] * 16 + __ffs(bits[k]) - 1;
+                        bits[k] &= bits[k] - 1;
+                        blocked |= blocks4(*reinterpret_cast<const uint4*>(w8 + (size_t)kMaxMulti * uu),
+                                           uu, w, v);
+                    }
+                }
             }
             const unsigned cand = und & ~blocked;
-            if (cand & 3u) {
-                if (cand & 1u) {
-                    w0.x |= kWordInSet;
-                    atomicOr(m.inb8 + (size_t)(2 * q) * m.words + (v0 >> 5), 1u << (v0 & 31));
-                }
-                if (cand & 2u) {
-                    w0.y |= kWordInSet;
-                    atomicOr(m.inb8 + (size_t)(2 * q + 1) * m.words + (v0 >> 5), 1u << (v0 & 31));
-                }
-                st_pair(m.word8, v0, q, w0);
-            }
-            if (cand & 12u) {
-                if (cand & 4u) {
-                    w1.x |= kWordInSet;
-                    atomicOr(m.inb8 + (size_t)(2 * q) * m.words + (v1 >> 5), 1u << (v1 & 31));
-                }
-                if (cand & 8u) {
-                    w1.y |= kWordInSet;
-                    atomicOr(m.inb8 + (size_t)(2 * q + 1) * m.words + (v1 >> 5), 1u << (v1 & 31));
-                }
-                st_pair(m.word8, v1, q, w1);
+            if (cand) {
+                if (cand & 1u) w.x |= kWordInSet;
+                if (cand & 2u) w.y |= kWordInSet;
+                if (cand & 4u) w.z |= kWordInSet;
+                if (cand & 8u) w.w |= kWordInSet;
+                *wp = w;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if ((cand >> k) & 1u)
+                        atomicOr(m.inb8 + (size_t)(4 * h + k) * m.words + (v >> 5), 1u << (v & 31));
             }
         }
     }
@@ -178,10 +204,17 @@ __device__ __forceinline__ void tm_exclude(const SolveArgs& a, const TmArgs& m,
         if (c0 >= cnt) break;
         const int c1 = min(c0 + ch, cnt);
         int nkeep = 0;
+        int rb_n = list[c0];
+        int t0_n = a.trp[rb_n], t1_n = a.trp[rb_n + 1];
         for (int item = c0; item < c1; ++item) {
-            const int rb = list[item];
+            const int rb = rb_n, t0 = t0_n, t1 = t1_n;
+            if (item + 1 < c1) {
+                rb_n = list[item + 1];
+                t0_n = a.trp[rb_n];
+                t1_n = a.trp[rb_n + 1];
+            }
             int d[4];
-            rowblock_nc<P>(a.tbits, a.tpay, a.trp[rb], a.trp[rb + 1],
+            rowblock_nc<P>(a.tbits, a.tpay, t0, t1,
                            [&](int t) -> uint32_t {
                                return cseg ? (uint32_t)cseg[__ldg(a.tcol + t)] : 0u;
                            },
