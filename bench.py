@@ -503,6 +503,8 @@ def run_single(args):
         line["batch4096"] = batch_leg(args, native, local, world)
     if "serve" in legs:
         line["serve"] = serve_leg(args, native, local, world, rank)
+    if "tc" in legs:
+        line["tiles_tc"] = tc_leg(args, native, local, world)
     if rank == 0 and args.cpu_baseline:
         import oracle
         rate, dt, res, reps = oracle_rate(g, min_seconds=args.cpu_seconds)
@@ -610,6 +612,71 @@ def batch_leg(args, native, local, world):
         "standalone_check": {"graphs_checked": checked, "all_equal": same},
         "clocks": clocks,
     }
+
+
+def tc_leg(args, native, local, world):
+    """The tile paths on the grid with natural ids (the densest tiles of the
+    configured workloads): one solve per path and tile payload, and 8 seeds
+    per launch on the CSR rows (CUDA cores) against the tiles with the
+    exclusion product A x [C_1 .. C_8] on tensor cores, per payload form."""
+    import torch
+    (n, rp, col), desc = make_workload("grid")
+    stream = torch.cuda.current_stream().cuda_stream
+    drp = torch.from_numpy(rp).cuda()
+    dcol = torch.from_numpy(col).cuda()
+    h = native.mis_create_ex(n, drp.data_ptr(), dcol.data_ptr(), 1,
+                             native.options(device=local, order_rows=0), stream)
+    out = torch.empty(8 * n, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
+
+    def timeit(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(max(5, args.steps // 2)):
+            flush.add_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    seeds8 = np.arange(1, 9, dtype=np.uint64)
+    one = lambda: native.mis_solve_ex(h, [1], out.data_ptr(), stream)  # noqa: E731
+    eight = lambda: native.mis_solve_multi_ex(h, seeds8, out.data_ptr(), stream)  # noqa: E731
+    native.mis_autotune(h, 3)
+    res = {"graph": desc, "n": n, "arcs": int(rp[-1]), "single_ms": {}, "multi8_ms": {}}
+    res["single_ms"]["csr"] = timeit(one)
+    res["multi8_ms"]["csr"] = timeit(eight)
+    ref8 = out.clone()
+    for T in (8, 16):
+        native.mis_set_path(h, native.MIS_PATH_TILE, T)
+        res["single_ms"][f"tile{T}_popc"] = timeit(one)
+    res["tiles16"] = native.mis_get_stats(h).ntiles
+    names = {native.MIS_TILE_BITS: "bits_fp16", native.MIS_TILE_BITS_B1: "b1",
+             native.MIS_TILE_INT8: "int8", native.MIS_TILE_FP16: "fp16"}
+    same = True
+    exclude_us = {}
+    for p, nm in names.items():
+        native.mis_set_tile_payload(h, p)
+        native.mis_set_path(h, native.MIS_PATH_TILE_TC, 16)
+        res["single_ms"][f"tc_{nm}"] = timeit(one)
+        res["multi8_ms"][f"tc_{nm}"] = timeit(eight)
+        st = native.mis_get_stats(h)
+        exclude_us[nm] = [round(st.exclude_ns[r] / 1e3, 1) for r in range(min(st.rounds, 64))]
+        same &= bool(torch.equal(out, ref8))
+    native.mis_destroy(h)
+    best = min((k for k in res["multi8_ms"] if k != "csr"), key=lambda k: res["multi8_ms"][k])
+    res["multi_seed_tc"] = {
+        "k": 8, "best_form": best, "tc_launch_ms": res["multi8_ms"][best],
+        "csr_launch_ms": res["multi8_ms"]["csr"],
+        "tc_over_csr_speed": res["multi8_ms"]["csr"] / res["multi8_ms"][best],
+        "exclude_phase_us_per_round": exclude_us,
+        "results_equal_csr": same}
+    return res
 
 
 def run_batch(args):
@@ -910,15 +977,15 @@ def main():
     ap.add_argument("--dyn-steps", type=int, default=5)
     ap.add_argument("--legs", default=None,
                     help="extra legs of the single-graph run, comma separated: batch (the "
-                         "4096-graph union), serve (the served pool); default both for rmat22, "
-                         "none otherwise")
+                         "4096-graph union), serve (the served pool), tc (tile and tensor-core "
+                         "paths on the grid); default all for rmat22, none otherwise")
     ap.add_argument("--no-amortized", dest="amortized", action="store_false",
                     help="skip the solve on a graph with create-time round-0 structures")
     ap.add_argument("--multi", type=int, default=8,
                     help="also time this many seeds of the graph per launch (0 = off)")
     args = ap.parse_args()
     if args.legs is None:
-        args.legs = "batch,serve" if args.workload == "rmat22" else ""
+        args.legs = "batch,serve,tc" if args.workload == "rmat22" else ""
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch4096":

@@ -65,7 +65,7 @@ def test_single_graph_line():
 
 def test_single_graph_line_with_legs():
     d = _run("--workload", "er10k", "--steps", "3", "--warmup", "3", "--e2e-steps", "0",
-             "--no-cpu-baseline", "--multi", "0", "--legs", "batch,serve", "--batch-count", "64",
+             "--no-cpu-baseline", "--multi", "0", "--legs", "batch,serve,tc", "--batch-count", "64",
              "--pool", "8", "--requests", "400", "--serve-check", "32")
     b = d["batch4096"]
     assert b["graphs"] == 64 and b["graphs_per_s"] > 0
@@ -76,3 +76,6 @@ def test_single_graph_line_with_legs():
     for k in ("saturated", "poisson_0.5", "poisson_0.8", "poisson_1.0"):
         assert s[k]["p99_ms"] >= s[k]["p50_ms"] > 0
     assert s["standalone_check"]["all_equal"] is True
+    t = d["tiles_tc"]
+    assert t["multi_seed_tc"]["results_equal_csr"] is True
+    assert set(t["multi8_ms"]) == {"csr", "tc_bits_fp16", "tc_b1", "tc_int8", "tc_fp16"}
