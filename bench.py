@@ -49,7 +49,7 @@ if ROOT not in sys.path:
 METRIC = "edges/s to full MIS on 1 GB300"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-PATH_NAMES = {1: "csr", 2: "tile", 3: "tile_tc", 4: "push"}
+PATH_NAMES = {1: "csr", 2: "tile", 3: "tile_tc", 4: "push", 5: "cluster"}
 
 
 def _peak_hbm():

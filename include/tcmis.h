@@ -70,9 +70,14 @@ enum {
     MIS_PATH_TILE = 2,     /* tile-CSR kernel, bitmask payload, popc on CUDA cores */
     MIS_PATH_TILE_TC = 3,  /* tile-CSR kernel, exclusion test as tensor-core MMA
                               (payload form: mis_set_tile_payload) */
-    MIS_PATH_PUSH = 4      /* CSR, work-efficient push/decrement rounds: a count of
+    MIS_PATH_PUSH = 4,     /* CSR, work-efficient push/decrement rounds: a count of
                               undecided higher neighbours per vertex, decremented
                               as they are excluded; every arc read O(1) times */
+    MIS_PATH_CLUSTER = 5   /* single graphs of up to about half a million vertices:
+                              one thread-block cluster (up to 16 SMs) keeps every
+                              vertex word in its distributed shared memory and
+                              separates the phases by the hardware cluster
+                              barrier instead of a grid barrier */
 };
 
 typedef struct mis_graph mis_graph;
@@ -272,9 +277,15 @@ int mis_keys_ex(mis_graph *g, const uint64_t *seeds, uint32_t *out_key, void *st
 /* Select the round kernel for later solves.  MIS_PATH_CSR (or AUTO): `param`
  * is the lanes per row as in mis_options.threads_per_row.  MIS_PATH_TILE:
  * `param` is the tile size, 8 or 16 (0 = 16); MIS_PATH_TILE_TC: 16 (or 0).
+ * MIS_PATH_CLUSTER: single graphs that fit one cluster (MIS_EINVAL for a
+ * batch or a larger graph; mis_cluster_max_vertices gives the limit).
  * The tile-CSR (non-empty tiles only, 0/1 bitmask payloads) is built on the
  * device the first time a tile size is selected. */
 int mis_set_path(mis_graph *g, int32_t path, int32_t param);
+
+/* The most vertices a graph may have for MIS_PATH_CLUSTER on the current
+ * device (0 when no cluster fits). */
+int32_t mis_cluster_max_vertices(void);
 
 /* CSR path with degree bins: bounds[0..3] are the inclusive upper degrees of
  * bins 0..3 (1, 4, 16 and 32 lanes per row; bin 4, a block of 512 threads per

@@ -488,7 +488,9 @@ int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_
     if (e != cudaSuccess) return set_cuda_error(e, "control reset");
     if (d.n > 0) {
         const bool tile = g->path == MIS_PATH_TILE || g->path == MIS_PATH_TILE_TC;
-        if (g->path == MIS_PATH_PUSH) {
+        if (g->path == MIS_PATH_CLUSTER) {
+            e = launch_cluster_solve(a, g->cluster_ncta, g->cluster_shift, s);
+        } else if (g->path == MIS_PATH_PUSH) {
             const int maxb = push_max_coresident_blocks(d.device);
             if (maxb <= 0) return set_error(MIS_EDEVICE, "no co-resident blocks for the push kernel");
             long long grid = std::min<long long>(maxb, std::max<long long>(1, (d.n + 255) / 256));
@@ -694,6 +696,12 @@ std::string density_class(mis_graph* g, double apt) {
 int apply_choice(mis_graph* g, const TuneChoice& c) {
     if (c.path == MIS_PATH_TILE_TC) g->tile_payload = c.payload;
     if (c.path == MIS_PATH_TILE || c.path == MIS_PATH_TILE_TC) return use_tiles(g, c.path, c.param);
+    if (c.path == MIS_PATH_CLUSTER) {
+        if (g->d.count != 0 || !cluster_plan(g->d.n, &g->cluster_ncta, &g->cluster_shift))
+            return set_error(MIS_EINVAL, "graph too large for one thread-block cluster");
+        g->path = MIS_PATH_CLUSTER;
+        return MIS_OK;
+    }
     if (c.path == MIS_PATH_PUSH) {
         g->path = MIS_PATH_PUSH;
         return MIS_OK;
@@ -788,6 +796,11 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
     {
         TuneChoice t;
         t.path = MIS_PATH_PUSH;
+        cands.push_back(t);
+    }
+    if (g->d.count == 0 && g->d.n <= cluster_max_vertices()) {
+        TuneChoice t;
+        t.path = MIS_PATH_CLUSTER;
         cands.push_back(t);
     }
     if (apt >= 2.5) {
@@ -1167,7 +1180,7 @@ int mis_set_path(mis_graph* g, int32_t path, int32_t threads_per_row) {
     if (!g) return set_error(MIS_EINVAL, "null graph");
     if ((path == MIS_PATH_CSR || path == MIS_PATH_AUTO) && !valid_tpr(threads_per_row))
         return set_error(MIS_EINVAL, "bad threads_per_row");
-    if (path < MIS_PATH_AUTO || path > MIS_PATH_PUSH)
+    if (path < MIS_PATH_AUTO || path > MIS_PATH_CLUSTER)
         return set_error(MIS_EINVAL, "unknown path");
     std::lock_guard<std::mutex> lk(g->mu);
     if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
@@ -1177,6 +1190,13 @@ int mis_set_path(mis_graph* g, int32_t path, int32_t threads_per_row) {
         return use_tiles(g, path, threads_per_row ? threads_per_row : 16);
     if (path == MIS_PATH_PUSH) {
         g->path = MIS_PATH_PUSH;
+        return MIS_OK;
+    }
+    if (path == MIS_PATH_CLUSTER) {
+        if (g->d.count != 0) return set_error(MIS_EINVAL, "the cluster path takes a single graph");
+        if (!cluster_plan(g->d.n, &g->cluster_ncta, &g->cluster_shift))
+            return set_error(MIS_EINVAL, "graph too large for one thread-block cluster");
+        g->path = MIS_PATH_CLUSTER;
         return MIS_OK;
     }
     g->path = MIS_PATH_CSR;
@@ -1297,6 +1317,11 @@ int mis_set_grid(mis_graph* g, int32_t blocks) {
 }
 
 int32_t mis_get_grid(const mis_graph* g) { return g ? g->grid : 0; }
+
+int32_t mis_cluster_max_vertices(void) {
+    clear_error();
+    return cluster_max_vertices();
+}
 
 int mis_tiles_ex(mis_graph* g, int32_t* trp, int32_t* tcol, uint64_t* tbits, void* stream) {
     clear_error();

@@ -219,6 +219,14 @@ cudaError_t build_tiles(const int32_t* rp, const int32_t* col, int32_t n, int64_
 cudaError_t launch_tile_solve(const SolveArgs& a, int T, int S, int tc_payload, int grid,
                               cudaStream_t s);
 int tile_max_coresident_blocks(int T, int S, int tc_payload, int device);
+// kernels_cluster.cu: a single graph solved by one thread-block cluster (its
+// vertex words in the CTAs' shared memory, cluster barriers between phases);
+// graphs of up to cluster_max_vertices() vertices (0: no cluster fits).
+int32_t cluster_max_vertices();
+// The cluster for n vertices: ncta CTAs of 2^shift words each (false: none).
+// Sets the kernel's attributes; call it before a launch is captured.
+bool cluster_plan(int32_t n, int* ncta, int* shift);
+cudaError_t launch_cluster_solve(const SolveArgs& a, int ncta, int shift, cudaStream_t s);
 // kernels_tile_multi.cu: k <= kMaxMulti solves of the graph of `a` on its
 // 16 x 16 tiles (a.trp, a.tcol, a.tbits, a.tpay; a.rbl0/1 row-block lists),
 // the exclusion test on tensor cores in payload form `payload` with the k

@@ -35,6 +35,7 @@ MIS_PATH_CSR = 1
 MIS_PATH_TILE = 2
 MIS_PATH_TILE_TC = 3
 MIS_PATH_PUSH = 4
+MIS_PATH_CLUSTER = 5
 MIS_PRIORITY_EQ1 = 0
 MIS_PRIORITY_HASH = 1
 MIS_PRIORITY_EQ1_Q8 = 2
@@ -139,6 +140,8 @@ def lib():
         L.mis_replay_destroy.restype = None
         L.mis_set_csr_pending.argtypes = [P, i32]
         L.mis_set_csr_pending.restype = ctypes.c_int
+        L.mis_cluster_max_vertices.argtypes = []
+        L.mis_cluster_max_vertices.restype = i32
         L.mis_tile_payload_ex.argtypes = [P, i32, P, P]
         L.mis_tile_payload_ex.restype = ctypes.c_int
         L.mis_set_tile_payload.argtypes = [P, i32]
@@ -182,7 +185,7 @@ def lib():
 EXPORTED = [
     "mis_options_init", "mis_create", "mis_create_ex", "mis_create_batch", "mis_graph_count",
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
-    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_set_csr_range0", "mis_set_tile_payload", "mis_tile_payload_ex", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
+    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_set_csr_range0", "mis_set_tile_payload", "mis_tile_payload_ex", "mis_cluster_max_vertices", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
     "mis_solve_noalloc", "mis_update_edges", "mis_repair", "mis_add_vertices",
 ]
