@@ -97,6 +97,8 @@ def test_noalloc_allocates_nothing():
     stream = torch.cuda.current_stream().cuda_stream
     native.mis_solve_noalloc(n, drp.data_ptr(), dcol.data_ptr(), 1, out.data_ptr(), stream)
     torch.cuda.synchronize()
+    import gc
+    gc.collect()  # tensors of earlier tests freed now, not during the measured calls
     free0, _ = torch.cuda.mem_get_info()
     reserved0 = torch.cuda.memory_reserved()
     allocated0 = torch.cuda.memory_allocated()
@@ -106,7 +108,8 @@ def test_noalloc_allocates_nothing():
     free1, _ = torch.cuda.mem_get_info()
     assert free1 == free0
     assert torch.cuda.memory_reserved() == reserved0
-    assert torch.cuda.memory_allocated() == allocated0
+    # a call that allocated through the pool would raise this count
+    assert torch.cuda.memory_allocated() <= allocated0
     assert np.array_equal(out.cpu().numpy(), _regular(g, 4))
 
 
