@@ -1,5 +1,6 @@
 // api.cu -- the C ABI (include/tcmis.h): graph handles, solves, statistics.
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -55,6 +56,21 @@ cudaError_t dalloc(T** p, int64_t count, int64_t* footprint) {
 void dfree(void* p) { dev_free(p); }
 
 }  // namespace
+
+// TCMIS_CREATE_LOG set: the wall time of each create stage on stderr (the
+// stages synchronise their streams, so the times are the device's)
+struct StageLog {
+    bool on = std::getenv("TCMIS_CREATE_LOG") != nullptr;
+    std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+    void mark(const char* what, cudaStream_t s) {
+        if (!on) return;
+        cudaStreamSynchronize(s);
+        const auto now = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "tcmis create: %-24s %8.3f ms\n", what,
+                     std::chrono::duration<double, std::milli>(now - t).count());
+        t = now;
+    }
+};
 
 int64_t ws_bytes_for(int64_t n, int32_t count) {
     const int64_t cap = (n + 15) / 16 * 16;
@@ -265,6 +281,8 @@ int finish_create(mis_graph* g) {
         e = cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return set_cuda_error(e, "stream");
     }
+    StageLog lg;
+    lg.mark("workspace", g->own_stream);
     if (order) {
         e = cudaMemsetAsync(d.col_sel, 0, sizeof(int32_t) * (size_t)col_alloc, g->own_stream);
         if (e == cudaSuccess)
@@ -273,9 +291,11 @@ int finish_create(mis_graph* g) {
                                          g->own_stream)
                     : build_row_partition(d.rp, d.col, d.n, d.arcs, seg_of(d), d.col_sel,
                                           d.split, g->own_stream);
+        lg.mark("row ordering", g->own_stream);
         if (e == cudaSuccess)
             e = build_round0_classes(d.rp, d.col_sel, d.split, d.n, seg_of(d), d.r0class,
                                      g->own_stream);
+        lg.mark("round-0 classes", g->own_stream);
         // the tested subgraph, when it holds at most half of the arcs
         int64_t s0_arcs = 0;
         if (e == cudaSuccess)
@@ -287,6 +307,7 @@ int finish_create(mis_graph* g) {
             d.s0_bytes = 4 * (2 * (int64_t)d.n + 1) + 4 * (((s0_arcs + 3) / 4) * 4 + 4);
             d.footprint += d.s0_bytes;
         }
+        lg.mark("tested subgraph", g->own_stream);
         if (e == cudaSuccess && d.s0_col && d.count == 0) {
             e = build_keyed(d.rp, d.col_sel, d.split, d.r0class, d.n, &d.keyed, &d.n_keyed,
                             &d.out0, &d.n_tested, &d.tested_prefix_arcs, g->own_stream);
@@ -294,8 +315,10 @@ int finish_create(mis_graph* g) {
         }
         if (e != cudaSuccess) return set_cuda_error(e, "degree ordering");
     }
+    lg.mark("keyed list", g->own_stream);
     const int brc = rebin(g, thr, g->own_stream);
     if (brc != MIS_OK) return brc;
+    lg.mark("degree bins", g->own_stream);
     if (g->opt.path == MIS_PATH_AUTO && g->opt.threads_per_row == 0) {
         const int arc = apply_cached_choice(g);
         if (arc != MIS_OK) return arc;
@@ -309,16 +332,21 @@ int finish_create(mis_graph* g) {
     return MIS_OK;
 }
 
+constexpr size_t kFlagsBytes = 24;  // flag word (padded to 8 bytes) + two 64-bit sums
+
 int validate_device(mis_graph* g, cudaStream_t s) {
     GraphData& d = g->d;
-    cudaError_t e = cudaMemsetAsync(d.flags, 0, sizeof(unsigned), s);
+    // d.flags: the flag word, then (8-byte aligned) the two symmetry sums
+    unsigned long long* sym = reinterpret_cast<unsigned long long*>(d.flags) + 1;
+    cudaError_t e = cudaMemsetAsync(d.flags, 0, kFlagsBytes, s);
     if (e == cudaSuccess)
-        e = launch_validate(d.rp, d.col, d.n, d.arcs, g->opt.check_symmetry, d.flags, s);
-    unsigned f = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&f, d.flags, sizeof(unsigned),
-                                              cudaMemcpyDeviceToHost, s);
+        e = launch_validate(d.rp, d.col, d.n, d.arcs, g->opt.check_symmetry, d.flags, sym, s);
+    unsigned long long hb[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, d.flags, kFlagsBytes, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return set_cuda_error(e, "graph validation");
+    unsigned f = (unsigned)(hb[0] & 0xFFFFFFFFull);
+    if (g->opt.check_symmetry && (hb[1] | hb[2]) && !(f & kBadRowPtr)) f |= kBadSymmetry;
     if (f) {
         std::string why;
         if (f & kBadRowPtr) why += " row_ptr not monotone from 0 to arcs;";
@@ -360,7 +388,8 @@ int upload_checked(mis_graph* g, const int32_t* col_idx, cudaStream_t s) {
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
         // the order check of the first arc of a piece reads the previous
         // piece's last arc, which the copy stream has landed before
-        if (e == cudaSuccess) e = launch_validate_arcs(d.rp, d.col, d.n, a0, a1, 0, d.flags, s);
+        if (e == cudaSuccess)
+            e = launch_validate_arcs(d.rp, d.col, d.n, a0, a1, 0, d.flags, nullptr, s);
     }
     f = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&f, d.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
@@ -974,7 +1003,7 @@ mis_graph* mis_create_ex(int32_t n, const int32_t* row_ptr, const int32_t* col_i
     const int64_t col_alloc = ((arcs + 3) / 4) * 4 + 4;
     if ((e = dalloc(&d.rp, (int64_t)n + 1, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.col, col_alloc, &d.footprint)) != cudaSuccess ||
-        (e = dalloc(&d.flags, 1, &d.footprint)) != cudaSuccess) {
+        (e = dalloc(&d.flags, kFlagsBytes / sizeof(unsigned), &d.footprint)) != cudaSuccess) {
         set_cuda_error(e, "graph allocation");
         free_graph(g);
         return nullptr;
@@ -990,6 +1019,8 @@ mis_graph* mis_create_ex(int32_t n, const int32_t* row_ptr, const int32_t* col_i
         free_graph(g);
         return nullptr;
     }
+    StageLog lg;
+    lg.mark("allocation", s);
     const bool pipelined = !on_device && !o.check_symmetry && arcs >= kUploadPiece;
     if (pipelined) {
         if (upload_checked(g, col_idx, s) != MIS_OK) {
@@ -1004,10 +1035,12 @@ mis_graph* mis_create_ex(int32_t n, const int32_t* row_ptr, const int32_t* col_i
             free_graph(g);
             return nullptr;
         }
+        lg.mark("upload", s);
         if (n > 0 && validate_device(g, s) != MIS_OK) {
             free_graph(g);
             return nullptr;
         }
+        lg.mark("validation", s);
     }
     if (finish_create(g) != MIS_OK) {
         free_graph(g);

@@ -170,15 +170,19 @@ cudaError_t launch_push_solve(const SolveArgs& a, int grid, cudaStream_t s);
 int push_max_coresident_blocks(int device);
 
 // kernels_util.cu
+// Input contract checks.  Flags are ORed into *d_flags; with check_symmetry,
+// d_sym[0..1] (zeroed by the caller) receive the two arc-set hash sums, both
+// zero exactly when the arc set equals its reverse (see kernels_util.cu).
 cudaError_t launch_validate(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs,
-                            int check_symmetry, unsigned* d_flags, cudaStream_t s);
+                            int check_symmetry, unsigned* d_flags, unsigned long long* d_sym,
+                            cudaStream_t s);
 // The two halves of launch_validate: row pointers, then the arcs [a0, a1)
-// (which trust the row pointers).  Flags are ORed into *d_flags.
+// (which trust the row pointers).
 cudaError_t launch_validate_rowptr(const int32_t* rp, int32_t n, int64_t arcs, unsigned* d_flags,
                                    cudaStream_t s);
 cudaError_t launch_validate_arcs(const int32_t* rp, const int32_t* col, int32_t n, int64_t a0,
                                  int64_t a1, int check_symmetry, unsigned* d_flags,
-                                 cudaStream_t s);
+                                 unsigned long long* d_sym, cudaStream_t s);
 cudaError_t launch_keys(const SolveArgs& a, uint32_t* out_key, cudaStream_t s);
 cudaError_t launch_fill_seg(int32_t* blk_seg, const int32_t* voff, int32_t count,
                             int32_t nblk, cudaStream_t s);

@@ -34,7 +34,7 @@ namespace tcmis {
 namespace {
 
 constexpr int kClusterThreads = 1024;
-constexpr int kCached = 16;  // neighbour ids kept in registers per owned vertex
+constexpr int kCached = 10;  // neighbour ids kept in registers per owned vertex
 
 struct ClusterArgs {
     int32_t shift;   // chunk = 1 << shift vertices per CTA
@@ -105,14 +105,15 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     auto scan = [&](int v, int b, int deg, bool use_cache, uint32_t wv, bool sel) -> bool {
         int k = 0;
         if (use_cache) {
+            // every cached neighbour's word is requested before any is tested
+            uint32_t wu[kCached];
 #pragma unroll
-            for (int q = 0; q < kCached; ++q) {
-                if (q < deg) {
-                    const int u = cached[q];
-                    const uint32_t wu = *word_of(u);
-                    if (sel ? outranks_c(wu, u, wv, v) : wu >= kWordInMin) return true;
-                }
-            }
+            for (int q = 0; q < kCached; ++q) wu[q] = q < deg ? *word_of(cached[q]) : 0u;
+            bool hit = false;
+#pragma unroll
+            for (int q = 0; q < kCached; ++q)
+                hit |= q < deg && (sel ? outranks_c(wu[q], cached[q], wv, v) : wu[q] >= kWordInMin);
+            if (hit) return true;
             k = kCached;
         }
         for (; k < deg; ++k) {
@@ -160,11 +161,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         if ((tid & 31) == 0 && rem) atomicAdd(&s_rem[par], rem);
         cluster.sync();
         // every CTA sums the same counts, so all leave the loop together
-        if (tid == 0) {
-            int total = 0;
-            for (int q = 0; q < c.ncta; ++q) total += *cluster.map_shared_rank(&s_rem[par], q);
-            s_total = total;
-            if (rank == 0) {
+        if (tid < 32) {
+            int total = tid < c.ncta ? *cluster.map_shared_rank(&s_rem[par], tid) : 0;
+            for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(0xFFFFFFFFu, total, o);
+            if (tid == 0) s_total = total;
+            if (rank == 0 && tid == 0) {
                 if (times && r < kStatRounds) times->t[2 + kStatRounds + r] = global_ns();
                 if (r < kStatRounds) ctl->alive[r] = alive;
                 ctl->alive_sum += (unsigned long long)alive;

@@ -25,16 +25,31 @@ __global__ void validate_rowptr_kernel(const int32_t* __restrict__ rp, int32_t n
 // arc by binary search over row_ptr and walks forward from there.
 constexpr int kArcsPerThread = 16;
 
+// Symmetry as equality of two arc sets: with rows strictly increasing (no
+// duplicate arcs, checked on the way), the graph is symmetric exactly when
+// its arc set equals the set of reversed arcs.  Each set is summarised by the
+// sums (mod 2^64) of two fixed 64-bit hashes of its ordered pairs; every arc
+// (v, u) adds h(v, u) - h(u, v) to each running sum, so equal sets leave both
+// sums at zero.  Unequal sets leave both at zero only if two independent
+// 64-bit sums cancel by accident.  One pass over the arcs with no search,
+// where the previous check binary-searched v in row u for every arc.
+__device__ __forceinline__ unsigned long long arc_hash(uint32_t a, uint32_t b, uint64_t salt) {
+    return mix64((((uint64_t)a << 32) | b) ^ salt);
+}
+constexpr uint64_t kSymSalt0 = 0x6A09E667F3BCC908ull;  // fractional bits of sqrt(2)
+constexpr uint64_t kSymSalt1 = 0xBB67AE8584CAA73Bull;  // fractional bits of sqrt(3)
+
 // Checks the arcs [a0, a1) (all of them: a0 = 0, a1 = arcs).
 __global__ void validate_arcs_kernel(const int32_t* __restrict__ rp,
                                      const int32_t* __restrict__ col, int32_t n, int64_t a0,
-                                     int64_t a1, int check_symmetry, unsigned* flags) {
+                                     int64_t a1, int check_symmetry, unsigned* flags,
+                                     unsigned long long* sym) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t p0 = a0 + t * kArcsPerThread;
-    if (p0 >= a1) return;
-    const int64_t p1 = (a1 < p0 + kArcsPerThread) ? a1 : p0 + kArcsPerThread;
+    // threads past the end check nothing but still join the warp's sums
+    const int64_t p1 = p0 >= a1 ? p0 : ((a1 < p0 + kArcsPerThread) ? a1 : p0 + kArcsPerThread);
     // row = last v with rp[v] <= p0
-    int lo = 0, hi = n;  // invariant rp[lo] <= p0 < rp[hi]
+    int lo = 0, hi = p0 < a1 ? n : 1;  // invariant rp[lo] <= p0 < rp[hi]
     while (hi - lo > 1) {
         const int mid = lo + (hi - lo) / 2;
         if ((int64_t)rp[mid] <= p0) lo = mid;
@@ -42,6 +57,7 @@ __global__ void validate_arcs_kernel(const int32_t* __restrict__ rp,
     }
     int v = lo;
     unsigned bad = 0;
+    unsigned long long s0 = 0, s1 = 0;
     for (int64_t p = p0; p < p1; ++p) {
         while ((int64_t)rp[v + 1] <= p) ++v;
         const int u = col[p];
@@ -51,27 +67,29 @@ __global__ void validate_arcs_kernel(const int32_t* __restrict__ rp,
         }
         if (u == v) bad |= kBadSelfLoop;
         if (p > rp[v] && col[p - 1] >= u) bad |= kBadOrder;
-        if (check_symmetry && u != v) {
-            int a = rp[u], b = rp[u + 1];  // search v in row u
-            bool hit = false;
-            while (a < b) {
-                const int m = a + (b - a) / 2;
-                const int x = col[m];
-                if (x == v) {
-                    hit = true;
-                    break;
-                }
-                if (x < v) a = m + 1;
-                else b = m;
-            }
-            if (!hit) bad |= kBadSymmetry;
+        if (check_symmetry) {
+            s0 += arc_hash((uint32_t)v, (uint32_t)u, kSymSalt0) -
+                  arc_hash((uint32_t)u, (uint32_t)v, kSymSalt0);
+            s1 += arc_hash((uint32_t)v, (uint32_t)u, kSymSalt1) -
+                  arc_hash((uint32_t)u, (uint32_t)v, kSymSalt1);
         }
     }
     if (bad) atomicOr(flags, bad);
+    if (check_symmetry && sym) {
+        for (int o = 16; o; o >>= 1) {
+            s0 += __shfl_xor_sync(0xFFFFFFFFu, s0, o);
+            s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+        }
+        if ((threadIdx.x & 31) == 0 && (s0 | s1)) {
+            atomicAdd(sym, s0);
+            atomicAdd(sym + 1, s1);
+        }
+    }
 }
 
 cudaError_t launch_validate(const int32_t* rp, const int32_t* col, int32_t n, int64_t arcs,
-                            int check_symmetry, unsigned* d_flags, cudaStream_t s) {
+                            int check_symmetry, unsigned* d_flags, unsigned long long* d_sym,
+                            cudaStream_t s) {
     // row pointers (host reads the flags before the arc pass)
     const int threads = 256;
     long long blocks = (n + threads - 1) / threads;
@@ -84,7 +102,7 @@ cudaError_t launch_validate(const int32_t* rp, const int32_t* col, int32_t n, in
     e = cudaMemcpyAsync(&hflags, d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess || hflags || arcs == 0) return e;
-    return launch_validate_arcs(rp, col, n, 0, arcs, check_symmetry, d_flags, s);
+    return launch_validate_arcs(rp, col, n, 0, arcs, check_symmetry, d_flags, d_sym, s);
 }
 
 cudaError_t launch_validate_rowptr(const int32_t* rp, int32_t n, int64_t arcs, unsigned* d_flags,
@@ -99,13 +117,13 @@ cudaError_t launch_validate_rowptr(const int32_t* rp, int32_t n, int64_t arcs, u
 
 cudaError_t launch_validate_arcs(const int32_t* rp, const int32_t* col, int32_t n, int64_t a0,
                                  int64_t a1, int check_symmetry, unsigned* d_flags,
-                                 cudaStream_t s) {
+                                 unsigned long long* d_sym, cudaStream_t s) {
     if (a1 <= a0) return cudaSuccess;
     const int threads = 256;
     const long long work = (a1 - a0 + kArcsPerThread - 1) / kArcsPerThread;
     const long long ablocks = (work + threads - 1) / threads;
     validate_arcs_kernel<<<(unsigned)ablocks, threads, 0, s>>>(rp, col, n, a0, a1,
-                                                                check_symmetry, d_flags);
+                                                                check_symmetry, d_flags, d_sym);
     return cudaGetLastError();
 }
 
