@@ -1125,7 +1125,7 @@ mis_graph* mis_create_batch(int32_t count, const int32_t* ns, const int32_t* con
     const int64_t nblk = N / 16;
     if ((e = dalloc(&d.rp, N + 1, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.col, col_alloc, &d.footprint)) != cudaSuccess ||
-        (e = dalloc(&d.flags, 1, &d.footprint)) != cudaSuccess ||
+        (e = dalloc(&d.flags, kFlagsBytes / sizeof(unsigned), &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.blk_seg, nblk, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.voff, count, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.nv, count, &d.footprint)) != cudaSuccess ||
