@@ -518,7 +518,7 @@ int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_
     if (d.n > 0) {
         const bool tile = g->path == MIS_PATH_TILE || g->path == MIS_PATH_TILE_TC;
         if (g->path == MIS_PATH_CLUSTER) {
-            e = launch_cluster_solve(a, g->cluster_ncta, g->cluster_shift, s);
+            e = launch_cluster_solve(a, g->cluster, s);
         } else if (g->path == MIS_PATH_PUSH) {
             const int maxb = push_max_coresident_blocks(d.device);
             if (maxb <= 0) return set_error(MIS_EDEVICE, "no co-resident blocks for the push kernel");
@@ -726,7 +726,7 @@ int apply_choice(mis_graph* g, const TuneChoice& c) {
     if (c.path == MIS_PATH_TILE_TC) g->tile_payload = c.payload;
     if (c.path == MIS_PATH_TILE || c.path == MIS_PATH_TILE_TC) return use_tiles(g, c.path, c.param);
     if (c.path == MIS_PATH_CLUSTER) {
-        if (g->d.count != 0 || !cluster_plan(g->d.n, &g->cluster_ncta, &g->cluster_shift))
+        if (g->d.count != 0 || !cluster_plan(g->d.rp, g->d.n, &g->cluster))
             return set_error(MIS_EINVAL, "graph too large for one thread-block cluster");
         g->path = MIS_PATH_CLUSTER;
         return MIS_OK;
@@ -1227,7 +1227,7 @@ int mis_set_path(mis_graph* g, int32_t path, int32_t threads_per_row) {
     }
     if (path == MIS_PATH_CLUSTER) {
         if (g->d.count != 0) return set_error(MIS_EINVAL, "the cluster path takes a single graph");
-        if (!cluster_plan(g->d.n, &g->cluster_ncta, &g->cluster_shift))
+        if (!cluster_plan(g->d.rp, g->d.n, &g->cluster))
             return set_error(MIS_EINVAL, "graph too large for one thread-block cluster");
         g->path = MIS_PATH_CLUSTER;
         return MIS_OK;

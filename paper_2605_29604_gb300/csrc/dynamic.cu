@@ -222,8 +222,7 @@ int adopt_csr(mis_graph* g, int32_t n, const int32_t* rp, const int32_t* col, vo
     g->csr_pending = g2->csr_pending;
     g->csr_range0 = g2->csr_range0;
     g->tile_payload = g2->tile_payload;
-    g->cluster_ncta = g2->cluster_ncta;
-    g->cluster_shift = g2->cluster_shift;
+    g->cluster = g2->cluster;
     mis_destroy(g2);  // frees the old graph's data
     return MIS_OK;
 }

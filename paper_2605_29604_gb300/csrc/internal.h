@@ -227,10 +227,18 @@ int tile_max_coresident_blocks(int T, int S, int tc_payload, int device);
 // vertex words in the CTAs' shared memory, cluster barriers between phases);
 // graphs of up to cluster_max_vertices() vertices (0: no cluster fits).
 int32_t cluster_max_vertices();
-// The cluster for n vertices: ncta CTAs of 2^shift words each (false: none).
-// Sets the kernel's attributes; call it before a launch is captured.
-bool cluster_plan(int32_t n, int* ncta, int* shift);
-cudaError_t launch_cluster_solve(const SolveArgs& a, int ncta, int shift, cudaStream_t s);
+// The cluster for a graph (d_rp: its row_ptr on the device, n vertices): ncta
+// CTAs of 2^shift words each, rows in shared memory or not, the dynamic
+// shared memory of a CTA; false when none fits.  Sets the kernel's
+// attributes; call it before a launch is captured.
+struct ClusterPlan {
+    int32_t ncta = 0;
+    int32_t shift = 0;
+    int32_t smem_rows = 0;
+    int64_t smem_bytes = 0;
+};
+bool cluster_plan(const int32_t* d_rp, int32_t n, ClusterPlan* plan);
+cudaError_t launch_cluster_solve(const SolveArgs& a, const ClusterPlan& p, cudaStream_t s);
 // kernels_tile_multi.cu: k <= kMaxMulti solves of the graph of `a` on its
 // 16 x 16 tiles (a.trp, a.tcol, a.tbits, a.tpay; a.rbl0/1 row-block lists),
 // the exclusion test on tensor cores in payload form `payload` with the k

@@ -13,9 +13,11 @@
 //            (barrier.cluster arrive/wait through cooperative groups), which
 //            every CTA reaches the same number of times: the loop exit is
 //            decided from counts that all CTAs read after the same barrier;
-//   rows     a thread that owns one vertex keeps up to kCached neighbour ids
-//            in registers for all rounds; longer rows, and threads with
-//            several vertices, read their rows from global memory each round.
+//   rows     where they fit, each CTA copies its vertices' row offsets and
+//            arcs into shared memory once (coalesced loads at init), so every
+//            later scan reads its row on chip; otherwise rows are read from
+//            global memory.  A scan requests kBatch neighbour words before it
+//            tests any of them.
 //
 // Phase 1 (selection test) and Phase 2 (exclusion test, state update) read
 // the round-start snapshot exactly as the grid kernel does (see common.cuh),
@@ -34,11 +36,13 @@ namespace tcmis {
 namespace {
 
 constexpr int kClusterThreads = 1024;
-constexpr int kCached = 10;  // neighbour ids kept in registers per owned vertex
+constexpr int kBatch = 8;  // neighbour words requested at once by a thread
 
 struct ClusterArgs {
-    int32_t shift;   // chunk = 1 << shift vertices per CTA
-    int32_t ncta;    // CTAs in the cluster
+    int32_t shift;      // chunk = 1 << shift vertices per CTA
+    int32_t ncta;       // CTAs in the cluster
+    int32_t smem_rows;  // 1: each CTA holds its rows (row_ptr and col_idx slices)
+                        // in shared memory; 0: rows are read from global memory
 };
 
 __device__ __forceinline__ bool outranks_c(uint32_t wu, int u, uint32_t wv, int v) {
@@ -47,17 +51,23 @@ __device__ __forceinline__ bool outranks_c(uint32_t wu, int u, uint32_t wv, int 
 
 __global__ void __launch_bounds__(kClusterThreads, 1)
     cluster_solve_kernel(const SolveArgs a, const ClusterArgs c) {
-    extern __shared__ uint32_t s_word[];  // this CTA's chunk of vertex words
-    __shared__ int s_rem[2];              // this CTA's undecided count, by round parity
-    __shared__ unsigned s_sel;            // candidates this CTA selected
+    // shared memory: this CTA's chunk of vertex words, then (smem_rows) the
+    // row offsets of its vertices relative to its first arc and its arcs
+    extern __shared__ uint32_t s_dyn[];
+    __shared__ int s_rem[2];  // this CTA's undecided count, by round parity
+    __shared__ unsigned s_sel;
     __shared__ int s_total;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int chunk = 1 << c.shift;
     const int32_t n = a.n;
     const int base = rank * chunk;
+    const int cnt = max(0, min(chunk, n - base));  // this CTA's vertices
     const int tid = (int)threadIdx.x;
     const int nth = (int)blockDim.x;
+    uint32_t* s_word = s_dyn;
+    int32_t* s_rp = reinterpret_cast<int32_t*>(s_dyn + chunk);
+    int32_t* s_col = s_rp + chunk + 1;
     Ctl* ctl = a.ctl;
     PhaseTimes* times = a.times;
     const int mode = a.priority;
@@ -69,57 +79,57 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         if (rank == 0 && times) times->t[0] = global_ns();
     }
     // the word of vertex u, wherever it lives in the cluster
-    auto word_of = [&](int u) -> uint32_t* {
+    auto word_of = [&](int u) -> const uint32_t* {
         return cluster.map_shared_rank(s_word + (u & (chunk - 1)), u >> c.shift);
     };
 
-    // ---- init: Eq. 1 priorities; isolated vertices straight into the set
-    // (and the result); the owned row cached when a thread has one vertex
-    const bool single = chunk <= nth;
-    int cached[kCached];
-    int my_b = 0, my_deg = 0;
+    // ---- init: the CTA's rows into shared memory (coalesced copies), then
+    // Eq. 1 priorities; isolated vertices straight into the set and result
+    const int arc0 = cnt > 0 ? a.rp[base] : 0;
+    if (c.smem_rows && cnt > 0) {
+        const int arc1 = a.rp[base + cnt];
+        for (int k = tid; k <= cnt; k += nth) s_rp[k] = a.rp[base + k] - arc0;
+        for (int p = tid; p < arc1 - arc0; p += nth) s_col[p] = __ldg(a.col + arc0 + p);
+    }
     for (int k = tid; k < chunk; k += nth) {
         const int v = base + k;
         uint32_t w = kWordOut;
         if (v < n) {
-            const int b = a.rp[v], deg = a.rp[v + 1] - b;
+            const int deg = a.rp[v + 1] - a.rp[v];
             w = deg ? undecided_word(mode, priority_key(mode, dbar, deg, smix, (uint32_t)v))
                     : (kKeyIsolated | kWordInSet);
             if (a.out) a.out[v] = deg ? 0 : 1;
-            if (single) {
-                my_b = b;
-                my_deg = deg;
-            }
         }
         s_word[k] = w;
-    }
-    if (single) {
-#pragma unroll
-        for (int k = 0; k < kCached; ++k) cached[k] = k < my_deg ? __ldg(a.col + my_b + k) : 0;
     }
     cluster.sync();
     if (rank == 0 && tid == 0 && times) times->t[1] = global_ns();
 
-    // Scan of v's row: kSelect: does an undecided or selected neighbour
-    // outrank v (word wv), else: is a neighbour in the set.
-    auto scan = [&](int v, int b, int deg, bool use_cache, uint32_t wv, bool sel) -> bool {
-        int k = 0;
-        if (use_cache) {
-            // every cached neighbour's word is requested before any is tested
-            uint32_t wu[kCached];
+    // Scan of the row of v (local index k): sel: does an undecided or
+    // selected neighbour outrank v (word wv); else: is a neighbour in the set.
+    // kBatch neighbour words are requested before any of them is tested.
+    auto scan = [&](int k, int v, uint32_t wv, bool sel) -> bool {
+        const int32_t* row;
+        int deg;
+        if (c.smem_rows) {
+            row = s_col + s_rp[k];
+            deg = s_rp[k + 1] - s_rp[k];
+        } else {
+            row = a.col + a.rp[v];
+            deg = a.rp[v + 1] - a.rp[v];
+        }
+        for (int q0 = 0; q0 < deg; q0 += kBatch) {
+            int u[kBatch];
+            uint32_t wu[kBatch];
 #pragma unroll
-            for (int q = 0; q < kCached; ++q) wu[q] = q < deg ? *word_of(cached[q]) : 0u;
+            for (int q = 0; q < kBatch; ++q) u[q] = q0 + q < deg ? row[q0 + q] : 0;
+#pragma unroll
+            for (int q = 0; q < kBatch; ++q) wu[q] = q0 + q < deg ? *word_of(u[q]) : 0u;
             bool hit = false;
 #pragma unroll
-            for (int q = 0; q < kCached; ++q)
-                hit |= q < deg && (sel ? outranks_c(wu[q], cached[q], wv, v) : wu[q] >= kWordInMin);
+            for (int q = 0; q < kBatch; ++q)
+                hit |= q0 + q < deg && (sel ? outranks_c(wu[q], u[q], wv, v) : wu[q] >= kWordInMin);
             if (hit) return true;
-            k = kCached;
-        }
-        for (; k < deg; ++k) {
-            const int u = __ldg(a.col + b + k);
-            const uint32_t wu = *word_of(u);
-            if (sel ? outranks_c(wu, u, wv, v) : wu >= kWordInMin) return true;
         }
         return false;
     };
@@ -129,14 +139,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         const int par = r & 1;
         // ---- Phase 1: selection test
         unsigned sel = 0;
-        for (int k = tid; k < chunk; k += nth) {
+        for (int k = tid; k < cnt; k += nth) {
             const int v = base + k;
-            if (v >= n) break;
             const uint32_t wv = s_word[k];
             if ((wv >> 29) != 1u) continue;  // decided
-            const int b = single ? my_b : a.rp[v];
-            const int deg = single ? my_deg : a.rp[v + 1] - b;
-            if (!scan(v, b, deg, single, wv, true)) {
+            if (!scan(k, v, wv, true)) {
                 s_word[k] = wv | kWordInSet;
                 if (a.out) a.out[v] = 1;
                 ++sel;
@@ -147,14 +154,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         if (rank == 0 && tid == 0 && times && r < kStatRounds) times->t[2 + r] = global_ns();
         // ---- Phases 2 and 3: exclusion test, state update; count the rest
         int rem = 0;
-        for (int k = tid; k < chunk; k += nth) {
-            const int v = base + k;
-            if (v >= n) break;
+        for (int k = tid; k < cnt; k += nth) {
             const uint32_t wv = s_word[k];
             if ((wv >> 29) != 1u) continue;
-            const int b = single ? my_b : a.rp[v];
-            const int deg = single ? my_deg : a.rp[v + 1] - b;
-            if (scan(v, b, deg, single, wv, false)) s_word[k] = kWordOut;
+            if (scan(k, base + k, wv, false)) s_word[k] = kWordOut;
             else ++rem;
         }
         for (int o = 16; o; o >>= 1) rem += __shfl_xor_sync(0xFFFFFFFFu, rem, o);
@@ -188,11 +191,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     // the MIS size: this CTA's candidates and its isolated vertices (put in
     // the set at init without a test)
     unsigned iso = 0;
-    for (int k = tid; k < chunk; k += nth) {
-        const int v = base + k;
-        if (v >= n) break;
-        iso += (a.rp[v + 1] == a.rp[v]) ? 1u : 0u;
-    }
+    for (int k = tid; k < cnt; k += nth) iso += (a.rp[base + k + 1] == a.rp[base + k]) ? 1u : 0u;
     for (int o = 16; o; o >>= 1) iso += __shfl_xor_sync(0xFFFFFFFFu, iso, o);
     if ((tid & 31) == 0 && iso) atomicAdd(&s_sel, iso);
     __syncthreads();
@@ -201,19 +200,38 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     cluster.sync();
 }
 
-// The cluster that takes a graph of n vertices: 16 CTAs where the device can
-// co-schedule them, else 8; each CTA holds chunk = 2^shift >= n / ncta words
-// in at most kClusterSmem bytes.  Returns false when the graph is too large.
-constexpr int kClusterSmem = 128 * 1024;
-
 }  // namespace
 
-bool cluster_plan(int32_t n, int* ncta_out, int* shift_out) {
+// The cluster that takes a graph of n vertices: 16 CTAs where the device can
+// co-schedule them, else 8; each CTA holds chunk = 2^shift >= n / ncta words
+// and, where they fit too, its rows.  Reads row_ptr at the CTAs' boundaries
+// (d_rp on the device) to size the largest slice of arcs.
+bool cluster_plan(const int32_t* d_rp, int32_t n, ClusterPlan* plan) {
+    int max_optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t budget = (size_t)max_optin > 1024 ? (size_t)max_optin - 1024 : 0;
     for (int ncta : {16, 8}) {
         int shift = 5;
         while ((long long)(1 << shift) * ncta < n) ++shift;
-        const size_t smem = sizeof(uint32_t) << shift;
-        if (smem > (size_t)kClusterSmem) continue;
+        const int chunk = 1 << shift;
+        const size_t words = sizeof(uint32_t) * (size_t)chunk;
+        if (words > budget) continue;
+        // the largest slice of arcs a CTA owns
+        long long max_slice = 0;
+        int32_t prev = 0;
+        for (int k = 1; k <= ncta; ++k) {
+            const long long vb = std::min<long long>((long long)k * chunk, n);
+            int32_t x = 0;
+            if (n > 0 && cudaMemcpy(&x, d_rp + vb, sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+                             cudaSuccess)
+                return false;
+            max_slice = std::max<long long>(max_slice, (long long)x - prev);
+            prev = x;
+        }
+        const size_t rows = sizeof(int32_t) * ((size_t)chunk + 1 + (size_t)max_slice);
+        const int smem_rows = words + rows <= budget ? 1 : 0;
+        const size_t smem = words + (smem_rows ? rows : 0);
         if (ncta > 8 && cudaFuncSetAttribute(cluster_solve_kernel,
                                              cudaFuncAttributeNonPortableClusterSizeAllowed,
                                              1) != cudaSuccess) {
@@ -227,7 +245,7 @@ bool cluster_plan(int32_t n, int* ncta_out, int* shift_out) {
         }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(ncta);
-        cfg.blockDim = dim3(std::min(kClusterThreads, std::max(32, 1 << shift)));
+        cfg.blockDim = dim3(std::min(kClusterThreads, std::max(32, chunk)));
         cfg.dynamicSmemBytes = smem;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -242,37 +260,44 @@ bool cluster_plan(int32_t n, int* ncta_out, int* shift_out) {
             cudaGetLastError();
             continue;
         }
-        *ncta_out = ncta;
-        *shift_out = shift;
+        plan->ncta = ncta;
+        plan->shift = shift;
+        plan->smem_rows = smem_rows;
+        plan->smem_bytes = (int64_t)smem;
         return true;
     }
     return false;
 }
 
 int32_t cluster_max_vertices() {
-    int ncta = 0, shift = 0;
-    // the largest n whose plan fits: one word per vertex within kClusterSmem per CTA
-    const int32_t guess = 16 * (kClusterSmem / 4);
-    for (int32_t n = guess; n >= 1024; n /= 2)
-        if (cluster_plan(n, &ncta, &shift)) return n;
-    return 0;
+    int max_optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+        cudaSuccess)
+        return 0;
+    // the vertex words alone in 16 CTAs (the rows may then stay in global memory)
+    const long long words = ((long long)max_optin - 1024) / 4;
+    int shift = 5;
+    while ((2LL << shift) <= words) ++shift;
+    return (int32_t)std::min<long long>(16LL << shift, 1LL << 30);
 }
 
-cudaError_t launch_cluster_solve(const SolveArgs& a, int ncta, int shift, cudaStream_t s) {
-    if (ncta < 1 || ncta > 16 || shift < 5 || (long long)ncta << shift < a.n)
+cudaError_t launch_cluster_solve(const SolveArgs& a, const ClusterPlan& p, cudaStream_t s) {
+    if (p.ncta < 1 || p.ncta > 16 || p.shift < 5 || ((long long)p.ncta << p.shift) < a.n)
         return cudaErrorInvalidConfiguration;
-    const int chunk = 1 << shift;
+    const int chunk = 1 << p.shift;
     ClusterArgs c;
-    c.shift = shift;
-    c.ncta = ncta;
+    c.shift = p.shift;
+    c.ncta = p.ncta;
+    c.smem_rows = p.smem_rows;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ncta);
+    cfg.gridDim = dim3(p.ncta);
     cfg.blockDim = dim3(std::min(kClusterThreads, std::max(32, chunk)));
-    cfg.dynamicSmemBytes = sizeof(uint32_t) * (size_t)chunk;
+    cfg.dynamicSmemBytes = (size_t)p.smem_bytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = ncta;
+    attr[0].val.clusterDim.x = p.ncta;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
