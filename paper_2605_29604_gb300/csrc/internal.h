@@ -235,6 +235,7 @@ struct ClusterPlan {
     int32_t ncta = 0;
     int32_t shift = 0;
     int32_t smem_rows = 0;
+    int32_t replicated = 0;  // every CTA holds a replica of all vertex words
     int64_t smem_bytes = 0;
 };
 bool cluster_plan(const int32_t* d_rp, int32_t n, ClusterPlan* plan);

@@ -6,9 +6,12 @@
 // (C <= 16, one per SM) takes the whole graph:
 //
 //   state    the packed vertex words (common.cuh) live in the CTAs' shared
-//            memory: vertex v in CTA v >> shift at slot v & (chunk - 1), chunk
-//            = 2^shift >= n / C; every neighbour word is read through
-//            distributed shared memory, never from global memory;
+//            memory.  CTA r owns the vertices of chunk r (chunk = 2^shift >=
+//            n / C).  Where a replica of every word fits in each CTA, every
+//            scan reads local shared memory and the CTAs exchange, after each
+//            phase, one bit per owned vertex whose state changed; otherwise a
+//            CTA holds its own chunk and neighbour words are read through
+//            distributed shared memory;
 //   barriers the phases are separated by the cluster's hardware barrier
 //            (barrier.cluster arrive/wait through cooperative groups), which
 //            every CTA reaches the same number of times: the loop exit is
@@ -49,10 +52,17 @@ __device__ __forceinline__ bool outranks_c(uint32_t wu, int u, uint32_t wv, int 
     return wu > wv || (wu == wv && u > v);
 }
 
+// kRep = false: CTA r holds the words of its own chunk only; neighbour words
+// are read through distributed shared memory.  kRep = true: every CTA holds a
+// replica of all words, so every scan reads local shared memory; after each
+// phase a CTA publishes one bit per owned vertex whose state changed (a
+// bitmask in its shared memory, one word per warp, written by a ballot), and
+// every other CTA folds those bits into its replica after the cluster
+// barrier.  Two bitmasks (selected, excluded) keep a phase's bits readable
+// until every CTA has passed the next barrier.
+template <bool kRep>
 __global__ void __launch_bounds__(kClusterThreads, 1)
     cluster_solve_kernel(const SolveArgs a, const ClusterArgs c) {
-    // shared memory: this CTA's chunk of vertex words, then (smem_rows) the
-    // row offsets of its vertices relative to its first arc and its arcs
     extern __shared__ uint32_t s_dyn[];
     __shared__ int s_rem[2];  // this CTA's undecided count, by round parity
     __shared__ unsigned s_sel;
@@ -65,9 +75,15 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     const int cnt = max(0, min(chunk, n - base));  // this CTA's vertices
     const int tid = (int)threadIdx.x;
     const int nth = (int)blockDim.x;
+    // shared memory: the words (own chunk, or all chunks), with kRep the two
+    // change bitmasks of the own chunk, then (smem_rows) the own rows
+    const int nwords = kRep ? c.ncta * chunk : chunk;
     uint32_t* s_word = s_dyn;
-    int32_t* s_rp = reinterpret_cast<int32_t*>(s_dyn + chunk);
+    uint32_t* s_new_in = s_dyn + nwords;
+    uint32_t* s_new_out = s_new_in + (kRep ? chunk / 32 : 0);
+    int32_t* s_rp = reinterpret_cast<int32_t*>(s_new_out + (kRep ? chunk / 32 : 0));
     int32_t* s_col = s_rp + chunk + 1;
+    uint32_t* s_own = kRep ? s_word + base : s_word;  // the own chunk's words
     Ctl* ctl = a.ctl;
     PhaseTimes* times = a.times;
     const int mode = a.priority;
@@ -78,29 +94,31 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         s_sel = 0;
         if (rank == 0 && times) times->t[0] = global_ns();
     }
-    // the word of vertex u, wherever it lives in the cluster
+    // the word of vertex u: in this CTA (kRep), else wherever it lives
     auto word_of = [&](int u) -> const uint32_t* {
+        if (kRep) return s_word + u;
         return cluster.map_shared_rank(s_word + (u & (chunk - 1)), u >> c.shift);
     };
 
     // ---- init: the CTA's rows into shared memory (coalesced copies), then
-    // Eq. 1 priorities; isolated vertices straight into the set and result
+    // Eq. 1 priorities (of all vertices with kRep); isolated vertices straight
+    // into the set, and the own vertices' result bytes
     const int arc0 = cnt > 0 ? a.rp[base] : 0;
     if (c.smem_rows && cnt > 0) {
         const int arc1 = a.rp[base + cnt];
         for (int k = tid; k <= cnt; k += nth) s_rp[k] = a.rp[base + k] - arc0;
         for (int p = tid; p < arc1 - arc0; p += nth) s_col[p] = __ldg(a.col + arc0 + p);
     }
-    for (int k = tid; k < chunk; k += nth) {
-        const int v = base + k;
+    for (int i = tid; i < nwords; i += nth) {
+        const int v = kRep ? i : base + i;
         uint32_t w = kWordOut;
         if (v < n) {
             const int deg = a.rp[v + 1] - a.rp[v];
             w = deg ? undecided_word(mode, priority_key(mode, dbar, deg, smix, (uint32_t)v))
                     : (kKeyIsolated | kWordInSet);
-            if (a.out) a.out[v] = deg ? 0 : 1;
+            if (a.out && v >= base && v < base + cnt) a.out[v] = deg ? 0 : 1;
         }
-        s_word[k] = w;
+        s_word[i] = w;
     }
     cluster.sync();
     if (rank == 0 && tid == 0 && times) times->t[1] = global_ns();
@@ -133,36 +151,76 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         }
         return false;
     };
+    // kRep: fold the other CTAs' published bits into the replica (in: OR the
+    // set bits, else: out)
+    auto fold = [&](const uint32_t* mask, bool in) {
+        const int per = chunk / 32;
+        for (int i = tid; i < c.ncta * per; i += nth) {
+            const int q = i / per, j = i - q * per;
+            if (q == rank) continue;
+            uint32_t bits = *cluster.map_shared_rank(mask + j, q);
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                uint32_t* w = s_word + q * chunk + 32 * j + b;
+                *w = in ? (*w | kWordInSet) : kWordOut;
+            }
+        }
+    };
 
     int alive = n;  // round 0's alive set: every vertex
     for (int r = 0;; ++r) {
         const int par = r & 1;
-        // ---- Phase 1: selection test
+        // ---- Phase 1: selection test over the own chunk (kRep: every warp
+        // covers whole 32-vertex words, so its ballot is the word's bits)
         unsigned sel = 0;
-        for (int k = tid; k < cnt; k += nth) {
-            const int v = base + k;
-            const uint32_t wv = s_word[k];
-            if ((wv >> 29) != 1u) continue;  // decided
-            if (!scan(k, v, wv, true)) {
-                s_word[k] = wv | kWordInSet;
-                if (a.out) a.out[v] = 1;
-                ++sel;
+        for (int k = tid; k < (kRep ? chunk : cnt); k += nth) {
+            bool cand = false;
+            if (k < cnt) {
+                const uint32_t wv = s_own[k];
+                if ((wv >> 29) == 1u && !scan(k, base + k, wv, true)) {
+                    s_own[k] = wv | kWordInSet;
+                    if (a.out) a.out[base + k] = 1;
+                    cand = true;
+                    ++sel;
+                }
+            }
+            if (kRep) {
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
+                if ((tid & 31) == 0) s_new_in[k >> 5] = m;
             }
         }
         if (sel) atomicAdd(&s_sel, sel);
         cluster.sync();
         if (rank == 0 && tid == 0 && times && r < kStatRounds) times->t[2 + r] = global_ns();
+        if (kRep) {
+            fold(s_new_in, true);
+            __syncthreads();
+        }
         // ---- Phases 2 and 3: exclusion test, state update; count the rest
         int rem = 0;
-        for (int k = tid; k < cnt; k += nth) {
-            const uint32_t wv = s_word[k];
-            if ((wv >> 29) != 1u) continue;
-            if (scan(k, base + k, wv, false)) s_word[k] = kWordOut;
-            else ++rem;
+        for (int k = tid; k < (kRep ? chunk : cnt); k += nth) {
+            bool out = false;
+            if (k < cnt) {
+                const uint32_t wv = s_own[k];
+                if ((wv >> 29) == 1u) {
+                    if (scan(k, base + k, wv, false)) {
+                        s_own[k] = kWordOut;
+                        out = true;
+                    } else {
+                        ++rem;
+                    }
+                }
+            }
+            if (kRep) {
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, out);
+                if ((tid & 31) == 0) s_new_out[k >> 5] = m;
+            }
         }
         for (int o = 16; o; o >>= 1) rem += __shfl_xor_sync(0xFFFFFFFFu, rem, o);
         if ((tid & 31) == 0 && rem) atomicAdd(&s_rem[par], rem);
         cluster.sync();
+        if (kRep) fold(s_new_out, false);
         // every CTA sums the same counts, so all leave the loop together
         if (tid < 32) {
             int total = tid < c.ncta ? *cluster.map_shared_rank(&s_rem[par], tid) : 0;
@@ -215,8 +273,6 @@ bool cluster_plan(const int32_t* d_rp, int32_t n, ClusterPlan* plan) {
         int shift = 5;
         while ((long long)(1 << shift) * ncta < n) ++shift;
         const int chunk = 1 << shift;
-        const size_t words = sizeof(uint32_t) * (size_t)chunk;
-        if (words > budget) continue;
         // the largest slice of arcs a CTA owns
         long long max_slice = 0;
         int32_t prev = 0;
@@ -230,16 +286,36 @@ bool cluster_plan(const int32_t* d_rp, int32_t n, ClusterPlan* plan) {
             prev = x;
         }
         const size_t rows = sizeof(int32_t) * ((size_t)chunk + 1 + (size_t)max_slice);
-        const int smem_rows = words + rows <= budget ? 1 : 0;
-        const size_t smem = words + (smem_rows ? rows : 0);
-        if (ncta > 8 && cudaFuncSetAttribute(cluster_solve_kernel,
-                                             cudaFuncAttributeNonPortableClusterSizeAllowed,
+        // a replica of every word (and the two change bitmasks) if it fits,
+        // else the own chunk's words; the rows on chip if they fit as well
+        const size_t rep = sizeof(uint32_t) * ((size_t)ncta * chunk + (size_t)chunk / 16);
+        const size_t own = sizeof(uint32_t) * (size_t)chunk;
+        int replicated, smem_rows;
+        if (rep + rows <= budget) {
+            replicated = 1;
+            smem_rows = 1;
+        } else if (own + rows <= budget) {
+            replicated = 0;
+            smem_rows = 1;
+        } else if (rep <= budget) {
+            replicated = 1;
+            smem_rows = 0;
+        } else if (own <= budget) {
+            replicated = 0;
+            smem_rows = 0;
+        } else {
+            continue;
+        }
+        const size_t smem = (replicated ? rep : own) + (smem_rows ? rows : 0);
+        const void* fn = replicated ? (const void*)cluster_solve_kernel<true>
+                                    : (const void*)cluster_solve_kernel<false>;
+        if (ncta > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed,
                                              1) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
-        if (cudaFuncSetAttribute(cluster_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -255,14 +331,14 @@ bool cluster_plan(const int32_t* d_rp, int32_t n, ClusterPlan* plan) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, cluster_solve_kernel, &cfg) != cudaSuccess ||
-            clusters < 1) {
+        if (cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg) != cudaSuccess || clusters < 1) {
             cudaGetLastError();
             continue;
         }
         plan->ncta = ncta;
         plan->shift = shift;
         plan->smem_rows = smem_rows;
+        plan->replicated = replicated;
         plan->smem_bytes = (int64_t)smem;
         return true;
     }
@@ -302,7 +378,8 @@ cudaError_t launch_cluster_solve(const SolveArgs& a, const ClusterPlan& p, cudaS
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, cluster_solve_kernel, a, c);
+    if (p.replicated) return cudaLaunchKernelEx(&cfg, cluster_solve_kernel<true>, a, c);
+    return cudaLaunchKernelEx(&cfg, cluster_solve_kernel<false>, a, c);
 }
 
 }  // namespace tcmis
