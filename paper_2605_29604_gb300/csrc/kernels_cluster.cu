@@ -54,12 +54,12 @@ __device__ __forceinline__ bool outranks_c(uint32_t wu, int u, uint32_t wv, int 
 
 // kRep = false: CTA r holds the words of its own chunk only; neighbour words
 // are read through distributed shared memory.  kRep = true: every CTA holds a
-// replica of all words, so every scan reads local shared memory; after each
-// phase a CTA publishes one bit per owned vertex whose state changed (a
-// bitmask in its shared memory, one word per warp, written by a ballot), and
-// every other CTA folds those bits into its replica after the cluster
-// barrier.  Two bitmasks (selected, excluded) keep a phase's bits readable
-// until every CTA has passed the next barrier.
+// replica of all words, so every scan reads local shared memory; in each
+// phase a CTA publishes one bit per owned vertex whose state changed (one
+// word per warp, from a ballot), storing it into every CTA's copy of the
+// change bitmask, and after the cluster barrier every CTA folds the bits it
+// received into its replica.  Two bitmasks (selected, excluded) keep a
+// phase's bits until every CTA has folded them.
 template <bool kRep>
 __global__ void __launch_bounds__(kClusterThreads, 1)
     cluster_solve_kernel(const SolveArgs a, const ClusterArgs c) {
@@ -78,10 +78,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     // shared memory: the words (own chunk, or all chunks), with kRep the two
     // change bitmasks of the own chunk, then (smem_rows) the own rows
     const int nwords = kRep ? c.ncta * chunk : chunk;
+    const int nmask = kRep ? c.ncta * (chunk / 32) : 0;  // change bits of every chunk
     uint32_t* s_word = s_dyn;
     uint32_t* s_new_in = s_dyn + nwords;
-    uint32_t* s_new_out = s_new_in + (kRep ? chunk / 32 : 0);
-    int32_t* s_rp = reinterpret_cast<int32_t*>(s_new_out + (kRep ? chunk / 32 : 0));
+    uint32_t* s_new_out = s_new_in + nmask;
+    int32_t* s_rp = reinterpret_cast<int32_t*>(s_new_out + nmask);
     int32_t* s_col = s_rp + chunk + 1;
     uint32_t* s_own = kRep ? s_word + base : s_word;  // the own chunk's words
     Ctl* ctl = a.ctl;
@@ -151,14 +152,20 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         }
         return false;
     };
-    // kRep: fold the other CTAs' published bits into the replica (in: OR the
-    // set bits, else: out)
+    // kRep: a warp's change word of the own chunk, stored into every CTA's
+    // copy of the bitmask (remote stores, made visible by the next barrier)
+    auto publish = [&](uint32_t* mask, int k, unsigned m) {
+        const int lane = tid & 31;
+        if (lane < c.ncta) *cluster.map_shared_rank(mask + rank * (chunk / 32) + (k >> 5), lane) = m;
+    };
+    // kRep: fold the other CTAs' changes, received in local shared memory,
+    // into the replica (in: OR the set bits, else: out)
     auto fold = [&](const uint32_t* mask, bool in) {
         const int per = chunk / 32;
         for (int i = tid; i < c.ncta * per; i += nth) {
             const int q = i / per, j = i - q * per;
             if (q == rank) continue;
-            uint32_t bits = *cluster.map_shared_rank(mask + j, q);
+            uint32_t bits = mask[i];
             while (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
@@ -185,10 +192,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
                     ++sel;
                 }
             }
-            if (kRep) {
-                const unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
-                if ((tid & 31) == 0) s_new_in[k >> 5] = m;
-            }
+            if (kRep) publish(s_new_in, k, __ballot_sync(0xFFFFFFFFu, cand));
         }
         if (sel) atomicAdd(&s_sel, sel);
         cluster.sync();
@@ -212,10 +216,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
                     }
                 }
             }
-            if (kRep) {
-                const unsigned m = __ballot_sync(0xFFFFFFFFu, out);
-                if ((tid & 31) == 0) s_new_out[k >> 5] = m;
-            }
+            if (kRep) publish(s_new_out, k, __ballot_sync(0xFFFFFFFFu, out));
         }
         for (int o = 16; o; o >>= 1) rem += __shfl_xor_sync(0xFFFFFFFFu, rem, o);
         if ((tid & 31) == 0 && rem) atomicAdd(&s_rem[par], rem);
@@ -288,7 +289,7 @@ bool cluster_plan(const int32_t* d_rp, int32_t n, ClusterPlan* plan) {
         const size_t rows = sizeof(int32_t) * ((size_t)chunk + 1 + (size_t)max_slice);
         // a replica of every word (and the two change bitmasks) if it fits,
         // else the own chunk's words; the rows on chip if they fit as well
-        const size_t rep = sizeof(uint32_t) * ((size_t)ncta * chunk + (size_t)chunk / 16);
+        const size_t rep = sizeof(uint32_t) * ((size_t)ncta * chunk + (size_t)ncta * chunk / 16);
         const size_t own = sizeof(uint32_t) * (size_t)chunk;
         int replicated, smem_rows;
         if (rep + rows <= budget) {
