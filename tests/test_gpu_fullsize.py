@@ -1,6 +1,8 @@
-"""Parity at the benchmark's full sizes, in the launch configuration bench.py
-times (create-time degree order, autotuned kernel, persistent launch; the
-batch as a captured and replayed launch).  The oracle solves these graphs in
+"""Parity at the benchmark's full sizes, in the launch configurations bench.py
+times (the headline: full rows, no create-time decisions, autotuned kernel;
+beside it the amortised graph with create-time degree order; the batch as a
+captured and replayed launch; the grid's tile paths and 8-seed tensor-core
+launch).  The oracle solves these graphs in
 seconds, so every output is compared, with the round structure; independence
 and maximality are checked on top."""
 import numpy as np
@@ -24,9 +26,12 @@ def _built():
     torch.cuda.set_device(0)
 
 
-def _bench_handle(g):
+def _bench_handle(g, order_rows=2):
+    """order_rows = 0: the headline solve (full rows, no create-time round-0
+    decisions); 2: the amortised one (create-time structures)."""
     n, rp, col = g
-    h = native.mis_create_ex(n, rp, col, 0, native.options(check_symmetry=1, order_rows=2), None)
+    h = native.mis_create_ex(n, rp, col, 0,
+                             native.options(check_symmetry=1, order_rows=order_rows), None)
     native.mis_autotune(h, 3)
     return h
 
@@ -39,13 +44,14 @@ def _solve(h, n, seeds):
     return out[:n].cpu().numpy(), native.mis_get_stats(h)
 
 
+@pytest.mark.parametrize("order_rows", [0, 2])
 @pytest.mark.parametrize("name", ["rmat22", "grid", "grid_perm"])
-def test_full_size_single_graph(name):
+def test_full_size_single_graph(name, order_rows):
     g = {"rmat22": lambda: gg.rmat22(seed=22),
          "grid": lambda: gg.grid2048(seed=3),
          "grid_perm": lambda: gg.grid2048(seed=3, permute_ids=True)}[name]()
     n, rp, col = g
-    h = _bench_handle(g)
+    h = _bench_handle(g, order_rows)
     try:
         for seed in (1, 2**63 + 11):
             got, st = _solve(h, n, [seed])
@@ -99,5 +105,30 @@ def test_full_size_batch4096_replayed():
             assert np.array_equal(host[off:off + n], want), i
             off += n
         assert off == size
+    finally:
+        native.mis_destroy(h)
+
+
+@pytest.mark.parametrize("payload", [native.MIS_TILE_BITS, native.MIS_TILE_BITS_B1,
+                                     native.MIS_TILE_INT8, native.MIS_TILE_FP16])
+def test_full_size_grid_tensor_core_forms(payload):
+    """The grid (natural ids) on the tensor-core tile path in every payload
+    form, one seed and eight seeds per launch, as bench.py's tc leg runs it."""
+    import torch
+    g = gg.grid2048(seed=3)
+    n, rp, col = g
+    h = native.mis_create_ex(n, rp, col, 0, native.options(order_rows=0), None)
+    try:
+        native.mis_set_tile_payload(h, payload)
+        native.mis_set_path(h, native.MIS_PATH_TILE_TC, 16)
+        got, st = _solve(h, n, [5])
+        assert_same(g, 5, got, st)
+        seeds = np.arange(1, 9, dtype=np.uint64)
+        out = torch.empty(8 * n, dtype=torch.uint8, device="cuda")
+        native.mis_solve_multi_ex(h, seeds, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        host = out.cpu().numpy()
+        for s in (0, 7):
+            want = oracle.solve(n, rp, col, int(seeds[s]))
+            assert np.array_equal(host[s * n:(s + 1) * n], want.status), s
     finally:
         native.mis_destroy(h)
