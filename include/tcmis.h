@@ -350,17 +350,6 @@ int mis_tile_payload_ex(mis_graph *g, int32_t payload, void *out, void *stream);
  * values, MIS_EBUSY while served requests on `g` are in flight. */
 int mis_set_csr_range0(mis_graph *g, int32_t on);
 
-/* CSR path: how the degree bins scanned by 4 or more lanes per row reach
- * their rows.  on = 1: a warp's passes over its share of a bin are staged
- * through shared memory -- the row records of the pass after next and the
- * first 16-byte slice of every row of the next pass are copied (cp.async)
- * while the current pass scans -- so a pass waits only for its neighbours'
- * words; on = 0 (default): each pass loads its records and slices itself.
- * Same result either way (chosen by mis_autotune; round 0's range mode, see
- * mis_set_csr_range0, takes precedence where it applies).  MIS_EINVAL for
- * other values, MIS_EBUSY while served requests on `g` are in flight. */
-int mis_set_csr_staged(mis_graph *g, int32_t on);
-
 /* The autotuner's choice for a graph. */
 typedef struct mis_tuning {
     int32_t path;        /* MIS_PATH_CSR, MIS_PATH_TILE or MIS_PATH_TILE_TC */
@@ -375,7 +364,6 @@ typedef struct mis_tuning {
                             the graph has round-0 classes) */
     int32_t tile_payload;/* MIS_PATH_TILE_TC: the MIS_TILE_* form of the choice,
                             else -1 */
-    int32_t csr_staged;  /* CSR: the mis_set_csr_staged mode of the choice */
 } mis_tuning;
 
 /*

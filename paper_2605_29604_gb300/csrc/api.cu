@@ -435,7 +435,6 @@ SolveArgs make_args(mis_graph* g, Workspace& w) {
     a.n_sure_out = d.n_sure_out;
     a.pending = g->csr_pending;
     a.range0_max = (g->csr_range0 && !d.r0class && d.thr[0] >= 1) ? d.thr[0] : 0;
-    a.pipe = g->csr_staged;
     a.priority = g->opt.priority;
     a.ctl = w.ctl;
     a.times = w.times;
@@ -592,7 +591,6 @@ struct TuneChoice {
     int32_t pending = 0; // CSR: Phase 1 lists its non-candidates for Phase 2
     int32_t range0 = 1;  // CSR: round 0 takes bin 0 by vertex ranges
     int32_t payload = 0; // tensor-core tile path: MIS_TILE_* form
-    int32_t staged = 0;  // CSR: passes staged through shared memory
 };
 
 std::mutex g_tune_mu;
@@ -615,7 +613,6 @@ void tune_load_locked() {
             if (!(ss >> c.pending)) c.pending = 0;  // lines written before the field
             if (!(ss >> c.range0)) c.range0 = 1;
             if (!(ss >> c.payload)) c.payload = 0;
-            if (!(ss >> c.staged)) c.staged = 0;
             g_tune_cache[key] = c;
         }
     }
@@ -629,8 +626,7 @@ void tune_save_locked() {
         const TuneChoice& c = kv.second;
         out << kv.first << ' ' << c.path << ' ' << c.param << ' ' << c.bounds[0] << ' '
             << c.bounds[1] << ' ' << c.bounds[2] << ' ' << c.bounds[3] << ' ' << c.grid << ' '
-            << c.ms << ' ' << c.pending << ' ' << c.range0 << ' ' << c.payload << ' '
-            << c.staged << '\n';
+            << c.ms << ' ' << c.pending << ' ' << c.range0 << ' ' << c.payload << '\n';
     }
 }
 
@@ -749,7 +745,6 @@ int apply_choice(mis_graph* g, const TuneChoice& c) {
     g->tpr = c.param;
     g->csr_pending = c.pending;
     g->csr_range0 = c.range0;
-    g->csr_staged = c.staged;
     if (g->last_stream) cudaStreamSynchronize(g->last_stream);
     const int rc = rebin(g, thr, g->own_stream);
     if (rc != MIS_OK) return rc;
@@ -815,18 +810,6 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
         bins(INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, maxg * 2 / 3);
     }
     bins(-1, 65536, 65536, 65536, 0);                                     // four lanes per row
-    // the same with the passes of the bins of 4 or more lanes staged through
-    // shared memory
-    {
-        const size_t k0 = cands.size();
-        bins(-1, 65536, 65536, 65536, 0);
-        bins(8, 4096, 4096, 65536, 0);
-        bins(4, 64, 1024, 65536, 0);
-        for (size_t k = k0; k < cands.size(); ++k) {
-            cands[k].staged = 1;
-            cands[k].range0 = 0;
-        }
-    }
     // without round-0 classes, round 0 can take bin 0 by vertex ranges (the
     // candidates above) or from its list
     if (!g->d.r0class) {
@@ -882,10 +865,10 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
         if (log)
             std::fprintf(stderr,
                          "tcmis tune: path %d param %d bounds %d %d %d %d grid %d pending %d "
-                         "range0 %d staged %d payload %d: %.4f ms\n",
+                         "range0 %d payload %d: %.4f ms\n",
                          c.path, c.param, c.bounds[0], c.bounds[1], c.bounds[2], c.bounds[3],
                          c.path == MIS_PATH_CSR ? g->grid : g->tile_grid, c.pending, c.range0,
-                         c.staged, c.payload, c.ms);
+                         c.payload, c.ms);
         if (c.ms > 0.f && (best.ms < 0.f || c.ms < best.ms)) best = c;
     }
     if (best.ms < 0.f) return set_error(MIS_EINTERNAL, "autotuner found no working configuration");
@@ -906,7 +889,6 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
         out->csr_pending = best.path == MIS_PATH_CSR ? best.pending : 0;
         out->csr_range0 = (best.path == MIS_PATH_CSR && !g->d.r0class) ? best.range0 : 0;
         out->tile_payload = best.path == MIS_PATH_TILE_TC ? best.payload : -1;
-        out->csr_staged = best.path == MIS_PATH_CSR ? best.staged : 0;
         out->arcs_per_tile = apt;
         out->candidates = (int32_t)cands.size();
     }
@@ -1333,16 +1315,6 @@ int mis_set_tile_payload(mis_graph* g, int32_t payload) {
     // a graph already on the tensor-core path switches now (and builds the
     // stored payload if the form reads one)
     if (g->path == MIS_PATH_TILE_TC) return use_tiles(g, MIS_PATH_TILE_TC, 16);
-    return MIS_OK;
-}
-
-int mis_set_csr_staged(mis_graph* g, int32_t on) {
-    clear_error();
-    if (!g) return set_error(MIS_EINVAL, "null graph");
-    if (on != 0 && on != 1) return set_error(MIS_EINVAL, "staged must be 0 or 1");
-    std::lock_guard<std::mutex> lk(g->mu);
-    if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
-    g->csr_staged = on;
     return MIS_OK;
 }
 

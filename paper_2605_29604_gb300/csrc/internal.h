@@ -80,9 +80,6 @@ struct SolveArgs {
     // > 0: round 0 tests bin 0 (degree 1 .. range0_max) by vertex ranges over
     // row_ptr instead of its order0 list (graphs without round-0 classes)
     int32_t range0_max = 0;
-    // 1: the bins of 4 or more lanes per row stage their passes through shared
-    // memory (cp.async of the next passes' records and first row slices)
-    int32_t pipe = 0;
     int32_t pending = 0;              // 1: Phase 1 lists its non-candidates for Phase 2
                                       // (in wlp); 0: Phase 2 triages W_r itself
     // tile-CSR (used by the tile kernels only)

@@ -111,93 +111,6 @@ __device__ __forceinline__ bool group_scan(const int32_t* __restrict__ col, Word
     return found;
 }
 
-// ---- staged scans (the `pipe` forms of the kernel)
-//
-// A warp's passes over a chunk of a bin are pipelined through shared memory
-// with cp.async (the copy holds no register while it is in flight): the row
-// records of pass p + 2 and the first 16-byte slice of every row of pass
-// p + 1 are requested before pass p is scanned, so a pass waits only for its
-// neighbour words.  Three record stages and two slice stages per warp.
-constexpr int kPipeRec = 3;
-constexpr int kPipeCol = 2;
-__shared__ int4 s_prec[kWarps][kPipeRec][8];
-__shared__ int4 s_pcol[kWarps][kPipeCol][32];
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem),
-                 "r"(valid ? 16 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
-
-// As group_scan, with the lane's first slice already in `c0` (the staged
-// slice at (b & ~3) + 4 glane); later slices are loaded as group_scan does.
-template <int TPR, bool kSelect, class Words>
-__device__ __forceinline__ bool group_scan_staged(const int32_t* __restrict__ col, Words nbw,
-                                                  int4 c0, int b, int e, int v, uint32_t wv,
-                                                  unsigned glane, unsigned gshift) {
-    constexpr unsigned gbits = (TPR == 32) ? 0xFFFFFFFFu : ((1u << TPR) - 1u);
-    bool found = false;
-    bool first = true;
-    int p0 = (b & ~3) + 4 * (int)glane;
-    for (;;) {
-        bool hit = false;
-        if (!found && p0 < e) {
-            const int4 c = first ? c0 : __ldg(reinterpret_cast<const int4*>(col + p0));
-            const uint32_t w0 = (p0 >= b) ? nbw(c.x) : 0u;
-            const uint32_t w1 = (p0 + 1 >= b && p0 + 1 < e) ? nbw(c.y) : 0u;
-            const uint32_t w2 = (p0 + 2 >= b && p0 + 2 < e) ? nbw(c.z) : 0u;
-            const uint32_t w3 = (p0 + 3 >= b && p0 + 3 < e) ? nbw(c.w) : 0u;
-            if (kSelect) {
-                hit = outranks(w0, c.x, wv, v) | outranks(w1, c.y, wv, v) |
-                      outranks(w2, c.z, wv, v) | outranks(w3, c.w, wv, v);
-            } else {
-                hit = max(max(w0, w1), max(w2, w3)) >= kWordInMin;
-            }
-        }
-        first = false;
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, hit);
-        found = found || ((bal >> gshift) & gbits) != 0u;
-        p0 += 4 * TPR;
-        const bool more = !found && (p0 - 4 * (int)glane) < e;
-        if (!__any_sync(0xFFFFFFFFu, more)) break;
-    }
-    return found;
-}
-
-// Stage the records of pass `pass` of the chunk [c0, c1) (G rows a pass).
-template <int G>
-__device__ __forceinline__ void stage_records(const int4* __restrict__ list, int c0, int c1,
-                                              int pass, int4 (*prec)[8]) {
-    const unsigned lane = lane_id();
-    if ((int)lane < G) {
-        const int item = c0 + pass * G + (int)lane;
-        const bool ok = item < c1;
-        cp_async16(&prec[pass % kPipeRec][lane], list + (ok ? item : c0), ok);
-    }
-}
-
-// Stage each row's first slice of pass `pass` (its records already staged);
-// `end` picks the row end the scan uses (prefix end or row end).
-template <int TPR, int G, bool kSelect>
-__device__ __forceinline__ void stage_slices(const int32_t* __restrict__ col, int c0, int c1,
-                                             int pass, int4 (*prec)[8], int4 (*pcol)[32]) {
-    const unsigned lane = lane_id();
-    const int gid = (int)lane / TPR, glane = (int)lane % TPR;
-    const int item = c0 + pass * G + gid;
-    const int4 rec = prec[pass % kPipeRec][gid];
-    const int e = kSelect ? rec.z : rec.w;
-    const int p0 = (rec.y & ~3) + 4 * glane;
-    const bool ok = item < c1 && p0 < e;
-    cp_async16(&pcol[pass % kPipeCol][lane], col + (ok ? p0 : 0), ok);
-}
-
 // Scans of R rows at once by one lane: the records list[idx[i]], i < R, of
 // the valid rows.  kSelect: flag[i] = some neighbour outranks the row's vertex
 // (only the prefix [b, es) of the row is read), else: flag[i] = some
@@ -306,7 +219,7 @@ __device__ __forceinline__ void mark_selected(const SolveArgs& a, int v) {
 // Candidates are marked in the MIS.  kPending: the others form the pending
 // list P_r of Phase 2 (appended to pdst, counted in *pnext), each entry the
 // row's record in the adjacency Phase 2 scans.
-template <int TPR, int CH, bool kPending, bool kPipe = false>
+template <int TPR, int CH, bool kPending>
 __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __restrict__ list,
                                            int cnt, RoundSched& ws, unsigned* grab, int* pnext,
                                            int4* __restrict__ pdst, int32_t* wbuf, bool late) {
@@ -323,45 +236,6 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __res
     for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps(), grab)) {
         int c0, c1;
         plan.range(k, cnt, c0, c1, G);
-        if constexpr (kPipe && TPR > 1) {
-            // staged passes (see stage_records / stage_slices)
-            int4(*prec)[8] = s_prec[threadIdx.x / 32];
-            int4(*pcol)[32] = s_pcol[threadIdx.x / 32];
-            const int32_t* col = select_col(a, late);
-            const int npass = (c1 - c0 + G - 1) / G;
-            stage_records<G>(list, c0, c1, 0, prec);
-            stage_records<G>(list, c0, c1, 1, prec);
-            cp_async_commit();
-            cp_async_wait_all();
-            __syncwarp();
-            stage_slices<TPR, G, true>(col, c0, c1, 0, prec, pcol);
-            cp_async_commit();
-            for (int pass = 0; pass < npass; ++pass) {
-                cp_async_wait_all();  // this pass's slices, the next pass's records
-                __syncwarp();
-                if (pass + 2 < npass) stage_records<G>(list, c0, c1, pass + 2, prec);
-                if (pass + 1 < npass) stage_slices<TPR, G, true>(col, c0, c1, pass + 1, prec, pcol);
-                cp_async_commit();
-                const int item = c0 + pass * G + (int)gid;
-                const bool valid = item < c1;
-                const int4 rec = valid ? prec[pass % kPipeRec][gid] : make_int4(0, 0, 0, 0);
-                const uint32_t wv = valid ? ld_word_l1(a.word + rec.x) : 0u;
-                const int e = valid ? rec.z : 0;
-                const bool blocked = group_scan_staged<TPR, true>(
-                    col, LiveWords{a.word}, pcol[pass % kPipeCol][lane], rec.y, e, rec.x, wv,
-                    glane, gshift);
-                const bool lead = glane == 0;
-                if (valid && !blocked && lead) {
-                    a.word[rec.x] = wv | kWordInSet;
-                    mark_selected(a, rec.x);
-                }
-                if (kPending) {
-                    fill = stage_keep(valid && blocked && lead, item, wbuf, fill);
-                    fill = flush_if_full(wbuf, fill, kPass, pending_view(a, list, late), pnext, pdst);
-                }
-            }
-            continue;
-        }
         for (int base = c0; base < c1; base += kPass) {
             if constexpr (TPR == 1) {
                 int4 rec[kRowsPerLane];
@@ -416,7 +290,7 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __res
 // non-candidates only); else it is W_r, and each chunk (at most kScanMax
 // rows) is first triaged one vertex per lane (Phase 1 candidates need no
 // scan) into `wscan`.
-template <int TPR, int CH, bool kPending, bool kPipe = false>
+template <int TPR, int CH, bool kPending>
 __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __restrict__ list,
                                             int cnt, RoundSched& ws, unsigned* grab, int* next,
                                             int4* __restrict__ dst, int32_t* wbuf,
@@ -436,38 +310,6 @@ __device__ __forceinline__ void exclude_bin(const SolveArgs& a, const int4* __re
     for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps(), grab)) {
         int c0, c1;
         plan.range(k, cnt, c0, c1, G);
-        if constexpr (kPipe && kPending && TPR > 1) {
-            // staged passes over the pending list (see stage_records / stage_slices)
-            int4(*prec)[8] = s_prec[threadIdx.x / 32];
-            int4(*pcol)[32] = s_pcol[threadIdx.x / 32];
-            const int32_t* col = exclude_col(a);
-            const int npass = (c1 - c0 + G - 1) / G;
-            stage_records<G>(list, c0, c1, 0, prec);
-            stage_records<G>(list, c0, c1, 1, prec);
-            cp_async_commit();
-            cp_async_wait_all();
-            __syncwarp();
-            stage_slices<TPR, G, false>(col, c0, c1, 0, prec, pcol);
-            cp_async_commit();
-            for (int pass = 0; pass < npass; ++pass) {
-                cp_async_wait_all();
-                __syncwarp();
-                if (pass + 2 < npass) stage_records<G>(list, c0, c1, pass + 2, prec);
-                if (pass + 1 < npass) stage_slices<TPR, G, false>(col, c0, c1, pass + 1, prec, pcol);
-                cp_async_commit();
-                const int item = c0 + pass * G + (int)gid;
-                const bool valid = item < c1;
-                const int4 rec = valid ? prec[pass % kPipeRec][gid] : make_int4(0, 0, 0, 0);
-                const int e = valid ? rec.w : 0;
-                const bool excl = group_scan_staged<TPR, false>(
-                    col, nbw, pcol[pass % kPipeCol][lane], rec.y, e, rec.x, 0u, glane, gshift);
-                const bool lead = glane == 0;
-                if (valid && excl && lead) a.word[rec.x] = kWordOut;
-                fill = stage_keep(valid && !excl && lead, item, wbuf, fill);
-                fill = flush_if_full(wbuf, fill, kPass, list, next, dst);
-            }
-            continue;
-        }
         if (!kPending) {
             // triage: wscan gets the list indices of the undecided rows
             __syncwarp();  // the previous chunk is done with wscan
@@ -714,30 +556,24 @@ __device__ __forceinline__ int lanes_per_row(int cnt, bool late, int nwarps) {
 }
 
 // Phase 1 of bin j (base width BASE, chunk CH) at the width lanes_per_row picks.
-template <int BASE, int CH, bool kPending, bool kPipe>
+template <int BASE, int CH, bool kPending>
 __device__ __forceinline__ void select_bin_at(const SolveArgs& a, const int4* list, int cnt,
                                               bool late, RoundSched& ws, unsigned* grab,
                                               int* pnext, int4* pend, int32_t* wbuf) {
     switch (lanes_per_row<BASE>(cnt, late, ws.nwarps())) {
         case 32:
-            select_bin<32, kChunk3, kPending, kPipe>(a, list, cnt, ws, grab, pnext, pend, wbuf,
-                                                     late);
+            select_bin<32, kChunk3, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf, late);
             break;
         case 16:
-            select_bin<16, kChunk2, kPending, kPipe>(a, list, cnt, ws, grab, pnext, pend, wbuf,
-                                                     late);
+            select_bin<16, kChunk2, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf, late);
             break;
-        case 4:
-            select_bin<4, kChunk1, kPending, kPipe>(a, list, cnt, ws, grab, pnext, pend, wbuf,
-                                                    late);
-            break;
-        default:
-            select_bin<BASE, CH, kPending, kPipe>(a, list, cnt, ws, grab, pnext, pend, wbuf, late);
+        case 4: select_bin<4, kChunk1, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf, late); break;
+        default: select_bin<BASE, CH, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf, late);
     }
 }
 
 // Phase 2+3 of one bin, likewise.  A triaged chunk must fit the triage buffer.
-template <int BASE, int CH, bool kPending, bool kPipe>
+template <int BASE, int CH, bool kPending>
 __device__ __forceinline__ void exclude_bin_at(const SolveArgs& a, const int4* list, int cnt,
                                                bool late, RoundSched& ws, unsigned* grab,
                                                int* next, int4* dst, int32_t* wbuf,
@@ -747,59 +583,52 @@ __device__ __forceinline__ void exclude_bin_at(const SolveArgs& a, const int4* l
     constexpr int kX1 = (kPending || kChunk1 <= kScanMax) ? kChunk1 : kScanMax;
     constexpr int kX = (kPending || CH <= kScanMax) ? CH : kScanMax;
     switch (lanes_per_row<BASE>(cnt, late, ws.nwarps())) {
-        case 32:
-            exclude_bin<32, kX3, kPending, kPipe>(a, list, cnt, ws, grab, next, dst, wbuf, wscan);
-            break;
-        case 16:
-            exclude_bin<16, kX2, kPending, kPipe>(a, list, cnt, ws, grab, next, dst, wbuf, wscan);
-            break;
-        case 4:
-            exclude_bin<4, kX1, kPending, kPipe>(a, list, cnt, ws, grab, next, dst, wbuf, wscan);
-            break;
-        default:
-            exclude_bin<BASE, kX, kPending, kPipe>(a, list, cnt, ws, grab, next, dst, wbuf, wscan);
+        case 32: exclude_bin<32, kX3, kPending>(a, list, cnt, ws, grab, next, dst, wbuf, wscan); break;
+        case 16: exclude_bin<16, kX2, kPending>(a, list, cnt, ws, grab, next, dst, wbuf, wscan); break;
+        case 4: exclude_bin<4, kX1, kPending>(a, list, cnt, ws, grab, next, dst, wbuf, wscan); break;
+        default: exclude_bin<BASE, kX, kPending>(a, list, cnt, ws, grab, next, dst, wbuf, wscan);
     }
 }
 
 // Phase 1 over the bins of one worklist: hubs first, then the bins of longer
 // rows.
-template <bool kPending, bool kRange0, bool kPipe>
+template <bool kPending, bool kRange0>
 __device__ __forceinline__ void select_phase(const SolveArgs& a, const int4* src, const int* cnt,
                                              bool late, RoundSched& ws, unsigned* grab,
                                              int* pnext, int4* pend, int32_t* wbuf) {
     const int* off = a.bin_off;
     block_bin<true, kPending>(a, src + off[4], cnt[4], &grab[4], &pnext[4], pend + off[4], late);
-    select_bin_at<32, kChunk3, kPending, kPipe>(a, src + off[3], cnt[3], late, ws, &grab[3], &pnext[3],
+    select_bin_at<32, kChunk3, kPending>(a, src + off[3], cnt[3], late, ws, &grab[3], &pnext[3],
                                          pend + off[3], wbuf);
-    select_bin_at<16, kChunk2, kPending, kPipe>(a, src + off[2], cnt[2], late, ws, &grab[2], &pnext[2],
+    select_bin_at<16, kChunk2, kPending>(a, src + off[2], cnt[2], late, ws, &grab[2], &pnext[2],
                                          pend + off[2], wbuf);
-    select_bin_at<4, kChunk1, kPending, kPipe>(a, src + off[1], cnt[1], late, ws, &grab[1], &pnext[1],
+    select_bin_at<4, kChunk1, kPending>(a, src + off[1], cnt[1], late, ws, &grab[1], &pnext[1],
                                         pend + off[1], wbuf);
     if (kRange0 && !late)
         select_range0(a, ws);
     else
-        select_bin_at<1, kChunk0, kPending, kPipe>(a, src + off[0], cnt[0], late, ws, &grab[0],
+        select_bin_at<1, kChunk0, kPending>(a, src + off[0], cnt[0], late, ws, &grab[0],
                                             &pnext[0], pend + off[0], wbuf);
 }
 
 // Phase 2+3 over the bins of `list` (W_r, or P_r when kPending).
-template <bool kPending, bool kRange0, bool kPipe>
+template <bool kPending, bool kRange0>
 __device__ __forceinline__ void exclude_phase(const SolveArgs& a, const int4* list,
                                               const int* cnt, bool late, RoundSched& ws,
                                               unsigned* grab, int* next, int4* dst,
                                               int32_t* wbuf, int32_t* wscan) {
     const int* off = a.bin_off;
     block_bin<false, kPending>(a, list + off[4], cnt[4], &grab[4], &next[4], dst + off[4], late);
-    exclude_bin_at<32, kChunk3, kPending, kPipe>(a, list + off[3], cnt[3], late, ws, &grab[3],
+    exclude_bin_at<32, kChunk3, kPending>(a, list + off[3], cnt[3], late, ws, &grab[3],
                                           &next[3], dst + off[3], wbuf, wscan);
-    exclude_bin_at<16, kChunk2, kPending, kPipe>(a, list + off[2], cnt[2], late, ws, &grab[2],
+    exclude_bin_at<16, kChunk2, kPending>(a, list + off[2], cnt[2], late, ws, &grab[2],
                                           &next[2], dst + off[2], wbuf, wscan);
-    exclude_bin_at<4, kChunk1, kPending, kPipe>(a, list + off[1], cnt[1], late, ws, &grab[1],
+    exclude_bin_at<4, kChunk1, kPending>(a, list + off[1], cnt[1], late, ws, &grab[1],
                                          &next[1], dst + off[1], wbuf, wscan);
     if (kRange0 && !late)
         exclude_range0(a, ws, &next[0], dst + off[0], wbuf);
     else
-        exclude_bin_at<1, kChunk0, kPending, kPipe>(a, list + off[0], cnt[0], late, ws, &grab[0],
+        exclude_bin_at<1, kChunk0, kPending>(a, list + off[0], cnt[0], late, ws, &grab[0],
                                              &next[0], dst + off[0], wbuf, wscan);
 }
 
@@ -908,7 +737,7 @@ __device__ __forceinline__ bool round_barrier(const SolveArgs& a, Book book, Aft
 
 // kRange0: round 0 takes bin 0 by vertex ranges (a.range0_max > 0); a
 // separate instance, so that the list form keeps its register budget.
-template <bool kPending, bool kRange0, bool kPipe>
+template <bool kPending, bool kRange0>
 __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     csr_solve_kernel(const SolveArgs a) {
     __shared__ int32_t s_stage[kWarps][kStageMax];
@@ -977,7 +806,7 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
         const int rr = r;
 
         // ---- Phase 1: selection test
-        select_phase<kPending, kRange0, kPipe>(a, src, s_cnt, r > 0, ws, ctl->grab[(2 * r) & 3], pnext, a.wlp,
+        select_phase<kPending, kRange0>(a, src, s_cnt, r > 0, ws, ctl->grab[(2 * r) & 3], pnext, a.wlp,
                                wbuf);
         if (!round_barrier<kPending>(
                 a,
@@ -1000,10 +829,10 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
             for (long long i = tid; i < a.n_sure_out; i += nthreads) a.word[a.sure_out[i]] = kWordOut;
         }
         if (kPending)
-            exclude_phase<true, kRange0, kPipe>(a, a.wlp, s_pcnt, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next,
+            exclude_phase<true, kRange0>(a, a.wlp, s_pcnt, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next,
                                 dst, wbuf, wscan);
         else  // W_r's rows in the adjacency Phase 2 scans
-            exclude_phase<false, kRange0, kPipe>(a, pending_view(a, src, r > 0), s_cnt, r > 0, ws,
+            exclude_phase<false, kRange0>(a, pending_view(a, src, r > 0), s_cnt, r > 0, ws,
                                  ctl->grab[(2 * r + 1) & 3], next, dst, wbuf, wscan);
         const int cur = total + (r == 0 ? decided0 : 0);
         if (!round_barrier<kPending>(
@@ -1042,14 +871,11 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
 
 const void* csr_kernel_fn(const SolveArgs& a) {
     const bool range0 = a.range0_max > 0;
-    if (a.pipe && !range0)
-        return a.pending ? (const void*)csr_solve_kernel<true, false, true>
-                         : (const void*)csr_solve_kernel<false, false, true>;
     if (a.pending)
-        return range0 ? (const void*)csr_solve_kernel<true, true, false>
-                      : (const void*)csr_solve_kernel<true, false, false>;
-    return range0 ? (const void*)csr_solve_kernel<false, true, false>
-                  : (const void*)csr_solve_kernel<false, false, false>;
+        return range0 ? (const void*)csr_solve_kernel<true, true>
+                      : (const void*)csr_solve_kernel<true, false>;
+    return range0 ? (const void*)csr_solve_kernel<false, true>
+                  : (const void*)csr_solve_kernel<false, false>;
 }
 
 cudaError_t launch_csr_solve(const SolveArgs& a, int grid, cudaStream_t s) {
@@ -1066,12 +892,10 @@ int csr_block_size() { return kCsrBlock; }
 
 int csr_max_coresident_blocks(int device) {
     // every form: the grid must fit whichever one a solve launches
-    const void* fns[] = {(const void*)csr_solve_kernel<false, false, false>,
-                         (const void*)csr_solve_kernel<true, false, false>,
-                         (const void*)csr_solve_kernel<false, true, false>,
-                         (const void*)csr_solve_kernel<true, true, false>,
-                         (const void*)csr_solve_kernel<false, false, true>,
-                         (const void*)csr_solve_kernel<true, false, true>};
+    const void* fns[] = {(const void*)csr_solve_kernel<false, false>,
+                         (const void*)csr_solve_kernel<true, false>,
+                         (const void*)csr_solve_kernel<false, true>,
+                         (const void*)csr_solve_kernel<true, true>};
     int per_sm = 1 << 30, sms = 0;
     for (const void* fn : fns) {
         int p = 0;

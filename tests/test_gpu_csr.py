@@ -282,31 +282,6 @@ def test_range_round0_bit_exact(name, priority):
         native.mis_destroy(h)
 
 
-@pytest.mark.parametrize("name", sorted(FAMILIES))
-@pytest.mark.parametrize("order_rows", [0, 2])
-def test_staged_passes_bit_exact(name, order_rows):
-    """Passes of the bins of 4 or more lanes staged through shared memory
-    (cp.async of records and first slices), with and without the pending
-    list, at several bin bounds, on graphs with and without the create-time
-    structures."""
-    g = graph(name)
-    h = create(g, order_rows=order_rows)
-    try:
-        seed = 13
-        want = oracle.solve(g[0], g[1], g[2], seed)
-        native.mis_set_csr_range0(h, 0)
-        native.mis_set_csr_staged(h, 1)
-        for bounds in ((-1, 65536, 65536, 65536), (8, 4096, 4096, 65536), (1, 2, 3, 4),
-                       (-1, -1, -1, 2), (-1, -1, 100000, 100000)):
-            native.mis_set_csr_bins(h, bounds)
-            for pending in (1, 0):
-                native.mis_set_csr_pending(h, pending)
-                got, st = gpu_solve(h, [seed])
-                assert_same(g, seed, got, st, want)
-    finally:
-        native.mis_destroy(h)
-
-
 def test_range_round0_rejects_bad_mode():
     h = create(graph("path"), order_rows=0)
     try:
