@@ -35,8 +35,8 @@
  *
  * Threading: every entry point may be called from any host thread.  Calls on
  * the same mis_graph are serialised by the library.  The serving entry points
- * (mis_submit / mis_poll / mis_wait) are driven by one scheduler thread per
- * process that the library starts on first use.
+ * (mis_submit / mis_poll / mis_wait) are driven by scheduler threads that the
+ * library starts on first use.
  *
  * Errors: functions returning int give MIS_OK (0) or a negative MIS_E* code;
  * functions returning a pointer give NULL on error.  In both cases
@@ -457,8 +457,9 @@ void mis_destroy(mis_graph *g);
  *
  * Continuous batching over resident graphs.  mis_submit queues a request
  * (graph, seed, HOST output buffer of n bytes that must stay valid until the
- * request completes).  One scheduler thread per process owns up to max_slots
- * solve slots, each with its own CUDA stream and workspace, and loops:
+ * request completes).  A few scheduler threads per process share up to
+ * max_slots solve slots, each slot with its own CUDA stream and workspace;
+ * each thread loops over its own slots:
  *   retire  slots whose solve finished: the result is copied to the caller's
  *           buffer, then the request is reported done;
  *   admit   queued requests, oldest first, while a slot is free and the

@@ -1,11 +1,13 @@
 // serve.cu -- continuous-batching request loop (mis_submit / mis_poll / mis_wait).
 //
-// One scheduler thread per process owns up to max_slots solve slots.  A slot
-// holds a CUDA stream, an event, a solve workspace (grown on demand) and
-// pinned staging for the result.  The scheduler loops:
+// A few scheduler threads per process (kWorkers) share max_slots solve
+// slots: worker w owns slots w, w + kWorkers, ...  A slot holds a CUDA
+// stream, an event, a solve workspace (grown on demand) and pinned staging
+// for the result.  Each worker loops over its own slots:
 //
 //   retire   every slot whose event has fired: copy its result bytes to the
-//            caller's host buffer, record the status, release the slot;
+//            caller's host buffer (outside the library lock), record the
+//            status, release the slot;
 //   admit    queued requests, oldest first, while a slot is free and the
 //            workspace bytes of all admitted requests stay within the HBM
 //            budget (a request is always admitted when nothing runs);
@@ -44,6 +46,7 @@ namespace {
 
 constexpr int32_t kSingleBlockMax = 16384;  // vertices solved by one block
 constexpr int kDefaultSlots = 64;
+constexpr int kWorkers = 4;  // scheduler threads; worker w owns slots w, w + kWorkers, ...
 constexpr int kGroupScan = 1024;  // queue entries searched for a request's group
 
 int64_t now_ns() {
@@ -122,7 +125,7 @@ class Server {
         reqs_[r->id] = r;
         queue_.push_back(r);
         *t = r->id;
-        cv_work_.notify_one();
+        cv_work_.notify_all();
         return MIS_OK;
     }
 
@@ -158,15 +161,17 @@ class Server {
     }
 
     void shutdown() {
-        std::thread th;
+        std::vector<std::thread> ths;
         {
             std::lock_guard<std::mutex> lk(mu_);
             if (!running_) return;
             stop_ = true;
             cv_work_.notify_all();
-            th = std::move(thread_);
+            ths = std::move(threads_);
+            threads_.clear();
         }
-        if (th.joinable()) th.join();
+        for (std::thread& th : ths)
+            if (th.joinable()) th.join();
         std::lock_guard<std::mutex> lk(mu_);
         cudaSetDevice(device_);
         for (Slot& s : slots_) {
@@ -199,7 +204,11 @@ class Server {
         }
         stop_ = false;
         running_ = true;
-        thread_ = std::thread([this] { loop(); });
+        // every slot exists from the start, so that its owner never changes
+        slots_.clear();
+        slots_.resize((size_t)max_slots_);
+        const int nw = std::max(1, std::min(kWorkers, max_slots_));
+        for (int w = 0; w < nw; ++w) threads_.emplace_back([this, w, nw] { loop(w, nw); });
         return MIS_OK;
     }
 
@@ -353,7 +362,11 @@ class Server {
         int rc = MIS_OK;
     };
 
-    void loop() {
+    // Worker w of nw: retires, admits and launches on its own slots (w, w +
+    // nw, ...); the queue, the budget and the requests are shared under mu_.
+    // A finished slot's results are copied to the callers' buffers without
+    // the lock, then its requests are completed under it.
+    void loop(int w, int nw) {
         cudaSetDevice(device_);
         std::vector<Job> jobs;
         std::unique_lock<std::mutex> lk(mu_);
@@ -361,7 +374,8 @@ class Server {
             bool progressed = false;
             int busy = 0;
             // retire
-            for (Slot& s : slots_) {
+            for (size_t si = (size_t)w; si < slots_.size(); si += (size_t)nw) {
+                Slot& s = slots_[si];
                 if (s.nreq == 0) continue;
                 const cudaError_t q = cudaEventQuery(s.ev);
                 if (q == cudaErrorNotReady) {
@@ -371,9 +385,6 @@ class Server {
                 const int k = s.nreq;
                 Request* rs[kMaxMulti];
                 for (int i = 0; i < k; ++i) rs[i] = s.reqs[i];
-                s.nreq = 0;
-                used_ -= s.charge;
-                s.charge = 0;
                 int st = MIS_OK;
                 if (q != cudaSuccess) {
                     cudaGetLastError();
@@ -382,27 +393,29 @@ class Server {
                     if (s.ctl_pinned->err == kErrTimedOut) st = MIS_ETIMEDOUT;
                     else if (s.ctl_pinned->err != 0) st = MIS_EINTERNAL;
                 }
+                // the slot and its requests belong to this worker until they
+                // are completed: copy the results without holding the lock
                 const int64_t nb = rs[0]->g->d.result_bytes;
-                for (int i = 0; i < k; ++i) {
-                    if (st == MIS_OK && nb > 0)
+                lk.unlock();
+                if (st == MIS_OK && nb > 0)
+                    for (int i = 0; i < k; ++i)
                         std::memcpy(rs[i]->host_out, s.pinned_out + i * nb, (size_t)nb);
-                    complete_locked(lk, rs[i], st);
-                }
+                lk.lock();
+                s.nreq = 0;
+                used_ -= s.charge;
+                s.charge = 0;
+                for (int i = 0; i < k; ++i) complete_locked(lk, rs[i], st);
                 progressed = true;
             }
             // admit: choose slots and groups under the lock ...
             jobs.clear();
             while (!queue_.empty()) {
                 Slot* free_slot = nullptr;
-                for (Slot& s : slots_)
-                    if (s.nreq == 0) {
-                        free_slot = &s;
+                for (size_t si = (size_t)w; si < slots_.size(); si += (size_t)nw)
+                    if (slots_[si].nreq == 0) {
+                        free_slot = &slots_[si];
                         break;
                     }
-                if (!free_slot && (int)slots_.size() < max_slots_) {
-                    slots_.emplace_back();
-                    free_slot = &slots_.back();
-                }
                 if (!free_slot) break;
                 const GraphData& d = queue_.front()->g->d;
                 // admission by HBM footprint (a lone request always fits)
@@ -455,8 +468,8 @@ class Server {
     std::condition_variable cv_work_, cv_done_;
     std::list<Request*> queue_;  // list: grouping erases from the middle
     std::unordered_map<mis_ticket, Request*> reqs_;
-    std::deque<Slot> slots_;  // deque: slots never move once created
-    std::thread thread_;
+    std::deque<Slot> slots_;  // all max_slots_ made at start; slots never move
+    std::vector<std::thread> threads_;
     bool running_ = false;
     bool stop_ = false;
     int device_ = 0;
