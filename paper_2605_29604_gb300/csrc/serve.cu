@@ -47,6 +47,7 @@ namespace {
 constexpr int32_t kSingleBlockMax = 16384;  // vertices solved by one block
 constexpr int kDefaultSlots = 64;
 constexpr int kWorkers = 4;  // scheduler threads; worker w owns slots w, w + kWorkers, ...
+constexpr int64_t kStagingBytes = 2 << 20;  // pinned result staging per slot at start
 constexpr int kGroupScan = 1024;  // queue entries searched for a request's group
 
 int64_t now_ns() {
@@ -174,11 +175,18 @@ class Server {
             if (th.joinable()) th.join();
         std::lock_guard<std::mutex> lk(mu_);
         cudaSetDevice(device_);
+        free_slots();
+        running_ = false;
+        stop_ = false;
+    }
+
+    // Releases every slot's stream, event, workspace and buffers.
+    void free_slots() {
         for (Slot& s : slots_) {
             if (s.stream) cudaStreamSynchronize(s.stream);
             ws_free(s.ws);
-            if (s.word8) cudaFree(s.word8);
-            if (s.out_multi) cudaFree(s.out_multi);
+            dev_free(s.word8);
+            dev_free(s.out_multi);
             if (s.pinned_out) cudaFreeHost(s.pinned_out);
             if (s.seeds_pinned) cudaFreeHost(s.seeds_pinned);
             if (s.ctl_pinned) cudaFreeHost(s.ctl_pinned);
@@ -186,8 +194,6 @@ class Server {
             if (s.stream) cudaStreamDestroy(s.stream);
         }
         slots_.clear();
-        running_ = false;
-        stop_ = false;
     }
 
   private:
@@ -204,9 +210,23 @@ class Server {
         }
         stop_ = false;
         running_ = true;
-        // every slot exists from the start, so that its owner never changes
+        // every slot exists from the start, so that its owner never changes,
+        // with its stream, event and 2 MB of pinned result staging made here
+        // rather than while solves run
         slots_.clear();
         slots_.resize((size_t)max_slots_);
+        for (Slot& sl : slots_) {
+            if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaMallocHost((void**)&sl.ctl_pinned, sizeof(Ctl))) != cudaSuccess ||
+                (e = cudaMallocHost((void**)&sl.pinned_out, kStagingBytes)) != cudaSuccess) {
+                running_ = false;
+                const int rc = set_cuda_error(e, "serving: slot setup");
+                free_slots();
+                return rc;
+            }
+            sl.pinned_cap = kStagingBytes;
+        }
         const int nw = std::max(1, std::min(kWorkers, max_slots_));
         for (int w = 0; w < nw; ++w) threads_.emplace_back([this, w, nw] { loop(w, nw); });
         return MIS_OK;
@@ -250,13 +270,16 @@ class Server {
         if ((e = ws_reserve(s.ws, d.n, d.count)) != cudaSuccess)
             return set_cuda_error(e, "serving: workspace");
         const int64_t out_bytes = (int64_t)k * d.result_bytes;
+        // buffers grow geometrically: freeing pinned or cudaMalloc'd memory
+        // synchronises the whole device, so regrowth must stay rare
         if (s.pinned_cap < out_bytes) {
+            const int64_t cap = std::max(out_bytes, 2 * s.pinned_cap);
             if (s.pinned_out) cudaFreeHost(s.pinned_out);
             s.pinned_out = nullptr;
             s.pinned_cap = 0;
-            if ((e = cudaMallocHost((void**)&s.pinned_out, (size_t)out_bytes)) != cudaSuccess)
+            if ((e = cudaMallocHost((void**)&s.pinned_out, (size_t)cap)) != cudaSuccess)
                 return set_cuda_error(e, "serving: pinned result");
-            s.pinned_cap = out_bytes;
+            s.pinned_cap = cap;
         }
         const int32_t count = std::max(1, d.count);
         if (s.seeds_cap < count) {
@@ -269,22 +292,25 @@ class Server {
         }
         uint8_t* dev_out = s.ws.out;
         if (k > 1) {
-            const int64_t cap = (d.n + 15) / 16 * 16;
-            if (s.word8_cap < cap) {
-                if (s.word8) cudaFree(s.word8);
+            // from the stream-ordered pool (no device-wide synchronisation);
+            // the slot's previous solve has finished, so its buffers are free
+            const int64_t cap = std::max((d.n + 15) / 16 * 16, 2 * s.word8_cap);
+            if (s.word8_cap < (d.n + 15) / 16 * 16) {
+                dev_free(s.word8);
                 s.word8 = nullptr;
                 s.word8_cap = 0;
-                if ((e = cudaMalloc((void**)&s.word8, 4 * (size_t)kMaxMulti * cap)) != cudaSuccess)
+                if ((e = dev_alloc((void**)&s.word8, 4 * (size_t)kMaxMulti * cap)) != cudaSuccess)
                     return set_cuda_error(e, "serving: multi-seed state");
                 s.word8_cap = cap;
             }
             if (s.out_multi_cap < out_bytes) {
-                if (s.out_multi) cudaFree(s.out_multi);
+                const int64_t ocap = std::max(out_bytes, 2 * s.out_multi_cap);
+                dev_free(s.out_multi);
                 s.out_multi = nullptr;
                 s.out_multi_cap = 0;
-                if ((e = cudaMalloc((void**)&s.out_multi, (size_t)out_bytes)) != cudaSuccess)
+                if ((e = dev_alloc((void**)&s.out_multi, (size_t)ocap)) != cudaSuccess)
                     return set_cuda_error(e, "serving: multi-seed results");
-                s.out_multi_cap = out_bytes;
+                s.out_multi_cap = ocap;
             }
             dev_out = s.out_multi;
         }
@@ -456,8 +482,11 @@ class Server {
                 if (busy == 0 && queue_.empty()) {
                     cv_work_.wait(lk);
                 } else {
+                    // solves in flight: poll again at once (a timed sleep rounds
+                    // up to the host's timer slack, tens of microseconds, which
+                    // delays every retirement and admission behind it)
                     lk.unlock();
-                    std::this_thread::sleep_for(std::chrono::microseconds(5));
+                    std::this_thread::yield();
                     lk.lock();
                 }
             }
