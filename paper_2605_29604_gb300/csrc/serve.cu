@@ -294,8 +294,8 @@ class Server {
         if (k > 1) {
             // from the stream-ordered pool (no device-wide synchronisation);
             // the slot's previous solve has finished, so its buffers are free
-            const int64_t cap = std::max((d.n + 15) / 16 * 16, 2 * s.word8_cap);
-            if (s.word8_cap < (d.n + 15) / 16 * 16) {
+            const int64_t cap = std::max<int64_t>((d.n + 15) / 16 * 16, 2 * s.word8_cap);
+            if (s.word8_cap < (int64_t)(d.n + 15) / 16 * 16) {
                 dev_free(s.word8);
                 s.word8 = nullptr;
                 s.word8_cap = 0;
