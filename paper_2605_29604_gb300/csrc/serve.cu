@@ -446,9 +446,13 @@ class Server {
                 const GraphData& d = queue_.front()->g->d;
                 // admission by HBM footprint (a lone request always fits)
                 if (used_ > 0 && used_ + charge_for(d, 1) > budget_) break;
-                // the largest group that fits the budget
+                // the largest group that fits the budget and the slot's pinned
+                // staging (regrowing that would synchronise the device)
                 int kmax = kMaxMulti;
                 while (kmax > 1 && used_ > 0 && used_ + charge_for(d, kmax) > budget_) --kmax;
+                if (d.result_bytes > 0)
+                    kmax = (int)std::max<int64_t>(
+                        1, std::min<int64_t>(kmax, free_slot->pinned_cap / d.result_bytes));
                 Job j;
                 j.slot = free_slot;
                 j.k = take_group_locked(j.rs, kmax);
