@@ -164,8 +164,6 @@ typedef struct mis_stats {
                                 0's selection test reads; -1 without one */
     int32_t tile_payload;    /* MIS_PATH_TILE_TC: the MIS_TILE_* form that ran; -1
                                 on other paths */
-    int32_t csr_scatter;     /* CSR path: 1 when the exclusion test read flags set
-                                by the candidates (mis_set_csr_scatter) */
 } mis_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -352,18 +350,6 @@ int mis_tile_payload_ex(mis_graph *g, int32_t payload, void *out, void *stream);
  * values, MIS_EBUSY while served requests on `g` are in flight. */
 int mis_set_csr_range0(mis_graph *g, int32_t on);
 
-/* CSR path: how Phase 2's exclusion test (Sec. 3.1: v is out when an
- * alive neighbour was selected, N_c = A x C > 0) is evaluated.  on = 1: in
- * Phase 1 every candidate, having just read its row, sets an exclusion flag
- * on each neighbour (A is symmetric, so this forms the same product from the
- * candidates' side, into a flag array apart from the vertex states), and
- * Phase 2 reads one flag per undecided non-candidate instead of scanning its
- * row; on = 0 (default): Phase 2 scans the rows.  Used with the triage form
- * of Phase 2 (mis_set_csr_pending 0; ignored with the pending list).  Same
- * result either way (chosen by mis_autotune).  MIS_EINVAL for other values,
- * MIS_EBUSY while served requests on `g` are in flight. */
-int mis_set_csr_scatter(mis_graph *g, int32_t on);
-
 /* The autotuner's choice for a graph. */
 typedef struct mis_tuning {
     int32_t path;        /* MIS_PATH_CSR, MIS_PATH_TILE or MIS_PATH_TILE_TC */
@@ -378,7 +364,6 @@ typedef struct mis_tuning {
                             the graph has round-0 classes) */
     int32_t tile_payload;/* MIS_PATH_TILE_TC: the MIS_TILE_* form of the choice,
                             else -1 */
-    int32_t csr_scatter; /* CSR: the mis_set_csr_scatter mode of the choice */
 } mis_tuning;
 
 /*

@@ -75,7 +75,7 @@ struct StageLog {
 int64_t ws_bytes_for(int64_t n, int32_t count) {
     const int64_t cap = (n + 15) / 16 * 16;
     return 4 * cap + 16 * cap * 3 + (cap / 32 + 1) * 4 + 2 * 4 * (cap / 8) + (int64_t)sizeof(Ctl) +
-           (int64_t)sizeof(PhaseTimes) + 8 * std::max<int64_t>(count, 1) + 2 * cap;
+           (int64_t)sizeof(PhaseTimes) + 8 * std::max<int64_t>(count, 1) + cap;
 }
 
 void ws_free(Workspace& w) {
@@ -90,7 +90,6 @@ void ws_free(Workspace& w) {
     dfree(w.times);
     dfree(w.seeds);
     dfree(w.out);
-    dfree(w.xflag);
     w = Workspace();
 }
 
@@ -108,8 +107,7 @@ cudaError_t ws_reserve(Workspace& w, int64_t n, int32_t count) {
         (e = dalloc(&w.rbl1, cap / 8, &b)) != cudaSuccess ||
         (e = dalloc(&w.ctl, 1, &b)) != cudaSuccess || (e = dalloc(&w.times, 1, &b)) != cudaSuccess ||
         (e = dalloc(&w.seeds, std::max(count, 1), &b)) != cudaSuccess ||
-        (e = dalloc(&w.out, cap, &b)) != cudaSuccess ||
-        (e = dalloc(&w.xflag, cap, &b)) != cudaSuccess) {
+        (e = dalloc(&w.out, cap, &b)) != cudaSuccess) {
         ws_free(w);
         return e;
     }
@@ -437,8 +435,6 @@ SolveArgs make_args(mis_graph* g, Workspace& w) {
     a.n_sure_out = d.n_sure_out;
     a.pending = g->csr_pending;
     a.range0_max = (g->csr_range0 && !d.r0class && d.thr[0] >= 1) ? d.thr[0] : 0;
-    a.scatter = g->csr_scatter;
-    a.xflag = w.xflag;
     a.priority = g->opt.priority;
     a.ctl = w.ctl;
     a.times = w.times;
@@ -595,7 +591,6 @@ struct TuneChoice {
     int32_t pending = 0; // CSR: Phase 1 lists its non-candidates for Phase 2
     int32_t range0 = 1;  // CSR: round 0 takes bin 0 by vertex ranges
     int32_t payload = 0; // tensor-core tile path: MIS_TILE_* form
-    int32_t scatter = 0; // CSR: exclusion by flags (triage form only)
 };
 
 std::mutex g_tune_mu;
@@ -618,7 +613,6 @@ void tune_load_locked() {
             if (!(ss >> c.pending)) c.pending = 0;  // lines written before the field
             if (!(ss >> c.range0)) c.range0 = 1;
             if (!(ss >> c.payload)) c.payload = 0;
-            if (!(ss >> c.scatter)) c.scatter = 0;
             g_tune_cache[key] = c;
         }
     }
@@ -632,8 +626,7 @@ void tune_save_locked() {
         const TuneChoice& c = kv.second;
         out << kv.first << ' ' << c.path << ' ' << c.param << ' ' << c.bounds[0] << ' '
             << c.bounds[1] << ' ' << c.bounds[2] << ' ' << c.bounds[3] << ' ' << c.grid << ' '
-            << c.ms << ' ' << c.pending << ' ' << c.range0 << ' ' << c.payload << ' '
-            << c.scatter << '\n';
+            << c.ms << ' ' << c.pending << ' ' << c.range0 << ' ' << c.payload << '\n';
     }
 }
 
@@ -752,7 +745,6 @@ int apply_choice(mis_graph* g, const TuneChoice& c) {
     g->tpr = c.param;
     g->csr_pending = c.pending;
     g->csr_range0 = c.range0;
-    g->csr_scatter = c.scatter;
     if (g->last_stream) cudaStreamSynchronize(g->last_stream);
     const int rc = rebin(g, thr, g->own_stream);
     if (rc != MIS_OK) return rc;
@@ -818,21 +810,6 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
         bins(INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, maxg * 2 / 3);
     }
     bins(-1, 65536, 65536, 65536, 0);                                     // four lanes per row
-    // the exclusion test by flags from the candidates' rows (triage form)
-    {
-        const size_t k0 = cands.size();
-        bins(-1, 65536, 65536, 65536, 0);
-        bins(8, 4096, 4096, 65536, 0);
-        bins(INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, INT32_MAX - 1, 0);
-        for (size_t k = k0; k < cands.size();) {
-            if (cands[k].pending) {
-                cands.erase(cands.begin() + (long)k);
-                continue;
-            }
-            cands[k].scatter = 1;
-            ++k;
-        }
-    }
     // without round-0 classes, round 0 can take bin 0 by vertex ranges (the
     // candidates above) or from its list
     if (!g->d.r0class) {
@@ -888,10 +865,10 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
         if (log)
             std::fprintf(stderr,
                          "tcmis tune: path %d param %d bounds %d %d %d %d grid %d pending %d "
-                         "range0 %d scatter %d payload %d: %.4f ms\n",
+                         "range0 %d payload %d: %.4f ms\n",
                          c.path, c.param, c.bounds[0], c.bounds[1], c.bounds[2], c.bounds[3],
                          c.path == MIS_PATH_CSR ? g->grid : g->tile_grid, c.pending, c.range0,
-                         c.scatter, c.payload, c.ms);
+                         c.payload, c.ms);
         if (c.ms > 0.f && (best.ms < 0.f || c.ms < best.ms)) best = c;
     }
     if (best.ms < 0.f) return set_error(MIS_EINTERNAL, "autotuner found no working configuration");
@@ -912,7 +889,6 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
         out->csr_pending = best.path == MIS_PATH_CSR ? best.pending : 0;
         out->csr_range0 = (best.path == MIS_PATH_CSR && !g->d.r0class) ? best.range0 : 0;
         out->tile_payload = best.path == MIS_PATH_TILE_TC ? best.payload : -1;
-        out->csr_scatter = best.path == MIS_PATH_CSR ? best.scatter : 0;
         out->arcs_per_tile = apt;
         out->candidates = (int32_t)cands.size();
     }
@@ -1342,16 +1318,6 @@ int mis_set_tile_payload(mis_graph* g, int32_t payload) {
     return MIS_OK;
 }
 
-int mis_set_csr_scatter(mis_graph* g, int32_t on) {
-    clear_error();
-    if (!g) return set_error(MIS_EINVAL, "null graph");
-    if (on != 0 && on != 1) return set_error(MIS_EINVAL, "scatter must be 0 or 1");
-    std::lock_guard<std::mutex> lk(g->mu);
-    if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
-    g->csr_scatter = on;
-    return MIS_OK;
-}
-
 int mis_set_csr_range0(mis_graph* g, int32_t on) {
     clear_error();
     if (!g) return set_error(MIS_EINVAL, "null graph");
@@ -1467,7 +1433,6 @@ int mis_get_stats(mis_graph* g, mis_stats* st) {
     st->threads_per_row = g->tpr;
     st->tile = g->d.tiles.T;
     st->csr_pending = g->csr_pending;
-    st->csr_scatter = g->last_path == MIS_PATH_CSR && g->csr_scatter && !g->csr_pending ? 1 : 0;
     st->tile_payload = g->last_path == MIS_PATH_TILE_TC ? g->tile_payload : -1;
     const bool csr = g->last_path == MIS_PATH_CSR;
     st->sure_in = csr ? g->d.n_sure_in : 0;

@@ -221,7 +221,6 @@ int adopt_csr(mis_graph* g, int32_t n, const int32_t* rp, const int32_t* col, vo
     g->tile_slots = g2->tile_slots;
     g->csr_pending = g2->csr_pending;
     g->csr_range0 = g2->csr_range0;
-    g->csr_scatter = g2->csr_scatter;
     g->tile_payload = g2->tile_payload;
     g->cluster = g2->cluster;
     mis_destroy(g2);  // frees the old graph's data

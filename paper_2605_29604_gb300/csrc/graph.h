@@ -36,7 +36,6 @@ struct Workspace {
     PhaseTimes* times = nullptr;
     uint64_t* seeds = nullptr;
     uint8_t* out = nullptr;
-    uint8_t* xflag = nullptr;  // exclusion flags of the CSR kernel's scatter form
     int64_t bytes = 0;
 };
 
@@ -120,7 +119,6 @@ struct mis_graph {
     int32_t csr_pending = 0;      // CSR kernel: Phase 1 lists non-candidates for Phase 2
     int32_t tile_payload = 0;     // tensor-core tile path: payload form (MIS_TILE_*)
     tcmis::ClusterPlan cluster;   // cluster path: its launch shape
-    int32_t csr_scatter = 0;      // CSR kernel: exclusion by flags from the candidates
     int32_t csr_range0 = 1;       // CSR kernel: round 0 tests bin 0 by vertex ranges
                                   // (graphs without round-0 classes only)
     cudaStream_t own_stream = nullptr;

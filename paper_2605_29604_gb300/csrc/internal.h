@@ -80,10 +80,6 @@ struct SolveArgs {
     // > 0: round 0 tests bin 0 (degree 1 .. range0_max) by vertex ranges over
     // row_ptr instead of its order0 list (graphs without round-0 classes)
     int32_t range0_max = 0;
-    // 1 (with pending = 0): the exclusion test reads flags that Phase 1's
-    // candidates set over their rows (xflag: n bytes, padded to 16)
-    int32_t scatter = 0;
-    uint8_t* xflag = nullptr;
     int32_t pending = 0;              // 1: Phase 1 lists its non-candidates for Phase 2
                                       // (in wlp); 0: Phase 2 triages W_r itself
     // tile-CSR (used by the tile kernels only)

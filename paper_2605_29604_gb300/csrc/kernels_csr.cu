@@ -215,41 +215,11 @@ __device__ __forceinline__ void mark_selected(const SolveArgs& a, int v) {
     }
 }
 
-// ---- the scatter form of the exclusion test (kScatter)
-//
-// Phase 2 needs N_c(v) > 0 for the undecided non-candidates, the product
-// N_c = A x C of Sec. 3.1.  With A symmetric it can be formed from the
-// candidates' side: in Phase 1 a candidate has just read its whole row, and
-// sets the exclusion flag (a byte array apart from the words, so the
-// round-start snapshot the other selection tests read is untouched) of every
-// neighbour; Phase 2 then reads one flag per undecided non-candidate instead
-// of scanning its row.  A flag is read before it is written, so the hub
-// flags that thousands of candidates share see few stores.  No flag is
-// cleared: an excluded vertex is never tested again, a survivor's flag is 0
-// (two candidates are never adjacent), and the array is zeroed at init.
-__device__ __forceinline__ void flag_excluded(uint8_t* __restrict__ f, int u) {
-    if (f[u] == 0) f[u] = 1;
-}
-
-// The lanes of a group of TPR lanes set the flags of the row [b, e) of col
-// (16-byte slices from the aligned start, as the scans read them).
-template <int TPR>
-__device__ __forceinline__ void flag_row(const int32_t* __restrict__ col, int b, int e,
-                                         uint8_t* __restrict__ f, unsigned glane) {
-    for (int p0 = (b & ~3) + 4 * (int)glane; p0 < e; p0 += 4 * TPR) {
-        const int4 c = __ldg(reinterpret_cast<const int4*>(col + p0));
-        if (p0 >= b) flag_excluded(f, c.x);
-        if (p0 + 1 >= b && p0 + 1 < e) flag_excluded(f, c.y);
-        if (p0 + 2 >= b && p0 + 2 < e) flag_excluded(f, c.z);
-        if (p0 + 3 >= b && p0 + 3 < e) flag_excluded(f, c.w);
-    }
-}
-
 // Phase 1, bins 0..3: selection test of every row of the bin's list W_r.
 // Candidates are marked in the MIS.  kPending: the others form the pending
 // list P_r of Phase 2 (appended to pdst, counted in *pnext), each entry the
 // row's record in the adjacency Phase 2 scans.
-template <int TPR, int CH, bool kPending, bool kScatter = false>
+template <int TPR, int CH, bool kPending>
 __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __restrict__ list,
                                            int cnt, RoundSched& ws, unsigned* grab, int* pnext,
                                            int4* __restrict__ pdst, int32_t* wbuf, bool late) {
@@ -288,7 +258,6 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __res
                     if (valid[i] && !blocked[i]) {
                         a.word[rec[i].x] = wv[i] | kWordInSet;
                         mark_selected(a, rec[i].x);
-                        if (kScatter) flag_row<1>(select_col(a, late), rec[i].y, rec[i].w, a.xflag, 0u);
                     }
                     if (kPending)
                         fill = stage_keep(valid[i] && blocked[i], base + (int)lane + 32 * i, wbuf,
@@ -307,8 +276,6 @@ __device__ __forceinline__ void select_bin(const SolveArgs& a, const int4* __res
                     a.word[rec.x] = wv | kWordInSet;
                     mark_selected(a, rec.x);
                 }
-                if (kScatter && valid && !blocked)
-                    flag_row<TPR>(select_col(a, late), rec.y, rec.w, a.xflag, glane);
                 if (kPending) fill = stage_keep(valid && blocked && lead, item, wbuf, fill);
             }
             if (kPending)
@@ -443,7 +410,6 @@ __device__ __forceinline__ void flush_stage_v(const SolveArgs& a, const int32_t*
 // Phase 1 of round 0, bin 0, by vertex ranges.  Candidates are marked in the
 // MIS; the non-candidates are found again by Phase 2's range pass (no
 // pending list).
-template <bool kScatter>
 __device__ __forceinline__ void select_range0(const SolveArgs& a, const RoundSched& ws) {
     constexpr int R = kRowsPerLane;
     const unsigned lane = lane_id();
@@ -467,7 +433,6 @@ __device__ __forceinline__ void select_range0(const SolveArgs& a, const RoundSch
             if (valid[i] && !blocked[i]) {
                 a.word[rec[i].x] = wv[i] | kWordInSet;
                 mark_selected(a, rec[i].x);
-                if (kScatter) flag_row<1>(a.col_sel, rec[i].y, rec[i].w, a.xflag, 0u);
             }
     }
 }
@@ -511,79 +476,11 @@ __device__ __forceinline__ void exclude_range0(const SolveArgs& a, const RoundSc
     flush_stage_v(a, wbuf, fill, next, dst);
 }
 
-// Phase 2+3 of round 0, bin 0, by vertex ranges, scatter form: the light
-// rows still undecided read their exclusion flag.
-__device__ __forceinline__ void exclude_range0_flags(const SolveArgs& a, const RoundSched& ws,
-                                                     int* next, int4* __restrict__ dst,
-                                                     int32_t* wbuf) {
-    const unsigned lane = lane_id();
-    int v0, v1;
-    range0_slice(a, ws, v0, v1);
-    int fill = 0;
-    for (int base = v0; base < v1; base += 32) {
-        const int v = base + (int)lane;
-        bool keep = false;
-        if (v < v1) {
-            int4 rec;
-            if (range0_record(a, v, rec) && (ld_word_l1(a.word + v) >> 29) == 1u) {
-                if (a.xflag[v]) a.word[v] = kWordOut;
-                else keep = true;
-            }
-        }
-        fill = stage_keep(keep, v, wbuf, fill);
-        if (fill > kStageMax - 32) {
-            flush_stage_v(a, wbuf, fill, next, dst);
-            fill = 0;
-        }
-    }
-    flush_stage_v(a, wbuf, fill, next, dst);
-}
-
-// Phases 2+3, scatter form, over every bin of `list` (W_r in the adjacency
-// the next round reads): an undecided non-candidate is out exactly when its
-// exclusion flag is set; the others are appended to W_{r+1}.  One lane per
-// row whatever its degree: no row is read.
-template <bool kRange0>
-__device__ __forceinline__ void exclude_phase_flags(const SolveArgs& a, const int4* list,
-                                                    const int* cnt, bool late, RoundSched& ws,
-                                                    int* next, int4* dst, int32_t* wbuf) {
-    const int* off = a.bin_off;
-    const unsigned lane = lane_id();
-    const int nw = ws.nwarps();
-    for (int j = 0; j < kBins; ++j) {
-        if (kRange0 && j == 0 && !late) {
-            exclude_range0_flags(a, ws, &next[0], dst + off[0], wbuf);
-            continue;
-        }
-        const int c = cnt[j];
-        if (c <= 0) continue;
-        const int per = (int)((((long long)c + nw - 1) / nw + 31) / 32 * 32);
-        const int c0 = (int)min((long long)ws.gw * per, (long long)c);
-        const int c1 = min(c0 + per, c);
-        const int4* L = list + off[j];
-        int fill = 0;
-        for (int base = c0; base < c1; base += 32) {
-            const int item = base + (int)lane;
-            bool keep = false;
-            if (item < c1) {
-                const int v = __ldg(&L[item].x);
-                if ((ld_word_l1(a.word + v) >> 29) == 1u) {  // an undecided non-candidate
-                    if (a.xflag[v]) a.word[v] = kWordOut;
-                    else keep = true;
-                }
-            }
-            fill = stage_keep(keep, item, wbuf, fill);
-            fill = flush_if_full(wbuf, fill, 32, L, &next[j], dst + off[j]);
-        }
-        flush_stage(wbuf, fill, L, &next[j], dst + off[j]);
-    }
-}
-
 // Bin 4 (hubs): the whole block scans one row at a time.  kSelect: Phase 1
 // (kPending: non-candidates appended to the pending list), else Phase 2+3
 // (survivors appended to W_{r+1}); hub rows are few, so entries are appended
 // one by one.
-template <bool kSelect, bool kPending, bool kScatter = false>
+template <bool kSelect, bool kPending>
 __device__ __forceinline__ void block_bin(const SolveArgs& a, const int4* __restrict__ list,
                                           int cnt, unsigned* grab, int* next,
                                           int4* __restrict__ dst, bool late) {
@@ -621,9 +518,6 @@ __device__ __forceinline__ void block_bin(const SolveArgs& a, const int4* __rest
                 break;
             }
         }
-        if (kScatter && kSelect && !found)  // a hub candidate: the block flags its row
-            for (int p = b + (int)threadIdx.x; p < rec.w; p += (int)blockDim.x)
-                flag_excluded(a.xflag, __ldg(col + p));
         if (threadIdx.x == 0 && !skip) {
             if (kSelect) {
                 if (!found) {
@@ -662,26 +556,19 @@ __device__ __forceinline__ int lanes_per_row(int cnt, bool late, int nwarps) {
 }
 
 // Phase 1 of bin j (base width BASE, chunk CH) at the width lanes_per_row picks.
-template <int BASE, int CH, bool kPending, bool kScatter>
+template <int BASE, int CH, bool kPending>
 __device__ __forceinline__ void select_bin_at(const SolveArgs& a, const int4* list, int cnt,
                                               bool late, RoundSched& ws, unsigned* grab,
                                               int* pnext, int4* pend, int32_t* wbuf) {
     switch (lanes_per_row<BASE>(cnt, late, ws.nwarps())) {
         case 32:
-            select_bin<32, kChunk3, kPending, kScatter>(a, list, cnt, ws, grab, pnext, pend,
-                                                        wbuf, late);
+            select_bin<32, kChunk3, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf, late);
             break;
         case 16:
-            select_bin<16, kChunk2, kPending, kScatter>(a, list, cnt, ws, grab, pnext, pend,
-                                                        wbuf, late);
+            select_bin<16, kChunk2, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf, late);
             break;
-        case 4:
-            select_bin<4, kChunk1, kPending, kScatter>(a, list, cnt, ws, grab, pnext, pend, wbuf,
-                                                       late);
-            break;
-        default:
-            select_bin<BASE, CH, kPending, kScatter>(a, list, cnt, ws, grab, pnext, pend, wbuf,
-                                                     late);
+        case 4: select_bin<4, kChunk1, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf, late); break;
+        default: select_bin<BASE, CH, kPending>(a, list, cnt, ws, grab, pnext, pend, wbuf, late);
     }
 }
 
@@ -705,23 +592,22 @@ __device__ __forceinline__ void exclude_bin_at(const SolveArgs& a, const int4* l
 
 // Phase 1 over the bins of one worklist: hubs first, then the bins of longer
 // rows.
-template <bool kPending, bool kRange0, bool kScatter>
+template <bool kPending, bool kRange0>
 __device__ __forceinline__ void select_phase(const SolveArgs& a, const int4* src, const int* cnt,
                                              bool late, RoundSched& ws, unsigned* grab,
                                              int* pnext, int4* pend, int32_t* wbuf) {
     const int* off = a.bin_off;
-    block_bin<true, kPending, kScatter>(a, src + off[4], cnt[4], &grab[4], &pnext[4],
-                                        pend + off[4], late);
-    select_bin_at<32, kChunk3, kPending, kScatter>(a, src + off[3], cnt[3], late, ws, &grab[3], &pnext[3],
+    block_bin<true, kPending>(a, src + off[4], cnt[4], &grab[4], &pnext[4], pend + off[4], late);
+    select_bin_at<32, kChunk3, kPending>(a, src + off[3], cnt[3], late, ws, &grab[3], &pnext[3],
                                          pend + off[3], wbuf);
-    select_bin_at<16, kChunk2, kPending, kScatter>(a, src + off[2], cnt[2], late, ws, &grab[2], &pnext[2],
+    select_bin_at<16, kChunk2, kPending>(a, src + off[2], cnt[2], late, ws, &grab[2], &pnext[2],
                                          pend + off[2], wbuf);
-    select_bin_at<4, kChunk1, kPending, kScatter>(a, src + off[1], cnt[1], late, ws, &grab[1], &pnext[1],
+    select_bin_at<4, kChunk1, kPending>(a, src + off[1], cnt[1], late, ws, &grab[1], &pnext[1],
                                         pend + off[1], wbuf);
     if (kRange0 && !late)
-        select_range0<kScatter>(a, ws);
+        select_range0(a, ws);
     else
-        select_bin_at<1, kChunk0, kPending, kScatter>(a, src + off[0], cnt[0], late, ws, &grab[0],
+        select_bin_at<1, kChunk0, kPending>(a, src + off[0], cnt[0], late, ws, &grab[0],
                                             &pnext[0], pend + off[0], wbuf);
 }
 
@@ -851,9 +737,7 @@ __device__ __forceinline__ bool round_barrier(const SolveArgs& a, Book book, Aft
 
 // kRange0: round 0 takes bin 0 by vertex ranges (a.range0_max > 0); a
 // separate instance, so that the list form keeps its register budget.
-// kScatter: the exclusion test by flags set from the candidates' rows (the
-// triage form only, kPending false).
-template <bool kPending, bool kRange0, bool kScatter>
+template <bool kPending, bool kRange0>
 __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     csr_solve_kernel(const SolveArgs a) {
     __shared__ int32_t s_stage[kWarps][kStageMax];
@@ -875,13 +759,6 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
     // ---- init: Eq. 1 priorities (and, direct, the create-time result bytes)
     if (a.out0) init_keyed(a);
     else init_words(a, (a.n + 15) / 16 * 16, true, a.direct ? a.out : nullptr);  // padded to 16
-    if (kScatter) {  // the exclusion flags start clear (16-byte stores; padded to 16)
-        const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-        const long long nthreads = (long long)gridDim.x * blockDim.x;
-        uint4* f = reinterpret_cast<uint4*>(a.xflag);
-        for (long long i = tid; i < ((long long)a.n + 15) / 16; i += nthreads)
-            f[i] = make_uint4(0u, 0u, 0u, 0u);
-    }
     if (!round_barrier<kPending>(
             a,
             [times]() {
@@ -929,7 +806,7 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
         const int rr = r;
 
         // ---- Phase 1: selection test
-        select_phase<kPending, kRange0, kScatter>(a, src, s_cnt, r > 0, ws, ctl->grab[(2 * r) & 3], pnext, a.wlp,
+        select_phase<kPending, kRange0>(a, src, s_cnt, r > 0, ws, ctl->grab[(2 * r) & 3], pnext, a.wlp,
                                wbuf);
         if (!round_barrier<kPending>(
                 a,
@@ -951,10 +828,7 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
             const long long nthreads = (long long)nblocks * blockDim.x;
             for (long long i = tid; i < a.n_sure_out; i += nthreads) a.word[a.sure_out[i]] = kWordOut;
         }
-        if (kScatter)  // flags set in Phase 1; records in the adjacency the next round reads
-            exclude_phase_flags<kRange0>(a, pending_view(a, src, r > 0), s_cnt, r > 0, ws, next,
-                                         dst, wbuf);
-        else if (kPending)
+        if (kPending)
             exclude_phase<true, kRange0>(a, a.wlp, s_pcnt, r > 0, ws, ctl->grab[(2 * r + 1) & 3], next,
                                 dst, wbuf, wscan);
         else  // W_r's rows in the adjacency Phase 2 scans
@@ -997,14 +871,11 @@ __global__ void __launch_bounds__(kCsrBlock, kCsrMinBlocksPerSm)
 
 const void* csr_kernel_fn(const SolveArgs& a) {
     const bool range0 = a.range0_max > 0;
-    if (a.scatter && !a.pending)
-        return range0 ? (const void*)csr_solve_kernel<false, true, true>
-                      : (const void*)csr_solve_kernel<false, false, true>;
     if (a.pending)
-        return range0 ? (const void*)csr_solve_kernel<true, true, false>
-                      : (const void*)csr_solve_kernel<true, false, false>;
-    return range0 ? (const void*)csr_solve_kernel<false, true, false>
-                  : (const void*)csr_solve_kernel<false, false, false>;
+        return range0 ? (const void*)csr_solve_kernel<true, true>
+                      : (const void*)csr_solve_kernel<true, false>;
+    return range0 ? (const void*)csr_solve_kernel<false, true>
+                  : (const void*)csr_solve_kernel<false, false>;
 }
 
 cudaError_t launch_csr_solve(const SolveArgs& a, int grid, cudaStream_t s) {
@@ -1021,12 +892,10 @@ int csr_block_size() { return kCsrBlock; }
 
 int csr_max_coresident_blocks(int device) {
     // every form: the grid must fit whichever one a solve launches
-    const void* fns[] = {(const void*)csr_solve_kernel<false, false, false>,
-                         (const void*)csr_solve_kernel<true, false, false>,
-                         (const void*)csr_solve_kernel<false, true, false>,
-                         (const void*)csr_solve_kernel<true, true, false>,
-                         (const void*)csr_solve_kernel<false, false, true>,
-                         (const void*)csr_solve_kernel<false, true, true>};
+    const void* fns[] = {(const void*)csr_solve_kernel<false, false>,
+                         (const void*)csr_solve_kernel<true, false>,
+                         (const void*)csr_solve_kernel<false, true>,
+                         (const void*)csr_solve_kernel<true, true>};
     int per_sm = 1 << 30, sms = 0;
     for (const void* fn : fns) {
         int p = 0;

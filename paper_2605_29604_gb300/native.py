@@ -69,7 +69,7 @@ class mis_stats(ctypes.Structure):
                 ("sure_in", ctypes.c_int64), ("sure_out", ctypes.c_int64),
                 ("tested_arcs", ctypes.c_int64), ("keyed", ctypes.c_int64),
                 ("tested_rows", ctypes.c_int64), ("tested_prefix_arcs", ctypes.c_int64),
-                ("tile_payload", ctypes.c_int32), ("csr_scatter", ctypes.c_int32)]
+                ("tile_payload", ctypes.c_int32)]
 
 
 class mis_tuning(ctypes.Structure):
@@ -78,7 +78,7 @@ class mis_tuning(ctypes.Structure):
                 ("candidates", ctypes.c_int32), ("ms", ctypes.c_float),
                 ("csr_pending", ctypes.c_int32),
                 ("arcs_per_tile", ctypes.c_double), ("csr_range0", ctypes.c_int32),
-                ("tile_payload", ctypes.c_int32), ("csr_scatter", ctypes.c_int32)]
+                ("tile_payload", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -146,8 +146,6 @@ def lib():
         L.mis_tile_payload_ex.restype = ctypes.c_int
         L.mis_set_tile_payload.argtypes = [P, i32]
         L.mis_set_tile_payload.restype = ctypes.c_int
-        L.mis_set_csr_scatter.argtypes = [P, i32]
-        L.mis_set_csr_scatter.restype = ctypes.c_int
         L.mis_set_csr_range0.argtypes = [P, i32]
         L.mis_set_csr_range0.restype = ctypes.c_int
         L.mis_destroy.argtypes = [P]
@@ -187,7 +185,7 @@ def lib():
 EXPORTED = [
     "mis_options_init", "mis_create", "mis_create_ex", "mis_create_batch", "mis_graph_count",
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
-    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_set_csr_range0", "mis_set_csr_scatter", "mis_set_tile_payload", "mis_tile_payload_ex", "mis_cluster_max_vertices", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
+    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_set_csr_range0", "mis_set_tile_payload", "mis_tile_payload_ex", "mis_cluster_max_vertices", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
     "mis_solve_noalloc", "mis_update_edges", "mis_repair", "mis_add_vertices",
 ]
@@ -380,10 +378,6 @@ def mis_tile_payload_ex(h, payload, out_ptr, stream=None):
 
 def mis_set_tile_payload(h, payload):
     return _check(lib().mis_set_tile_payload(h, int(payload)))
-
-
-def mis_set_csr_scatter(h, on):
-    return _check(lib().mis_set_csr_scatter(h, int(on)))
 
 
 def mis_set_csr_range0(h, on):

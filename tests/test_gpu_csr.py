@@ -282,31 +282,6 @@ def test_range_round0_bit_exact(name, priority):
         native.mis_destroy(h)
 
 
-@pytest.mark.parametrize("name", sorted(FAMILIES))
-@pytest.mark.parametrize("order_rows", [0, 2])
-def test_scatter_exclusion_bit_exact(name, order_rows):
-    """The exclusion test read from flags that the candidates set over their
-    rows, at several bin bounds, with and without round 0's range mode, on
-    graphs with and without the create-time structures."""
-    g = graph(name)
-    h = create(g, order_rows=order_rows)
-    try:
-        seed = 17
-        want = oracle.solve(g[0], g[1], g[2], seed)
-        native.mis_set_csr_pending(h, 0)
-        native.mis_set_csr_scatter(h, 1)
-        for bounds in ((-1, 65536, 65536, 65536), (8, 4096, 4096, 65536), (1, 2, 3, 4),
-                       (-1, -1, -1, 2), (2**31 - 2,) * 4):
-            native.mis_set_csr_bins(h, bounds)
-            for range0 in (1, 0):
-                native.mis_set_csr_range0(h, range0)
-                got, st = gpu_solve(h, [seed])
-                assert st.csr_scatter == 1
-                assert_same(g, seed, got, st, want)
-    finally:
-        native.mis_destroy(h)
-
-
 def test_range_round0_rejects_bad_mode():
     h = create(graph("path"), order_rows=0)
     try:
