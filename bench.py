@@ -50,6 +50,7 @@ METRIC = "edges/s to full MIS on 1 GB300"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 PATH_NAMES = {1: "csr", 2: "tile", 3: "tile_tc", 4: "push", 5: "cluster"}
+PAYLOADS = {"bits": 0, "b1": 1, "int8": 2, "fp16": 3}  # mis_set_tile_payload forms
 
 
 def _peak_hbm():
@@ -319,8 +320,10 @@ def tuned_handle(native, n, drp, dcol, stream, local, order_rows, args):
         if args.grid:
             native.mis_set_grid(h, args.grid)
     elif args.path:
-        native.mis_set_path(h, {"tile": 2, "tile_tc": 3, "push": 4}[args.path],
-                            args.tile if args.path != "push" else 0)
+        if args.path == "tile_tc":
+            native.mis_set_tile_payload(h, PAYLOADS[args.payload])
+        native.mis_set_path(h, {"tile": 2, "tile_tc": 3, "push": 4, "cluster": 5}[args.path],
+                            args.tile if args.path in ("tile", "tile_tc") else 0)
     else:
         t0 = time.perf_counter()
         tuning = native.mis_autotune(h, 3)
@@ -378,6 +381,29 @@ def run_single(args):
     value = replica_throughput(world, args.steps, arcs, total_ms)
     launch_s = (total_ms / 1e3) / args.steps
     full_result = out[:n].cpu().numpy()
+    # with a pinned tile path: several seeds of the same graph per launch on it
+    path_multi = None
+    if args.path in ("tile", "tile_tc") and args.multi > 0:
+        kk = min(args.multi, 8)
+        mout = torch.empty(max(kk * n, 1), dtype=torch.uint8, device="cuda")
+        mseeds = np.arange(1, kk + 1, dtype=np.uint64)
+        flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
+        for _ in range(max(args.warmup, 3)):
+            native.mis_solve_multi_ex(h, mseeds, mout.data_ptr(), stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for e0, e1 in ev:
+            flush.add_(1.0)
+            e0.record()
+            native.mis_solve_multi_ex(h, mseeds, mout.data_ptr(), stream)
+            e1.record()
+        torch.cuda.synchronize()
+        mst = native.mis_get_stats(h)
+        mt = float(np.median([e0.elapsed_time(e1) for e0, e1 in ev]))
+        path_multi = {"k": kk, "launch_ms_p50": mt, "per_solve_ms": mt / kk,
+                      "path": PATH_NAMES.get(mst.path), "rounds": mst.rounds,
+                      "phase_us": phase_us(mst)}
     native.mis_destroy(h)
 
     # ---- amortised: the same solve on a graph whose create-time structures
@@ -496,6 +522,10 @@ def run_single(args):
     }
     if amort is not None:
         line["config"]["amortized"] = amort
+    if path_multi is not None:
+        line["config"]["multi_seed_on_path"] = path_multi
+    if args.path == "tile_tc":
+        line["config"]["tile_payload"] = args.payload
     if multi is not None:
         line["config"]["multi_seed"] = multi
     legs = [x for x in (args.legs or "").split(",") if x]
@@ -957,7 +987,9 @@ def main():
                     help="with --tpr 0: the CSR kernel's four degree-bin bounds, comma separated")
     ap.add_argument("--grid", type=int, default=0,
                     help="with --tpr: blocks of the persistent CSR launch (0 = all co-resident)")
-    ap.add_argument("--path", default=None, choices=["tile", "tile_tc", "push"])
+    ap.add_argument("--path", default=None, choices=["tile", "tile_tc", "push", "cluster"])
+    ap.add_argument("--payload", default="b1", choices=sorted(PAYLOADS),
+                    help="with --path tile_tc: the tile payload form of the tensor-core exclusion")
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
