@@ -117,7 +117,6 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
             const int deg = a.rp[v + 1] - a.rp[v];
             w = deg ? undecided_word(mode, priority_key(mode, dbar, deg, smix, (uint32_t)v))
                     : (kKeyIsolated | kWordInSet);
-            if (a.out && v >= base && v < base + cnt) a.out[v] = deg ? 0 : 1;
         }
         s_word[i] = w;
     }
@@ -187,7 +186,6 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
                 const uint32_t wv = s_own[k];
                 if ((wv >> 29) == 1u && !scan(k, base + k, wv, true)) {
                     s_own[k] = wv | kWordInSet;
-                    if (a.out) a.out[base + k] = 1;
                     cand = true;
                     ++sel;
                 }
@@ -247,10 +245,15 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         alive = total;
         __syncthreads();
     }
-    // the MIS size: this CTA's candidates and its isolated vertices (put in
-    // the set at init without a test)
+    // the result of the own vertices, written once after the rounds (so that
+    // no phase has global stores for the cluster barrier's fence to wait on),
+    // and the MIS size: this CTA's candidates and its isolated vertices (put
+    // in the set at init without a test)
     unsigned iso = 0;
-    for (int k = tid; k < cnt; k += nth) iso += (a.rp[base + k + 1] == a.rp[base + k]) ? 1u : 0u;
+    for (int k = tid; k < cnt; k += nth) {
+        if (a.out) a.out[base + k] = s_own[k] >= kWordInMin ? 1 : 0;
+        iso += (a.rp[base + k + 1] == a.rp[base + k]) ? 1u : 0u;
+    }
     for (int o = 16; o; o >>= 1) iso += __shfl_xor_sync(0xFFFFFFFFu, iso, o);
     if ((tid & 31) == 0 && iso) atomicAdd(&s_sel, iso);
     __syncthreads();
