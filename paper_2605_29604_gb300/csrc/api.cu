@@ -72,10 +72,19 @@ struct StageLog {
     }
 };
 
+// The control block and the phase times share one allocation, so that one
+// memset before each solve resets both.
+constexpr size_t kCtlTimesOffset = (sizeof(Ctl) + 255) / 256 * 256;
+constexpr size_t kCtlBlockBytes = kCtlTimesOffset + sizeof(PhaseTimes);
+
+cudaError_t reset_control(const Workspace& w, cudaStream_t s) {
+    return cudaMemsetAsync(w.ctl, 0, kCtlBlockBytes, s);
+}
+
 int64_t ws_bytes_for(int64_t n, int32_t count) {
     const int64_t cap = (n + 15) / 16 * 16;
-    return 4 * cap + 16 * cap * 3 + (cap / 32 + 1) * 4 + 2 * 4 * (cap / 8) + (int64_t)sizeof(Ctl) +
-           (int64_t)sizeof(PhaseTimes) + 8 * std::max<int64_t>(count, 1) + cap;
+    return 4 * cap + 16 * cap * 3 + (cap / 32 + 1) * 4 + 2 * 4 * (cap / 8) +
+           (int64_t)kCtlBlockBytes + 8 * std::max<int64_t>(count, 1) + cap;
 }
 
 void ws_free(Workspace& w) {
@@ -86,8 +95,7 @@ void ws_free(Workspace& w) {
     dfree(w.inbits);
     dfree(w.rbl0);
     dfree(w.rbl1);
-    dfree(w.ctl);
-    dfree(w.times);
+    dfree(w.ctl);  // w.times lies inside this block
     dfree(w.seeds);
     dfree(w.out);
     w = Workspace();
@@ -105,15 +113,16 @@ cudaError_t ws_reserve(Workspace& w, int64_t n, int32_t count) {
         (e = dalloc(&w.inbits, cap / 32 + 1, &b)) != cudaSuccess ||
         (e = dalloc(&w.rbl0, cap / 8, &b)) != cudaSuccess ||
         (e = dalloc(&w.rbl1, cap / 8, &b)) != cudaSuccess ||
-        (e = dalloc(&w.ctl, 1, &b)) != cudaSuccess || (e = dalloc(&w.times, 1, &b)) != cudaSuccess ||
+        (e = dalloc(reinterpret_cast<unsigned char**>(&w.ctl), (int64_t)kCtlBlockBytes, &b)) !=
+            cudaSuccess ||
         (e = dalloc(&w.seeds, std::max(count, 1), &b)) != cudaSuccess ||
         (e = dalloc(&w.out, cap, &b)) != cudaSuccess) {
         ws_free(w);
         return e;
     }
+    w.times = reinterpret_cast<PhaseTimes*>(reinterpret_cast<unsigned char*>(w.ctl) + kCtlTimesOffset);
     // pool memory is recycled: the control block must read as "no solve yet"
-    if ((e = cudaMemset(w.ctl, 0, sizeof(Ctl))) != cudaSuccess ||
-        (e = cudaMemset(w.times, 0, sizeof(PhaseTimes))) != cudaSuccess) {
+    if ((e = cudaMemset(w.ctl, 0, kCtlBlockBytes)) != cudaSuccess) {
         ws_free(w);
         return e;
     }
@@ -512,8 +521,9 @@ int solve_in(mis_graph* g, Workspace& w, const uint64_t* seeds, uint64_t* seeds_
                             cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return set_cuda_error(e, "seed upload");
     }
-    e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(w.times, 0, sizeof(PhaseTimes), s);
+    // the cluster kernel writes every reported field of the control block
+    // and the phase times itself
+    if (d.n == 0 || g->path != MIS_PATH_CLUSTER) e = reset_control(w, s);
     if (e != cudaSuccess) return set_cuda_error(e, "control reset");
     if (d.n > 0) {
         const bool tile = g->path == MIS_PATH_TILE || g->path == MIS_PATH_TILE_TC;
@@ -548,8 +558,7 @@ int solve_multi_in(mis_graph* g, Workspace& w, uint32_t* word8, int k, const uin
     for (int i = 0; i < k; ++i) ms.seed[i] = seeds[i];
     SolveArgs a = make_args(g, w);
     a.out = out_dev;
-    e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(w.times, 0, sizeof(PhaseTimes), s);
+    e = reset_control(w, s);
     if (e != cudaSuccess) return set_cuda_error(e, "control reset");
     if (d.n > 0) {
         const int maxb = multi_max_coresident_blocks(d.device);
@@ -1515,8 +1524,7 @@ int mis_solve_multi_ex(mis_graph* g, int32_t k, const uint64_t* seeds, uint8_t* 
         SolveArgs a = make_args(g, d.ws);
         a.out = out_status;
         cudaStream_t s = (cudaStream_t)stream;
-        e = cudaMemsetAsync(d.ws.ctl, 0, sizeof(Ctl), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(d.ws.times, 0, sizeof(PhaseTimes), s);
+        e = reset_control(d.ws, s);
         if (e != cudaSuccess) return set_cuda_error(e, "control reset");
         if (d.n > 0) {
             const int maxb = tile_multi_max_coresident_blocks(g->tile_payload, d.device);

@@ -8,10 +8,10 @@
 //   state    the packed vertex words (common.cuh) live in the CTAs' shared
 //            memory.  CTA r owns the vertices of chunk r (chunk = 2^shift >=
 //            n / C).  Where a replica of every word fits in each CTA, every
-//            scan reads local shared memory and the CTAs exchange, after each
-//            phase, one bit per owned vertex whose state changed; otherwise a
-//            CTA holds its own chunk and neighbour words are read through
-//            distributed shared memory;
+//            scan reads local shared memory and, after each phase's barrier,
+//            every CTA reads (pulls) from the others one bit per owned vertex
+//            whose state changed; otherwise a CTA holds its own chunk and
+//            neighbour words are read through distributed shared memory;
 //   barriers the phases are separated by the cluster's hardware barrier
 //            (barrier.cluster arrive/wait through cooperative groups), which
 //            every CTA reaches the same number of times: the loop exit is
@@ -54,19 +54,36 @@ __device__ __forceinline__ bool outranks_c(uint32_t wu, int u, uint32_t wv, int 
 
 // kRep = false: CTA r holds the words of its own chunk only; neighbour words
 // are read through distributed shared memory.  kRep = true: every CTA holds a
-// replica of all words, so every scan reads local shared memory; in each
-// phase a CTA publishes one bit per owned vertex whose state changed (one
-// word per warp, from a ballot), storing it into every CTA's copy of the
-// change bitmask, and after the cluster barrier every CTA folds the bits it
-// received into its replica.  Two bitmasks (selected, excluded) keep a
-// phase's bits until every CTA has folded them.
-template <bool kRep>
+// replica of all words, so no scan leaves the SM.  In each phase a CTA
+// writes one bit per owned vertex whose state changed (one word per warp,
+// from a ballot) into its own part of that phase's bitmask; after the
+// cluster barrier every CTA reads the other CTAs' parts (remote loads: a
+// pull costs one load latency, where remote stores before the barrier would
+// make its release wait for every store to be acknowledged).  Phase 2 tests
+// a neighbour's bit in the round's selection bitmask (a vertex still
+// undecided at a round's start has no neighbour in the set, so only this
+// round's selections can exclude it).  After Phase 2 every CTA ORs the
+// round's exclusion bits into its bitmask of excluded vertices; the replica
+// keeps every other chunk's initial words, and Phase 1 counts a neighbour
+// that outranks v by its word only if its excluded bit is clear (an
+// undecided vertex has no neighbour in the set, so the excluded bit is the
+// only state change Phase 1 needs).  kRows: the CTA's rows are in shared
+// memory.
+//
+// No store in the round loop goes to global or remote shared memory: the
+// undecided counts are read by every CTA from every CTA after the barrier,
+// and the statistics (undecided counts, phase end times) stay in rank 0's
+// shared memory until the end.
+template <bool kRep, bool kRows>
 __global__ void __launch_bounds__(kClusterThreads, 1)
     cluster_solve_kernel(const SolveArgs a, const ClusterArgs c) {
-    extern __shared__ uint32_t s_dyn[];
-    __shared__ int s_rem[2];  // this CTA's undecided count, by round parity
-    __shared__ unsigned s_sel;
-    __shared__ int s_total;
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    __shared__ int s_cnt[2];     // this CTA's undecided count, by round parity
+    __shared__ int s_total;      // the cluster's undecided count
+    __shared__ unsigned s_size;  // this CTA's part of the MIS size
+    __shared__ int s_err;        // rank 0: the error code
+    __shared__ unsigned long long s_t[2 + 2 * kStatRounds];  // rank 0: phase end times
+    __shared__ int s_alive[kStatRounds];                     // rank 0: alive set sizes
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int chunk = 1 << c.shift;
@@ -75,25 +92,37 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     const int cnt = max(0, min(chunk, n - base));  // this CTA's vertices
     const int tid = (int)threadIdx.x;
     const int nth = (int)blockDim.x;
+    const int lane = tid & 31;
     // shared memory: the words (own chunk, or all chunks), with kRep the two
-    // change bitmasks of the own chunk, then (smem_rows) the own rows
+    // change bitmasks of every chunk and the excluded bitmask, then (kRows)
+    // the own rows
     const int nwords = kRep ? c.ncta * chunk : chunk;
-    const int nmask = kRep ? c.ncta * (chunk / 32) : 0;  // change bits of every chunk
+    const int mshift = c.shift - 5;  // bitmask words per chunk: 2^mshift
+    const int nmask = kRep ? c.ncta << mshift : 0;
     uint32_t* s_word = s_dyn;
     uint32_t* s_new_in = s_dyn + nwords;
     uint32_t* s_new_out = s_new_in + nmask;
-    int32_t* s_rp = reinterpret_cast<int32_t*>(s_new_out + nmask);
+    uint32_t* s_gone = s_new_out + nmask;
+    int32_t* s_rp = reinterpret_cast<int32_t*>(s_gone + nmask);
     int32_t* s_col = s_rp + chunk + 1;
     uint32_t* s_own = kRep ? s_word + base : s_word;  // the own chunk's words
-    Ctl* ctl = a.ctl;
-    PhaseTimes* times = a.times;
     const int mode = a.priority;
     const uint64_t smix = mix64(a.seed0);
-    const float dbar = n > 0 ? average_degree(a.rp[n], n) : 0.f;
+    // the loads init depends on, issued first: the arc count (for d-bar) and
+    // the bounds of the own slice of arcs
+    const int32_t arcs_all = n > 0 ? a.rp[n] : 0;
+    const int arc0 = kRows && cnt > 0 ? a.rp[base] : 0;
+    const int arcs = kRows && cnt > 0 ? a.rp[base + cnt] - arc0 : 0;
+    const float dbar = n > 0 ? average_degree(arcs_all, n) : 0.f;
+    const bool stats = rank == 0;
     if (tid == 0) {
-        s_rem[0] = s_rem[1] = 0;
-        s_sel = 0;
-        if (rank == 0 && times) times->t[0] = global_ns();
+        s_cnt[0] = s_cnt[1] = 0;
+        s_size = 0;
+        s_err = 0;
+    }
+    if (stats) {
+        for (int i = tid; i < 2 + 2 * kStatRounds; i += nth) s_t[i] = 0;
+        if (tid == 0) s_t[0] = global_ns();
     }
     // the word of vertex u: in this CTA (kRep), else wherever it lives
     auto word_of = [&](int u) -> const uint32_t* {
@@ -101,35 +130,70 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         return cluster.map_shared_rank(s_word + (u & (chunk - 1)), u >> c.shift);
     };
 
-    // ---- init: the CTA's rows into shared memory (coalesced copies), then
-    // Eq. 1 priorities (of all vertices with kRep); isolated vertices straight
-    // into the set, and the own vertices' result bytes
-    const int arc0 = cnt > 0 ? a.rp[base] : 0;
-    if (c.smem_rows && cnt > 0) {
-        const int arc1 = a.rp[base + cnt];
-        for (int k = tid; k <= cnt; k += nth) s_rp[k] = a.rp[base + k] - arc0;
-        for (int p = tid; p < arc1 - arc0; p += nth) s_col[p] = __ldg(a.col + arc0 + p);
-    }
-    for (int i = tid; i < nwords; i += nth) {
-        const int v = kRep ? i : base + i;
+    // ---- init: the own vertices' Eq. 1 priorities (isolated vertices
+    // straight into the set) and row offsets, the CTA's arcs into shared
+    // memory (coalesced copies, four loads in flight per thread); after the
+    // barrier, with kRep, the other chunks' words into the replica (16-byte
+    // remote loads)
+    for (int k = tid; k < chunk; k += nth) {
+        const int v = base + k;
         uint32_t w = kWordOut;
         if (v < n) {
-            const int deg = a.rp[v + 1] - a.rp[v];
+            const int r0 = a.rp[v];
+            const int deg = a.rp[v + 1] - r0;
+            if (kRows) s_rp[k] = r0 - arc0;
             w = deg ? undecided_word(mode, priority_key(mode, dbar, deg, smix, (uint32_t)v))
                     : (kKeyIsolated | kWordInSet);
         }
-        s_word[i] = w;
+        s_own[k] = w;
     }
+    if (kRows && tid == 0) s_rp[cnt] = arcs;
+    if (kRows) {
+        for (int p0 = tid; p0 < arcs; p0 += 4 * nth) {
+            int32_t x[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = p0 + j * nth < arcs ? __ldg(a.col + arc0 + p0 + j * nth) : 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (p0 + j * nth < arcs) s_col[p0 + j * nth] = x[j];
+        }
+    }
+    for (int j = tid; j < nmask; j += nth) s_gone[j] = 0u;
     cluster.sync();
-    if (rank == 0 && tid == 0 && times) times->t[1] = global_ns();
+    if (kRep) {
+        // a word pulled while its owner marks it selected in round 0 is
+        // either value; both compare the same way in every later test (a
+        // candidate outranks each undecided neighbour, and no undecided
+        // vertex neighbours a vertex in the set)
+        // (four loads in flight per thread before any store)
+        const int qshift = c.shift - 2;  // 16-byte quads per chunk: 2^qshift
+        const int nquad = c.ncta << qshift;
+        for (int p0 = tid; p0 < nquad; p0 += 4 * nth) {
+            uint4 x[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int p = p0 + j * nth, q = p >> qshift;
+                if (p < nquad && q != rank)
+                    x[j] = *reinterpret_cast<const uint4*>(cluster.map_shared_rank(s_word, q) + 4 * p);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int p = p0 + j * nth;
+                if (p < nquad && (p >> qshift) != rank) reinterpret_cast<uint4*>(s_word)[p] = x[j];
+            }
+        }
+        __syncthreads();
+    }
+    if (stats && tid == 0) s_t[1] = global_ns();
 
-    // Scan of the row of v (local index k): sel: does an undecided or
-    // selected neighbour outrank v (word wv); else: is a neighbour in the set.
-    // kBatch neighbour words are requested before any of them is tested.
+    // Scan of the row of v (local index k).  sel: does an undecided or
+    // selected neighbour outrank v (word wv; kRep: and is it not excluded)?
+    // else: is a neighbour in the set (kRep: selected in this round)?
+    // kBatch loads are issued before any of them is tested.
     auto scan = [&](int k, int v, uint32_t wv, bool sel) -> bool {
         const int32_t* row;
         int deg;
-        if (c.smem_rows) {
+        if (kRows) {
             row = s_col + s_rp[k];
             deg = s_rp[k + 1] - s_rp[k];
         } else {
@@ -138,48 +202,39 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         }
         for (int q0 = 0; q0 < deg; q0 += kBatch) {
             int u[kBatch];
-            uint32_t wu[kBatch];
+            uint32_t x[kBatch];
 #pragma unroll
             for (int q = 0; q < kBatch; ++q) u[q] = q0 + q < deg ? row[q0 + q] : 0;
 #pragma unroll
-            for (int q = 0; q < kBatch; ++q) wu[q] = q0 + q < deg ? *word_of(u[q]) : 0u;
-            bool hit = false;
+            for (int q = 0; q < kBatch; ++q)
+                x[q] = q0 + q >= deg ? 0u
+                       : (kRep && !sel) ? (s_new_in[u[q] >> 5] >> (u[q] & 31)) & 1u
+                                        : *word_of(u[q]);
+            bool hit[kBatch];
 #pragma unroll
             for (int q = 0; q < kBatch; ++q)
-                hit |= q0 + q < deg && (sel ? outranks_c(wu[q], u[q], wv, v) : wu[q] >= kWordInMin);
-            if (hit) return true;
+                hit[q] = q0 + q < deg && (sel ? outranks_c(x[q], u[q], wv, v)
+                                              : kRep ? x[q] != 0u : x[q] >= kWordInMin);
+            if (kRep && sel) {
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q)
+                    hit[q] = hit[q] && !((s_gone[u[q] >> 5] >> (u[q] & 31)) & 1u);
+            }
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < kBatch; ++q) any |= hit[q];
+            if (any) return true;
         }
         return false;
     };
-    // kRep: a warp's change word of the own chunk, stored into every CTA's
-    // copy of the bitmask (remote stores, made visible by the next barrier)
-    auto publish = [&](uint32_t* mask, int k, unsigned m) {
-        const int lane = tid & 31;
-        if (lane < c.ncta) *cluster.map_shared_rank(mask + rank * (chunk / 32) + (k >> 5), lane) = m;
-    };
-    // kRep: fold the other CTAs' changes, received in local shared memory,
-    // into the replica (in: OR the set bits, else: out)
-    auto fold = [&](const uint32_t* mask, bool in) {
-        const int per = chunk / 32;
-        for (int i = tid; i < c.ncta * per; i += nth) {
-            const int q = i / per, j = i - q * per;
-            if (q == rank) continue;
-            uint32_t bits = mask[i];
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1;
-                uint32_t* w = s_word + q * chunk + 32 * j + b;
-                *w = in ? (*w | kWordInSet) : kWordOut;
-            }
-        }
-    };
 
     int alive = n;  // round 0's alive set: every vertex
-    for (int r = 0;; ++r) {
+    unsigned long long alive_sum = 0;
+    int r = 0;
+    for (;; ++r) {
         const int par = r & 1;
         // ---- Phase 1: selection test over the own chunk (kRep: every warp
         // covers whole 32-vertex words, so its ballot is the word's bits)
-        unsigned sel = 0;
         for (int k = tid; k < (kRep ? chunk : cnt); k += nth) {
             bool cand = false;
             if (k < cnt) {
@@ -187,18 +242,23 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
                 if ((wv >> 29) == 1u && !scan(k, base + k, wv, true)) {
                     s_own[k] = wv | kWordInSet;
                     cand = true;
-                    ++sel;
                 }
             }
-            if (kRep) publish(s_new_in, k, __ballot_sync(0xFFFFFFFFu, cand));
+            if (kRep) {
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
+                if (lane == 0) s_new_in[(rank << mshift) + (k >> 5)] = m;
+            }
         }
-        if (sel) atomicAdd(&s_sel, sel);
         cluster.sync();
-        if (rank == 0 && tid == 0 && times && r < kStatRounds) times->t[2 + r] = global_ns();
         if (kRep) {
-            fold(s_new_in, true);
+            // the other CTAs' selections of this round
+            for (int i = tid; i < nmask; i += nth) {
+                const int q = i >> mshift;
+                if (q != rank) s_new_in[i] = *cluster.map_shared_rank(s_new_in + i, q);
+            }
             __syncthreads();
         }
+        if (stats && tid == 0 && r < kStatRounds) s_t[2 + r] = global_ns();
         // ---- Phases 2 and 3: exclusion test, state update; count the rest
         int rem = 0;
         for (int k = tid; k < (kRep ? chunk : cnt); k += nth) {
@@ -214,52 +274,92 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
                     }
                 }
             }
-            if (kRep) publish(s_new_out, k, __ballot_sync(0xFFFFFFFFu, out));
+            if (kRep) {
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, out);
+                if (lane == 0) s_new_out[(rank << mshift) + (k >> 5)] = m;
+            }
         }
         for (int o = 16; o; o >>= 1) rem += __shfl_xor_sync(0xFFFFFFFFu, rem, o);
-        if ((tid & 31) == 0 && rem) atomicAdd(&s_rem[par], rem);
+        if (lane == 0 && rem) atomicAdd(&s_cnt[par], rem);
         cluster.sync();
-        if (kRep) fold(s_new_out, false);
-        // every CTA sums the same counts, so all leave the loop together
+        // every CTA's count (the same sum in every CTA, so all leave the loop
+        // together) and, with kRep, the round's exclusions of every chunk
         if (tid < 32) {
-            int total = tid < c.ncta ? *cluster.map_shared_rank(&s_rem[par], tid) : 0;
-            for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(0xFFFFFFFFu, total, o);
-            if (tid == 0) s_total = total;
-            if (rank == 0 && tid == 0) {
-                if (times && r < kStatRounds) times->t[2 + kStatRounds + r] = global_ns();
-                if (r < kStatRounds) ctl->alive[r] = alive;
-                ctl->alive_sum += (unsigned long long)alive;
-                ctl->rounds = r + 1;
+            int t = lane < c.ncta ? *cluster.map_shared_rank(&s_cnt[par], lane) : 0;
+            for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+            if (lane == 0) s_total = t;
+        }
+        if (kRep) {
+            for (int i = tid; i < nmask; i += nth) {
+                const int q = i >> mshift;
+                s_gone[i] |= q == rank ? s_new_out[i] : *cluster.map_shared_rank(s_new_out + i, q);
             }
+        }
+        if (stats && tid == 0) {
+            if (r < kStatRounds) {
+                s_t[2 + kStatRounds + r] = global_ns();
+                s_alive[r] = alive;
+            }
+            alive_sum += (unsigned long long)alive;
         }
         __syncthreads();
         const int total = s_total;
-        // the other slot, last read (by every CTA) before this round's first
-        // barrier, is cleared for the next round's count
-        if (tid == 0) s_rem[par ^ 1] = 0;
+        // the other count, last read by the other CTAs before this round's
+        // first barrier, is cleared for round r + 1
+        if (tid == 0) s_cnt[par ^ 1] = 0;
         if (total == 0) break;
         if (r + 1 >= a.max_rounds) {
-            if (rank == 0 && tid == 0) atomicCAS(&ctl->err, 0, kErrInternal);
+            if (stats && tid == 0) s_err = kErrInternal;
             break;  // uniform: every CTA saw the same total and round
         }
         alive = total;
         __syncthreads();
     }
-    // the result of the own vertices, written once after the rounds (so that
-    // no phase has global stores for the cluster barrier's fence to wait on),
-    // and the MIS size: this CTA's candidates and its isolated vertices (put
-    // in the set at init without a test)
-    unsigned iso = 0;
-    for (int k = tid; k < cnt; k += nth) {
-        if (a.out) a.out[base + k] = s_own[k] >= kWordInMin ? 1 : 0;
-        iso += (a.rp[base + k + 1] == a.rp[base + k]) ? 1u : 0u;
-    }
-    for (int o = 16; o; o >>= 1) iso += __shfl_xor_sync(0xFFFFFFFFu, iso, o);
-    if ((tid & 31) == 0 && iso) atomicAdd(&s_sel, iso);
-    __syncthreads();
-    if (tid == 0 && s_sel) atomicAdd(&ctl->mis_size, (unsigned long long)s_sel);
-    // no CTA may leave while another still reads its shared memory
+    // this CTA's part of the MIS size (isolated vertices included); rank 0
+    // reads every CTA's after the barrier
+    unsigned in_cnt = 0;
+    for (int k = tid; k < cnt; k += nth) in_cnt += s_own[k] >= kWordInMin ? 1u : 0u;
+    for (int o = 16; o; o >>= 1) in_cnt += __shfl_xor_sync(0xFFFFFFFFu, in_cnt, o);
+    if (lane == 0 && in_cnt) atomicAdd(&s_size, in_cnt);
     cluster.sync();
+    unsigned long long mis_size = 0;
+    if (stats && tid < 32) {
+        unsigned long long t = lane < c.ncta ? *cluster.map_shared_rank(&s_size, lane) : 0ull;
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+        mis_size = t;
+    }
+    // no CTA leaves while another may still read its shared memory
+    cluster.sync();
+    // the result of the own vertices: global stores only after the last
+    // barrier, whose release would otherwise wait for them
+    if (a.out)
+        for (int k = tid; k < cnt; k += nth) a.out[base + k] = s_own[k] >= kWordInMin ? 1 : 0;
+    // rank 0 writes every field of the control block and of the phase times
+    // that a solve reports, so the launch needs no reset before it
+    if (stats) {
+        const int rounds = r + 1;
+        if (tid == 0) {
+            a.ctl->err = s_err;
+            a.ctl->mis_size = mis_size;
+            a.ctl->rounds = rounds;
+            a.ctl->alive_sum = alive_sum;
+        }
+        for (int i = tid; i < kStatRounds; i += nth) a.ctl->alive[i] = i < rounds ? s_alive[i] : 0;
+        if (a.times)
+            for (int i = tid; i < 2 + 2 * kStatRounds; i += nth) a.times->t[i] = s_t[i];
+    }
+}
+
+// static shared memory of the kernel (counters, rank 0's statistics) and a
+// margin, kept out of the dynamic budget
+constexpr size_t kStaticSmem = 2048;
+
+const void* cluster_fn(int replicated, int smem_rows) {
+    if (replicated)
+        return smem_rows ? (const void*)cluster_solve_kernel<true, true>
+                         : (const void*)cluster_solve_kernel<true, false>;
+    return smem_rows ? (const void*)cluster_solve_kernel<false, true>
+                     : (const void*)cluster_solve_kernel<false, false>;
 }
 
 }  // namespace
@@ -272,7 +372,7 @@ bool cluster_plan(const int32_t* d_rp, int32_t n, ClusterPlan* plan) {
     int max_optin = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t budget = (size_t)max_optin > 1024 ? (size_t)max_optin - 1024 : 0;
+    const size_t budget = (size_t)max_optin > kStaticSmem ? (size_t)max_optin - kStaticSmem : 0;
     for (int ncta : {16, 8}) {
         int shift = 5;
         while ((long long)(1 << shift) * ncta < n) ++shift;
@@ -290,9 +390,9 @@ bool cluster_plan(const int32_t* d_rp, int32_t n, ClusterPlan* plan) {
             prev = x;
         }
         const size_t rows = sizeof(int32_t) * ((size_t)chunk + 1 + (size_t)max_slice);
-        // a replica of every word (and the two change bitmasks) if it fits,
+        // a replica of every word (and the three bitmasks) if it fits,
         // else the own chunk's words; the rows on chip if they fit as well
-        const size_t rep = sizeof(uint32_t) * ((size_t)ncta * chunk + (size_t)ncta * chunk / 16);
+        const size_t rep = sizeof(uint32_t) * ((size_t)ncta * chunk + 3 * ((size_t)ncta * chunk / 32));
         const size_t own = sizeof(uint32_t) * (size_t)chunk;
         int replicated, smem_rows;
         if (rep + rows <= budget) {
@@ -311,8 +411,7 @@ bool cluster_plan(const int32_t* d_rp, int32_t n, ClusterPlan* plan) {
             continue;
         }
         const size_t smem = (replicated ? rep : own) + (smem_rows ? rows : 0);
-        const void* fn = replicated ? (const void*)cluster_solve_kernel<true>
-                                    : (const void*)cluster_solve_kernel<false>;
+        const void* fn = cluster_fn(replicated, smem_rows);
         if (ncta > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed,
                                              1) != cudaSuccess) {
             cudaGetLastError();
@@ -356,7 +455,7 @@ int32_t cluster_max_vertices() {
         cudaSuccess)
         return 0;
     // the vertex words alone in 16 CTAs (the rows may then stay in global memory)
-    const long long words = ((long long)max_optin - 1024) / 4;
+    const long long words = ((long long)max_optin - (long long)kStaticSmem) / 4;
     int shift = 5;
     while ((2LL << shift) <= words) ++shift;
     return (int32_t)std::min<long long>(16LL << shift, 1LL << 30);
@@ -382,8 +481,11 @@ cudaError_t launch_cluster_solve(const SolveArgs& a, const ClusterPlan& p, cudaS
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (p.replicated) return cudaLaunchKernelEx(&cfg, cluster_solve_kernel<true>, a, c);
-    return cudaLaunchKernelEx(&cfg, cluster_solve_kernel<false>, a, c);
+    if (p.replicated)
+        return p.smem_rows ? cudaLaunchKernelEx(&cfg, cluster_solve_kernel<true, true>, a, c)
+                           : cudaLaunchKernelEx(&cfg, cluster_solve_kernel<true, false>, a, c);
+    return p.smem_rows ? cudaLaunchKernelEx(&cfg, cluster_solve_kernel<false, true>, a, c)
+                       : cudaLaunchKernelEx(&cfg, cluster_solve_kernel<false, false>, a, c);
 }
 
 }  // namespace tcmis
