@@ -520,11 +520,10 @@ void mis_serve_shutdown(void);
  * Scratch: the library holds one fixed array of 3 MiB + 1 KiB in device
  * memory on every GPU that loads it, until the process exits.  Each call
  * looks up that array's device address on the current device; the first
- * call on a device also loads the library's device code there, so make it
- * before any stream capture begins on that device.  All calls share the
- * array, and each call clears the part that must start at zero; calls whose
- * work overlaps on a GPU (different streams or threads) race and must be
- * serialised by the caller.
+ * call on a device also loads the library's device code there.  All calls
+ * share the array, and each call clears the part that must start at zero;
+ * calls whose work overlaps on a GPU (different streams or threads) race and
+ * must be serialised by the caller.
  */
 int mis_solve_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint64_t seed,
                       uint8_t *out_status, void *stream);

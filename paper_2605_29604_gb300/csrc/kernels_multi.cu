@@ -31,8 +31,13 @@ namespace {
 constexpr int kMultiBlock = 512;
 constexpr int kMultiMinBlocksPerSm = 2;
 constexpr int kMultiWarps = kMultiBlock / 32;
-// rows per chunk, per lane-group width (1, 4, 16, 32 lanes per row)
-constexpr int kMChunk1 = 512, kMChunk4 = 256, kMChunk16 = 128, kMChunk32 = 64;
+// Schedule of a bin's rows: warp passes of G = 32 / TPR rows, pass k taken
+// by warp k mod nwarps (counted from the bin's first warp), so at any moment
+// the grid works on a window of about nwarps * G consecutive rows.  On a
+// graph with local rows the neighbours' eight-word records (32 bytes per
+// vertex, more than L2 holds at 4 M vertices) are then re-read from L2
+// rather than DRAM; contiguous chunks per warp spread the window over the
+// whole list.
 
 // The eight words of vertex v (solves beyond K hold "out" and never count).
 __device__ __forceinline__ void load8(const uint32_t* word8, int v, uint32_t (&w)[kMaxMulti]) {
@@ -118,20 +123,19 @@ __shared__ unsigned s_msel;
 // Phase 1 over one bin at TPR lanes per row: for every row, the selection
 // test in each solve that has the row undecided; candidates are marked in.
 // Counts the undecided (vertex, solve) pairs into *alive.
-template <int TPR, int CH>
+template <int TPR>
 __device__ __forceinline__ void select_bin8(const MultiCtx& x, const int4* __restrict__ list,
-                                            int cnt, WarpSched& ws, unsigned* grab,
-                                            unsigned long long* alive, bool late) {
+                                            int cnt, WarpSched& ws, unsigned long long* alive,
+                                            bool late) {
     constexpr int G = 32 / TPR;
     if (cnt <= 0) return;
     const unsigned lane = lane_id();
     const unsigned glane = lane % TPR;
     const unsigned gid = lane / TPR;
-    const ChunkPlan plan = plan_of<G, CH>(cnt, ws.nwarps);
+    const int total = (cnt + G - 1) / G;
     unsigned count = 0;
-    for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps, grab)) {
-        int c0, c1;
-        plan.range(k, cnt, c0, c1, G);
+    for (int k = ws.first(total); k < total; k += ws.nwarps) {
+        const int c0 = k * G, c1 = min(c0 + G, cnt);
         for (int base = c0; base < c1; base += G) {
             const int item = base + (int)gid;
             const bool valid = item < c1;
@@ -175,20 +179,19 @@ __device__ __forceinline__ void select_bin8(const MultiCtx& x, const int4* __res
 // Phase 2+3 over one bin: in each solve that still has the row undecided (a
 // non-candidate), the exclusion test; the row stays on the worklist while
 // some solve keeps it undecided.
-template <int TPR, int CH>
+template <int TPR>
 __device__ __forceinline__ void exclude_bin8(const MultiCtx& x, const int4* __restrict__ list,
-                                             int cnt, WarpSched& ws, unsigned* grab, int* next,
+                                             int cnt, WarpSched& ws, int* next,
                                              int4* __restrict__ dst) {
     constexpr int G = 32 / TPR;
     if (cnt <= 0) return;
     const unsigned lane = lane_id();
     const unsigned glane = lane % TPR;
     const unsigned gid = lane / TPR;
-    const ChunkPlan plan = plan_of<G, CH>(cnt, ws.nwarps);
+    const int total = (cnt + G - 1) / G;
     int fill = 0;
-    for (int k = ws.first(plan.total); k < plan.total; k = next_chunk(plan.total, ws.nwarps, grab)) {
-        int c0, c1;
-        plan.range(k, cnt, c0, c1, G);
+    for (int k = ws.first(total); k < total; k += ws.nwarps) {
+        const int c0 = k * G, c1 = min(c0 + G, cnt);
         for (int base = c0; base < c1; base += G) {
             const int item = base + (int)gid;
             const bool valid = item < c1;
@@ -230,27 +233,25 @@ __device__ __forceinline__ int multi_lanes(int cnt, bool late, int nwarps) {
     return BASE;
 }
 
-template <int BASE, int CH>
+template <int BASE>
 __device__ __forceinline__ void select_at8(const MultiCtx& x, const int4* list, int cnt, bool late,
-                                           WarpSched& ws, unsigned* grab,
-                                           unsigned long long* alive) {
+                                           WarpSched& ws, unsigned long long* alive) {
     switch (multi_lanes<BASE>(cnt, late, ws.nwarps)) {
-        case 32: select_bin8<32, kMChunk32>(x, list, cnt, ws, grab, alive, late); break;
-        case 16: select_bin8<16, kMChunk16>(x, list, cnt, ws, grab, alive, late); break;
-        case 4: select_bin8<4, kMChunk4>(x, list, cnt, ws, grab, alive, late); break;
-        default: select_bin8<BASE, CH>(x, list, cnt, ws, grab, alive, late);
+        case 32: select_bin8<32>(x, list, cnt, ws, alive, late); break;
+        case 16: select_bin8<16>(x, list, cnt, ws, alive, late); break;
+        case 4: select_bin8<4>(x, list, cnt, ws, alive, late); break;
+        default: select_bin8<BASE>(x, list, cnt, ws, alive, late);
     }
 }
 
-template <int BASE, int CH>
+template <int BASE>
 __device__ __forceinline__ void exclude_at8(const MultiCtx& x, const int4* list, int cnt,
-                                            bool late, WarpSched& ws, unsigned* grab, int* next,
-                                            int4* dst) {
+                                            bool late, WarpSched& ws, int* next, int4* dst) {
     switch (multi_lanes<BASE>(cnt, late, ws.nwarps)) {
-        case 32: exclude_bin8<32, kMChunk32>(x, list, cnt, ws, grab, next, dst); break;
-        case 16: exclude_bin8<16, kMChunk16>(x, list, cnt, ws, grab, next, dst); break;
-        case 4: exclude_bin8<4, kMChunk4>(x, list, cnt, ws, grab, next, dst); break;
-        default: exclude_bin8<BASE, CH>(x, list, cnt, ws, grab, next, dst);
+        case 32: exclude_bin8<32>(x, list, cnt, ws, next, dst); break;
+        case 16: exclude_bin8<16>(x, list, cnt, ws, next, dst); break;
+        case 4: exclude_bin8<4>(x, list, cnt, ws, next, dst); break;
+        default: exclude_bin8<BASE>(x, list, cnt, ws, next, dst);
     }
 }
 
@@ -362,15 +363,13 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
         const bool late = r > 0;
 
         // ---- Phase 1: selection test of every solve; hubs take a warp per row
-        unsigned* grab = ctl->grab[(2 * r) & 3];
-        select_at8<32, kMChunk32>(x, src + off[4], s_cnt[4], late, ws, &grab[4], acc);
-        select_at8<32, kMChunk32>(x, src + off[3], s_cnt[3], late, ws, &grab[3], acc);
-        select_at8<16, kMChunk16>(x, src + off[2], s_cnt[2], late, ws, &grab[2], acc);
-        select_at8<4, kMChunk4>(x, src + off[1], s_cnt[1], late, ws, &grab[1], acc);
-        select_at8<1, kMChunk1>(x, src + off[0], s_cnt[0], late, ws, &grab[0], acc);
-        if (!grid_barrier(ctl, nblocks, a.spin_cap, [ctl, times, rr]() {
+        select_at8<32>(x, src + off[4], s_cnt[4], late, ws, acc);
+        select_at8<32>(x, src + off[3], s_cnt[3], late, ws, acc);
+        select_at8<16>(x, src + off[2], s_cnt[2], late, ws, acc);
+        select_at8<4>(x, src + off[1], s_cnt[1], late, ws, acc);
+        select_at8<1>(x, src + off[0], s_cnt[0], late, ws, acc);
+        if (!grid_barrier(ctl, nblocks, a.spin_cap, [times, rr]() {
                 if (times && rr < kStatRounds) times->t[2 + rr] = global_ns();
-                for (int j = 0; j < kBins; ++j) ctl->grab[(2 * rr + 2) & 3][j] = 0;
             }))
             return;
 
@@ -385,14 +384,13 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
                 p[1] = out4;
             }
         }
-        grab = ctl->grab[(2 * r + 1) & 3];
         // round 0's rows in the tested subgraph, where the graph has one
         if (r == 0 && a.order0_s0) src = a.order0_s0;
-        exclude_at8<32, kMChunk32>(x, src + off[4], s_cnt[4], late, ws, &grab[4], &next[4], dst + off[4]);
-        exclude_at8<32, kMChunk32>(x, src + off[3], s_cnt[3], late, ws, &grab[3], &next[3], dst + off[3]);
-        exclude_at8<16, kMChunk16>(x, src + off[2], s_cnt[2], late, ws, &grab[2], &next[2], dst + off[2]);
-        exclude_at8<4, kMChunk4>(x, src + off[1], s_cnt[1], late, ws, &grab[1], &next[1], dst + off[1]);
-        exclude_at8<1, kMChunk1>(x, src + off[0], s_cnt[0], late, ws, &grab[0], &next[0], dst + off[0]);
+        exclude_at8<32>(x, src + off[4], s_cnt[4], late, ws, &next[4], dst + off[4]);
+        exclude_at8<32>(x, src + off[3], s_cnt[3], late, ws, &next[3], dst + off[3]);
+        exclude_at8<16>(x, src + off[2], s_cnt[2], late, ws, &next[2], dst + off[2]);
+        exclude_at8<4>(x, src + off[1], s_cnt[1], late, ws, &next[1], dst + off[1]);
+        exclude_at8<1>(x, src + off[0], s_cnt[0], late, ws, &next[0], dst + off[0]);
         const long long extra = r == 0 ? (long long)k * decided0 : 0;
         if (!grid_barrier(
                 ctl, nblocks, a.spin_cap,
@@ -405,10 +403,7 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
                     if (rr < kStatRounds) ctl->alive[rr] = (int)cur;
                     ctl->alive_sum += cur;
                     ctl->rounds = rr + 1;
-                    for (int j = 0; j < kBins; ++j) {
-                        ctl->grab[(2 * rr + 3) & 3][j] = 0;
-                        ctl->bcnt[(rr + 2) & 3][j] = 0;
-                    }
+                    for (int j = 0; j < kBins; ++j) ctl->bcnt[(rr + 2) & 3][j] = 0;
                 },
                 [next]() {
                     for (int j = 0; j < kBins; ++j) s_cnt[j] = __ldcg(next + j);

@@ -22,6 +22,10 @@
 //   Phase 3  the row block stays on the worklist while any of its 16 x K
 //            entries is undecided.
 //
+// Warp w takes list entries w, w + W, w + 2W, ... (W warps in the grid), so
+// the grid works on a window of about W consecutive row blocks at a time and
+// the neighbour words of a graph with local rows come from L2.
+//
 // Every solve sees the round-start snapshot exactly as a single solve does,
 // so each solve's set and rounds are those of its single solve.
 #include <algorithm>
@@ -36,17 +40,10 @@ namespace {
 
 constexpr int kTmBlock = 512;
 constexpr int kTmWarps = kTmBlock / 32;
-constexpr int kTmChunk = 64;  // row blocks per warp chunk (upper bound)
+constexpr int kTmChunk = 64;  // survivors staged per warp before an append
 
 __device__ __forceinline__ bool outranks_m(uint32_t wu, int u, uint32_t wv, int v) {
     return wu > wv || (wu == wv && u > v);
-}
-
-__device__ __forceinline__ int tm_chunk(int cnt) {
-    const long long nwarps = (long long)gridDim.x * (blockDim.x / 32);
-    long long per = (cnt + nwarps - 1) / nwarps;
-    if (per < 1) per = 1;
-    return per < kTmChunk ? (int)per : kTmChunk;
 }
 
 __device__ __forceinline__ uint2 ld_pair(const uint32_t* word8, int v, int q) {
@@ -93,26 +90,23 @@ __device__ __forceinline__ unsigned blocks4(uint4 wu, int u, uint4 wv, int v) {
 
 __device__ __forceinline__ void tm_select(const SolveArgs& a, const TmArgs& m,
                                           const int32_t* __restrict__ list, int cnt,
-                                          unsigned* grab, unsigned long long& alive) {
+                                          unsigned long long& alive) {
     if (cnt <= 0) return;
     const unsigned lane = lane_id();
     const int i = (int)(lane >> 1), h = (int)(lane & 1);
-    const int ch = tm_chunk(cnt);
+    // warp gw takes list entries gw, gw + nw, gw + 2 nw, ...: at any moment
+    // the warps work on a window of about nw consecutive entries, so the
+    // neighbour words of a graph with local rows are re-read from L2
+    const long long nw = (long long)gridDim.x * (blockDim.x / 32);
     const long long gw = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    if (gw >= (cnt + ch - 1) / ch) return;
-    for (;;) {
-        int c0 = 0;
-        if (lane == 0) c0 = (int)atomicAdd(grab, (unsigned)ch);
-        c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
-        if (c0 >= cnt) break;
-        const int c1 = min(c0 + ch, cnt);
-        // the next row block's id and tile range are loaded one item ahead
-        int rb_n = list[c0];
+    {
+        if (gw >= cnt) return;
+        int rb_n = list[gw];
         int t0_n = a.trp[rb_n], t1_n = a.trp[rb_n + 1];
-        for (int item = c0; item < c1; ++item) {
+        for (long long item = gw; item < cnt; item += nw) {
             const int rb = rb_n, t0 = t0_n, t1 = t1_n;
-            if (item + 1 < c1) {
-                rb_n = list[item + 1];
+            if (item + nw < cnt) {
+                rb_n = list[item + nw];
                 t0_n = a.trp[rb_n];
                 t1_n = a.trp[rb_n + 1];
             }
@@ -185,31 +179,36 @@ __device__ __forceinline__ void tm_select(const SolveArgs& a, const TmArgs& m,
 // compaction of the row blocks that keep an undecided entry.
 template <int P>
 __device__ __forceinline__ void tm_exclude(const SolveArgs& a, const TmArgs& m,
-                                           const int32_t* __restrict__ list, int cnt,
-                                           unsigned* grab, int* next, int32_t* __restrict__ dst,
-                                           int32_t* wkeep) {
+                                           const int32_t* __restrict__ list, int cnt, int* next,
+                                           int32_t* __restrict__ dst, int32_t* wkeep) {
     if (cnt <= 0) return;
     const unsigned lane = lane_id();
     const int g = (int)(lane >> 2), q = (int)(lane & 3);
     // C of solve g (this lane's B column), 16 bits per column block
     const uint16_t* cseg = g < m.k ? reinterpret_cast<const uint16_t*>(m.inb8 + (size_t)g * m.words)
                                    : nullptr;
-    const int ch = tm_chunk(cnt);
+    // the schedule of tm_select: warp gw takes entries gw, gw + nw, ...
+    const long long nw = (long long)gridDim.x * (blockDim.x / 32);
     const long long gw = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    if (gw >= (cnt + ch - 1) / ch) return;
-    for (;;) {
-        int c0 = 0;
-        if (lane == 0) c0 = (int)atomicAdd(grab, (unsigned)ch);
-        c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
-        if (c0 >= cnt) break;
-        const int c1 = min(c0 + ch, cnt);
-        int nkeep = 0;
-        int rb_n = list[c0];
+    if (gw >= cnt) return;
+    int nkeep = 0;
+    // survivors are staged per warp and appended kTmChunk at a time
+    auto flush = [&]() {
+        __syncwarp();
+        int o = 0;
+        if (lane == 0) o = atomicAdd(next, nkeep);
+        o = __shfl_sync(0xFFFFFFFFu, o, 0);
+        for (int k = (int)lane; k < nkeep; k += 32) dst[o + k] = wkeep[k];
+        __syncwarp();
+        nkeep = 0;
+    };
+    {
+        int rb_n = list[gw];
         int t0_n = a.trp[rb_n], t1_n = a.trp[rb_n + 1];
-        for (int item = c0; item < c1; ++item) {
+        for (long long item = gw; item < cnt; item += nw) {
             const int rb = rb_n, t0 = t0_n, t1 = t1_n;
-            if (item + 1 < c1) {
-                rb_n = list[item + 1];
+            if (item + nw < cnt) {
+                rb_n = list[item + nw];
                 t0_n = a.trp[rb_n];
                 t1_n = a.trp[rb_n + 1];
             }
@@ -237,16 +236,10 @@ __device__ __forceinline__ void tm_exclude(const SolveArgs& a, const TmArgs& m,
             if (__any_sync(0xFFFFFFFFu, (und & ~out) != 0u)) {
                 if (lane == 0) wkeep[nkeep] = rb;
                 ++nkeep;
+                if (nkeep == kTmChunk) flush();
             }
         }
-        __syncwarp();
-        if (nkeep) {
-            int o = 0;
-            if (lane == 0) o = atomicAdd(next, nkeep);
-            o = __shfl_sync(0xFFFFFFFFu, o, 0);
-            for (int k = (int)lane; k < nkeep; k += 32) dst[o + k] = wkeep[k];
-        }
-        __syncwarp();
+        if (nkeep) flush();
     }
 }
 
@@ -304,7 +297,7 @@ __global__ void __launch_bounds__(kTmBlock, 2) tile_multi_kernel(const SolveArgs
 
         // ---- Phase 1: selection test (CUDA cores)
         unsigned long long alive = 0;
-        tm_select(a, m, src, count, &ctl->grab[(2 * r) & 3][0], alive);
+        tm_select(a, m, src, count, alive);
         for (int o = 16; o; o >>= 1) alive += __shfl_xor_sync(0xFFFFFFFFu, alive, o);
         if (lane == 0 && alive) atomicAdd(&s_alive, alive);
         __syncthreads();
@@ -313,21 +306,19 @@ __global__ void __launch_bounds__(kTmBlock, 2) tile_multi_kernel(const SolveArgs
             s_alive = 0;
         }
         const int rr = r;
-        if (!grid_barrier(ctl, nblocks, a.spin_cap, [ctl, times, rr]() {
+        if (!grid_barrier(ctl, nblocks, a.spin_cap, [times, rr]() {
                 if (times && rr < kStatRounds) times->t[2 + rr] = global_ns();
-                ctl->grab[(2 * rr + 2) & 3][0] = 0;
             }))
             return;
 
         // ---- Phases 2 and 3: exclusion test (tensor cores), update, compaction
-        tm_exclude<P>(a, m, src, count, &ctl->grab[(2 * r + 1) & 3][0], next, dst, wkeep);
+        tm_exclude<P>(a, m, src, count, next, dst, wkeep);
         if (!grid_barrier(ctl, nblocks, a.spin_cap, [ctl, times, rr]() {
                 const unsigned long long alive = ctl->alive_acc64[rr & 3];
                 if (times && rr < kStatRounds) times->t[2 + kStatRounds + rr] = global_ns();
                 if (rr < kStatRounds) ctl->alive[rr] = (int)alive;
                 ctl->alive_sum += alive;
                 if (alive > 0) ctl->rounds = rr + 1;
-                ctl->grab[(2 * rr + 3) & 3][0] = 0;
                 ctl->bcnt[(rr + 2) & 3][0] = 0;
                 ctl->alive_acc64[(rr + 2) & 3] = 0;
             },
