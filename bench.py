@@ -91,6 +91,8 @@ def make_workload(name):
         return gg.grid2048(seed=3), "2048x2048 grid + 5% random diagonals, natural ids"
     if name == "grid_perm":
         return gg.grid2048(seed=3, permute_ids=True), "2048x2048 grid + 5% diagonals, permuted ids"
+    if name == "stencil":
+        return gg.stencil160(), "160x160x160 lattice, 27-point stencil, natural ids"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -534,7 +536,8 @@ def run_single(args):
     if "serve" in legs:
         line["serve"] = serve_leg(args, native, local, world, rank)
     if "tc" in legs:
-        line["tiles_tc"] = tc_leg(args, native, local, world)
+        line["tiles_tc"] = tc_leg(args, native, local, world, "grid")
+        line["tiles_tc_stencil"] = tc_leg(args, native, local, world, "stencil")
     if rank == 0 and args.cpu_baseline:
         import oracle
         rate, dt, res, reps = oracle_rate(g, min_seconds=args.cpu_seconds)
@@ -644,13 +647,14 @@ def batch_leg(args, native, local, world):
     }
 
 
-def tc_leg(args, native, local, world):
-    """The tile paths on the grid with natural ids (the densest tiles of the
-    configured workloads): one solve per path and tile payload, and 8 seeds
-    per launch on the CSR rows (CUDA cores) against the tiles with the
-    exclusion product A x [C_1 .. C_8] on tensor cores, per payload form."""
+def tc_leg(args, native, local, world, workload="grid"):
+    """The tile paths on a graph with dense 16 x 16 tiles (the grid with
+    natural ids, 13 arcs per tile; the 27-point stencil, 16): one solve per
+    path and tile payload, and 8 seeds per launch on the CSR rows (CUDA
+    cores) against the tiles with the exclusion product A x [C_1 .. C_8] on
+    tensor cores, per payload form."""
     import torch
-    (n, rp, col), desc = make_workload("grid")
+    (n, rp, col), desc = make_workload(workload)
     stream = torch.cuda.current_stream().cuda_stream
     drp = torch.from_numpy(rp).cuda()
     dcol = torch.from_numpy(col).cuda()
@@ -690,6 +694,7 @@ def tc_leg(args, native, local, world):
              native.MIS_TILE_INT8: "int8", native.MIS_TILE_FP16: "fp16"}
     same = True
     exclude_us = {}
+    select_us = {}
     for p, nm in names.items():
         native.mis_set_tile_payload(h, p)
         native.mis_set_path(h, native.MIS_PATH_TILE_TC, 16)
@@ -697,6 +702,7 @@ def tc_leg(args, native, local, world):
         res["multi8_ms"][f"tc_{nm}"] = timeit(eight)
         st = native.mis_get_stats(h)
         exclude_us[nm] = [round(st.exclude_ns[r] / 1e3, 1) for r in range(min(st.rounds, 64))]
+        select_us[nm] = [round(st.select_ns[r] / 1e3, 1) for r in range(min(st.rounds, 64))]
         same &= bool(torch.equal(out, ref8))
     native.mis_destroy(h)
     best = min((k for k in res["multi8_ms"] if k != "csr"), key=lambda k: res["multi8_ms"][k])
@@ -705,7 +711,9 @@ def tc_leg(args, native, local, world):
         "csr_launch_ms": res["multi8_ms"]["csr"],
         "tc_over_csr_speed": res["multi8_ms"]["csr"] / res["multi8_ms"][best],
         "exclude_phase_us_per_round": exclude_us,
+        "select_phase_us_per_round": select_us,
         "results_equal_csr": same}
+    res["arcs_per_tile16"] = res["arcs"] / max(res["tiles16"], 1)
     return res
 
 

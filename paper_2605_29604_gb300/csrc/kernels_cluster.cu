@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     // selected neighbour outrank v (word wv; kRep: and is it not excluded)?
     // else: is a neighbour in the set (kRep: selected in this round)?
     // kBatch loads are issued before any of them is tested.
-    auto scan = [&](int k, int v, uint32_t wv, bool sel) -> bool {
+    auto scan = [&](int k, int v, uint32_t wv, bool sel, bool late) -> bool {
         const int32_t* row;
         int deg;
         if (kRows) {
@@ -211,18 +211,22 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
                        : (kRep && !sel) ? (s_new_in[u[q] >> 5] >> (u[q] & 31)) & 1u
                                         : *word_of(u[q]);
             bool hit[kBatch];
-#pragma unroll
-            for (int q = 0; q < kBatch; ++q)
-                hit[q] = q0 + q < deg && (sel ? outranks_c(x[q], u[q], wv, v)
-                                              : kRep ? x[q] != 0u : x[q] >= kWordInMin);
-            if (kRep && sel) {
-#pragma unroll
-                for (int q = 0; q < kBatch; ++q)
-                    hit[q] = hit[q] && !((s_gone[u[q] >> 5] >> (u[q] & 31)) & 1u);
-            }
             bool any = false;
 #pragma unroll
-            for (int q = 0; q < kBatch; ++q) any |= hit[q];
+            for (int q = 0; q < kBatch; ++q) {
+                hit[q] = q0 + q < deg && (sel ? outranks_c(x[q], u[q], wv, v)
+                                              : kRep ? x[q] != 0u : x[q] >= kWordInMin);
+                any |= hit[q];
+            }
+            // a neighbour that outranks v by its word counts only if it is
+            // not excluded; the bits are read only for such neighbours, and
+            // not at all in round 0 (nothing is excluded yet)
+            if (kRep && sel && any && late) {
+                any = false;
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q)
+                    any |= hit[q] && !((s_gone[u[q] >> 5] >> (u[q] & 31)) & 1u);
+            }
             if (any) return true;
         }
         return false;
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
             bool cand = false;
             if (k < cnt) {
                 const uint32_t wv = s_own[k];
-                if ((wv >> 29) == 1u && !scan(k, base + k, wv, true)) {
+                if ((wv >> 29) == 1u && !scan(k, base + k, wv, true, r > 0)) {
                     s_own[k] = wv | kWordInSet;
                     cand = true;
                 }
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
             if (k < cnt) {
                 const uint32_t wv = s_own[k];
                 if ((wv >> 29) == 1u) {
-                    if (scan(k, base + k, wv, false)) {
+                    if (scan(k, base + k, wv, false, r > 0)) {
                         s_own[k] = kWordOut;
                         out = true;
                     } else {

@@ -72,6 +72,8 @@ def _load():
         lib.gg_grid_diag.restype = P
         lib.gg_rgg.argtypes = [i32, dbl, u64]
         lib.gg_rgg.restype = P
+        lib.gg_stencil27.argtypes = [i32, i32, i32]
+        lib.gg_stencil27.restype = P
         lib.gg_permute.argtypes = [P, u64]
         lib.gg_permute.restype = P
         lib.gg_stream.argtypes = [u64, u64]
@@ -175,6 +177,13 @@ def rgg(n: int, avg_degree: float, seed: int):
     return _take(_load().gg_rgg(n, r, seed & (2**64 - 1)))
 
 
+def stencil27(nx: int, ny: int, nz: int):
+    """nx x ny x nz lattice with the 27-point stencil (every vertex adjacent
+    to the up to 26 others within one step in each axis), natural ids
+    (z * ny + y) * nx + x."""
+    return _take(_load().gg_stencil27(nx, ny, nz))
+
+
 def permute(n: int, row_ptr, col_idx, seed: int):
     """Uniform random relabelling of an existing graph."""
     lib = _load()
@@ -255,6 +264,12 @@ def rmat22(seed: int = 22, scale: int = 22):
 def grid2048(seed: int = 3, permute_ids: bool = False, width: int = 2048):
     """2048 x 2048 grid plus 5% random diagonals, natural or permuted ids."""
     return grid_diag(width, 0.05, seed, permute=permute_ids)
+
+
+def stencil160():
+    """160 x 160 x 160 lattice, 27-point stencil, natural ids: 4,096,000
+    vertices, 26 neighbours inside the box."""
+    return stencil27(160, 160, 160)
 
 
 def batch_mixed(count: int, seed: int, nmin: int = 64, nmax: int = 65_536, threads: int = 0):

@@ -352,6 +352,54 @@ gg_graph *gg_grid_diag(int32_t W, int64_t ndiag, uint64_t seed)
     return g;
 }
 
+/*
+ * nx x ny x nz box of a 3D lattice, vertex (x, y, z) has id (z ny + y) nx + x
+ * (natural order); every pair of distinct vertices whose coordinates differ by
+ * at most 1 in each axis is an edge (the 27-point stencil: 26 neighbours
+ * inside the box).  Edges are emitted for the 13 offsets that come after
+ * (0, 0, 0) in (dz, dy, dx) order.
+ */
+gg_graph *gg_stencil27(int32_t nx, int32_t ny, int32_t nz)
+{
+    if (nx < 1 || ny < 1 || nz < 1) return NULL;
+    int64_t n64 = (int64_t)nx * ny * nz;
+    if (n64 > INT32_MAX) return NULL;
+    int64_t ne = 0;
+    for (int dz = 0; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;
+                ne += (int64_t)(nx - (dx ? 1 : 0)) * (ny - (dy ? 1 : 0)) * (nz - dz);
+            }
+    int32_t *eu = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ne ? ne : 1));
+    int32_t *ev = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ne ? ne : 1));
+    if (!eu || !ev) {
+        free(eu);
+        free(ev);
+        return NULL;
+    }
+    int64_t k = 0;
+    for (int32_t z = 0; z < nz; ++z)
+        for (int32_t y = 0; y < ny; ++y)
+            for (int32_t x = 0; x < nx; ++x) {
+                const int32_t id = (int32_t)(((int64_t)z * ny + y) * nx + x);
+                for (int dz = 0; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;
+                            const int32_t x2 = x + dx, y2 = y + dy, z2 = z + dz;
+                            if (x2 < 0 || x2 >= nx || y2 < 0 || y2 >= ny || z2 >= nz) continue;
+                            eu[k] = id;
+                            ev[k] = (int32_t)(((int64_t)z2 * ny + y2) * nx + x2);
+                            ++k;
+                        }
+            }
+    gg_graph *g = k == ne ? gg_from_edges((int32_t)n64, ne, eu, ev) : NULL;
+    free(eu);
+    free(ev);
+    return g;
+}
+
 typedef struct {
     int64_t cell;
     int32_t idx;

@@ -29,6 +29,7 @@ FAMILIES = {
     "er_small": lambda: gg.er_gnm(3000, 12000, 4),
     "rmat14": lambda: gg.rmat(14, 16, 0.57, 0.19, 0.19, 9, permute=True),
     "grid": lambda: gg.grid_diag(127, 0.05, 2),
+    "stencil27": lambda: gg.stencil27(23, 19, 17),  # ragged in every axis
     "rgg": lambda: gg.rgg(20000, 10.0, 3),
     "dense": lambda: gg.random_small(700, 0.3, 6),
     "star": lambda: gg.star(5000),

@@ -27,6 +27,7 @@ FAMILIES = {
     "rmat14_natural": lambda: gg.rmat(14, 16, 0.57, 0.19, 0.19, 9, permute=False),
     "grid": lambda: gg.grid_diag(127, 0.05, 2),
     "grid_perm": lambda: gg.grid_diag(127, 0.05, 2, permute=True),
+    "stencil27": lambda: gg.stencil27(23, 19, 17),  # ragged in every axis
     "star_hub": lambda: gg.disjoint_union([gg.star(150000), gg.er_gnm(5000, 20000, 3)]),
     "dense": lambda: gg.random_small(700, 0.3, 6),
     "k_ab": lambda: gg.complete_bipartite(40, 900),

@@ -30,6 +30,7 @@ FAMILIES = {
     "rmat14": lambda: gg.rmat(14, 16, 0.57, 0.19, 0.19, 9, permute=True),
     "grid": lambda: gg.grid_diag(131, 0.05, 2),
     "grid_perm": lambda: gg.grid_diag(131, 0.05, 2, permute=True),
+    "stencil27": lambda: gg.stencil27(23, 19, 17),  # ragged in every axis
     "rgg": lambda: gg.rgg(20001, 10.0, 3),
     "dense": lambda: gg.random_small(300, 0.5, 6),
     "star_hub": lambda: gg.disjoint_union([gg.star(40000), gg.er_gnm(5000, 20000, 3)]),
@@ -65,7 +66,7 @@ def numpy_tiles(n, rp, col, T):
     return trp, (uniq % nrb).astype(np.int32), bits.reshape(-1)
 
 
-@pytest.mark.parametrize("name", ["er_10k", "rmat14", "grid", "grid_perm", "path_ragged", "empty"])
+@pytest.mark.parametrize("name", ["er_10k", "rmat14", "grid", "grid_perm", "stencil27", "path_ragged", "empty"])
 @pytest.mark.parametrize("T", [8, 16])
 def test_converter_matches_definition(name, T):
     import torch
@@ -98,7 +99,7 @@ PAYLOADS = [native.MIS_TILE_BITS, native.MIS_TILE_BITS_B1, native.MIS_TILE_INT8,
             native.MIS_TILE_FP16]
 
 
-@pytest.mark.parametrize("name", ["er_10k", "rmat14", "grid", "grid_perm", "path_ragged", "empty",
+@pytest.mark.parametrize("name", ["er_10k", "rmat14", "grid", "grid_perm", "stencil27", "path_ragged", "empty",
                                   "complete"])
 @pytest.mark.parametrize("payload", PAYLOADS)
 def test_payload_matches_definition(name, payload):
