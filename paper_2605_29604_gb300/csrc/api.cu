@@ -18,7 +18,14 @@
 
 namespace tcmis {
 
-int apply_cached_choice(mis_graph* g);  // autotuner section below
+// autotuner section below: the process's cached choice for the graph's
+// class (false if none); is_csr tells whether it is the CSR kernel's
+namespace {
+struct TuneChoice;
+}
+bool cached_choice(mis_graph* g, TuneChoice** c, bool* is_csr);
+int apply_cached(mis_graph* g, TuneChoice* c);
+void drop_choice(TuneChoice* c);
 
 namespace {
 thread_local int t_err_code = 0;
@@ -49,6 +56,16 @@ template <class T>
 cudaError_t dalloc(T** p, int64_t count, int64_t* footprint) {
     const size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(count, 1);
     cudaError_t e = dev_alloc((void**)p, bytes);
+    if (e == cudaSuccess && footprint) *footprint += (int64_t)bytes;
+    return e;
+}
+
+// The same without the fence: a group of these is followed by one
+// dev_alloc_fence before any of the buffers is used on another stream.
+template <class T>
+cudaError_t dalloc_deferred(T** p, int64_t count, int64_t* footprint) {
+    const size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(count, 1);
+    cudaError_t e = dev_alloc_deferred((void**)p, bytes);
     if (e == cudaSuccess && footprint) *footprint += (int64_t)bytes;
     return e;
 }
@@ -107,16 +124,19 @@ cudaError_t ws_reserve(Workspace& w, int64_t n, int32_t count) {
     ws_free(w);
     cudaError_t e;
     int64_t b = 0;
-    if ((e = dalloc(&w.word, cap, &b)) != cudaSuccess || (e = dalloc(&w.wl0, cap, &b)) != cudaSuccess ||
-        (e = dalloc(&w.wl1, cap, &b)) != cudaSuccess ||
-        (e = dalloc(&w.wlp, cap, &b)) != cudaSuccess ||
-        (e = dalloc(&w.inbits, cap / 32 + 1, &b)) != cudaSuccess ||
-        (e = dalloc(&w.rbl0, cap / 8, &b)) != cudaSuccess ||
-        (e = dalloc(&w.rbl1, cap / 8, &b)) != cudaSuccess ||
-        (e = dalloc(reinterpret_cast<unsigned char**>(&w.ctl), (int64_t)kCtlBlockBytes, &b)) !=
-            cudaSuccess ||
-        (e = dalloc(&w.seeds, std::max(count, 1), &b)) != cudaSuccess ||
-        (e = dalloc(&w.out, cap, &b)) != cudaSuccess) {
+    if ((e = dalloc_deferred(&w.word, cap, &b)) != cudaSuccess ||
+        (e = dalloc_deferred(&w.wl0, cap, &b)) != cudaSuccess ||
+        (e = dalloc_deferred(&w.wl1, cap, &b)) != cudaSuccess ||
+        (e = dalloc_deferred(&w.wlp, cap, &b)) != cudaSuccess ||
+        (e = dalloc_deferred(&w.inbits, cap / 32 + 1, &b)) != cudaSuccess ||
+        (e = dalloc_deferred(&w.rbl0, cap / 8, &b)) != cudaSuccess ||
+        (e = dalloc_deferred(&w.rbl1, cap / 8, &b)) != cudaSuccess ||
+        (e = dalloc_deferred(reinterpret_cast<unsigned char**>(&w.ctl),
+                             (int64_t)kCtlBlockBytes, &b)) != cudaSuccess ||
+        (e = dalloc_deferred(&w.seeds, std::max(count, 1), &b)) != cudaSuccess ||
+        (e = dalloc_deferred(&w.out, cap, &b)) != cudaSuccess ||
+        (e = dev_alloc_fence()) != cudaSuccess) {
+        dev_alloc_fence();
         ws_free(w);
         return e;
     }
@@ -268,17 +288,19 @@ int finish_create(mis_graph* g) {
     const int64_t col_alloc = ((d.arcs + 3) / 4) * 4 + 4;
     // the selection prefixes and round-0 classes hold for Eq. 1's degree order only
     const bool order = g->opt.order_rows != 0 && g->opt.priority == MIS_PRIORITY_EQ1;
-    if ((e = ws_reserve(d.ws, d.n, d.count)) != cudaSuccess ||
-        (e = dalloc(&d.order0, d.n, &d.footprint)) != cudaSuccess ||
-        (order && (e = dalloc(&d.r0class, d.n, &d.footprint)) != cudaSuccess) ||
-        (order && (e = dalloc(&d.sure_out, d.n, &d.footprint)) != cudaSuccess) ||
-        (order && (e = dalloc(&d.col_sel, col_alloc, &d.footprint)) != cudaSuccess) ||
-        (order && (e = dalloc(&d.split, d.n, &d.footprint)) != cudaSuccess))
+    if ((e = dalloc_deferred(&d.order0, d.n, &d.footprint)) != cudaSuccess ||
+        (order && (e = dalloc_deferred(&d.r0class, d.n, &d.footprint)) != cudaSuccess) ||
+        (order && (e = dalloc_deferred(&d.sure_out, d.n, &d.footprint)) != cudaSuccess) ||
+        (order && (e = dalloc_deferred(&d.col_sel, col_alloc, &d.footprint)) != cudaSuccess) ||
+        (order && (e = dalloc_deferred(&d.split, d.n, &d.footprint)) != cudaSuccess) ||
+        (e = ws_reserve(d.ws, d.n, d.count)) != cudaSuccess) {  // its fence covers these
+        dev_alloc_fence();
         return set_cuda_error(e, "workspace allocation");
+    }
     d.footprint += d.ws.bytes;
-    if ((e = cudaMallocHost((void**)&d.ctl_host, sizeof(Ctl))) != cudaSuccess ||
-        (e = cudaMallocHost((void**)&d.times_host, sizeof(PhaseTimes))) != cudaSuccess)
-        return set_cuda_error(e, "pinned allocation");
+    d.ctl_host = static_cast<Ctl*>(host_small_alloc(sizeof(Ctl)));
+    d.times_host = static_cast<PhaseTimes*>(host_small_alloc(sizeof(PhaseTimes)));
+    if (!d.ctl_host || !d.times_host) return set_cuda_error(cudaErrorMemoryAllocation, "pinned allocation");
     std::memset(d.ctl_host, 0, sizeof(Ctl));
     g->tpr = g->opt.threads_per_row;
     g->path = MIS_PATH_CSR;
@@ -325,13 +347,20 @@ int finish_create(mis_graph* g) {
         if (e != cudaSuccess) return set_cuda_error(e, "degree ordering");
     }
     lg.mark("keyed list", g->own_stream);
-    const int brc = rebin(g, thr, g->own_stream);
-    if (brc != MIS_OK) return brc;
+    // AUTO: the autotuner's cached choice for the graph's class, if any; a
+    // CSR choice takes the place of the default degree bins
+    TuneChoice* cached = nullptr;
+    bool cached_csr = false;
+    if (g->opt.path == MIS_PATH_AUTO && g->opt.threads_per_row == 0)
+        cached_choice(g, &cached, &cached_csr);
+    lg.mark("tuning lookup", g->own_stream);
+    int brc = MIS_OK;
+    if (!cached_csr) brc = rebin(g, thr, g->own_stream);
     lg.mark("degree bins", g->own_stream);
-    if (g->opt.path == MIS_PATH_AUTO && g->opt.threads_per_row == 0) {
-        const int arc = apply_cached_choice(g);
-        if (arc != MIS_OK) return arc;
-    }
+    if (brc == MIS_OK && cached) brc = apply_cached(g, cached);
+    lg.mark("tuned choice", g->own_stream);
+    drop_choice(cached);
+    if (brc != MIS_OK) return brc;
     if (g->opt.build_tiles == 1 || g->opt.path == MIS_PATH_TILE || g->opt.path == MIS_PATH_TILE_TC) {
         const int rc = use_tiles(g, g->opt.path == MIS_PATH_AUTO || g->opt.path == MIS_PATH_CSR
                                         ? MIS_PATH_TILE : g->opt.path, 16);
@@ -341,7 +370,10 @@ int finish_create(mis_graph* g) {
     return MIS_OK;
 }
 
-constexpr size_t kFlagsBytes = 24;  // flag word (padded to 8 bytes) + two 64-bit sums
+// flag word (padded to 8 bytes), the two 64-bit sums of the symmetry check,
+// and the two 64-bit counters of the tile-density sample (estimate_arcs_per_tile)
+constexpr size_t kFlagsBytes = 40;
+constexpr size_t kSampleAccOffset = 24;
 
 int validate_device(mis_graph* g, cudaStream_t s) {
     GraphData& d = g->d;
@@ -350,8 +382,9 @@ int validate_device(mis_graph* g, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(d.flags, 0, kFlagsBytes, s);
     if (e == cudaSuccess)
         e = launch_validate(d.rp, d.col, d.n, d.arcs, g->opt.check_symmetry, d.flags, sym, s);
-    unsigned long long hb[3] = {0, 0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, d.flags, kFlagsBytes, cudaMemcpyDeviceToHost, s);
+    unsigned long long hb[3] = {0, 0, 0};  // the flag word and the two sums
+    static_assert(sizeof(hb) == kSampleAccOffset, "flag word and sums");
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, d.flags, sizeof(hb), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return set_cuda_error(e, "graph validation");
     unsigned f = (unsigned)(hb[0] & 0xFFFFFFFFull);
@@ -369,21 +402,15 @@ int validate_device(mis_graph* g, cudaStream_t s) {
 }
 
 // Host CSR without the symmetry check: col_idx goes up in pieces on the
-// handle's own stream while each landed piece is checked on `s`, so the
-// checks hide behind the copy (host-to-device bandwidth bounds a create).
-constexpr int64_t kUploadPiece = 16 << 20;  // arcs per piece
+// handle's own stream, all enqueued at once, while row_ptr is checked and
+// then each landed piece is checked on `s`, so the checks hide behind the
+// copy (host-to-device bandwidth bounds a create).
+constexpr int64_t kUploadPiece = 4 << 20;  // arcs per piece
 
 int upload_checked(mis_graph* g, const int32_t* col_idx, cudaStream_t s) {
     GraphData& d = g->d;
     cudaError_t e = cudaSuccess;
     if (!g->own_stream) e = cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.flags, 0, sizeof(unsigned), s);
-    if (e == cudaSuccess) e = launch_validate_rowptr(d.rp, d.n, d.arcs, d.flags, s);
-    unsigned f = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&f, d.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the arc checks trust row_ptr
-    if (e != cudaSuccess) return set_cuda_error(e, "graph upload");
-    if (f) return set_error(MIS_EINVAL, "invalid graph: row_ptr not monotone from 0 to arcs;");
     std::vector<cudaEvent_t> evs;
     for (int64_t a0 = 0; a0 < d.arcs && e == cudaSuccess; a0 += kUploadPiece) {
         const int64_t a1 = std::min(d.arcs, a0 + kUploadPiece);
@@ -394,11 +421,26 @@ int upload_checked(mis_graph* g, const int32_t* col_idx, cudaStream_t s) {
         e = cudaMemcpyAsync(d.col + a0, col_idx + a0, sizeof(int32_t) * (size_t)(a1 - a0),
                             cudaMemcpyHostToDevice, g->own_stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev, g->own_stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.flags, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = launch_validate_rowptr(d.rp, d.n, d.arcs, d.flags, s);
+    unsigned f = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&f, d.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the arc checks trust row_ptr
+    if (e == cudaSuccess && f) e = cudaErrorInvalidValue;
+    for (size_t k = 0; k < evs.size() && e == cudaSuccess; ++k) {
+        const int64_t a0 = (int64_t)k * kUploadPiece, a1 = std::min(d.arcs, a0 + kUploadPiece);
+        e = cudaStreamWaitEvent(s, evs[k], 0);
         // the order check of the first arc of a piece reads the previous
         // piece's last arc, which the copy stream has landed before
         if (e == cudaSuccess)
             e = launch_validate_arcs(d.rp, d.col, d.n, a0, a1, 0, d.flags, nullptr, s);
+    }
+    if (f) {
+        // the copies still run: they finish before the caller frees the graph
+        cudaStreamSynchronize(g->own_stream);
+        for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+        return set_error(MIS_EINVAL, "invalid graph: row_ptr not monotone from 0 to arcs;");
     }
     f = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&f, d.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
@@ -479,7 +521,7 @@ void free_graph(mis_graph* g) {
     dfree(d.nv);
     dfree(d.garcs);
     dfree(d.roff);
-    if (d.seeds_host) cudaFreeHost(d.seeds_host);
+    host_small_free(d.seeds_host);
     free_tiles(d);
     dfree(d.order0);
     dfree(d.word8);
@@ -497,8 +539,8 @@ void free_graph(mis_graph* g) {
     dfree(d.col_sel);
     dfree(d.split);
     ws_free(d.ws);
-    if (d.ctl_host) cudaFreeHost(d.ctl_host);
-    if (d.times_host) cudaFreeHost(d.times_host);
+    host_small_free(d.ctl_host);
+    host_small_free(d.times_host);
     dfree(d.flags);
     if (g->own_stream) cudaStreamDestroy(g->own_stream);
     cudaSetDevice(prev);
@@ -642,14 +684,14 @@ void tune_save_locked() {
 // Distinct 8-column blocks of 8-row block rb: an 8-way merge of its sorted
 // rows, stopped after kSampleArcs arcs (a hub row would make one thread walk
 // it all); the tiles of the rest are extrapolated at the same rate.
-constexpr int kSampleArcs = 256;
+constexpr int kSampleArcs = 64;
 
 __global__ void tile_sample_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                   int32_t n, const int32_t* __restrict__ rbs, int count,
+                                   int32_t n, int32_t nrb, int count,
                                    unsigned long long* __restrict__ acc) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= count) return;
-    const int rb = rbs[k];
+    const int rb = (int)((long long)k * nrb / count);
     int cur[8], end[8];
     long long arcs = 0;
     for (int i = 0; i < 8; ++i) {
@@ -658,17 +700,21 @@ __global__ void tile_sample_kernel(const int32_t* __restrict__ rp, const int32_t
         end[i] = v < n ? rp[v + 1] : 0;
         arcs += end[i] - cur[i];
     }
+    // the column block of each row's next arc, kept in registers (one load
+    // per arc consumed)
+    int head[8];
+    for (int i = 0; i < 8; ++i) head[i] = cur[i] < end[i] ? (col[cur[i]] >> 3) : INT32_MAX;
     long long tiles = 0, seen = 0;
     while (seen < kSampleArcs) {
         int cb = INT32_MAX;
-        for (int i = 0; i < 8; ++i)
-            if (cur[i] < end[i]) cb = min(cb, col[cur[i]] >> 3);
+        for (int i = 0; i < 8; ++i) cb = min(cb, head[i]);
         if (cb == INT32_MAX) break;
         ++tiles;
         for (int i = 0; i < 8; ++i)
-            while (cur[i] < end[i] && (col[cur[i]] >> 3) == cb) {
+            while (head[i] == cb) {
                 ++cur[i];
                 ++seen;
+                head[i] = cur[i] < end[i] ? (col[cur[i]] >> 3) : INT32_MAX;
             }
     }
     if (seen > 0 && seen < arcs) tiles = (tiles * arcs + seen - 1) / seen;
@@ -676,38 +722,48 @@ __global__ void tile_sample_kernel(const int32_t* __restrict__ rp, const int32_t
     atomicAdd(&acc[1], (unsigned long long)tiles);
 }
 
-// Estimated arcs per non-empty 8 x 8 tile, from up to 2048 row blocks spread
+// Estimated arcs per non-empty 8 x 8 tile, from up to 4096 row blocks spread
 // evenly over the graph.
 double estimate_arcs_per_tile(mis_graph* g) {
     GraphData& d = g->d;
     const int32_t nrb = (d.n + 7) / 8;
     if (nrb == 0 || d.arcs == 0) return 0.0;
-    const int count = std::min<int32_t>(nrb, 2048);
-    std::vector<int32_t> rbs((size_t)count);
-    for (int k = 0; k < count; ++k) rbs[(size_t)k] = (int32_t)((int64_t)k * nrb / count);
-    int32_t* d_rbs = nullptr;
-    unsigned long long* d_acc = nullptr;
+    const int count = std::min<int32_t>(nrb, 4096);
+    // the counters live in the graph's flag buffer: no allocation here
+    unsigned long long* d_acc =
+        reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(d.flags) +
+                                              kSampleAccOffset);
     unsigned long long h[2] = {0, 0};
     cudaStream_t s = g->own_stream;
-    cudaError_t e = dev_alloc((void**)&d_rbs, 4 * (size_t)count);
-    if (e == cudaSuccess) e = dev_alloc((void**)&d_acc, 16);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rbs, rbs.data(), 4 * (size_t)count,
-                                              cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_acc, 0, 16, s);
+    cudaError_t e = cudaMemsetAsync(d_acc, 0, 16, s);
     if (e == cudaSuccess) {
-        tile_sample_kernel<<<(count + 127) / 128, 128, 0, s>>>(d.rp, d.col, d.n, d_rbs, count,
-                                                               d_acc);
+        tile_sample_kernel<<<(count + 127) / 128, 128, 0, s>>>(d.rp, d.col, d.n, nrb, count, d_acc);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_acc, 16, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    dev_free(d_rbs);
-    dev_free(d_acc);
     if (e != cudaSuccess || h[1] == 0) {
         cudaGetLastError();
         return 0.0;
     }
     return (double)h[0] / (double)h[1];
+}
+
+// The device's name with blanks as underscores, looked up once per device
+// (cudaGetDeviceProperties takes hundreds of microseconds).
+std::string device_name(int device) {
+    static std::mutex mu;
+    static std::map<int, std::string> names;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = names.find(device);
+    if (it != names.end()) return it->second;
+    cudaDeviceProp prop;
+    std::string dev = "gpu";
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) dev = prop.name;
+    for (char& c : dev)
+        if (c == ' ') c = '_';
+    names[device] = dev;
+    return dev;
 }
 
 std::string density_class(mis_graph* g, double apt) {
@@ -718,11 +774,7 @@ std::string density_class(mis_graph* g, double apt) {
     int size_b = 0;
     while (size_b < 31 && (1ll << size_b) <= (long long)d.n) ++size_b;
     const char loc = apt < 1.5 ? 's' : (apt < 3.0 ? 'm' : 'd');
-    cudaDeviceProp prop;
-    std::string dev = "gpu";
-    if (cudaGetDeviceProperties(&prop, d.device) == cudaSuccess) dev = prop.name;
-    for (char& c : dev)
-        if (c == ' ') c = '_';
+    const std::string dev = device_name(d.device);
     // graphs with create-time round-0 structures solve a different problem
     // size than graphs scanned from their full rows: tuned apart
     const int order = d.col_sel ? g->opt.order_rows : 0;
@@ -905,22 +957,26 @@ int autotune(mis_graph* g, int reps, mis_tuning* out) {
 }
 
 // AUTO at create: the cached choice of the graph's class, if any.
-int apply_cached_choice(mis_graph* g) {
-    TuneChoice c;
+bool cached_choice(mis_graph* g, TuneChoice** out, bool* is_csr) {
+    *out = nullptr;
+    *is_csr = false;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_load_locked();
-        if (g_tune_cache.empty()) return MIS_OK;
+        if (g_tune_cache.empty()) return false;
     }
     const std::string key = density_class(g, estimate_arcs_per_tile(g));
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(key);
-        if (it == g_tune_cache.end()) return MIS_OK;
-        c = it->second;
-    }
-    return apply_choice(g, c);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it == g_tune_cache.end()) return false;
+    *out = new TuneChoice(it->second);
+    *is_csr = it->second.path == MIS_PATH_CSR;
+    return true;
 }
+
+int apply_cached(mis_graph* g, TuneChoice* c) { return apply_choice(g, *c); }
+
+void drop_choice(TuneChoice* c) { delete c; }
 
 }  // namespace tcmis
 
@@ -1140,8 +1196,8 @@ mis_graph* mis_create_batch(int32_t count, const int32_t* ns, const int32_t* con
         (e = dalloc(&d.nv, count, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.garcs, count, &d.footprint)) != cudaSuccess ||
         (e = dalloc(&d.roff, count, &d.footprint)) != cudaSuccess ||
-        (e = cudaMallocHost((void**)&d.seeds_host, sizeof(uint64_t) * (size_t)count)) !=
-            cudaSuccess) {
+        !(d.seeds_host = static_cast<uint64_t*>(host_small_alloc(sizeof(uint64_t) * (size_t)count)))) {
+        if (e == cudaSuccess) e = cudaErrorMemoryAllocation;
         set_cuda_error(e, "batch allocation");
         free_graph(g);
         return nullptr;

@@ -95,8 +95,17 @@ struct SolveArgs {
 
 // mem.cu: device memory from the stream-ordered pool (reused across
 // creates); callers synchronise their streams before dev_free.
+// dev_alloc_deferred leaves the allocation ordered on the legacy stream
+// only: dev_alloc_fence makes every deferred allocation before it usable on
+// any stream.
 cudaError_t dev_alloc(void** p, size_t bytes);
+cudaError_t dev_alloc_deferred(void** p, size_t bytes);
+cudaError_t dev_alloc_fence();
 void dev_free(void* p);
+// mem.cu: small pinned host blocks from never-returned slabs (larger
+// requests: cudaMallocHost); null on failure.
+void* host_small_alloc(size_t bytes);
+void host_small_free(void* p);
 
 // Launch configuration chosen by the host.
 struct LaunchCfg {

@@ -12,9 +12,11 @@
 // A warp takes one row block (16 vertices):
 //
 //   Phase 1  selection test (CUDA cores): lane (i, h) owns row i in solves
-//            4h .. 4h + 3; each set bit j of the row in a tile is a neighbour
-//            u = 16 tcol + j, whose four words (16 bytes) are compared with
+//            4h .. 4h + 3 and scans the row in the CSR, four neighbours per
+//            step; each neighbour's four words (16 bytes) are compared with
 //            the row's.  Candidates are marked in their words and in C_s.
+//            (Visiting the row's neighbours tile by tile costs a step per
+//            tile of the row block, also where the row has no bit in it.)
 //   Phase 2  exclusion test (tensor cores): D = sum over tiles of A_t x C.
 //            Lane (g, q), g = lane / 4 and q = lane % 4, receives the MMA
 //            entries D[g][2q], D[g][2q+1], D[g+8][2q], D[g+8][2q+1] and owns
@@ -69,15 +71,6 @@ struct TmArgs {
     MultiSeeds seeds;
 };
 
-// Phase 1 over the row-block list.  Here lane (i, h), i = lane / 2 and
-// h = lane % 2, owns row i in solves 4h .. 4h + 3.  The row block's tiles
-// are taken two at a time: their column blocks and the row's bits are
-// loaded together, then the first two neighbours of the row in each of the
-// two tiles (the usual case; more are taken one by one), so that the words
-// of up to four neighbours (16 bytes each: the lane's four solves) are
-// loaded at once instead of one after another.
-constexpr int kSelTiles = 2;  // tiles per step
-constexpr int kSelBits = 2;   // neighbours per tile-row loaded in the batch
 __device__ __forceinline__ unsigned und_quad(uint4 w) {
     return ((w.x >> 29) == 1u ? 1u : 0u) | ((w.y >> 29) == 1u ? 2u : 0u) |
            ((w.z >> 29) == 1u ? 4u : 0u) | ((w.w >> 29) == 1u ? 8u : 0u);
@@ -88,6 +81,8 @@ __device__ __forceinline__ unsigned blocks4(uint4 wu, int u, uint4 wv, int v) {
            (outranks_m(wu.z, u, wv.z, v) ? 4u : 0u) | (outranks_m(wu.w, u, wv.w, v) ? 8u : 0u);
 }
 
+// Phase 1 over the row-block list.  Here lane (i, h), i = lane / 2 and
+// h = lane % 2, owns row i in solves 4h .. 4h + 3.
 __device__ __forceinline__ void tm_select(const SolveArgs& a, const TmArgs& m,
                                           const int32_t* __restrict__ list, int cnt,
                                           unsigned long long& alive) {
@@ -102,14 +97,9 @@ __device__ __forceinline__ void tm_select(const SolveArgs& a, const TmArgs& m,
     {
         if (gw >= cnt) return;
         int rb_n = list[gw];
-        int t0_n = a.trp[rb_n], t1_n = a.trp[rb_n + 1];
         for (long long item = gw; item < cnt; item += nw) {
-            const int rb = rb_n, t0 = t0_n, t1 = t1_n;
-            if (item + nw < cnt) {
-                rb_n = list[item + nw];
-                t0_n = a.trp[rb_n];
-                t1_n = a.trp[rb_n + 1];
-            }
+            const int rb = rb_n;
+            if (item + nw < cnt) rb_n = list[item + nw];
             const int v = rb * 16 + i;
             uint4* wp = reinterpret_cast<uint4*>(m.word8 + (size_t)kMaxMulti * v + 4 * h);
             uint4 w = *wp;
@@ -117,47 +107,28 @@ __device__ __forceinline__ void tm_select(const SolveArgs& a, const TmArgs& m,
             alive += __popc(und);
             unsigned blocked = ~und & 0xFu;
             const uint32_t* w8 = m.word8 + 4 * h;
-            for (int tb = t0; tb < t1; tb += kSelTiles) {
-                if (!__any_sync(0xFFFFFFFFu, blocked != 0xFu)) break;
-                int cb[kSelTiles];
-                uint32_t bits[kSelTiles];
-#pragma unroll
-                for (int k = 0; k < kSelTiles; ++k) {
-                    const bool ok = tb + k < t1 && blocked != 0xFu;
-                    cb[k] = ok ? __ldg(a.tcol + tb + k) : 0;
-                    bits[k] = ok ? tile_row16(a.tbits, tb + k, i) : 0u;
+            // row v from the CSR, four neighbours per step (one 16-byte load
+            // of col_idx), their words in this lane's four solves gathered
+            // before any test
+            const int rb0 = und ? a.rp[v] : 0;
+            const int re0 = und ? a.rp[v + 1] : 0;
+            int p0 = rb0 & ~3;
+            for (;;) {
+                const bool act = blocked != 0xFu && p0 < re0;
+                if (!__any_sync(0xFFFFFFFFu, act)) break;
+                if (act) {
+                    const int4 c = __ldg(reinterpret_cast<const int4*>(a.col + p0));
+                    const bool h0 = p0 >= rb0, h1 = p0 + 1 >= rb0 && p0 + 1 < re0,
+                               h2 = p0 + 2 >= rb0 && p0 + 2 < re0, h3 = p0 + 3 < re0;
+                    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+                    const uint4 q0 = h0 ? *reinterpret_cast<const uint4*>(w8 + (size_t)kMaxMulti * c.x) : z;
+                    const uint4 q1 = h1 ? *reinterpret_cast<const uint4*>(w8 + (size_t)kMaxMulti * c.y) : z;
+                    const uint4 q2 = h2 ? *reinterpret_cast<const uint4*>(w8 + (size_t)kMaxMulti * c.z) : z;
+                    const uint4 q3 = h3 ? *reinterpret_cast<const uint4*>(w8 + (size_t)kMaxMulti * c.w) : z;
+                    blocked |= (h0 ? blocks4(q0, c.x, w, v) : 0u) | (h1 ? blocks4(q1, c.y, w, v) : 0u) |
+                               (h2 ? blocks4(q2, c.z, w, v) : 0u) | (h3 ? blocks4(q3, c.w, w, v) : 0u);
                 }
-                constexpr int kU = kSelTiles * kSelBits;
-                int u[kU];
-                bool has[kU];
-#pragma unroll
-                for (int k = 0; k < kSelTiles; ++k) {
-#pragma unroll
-                    for (int r = 0; r < kSelBits; ++r) {
-                        has[kSelBits * k + r] = bits[k] != 0u;
-                        u[kSelBits * k + r] =
-                            cb[k] * 16 + (has[kSelBits * k + r] ? __ffs(bits[k]) - 1 : 0);
-                        bits[k] &= bits[k] - 1;
-                    }
-                }
-                uint4 wu[kU];
-#pragma unroll
-                for (int k = 0; k < kU; ++k)
-                    wu[k] = has[k] ? *reinterpret_cast<const uint4*>(w8 + (size_t)kMaxMulti * u[k])
-                                   : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-                for (int k = 0; k < kU; ++k)
-                    if (has[k]) blocked |= blocks4(wu[k], u[k], w, v);
-                // rows with more neighbours in a tile
-#pragma unroll
-                for (int k = 0; k < kSelTiles; ++k) {
-                    while (bits[k] && blocked != 0xFu) {
-                        const int uu = cb[k] * 16 + __ffs(bits[k]) - 1;
-                        bits[k] &= bits[k] - 1;
-                        blocked |= blocks4(*reinterpret_cast<const uint4*>(w8 + (size_t)kMaxMulti * uu),
-                                           uu, w, v);
-                    }
-                }
+                p0 += 4;
             }
             const unsigned cand = und & ~blocked;
             if (cand) {
