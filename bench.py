@@ -651,8 +651,9 @@ def tc_leg(args, native, local, world, workload="grid"):
     """The tile paths on a graph with dense 16 x 16 tiles (the grid with
     natural ids, 13 arcs per tile; the 27-point stencil, 16): one solve per
     path and tile payload, and 8 seeds per launch on the CSR rows (CUDA
-    cores) against the tiles with the exclusion product A x [C_1 .. C_8] on
-    tensor cores, per payload form."""
+    cores) against the forms with the exclusion product A x [C_1 .. C_8] on
+    tensor cores: the selection on the CSR rows with the product over the
+    bitmask tiles (rows_tc_b1), and the tile kernel per payload form."""
     import torch
     (n, rp, col), desc = make_workload(workload)
     stream = torch.cuda.current_stream().cuda_stream
@@ -686,15 +687,28 @@ def tc_leg(args, native, local, world, workload="grid"):
     res["single_ms"]["csr"] = timeit(one)
     res["multi8_ms"]["csr"] = timeit(eight)
     ref8 = out.clone()
+    exclude_us = {}
+    select_us = {}
+
+    def phases(nm):
+        st = native.mis_get_stats(h)
+        exclude_us[nm] = [round(st.exclude_ns[r] / 1e3, 1) for r in range(min(st.rounds, 64))]
+        select_us[nm] = [round(st.select_ns[r] / 1e3, 1) for r in range(min(st.rounds, 64))]
+
+    phases("csr")
+    # selection on the CSR rows, exclusion as the single-bit MMA over the tiles
+    native.mis_set_multi_form(h, native.MIS_MULTI_ROWS_TC)
+    res["multi8_ms"]["rows_tc_b1"] = timeit(eight)
+    phases("rows_tc_b1")
+    same_rows_tc = bool(torch.equal(out, ref8))
+    native.mis_set_multi_form(h, native.MIS_MULTI_ROWS)
     for T in (8, 16):
         native.mis_set_path(h, native.MIS_PATH_TILE, T)
         res["single_ms"][f"tile{T}_popc"] = timeit(one)
     res["tiles16"] = native.mis_get_stats(h).ntiles
     names = {native.MIS_TILE_BITS: "bits_fp16", native.MIS_TILE_BITS_B1: "b1",
              native.MIS_TILE_INT8: "int8", native.MIS_TILE_FP16: "fp16"}
-    same = True
-    exclude_us = {}
-    select_us = {}
+    same = same_rows_tc
     for p, nm in names.items():
         native.mis_set_tile_payload(h, p)
         native.mis_set_path(h, native.MIS_PATH_TILE_TC, 16)

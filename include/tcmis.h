@@ -73,11 +73,15 @@ enum {
     MIS_PATH_PUSH = 4,     /* CSR, work-efficient push/decrement rounds: a count of
                               undecided higher neighbours per vertex, decremented
                               as they are excluded; every arc read O(1) times */
-    MIS_PATH_CLUSTER = 5   /* single graphs of up to about half a million vertices:
+    MIS_PATH_CLUSTER = 5,  /* single graphs of up to about half a million vertices:
                               one thread-block cluster (up to 16 SMs) keeps every
                               vertex word in its distributed shared memory and
                               separates the phases by the hardware cluster
                               barrier instead of a grid barrier */
+    MIS_PATH_ROWS_TC = 6   /* reported by mis_get_stats only (not a value for
+                              mis_set_path): multi-seed solves with the
+                              selection test on the CSR rows and the exclusion
+                              test on tensor cores (mis_set_multi_form) */
 };
 
 typedef struct mis_graph mis_graph;
@@ -242,6 +246,31 @@ int mis_solve_ex(mis_graph *g, const uint64_t *seeds, uint8_t *out_status, void 
  */
 int mis_solve_multi_ex(mis_graph *g, int32_t k, const uint64_t *seeds, uint8_t *out_status,
                        void *stream);
+
+/*
+ * The form of mis_solve_multi_ex on a graph whose path is not
+ * MIS_PATH_TILE_TC (Sec. 3.1 Phase 2 as the product A x [C_1 .. C_k]):
+ *   MIS_MULTI_ROWS     both tests on the CSR rows on CUDA cores (default)
+ *   MIS_MULTI_ROWS_TC  the selection test on the CSR rows (per-vertex
+ *                      worklists), the exclusion test over the graph's 16 x 16
+ *                      bitmask tiles (Sec. 3.2) on the single-bit tensor-core
+ *                      MMA (AND, then population count, int32 accumulation:
+ *                      exact), the k solves as k of its eight columns.  The
+ *                      16 x 16 tile-CSR is built on the first such solve and
+ *                      kept by the handle (mis_footprint counts it); a graph
+ *                      whose single solves run on 8 x 8 tiles (MIS_PATH_TILE,
+ *                      tile size 8) is refused at solve time (MIS_EINVAL).
+ *                      mis_get_stats reports MIS_PATH_ROWS_TC.
+ * Both forms give every solve the set and rounds of its single solve.
+ * MIS_MULTI_ROWS_TC takes a single graph created without round-0 structures
+ * (mis_options.order_rows = 0): MIS_EINVAL otherwise, and for unknown forms;
+ * MIS_EBUSY while served requests on `g` are in flight.
+ */
+enum {
+    MIS_MULTI_ROWS = 0,
+    MIS_MULTI_ROWS_TC = 1
+};
+int mis_set_multi_form(mis_graph *g, int32_t form);
 
 /*
  * Captured solves (no counterpart in the paper: launch-overhead removal for

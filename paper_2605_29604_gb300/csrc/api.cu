@@ -486,6 +486,7 @@ SolveArgs make_args(mis_graph* g, Workspace& w) {
     a.n_sure_out = d.n_sure_out;
     a.pending = g->csr_pending;
     a.range0_max = (g->csr_range0 && !d.r0class && d.thr[0] >= 1) ? d.thr[0] : 0;
+    for (int j = 0; j < 4; ++j) a.thr[j] = d.thr[j];
     a.priority = g->opt.priority;
     a.ctl = w.ctl;
     a.times = w.times;
@@ -1383,6 +1384,21 @@ int mis_set_tile_payload(mis_graph* g, int32_t payload) {
     return MIS_OK;
 }
 
+int mis_set_multi_form(mis_graph* g, int32_t form) {
+    clear_error();
+    if (!g) return set_error(MIS_EINVAL, "null graph");
+    if (form != MIS_MULTI_ROWS && form != MIS_MULTI_ROWS_TC)
+        return set_error(MIS_EINVAL, "unknown multi-seed form");
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
+    if (form == MIS_MULTI_ROWS_TC && (g->d.count != 0 || g->d.r0class || g->d.out0 || g->d.s0_col))
+        return set_error(MIS_EINVAL,
+                         "the tensor-core multi-seed form takes a single graph created "
+                         "without round-0 structures (order_rows = 0)");
+    g->multi_form = form;
+    return MIS_OK;
+}
+
 int mis_set_csr_range0(mis_graph* g, int32_t on) {
     clear_error();
     if (!g) return set_error(MIS_EINVAL, "null graph");
@@ -1592,6 +1608,49 @@ int mis_solve_multi_ex(mis_graph* g, int32_t k, const uint64_t* seeds, uint8_t* 
         }
         g->last_stream = s;
         g->last_path = MIS_PATH_TILE_TC;
+        return MIS_OK;
+    }
+    if (g->multi_form == MIS_MULTI_ROWS_TC) {
+        // selection on the CSR rows, exclusion on the 16 x 16 bitmask tiles
+        // with the solves as the single-bit MMA's right-hand sides
+        if (g->path == MIS_PATH_TILE && d.tiles.T != 16)
+            return set_error(MIS_EINVAL, "the graph's single solves use 8 x 8 tiles; "
+                                         "set another path before this multi-seed form");
+        if (d.tiles.T != 16) {
+            if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+            free_tiles(d);
+            e = build_tiles(d.rp, d.col, d.n, d.arcs, 16, &d.tiles, g->own_stream);
+            if (e != cudaSuccess) {
+                free_tiles(d);
+                return set_cuda_error(e, "tile-CSR conversion");
+            }
+            d.tile_footprint = 4 * ((int64_t)d.tiles.nrb + 1) + 4 * d.tiles.ntiles +
+                               32 * (int64_t)d.tiles.ntiles;
+            d.footprint += d.tile_footprint;
+        }
+        const int32_t words = tile_multi_bitvector_words(d.tiles.nrb);  // 8 * words >= 4 * nrb
+        if (!d.inb8) {
+            if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+            if ((e = dalloc(&d.inb8, (int64_t)kMaxMulti * words, &d.footprint)) != cudaSuccess)
+                return set_cuda_error(e, "multi-seed workspace");
+        }
+        MultiSeeds ms{};
+        for (int i = 0; i < k; ++i) ms.seed[i] = seeds[i];
+        SolveArgs a = make_args(g, d.ws);
+        a.out = out_status;
+        cudaStream_t s = (cudaStream_t)stream;
+        e = reset_control(d.ws, s);
+        if (e != cudaSuccess) return set_cuda_error(e, "control reset");
+        if (d.n > 0) {
+            const int maxb = multi_rows_tc_max_coresident_blocks(d.device);
+            if (maxb <= 0) return set_error(MIS_EDEVICE, "no co-resident blocks for the kernel");
+            const long long want = std::max<long long>(1, ((long long)d.n + 255) / 256);
+            e = launch_multi_rows_tc_solve(a, d.word8, d.inb8, k, ms,
+                                           (int)std::min<long long>(want, maxb), s);
+            if (e != cudaSuccess) return set_cuda_error(e, "multi-seed rows-tc kernel launch");
+        }
+        g->last_stream = s;
+        g->last_path = MIS_PATH_ROWS_TC;
         return MIS_OK;
     }
     const int rc = solve_multi_in(g, d.ws, d.word8, k, seeds, out_status, (cudaStream_t)stream, 0);

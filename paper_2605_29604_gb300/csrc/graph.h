@@ -120,6 +120,7 @@ struct mis_graph {
     int32_t tile_payload = 0;     // tensor-core tile path: payload form (MIS_TILE_*)
     tcmis::ClusterPlan cluster;   // cluster path: its launch shape
     int32_t csr_range0 = 1;       // CSR kernel: round 0 tests bin 0 by vertex ranges
+    int32_t multi_form = 0;       // multi-seed solves off the tile path (MIS_MULTI_*)
                                   // (graphs without round-0 classes only)
     cudaStream_t own_stream = nullptr;
     cudaStream_t last_stream = nullptr;

@@ -80,6 +80,7 @@ struct SolveArgs {
     // > 0: round 0 tests bin 0 (degree 1 .. range0_max) by vertex ranges over
     // row_ptr instead of its order0 list (graphs without round-0 classes)
     int32_t range0_max = 0;
+    int32_t thr[4] = {0, 0, 0, 0};    // the degree bins' upper bounds (bins 0..3)
     int32_t pending = 0;              // 1: Phase 1 lists its non-candidates for Phase 2
                                       // (in wlp); 0: Phase 2 triages W_r itself
     // tile-CSR (used by the tile kernels only)
@@ -172,6 +173,14 @@ cudaError_t build_round0_classes(const int32_t* rp, const int32_t* col_sel, cons
 cudaError_t launch_multi_solve(const SolveArgs& a, uint32_t* word8, int k,
                                const MultiSeeds& seeds, int grid, cudaStream_t s);
 int multi_max_coresident_blocks(int device);
+// The same with Phase 2 on tensor cores (kernels_multi.cu, multi_rows_tc_kernel):
+// the selection test on the CSR rows of `a` (a graph without create-time
+// round-0 structures), the exclusion test as the single-bit MMA over its
+// 16 x 16 bitmask tiles (a.trp, a.tcol, a.tbits; a.rbl0/1 row-block lists,
+// a.nrb).  inb4: 4 * a.nrb words of in-set bits, 16-byte aligned.
+cudaError_t launch_multi_rows_tc_solve(const SolveArgs& a, uint32_t* word8, uint32_t* inb4, int k,
+                                      const MultiSeeds& seeds, int grid, cudaStream_t s);
+int multi_rows_tc_max_coresident_blocks(int device);
 
 // kernels_push.cu: the push/decrement form of the rounds (uses the worklist
 // buffers of `a` for its ready and excluded lists and per-vertex counts).

@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tile_tc.cuh"
 #include "worklist.cuh"
 
 namespace tcmis {
@@ -114,7 +115,8 @@ struct MultiCtx {
     const SolveArgs& a;
     uint32_t* word8;
     int32_t* wbuf;
-    int k;  // solves in the launch
+    int k;                     // solves in the launch
+    uint32_t* inb4 = nullptr;  // in-set bits of the tensor-core form (see select_bin8)
 };
 
 // Candidates marked in the results by this block (with the keyed vertices).
@@ -123,7 +125,9 @@ __shared__ unsigned s_msel;
 // Phase 1 over one bin at TPR lanes per row: for every row, the selection
 // test in each solve that has the row undecided; candidates are marked in.
 // Counts the undecided (vertex, solve) pairs into *alive.
-template <int TPR>
+// kRowsTc (the kernel with the exclusion on tensor cores, below): each
+// candidate also sets its bits in the in-set bits `x.inb4`.
+template <int TPR, bool kRowsTc = false>
 __device__ __forceinline__ void select_bin8(const MultiCtx& x, const int4* __restrict__ list,
                                             int cnt, WarpSched& ws, unsigned long long* alive,
                                             bool late) {
@@ -167,6 +171,17 @@ __device__ __forceinline__ void select_bin8(const MultiCtx& x, const int4* __res
                             for (int s = 0; s < x.k; ++s)
                                 if ((cand >> s) & 1u) x.a.out[(long long)s * x.a.n + rec.x] = 1;
                         atomicAdd(&s_msel, (unsigned)__popc(cand));
+                    }
+                    if constexpr (kRowsTc) {
+                        // solve s's bit of v: word 4 (v / 16) + s / 2, bit v % 16 + 16 (s & 1)
+                        const int sh = rec.x & 15;
+                        uint32_t* wb = x.inb4 + 4LL * (rec.x >> 4);
+#pragma unroll
+                        for (int j = 0; j < kMaxMulti / 2; ++j) {
+                            const uint32_t bits = (((cand >> (2 * j)) & 1u) << sh) |
+                                                  (((cand >> (2 * j + 1)) & 1u) << (sh + 16));
+                            if (bits) atomicOr(wb + j, bits);
+                        }
                     }
                 }
             }
@@ -233,14 +248,14 @@ __device__ __forceinline__ int multi_lanes(int cnt, bool late, int nwarps) {
     return BASE;
 }
 
-template <int BASE>
+template <int BASE, bool kRowsTc = false>
 __device__ __forceinline__ void select_at8(const MultiCtx& x, const int4* list, int cnt, bool late,
                                            WarpSched& ws, unsigned long long* alive) {
     switch (multi_lanes<BASE>(cnt, late, ws.nwarps)) {
-        case 32: select_bin8<32>(x, list, cnt, ws, alive, late); break;
-        case 16: select_bin8<16>(x, list, cnt, ws, alive, late); break;
-        case 4: select_bin8<4>(x, list, cnt, ws, alive, late); break;
-        default: select_bin8<BASE>(x, list, cnt, ws, alive, late);
+        case 32: select_bin8<32, kRowsTc>(x, list, cnt, ws, alive, late); break;
+        case 16: select_bin8<16, kRowsTc>(x, list, cnt, ws, alive, late); break;
+        case 4: select_bin8<4, kRowsTc>(x, list, cnt, ws, alive, late); break;
+        default: select_bin8<BASE, kRowsTc>(x, list, cnt, ws, alive, late);
     }
 }
 
@@ -445,6 +460,355 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
     }
 }
 
+// ---------------------------------------------------------------- rows + tensor cores
+//
+// The same k solves with Phase 2 as the product N_c = A x [C_1 .. C_k] over
+// the graph's 16 x 16 bitmask tiles on the single-bit MMA (Sec. 3.1 Phase 2,
+// Sec. 3.2), and Phase 1 as above on the CSR rows with per-vertex worklists.
+// (On tiles alone, Phase 1 keeps a row block on its list while any of its
+// 16 x k entries is undecided and scans no faster than the rows; the product
+// is where the tiles pay.)  Per round:
+//
+//   Phase 1  selection test over the vertex lists (select_bin8<kRowsTc>):
+//            candidates are marked in their words and set their bits in the
+//            in-set bits inb4 (4 words per row block: solve s's 16 bits of
+//            row block b at word 4 b + s / 2, bits 16 (s & 1) ..).
+//   Phase 2  exclusion test over the row-block list: D = A x C with C the
+//            in-set bits of every round so far.  That equals this round's
+//            product on the entries it decides: a vertex undecided at a
+//            round's start has no neighbour in the set (it would have been
+//            excluded), so its in-set neighbours are this round's candidates.
+//            Undecided entries with D > 0 are out.  A row block stays on the
+//            row-block list while it keeps an undecided entry, and each row
+//            that keeps one goes on the next vertex list, in its degree bin,
+//            with its record rebuilt from row_ptr (a graph without
+//            create-time structures has no selection prefixes).
+//
+// A warp takes row blocks gw, gw + W, ... of the list and keeps the next
+// one's tiles, words and row offsets in flight while it multiplies the
+// current one.  The loop ends when the row-block list is empty, i.e. every
+// entry of every solve is decided, so the round count is Algorithm 2's.
+// Graphs with create-time round-0 structures do not take this kernel (the
+// host checks).
+
+constexpr int kRbKeep = 64;   // row blocks staged per warp before an append
+constexpr int kSvMax = 48;    // survivors staged per warp and bin before an append
+// shared words per warp: 32 gathered tiles (12 words each), the staged row
+// blocks, the staged survivors of each bin
+constexpr int kRtWords = 384 + kRbKeep + kBins * kSvMax;
+
+__device__ __forceinline__ uint2 ld_pair8(const uint32_t* word8, int v, int q) {
+    return *reinterpret_cast<const uint2*>(word8 + (size_t)kMaxMulti * v + 2 * q);
+}
+
+__device__ __forceinline__ void st_pair8(uint32_t* word8, int v, int q, uint2 w) {
+    *reinterpret_cast<uint2*>(word8 + (size_t)kMaxMulti * v + 2 * q) = w;
+}
+
+// What lane l of a warp holds of a row block before its product: the row
+// block's tile range and tile t0 + l of its first pass (bits and column block).
+struct RbLane {
+    int rb, t0, t1;
+    uint4 lo, hi;
+    int cb;  // -1: no tile
+};
+
+__device__ __forceinline__ void rb_issue(const SolveArgs& a, int rb, int t0, int t1, RbLane& L) {
+    const int t = t0 + (int)lane_id();
+    L.rb = rb;
+    L.t0 = t0;
+    L.t1 = t1;
+    L.cb = -1;
+    L.lo = make_uint4(0u, 0u, 0u, 0u);
+    L.hi = L.lo;
+    if (t < t1) {
+        L.cb = __ldg(a.tcol + t);
+        const uint4* bp = reinterpret_cast<const uint4*>(a.tbits + 4LL * t);
+        L.lo = __ldg(bp);
+        L.hi = __ldg(bp + 1);
+    }
+}
+
+// Appends a warp's staged survivors of bin j (vertex ids) to the bin's list
+// as row records {v, row begin, row end, row end}.
+__device__ __forceinline__ void flush_survivors(const SolveArgs& a, const int32_t* sv, int cnt,
+                                                int* next, int4* __restrict__ dst) {
+    __syncwarp();
+    const unsigned lane = lane_id();
+    int o = 0;
+    if (lane == 0) o = atomicAdd(next, cnt);
+    o = __shfl_sync(0xFFFFFFFFu, o, 0);
+    for (int i = (int)lane; i < cnt; i += 32) {
+        const int v = sv[i];
+        const int b = __ldg(a.rp + v), e = __ldg(a.rp + v + 1);
+        dst[o + i] = make_int4(v, b, e, e);
+    }
+    __syncwarp();
+}
+
+// Phases 2 and 3 over the row-block list `list` (cnt entries).  Lane (g, q)
+// owns rows g and g + 8 in solves 2q and 2q + 1 (the MMA's D fragment).
+// `sw`: the warp's kRtWords words of shared memory.  next_rb / dst_rb: the
+// next row-block list; next_v / dst_v: the next vertex lists, per bin.
+__device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* word8,
+                                                const uint32_t* inb4,
+                                                const int32_t* __restrict__ list, int cnt,
+                                                int* next_rb, int32_t* __restrict__ dst_rb,
+                                                int* next_v, int4* __restrict__ dst_v,
+                                                uint32_t* sw) {
+    const unsigned lane = lane_id();
+    const int g = (int)(lane >> 2), q = (int)(lane & 3);
+    const long long nw = (long long)gridDim.x * (blockDim.x / 32);
+    const long long gw = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (gw >= cnt) return;
+    int32_t* keep = reinterpret_cast<int32_t*>(sw + 384);
+    int32_t* sv = keep + kRbKeep;  // kBins x kSvMax
+    int nkeep = 0;
+    uint32_t nsv = 0;  // survivors staged per bin, 6 bits each (at most kSvMax)
+    const int32_t* off = a.bin_off;
+    // the in-set bits were written in Phase 1 of this launch: read through L2
+    auto cseg4 = [inb4](int cb) -> uint4 {
+        return cb >= 0 ? __ldcg(reinterpret_cast<const uint4*>(inb4 + 4LL * cb))
+                       : make_uint4(0u, 0u, 0u, 0u);
+    };
+    RbLane cur;
+    {
+        const int rb = list[gw];
+        rb_issue(a, rb, a.trp[rb], a.trp[rb + 1], cur);
+    }
+    uint4 c = cseg4(cur.cb);
+    int rb_n = -1, t0_n = 0, t1_n = 0;  // the row block after the current one
+    if (gw + nw < cnt) {
+        rb_n = list[gw + nw];
+        t0_n = a.trp[rb_n];
+        t1_n = a.trp[rb_n + 1];
+    }
+    for (long long item = gw; item < cnt; item += nw) {
+        // the next row block's loads go out before this one's product
+        RbLane nxt;
+        nxt.cb = -1;
+        if (rb_n >= 0) rb_issue(a, rb_n, t0_n, t1_n, nxt);
+        // this row block's words and row offsets (row_ptr[16 rb + l], l <= 16)
+        const int rb = cur.rb;
+        const int v0 = rb * 16 + g, v1 = v0 + 8;
+        uint2 w0 = ld_pair8(word8, v0, q), w1 = ld_pair8(word8, v1, q);
+        const int rpv = __ldg(a.rp + min(rb * 16 + (int)min(lane, 16u), a.n));
+        int rb_nn = -1, t0_nn = 0, t1_nn = 0;
+        if (item + 2 * nw < cnt) {
+            rb_nn = list[item + 2 * nw];
+            t0_nn = a.trp[rb_nn];
+            t1_nn = a.trp[rb_nn + 1];
+        }
+        int acc[4] = {0, 0, 0, 0};
+        b1_pass(cur.lo, cur.hi, c, sw, acc);
+        for (int tb = cur.t0 + 32; tb < cur.t1; tb += 32) {  // row blocks of > 32 tiles
+            const int t = tb + (int)lane;
+            uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo, cc = lo;
+            if (t < cur.t1) {
+                const uint4* bp = reinterpret_cast<const uint4*>(a.tbits + 4LL * t);
+                lo = __ldg(bp);
+                hi = __ldg(bp + 1);
+                cc = cseg4(__ldg(a.tcol + t));
+            }
+            b1_pass(lo, hi, cc, sw, acc);
+        }
+        // the next row block's C segments go out before this one's update
+        const uint4 c_n = cseg4(nxt.cb);
+
+        // ---- update: undecided entries (the non-candidates) with D > 0 are out
+        const unsigned und = ((w0.x >> 29) == 1u ? 1u : 0u) | ((w0.y >> 29) == 1u ? 2u : 0u) |
+                             ((w1.x >> 29) == 1u ? 4u : 0u) | ((w1.y >> 29) == 1u ? 8u : 0u);
+        const unsigned out = und & ((acc[0] > 0 ? 1u : 0u) | (acc[1] > 0 ? 2u : 0u) |
+                                    (acc[2] > 0 ? 4u : 0u) | (acc[3] > 0 ? 8u : 0u));
+        if (out & 3u) {
+            if (out & 1u) w0.x = kWordOut;
+            if (out & 2u) w0.y = kWordOut;
+            st_pair8(word8, v0, q, w0);
+        }
+        if (out & 12u) {
+            if (out & 4u) w1.x = kWordOut;
+            if (out & 8u) w1.y = kWordOut;
+            st_pair8(word8, v1, q, w1);
+        }
+        const unsigned rem = und & ~out;
+        if (__any_sync(0xFFFFFFFFu, rem != 0u)) {
+            if (lane == 0) keep[nkeep] = rb;
+            ++nkeep;
+            if (nkeep == kRbKeep) {
+                __syncwarp();
+                int o = 0;
+                if (lane == 0) o = atomicAdd(next_rb, nkeep);
+                o = __shfl_sync(0xFFFFFFFFu, o, 0);
+                for (int k = (int)lane; k < nkeep; k += 32) dst_rb[o + k] = keep[k];
+                __syncwarp();
+                nkeep = 0;
+            }
+            // rows with an undecided entry in some solve: onto the next vertex list
+            unsigned r0 = (rem & 3u) != 0u ? 1u : 0u, r1 = (rem & 12u) != 0u ? 1u : 0u;
+            r0 |= __shfl_xor_sync(0xFFFFFFFFu, r0, 1);
+            r0 |= __shfl_xor_sync(0xFFFFFFFFu, r0, 2);
+            r1 |= __shfl_xor_sync(0xFFFFFFFFu, r1, 1);
+            r1 |= __shfl_xor_sync(0xFFFFFFFFu, r1, 2);
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int i = g + 8 * half;  // row of the block
+                const int b = __shfl_sync(0xFFFFFFFFu, rpv, i);
+                const int e = __shfl_sync(0xFFFFFFFFu, rpv, i + 1);
+                const bool kp = q == 0 && (half ? r1 : r0) != 0u;
+                int j = -1;
+                if (kp) {
+                    const int deg = e - b;
+                    j = 0;
+#pragma unroll
+                    for (int t = 0; t < kBins - 1; ++t) j += deg > a.thr[t];
+                }
+#pragma unroll
+                for (int bj = 0; bj < kBins; ++bj) {
+                    const unsigned m = __ballot_sync(0xFFFFFFFFu, j == bj);
+                    if (m == 0u) continue;
+                    const int have = (int)((nsv >> (6 * bj)) & 63u);
+                    if (j == bj) sv[bj * kSvMax + have + __popc(m & lanemask_lt())] = rb * 16 + i;
+                    const int now = have + __popc(m);
+                    nsv = (nsv & ~(63u << (6 * bj))) | ((uint32_t)now << (6 * bj));
+                    if (now > kSvMax - 16) {
+                        flush_survivors(a, sv + bj * kSvMax, now, &next_v[bj], dst_v + off[bj]);
+                        nsv &= ~(63u << (6 * bj));
+                    }
+                }
+            }
+        }
+        cur = nxt;
+        c = c_n;
+        rb_n = rb_nn;
+        t0_n = t0_nn;
+        t1_n = t1_nn;
+    }
+    if (nkeep) {
+        __syncwarp();
+        int o = 0;
+        if (lane == 0) o = atomicAdd(next_rb, nkeep);
+        o = __shfl_sync(0xFFFFFFFFu, o, 0);
+        for (int k = (int)lane; k < nkeep; k += 32) dst_rb[o + k] = keep[k];
+        __syncwarp();
+    }
+#pragma unroll
+    for (int bj = 0; bj < kBins; ++bj) {
+        const int have = (int)((nsv >> (6 * bj)) & 63u);
+        if (have) flush_survivors(a, sv + bj * kSvMax, have, &next_v[bj], dst_v + off[bj]);
+    }
+}
+
+__global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
+    multi_rows_tc_kernel(const SolveArgs a, uint32_t* word8, uint32_t* inb4, int k,
+                         const MultiSeeds seeds) {
+    // 16-byte aligned: rows_tc_exclude packs uint4 tiles into it
+    __shared__ __align__(16) uint32_t s_rt[kMultiWarps][kRtWords];
+    __shared__ int s_cnt[kBins];
+    __shared__ int s_rbcnt;
+    const unsigned nblocks = gridDim.x;
+    Ctl* ctl = a.ctl;
+    PhaseTimes* times = a.times;
+    MultiCtx x{a, word8, nullptr, k};  // Phase 1 stages nothing here
+    x.inb4 = inb4;
+    grid_barrier_start();
+    if (threadIdx.x < kBins) s_cnt[threadIdx.x] = a.bin_off[threadIdx.x + 1] - a.bin_off[threadIdx.x];
+    if (threadIdx.x == 0) s_rbcnt = a.nrb;
+    if (times && blockIdx.x == 0 && threadIdx.x == 0) times->t[0] = global_ns();
+
+    // ---- init: Eq. 1 priorities of every solve, no vertex in the set, every
+    // row block on the list
+    {
+        uint64_t smix[kMaxMulti];
+#pragma unroll
+        for (int s = 0; s < kMaxMulti; ++s) smix[s] = mix64(seeds.seed[s]);
+        init_words8(a, word8, k, smix);
+        const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        const long long nthreads = (long long)nblocks * blockDim.x;
+        for (long long i = tid; i < (long long)a.nrb; i += nthreads) {
+            reinterpret_cast<uint4*>(inb4)[i] = make_uint4(0u, 0u, 0u, 0u);
+            a.rbl0[i] = (int32_t)i;
+        }
+    }
+    if (!grid_barrier(ctl, nblocks, a.spin_cap, [times]() {
+            if (times) times->t[1] = global_ns();
+        }))
+        return;
+
+    const int decided0 = a.n_isolated;
+    WarpSched ws;
+    ws.gw = (int)(blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32);
+    ws.nwarps = (int)(nblocks * (blockDim.x / 32));
+    ws.base = 0;
+    const int* off = a.bin_off;
+    for (int r = 0; s_rbcnt > 0; ++r) {
+        if (r >= a.max_rounds) {
+            if (threadIdx.x == 0) atomicCAS(&ctl->err, 0, kErrInternal);
+            return;
+        }
+        const int4* src = (r == 0) ? a.order0 : ((r & 1) ? a.wl1 : a.wl0);
+        int4* dst = ((r + 1) & 1) ? a.wl1 : a.wl0;
+        int* next = ctl->bcnt[(r + 1) & 3];
+        unsigned long long* acc = &ctl->alive_acc64[r & 3];
+        const int rr = r;
+        const bool late = r > 0;
+
+        // ---- Phase 1: selection test of every solve on the CSR rows
+        select_at8<32, true>(x, src + off[4], s_cnt[4], late, ws, acc);
+        select_at8<32, true>(x, src + off[3], s_cnt[3], late, ws, acc);
+        select_at8<16, true>(x, src + off[2], s_cnt[2], late, ws, acc);
+        select_at8<4, true>(x, src + off[1], s_cnt[1], late, ws, acc);
+        select_at8<1, true>(x, src + off[0], s_cnt[0], late, ws, acc);
+        if (!grid_barrier(ctl, nblocks, a.spin_cap, [times, rr]() {
+                if (times && rr < kStatRounds) times->t[2 + rr] = global_ns();
+            }))
+            return;
+
+        // ---- Phases 2 and 3: exclusion test on tensor cores, update, compaction
+        rows_tc_exclude(a, word8, inb4, (r & 1) ? a.rbl1 : a.rbl0, s_rbcnt,
+                        &ctl->cnt[(r + 1) & 3], (r & 1) ? a.rbl0 : a.rbl1, next, dst,
+                        s_rt[threadIdx.x / 32]);
+        const long long extra = r == 0 ? (long long)k * decided0 : 0;
+        if (!grid_barrier(
+                ctl, nblocks, a.spin_cap,
+                [ctl, times, rr, extra]() {
+                    const unsigned long long cur = ctl->alive_acc64[rr & 3] + (unsigned long long)extra;
+                    ctl->alive_acc64[(rr + 2) & 3] = 0;
+                    if (times && rr < kStatRounds) times->t[2 + kStatRounds + rr] = global_ns();
+                    if (rr < kStatRounds) ctl->alive[rr] = (int)cur;
+                    ctl->alive_sum += cur;
+                    ctl->rounds = rr + 1;
+                    for (int j = 0; j < kBins; ++j) ctl->bcnt[(rr + 2) & 3][j] = 0;
+                    ctl->cnt[(rr + 2) & 3] = 0;
+                },
+                [ctl, next, rr]() {
+                    for (int j = 0; j < kBins; ++j) s_cnt[j] = __ldcg(next + j);
+                    s_rbcnt = __ldcg(&ctl->cnt[(rr + 1) & 3]);
+                }))
+            return;
+    }
+
+    // ---- output: out[s * n + v] = [v in the MIS of solve s]
+    if (a.out) {
+        const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        const long long nthreads = (long long)nblocks * blockDim.x;
+        unsigned in_cnt = 0;
+        for (long long v = tid; v < a.n; v += nthreads) {
+            uint32_t w[kMaxMulti];
+            load8(word8, (int)v, w);
+#pragma unroll
+            for (int s = 0; s < kMaxMulti; ++s) {
+                if (s < k) {
+                    const bool in = w[s] >= kWordInMin;
+                    a.out[(long long)s * a.n + v] = in;
+                    in_cnt += in;
+                }
+            }
+        }
+        for (int o = 16; o; o >>= 1) in_cnt += __shfl_xor_sync(0xFFFFFFFFu, in_cnt, o);
+        if (lane_id() == 0 && in_cnt) atomicAdd(&ctl->mis_size, (unsigned long long)in_cnt);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_multi_solve(const SolveArgs& a, uint32_t* word8, int k,
@@ -452,6 +816,24 @@ cudaError_t launch_multi_solve(const SolveArgs& a, uint32_t* word8, int k,
     void* args[] = {const_cast<SolveArgs*>(&a), &word8, &k, const_cast<MultiSeeds*>(&seeds)};
     return cudaLaunchCooperativeKernel((const void*)multi_solve_kernel, dim3(grid),
                                        dim3(kMultiBlock), args, 0, s);
+}
+
+cudaError_t launch_multi_rows_tc_solve(const SolveArgs& a, uint32_t* word8, uint32_t* inb4, int k,
+                                      const MultiSeeds& seeds, int grid, cudaStream_t s) {
+    void* args[] = {const_cast<SolveArgs*>(&a), &word8, &inb4, &k,
+                    const_cast<MultiSeeds*>(&seeds)};
+    return cudaLaunchCooperativeKernel((const void*)multi_rows_tc_kernel, dim3(grid),
+                                       dim3(kMultiBlock), args, 0, s);
+}
+
+int multi_rows_tc_max_coresident_blocks(int device) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)multi_rows_tc_kernel,
+                                                      kMultiBlock, 0) != cudaSuccess)
+        return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return 0;
+    return per_sm * sms;
 }
 
 int multi_max_coresident_blocks(int device) {

@@ -36,6 +36,9 @@ MIS_PATH_TILE = 2
 MIS_PATH_TILE_TC = 3
 MIS_PATH_PUSH = 4
 MIS_PATH_CLUSTER = 5
+MIS_PATH_ROWS_TC = 6  # reported by mis_get_stats for the tensor-core multi-seed form
+MIS_MULTI_ROWS = 0
+MIS_MULTI_ROWS_TC = 1
 MIS_PRIORITY_EQ1 = 0
 MIS_PRIORITY_HASH = 1
 MIS_PRIORITY_EQ1_Q8 = 2
@@ -146,6 +149,8 @@ def lib():
         L.mis_tile_payload_ex.restype = ctypes.c_int
         L.mis_set_tile_payload.argtypes = [P, i32]
         L.mis_set_tile_payload.restype = ctypes.c_int
+        L.mis_set_multi_form.argtypes = [P, i32]
+        L.mis_set_multi_form.restype = ctypes.c_int
         L.mis_set_csr_range0.argtypes = [P, i32]
         L.mis_set_csr_range0.restype = ctypes.c_int
         L.mis_destroy.argtypes = [P]
@@ -185,7 +190,7 @@ def lib():
 EXPORTED = [
     "mis_options_init", "mis_create", "mis_create_ex", "mis_create_batch", "mis_graph_count",
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
-    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_set_csr_range0", "mis_set_tile_payload", "mis_tile_payload_ex", "mis_cluster_max_vertices", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
+    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_set_csr_range0", "mis_set_tile_payload", "mis_set_multi_form", "mis_tile_payload_ex", "mis_cluster_max_vertices", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
     "mis_solve_noalloc", "mis_update_edges", "mis_repair", "mis_add_vertices",
 ]
@@ -378,6 +383,10 @@ def mis_tile_payload_ex(h, payload, out_ptr, stream=None):
 
 def mis_set_tile_payload(h, payload):
     return _check(lib().mis_set_tile_payload(h, int(payload)))
+
+
+def mis_set_multi_form(h, form):
+    return _check(lib().mis_set_multi_form(h, int(form)))
 
 
 def mis_set_csr_range0(h, on):

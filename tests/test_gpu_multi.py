@@ -4,6 +4,7 @@ round statistics match the oracle's per-seed rounds."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2605_29604_gb300 import graphgen as gg
 from paper_2605_29604_gb300 import native
 
@@ -147,5 +148,83 @@ def test_multi_on_tiles_tensor_cores_bit_exact(name, payload, k):
         seeds2 = [s + 1 for s in seeds]
         got2, st2 = multi_solve(h, g[0], seeds2)
         check(g, seeds2, got2, st2)
+    finally:
+        native.mis_destroy(h)
+
+
+@pytest.mark.parametrize("name", sorted(FAMILIES))
+@pytest.mark.parametrize("k", [1, 6, 8])
+def test_multi_rows_tc_bit_exact(name, k):
+    """Selection test on the CSR rows, exclusion test as the single-bit MMA
+    over the 16 x 16 bitmask tiles (MIS_MULTI_ROWS_TC): every solve's set
+    equals the oracle's, and the summed rounds and alive sets match; a second
+    launch on the same handle (kept tiles, in-set bits and words) too."""
+    g = graph(name)
+    h = create(g, order_rows=0)
+    try:
+        native.mis_set_multi_form(h, native.MIS_MULTI_ROWS_TC)
+        seeds = [7 + 1009 * i for i in range(k)]
+        got, st = multi_solve(h, g[0], seeds)
+        assert st.path == native.MIS_PATH_ROWS_TC
+        check(g, seeds, got, st)
+        seeds2 = [s + 2 for s in seeds]
+        got2, st2 = multi_solve(h, g[0], seeds2)
+        check(g, seeds2, got2, st2)
+        # the CSR-row form on the same handle gives the same sets
+        native.mis_set_multi_form(h, native.MIS_MULTI_ROWS)
+        got3, st3 = multi_solve(h, g[0], seeds2)
+        assert st3.path == native.MIS_PATH_CSR
+        assert np.array_equal(got3, got2)
+    finally:
+        native.mis_destroy(h)
+
+
+@pytest.mark.parametrize("priority", [native.MIS_PRIORITY_HASH, native.MIS_PRIORITY_EQ1_Q8])
+def test_multi_rows_tc_priorities(priority):
+    """The tensor-core multi-seed form under the other priority heuristics
+    (H1 hash, Eq. 1 on 8 bits), where ties between neighbours are common."""
+    g = graph("grid")
+    h = create(g, order_rows=0, priority=priority)
+    try:
+        native.mis_set_multi_form(h, native.MIS_MULTI_ROWS_TC)
+        seeds = [11, 12, 13, 14, 15, 16, 17, 18]
+        got, st = multi_solve(h, g[0], seeds)
+        n, rp, col = g
+        for s, row in zip(seeds, got):
+            want = oracle.solve(n, rp, col, s, priority)
+            assert np.array_equal(row, want.status), f"seed {s}"
+    finally:
+        native.mis_destroy(h)
+
+
+def test_multi_rows_tc_refusals():
+    """The form needs a single graph without create-time round-0 structures;
+    a graph on 8 x 8 tiles is refused at solve time."""
+    import torch
+    g = graph("grid")
+    h = create(g, order_rows=1)
+    try:
+        with pytest.raises(native.MisError):
+            native.mis_set_multi_form(h, native.MIS_MULTI_ROWS_TC)
+        with pytest.raises(native.MisError):
+            native.mis_set_multi_form(h, 5)
+    finally:
+        native.mis_destroy(h)
+    hb = native.mis_create_batch([gg.path(10), gg.path(20)])
+    try:
+        with pytest.raises(native.MisError):
+            native.mis_set_multi_form(hb, native.MIS_MULTI_ROWS_TC)
+    finally:
+        native.mis_destroy(hb)
+    h = create(g, order_rows=0)
+    out = torch.empty(2 * g[0], dtype=torch.uint8, device="cuda")
+    try:
+        native.mis_set_multi_form(h, native.MIS_MULTI_ROWS_TC)
+        native.mis_set_path(h, native.MIS_PATH_TILE, 8)
+        with pytest.raises(native.MisError):
+            native.mis_solve_multi_ex(h, np.asarray([1, 2], dtype=np.uint64), out.data_ptr())
+        native.mis_set_path(h, native.MIS_PATH_CSR, 0)
+        got, st = multi_solve(h, g[0], [1, 2])
+        check(g, [1, 2], got, st)
     finally:
         native.mis_destroy(h)
