@@ -49,7 +49,7 @@ if ROOT not in sys.path:
 METRIC = "edges/s to full MIS on 1 GB300"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-PATH_NAMES = {1: "csr", 2: "tile", 3: "tile_tc", 4: "push", 5: "cluster"}
+PATH_NAMES = {1: "csr", 2: "tile", 3: "tile_tc", 4: "push", 5: "cluster", 6: "rows_tc"}
 PAYLOADS = {"bits": 0, "b1": 1, "int8": 2, "fp16": 3}  # mis_set_tile_payload forms
 
 
@@ -385,8 +385,11 @@ def run_single(args):
     full_result = out[:n].cpu().numpy()
     # with a pinned tile path: several seeds of the same graph per launch on it
     path_multi = None
-    if args.path in ("tile", "tile_tc") and args.multi > 0:
+    if (args.path in ("tile", "tile_tc") or args.multi_form) and args.multi > 0:
         kk = min(args.multi, 8)
+        if args.multi_form:
+            native.mis_set_multi_form(h, {"rows": native.MIS_MULTI_ROWS,
+                                          "rows_tc": native.MIS_MULTI_ROWS_TC}[args.multi_form])
         mout = torch.empty(max(kk * n, 1), dtype=torch.uint8, device="cuda")
         mseeds = np.arange(1, kk + 1, dtype=np.uint64)
         flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
@@ -709,6 +712,10 @@ def tc_leg(args, native, local, world, workload="grid"):
     names = {native.MIS_TILE_BITS: "bits_fp16", native.MIS_TILE_BITS_B1: "b1",
              native.MIS_TILE_INT8: "int8", native.MIS_TILE_FP16: "fp16"}
     same = same_rows_tc
+    res["autotune_multi_form"] = {native.MIS_MULTI_ROWS: "csr",
+                                  native.MIS_MULTI_ROWS_TC: "rows_tc_b1"}[
+        native.mis_autotune_multi(h, 8, 3)]
+    native.mis_set_multi_form(h, native.MIS_MULTI_ROWS)
     for p, nm in names.items():
         native.mis_set_tile_payload(h, p)
         native.mis_set_path(h, native.MIS_PATH_TILE_TC, 16)
@@ -1037,6 +1044,10 @@ def main():
                     help="skip the solve on a graph with create-time round-0 structures")
     ap.add_argument("--multi", type=int, default=8,
                     help="also time this many seeds of the graph per launch (0 = off)")
+    ap.add_argument("--multi-form", choices=["rows", "rows_tc"], default=None,
+                    help="with --multi: also time that many seeds per launch on the full-row "
+                         "graph in this multi-seed form (rows: CUDA cores; rows_tc: the "
+                         "exclusion on tensor cores over 16 x 16 bitmask tiles)")
     args = ap.parse_args()
     if args.legs is None:
         args.legs = "batch,serve,tc" if args.workload == "rmat22" else ""

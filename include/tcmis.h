@@ -272,6 +272,16 @@ enum {
 };
 int mis_set_multi_form(mis_graph *g, int32_t form);
 
+/* Autotuner for the form above: times mis_solve_multi_ex with k seeds (1 ..
+ * k; median of `reps` launches, reps <= 0 means 3) in each form the graph can
+ * take, keeps the faster for later multi-seed solves on `g` and returns it in
+ * *form (may be NULL).  A graph that cannot take MIS_MULTI_ROWS_TC (see above)
+ * gets MIS_MULTI_ROWS without timing.  Allocates k * n bytes of device output
+ * for the timing and frees it.  Blocks the calling thread.  MIS_EINVAL for a
+ * batch or k outside [1, 8], MIS_EBUSY while served requests on `g` are in
+ * flight. */
+int mis_autotune_multi(mis_graph *g, int32_t k, int32_t reps, int32_t *form);
+
 /*
  * Captured solves (no counterpart in the paper: launch-overhead removal for
  * repeated solves, e.g. a batched union solved again and again).

@@ -1399,6 +1399,82 @@ int mis_set_multi_form(mis_graph* g, int32_t form) {
     return MIS_OK;
 }
 
+int mis_autotune_multi(mis_graph* g, int32_t k, int32_t reps, int32_t* form) {
+    clear_error();
+    if (!g) return set_error(MIS_EINVAL, "null graph");
+    if (k < 1 || k > kMaxMulti) return set_error(MIS_EINVAL, "k must be in [1, 8]");
+    if (g->d.count != 0) return set_error(MIS_EINVAL, "multi-seed solves take a single graph");
+    if (reps <= 0) reps = 3;
+    GraphData& d = g->d;
+    bool tc_ok;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (g->inflight.load() > 0) return set_error(MIS_EBUSY, "served requests in flight");
+        tc_ok = d.n > 0 && !d.r0class && !d.out0 && !d.s0_col && g->path != MIS_PATH_TILE_TC &&
+                !(g->path == MIS_PATH_TILE && d.tiles.T != 16);
+        if (!tc_ok) g->multi_form = MIS_MULTI_ROWS;
+    }
+    if (!tc_ok) {
+        if (form) *form = MIS_MULTI_ROWS;
+        return MIS_OK;
+    }
+    cudaError_t e = cudaSetDevice(d.device);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaSetDevice");
+    int64_t scratch_bytes = 0;
+    uint8_t* out = nullptr;
+    if ((e = dalloc(&out, (int64_t)k * d.n, &scratch_bytes)) != cudaSuccess)
+        return set_cuda_error(e, "autotune output");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    uint64_t seeds[kMaxMulti];
+    for (int i = 0; i < kMaxMulti; ++i) seeds[i] = (uint64_t)i + 1;
+    const cudaStream_t s = g->own_stream;
+    const int32_t forms[2] = {MIS_MULTI_ROWS, MIS_MULTI_ROWS_TC};
+    float best_ms = 0.f;
+    int32_t best = MIS_MULTI_ROWS;
+    int rc = MIS_OK;
+    for (int f = 0; f < 2 && rc == MIS_OK; ++f) {
+        {
+            std::lock_guard<std::mutex> lk(g->mu);
+            g->multi_form = forms[f];
+        }
+        // the first solve builds what the form needs (tiles, bit vectors)
+        rc = mis_solve_multi_ex(g, k, seeds, out, s);
+        std::vector<float> ms;
+        for (int r = 0; r < reps && rc == MIS_OK; ++r) {
+            cudaEventRecord(e0, s);
+            rc = mis_solve_multi_ex(g, k, seeds, out, s);
+            cudaEventRecord(e1, s);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                rc = set_cuda_error(e, "autotune timing");
+                break;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms.push_back(t);
+        }
+        if (rc != MIS_OK) break;
+        std::sort(ms.begin(), ms.end());
+        const float med = ms[ms.size() / 2];
+        if (f == 0 || med < best_ms) {
+            best_ms = med;
+            best = forms[f];
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dfree(out);
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        g->multi_form = rc == MIS_OK ? best : MIS_MULTI_ROWS;
+    }
+    if (rc != MIS_OK) return rc;
+    if (form) *form = best;
+    return MIS_OK;
+}
+
 int mis_set_csr_range0(mis_graph* g, int32_t on) {
     clear_error();
     if (!g) return set_error(MIS_EINVAL, "null graph");

@@ -126,7 +126,7 @@ __shared__ unsigned s_msel;
 // test in each solve that has the row undecided; candidates are marked in.
 // Counts the undecided (vertex, solve) pairs into *alive.
 // kRowsTc (the kernel with the exclusion on tensor cores, below): each
-// candidate also sets its bits in the in-set bits `x.inb4`.
+// candidate also sets its bits in the in-set bits `x.inb4` (while non-null).
 template <int TPR, bool kRowsTc = false>
 __device__ __forceinline__ void select_bin8(const MultiCtx& x, const int4* __restrict__ list,
                                             int cnt, WarpSched& ws, unsigned long long* alive,
@@ -172,7 +172,7 @@ __device__ __forceinline__ void select_bin8(const MultiCtx& x, const int4* __res
                                 if ((cand >> s) & 1u) x.a.out[(long long)s * x.a.n + rec.x] = 1;
                         atomicAdd(&s_msel, (unsigned)__popc(cand));
                     }
-                    if constexpr (kRowsTc) {
+                    if (kRowsTc && x.inb4) {
                         // solve s's bit of v: word 4 (v / 16) + s / 2, bit v % 16 + 16 (s & 1)
                         const int sh = rec.x & 15;
                         uint32_t* wb = x.inb4 + 4LL * (rec.x >> 4);
@@ -484,18 +484,26 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
 //            with its record rebuilt from row_ptr (a graph without
 //            create-time structures has no selection prefixes).
 //
-// A warp takes row blocks gw, gw + W, ... of the list and keeps the next
-// one's tiles, words and row offsets in flight while it multiplies the
-// current one.  The loop ends when the row-block list is empty, i.e. every
-// entry of every solve is decided, so the round count is Algorithm 2's.
-// Graphs with create-time round-0 structures do not take this kernel (the
-// host checks).
+// The product costs the same for a listed row block however few of its
+// 16 x k entries are still undecided, and the scans of the CSR form shrink
+// with them.  So after each Phase 1 the kernel compares the round's undecided
+// pairs with the entries of the listed row blocks: from the first round where
+// fewer than one in kTcMinFill is undecided, Phase 2 is the CSR form's
+// exclusion scan over the (exact) vertex lists for the rest of the solve, and
+// the loop ends when those are empty.  Until then it ends when the row-block
+// list is empty.  Either way every entry of every solve is decided at the
+// end, and the round count is Algorithm 2's.  Graphs with create-time round-0
+// structures do not take this kernel (the host checks).
 
+constexpr int kTcMinFill = 8;  // tensor-core Phase 2 while >= 1 / kTcMinFill entries undecided
 constexpr int kRbKeep = 64;   // row blocks staged per warp before an append
 constexpr int kSvMax = 48;    // survivors staged per warp and bin before an append
-// shared words per warp: 32 gathered tiles (12 words each), the staged row
-// blocks, the staged survivors of each bin
-constexpr int kRtWords = 384 + kRbKeep + kBins * kSvMax;
+// shared words per warp: two buffers of 32 tiles' bits (8 words each), the
+// listed tiles' C segments and slots, the staged row blocks, the staged
+// survivors of each bin
+constexpr int kRtBits = 2 * 32 * 8;
+constexpr int kRtWords = kRtBits + 128 + 32 + kRbKeep + kBins * kSvMax;
+constexpr int kRtSmemBytes = kMultiWarps * kRtWords * 4;
 
 __device__ __forceinline__ uint2 ld_pair8(const uint32_t* word8, int v, int q) {
     return *reinterpret_cast<const uint2*>(word8 + (size_t)kMaxMulti * v + 2 * q);
@@ -505,28 +513,20 @@ __device__ __forceinline__ void st_pair8(uint32_t* word8, int v, int q, uint2 w)
     *reinterpret_cast<uint2*>(word8 + (size_t)kMaxMulti * v + 2 * q) = w;
 }
 
-// What lane l of a warp holds of a row block before its product: the row
-// block's tile range and tile t0 + l of its first pass (bits and column block).
-struct RbLane {
-    int rb, t0, t1;
-    uint4 lo, hi;
-    int cb;  // -1: no tile
-};
-
-__device__ __forceinline__ void rb_issue(const SolveArgs& a, int rb, int t0, int t1, RbLane& L) {
+// Lane l starts the copy of tile t0 + l of a row block (its 32 bytes of bits)
+// into slot l of `buf` and returns the tile's column block (-1: no tile);
+// commits one copy group either way.
+__device__ __forceinline__ int rb_copy(const SolveArgs& a, int t0, int t1, uint32_t* buf) {
     const int t = t0 + (int)lane_id();
-    L.rb = rb;
-    L.t0 = t0;
-    L.t1 = t1;
-    L.cb = -1;
-    L.lo = make_uint4(0u, 0u, 0u, 0u);
-    L.hi = L.lo;
+    int cb = -1;
     if (t < t1) {
-        L.cb = __ldg(a.tcol + t);
-        const uint4* bp = reinterpret_cast<const uint4*>(a.tbits + 4LL * t);
-        L.lo = __ldg(bp);
-        L.hi = __ldg(bp + 1);
+        cb = __ldg(a.tcol + t);
+        const uint64_t* src = a.tbits + 4LL * t;
+        cp_async16(buf + 8 * lane_id(), src);
+        cp_async16(buf + 8 * lane_id() + 4, src + 2);
     }
+    cp_async_commit();
+    return cb;
 }
 
 // Appends a warp's staged survivors of bin j (vertex ids) to the bin's list
@@ -546,10 +546,27 @@ __device__ __forceinline__ void flush_survivors(const SolveArgs& a, const int32_
     __syncwarp();
 }
 
+__device__ __forceinline__ void flush_blocks(const int32_t* keep, int cnt, int* next,
+                                             int32_t* __restrict__ dst) {
+    __syncwarp();
+    const unsigned lane = lane_id();
+    int o = 0;
+    if (lane == 0) o = atomicAdd(next, cnt);
+    o = __shfl_sync(0xFFFFFFFFu, o, 0);
+    for (int k = (int)lane; k < cnt; k += 32) dst[o + k] = keep[k];
+    __syncwarp();
+}
+
 // Phases 2 and 3 over the row-block list `list` (cnt entries).  Lane (g, q)
 // owns rows g and g + 8 in solves 2q and 2q + 1 (the MMA's D fragment).
 // `sw`: the warp's kRtWords words of shared memory.  next_rb / dst_rb: the
 // next row-block list; next_v / dst_v: the next vertex lists, per bin.
+//
+// Warp gw takes list entries gw, gw + W, ... (W warps).  While it multiplies
+// one row block, the next one's bits are on their way into the other shared
+// buffer (cp.async), its words and column blocks into registers, the tile
+// range of the one after and the list entry of the third: each load has a
+// whole row block's work to arrive in.
 __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* word8,
                                                 const uint32_t* inb4,
                                                 const int32_t* __restrict__ list, int cnt,
@@ -561,7 +578,9 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
     const long long nw = (long long)gridDim.x * (blockDim.x / 32);
     const long long gw = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (gw >= cnt) return;
-    int32_t* keep = reinterpret_cast<int32_t*>(sw + 384);
+    uint32_t* cs = sw + kRtBits;
+    int32_t* idx = reinterpret_cast<int32_t*>(cs + 128);
+    int32_t* keep = idx + 32;
     int32_t* sv = keep + kRbKeep;  // kBins x kSvMax
     int nkeep = 0;
     uint32_t nsv = 0;  // survivors staged per bin, 6 bits each (at most kSvMax)
@@ -571,51 +590,63 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
         return cb >= 0 ? __ldcg(reinterpret_cast<const uint4*>(inb4 + 4LL * cb))
                        : make_uint4(0u, 0u, 0u, 0u);
     };
-    RbLane cur;
-    {
-        const int rb = list[gw];
-        rb_issue(a, rb, a.trp[rb], a.trp[rb + 1], cur);
-    }
-    uint4 c = cseg4(cur.cb);
-    int rb_n = -1, t0_n = 0, t1_n = 0;  // the row block after the current one
+    // stage 0: the current row block; 1: the next; 2: the one after
+    int rb0 = list[gw];
+    int t00 = a.trp[rb0], t10 = a.trp[rb0 + 1];
+    const int cb0 = rb_copy(a, t00, t10, sw);
+    uint2 w0 = ld_pair8(word8, rb0 * 16 + g, q), w1 = ld_pair8(word8, rb0 * 16 + g + 8, q);
+    int rb1 = -1, t01 = 0, t11 = 0, rb2 = -1;
     if (gw + nw < cnt) {
-        rb_n = list[gw + nw];
-        t0_n = a.trp[rb_n];
-        t1_n = a.trp[rb_n + 1];
+        rb1 = list[gw + nw];
+        t01 = a.trp[rb1];
+        t11 = a.trp[rb1 + 1];
     }
-    for (long long item = gw; item < cnt; item += nw) {
-        // the next row block's loads go out before this one's product
-        RbLane nxt;
-        nxt.cb = -1;
-        if (rb_n >= 0) rb_issue(a, rb_n, t0_n, t1_n, nxt);
-        // this row block's words and row offsets (row_ptr[16 rb + l], l <= 16)
-        const int rb = cur.rb;
-        const int v0 = rb * 16 + g, v1 = v0 + 8;
-        uint2 w0 = ld_pair8(word8, v0, q), w1 = ld_pair8(word8, v1, q);
-        const int rpv = __ldg(a.rp + min(rb * 16 + (int)min(lane, 16u), a.n));
-        int rb_nn = -1, t0_nn = 0, t1_nn = 0;
-        if (item + 2 * nw < cnt) {
-            rb_nn = list[item + 2 * nw];
-            t0_nn = a.trp[rb_nn];
-            t1_nn = a.trp[rb_nn + 1];
+    if (gw + 2 * nw < cnt) rb2 = list[gw + 2 * nw];
+    uint4 c = cseg4(cb0);
+    int it = 0;
+    for (long long item = gw; item < cnt; item += nw, ++it) {
+        uint32_t* bits = sw + 256 * (it & 1);
+        // ---- the next row block's bits, words and column blocks; the tile
+        // range of the one after; the list entry of the third
+        int cb1 = -1;
+        uint2 w0n = make_uint2(0u, 0u), w1n = w0n;
+        if (rb1 >= 0) {
+            cb1 = rb_copy(a, t01, t11, sw + 256 * ((it + 1) & 1));
+            w0n = ld_pair8(word8, rb1 * 16 + g, q);
+            w1n = ld_pair8(word8, rb1 * 16 + g + 8, q);
+        } else {
+            cp_async_commit();  // one group per row block, for the count below
         }
+        int t02 = 0, t12 = 0;
+        if (rb2 >= 0) {
+            t02 = a.trp[rb2];
+            t12 = a.trp[rb2 + 1];
+        }
+        const int rb3 = item + 3 * nw < cnt ? list[item + 3 * nw] : -1;
+        const int rb = rb0;
+        const int rpv = __ldg(a.rp + min(rb * 16 + (int)min(lane, 16u), a.n));
+
+        // ---- D = A x C of this row block: its bits are the older copy group
+        cp_async_wait<1>();
+        __syncwarp();
         int acc[4] = {0, 0, 0, 0};
-        b1_pass(cur.lo, cur.hi, c, sw, acc);
-        for (int tb = cur.t0 + 32; tb < cur.t1; tb += 32) {  // row blocks of > 32 tiles
+        b1_pass(bits, c, cs, idx, acc);
+        for (int tb = t00 + 32; tb < t10; tb += 32) {  // row blocks of > 32 tiles
             const int t = tb + (int)lane;
-            uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo, cc = lo;
-            if (t < cur.t1) {
+            uint4 cc = make_uint4(0u, 0u, 0u, 0u);
+            if (t < t10) {
                 const uint4* bp = reinterpret_cast<const uint4*>(a.tbits + 4LL * t);
-                lo = __ldg(bp);
-                hi = __ldg(bp + 1);
+                *reinterpret_cast<uint4*>(bits + 8 * lane) = __ldg(bp);
+                *reinterpret_cast<uint4*>(bits + 8 * lane + 4) = __ldg(bp + 1);
                 cc = cseg4(__ldg(a.tcol + t));
             }
-            b1_pass(lo, hi, cc, sw, acc);
+            __syncwarp();
+            b1_pass(bits, cc, cs, idx, acc);
         }
-        // the next row block's C segments go out before this one's update
-        const uint4 c_n = cseg4(nxt.cb);
+        const uint4 c_n = cseg4(cb1);  // the next row block's C segments
 
         // ---- update: undecided entries (the non-candidates) with D > 0 are out
+        const int v0 = rb * 16 + g, v1 = v0 + 8;
         const unsigned und = ((w0.x >> 29) == 1u ? 1u : 0u) | ((w0.y >> 29) == 1u ? 2u : 0u) |
                              ((w1.x >> 29) == 1u ? 4u : 0u) | ((w1.y >> 29) == 1u ? 8u : 0u);
         const unsigned out = und & ((acc[0] > 0 ? 1u : 0u) | (acc[1] > 0 ? 2u : 0u) |
@@ -633,64 +664,69 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
         const unsigned rem = und & ~out;
         if (__any_sync(0xFFFFFFFFu, rem != 0u)) {
             if (lane == 0) keep[nkeep] = rb;
-            ++nkeep;
-            if (nkeep == kRbKeep) {
-                __syncwarp();
-                int o = 0;
-                if (lane == 0) o = atomicAdd(next_rb, nkeep);
-                o = __shfl_sync(0xFFFFFFFFu, o, 0);
-                for (int k = (int)lane; k < nkeep; k += 32) dst_rb[o + k] = keep[k];
-                __syncwarp();
+            if (++nkeep == kRbKeep) {
+                flush_blocks(keep, nkeep, next_rb, dst_rb);
                 nkeep = 0;
             }
-            // rows with an undecided entry in some solve: onto the next vertex list
+            // rows with an undecided entry in some solve: onto the next vertex
+            // list, in their degree bin; lane (g, 0) takes rows g and g + 8
             unsigned r0 = (rem & 3u) != 0u ? 1u : 0u, r1 = (rem & 12u) != 0u ? 1u : 0u;
             r0 |= __shfl_xor_sync(0xFFFFFFFFu, r0, 1);
             r0 |= __shfl_xor_sync(0xFFFFFFFFu, r0, 2);
             r1 |= __shfl_xor_sync(0xFFFFFFFFu, r1, 1);
             r1 |= __shfl_xor_sync(0xFFFFFFFFu, r1, 2);
+            const int b0 = __shfl_sync(0xFFFFFFFFu, rpv, g);
+            const int bm = __shfl_sync(0xFFFFFFFFu, rpv, g + 1);
+            const int b8 = __shfl_sync(0xFFFFFFFFu, rpv, g + 8);
+            const int be = __shfl_sync(0xFFFFFFFFu, rpv, g + 9);
+            int j0 = -1, j1 = -1;
+            if (q == 0 && r0) {
+                j0 = 0;
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int i = g + 8 * half;  // row of the block
-                const int b = __shfl_sync(0xFFFFFFFFu, rpv, i);
-                const int e = __shfl_sync(0xFFFFFFFFu, rpv, i + 1);
-                const bool kp = q == 0 && (half ? r1 : r0) != 0u;
-                int j = -1;
-                if (kp) {
-                    const int deg = e - b;
-                    j = 0;
+                for (int t = 0; t < kBins - 1; ++t) j0 += bm - b0 > a.thr[t];
+            }
+            if (q == 0 && r1) {
+                j1 = 0;
 #pragma unroll
-                    for (int t = 0; t < kBins - 1; ++t) j += deg > a.thr[t];
-                }
+                for (int t = 0; t < kBins - 1; ++t) j1 += be - b8 > a.thr[t];
+            }
+            // one bin for every kept row (the usual case): one pass of staging
+            const int jr = __shfl_sync(0xFFFFFFFFu, j0 >= 0 ? j0 : j1, __ffs(__ballot_sync(
+                                           0xFFFFFFFFu, j0 >= 0 || j1 >= 0)) - 1);
+            const bool one_bin = !__any_sync(0xFFFFFFFFu, (j0 >= 0 && j0 != jr) ||
+                                                               (j1 >= 0 && j1 != jr));
 #pragma unroll
-                for (int bj = 0; bj < kBins; ++bj) {
-                    const unsigned m = __ballot_sync(0xFFFFFFFFu, j == bj);
-                    if (m == 0u) continue;
-                    const int have = (int)((nsv >> (6 * bj)) & 63u);
-                    if (j == bj) sv[bj * kSvMax + have + __popc(m & lanemask_lt())] = rb * 16 + i;
-                    const int now = have + __popc(m);
-                    nsv = (nsv & ~(63u << (6 * bj))) | ((uint32_t)now << (6 * bj));
-                    if (now > kSvMax - 16) {
-                        flush_survivors(a, sv + bj * kSvMax, now, &next_v[bj], dst_v + off[bj]);
-                        nsv &= ~(63u << (6 * bj));
-                    }
+            for (int bj = 0; bj < kBins; ++bj) {
+                if (one_bin && bj != jr) continue;
+                const unsigned m0 = __ballot_sync(0xFFFFFFFFu, j0 == bj);
+                const unsigned m1 = __ballot_sync(0xFFFFFFFFu, j1 == bj);
+                if ((m0 | m1) == 0u) continue;
+                const int have = (int)((nsv >> (6 * bj)) & 63u);
+                int32_t* dst = sv + bj * kSvMax + have;
+                if (j0 == bj) dst[__popc(m0 & lanemask_lt())] = v0;
+                if (j1 == bj) dst[__popc(m0) + __popc(m1 & lanemask_lt())] = v1;
+                const int now = have + __popc(m0) + __popc(m1);
+                nsv = (nsv & ~(63u << (6 * bj))) | ((uint32_t)now << (6 * bj));
+                if (now > kSvMax - 16) {
+                    flush_survivors(a, sv + bj * kSvMax, now, &next_v[bj], dst_v + off[bj]);
+                    nsv &= ~(63u << (6 * bj));
                 }
             }
         }
-        cur = nxt;
+        // ---- shift the stages
+        rb0 = rb1;
+        t00 = t01;
+        t10 = t11;
+        w0 = w0n;
+        w1 = w1n;
         c = c_n;
-        rb_n = rb_nn;
-        t0_n = t0_nn;
-        t1_n = t1_nn;
+        rb1 = rb2;
+        t01 = t02;
+        t11 = t12;
+        rb2 = rb3;
     }
-    if (nkeep) {
-        __syncwarp();
-        int o = 0;
-        if (lane == 0) o = atomicAdd(next_rb, nkeep);
-        o = __shfl_sync(0xFFFFFFFFu, o, 0);
-        for (int k = (int)lane; k < nkeep; k += 32) dst_rb[o + k] = keep[k];
-        __syncwarp();
-    }
+    cp_async_wait<0>();
+    if (nkeep) flush_blocks(keep, nkeep, next_rb, dst_rb);
 #pragma unroll
     for (int bj = 0; bj < kBins; ++bj) {
         const int have = (int)((nsv >> (6 * bj)) & 63u);
@@ -701,15 +737,19 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
 __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
     multi_rows_tc_kernel(const SolveArgs a, uint32_t* word8, uint32_t* inb4, int k,
                          const MultiSeeds seeds) {
-    // 16-byte aligned: rows_tc_exclude packs uint4 tiles into it
-    __shared__ __align__(16) uint32_t s_rt[kMultiWarps][kRtWords];
+    // kRtSmemBytes of dynamic shared memory: kRtWords words per warp
+    extern __shared__ __align__(16) uint32_t s_rt[];
     __shared__ int s_cnt[kBins];
     __shared__ int s_rbcnt;
+    __shared__ int s_tc;  // Phase 2 of this round on tensor cores
     const unsigned nblocks = gridDim.x;
     Ctl* ctl = a.ctl;
     PhaseTimes* times = a.times;
-    MultiCtx x{a, word8, nullptr, k};  // Phase 1 stages nothing here
+    uint32_t* sw = s_rt + (threadIdx.x / 32) * kRtWords;
+    // the CSR form's Phase 2 stages its survivors in the same shared words
+    MultiCtx x{a, word8, reinterpret_cast<int32_t*>(sw), k};
     x.inb4 = inb4;
+    bool tc = true;
     grid_barrier_start();
     if (threadIdx.x < kBins) s_cnt[threadIdx.x] = a.bin_off[threadIdx.x + 1] - a.bin_off[threadIdx.x];
     if (threadIdx.x == 0) s_rbcnt = a.nrb;
@@ -740,7 +780,14 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
     ws.nwarps = (int)(nblocks * (blockDim.x / 32));
     ws.base = 0;
     const int* off = a.bin_off;
-    for (int r = 0; s_rbcnt > 0; ++r) {
+    for (int r = 0;; ++r) {
+        if (tc) {
+            if (s_rbcnt == 0) break;
+        } else {
+            int total = 0;
+            for (int j = 0; j < kBins; ++j) total += s_cnt[j];
+            if (total == 0) break;
+        }
         if (r >= a.max_rounds) {
             if (threadIdx.x == 0) atomicCAS(&ctl->err, 0, kErrInternal);
             return;
@@ -758,15 +805,32 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
         select_at8<16, true>(x, src + off[2], s_cnt[2], late, ws, acc);
         select_at8<4, true>(x, src + off[1], s_cnt[1], late, ws, acc);
         select_at8<1, true>(x, src + off[0], s_cnt[0], late, ws, acc);
+        // every block decides the form of Phase 2 from the same counts
+        const int rbcnt = s_rbcnt;
         if (!grid_barrier(ctl, nblocks, a.spin_cap, [times, rr]() {
                 if (times && rr < kStatRounds) times->t[2 + rr] = global_ns();
+            },
+            [ctl, rr, rbcnt, k, tc]() {
+                const unsigned long long und = __ldcg(&ctl->alive_acc64[rr & 3]);
+                s_tc = tc && und * kTcMinFill >= (unsigned long long)rbcnt * 16ull * k;
             }))
             return;
+        if (tc && !s_tc) {
+            tc = false;  // for the rest of the solve
+            x.inb4 = nullptr;
+        }
 
-        // ---- Phases 2 and 3: exclusion test on tensor cores, update, compaction
-        rows_tc_exclude(a, word8, inb4, (r & 1) ? a.rbl1 : a.rbl0, s_rbcnt,
-                        &ctl->cnt[(r + 1) & 3], (r & 1) ? a.rbl0 : a.rbl1, next, dst,
-                        s_rt[threadIdx.x / 32]);
+        // ---- Phases 2 and 3: exclusion test, update, compaction
+        if (tc) {
+            rows_tc_exclude(a, word8, inb4, (r & 1) ? a.rbl1 : a.rbl0, rbcnt,
+                            &ctl->cnt[(r + 1) & 3], (r & 1) ? a.rbl0 : a.rbl1, next, dst, sw);
+        } else {
+            exclude_at8<32>(x, src + off[4], s_cnt[4], late, ws, &next[4], dst + off[4]);
+            exclude_at8<32>(x, src + off[3], s_cnt[3], late, ws, &next[3], dst + off[3]);
+            exclude_at8<16>(x, src + off[2], s_cnt[2], late, ws, &next[2], dst + off[2]);
+            exclude_at8<4>(x, src + off[1], s_cnt[1], late, ws, &next[1], dst + off[1]);
+            exclude_at8<1>(x, src + off[0], s_cnt[0], late, ws, &next[0], dst + off[0]);
+        }
         const long long extra = r == 0 ? (long long)k * decided0 : 0;
         if (!grid_barrier(
                 ctl, nblocks, a.spin_cap,
@@ -823,13 +887,18 @@ cudaError_t launch_multi_rows_tc_solve(const SolveArgs& a, uint32_t* word8, uint
     void* args[] = {const_cast<SolveArgs*>(&a), &word8, &inb4, &k,
                     const_cast<MultiSeeds*>(&seeds)};
     return cudaLaunchCooperativeKernel((const void*)multi_rows_tc_kernel, dim3(grid),
-                                       dim3(kMultiBlock), args, 0, s);
+                                       dim3(kMultiBlock), args, kRtSmemBytes, s);
 }
 
 int multi_rows_tc_max_coresident_blocks(int device) {
     int per_sm = 0, sms = 0;
+    // above the default 48 KB of dynamic shared memory per block
+    if (cudaFuncSetAttribute((const void*)multi_rows_tc_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kRtSmemBytes) != cudaSuccess)
+        return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)multi_rows_tc_kernel,
-                                                      kMultiBlock, 0) != cudaSuccess)
+                                                      kMultiBlock, kRtSmemBytes) != cudaSuccess)
         return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return 0;

@@ -158,19 +158,32 @@ __device__ __forceinline__ void rowblock_nc(const uint64_t* __restrict__ tbits,
     }
 }
 
-// One pass of up to 32 tiles of a row block on the single-bit MMA, the tiles
-// already gathered by the warp's lanes: lane l holds tile l of the pass (its
-// 32 bytes of bits `lo`, `hi`, and `c`, the C segments of its column block
-// for all eight solves: 16 bytes, solve s's 16 bits at word s / 2, bits
-// 16 (s & 1) ..; zero for lanes without a tile).  Tiles whose segments are
-// zero in every solve add nothing and are dropped (the early exit of Sec.
-// 3.2); the others are packed into the warp's shared buffer `sw` (12 words per
-// tile, 32 tiles) and fed to m16n8k128 eight at a time, accumulating into
-// `acc` (the D fragment of rowblock_nc).  So a row block costs its loads
-// once, whatever its tile count, instead of a dependent load per group of
-// eight tiles.  Warp-uniform.
-__device__ __forceinline__ void b1_pass(const uint4& lo, const uint4& hi, const uint4& c,
-                                        uint32_t* sw, int (&acc)[4]) {
+// Asynchronous 16-byte copy global -> shared (L2 only) and its groups.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// Waits until at most N of this thread's committed groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One pass of up to 32 tiles of a row block on the single-bit MMA.  The
+// tiles' bits sit in the warp's shared buffer `bits` (tile slot l at words
+// 8 l .. 8 l + 7: row i at word i / 2, bits 16 (i & 1) ..), and lane l holds
+// `c`, the C segments of slot l's column block for all eight solves (16
+// bytes: solve s's 16 bits at word s / 2, bits 16 (s & 1) ..; zero for a slot
+// without a tile).  Tiles whose segments are zero in every solve add nothing
+// and are dropped (the early exit of Sec. 3.2); the others are listed in
+// `idx` with their segments in `cs` (4 words each) and fed to m16n8k128
+// eight at a time, accumulating into `acc` (the D fragment of rowblock_nc).
+// Warp-uniform; every lane's part of `bits` must be visible (__syncwarp).
+__device__ __forceinline__ void b1_pass(const uint32_t* bits, const uint4& c, uint32_t* cs,
+                                        int32_t* idx, int (&acc)[4]) {
     const unsigned lane = lane_id();
     const int g = (int)(lane >> 2), q = (int)(lane & 3);
     const bool nz = (c.x | c.y | c.z | c.w) != 0u;
@@ -178,29 +191,28 @@ __device__ __forceinline__ void b1_pass(const uint4& lo, const uint4& hi, const 
     const int m = __popc(bal);
     if (m == 0) return;
     if (nz) {
-        uint32_t* s = sw + 12 * __popc(bal & lanemask_lt());
-        *reinterpret_cast<uint4*>(s) = lo;
-        *reinterpret_cast<uint4*>(s + 4) = hi;
-        *reinterpret_cast<uint4*>(s + 8) = c;
+        const int p = __popc(bal & lanemask_lt());
+        idx[p] = (int32_t)lane;
+        *reinterpret_cast<uint4*>(cs + 4 * p) = c;
     }
     __syncwarp();
     const int sh = 16 * (g & 1);
     for (int k = 0; k < m; k += 8) {
-        // this lane's 32 k-slots: packed tiles k + 2q (bits 0..15) and
-        // k + 2q + 1 (bits 16..31); row i of a tile is at word i / 2
+        // this lane's 32 k-slots: listed tiles k + 2q (bits 0..15) and
+        // k + 2q + 1 (bits 16..31)
         const int ta = k + 2 * q, tc = ta + 1;
         uint32_t a0 = 0, a1 = 0, b0 = 0;
         if (ta < m) {
-            const uint32_t* s = sw + 12 * ta;
+            const uint32_t* s = bits + 8 * idx[ta];
             a0 = (s[g >> 1] >> sh) & 0xFFFFu;
             a1 = (s[(g + 8) >> 1] >> sh) & 0xFFFFu;
-            b0 = (s[8 + (g >> 1)] >> sh) & 0xFFFFu;
+            b0 = (cs[4 * ta + (g >> 1)] >> sh) & 0xFFFFu;
         }
         if (tc < m) {
-            const uint32_t* s = sw + 12 * tc;
+            const uint32_t* s = bits + 8 * idx[tc];
             a0 |= ((s[g >> 1] >> sh) & 0xFFFFu) << 16;
             a1 |= ((s[(g + 8) >> 1] >> sh) & 0xFFFFu) << 16;
-            b0 |= ((s[8 + (g >> 1)] >> sh) & 0xFFFFu) << 16;
+            b0 |= ((cs[4 * tc + (g >> 1)] >> sh) & 0xFFFFu) << 16;
         }
         mma_b1(acc, a0, a1, b0);
     }

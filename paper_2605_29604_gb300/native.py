@@ -151,6 +151,8 @@ def lib():
         L.mis_set_tile_payload.restype = ctypes.c_int
         L.mis_set_multi_form.argtypes = [P, i32]
         L.mis_set_multi_form.restype = ctypes.c_int
+        L.mis_autotune_multi.argtypes = [P, i32, i32, ctypes.POINTER(ctypes.c_int32)]
+        L.mis_autotune_multi.restype = ctypes.c_int
         L.mis_set_csr_range0.argtypes = [P, i32]
         L.mis_set_csr_range0.restype = ctypes.c_int
         L.mis_destroy.argtypes = [P]
@@ -190,7 +192,7 @@ def lib():
 EXPORTED = [
     "mis_options_init", "mis_create", "mis_create_ex", "mis_create_batch", "mis_graph_count",
     "mis_result_size", "mis_solve", "mis_solve_ex", "mis_get_stats", "mis_keys_ex",
-    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_set_csr_range0", "mis_set_tile_payload", "mis_set_multi_form", "mis_tile_payload_ex", "mis_cluster_max_vertices", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
+    "mis_set_path", "mis_set_csr_bins", "mis_set_csr_pending", "mis_set_csr_range0", "mis_set_tile_payload", "mis_set_multi_form", "mis_autotune_multi", "mis_tile_payload_ex", "mis_cluster_max_vertices", "mis_capture", "mis_replay_launch", "mis_replay_destroy", "mis_solve_multi_ex", "mis_tiles_ex", "mis_set_grid", "mis_get_grid", "mis_autotune", "mis_footprint", "mis_destroy", "mis_submit", "mis_poll", "mis_poll_ex", "mis_wait",
     "mis_serve_configure", "mis_serve_shutdown", "mis_last_error", "mis_version",
     "mis_solve_noalloc", "mis_update_edges", "mis_repair", "mis_add_vertices",
 ]
@@ -387,6 +389,13 @@ def mis_set_tile_payload(h, payload):
 
 def mis_set_multi_form(h, form):
     return _check(lib().mis_set_multi_form(h, int(form)))
+
+
+def mis_autotune_multi(h, k=8, reps=3):
+    """Times the multi-seed forms with k seeds, keeps the faster; returns it."""
+    form = ctypes.c_int32(-1)
+    _check(lib().mis_autotune_multi(h, int(k), int(reps), ctypes.byref(form)))
+    return int(form.value)
 
 
 def mis_set_csr_range0(h, on):

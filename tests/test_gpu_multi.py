@@ -228,3 +228,30 @@ def test_multi_rows_tc_refusals():
         check(g, [1, 2], got, st)
     finally:
         native.mis_destroy(h)
+
+
+@pytest.mark.parametrize("name", ["grid", "stencil27", "rmat14", "empty"])
+def test_multi_autotune_form(name):
+    """mis_autotune_multi times both multi-seed forms and keeps one; the
+    solves that follow in that form are bit-exact, and a graph with
+    create-time round-0 structures keeps the CSR-row form untimed."""
+    g = graph(name)
+    h = create(g, order_rows=0)
+    try:
+        form = native.mis_autotune_multi(h, 8, 2)
+        assert form in (native.MIS_MULTI_ROWS, native.MIS_MULTI_ROWS_TC)
+        seeds = [31 + i for i in range(8)]
+        got, st = multi_solve(h, g[0], seeds)
+        if g[0] > 0:
+            assert st.path == (native.MIS_PATH_ROWS_TC if form == native.MIS_MULTI_ROWS_TC
+                               else native.MIS_PATH_CSR)
+        check(g, seeds, got, st)
+    finally:
+        native.mis_destroy(h)
+    h = create(g, order_rows=1)
+    try:
+        assert native.mis_autotune_multi(h, 4, 1) == native.MIS_MULTI_ROWS
+        with pytest.raises(native.MisError):
+            native.mis_autotune_multi(h, 9, 1)
+    finally:
+        native.mis_destroy(h)
