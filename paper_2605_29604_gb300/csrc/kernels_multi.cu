@@ -502,7 +502,7 @@ constexpr int kSvMax = 48;    // survivors staged per warp and bin before an app
 // listed tiles' C segments and slots, the staged row blocks, the staged
 // survivors of each bin
 constexpr int kRtBits = 2 * 32 * 8;
-constexpr int kRtWords = kRtBits + 128 + 32 + kRbKeep + kBins * kSvMax;
+constexpr int kRtWords = kRtBits + 128 + 32 + 16 + kRbKeep + kBins * kSvMax;
 constexpr int kRtSmemBytes = kMultiWarps * kRtWords * 4;
 
 __device__ __forceinline__ uint2 ld_pair8(const uint32_t* word8, int v, int q) {
@@ -580,7 +580,8 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
     if (gw >= cnt) return;
     uint32_t* cs = sw + kRtBits;
     int32_t* idx = reinterpret_cast<int32_t*>(cs + 128);
-    int32_t* keep = idx + 32;
+    uint32_t* sd = reinterpret_cast<uint32_t*>(idx + 32);  // 16 row masks
+    int32_t* keep = reinterpret_cast<int32_t*>(sd + 16);
     int32_t* sv = keep + kRbKeep;  // kBins x kSvMax
     int nkeep = 0;
     uint32_t nsv = 0;  // survivors staged per bin, 6 bits each (at most kSvMax)
@@ -628,9 +629,10 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
 
         // ---- D = A x C of this row block: its bits are the older copy group
         cp_async_wait<1>();
+        if (lane < 16) sd[lane] = 0u;
         __syncwarp();
         int acc[4] = {0, 0, 0, 0};
-        b1_pass(bits, c, cs, idx, acc);
+        b1_pass(bits, c, cs, idx, sd, acc);
         for (int tb = t00 + 32; tb < t10; tb += 32) {  // row blocks of > 32 tiles
             const int t = tb + (int)lane;
             uint4 cc = make_uint4(0u, 0u, 0u, 0u);
@@ -641,16 +643,20 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
                 cc = cseg4(__ldg(a.tcol + t));
             }
             __syncwarp();
-            b1_pass(bits, cc, cs, idx, acc);
+            b1_pass(bits, cc, cs, idx, sd, acc);
         }
+        __syncwarp();  // the sparse tiles' row masks
+        const uint32_t sd0 = sd[g] >> (2 * q), sd8 = sd[g + 8] >> (2 * q);
         const uint4 c_n = cseg4(cb1);  // the next row block's C segments
 
         // ---- update: undecided entries (the non-candidates) with D > 0 are out
         const int v0 = rb * 16 + g, v1 = v0 + 8;
         const unsigned und = ((w0.x >> 29) == 1u ? 1u : 0u) | ((w0.y >> 29) == 1u ? 2u : 0u) |
                              ((w1.x >> 29) == 1u ? 4u : 0u) | ((w1.y >> 29) == 1u ? 8u : 0u);
-        const unsigned out = und & ((acc[0] > 0 ? 1u : 0u) | (acc[1] > 0 ? 2u : 0u) |
-                                    (acc[2] > 0 ? 4u : 0u) | (acc[3] > 0 ? 8u : 0u));
+        const unsigned out = und & ((acc[0] > 0 || (sd0 & 1u) ? 1u : 0u) |
+                                    (acc[1] > 0 || (sd0 & 2u) ? 2u : 0u) |
+                                    (acc[2] > 0 || (sd8 & 1u) ? 4u : 0u) |
+                                    (acc[3] > 0 || (sd8 & 2u) ? 8u : 0u));
         if (out & 3u) {
             if (out & 1u) w0.x = kWordOut;
             if (out & 2u) w0.y = kWordOut;

@@ -172,25 +172,67 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// One pass of up to 32 tiles of a row block on the single-bit MMA.  The
-// tiles' bits sit in the warp's shared buffer `bits` (tile slot l at words
-// 8 l .. 8 l + 7: row i at word i / 2, bits 16 (i & 1) ..), and lane l holds
-// `c`, the C segments of slot l's column block for all eight solves (16
-// bytes: solve s's 16 bits at word s / 2, bits 16 (s & 1) ..; zero for a slot
-// without a tile).  Tiles whose segments are zero in every solve add nothing
-// and are dropped (the early exit of Sec. 3.2); the others are listed in
-// `idx` with their segments in `cs` (4 words each) and fed to m16n8k128
+// Tiles with at most this many arcs are multiplied on CUDA cores (an arc
+// (i, j) adds C_s(j) to row i for every solve s), the rest on the MMA: a
+// sparse tile costs the MMA as much as a dense one.
+constexpr int kSparseTileArcs = 2;
+
+// One pass of up to 32 tiles of a row block.  The tiles' bits sit in the
+// warp's shared buffer `bits` (tile slot l at words 8 l .. 8 l + 7: row i at
+// word i / 2, bits 16 (i & 1) ..), and lane l holds `c`, the C segments of
+// slot l's column block for all eight solves (16 bytes: solve s's 16 bits at
+// word s / 2, bits 16 (s & 1) ..; zero for a slot without a tile).  Tiles
+// whose segments are zero in every solve add nothing and are dropped (the
+// early exit of Sec. 3.2).  Where it lowers the pass's MMA count, tiles of at
+// most kSparseTileArcs arcs are taken by their lane on CUDA cores: for each
+// arc (i, j) the solves s with j in C_s are ORed into the warp's row masks
+// `sd[i]` (bit s).  The others are listed
+// in `idx` with their segments in `cs` (4 words each) and fed to m16n8k128
 // eight at a time, accumulating into `acc` (the D fragment of rowblock_nc).
-// Warp-uniform; every lane's part of `bits` must be visible (__syncwarp).
+// Row (i, s) has a neighbour in C iff acc's entry > 0 or bit s of sd[i] is
+// set.  Warp-uniform; every lane's part of `bits` must be visible
+// (__syncwarp), and sd is cleared by the caller once per row block.
 __device__ __forceinline__ void b1_pass(const uint32_t* bits, const uint4& c, uint32_t* cs,
-                                        int32_t* idx, int (&acc)[4]) {
+                                        int32_t* idx, uint32_t* sd, int (&acc)[4]) {
     const unsigned lane = lane_id();
     const int g = (int)(lane >> 2), q = (int)(lane & 3);
     const bool nz = (c.x | c.y | c.z | c.w) != 0u;
-    const unsigned bal = __ballot_sync(0xFFFFFFFFu, nz);
+    uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+    int arcs = 0;
+    if (nz) {
+        lo = *reinterpret_cast<const uint4*>(bits + 8 * lane);
+        hi = *reinterpret_cast<const uint4*>(bits + 8 * lane + 4);
+        arcs = __popc(lo.x) + __popc(lo.y) + __popc(lo.z) + __popc(lo.w) + __popc(hi.x) +
+               __popc(hi.y) + __popc(hi.z) + __popc(hi.w);
+    }
+    // the split only where it saves an MMA (a warp-uniform choice)
+    const int n_nz = __popc(__ballot_sync(0xFFFFFFFFu, nz));
+    const int n_dense = __popc(__ballot_sync(0xFFFFFFFFu, nz && arcs > kSparseTileArcs));
+    const bool split = (n_dense + 7) / 8 < (n_nz + 7) / 8;
+    const bool dense = nz && (!split || arcs > kSparseTileArcs);
+    if (nz && !dense) {
+        const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            uint32_t x = w[k];
+            while (x) {
+                const int bit = 32 * k + __ffs(x) - 1;
+                x &= x - 1u;
+                const int i = bit >> 4, j = bit & 15;
+                // bit s of m: column j of solve s's segment
+                const uint32_t t0 = (c.x >> j) & 0x10001u, t1 = (c.y >> j) & 0x10001u;
+                const uint32_t t2 = (c.z >> j) & 0x10001u, t3 = (c.w >> j) & 0x10001u;
+                const uint32_t m = ((t0 | (t0 >> 15)) & 3u) | (((t1 | (t1 >> 15)) & 3u) << 2) |
+                                   (((t2 | (t2 >> 15)) & 3u) << 4) |
+                                   (((t3 | (t3 >> 15)) & 3u) << 6);
+                if (m) atomicOr(sd + i, m);
+            }
+        }
+    }
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, dense);
     const int m = __popc(bal);
     if (m == 0) return;
-    if (nz) {
+    if (dense) {
         const int p = __popc(bal & lanemask_lt());
         idx[p] = (int32_t)lane;
         *reinterpret_cast<uint4*>(cs + 4 * p) = c;
