@@ -78,4 +78,6 @@ def test_single_graph_line_with_legs():
     assert s["standalone_check"]["all_equal"] is True
     t = d["tiles_tc"]
     assert t["multi_seed_tc"]["results_equal_csr"] is True
-    assert set(t["multi8_ms"]) == {"csr", "tc_bits_fp16", "tc_b1", "tc_int8", "tc_fp16"}
+    assert set(t["multi8_ms"]) == {"csr", "rows_tc_b1", "tc_bits_fp16", "tc_b1", "tc_int8",
+                                   "tc_fp16"}
+    assert t["autotune_multi_form"] in ("csr", "rows_tc_b1")

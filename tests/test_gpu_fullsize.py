@@ -132,3 +132,35 @@ def test_full_size_grid_tensor_core_forms(payload):
             assert np.array_equal(host[s * n:(s + 1) * n], want.status), s
     finally:
         native.mis_destroy(h)
+
+
+@pytest.mark.parametrize("name", ["grid", "stencil"])
+def test_full_size_multi_rows_tc(name):
+    """Eight seeds per launch with the selection on the CSR rows and the
+    exclusion on tensor cores, as bench.py's tc legs time it (the 2048 x 2048
+    grid and the 160^3 stencil lattice, natural ids, full-row graphs after the
+    autotuner): every solve equals its oracle solve, and the summed rounds and
+    alive sets match."""
+    import torch
+    g = gg.grid2048(seed=3) if name == "grid" else gg.stencil160()
+    n, rp, col = g
+    h = native.mis_create_ex(n, rp, col, 0, native.options(order_rows=0), None)
+    try:
+        native.mis_autotune(h, 3)
+        native.mis_set_multi_form(h, native.MIS_MULTI_ROWS_TC)
+        seeds = np.arange(1, 9, dtype=np.uint64)
+        out = torch.empty(8 * n, dtype=torch.uint8, device="cuda")
+        native.mis_solve_multi_ex(h, seeds, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        st = native.mis_get_stats(h)
+        assert st.path == native.MIS_PATH_ROWS_TC
+        host = out.cpu().numpy()
+        wants = [oracle.solve(n, rp, col, int(s)) for s in seeds]
+        for s, want in enumerate(wants):
+            assert np.array_equal(host[s * n:(s + 1) * n], want.status), s
+        assert st.rounds == max(w.rounds for w in wants)
+        alive = np.zeros(st.rounds, dtype=np.int64)
+        for w in wants:
+            alive[:w.rounds] += np.asarray(w.alive_per_round[:w.rounds], dtype=np.int64)
+        assert list(st.alive_per_round[:st.rounds]) == [int(x) for x in alive]
+    finally:
+        native.mis_destroy(h)
