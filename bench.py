@@ -16,6 +16,9 @@ Workloads (synthetic, seeded; stand-ins for the paper's SuiteSparse graphs):
   er10k      Erdos-Renyi G(10,000, 40,000)
   grid       2048 x 2048 grid + 5% random diagonals, natural ids
   grid_perm  the same grid, permuted ids
+  stencil    160^3 lattice, 27-point stencil, natural ids (dense 16 x 16 tiles)
+  rgg4m      random geometric graph, 2^22 vertices, average degree 10, cell-sorted ids
+             (the geometric family of batch4096 as one graph; dense 16 x 16 tiles)
   batch4096  4096 graphs (log-uniform 64..65,536 vertices, ER / random geometric)
              packed as one block-diagonal union and solved in one launch
   serve      Poisson arrivals of solve requests over a resident pool of 512 graphs
@@ -93,6 +96,10 @@ def make_workload(name):
         return gg.grid2048(seed=3, permute_ids=True), "2048x2048 grid + 5% diagonals, permuted ids"
     if name == "stencil":
         return gg.stencil160(), "160x160x160 lattice, 27-point stencil, natural ids"
+    if name == "rgg4m":
+        return (gg.rgg(1 << 22, 10.0, 7),
+                "random geometric graph, 4,194,304 vertices in the unit square, average degree 10, "
+                "cell-sorted ids")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -387,7 +394,9 @@ def run_single(args):
     path_multi = None
     if (args.path in ("tile", "tile_tc") or args.multi_form) and args.multi > 0:
         kk = min(args.multi, 8)
-        if args.multi_form:
+        if args.multi_form == "auto":
+            native.mis_autotune_multi(h, kk, 3)
+        elif args.multi_form:
             native.mis_set_multi_form(h, {"rows": native.MIS_MULTI_ROWS,
                                           "rows_tc": native.MIS_MULTI_ROWS_TC}[args.multi_form])
         mout = torch.empty(max(kk * n, 1), dtype=torch.uint8, device="cuda")
@@ -541,6 +550,7 @@ def run_single(args):
     if "tc" in legs:
         line["tiles_tc"] = tc_leg(args, native, local, world, "grid")
         line["tiles_tc_stencil"] = tc_leg(args, native, local, world, "stencil")
+        line["tiles_tc_rgg"] = tc_leg(args, native, local, world, "rgg4m")
     if rank == 0 and args.cpu_baseline:
         import oracle
         rate, dt, res, reps = oracle_rate(g, min_seconds=args.cpu_seconds)
@@ -715,6 +725,8 @@ def tc_leg(args, native, local, world, workload="grid"):
     res["autotune_multi_form"] = {native.MIS_MULTI_ROWS: "csr",
                                   native.MIS_MULTI_ROWS_TC: "rows_tc_b1"}[
         native.mis_autotune_multi(h, 8, 3)]
+    res["autotuned_multi8_ms"] = timeit(eight)  # the form and switch point it kept
+    same &= bool(torch.equal(out, ref8))
     native.mis_set_multi_form(h, native.MIS_MULTI_ROWS)
     for p, nm in names.items():
         native.mis_set_tile_payload(h, p)
@@ -1039,15 +1051,17 @@ def main():
     ap.add_argument("--legs", default=None,
                     help="extra legs of the single-graph run, comma separated: batch (the "
                          "4096-graph union), serve (the served pool), tc (tile and tensor-core "
-                         "paths on the grid); default all for rmat22, none otherwise")
+                         "paths on the grid, the stencil lattice and the geometric graph); "
+                         "default all for rmat22, none otherwise")
     ap.add_argument("--no-amortized", dest="amortized", action="store_false",
                     help="skip the solve on a graph with create-time round-0 structures")
     ap.add_argument("--multi", type=int, default=8,
                     help="also time this many seeds of the graph per launch (0 = off)")
-    ap.add_argument("--multi-form", choices=["rows", "rows_tc"], default=None,
+    ap.add_argument("--multi-form", choices=["rows", "rows_tc", "auto"], default=None,
                     help="with --multi: also time that many seeds per launch on the full-row "
                          "graph in this multi-seed form (rows: CUDA cores; rows_tc: the "
-                         "exclusion on tensor cores over 16 x 16 bitmask tiles)")
+                         "exclusion on tensor cores over 16 x 16 bitmask tiles; auto: "
+                         "mis_autotune_multi's choice)")
     args = ap.parse_args()
     if args.legs is None:
         args.legs = "batch,serve,tc" if args.workload == "rmat22" else ""

@@ -260,6 +260,10 @@ int mis_solve_multi_ex(mis_graph *g, int32_t k, const uint64_t *seeds, uint8_t *
  *                      kept by the handle (mis_footprint counts it); a graph
  *                      whose single solves run on 8 x 8 tiles (MIS_PATH_TILE,
  *                      tile size 8) is refused at solve time (MIS_EINVAL).
+ *                      Phase 2 runs on the tensor cores while at least
+ *                      one in eight of the entries of the row blocks still
+ *                      listed is undecided, and as the CSR scan for the rest
+ *                      of the solve (mis_autotune_multi may move that point).
  *                      mis_get_stats reports MIS_PATH_ROWS_TC.
  * Both forms give every solve the set and rounds of its single solve.
  * MIS_MULTI_ROWS_TC takes a single graph created without round-0 structures
@@ -274,8 +278,10 @@ int mis_set_multi_form(mis_graph *g, int32_t form);
 
 /* Autotuner for the form above: times mis_solve_multi_ex with k seeds (1 ..
  * k; median of `reps` launches, reps <= 0 means 3) in each form the graph can
- * take, keeps the faster for later multi-seed solves on `g` and returns it in
- * *form (may be NULL).  A graph that cannot take MIS_MULTI_ROWS_TC (see above)
+ * take -- MIS_MULTI_ROWS_TC with its switch to the CSR scan at three points
+ * (while 1/8, 3/8 or 25/32 of the listed entries are undecided) -- keeps the
+ * fastest for later multi-seed solves on `g` and returns its form in *form
+ * (may be NULL).  mis_set_multi_form restores the default switch point.  A graph that cannot take MIS_MULTI_ROWS_TC (see above)
  * gets MIS_MULTI_ROWS without timing.  Allocates k * n bytes of device output
  * for the timing and frees it.  Blocks the calling thread.  MIS_EINVAL for a
  * batch or k outside [1, 8], MIS_EBUSY while served requests on `g` are in

@@ -1396,6 +1396,7 @@ int mis_set_multi_form(mis_graph* g, int32_t form) {
                          "the tensor-core multi-seed form takes a single graph created "
                          "without round-0 structures (order_rows = 0)");
     g->multi_form = form;
+    g->multi_tc_fill = 32;
     return MIS_OK;
 }
 
@@ -1430,14 +1431,20 @@ int mis_autotune_multi(mis_graph* g, int32_t k, int32_t reps, int32_t* form) {
     uint64_t seeds[kMaxMulti];
     for (int i = 0; i < kMaxMulti; ++i) seeds[i] = (uint64_t)i + 1;
     const cudaStream_t s = g->own_stream;
-    const int32_t forms[2] = {MIS_MULTI_ROWS, MIS_MULTI_ROWS_TC};
+    // the CSR rows, then the tensor-core form with its switch at three fills:
+    // while 1/8, 3/8 or 25/32 of the listed entries are undecided (the last
+    // is in practice round 0 only)
+    const int32_t forms[4] = {MIS_MULTI_ROWS, MIS_MULTI_ROWS_TC, MIS_MULTI_ROWS_TC,
+                              MIS_MULTI_ROWS_TC};
+    const int32_t fills[4] = {32, 32, 96, 200};
     float best_ms = 0.f;
-    int32_t best = MIS_MULTI_ROWS;
+    int32_t best = MIS_MULTI_ROWS, best_fill = 32;
     int rc = MIS_OK;
-    for (int f = 0; f < 2 && rc == MIS_OK; ++f) {
+    for (int f = 0; f < 4 && rc == MIS_OK; ++f) {
         {
             std::lock_guard<std::mutex> lk(g->mu);
             g->multi_form = forms[f];
+            g->multi_tc_fill = fills[f];
         }
         // the first solve builds what the form needs (tiles, bit vectors)
         rc = mis_solve_multi_ex(g, k, seeds, out, s);
@@ -1460,6 +1467,7 @@ int mis_autotune_multi(mis_graph* g, int32_t k, int32_t reps, int32_t* form) {
         if (f == 0 || med < best_ms) {
             best_ms = med;
             best = forms[f];
+            best_fill = fills[f];
         }
     }
     cudaStreamSynchronize(s);
@@ -1469,6 +1477,7 @@ int mis_autotune_multi(mis_graph* g, int32_t k, int32_t reps, int32_t* form) {
     {
         std::lock_guard<std::mutex> lk(g->mu);
         g->multi_form = rc == MIS_OK ? best : MIS_MULTI_ROWS;
+        g->multi_tc_fill = rc == MIS_OK ? best_fill : 32;
     }
     if (rc != MIS_OK) return rc;
     if (form) *form = best;
@@ -1721,7 +1730,7 @@ int mis_solve_multi_ex(mis_graph* g, int32_t k, const uint64_t* seeds, uint8_t* 
             const int maxb = multi_rows_tc_max_coresident_blocks(d.device);
             if (maxb <= 0) return set_error(MIS_EDEVICE, "no co-resident blocks for the kernel");
             const long long want = std::max<long long>(1, ((long long)d.n + 255) / 256);
-            e = launch_multi_rows_tc_solve(a, d.word8, d.inb8, k, ms,
+            e = launch_multi_rows_tc_solve(a, d.word8, d.inb8, k, ms, g->multi_tc_fill,
                                            (int)std::min<long long>(want, maxb), s);
             if (e != cudaSuccess) return set_cuda_error(e, "multi-seed rows-tc kernel launch");
         }

@@ -121,6 +121,8 @@ struct mis_graph {
     tcmis::ClusterPlan cluster;   // cluster path: its launch shape
     int32_t csr_range0 = 1;       // CSR kernel: round 0 tests bin 0 by vertex ranges
     int32_t multi_form = 0;       // multi-seed solves off the tile path (MIS_MULTI_*)
+    int32_t multi_tc_fill = 32;   // MIS_MULTI_ROWS_TC: Phase 2 on tensor cores while at
+                                  // least multi_tc_fill / 256 of the listed entries are undecided
                                   // (graphs without round-0 classes only)
     cudaStream_t own_stream = nullptr;
     cudaStream_t last_stream = nullptr;

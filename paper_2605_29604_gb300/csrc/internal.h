@@ -177,9 +177,12 @@ int multi_max_coresident_blocks(int device);
 // the selection test on the CSR rows of `a` (a graph without create-time
 // round-0 structures), the exclusion test as the single-bit MMA over its
 // 16 x 16 bitmask tiles (a.trp, a.tcol, a.tbits; a.rbl0/1 row-block lists,
-// a.nrb).  inb4: 4 * a.nrb words of in-set bits, 16-byte aligned.
+// a.nrb).  inb4: 4 * a.nrb words of in-set bits, 16-byte aligned.  Phase 2
+// stays on tensor cores while at least tc_fill / 256 of the listed row blocks'
+// entries are undecided (then the CSR scan, for the rest of the solve).
 cudaError_t launch_multi_rows_tc_solve(const SolveArgs& a, uint32_t* word8, uint32_t* inb4, int k,
-                                      const MultiSeeds& seeds, int grid, cudaStream_t s);
+                                      const MultiSeeds& seeds, int tc_fill, int grid,
+                                      cudaStream_t s);
 int multi_rows_tc_max_coresident_blocks(int device);
 
 // kernels_push.cu: the push/decrement form of the rounds (uses the worklist

@@ -488,14 +488,14 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
 // 16 x k entries are still undecided, and the scans of the CSR form shrink
 // with them.  So after each Phase 1 the kernel compares the round's undecided
 // pairs with the entries of the listed row blocks: from the first round where
-// fewer than one in kTcMinFill is undecided, Phase 2 is the CSR form's
+// fewer than tc_fill / 256 of them are undecided, Phase 2 is the CSR form's
 // exclusion scan over the (exact) vertex lists for the rest of the solve, and
-// the loop ends when those are empty.  Until then it ends when the row-block
+// the loop ends when those are empty.  (Where the break-even lies depends on
+// the graph's degree and tile density; the host's autotuner times a few.)  Until then it ends when the row-block
 // list is empty.  Either way every entry of every solve is decided at the
 // end, and the round count is Algorithm 2's.  Graphs with create-time round-0
 // structures do not take this kernel (the host checks).
 
-constexpr int kTcMinFill = 8;  // tensor-core Phase 2 while >= 1 / kTcMinFill entries undecided
 constexpr int kRbKeep = 64;   // row blocks staged per warp before an append
 constexpr int kSvMax = 48;    // survivors staged per warp and bin before an append
 // shared words per warp: two buffers of 32 tiles' bits (8 words each), the
@@ -742,7 +742,7 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
 
 __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
     multi_rows_tc_kernel(const SolveArgs a, uint32_t* word8, uint32_t* inb4, int k,
-                         const MultiSeeds seeds) {
+                         const MultiSeeds seeds, int tc_fill) {
     // kRtSmemBytes of dynamic shared memory: kRtWords words per warp
     extern __shared__ __align__(16) uint32_t s_rt[];
     __shared__ int s_cnt[kBins];
@@ -816,9 +816,9 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
         if (!grid_barrier(ctl, nblocks, a.spin_cap, [times, rr]() {
                 if (times && rr < kStatRounds) times->t[2 + rr] = global_ns();
             },
-            [ctl, rr, rbcnt, k, tc]() {
+            [ctl, rr, rbcnt, k, tc, tc_fill]() {
                 const unsigned long long und = __ldcg(&ctl->alive_acc64[rr & 3]);
-                s_tc = tc && und * kTcMinFill >= (unsigned long long)rbcnt * 16ull * k;
+                s_tc = tc && und * 256ull >= (unsigned long long)rbcnt * 16ull * k * tc_fill;
             }))
             return;
         if (tc && !s_tc) {
@@ -889,9 +889,10 @@ cudaError_t launch_multi_solve(const SolveArgs& a, uint32_t* word8, int k,
 }
 
 cudaError_t launch_multi_rows_tc_solve(const SolveArgs& a, uint32_t* word8, uint32_t* inb4, int k,
-                                      const MultiSeeds& seeds, int grid, cudaStream_t s) {
+                                      const MultiSeeds& seeds, int tc_fill, int grid,
+                                      cudaStream_t s) {
     void* args[] = {const_cast<SolveArgs*>(&a), &word8, &inb4, &k,
-                    const_cast<MultiSeeds*>(&seeds)};
+                    const_cast<MultiSeeds*>(&seeds), &tc_fill};
     return cudaLaunchCooperativeKernel((const void*)multi_rows_tc_kernel, dim3(grid),
                                        dim3(kMultiBlock), args, kRtSmemBytes, s);
 }
