@@ -627,13 +627,20 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
         const int rb = rb0;
         const int rpv = __ldg(a.rp + min(rb * 16 + (int)min(lane, 16u), a.n));
 
+        // undecided entries after Phase 1 (the non-candidates): a row block
+        // without any needs no product and leaves the list
+        const int v0 = rb * 16 + g, v1 = v0 + 8;
+        const unsigned und = ((w0.x >> 29) == 1u ? 1u : 0u) | ((w0.y >> 29) == 1u ? 2u : 0u) |
+                             ((w1.x >> 29) == 1u ? 4u : 0u) | ((w1.y >> 29) == 1u ? 8u : 0u);
+        const bool work = __any_sync(0xFFFFFFFFu, und != 0u);
+
         // ---- D = A x C of this row block: its bits are the older copy group
         cp_async_wait<1>();
         if (lane < 16) sd[lane] = 0u;
         __syncwarp();
         int acc[4] = {0, 0, 0, 0};
-        b1_pass(bits, c, cs, idx, sd, acc);
-        for (int tb = t00 + 32; tb < t10; tb += 32) {  // row blocks of > 32 tiles
+        if (work) b1_pass(bits, c, cs, idx, sd, acc);
+        for (int tb = t00 + 32; work && tb < t10; tb += 32) {  // row blocks of > 32 tiles
             const int t = tb + (int)lane;
             uint4 cc = make_uint4(0u, 0u, 0u, 0u);
             if (t < t10) {
@@ -650,9 +657,6 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
         const uint4 c_n = cseg4(cb1);  // the next row block's C segments
 
         // ---- update: undecided entries (the non-candidates) with D > 0 are out
-        const int v0 = rb * 16 + g, v1 = v0 + 8;
-        const unsigned und = ((w0.x >> 29) == 1u ? 1u : 0u) | ((w0.y >> 29) == 1u ? 2u : 0u) |
-                             ((w1.x >> 29) == 1u ? 4u : 0u) | ((w1.y >> 29) == 1u ? 8u : 0u);
         const unsigned out = und & ((acc[0] > 0 || (sd0 & 1u) ? 1u : 0u) |
                                     (acc[1] > 0 || (sd0 & 2u) ? 2u : 0u) |
                                     (acc[2] > 0 || (sd8 & 1u) ? 4u : 0u) |

@@ -197,17 +197,19 @@ __device__ __forceinline__ void b1_pass(const uint32_t* bits, const uint4& c, ui
     const unsigned lane = lane_id();
     const int g = (int)(lane >> 2), q = (int)(lane & 3);
     const bool nz = (c.x | c.y | c.z | c.w) != 0u;
+    // the split only where it saves an MMA (a warp-uniform choice): never
+    // with at most eight tiles
+    const int n_nz = __popc(__ballot_sync(0xFFFFFFFFu, nz));
     uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
     int arcs = 0;
-    if (nz) {
+    if (n_nz > 8 && nz) {
         lo = *reinterpret_cast<const uint4*>(bits + 8 * lane);
         hi = *reinterpret_cast<const uint4*>(bits + 8 * lane + 4);
         arcs = __popc(lo.x) + __popc(lo.y) + __popc(lo.z) + __popc(lo.w) + __popc(hi.x) +
                __popc(hi.y) + __popc(hi.z) + __popc(hi.w);
     }
-    // the split only where it saves an MMA (a warp-uniform choice)
-    const int n_nz = __popc(__ballot_sync(0xFFFFFFFFu, nz));
-    const int n_dense = __popc(__ballot_sync(0xFFFFFFFFu, nz && arcs > kSparseTileArcs));
+    const int n_dense =
+        n_nz > 8 ? __popc(__ballot_sync(0xFFFFFFFFu, nz && arcs > kSparseTileArcs)) : n_nz;
     const bool split = (n_dense + 7) / 8 < (n_nz + 7) / 8;
     const bool dense = nz && (!split || arcs > kSparseTileArcs);
     if (nz && !dense) {
