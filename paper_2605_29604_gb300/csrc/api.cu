@@ -1730,7 +1730,10 @@ int mis_solve_multi_ex(mis_graph* g, int32_t k, const uint64_t* seeds, uint8_t* 
             const int maxb = multi_rows_tc_max_coresident_blocks(d.device);
             if (maxb <= 0) return set_error(MIS_EDEVICE, "no co-resident blocks for the kernel");
             const long long want = std::max<long long>(1, ((long long)d.n + 255) / 256);
-            e = launch_multi_rows_tc_solve(a, d.word8, d.inb8, k, ms, g->multi_tc_fill,
+            // the sparse-tile split pays only where a row block's tiles
+            // take more than one MMA (more than eight tiles on average)
+            const bool split = d.tiles.ntiles > 8LL * d.tiles.nrb;
+            e = launch_multi_rows_tc_solve(a, d.word8, d.inb8, k, ms, g->multi_tc_fill, split,
                                            (int)std::min<long long>(want, maxb), s);
             if (e != cudaSuccess) return set_cuda_error(e, "multi-seed rows-tc kernel launch");
         }

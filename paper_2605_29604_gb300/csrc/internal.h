@@ -180,8 +180,10 @@ int multi_max_coresident_blocks(int device);
 // a.nrb).  inb4: 4 * a.nrb words of in-set bits, 16-byte aligned.  Phase 2
 // stays on tensor cores while at least tc_fill / 256 of the listed row blocks'
 // entries are undecided (then the CSR scan, for the rest of the solve).
+// split: sparse tiles on CUDA cores where that saves an MMA (worth it only
+// where row blocks have more than eight tiles).
 cudaError_t launch_multi_rows_tc_solve(const SolveArgs& a, uint32_t* word8, uint32_t* inb4, int k,
-                                      const MultiSeeds& seeds, int tc_fill, int grid,
+                                      const MultiSeeds& seeds, int tc_fill, bool split, int grid,
                                       cudaStream_t s);
 int multi_rows_tc_max_coresident_blocks(int device);
 

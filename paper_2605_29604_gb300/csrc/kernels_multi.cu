@@ -567,6 +567,7 @@ __device__ __forceinline__ void flush_blocks(const int32_t* keep, int cnt, int* 
 // buffer (cp.async), its words and column blocks into registers, the tile
 // range of the one after and the list entry of the third: each load has a
 // whole row block's work to arrive in.
+template <bool kSplit>
 __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* word8,
                                                 const uint32_t* inb4,
                                                 const int32_t* __restrict__ list, int cnt,
@@ -636,10 +637,10 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
 
         // ---- D = A x C of this row block: its bits are the older copy group
         cp_async_wait<1>();
-        if (lane < 16) sd[lane] = 0u;
+        if (kSplit && lane < 16) sd[lane] = 0u;
         __syncwarp();
         int acc[4] = {0, 0, 0, 0};
-        if (work) b1_pass(bits, c, cs, idx, sd, acc);
+        if (work) b1_pass<kSplit>(bits, c, cs, idx, sd, acc);
         for (int tb = t00 + 32; work && tb < t10; tb += 32) {  // row blocks of > 32 tiles
             const int t = tb + (int)lane;
             uint4 cc = make_uint4(0u, 0u, 0u, 0u);
@@ -650,10 +651,14 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
                 cc = cseg4(__ldg(a.tcol + t));
             }
             __syncwarp();
-            b1_pass(bits, cc, cs, idx, sd, acc);
+            b1_pass<kSplit>(bits, cc, cs, idx, sd, acc);
         }
-        __syncwarp();  // the sparse tiles' row masks
-        const uint32_t sd0 = sd[g] >> (2 * q), sd8 = sd[g + 8] >> (2 * q);
+        uint32_t sd0 = 0, sd8 = 0;
+        if (kSplit) {
+            __syncwarp();  // the sparse tiles' row masks
+            sd0 = sd[g] >> (2 * q);
+            sd8 = sd[g + 8] >> (2 * q);
+        }
         const uint4 c_n = cseg4(cb1);  // the next row block's C segments
 
         // ---- update: undecided entries (the non-candidates) with D > 0 are out
@@ -744,6 +749,10 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
     }
 }
 
+// kSplit: the exclusion passes take sparse tiles on CUDA cores where that
+// saves an MMA (row blocks of more than eight tiles; the host picks the form
+// from the graph's tiles per row block).
+template <bool kSplit>
 __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
     multi_rows_tc_kernel(const SolveArgs a, uint32_t* word8, uint32_t* inb4, int k,
                          const MultiSeeds seeds, int tc_fill) {
@@ -832,7 +841,7 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
 
         // ---- Phases 2 and 3: exclusion test, update, compaction
         if (tc) {
-            rows_tc_exclude(a, word8, inb4, (r & 1) ? a.rbl1 : a.rbl0, rbcnt,
+            rows_tc_exclude<kSplit>(a, word8, inb4, (r & 1) ? a.rbl1 : a.rbl0, rbcnt,
                             &ctl->cnt[(r + 1) & 3], (r & 1) ? a.rbl0 : a.rbl1, next, dst, sw);
         } else {
             exclude_at8<32>(x, src + off[4], s_cnt[4], late, ws, &next[4], dst + off[4]);
@@ -893,24 +902,30 @@ cudaError_t launch_multi_solve(const SolveArgs& a, uint32_t* word8, int k,
 }
 
 cudaError_t launch_multi_rows_tc_solve(const SolveArgs& a, uint32_t* word8, uint32_t* inb4, int k,
-                                      const MultiSeeds& seeds, int tc_fill, int grid,
+                                      const MultiSeeds& seeds, int tc_fill, bool split, int grid,
                                       cudaStream_t s) {
     void* args[] = {const_cast<SolveArgs*>(&a), &word8, &inb4, &k,
                     const_cast<MultiSeeds*>(&seeds), &tc_fill};
-    return cudaLaunchCooperativeKernel((const void*)multi_rows_tc_kernel, dim3(grid),
-                                       dim3(kMultiBlock), args, kRtSmemBytes, s);
+    const void* fn = split ? (const void*)multi_rows_tc_kernel<true>
+                           : (const void*)multi_rows_tc_kernel<false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kMultiBlock), args, kRtSmemBytes, s);
 }
 
 int multi_rows_tc_max_coresident_blocks(int device) {
-    int per_sm = 0, sms = 0;
-    // above the default 48 KB of dynamic shared memory per block
-    if (cudaFuncSetAttribute((const void*)multi_rows_tc_kernel,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kRtSmemBytes) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)multi_rows_tc_kernel,
-                                                      kMultiBlock, kRtSmemBytes) != cudaSuccess)
-        return 0;
+    int per_sm = 1 << 30, sms = 0;
+    // above the default 48 KB of dynamic shared memory per block; the grid
+    // must fit either form
+    const void* fns[] = {(const void*)multi_rows_tc_kernel<false>,
+                         (const void*)multi_rows_tc_kernel<true>};
+    for (const void* fn : fns) {
+        int p = 0;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kRtSmemBytes) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, fn, kMultiBlock, kRtSmemBytes) !=
+                cudaSuccess)
+            return 0;
+        per_sm = std::min(per_sm, p);
+    }
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return 0;
     return per_sm * sms;

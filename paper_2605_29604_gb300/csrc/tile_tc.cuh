@@ -183,15 +183,16 @@ constexpr int kSparseTileArcs = 2;
 // slot l's column block for all eight solves (16 bytes: solve s's 16 bits at
 // word s / 2, bits 16 (s & 1) ..; zero for a slot without a tile).  Tiles
 // whose segments are zero in every solve add nothing and are dropped (the
-// early exit of Sec. 3.2).  Where it lowers the pass's MMA count, tiles of at
-// most kSparseTileArcs arcs are taken by their lane on CUDA cores: for each
-// arc (i, j) the solves s with j in C_s are ORed into the warp's row masks
-// `sd[i]` (bit s).  The others are listed
+// early exit of Sec. 3.2).  With kSplit, where it lowers the pass's MMA
+// count, tiles of at most kSparseTileArcs arcs are taken by their lane on CUDA
+// cores: for each arc (i, j) the solves s with j in C_s are ORed into the
+// warp's row masks `sd[i]` (bit s).  The others are listed
 // in `idx` with their segments in `cs` (4 words each) and fed to m16n8k128
 // eight at a time, accumulating into `acc` (the D fragment of rowblock_nc).
 // Row (i, s) has a neighbour in C iff acc's entry > 0 or bit s of sd[i] is
 // set.  Warp-uniform; every lane's part of `bits` must be visible
 // (__syncwarp), and sd is cleared by the caller once per row block.
+template <bool kSplit>
 __device__ __forceinline__ void b1_pass(const uint32_t* bits, const uint4& c, uint32_t* cs,
                                         int32_t* idx, uint32_t* sd, int (&acc)[4]) {
     const unsigned lane = lane_id();
@@ -199,7 +200,7 @@ __device__ __forceinline__ void b1_pass(const uint32_t* bits, const uint4& c, ui
     const bool nz = (c.x | c.y | c.z | c.w) != 0u;
     // the split only where it saves an MMA (a warp-uniform choice): never
     // with at most eight tiles
-    const int n_nz = __popc(__ballot_sync(0xFFFFFFFFu, nz));
+    const int n_nz = kSplit ? __popc(__ballot_sync(0xFFFFFFFFu, nz)) : 0;
     uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
     int arcs = 0;
     if (n_nz > 8 && nz) {
@@ -211,8 +212,8 @@ __device__ __forceinline__ void b1_pass(const uint32_t* bits, const uint4& c, ui
     const int n_dense =
         n_nz > 8 ? __popc(__ballot_sync(0xFFFFFFFFu, nz && arcs > kSparseTileArcs)) : n_nz;
     const bool split = (n_dense + 7) / 8 < (n_nz + 7) / 8;
-    const bool dense = nz && (!split || arcs > kSparseTileArcs);
-    if (nz && !dense) {
+    const bool dense = nz && (!kSplit || !split || arcs > kSparseTileArcs);
+    if (kSplit && nz && !dense) {
         const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
