@@ -560,7 +560,9 @@ __device__ __forceinline__ void flush_blocks(const int32_t* keep, int cnt, int* 
 // Phases 2 and 3 over the row-block list `list` (cnt entries).  Lane (g, q)
 // owns rows g and g + 8 in solves 2q and 2q + 1 (the MMA's D fragment).
 // `sw`: the warp's kRtWords words of shared memory.  next_rb / dst_rb: the
-// next row-block list; next_v / dst_v: the next vertex lists, per bin.
+// next row-block list; next_v / dst_v: the next vertex lists, per bin;
+// one_bin: the bin of every row of degree >= 1 when only one bin is in use,
+// else -1.
 //
 // Warp gw takes list entries gw, gw + W, ... (W warps).  While it multiplies
 // one row block, the next one's bits are on their way into the other shared
@@ -573,7 +575,7 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
                                                 const int32_t* __restrict__ list, int cnt,
                                                 int* next_rb, int32_t* __restrict__ dst_rb,
                                                 int* next_v, int4* __restrict__ dst_v,
-                                                uint32_t* sw) {
+                                                uint32_t* sw, int one_bin) {
     const unsigned lane = lane_id();
     const int g = (int)(lane >> 2), q = (int)(lane & 3);
     const long long nw = (long long)gridDim.x * (blockDim.x / 32);
@@ -626,7 +628,7 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
         }
         const int rb3 = item + 3 * nw < cnt ? list[item + 3 * nw] : -1;
         const int rb = rb0;
-        const int rpv = __ldg(a.rp + min(rb * 16 + (int)min(lane, 16u), a.n));
+        const int rpv = one_bin >= 0 ? 0 : __ldg(a.rp + min(rb * 16 + (int)min(lane, 16u), a.n));
 
         // undecided entries after Phase 1 (the non-candidates): a row block
         // without any needs no product and leaves the list
@@ -684,35 +686,44 @@ __device__ __forceinline__ void rows_tc_exclude(const SolveArgs& a, uint32_t* wo
                 nkeep = 0;
             }
             // rows with an undecided entry in some solve: onto the next vertex
-            // list, in their degree bin; lane (g, 0) takes rows g and g + 8
-            unsigned r0 = (rem & 3u) != 0u ? 1u : 0u, r1 = (rem & 12u) != 0u ? 1u : 0u;
-            r0 |= __shfl_xor_sync(0xFFFFFFFFu, r0, 1);
-            r0 |= __shfl_xor_sync(0xFFFFFFFFu, r0, 2);
-            r1 |= __shfl_xor_sync(0xFFFFFFFFu, r1, 1);
-            r1 |= __shfl_xor_sync(0xFFFFFFFFu, r1, 2);
-            const int b0 = __shfl_sync(0xFFFFFFFFu, rpv, g);
-            const int bm = __shfl_sync(0xFFFFFFFFu, rpv, g + 1);
-            const int b8 = __shfl_sync(0xFFFFFFFFu, rpv, g + 8);
-            const int be = __shfl_sync(0xFFFFFFFFu, rpv, g + 9);
+            // list, in their degree bin; lane (g, 0) takes rows g and g + 8,
+            // which keep an entry iff some lane (g, q) does
+            const unsigned k0 = __ballot_sync(0xFFFFFFFFu, (rem & 3u) != 0u);
+            const unsigned k1 = __ballot_sync(0xFFFFFFFFu, (rem & 12u) != 0u);
+            const bool r0 = q == 0 && ((k0 >> (lane & ~3u)) & 0xFu) != 0u;
+            const bool r1 = q == 0 && ((k1 >> (lane & ~3u)) & 0xFu) != 0u;
             int j0 = -1, j1 = -1;
-            if (q == 0 && r0) {
-                j0 = 0;
+            if (one_bin >= 0) {
+                // every row of degree >= 1 in one bin: no degrees needed
+                j0 = r0 ? one_bin : -1;
+                j1 = r1 ? one_bin : -1;
+            } else {
+                const int b0 = __shfl_sync(0xFFFFFFFFu, rpv, g);
+                const int bm = __shfl_sync(0xFFFFFFFFu, rpv, g + 1);
+                const int b8 = __shfl_sync(0xFFFFFFFFu, rpv, g + 8);
+                const int be = __shfl_sync(0xFFFFFFFFu, rpv, g + 9);
+                if (r0) {
+                    j0 = 0;
 #pragma unroll
-                for (int t = 0; t < kBins - 1; ++t) j0 += bm - b0 > a.thr[t];
-            }
-            if (q == 0 && r1) {
-                j1 = 0;
+                    for (int t = 0; t < kBins - 1; ++t) j0 += bm - b0 > a.thr[t];
+                }
+                if (r1) {
+                    j1 = 0;
 #pragma unroll
-                for (int t = 0; t < kBins - 1; ++t) j1 += be - b8 > a.thr[t];
+                    for (int t = 0; t < kBins - 1; ++t) j1 += be - b8 > a.thr[t];
+                }
             }
             // one bin for every kept row (the usual case): one pass of staging
-            const int jr = __shfl_sync(0xFFFFFFFFu, j0 >= 0 ? j0 : j1, __ffs(__ballot_sync(
-                                           0xFFFFFFFFu, j0 >= 0 || j1 >= 0)) - 1);
-            const bool one_bin = !__any_sync(0xFFFFFFFFu, (j0 >= 0 && j0 != jr) ||
-                                                               (j1 >= 0 && j1 != jr));
+            int jr = one_bin;
+            bool single = one_bin >= 0;
+            if (!single) {
+                jr = __shfl_sync(0xFFFFFFFFu, j0 >= 0 ? j0 : j1,
+                                 __ffs(__ballot_sync(0xFFFFFFFFu, j0 >= 0 || j1 >= 0)) - 1);
+                single = !__any_sync(0xFFFFFFFFu, (j0 >= 0 && j0 != jr) || (j1 >= 0 && j1 != jr));
+            }
 #pragma unroll
             for (int bj = 0; bj < kBins; ++bj) {
-                if (one_bin && bj != jr) continue;
+                if (single && bj != jr) continue;
                 const unsigned m0 = __ballot_sync(0xFFFFFFFFu, j0 == bj);
                 const unsigned m1 = __ballot_sync(0xFFFFFFFFu, j1 == bj);
                 if ((m0 | m1) == 0u) continue;
@@ -765,6 +776,11 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
     Ctl* ctl = a.ctl;
     PhaseTimes* times = a.times;
     uint32_t* sw = s_rt + (threadIdx.x / 32) * kRtWords;
+    // the one degree bin in use, if there is only one (-1: several)
+    int one_bin = -1;
+    for (int j = 0; j < kBins; ++j)
+        if (a.bin_off[j + 1] > a.bin_off[j]) one_bin = one_bin == -1 ? j : -2;
+    if (one_bin < 0) one_bin = -1;
     // the CSR form's Phase 2 stages its survivors in the same shared words
     MultiCtx x{a, word8, reinterpret_cast<int32_t*>(sw), k};
     x.inb4 = inb4;
@@ -842,7 +858,8 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
         // ---- Phases 2 and 3: exclusion test, update, compaction
         if (tc) {
             rows_tc_exclude<kSplit>(a, word8, inb4, (r & 1) ? a.rbl1 : a.rbl0, rbcnt,
-                            &ctl->cnt[(r + 1) & 3], (r & 1) ? a.rbl0 : a.rbl1, next, dst, sw);
+                            &ctl->cnt[(r + 1) & 3], (r & 1) ? a.rbl0 : a.rbl1, next, dst, sw,
+                            one_bin);
         } else {
             exclude_at8<32>(x, src + off[4], s_cnt[4], late, ws, &next[4], dst + off[4]);
             exclude_at8<32>(x, src + off[3], s_cnt[3], late, ws, &next[3], dst + off[3]);
