@@ -500,7 +500,7 @@ def run_single(args):
                        "mis_destroy"}
 
     peak, peak_kind = _peak_hbm()
-    # SURVEY-defined one-read volume of the CSR: every arc and row pointer once
+    # the one-read volume of the CSR (B0): every arc and row pointer once
     b0 = 4 * arcs + 4 * (n + 1)
     achieved = b0 / launch_s / 1e9
     traffic = args.traffic
