@@ -490,11 +490,17 @@ __global__ void __launch_bounds__(kMultiBlock, kMultiMinBlocksPerSm)
 // pairs with the entries of the listed row blocks: from the first round where
 // fewer than tc_fill / 256 of them are undecided, Phase 2 is the CSR form's
 // exclusion scan over the (exact) vertex lists for the rest of the solve, and
-// the loop ends when those are empty.  (Where the break-even lies depends on
-// the graph's degree and tile density; the host's autotuner times a few.)  Until then it ends when the row-block
-// list is empty.  Either way every entry of every solve is decided at the
-// end, and the round count is Algorithm 2's.  Graphs with create-time round-0
-// structures do not take this kernel (the host checks).
+// the loop ends when those are empty; until then it ends when the row-block
+// list is empty.  (Where the break-even lies depends on the graph's degree and
+// tile density; the host's autotuner times a few fills.)  Either way every
+// entry of every solve is decided at the end, and the round count is
+// Algorithm 2's.  Graphs with create-time round-0 structures do not take this
+// kernel (the host checks).
+//
+// A warp takes row blocks gw, gw + W, ... of the list; each tile of a row
+// block goes to one lane, whose bits arrive by cp.async a row block ahead.
+// Where only one degree bin is in use, survivors are staged without their
+// row degrees.
 
 constexpr int kRbKeep = 64;   // row blocks staged per warp before an append
 constexpr int kSvMax = 48;    // survivors staged per warp and bin before an append
@@ -502,7 +508,7 @@ constexpr int kSvMax = 48;    // survivors staged per warp and bin before an app
 // listed tiles' C segments and slots, the staged row blocks, the staged
 // survivors of each bin
 constexpr int kRtBits = 2 * 32 * 8;
-constexpr int kRtWords = kRtBits + 128 + 32 + 16 + kRbKeep + kBins * kSvMax;
+constexpr int kRtWords = kRtBits + 128 + 32 + 16 + kRbKeep + kBins * kSvMax;  // + 16 row masks
 constexpr int kRtSmemBytes = kMultiWarps * kRtWords * 4;
 
 __device__ __forceinline__ uint2 ld_pair8(const uint32_t* word8, int v, int q) {
